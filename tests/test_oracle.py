@@ -1,0 +1,354 @@
+"""Pins for the FP64 oracle: it is checked against what the paper and the
+mathematics fix -- closed forms, invariants, library routines and brute force
+on tiny inputs -- never against itself or the CUDA path."""
+import os
+
+import numpy as np
+import pytest
+import scipy.optimize
+import scipy.stats
+
+import oracle
+from paper_1707_09094_gb300 import synth
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _rand_model(rng, G, D, spread=3.0):
+    means = rng.normal(0, spread, (G, D))
+    dcovs = rng.uniform(0.3, 2.0, (G, D))
+    hefts = rng.dirichlet(np.ones(G))
+    return means, dcovs, hefts
+
+
+# ---------------------------------------------------------------- Eq. 2 / 15
+def test_log_gauss_matches_scipy_and_bruteforce():
+    rng = np.random.default_rng(1)
+    for D in (1, 3, 7):
+        mu = rng.normal(0, 2, D)
+        var = rng.uniform(0.2, 3.0, D)
+        x = rng.normal(0, 2, D).astype(np.float32)
+        got = oracle.log_gauss(x, mu, var)
+        ref = scipy.stats.multivariate_normal(mean=mu, cov=np.diag(var)).logpdf(x.astype(np.float64))
+        assert got == pytest.approx(ref, rel=1e-13, abs=1e-13)
+        # Eq. 2 written out, non-log, in long double
+        xl = x.astype(np.longdouble)
+        dens = np.prod(1.0 / np.sqrt(2 * np.pi * var.astype(np.longdouble))) * \
+            np.exp(-0.5 * np.sum((xl - mu) ** 2 / var))
+        assert got == pytest.approx(float(np.log(dens)), rel=1e-12, abs=1e-12)
+
+
+# ------------------------------------------------------------- Eqs. 16-18
+def test_log_add_closed_forms():
+    assert oracle.log_add(np.log(2.0), np.log(3.0)) == pytest.approx(np.log(5.0), rel=1e-15)
+    assert oracle.log_add(np.log(3.0), np.log(2.0)) == pytest.approx(np.log(5.0), rel=1e-15)
+    assert oracle.log_add(-np.inf, 1.5) == 1.5
+    assert oracle.log_add(1.5, -np.inf) == 1.5
+    assert oracle.log_add(-np.inf, -np.inf) == -np.inf
+    # far apart: the smaller one vanishes, no overflow from exp of a big gap
+    assert oracle.log_add(-1000.0, 0.0) == 0.0
+    assert oracle.log_add(800.0, 800.0) == pytest.approx(800.0 + np.log(2.0), rel=1e-15)
+
+
+def test_mixture_log_p_bruteforce_and_cross_forms():
+    rng = np.random.default_rng(2)
+    for (N, D, G) in ((20, 1, 1), (30, 2, 3), (40, 4, 4)):
+        m, v, h = _rand_model(rng, G, D, spread=1.0)
+        X = rng.normal(0, 1.5, (N, D)).astype(np.float32)
+        lp = oracle.log_p(X, m, v, h)
+        lp2 = oracle.log_p(X, m, v, h, maxsum=True)
+        np.testing.assert_allclose(lp, lp2, rtol=1e-14, atol=1e-14)
+        # Eq. 1 with Eq. 2, non-log, long double
+        Xl = X.astype(np.longdouble)
+        dens = np.zeros(N, np.longdouble)
+        for g in range(G):
+            norm = np.prod(1.0 / np.sqrt(2 * np.pi * v[g].astype(np.longdouble)))
+            dens += h[g] * norm * np.exp(-0.5 * np.sum((Xl - m[g]) ** 2 / v[g], axis=1))
+        np.testing.assert_allclose(lp, np.log(dens).astype(np.float64), rtol=1e-12, atol=1e-12)
+        # per-Gaussian form: N(x|g) without heft
+        for g in range(G):
+            ref = scipy.stats.multivariate_normal(mean=m[g], cov=np.diag(v[g])).logpdf(
+                X.astype(np.float64))
+            np.testing.assert_allclose(oracle.log_p(X, m, v, h, g=g), np.atleast_1d(ref),
+                                       rtol=1e-12, atol=1e-12)
+        assert oracle.avg_log_p(X, m, v, h) == pytest.approx(lp.mean(), rel=1e-14)
+
+
+def test_log_p_underflow_robust():
+    # Far-away samples: direct densities underflow to 0 in double, the log
+    # domain form stays finite (Sec. 2.2).
+    m = np.array([[0.0], [1.0]])
+    v = np.array([[1e-4], [1e-4]])
+    h = np.array([0.5, 0.5])
+    X = np.array([[500.0]], np.float32)
+    lp = oracle.log_p(X, m, v, h)
+    assert np.isfinite(lp).all()
+    ref = np.logaddexp(np.log(0.5) + scipy.stats.norm(0, 1e-2).logpdf(500.0),
+                       np.log(0.5) + scipy.stats.norm(1, 1e-2).logpdf(500.0))
+    assert lp[0] == pytest.approx(ref, rel=1e-12)
+
+
+# ------------------------------------------------------------------- Eq. 3
+def test_posteriors_sum_to_one_and_bruteforce():
+    rng = np.random.default_rng(3)
+    G, D, N = 4, 3, 50
+    m, v, h = _rand_model(rng, G, D, spread=1.0)
+    X = rng.normal(0, 1.5, (N, D)).astype(np.float32)
+    post = oracle.posteriors(X, m, v, h)
+    np.testing.assert_allclose(post.sum(axis=1), 1.0, atol=1e-15 * G * 4)
+    assert (post >= 0).all() and (post <= 1).all()
+    Xl = X.astype(np.longdouble)
+    num = np.zeros((N, G), np.longdouble)
+    for g in range(G):
+        norm = np.prod(1.0 / np.sqrt(2 * np.pi * v[g].astype(np.longdouble)))
+        num[:, g] = h[g] * norm * np.exp(-0.5 * np.sum((Xl - m[g]) ** 2 / v[g], axis=1))
+    ref = (num / num.sum(axis=1, keepdims=True)).astype(np.float64)
+    np.testing.assert_allclose(post, ref, rtol=1e-12, atol=1e-15)
+
+
+# ---------------------------------------------------------------- Eqs. 4-14
+def test_single_gaussian_is_sample_mean_and_variance():
+    rng = np.random.default_rng(4)
+    X = (rng.normal(3.0, 2.0, (5000, 6))).astype(np.float32)
+    m0 = np.zeros((1, 6)); v0 = np.ones((1, 6)); h0 = np.ones(1)
+    m, v, h, ll = oracle.em_iterate(X, m0, v0, h0, 1, 1e-10)
+    Xd = X.astype(np.float64)
+    np.testing.assert_allclose(m[0], Xd.mean(axis=0), rtol=1e-12)
+    np.testing.assert_allclose(v[0], Xd.var(axis=0, ddof=0), rtol=1e-10)
+    assert h[0] == pytest.approx(1.0, abs=1e-15)
+    # the likelihood reported is that of the starting parameters
+    ref = scipy.stats.multivariate_normal(mean=np.zeros(6), cov=np.eye(6)).logpdf(Xd).mean()
+    assert ll[0] == pytest.approx(ref, rel=1e-12)
+
+
+def test_mstep_is_weighted_mean_and_variance():
+    rng = np.random.default_rng(5)
+    G, D, N = 3, 4, 3000
+    m0, v0, h0 = _rand_model(rng, G, D, spread=2.0)
+    X = rng.normal(0, 2.0, (N, D)).astype(np.float32)
+    post = oracle.posteriors(X, m0, v0, h0)
+    m, v, h, _ = oracle.em_iterate(X, m0, v0, h0, 1, 0.0)
+    Xd = X.astype(np.float64)
+    for g in range(G):
+        mu = np.average(Xd, axis=0, weights=post[:, g])
+        var = np.average((Xd - mu) ** 2, axis=0, weights=post[:, g])
+        np.testing.assert_allclose(m[g], mu, rtol=1e-11, atol=1e-12)
+        np.testing.assert_allclose(v[g], var, rtol=1e-9)
+    np.testing.assert_allclose(h, post.mean(axis=0), rtol=1e-12)
+    assert h.sum() == pytest.approx(1.0, abs=1e-13)
+
+
+def test_one_pass_matches_two_pass_within_cancellation_bound():
+    X, _, _ = synth.make("c1", N=4000)
+    rng = np.random.default_rng(6)
+    G = 8
+    m0 = X[rng.choice(X.shape[0], G, replace=False)].astype(np.float64)
+    v0 = np.ones((G, X.shape[1])); h0 = np.full(G, 1.0 / G)
+    m1, v1, h1, _ = oracle.em_iterate(X, m0, v0, h0, 1, 1e-10)
+    m2, v2, h2 = oracle.em_step_twopass(X, m0, v0, h0, 1e-10)
+    np.testing.assert_allclose(m1, m2, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(h1, h2, rtol=1e-12)
+    eps = np.finfo(np.float64).eps
+    bound = 64 * eps * (m2 ** 2 + v2)      # one-pass error ~ eps * E[x^2]
+    assert (np.abs(v1 - v2) <= bound).all()
+
+
+def test_mapreduce_chunks_equal_single_pass():
+    X, _, _ = synth.make("c1", N=5000)
+    rng = np.random.default_rng(7)
+    m0 = X[rng.choice(5000, 8, replace=False)].astype(np.float64)
+    v0 = np.ones((8, 10)); h0 = np.full(8, 1 / 8)
+    a = oracle.em_iterate(X, m0, v0, h0, 3, 1e-10, n_chunks=1)
+    b = oracle.em_iterate(X, m0, v0, h0, 3, 1e-10, n_chunks=7)
+    for u, w in zip(a, b):
+        np.testing.assert_allclose(u, w, rtol=1e-11, atol=1e-13)
+
+
+def test_em_loglik_non_decreasing_and_floor():
+    X, _, _ = synth.make("c1", N=20000)
+    rng = np.random.default_rng(8)
+    m0 = X[rng.choice(20000, 8, replace=False)].astype(np.float64)
+    v0 = np.ones((8, 10)); h0 = np.full(8, 1 / 8)
+    m, v, h, ll = oracle.em_iterate(X, m0, v0, h0, 15, 1e-10)
+    assert (np.diff(ll) >= -1e-12 * np.abs(ll[1:])).all()
+    # the final parameters are at least as good as the last E-step's
+    assert oracle.avg_log_p(X, m, v, h) >= ll[-1] - 1e-12 * abs(ll[-1])
+    assert h.sum() == pytest.approx(1.0, abs=1e-12)
+    # floor: a constant dimension gets exactly the floor
+    Xc = X.copy(); Xc[:, 3] = 1.25
+    _, vc, _, _ = oracle.em_iterate(Xc, m0, v0, h0, 3, 1e-3)
+    assert (vc >= 1e-3).all()
+    assert np.allclose(vc[:, 3], 1e-3)
+
+
+def _q_function(X, post, m, v, h):
+    """Appendix A's Q(theta | theta_old) for diagonal Gaussians, FP64."""
+    Xd = X.astype(np.float64)
+    q = 0.0
+    for g in range(m.shape[0]):
+        lg = -0.5 * np.sum(np.log(2 * np.pi * v[g])) - 0.5 * np.sum((Xd - m[g]) ** 2 / v[g], axis=1)
+        q += np.sum(post[:, g] * (np.log(h[g]) + lg))
+    return q
+
+
+def test_mstep_is_stationary_point_of_q():
+    """Appendix A: the M-step solves dQ/dmu = dQ/dsigma = 0 and, with the
+    Lagrange multiplier psi = -N, dQ/dw_m = N for every m."""
+    rng = np.random.default_rng(9)
+    G, D, N = 3, 2, 400
+    m0, v0, h0 = _rand_model(rng, G, D, spread=1.5)
+    X = rng.normal(0, 1.5, (N, D)).astype(np.float32)
+    post = oracle.posteriors(X, m0, v0, h0)
+    m, v, h, _ = oracle.em_iterate(X, m0, v0, h0, 1, 0.0)
+    for g in range(G):
+        for d in range(D):
+            for arr, step in ((m, 1e-5), (v, 1e-6)):
+                p = arr.copy(); p[g, d] += step
+                mm = arr.copy(); mm[g, d] -= step
+                args_p = (p, v, h) if arr is m else (m, p, h)
+                args_m = (mm, v, h) if arr is m else (m, mm, h)
+                grad = (_q_function(X, post, *args_p) - _q_function(X, post, *args_m)) / (2 * step)
+                assert abs(grad) < 1e-5 * N
+    # weights: dQ/dw_g = L_g / w_g equals N for every g
+    L = post.sum(axis=0)
+    np.testing.assert_allclose(L / h, N, rtol=1e-12)
+
+
+def test_zero_responsibility_component_keeps_parameters():
+    X = np.random.default_rng(10).normal(0, 1, (500, 2)).astype(np.float32)
+    m0 = np.array([[0.0, 0.0], [1e4, 1e4]])
+    v0 = np.array([[1.0, 1.0], [1e-6, 1e-6]])
+    h0 = np.array([0.5, 0.5])
+    m, v, h, _ = oracle.em_iterate(X, m0, v0, h0, 1, 1e-10)
+    np.testing.assert_array_equal(m[1], m0[1])
+    np.testing.assert_array_equal(v[1], v0[1])
+    assert h[1] == 0.0 and h[0] == pytest.approx(1.0)
+
+
+# ------------------------------------------------------- Sec. 3 (k-means)
+def test_km_assign_bruteforce():
+    rng = np.random.default_rng(11)
+    X = rng.normal(0, 2, (300, 3)).astype(np.float32)
+    mu = rng.normal(0, 2, (5, 3))
+    w = rng.uniform(0.2, 3, 3)
+    a, b1, b2 = oracle.km_assign(X, mu, w)
+    d = ((X.astype(np.float64)[:, None, :] - mu[None]) ** 2 * w).sum(-1)
+    np.testing.assert_array_equal(a, np.argmin(d, axis=1))
+    np.testing.assert_allclose(b1, d.min(axis=1), rtol=1e-14)
+    np.testing.assert_allclose(b2, np.sort(d, axis=1)[:, 1], rtol=1e-14)
+    # exact tie -> lowest index
+    mu2 = np.array([[1.0, 0, 0], [1.0, 0, 0]])
+    a2, _, _ = oracle.km_assign(X, mu2, w)
+    assert (a2 == 0).all()
+
+
+def test_kmeans_update_is_average_and_objective_non_increasing():
+    X, _, _ = synth.make("c1", N=6000)
+    gm, gv = oracle.global_stats(X)
+    w = 1.0 / gv
+    seeds = synth.seeds_subset(X, 8, 3)
+    prev = np.inf
+    means = seeds
+    Xd = X.astype(np.float64)
+    for it in range(1, 6):
+        m, v, h, a = oracle.kmeans(X, means, w, gv, 1, 1e-10)
+        # update = average of the assigned samples (Sec. 3, step (ii))
+        for g in range(8):
+            sel = a == g
+            if sel.any():
+                np.testing.assert_allclose(m[g], Xd[sel].mean(axis=0), rtol=1e-12, atol=1e-12)
+                np.testing.assert_allclose(v[g], np.maximum(Xd[sel].var(axis=0), 1e-10), rtol=1e-9,
+                                           atol=1e-12)
+                assert h[g] == pytest.approx(sel.mean(), rel=1e-15)
+        obj = sum((((Xd[a == g] - m[g]) ** 2) * w).sum() for g in range(8))
+        assert obj <= prev * (1 + 1e-12)
+        prev = obj
+        means = m
+
+
+def test_kmeans_dead_mean_resurrection():
+    # three samples near 0, two near 10, one seed far from everything -> dead
+    X = np.array([[0.0], [0.1], [0.2], [10.0], [10.1]], np.float32)
+    seeds = np.array([[0.1], [10.05], [1e6]])
+    w = np.ones(1)
+    gv = np.array([25.0])
+    m, v, h, a = oracle.kmeans(X, seeds, w, gv, 1, 1e-10)
+    # the popular mean (index 0, three samples) gives its lowest-index sample
+    assert m[2, 0] == pytest.approx(0.0)
+    assert v[2, 0] == 25.0
+    # hefts: 3/5, 2/5, 1/5, renormalised
+    np.testing.assert_allclose(h, np.array([3, 2, 1]) / 6.0, rtol=1e-15)
+    # one more iteration: the resurrected mean at 0 now wins sample 0 (tie ->
+    # lowest index keeps mean 0 for x=0? mean0 = 0.1, mean2 = 0.0)
+    m2, _, _, a2 = oracle.kmeans(X, m, w, gv, 1, 1e-10)
+    assert a2[0] == 2 and (a2[3:] == 1).all()
+
+
+def test_random_subset_seeding_pins_splitmix64():
+    with open(os.path.join(HERE, "golden", "splitmix64_seed0.txt")) as f:
+        vals = [int(l, 16) for l in f if l.strip() and not l.startswith("#")]
+    N = 1000
+    idx = oracle.seed_random_subset(N, 2, 0)
+    first = vals[0] % N
+    assert idx[0] == first
+    r1 = 1 + vals[1] % (N - 1)
+    assert idx[1] == (0 if r1 == first else r1)
+    big = oracle.seed_random_subset(100000, 256, 12345)
+    assert len(set(big.tolist())) == 256 and big.min() >= 0 and big.max() < 100000
+
+
+def test_global_stats_matches_numpy():
+    X, _, _ = synth.make("c1", N=3000)
+    m, v = oracle.global_stats(X)
+    np.testing.assert_allclose(m, X.astype(np.float64).mean(axis=0), rtol=1e-13)
+    np.testing.assert_allclose(v, X.astype(np.float64).var(axis=0), rtol=1e-12)
+
+
+# ------------------------------------------------------- learn (Sec. 4.1)
+@pytest.mark.parametrize("G", [2, 4, 8])
+def test_recovers_well_separated_mixture(G):
+    # k-means + EM only climbs to a local maximum (Sec. 2), and a random
+    # subset rarely seeds every cluster, so the start is one sample of each
+    # true cluster (keep_existing); k-means and EM must then find the truth.
+    X, lab, mix = synth.separated(8000 * G, 4, G, seed=100 + G)
+    first = [int(np.flatnonzero(lab == k)[0]) for k in range(G)]
+    init = (X[first].astype(np.float64), np.ones((G, 4)), np.full(G, 1.0 / G))
+    m, v, h, ll = oracle.learn(X, G, seed_mode=oracle.SEED_KEEP_EXISTING, km_iter=10,
+                               em_iter=10, init=init)
+    cost = ((m[:, None, :] - mix.means[None]) ** 2).sum(-1)
+    r, c = scipy.optimize.linear_sum_assignment(cost)
+    for g, k in zip(r, c):
+        n = max((lab == k).sum(), 1)
+        tol = 4 * mix.stds[k] / np.sqrt(n)
+        assert (np.abs(m[g] - mix.means[k]) <= tol + 1e-9).all()
+        assert (np.abs(np.sqrt(v[g]) - mix.stds[k]) <= 4 * mix.stds[k] / np.sqrt(n) + 1e-9).all()
+        assert h[g] == pytest.approx((lab == k).mean(), abs=1e-6)
+
+
+def test_fig1_example_program_hefts():
+    X, lab, _ = synth.make("fig1")
+    m, v, h, ll = oracle.learn(X, 2, seed=1, km_iter=10, em_iter=5)
+    order = np.argsort(m[:, 0])
+    assert h[order][0] == pytest.approx(2 / 3, abs=0.05)
+    assert h[order][1] == pytest.approx(1 / 3, abs=0.05)
+
+
+def test_assign_modes():
+    rng = np.random.default_rng(12)
+    m, v, h = _rand_model(rng, 4, 3)
+    X = rng.normal(0, 3, (200, 3)).astype(np.float32)
+    a_e = oracle.assign(X, m, v, h, 0)
+    a_p = oracle.assign(X, m, v, h, 2)
+    Xd = X.astype(np.float64)
+    np.testing.assert_array_equal(a_e, np.argmin(((Xd[:, None] - m[None]) ** 2).sum(-1), axis=1))
+    lt = np.stack([np.log(h[g]) + scipy.stats.multivariate_normal(m[g], np.diag(v[g])).logpdf(Xd)
+                   for g in range(4)], axis=1)
+    np.testing.assert_array_equal(a_p, np.argmax(lt, axis=1))
+
+
+def test_learn_rejects_bad_arguments():
+    X = np.zeros((5, 2), np.float32)
+    with pytest.raises(RuntimeError):
+        oracle.learn(X, 6)
+    with pytest.raises(RuntimeError):
+        oracle.learn(X, 2, var_floor=-1.0)
