@@ -1,0 +1,312 @@
+"""EM throughput benchmark: units = N * N_G * D per EM iteration.
+
+Workload: a seeded synthetic diagonal GMM with N = 2,000,000 samples, D = 60
+(speech-like: 20 base dims + deltas + delta-deltas), N_G = 256; k-means
+initialisation (10 iterations) outside the timed region, then each timed
+step is ONE EM iteration (fused E+M data pass, FP64 reduce, update, floor,
+operands of the next E-step) through the library's C ABI (gmm_em_iterate).
+X (480 MB) is larger than the 129 MB L2, so every step streams it from HBM.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+(the only reference implementation there is) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "EM iters/sec (N·N_G·D/s) at D=60,N_G=256; BF16-TC vs FP32 at stated ΔLL"
+UNIT = "N·N_G·D/s"
+N_FULL, D_FULL, G_FULL = 2_000_000, 60, 256
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if p[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_data():
+    from paper_1707_09094_gb300 import synth
+    X, _, _ = synth.make("c2")
+    return X
+
+
+def cpu_oracle_rate(X, target_s: float = 12.0):
+    """FP64 oracle EM iteration (MapReduce chunks over the host cores) on a
+    bounded prefix of the workload; returns (units/s, cores, sample text)."""
+    import oracle
+    cores = oracle.num_threads()
+    G = G_FULL
+    rng = np.random.default_rng(5)
+    n = 20000
+    start = None
+    while True:
+        Xs = X[:n]
+        if start is None:
+            idx = rng.choice(n, G, replace=False)
+            start = (Xs[idx].astype(np.float64), np.ones((G, X.shape[1])), np.full(G, 1.0 / G))
+        t0 = time.perf_counter()
+        oracle.em_iterate(Xs, *start, 1, 1e-10, n_chunks=cores * 4)
+        dt = time.perf_counter() - t0
+        if dt >= target_s / 4 or n >= X.shape[0]:
+            break
+        n = min(X.shape[0], int(n * max(2.0, target_s / 4 / max(dt, 1e-3))))
+    units = n * G * X.shape[1]
+    return units / dt, cores, "1 FP64 EM iteration on the first %d of %d samples (D=%d, N_G=%d), %d OpenMP " \
+                              "threads, %.2f s" % (n, X.shape[0], X.shape[1], G, cores, dt)
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    X = make_data()
+    vals = []
+    info = None
+    for k in range(args.warmup + args.steps):
+        rate, cores, sample = cpu_oracle_rate(X, target_s=max(2.0, 60.0 / max(args.steps + args.warmup, 1)))
+        if k >= args.warmup:
+            vals.append(rate)
+            info = (cores, sample)
+    v = statistics.median(vals)
+    units_per_iter = N_FULL * G_FULL * D_FULL
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * units_per_iter / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "c2 EM iteration: N=2000000 D=60 N_G=256 (FP64 CPU oracle, bounded prefix, "
+                                   "scaled per unit)", "N": N_FULL, "D": D_FULL, "N_G": G_FULL},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": info[0], "kind": "oracle", "sample": info[1]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1707_09094_gb300 import GMM, build
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    build.build()
+    X = make_data()
+    Xd = torch.from_numpy(X).cuda()
+    N, D = X.shape
+    G = G_FULL
+    units = N * G * D
+    stream = torch.cuda.current_stream()
+
+    # k-means initialisation (not timed), shared by every form
+    base = GMM().learn(Xd, G, km_iter=10, em_iter=0, seed=1002, var_floor=1e-10)
+    start = base.get_params()
+
+    def em_model():
+        g = GMM().set_params(*start)
+        g.em_iterate(Xd, 0, recompute_center=True)   # global centre for the tensor-core forms
+        return g
+
+    # quality: 10 EM iterations per form from the same start, judged on the same evaluator
+    quality = {}
+    for prec in args.forms:
+        g = em_model()
+        try:
+            g.em_iterate(Xd, 10, prec=prec)
+        except Exception as e:  # noqa: BLE001  (form not available on this build)
+            quality[prec] = {"error": str(e)}
+            continue
+        quality[prec] = {"avg_log_p": base_eval(base, g, Xd)}
+    ref_ll = quality.get("fp32", {}).get("avg_log_p")
+
+    def time_form(prec, host_input=False):
+        g = em_model()
+        Xin = X if not host_input else torch.from_numpy(X).pin_memory()
+        for _ in range(args.warmup):
+            g.set_params(*start)
+            g.em_iterate(Xin if host_input else Xd, 1, prec=prec)
+        g.set_params(*start)
+        g.profile(True)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(local) as cs:
+            ev0.record(stream)
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                g.em_iterate(Xin if host_input else Xd, 1, prec=prec)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+        ms = ev0.elapsed_time(ev1)
+        if world > 1:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        pass_ms, pass_n, launches = g.profile_read()
+        g.profile(False)
+        return {"ms": ms, "wall_s": wall, "pass_ms": pass_ms, "pass_n": pass_n, "launches": launches,
+                "clocks": cs.summary()}
+
+    results = {}
+    for prec in args.forms:
+        if "error" in quality.get(prec, {}):
+            continue
+        results[prec] = time_form(prec)
+    head = args.forms[-1] if args.forms[-1] in results else "fp32"
+    r = results[head]
+    e2e = time_form(head, host_input=True)
+    step_ms = r["ms"] / args.steps
+    value = world * units / (step_ms * 1e-3)
+
+    peaks, peak_src = _peaks()
+    pass_ms = r["pass_ms"] / max(r["pass_n"], 1)
+    if head == "fp32":
+        # CUDA-core form: 4 FMA per (i, g, d) (E: 2, M: 2); peak = 152 SMs x 128 FMA/clk x 2 flop x max clock
+        flops = 8.0 * units
+        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": flops / (pass_ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (%s clock)" %
+                               (peaks.get("sm_max_mhz", 2070.0), peak_src)}
+    else:
+        flops = 8.0 * units   # algorithmic: E 2 MAC + M 2 MAC per (i, g, d)
+        peak = peaks["bf16_tflops"]
+        roof = {"bound": "tensor", "achieved": flops / (pass_ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "peak_source": "bf16_tflops (%s)" % peak_src}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = args.traffic
+    roof["kernel_ms"] = pass_ms
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "split_bf16": "bf16"}[head],
+        "data": "synthetic",
+        "config": {"workload": "c2 EM iteration (fused E+M pass + FP64 reduce/update): N=2000000 D=60 N_G=256, "
+                               "k-means-initialised, E-step %s" % head,
+                   "N": N, "D": D, "N_G": G, "form": head,
+                   "l2": "inputs larger than L2 (X = %.0f MB)" % (X.nbytes / 1e6),
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": roof,
+        "gpu_launches": int(r["launches"]),
+        "clocks": r["clocks"],
+        "e2e": {"value": world * units / (e2e["ms"] / args.steps * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": int(X.nbytes), "d2h_bytes_per_step": 8 + 32},
+        "forms": {p: {"value": world * units / (results[p]["ms"] / args.steps * 1e-3),
+                      "ms_per_step": results[p]["ms"] / args.steps,
+                      "pass_ms": results[p]["pass_ms"] / max(results[p]["pass_n"], 1),
+                      "avg_log_p_after_10_em": quality[p]["avg_log_p"],
+                      "delta_ll_vs_fp32": (quality[p]["avg_log_p"] - ref_ll) if ref_ll is not None else None}
+                  for p in results},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, cores, sample = cpu_oracle_rate(X)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def base_eval(base, g, Xd):
+    return g.avg_log_p(Xd)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--forms", default="fp32,bf16",
+                    help="comma list of E-step forms; the last available one is the headline")
+    ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per pass launch, if measured")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.forms = [f for f in args.forms.split(",") if f]
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,200 @@
+/*
+ * gmm_gb300.h -- C ABI of the GB300 (sm_103a) library for training and using
+ * diagonal-covariance Gaussian mixture models by k-means + EM, following
+ * arXiv 1707.09094 ("An Open Source C++ Implementation of Multi-Threaded
+ * Gaussian Mixture Models, k-Means and Expectation Maximisation").
+ *
+ * Layouts (all row-major, C order):
+ *   X      const float  [N][D]   one sample per row.  The paper stores one
+ *                                sample per column of a D x N matrix; the
+ *                                bytes in memory are identical.
+ *   means  double [G][D]         the paper's `means`, one Gaussian per row
+ *   dcovs  double [G][D]         diagonal covariances, one Gaussian per row
+ *   hefts  double [G]            mixture weights (Eq. 1, sum to one)
+ *
+ * Pointers: every X / out argument may be a host pointer or a device pointer
+ * of the current CUDA device; the library tells them apart with
+ * cudaPointerGetAttributes.  Host inputs are copied to a device staging area
+ * owned by the model; host outputs are written after a device->host copy.
+ * The caller owns every buffer it passes; the library keeps no caller pointer
+ * after a call returns.  A model owns its parameters and workspace (device
+ * memory) until gmm_destroy.
+ *
+ * Errors: every call returns a gmm_status; 0 is success (the paper's `learn`
+ * returns a bool, Sec. 4.1).  gmm_last_error() gives a thread-local message.
+ * On failure a model keeps the last valid parameters.  Calls on one model
+ * are not thread-safe; distinct models are independent.
+ *
+ * Streams: `stream` is a cudaStream_t (NULL = the legacy default stream).
+ * Calls return after the work they queued has finished (they synchronise the
+ * stream), so host outputs are valid on return.
+ */
+#ifndef GMM_GB300_H
+#define GMM_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gmm_model gmm_model;
+
+typedef enum {
+    GMM_OK = 0,
+    GMM_ERR_ARG = -1,         /* invalid argument or shape                    */
+    GMM_ERR_NONFINITE = -2,   /* a NaN/Inf appeared (e.g. in X); model kept   */
+    GMM_ERR_CUDA = -3,        /* a CUDA call failed                           */
+    GMM_ERR_TIMEOUT = -4,     /* a bounded device wait gave up                */
+    GMM_ERR_OOM = -5,         /* device or host allocation failed             */
+    GMM_ERR_STATE = -6,       /* model has no parameters / shape mismatch     */
+    GMM_ERR_UNSUPPORTED = -7  /* shape outside what the kernels handle        */
+} gmm_status;
+
+/* Distances (Sec. 3.1, Sec. 4.1 `dist_mode`): EUCL squared Euclidean, MAHA
+ * squared Mahalanobis with a global diagonal covariance (Eq. 20), PROB the
+ * "probabilistic distance" of `assign` (largest log w_g N(x|g)). */
+typedef enum { GMM_EUCL = 0, GMM_MAHA = 1, GMM_PROB = 2 } gmm_dist;
+
+/* Seeding (Sec. 4.1 `seed_mode`): KEEP_EXISTING starts from the model's
+ * parameters; RANDOM_SUBSET takes n_gaus distinct random samples as means
+ * (SplitMix64(seed) driving a partial Fisher-Yates shuffle of 0..N-1). */
+typedef enum { GMM_KEEP_EXISTING = 0, GMM_RANDOM_SUBSET = 1 } gmm_seed;
+
+/* Arithmetic of the E-step log-density contraction.
+ *   FP32        plain FP32 CUDA-core form (direct sum of (x-mu)^2/sigma^2)
+ *   BF16        tcgen05 tensor cores, BF16 operands, FP32 accumulation
+ *   SPLIT_BF16  tcgen05, each operand split hi+lo in BF16, three products
+ * Sufficient statistics are reduced in FP64 in every mode. */
+typedef enum { GMM_FP32 = 0, GMM_BF16 = 1, GMM_TF32 = 2, GMM_SPLIT_BF16 = 3 } gmm_prec;
+
+typedef struct {
+    int32_t dist;       /* gmm_dist for seeding/k-means: EUCL or MAHA (default MAHA) */
+    int32_t seed_mode;  /* gmm_seed (default RANDOM_SUBSET)                           */
+    uint64_t seed;      /* RNG seed for RANDOM_SUBSET (default 0)                     */
+    double em_tol;      /* > 0: stop EM once the mean log-likelihood gains < em_tol   */
+    int32_t prec;       /* gmm_prec of the EM E-step (default FP32)                   */
+    int32_t print;      /* non-zero: print per-iteration progress to stderr           */
+    void *stream;       /* cudaStream_t, NULL = default stream                        */
+} gmm_learn_opts;
+
+/* Per-call limits of the kernels.  D <= GMM_MAX_DIMS; the FP32 E-step and
+ * the k-means pass handle any n_gaus; the tensor-core E-step needs
+ * 2*D+1 <= 128 and n_gaus <= 256 (larger shapes use the FP32 form). */
+#define GMM_MAX_DIMS 128
+
+/* Create an empty model (no parameters) on the current CUDA device. */
+gmm_status gmm_create(gmm_model **out);
+
+/* Free a model and everything it owns.  NULL is ignored. */
+void gmm_destroy(gmm_model *m);
+
+/* Fill *o with the defaults listed in gmm_learn_opts. */
+void gmm_default_opts(gmm_learn_opts *o);
+
+/*
+ * learn(data, n_gaus, dist_mode, seed_mode, km_iter, em_iter, var_floor,
+ * print_mode) of Sec. 4.1.  Steps: global per-dimension mean and variance of
+ * X (Eq. 20's global covariance, also the centring used by the tensor-core
+ * forms); seeding; km_iter iterations of k-means (Sec. 3, Eq. 19; dead means
+ * resurrected from the most popular mean's samples, Sec. 3.1), whose last
+ * iteration's hard statistics give the first hefts/means/dcovs (Eqs. 5-7 with
+ * Eq. 19); then em_iter EM iterations (Eqs. 3-14 in the log domain,
+ * Eqs. 15-18), each one fused data pass plus an FP64 reduce/update, with the
+ * variance floor applied after every iteration (Sec. 2.2).  With km_iter == 0
+ * and RANDOM_SUBSET the start is means = seeds, dcovs = 1, hefts = 1/n_gaus
+ * (Sec. 3, first paragraph).  opts NULL = defaults.
+ * X: [N][D] host or device.  Requires 1 <= n_gaus <= N, 1 <= D <= 128,
+ * var_floor >= 0 and finite; KEEP_EXISTING requires parameters of shape
+ * (n_gaus, D).  GMM_ERR_NONFINITE if an update produced NaN/Inf (the model
+ * keeps the last finite parameters).
+ */
+gmm_status gmm_learn(gmm_model *m, const float *X, int64_t N, int32_t D, int32_t n_gaus,
+                     int32_t km_iter, int32_t em_iter, double var_floor,
+                     const gmm_learn_opts *opts);
+
+/*
+ * n_iter EM iterations (Sec. 2 / 2.1) from the model's current parameters on
+ * X, i.e. learn() with KEEP_EXISTING and km_iter = 0 without recomputing the
+ * global statistics when X is the data the model last learned on (the
+ * tensor-core forms centre the data by the stored global mean; pass
+ * recompute_center != 0 for new data).  Appends to the log-likelihood
+ * history read by gmm_get_stats.  This is the call the EM throughput
+ * benchmark times.
+ */
+gmm_status gmm_em_iterate(gmm_model *m, const float *X, int64_t N, int32_t n_iter,
+                          double var_floor, int32_t prec, int32_t recompute_center,
+                          void *stream);
+
+/*
+ * k-means (Sec. 3) alone: from the model's current means (KEEP_EXISTING) run
+ * km_iter iterations with distance `dist` (EUCL or MAHA; MAHA weights come
+ * from the global variance of X, floored by var_floor); on return the model
+ * holds the hard-statistics estimate (hefts, means, dcovs) of the last
+ * iteration and, if assign_out != NULL, assign_out[N] (int32, host or device)
+ * receives that iteration's assignments (Eq. 19, lowest index on exact ties).
+ */
+gmm_status gmm_kmeans(gmm_model *m, const float *X, int64_t N, int32_t km_iter, int32_t dist,
+                      double var_floor, int32_t *assign_out, void *stream);
+
+/*
+ * log_p(X) / log_p(X, g) of Sec. 4.1: out[i] = log p(x_i | lambda) (Eq. 16)
+ * for g = -1, or log N(x_i | mu_g, Sigma_g) (Eq. 15, without the heft) for
+ * 0 <= g < n_gaus.  out: double [N], host or device.
+ */
+gmm_status gmm_log_p(const gmm_model *m, const float *X, int64_t N, int32_t g, double *out,
+                     void *stream);
+
+/* avg_log_p(X[, g]) of Sec. 4.1: *out (host double) = mean over i of log_p. */
+gmm_status gmm_avg_log_p(const gmm_model *m, const float *X, int64_t N, int32_t g, double *out,
+                         void *stream);
+
+/*
+ * assign(X, dist_mode) of Sec. 4.1: out[i] (int32 [N], host or device) = the
+ * closest Gaussian.  EUCL: argmin ||x - mu_g||^2 (exact: FP32 with an FP64
+ * recheck of near ties); PROB: argmax log(w_g N(x|g)) in FP32.  Lowest index
+ * on ties.
+ */
+gmm_status gmm_assign(const gmm_model *m, const float *X, int64_t N, int32_t mode, int32_t *out,
+                      void *stream);
+
+/* raw_hist / norm_hist of Sec. 4.1: counts (int64 [n_gaus]) or normalised
+ * counts (double [n_gaus]) of assign(X, mode); host pointers. */
+gmm_status gmm_raw_hist(const gmm_model *m, const float *X, int64_t N, int32_t mode,
+                        int64_t *counts, void *stream);
+gmm_status gmm_norm_hist(const gmm_model *m, const float *X, int64_t N, int32_t mode,
+                         double *hist, void *stream);
+
+/* Read the parameters (host pointers; any may be NULL).  D / n_gaus receive
+ * the shape.  GMM_ERR_STATE if the model has none. */
+gmm_status gmm_get_params(const gmm_model *m, int32_t *D, int32_t *n_gaus, double *means,
+                          double *dcovs, double *hefts);
+
+/* set_params of Sec. 4.1 (host pointers): the shape may differ from the
+ * model's.  Requires dcovs > 0, hefts >= 0 (not renormalised). */
+gmm_status gmm_set_params(gmm_model *m, int32_t D, int32_t n_gaus, const double *means,
+                          const double *dcovs, const double *hefts);
+
+/* Per-EM-iteration mean log-likelihood of the parameters each E-step used
+ * (host double ll_hist[cap]); *n receives how many are stored (up to cap). */
+gmm_status gmm_get_stats(const gmm_model *m, double *ll_hist, int32_t cap, int32_t *n);
+
+/* Measurement hooks (no counterpart in the paper).  gmm_profile(m, 1)
+ * resets the counters and makes later calls on m record CUDA events, on the
+ * stream the kernels are launched on, around every launch of the fused data
+ * pass (EM or k-means); gmm_profile(m, 0) stops recording.
+ * gmm_profile_read returns the summed device time of those launches (ms),
+ * their number, and the number of library kernels launched since the reset.
+ * Any output pointer may be NULL. */
+gmm_status gmm_profile(gmm_model *m, int32_t enable);
+gmm_status gmm_profile_read(const gmm_model *m, double *pass_ms, int64_t *pass_launches,
+                            int64_t *kernel_launches);
+
+/* Thread-local text of the last error ("" if none). */
+const char *gmm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GMM_GB300_H */

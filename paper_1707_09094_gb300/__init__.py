@@ -1,0 +1,202 @@
+"""GB300 (sm_103a) diagonal-GMM training by k-means + EM (arXiv 1707.09094).
+
+The computation runs in the CUDA library built from ``csrc/`` (C ABI in
+``include/gmm_gb300.h``); this package only marshals arguments.  Inputs may
+be torch tensors (CUDA or CPU) or numpy arrays; PyTorch supplies device
+memory and the current stream.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import (GMM_BF16, GMM_EUCL, GMM_FP32, GMM_KEEP_EXISTING, GMM_MAHA, GMM_PROB,  # noqa: F401
+                   GMM_RANDOM_SUBSET, GMM_SPLIT_BF16, GMM_TF32, GmmError)
+
+PREC = {"fp32": GMM_FP32, "bf16": GMM_BF16, "tf32": GMM_TF32, "split_bf16": GMM_SPLIT_BF16}
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(X):
+    torch = _torch()
+    if isinstance(X, torch.Tensor) and X.is_cuda:
+        return ctypes.c_void_p(torch.cuda.current_stream(X.device).cuda_stream)
+    return ctypes.c_void_p(0)
+
+
+def _as_input(X):
+    """(pointer, N, D, keepalive) for a float32 [N][D] tensor/array."""
+    torch = _torch()
+    if isinstance(X, torch.Tensor):
+        if X.dtype != torch.float32 or X.dim() != 2:
+            raise ValueError("X must be a float32 [N][D] tensor")
+        X = X.contiguous()
+        return ctypes.c_void_p(X.data_ptr()), X.shape[0], X.shape[1], X
+    A = np.ascontiguousarray(X, dtype=np.float32)
+    if A.ndim != 2:
+        raise ValueError("X must be [N][D]")
+    return A.ctypes.data_as(ctypes.c_void_p), A.shape[0], A.shape[1], A
+
+
+def _out_like(X, n, dtype):
+    torch = _torch()
+    if isinstance(X, torch.Tensor) and X.is_cuda:
+        t = torch.empty(n, dtype={np.float64: torch.float64, np.int32: torch.int32}[dtype], device=X.device)
+        return ctypes.c_void_p(t.data_ptr()), t
+    a = np.empty(n, dtype)
+    return a.ctypes.data_as(ctypes.c_void_p), a
+
+
+class GMM:
+    """A diagonal-covariance GMM held on the GPU (the paper's gmm_diag)."""
+
+    def __init__(self):
+        lib = _lib.load()
+        h = ctypes.c_void_p()
+        _lib.check(lib.gmm_create(ctypes.byref(h)), "gmm_create")
+        self._h = h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            _lib.load().gmm_destroy(h)
+            self._h = None
+
+    # --------------------------------------------------------------- training
+    def learn(self, X, n_gaus, dist_mode=GMM_MAHA, seed_mode=GMM_RANDOM_SUBSET, km_iter=10, em_iter=10,
+              var_floor=1e-10, print_mode=False, seed=0, em_tol=0.0, prec="fp32"):
+        ptr, N, D, keep = _as_input(X)
+        o = _lib.gmm_learn_opts()
+        _lib.load().gmm_default_opts(ctypes.byref(o))
+        o.dist, o.seed_mode, o.seed, o.em_tol = dist_mode, seed_mode, seed & (2**64 - 1), em_tol
+        o.prec, o.print, o.stream = PREC.get(prec, prec), int(print_mode), _stream_ptr(X)
+        _lib.check(_lib.load().gmm_learn(self._h, ptr, N, D, n_gaus, km_iter, em_iter, var_floor, ctypes.byref(o)),
+                   "gmm_learn")
+        del keep
+        return self
+
+    def em_iterate(self, X, n_iter, var_floor=1e-10, prec="fp32", recompute_center=False):
+        ptr, N, D, keep = _as_input(X)
+        _lib.check(_lib.load().gmm_em_iterate(self._h, ptr, N, n_iter, var_floor, PREC.get(prec, prec),
+                                              int(recompute_center), _stream_ptr(X)), "gmm_em_iterate")
+        del keep
+        return self
+
+    def kmeans(self, X, km_iter, dist_mode=GMM_MAHA, var_floor=1e-10, return_assign=True):
+        ptr, N, D, keep = _as_input(X)
+        optr, out = _out_like(X, N, np.int32) if return_assign else (ctypes.c_void_p(0), None)
+        _lib.check(_lib.load().gmm_kmeans(self._h, ptr, N, km_iter, dist_mode, var_floor, optr, _stream_ptr(X)),
+                   "gmm_kmeans")
+        del keep
+        return out
+
+    # -------------------------------------------------------------- inference
+    def log_p(self, X, g=-1):
+        ptr, N, D, keep = _as_input(X)
+        optr, out = _out_like(X, N, np.float64)
+        _lib.check(_lib.load().gmm_log_p(self._h, ptr, N, g, optr, _stream_ptr(X)), "gmm_log_p")
+        del keep
+        return out
+
+    def avg_log_p(self, X, g=-1):
+        ptr, N, D, keep = _as_input(X)
+        v = ctypes.c_double()
+        _lib.check(_lib.load().gmm_avg_log_p(self._h, ptr, N, g, ctypes.byref(v), _stream_ptr(X)), "gmm_avg_log_p")
+        del keep
+        return v.value
+
+    def assign(self, X, dist_mode=GMM_EUCL):
+        ptr, N, D, keep = _as_input(X)
+        optr, out = _out_like(X, N, np.int32)
+        _lib.check(_lib.load().gmm_assign(self._h, ptr, N, dist_mode, optr, _stream_ptr(X)), "gmm_assign")
+        del keep
+        return out
+
+    def raw_hist(self, X, dist_mode=GMM_EUCL):
+        ptr, N, D, keep = _as_input(X)
+        out = np.empty(self.n_gaus, np.int64)
+        _lib.check(_lib.load().gmm_raw_hist(self._h, ptr, N, dist_mode, out.ctypes.data_as(ctypes.c_void_p),
+                                            _stream_ptr(X)), "gmm_raw_hist")
+        del keep
+        return out
+
+    def norm_hist(self, X, dist_mode=GMM_EUCL):
+        ptr, N, D, keep = _as_input(X)
+        out = np.empty(self.n_gaus, np.float64)
+        _lib.check(_lib.load().gmm_norm_hist(self._h, ptr, N, dist_mode, out.ctypes.data_as(ctypes.c_void_p),
+                                             _stream_ptr(X)), "gmm_norm_hist")
+        del keep
+        return out
+
+    # ------------------------------------------------------------- parameters
+    def _shape(self):
+        D, G = ctypes.c_int32(), ctypes.c_int32()
+        _lib.check(_lib.load().gmm_get_params(self._h, ctypes.byref(D), ctypes.byref(G), None, None, None),
+                   "gmm_get_params")
+        return D.value, G.value
+
+    @property
+    def n_dims(self):
+        return self._shape()[0]
+
+    @property
+    def n_gaus(self):
+        return self._shape()[1]
+
+    def get_params(self):
+        D, G = self._shape()
+        m = np.empty((G, D)); v = np.empty((G, D)); h = np.empty(G)
+        vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+        _lib.check(_lib.load().gmm_get_params(self._h, None, None, vp(m), vp(v), vp(h)), "gmm_get_params")
+        return m, v, h
+
+    @property
+    def means(self):
+        return self.get_params()[0]
+
+    @property
+    def dcovs(self):
+        return self.get_params()[1]
+
+    @property
+    def hefts(self):
+        return self.get_params()[2]
+
+    def set_params(self, means, dcovs, hefts):
+        m = np.ascontiguousarray(means, np.float64)
+        v = np.ascontiguousarray(dcovs, np.float64)
+        h = np.ascontiguousarray(hefts, np.float64)
+        G, D = m.shape
+        vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+        _lib.check(_lib.load().gmm_set_params(self._h, D, G, vp(m), vp(v), vp(h)), "gmm_set_params")
+        return self
+
+    def reset(self, n_dims, n_gaus):
+        """reset() of Sec. 4.1: zero means, unit covariances, uniform hefts."""
+        return self.set_params(np.zeros((n_gaus, n_dims)), np.ones((n_gaus, n_dims)),
+                               np.full(n_gaus, 1.0 / n_gaus))
+
+    def profile(self, enable=True):
+        """Start (reset) or stop event timing of the fused-pass launches."""
+        _lib.check(_lib.load().gmm_profile(self._h, int(enable)), "gmm_profile")
+        return self
+
+    def profile_read(self):
+        """(summed pass time in ms, pass launches, library kernel launches)."""
+        ms, n, k = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()
+        _lib.check(_lib.load().gmm_profile_read(self._h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(k)),
+                   "gmm_profile_read")
+        return ms.value, n.value, k.value
+
+    def ll_history(self, cap=4096):
+        out = np.empty(cap)
+        n = ctypes.c_int32()
+        _lib.check(_lib.load().gmm_get_stats(self._h, out.ctypes.data_as(ctypes.c_void_p), cap, ctypes.byref(n)),
+                   "gmm_get_stats")
+        return out[: n.value].copy()

@@ -1,0 +1,652 @@
+// C ABI of the library (declared in include/gmm_gb300.h): argument checks,
+// the model object and its device workspace, host<->device staging, and the
+// order in which the kernels of one call are queued on the caller's stream.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "gmm_internal.cuh"
+
+using gmm::DevStatus;
+using gmm::Operands;
+
+namespace {
+
+thread_local std::string g_err;
+
+gmm_status fail(gmm_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define CK(call)                                                                                 \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess)                                                                   \
+            return fail(GMM_ERR_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),    \
+                        __FILE__, __LINE__);                                                     \
+    } while (0)
+
+template <class T>
+cudaError_t grow(T *&p, size_t &cap, size_t n)
+{
+    if (n <= cap && p) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&p), (n ? n : 1) * sizeof(T));
+    if (e == cudaSuccess) cap = n;
+    return e;
+}
+
+bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): state advances by the
+// golden-gamma constant, output is the variant-13 mix of the state.
+uint64_t splitmix64_next(uint64_t &state)
+{
+    uint64_t z = (state += 0x9e3779b97f4a7c15ULL);
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+// random_subset seeding: the first G entries of a partial Fisher-Yates
+// shuffle of 0..N-1 driven by SplitMix64(seed); the untouched identity
+// permutation is kept implicit (only swapped slots are stored).
+std::vector<int64_t> random_subset(int64_t N, int32_t G, uint64_t seed)
+{
+    std::unordered_map<int64_t, int64_t> moved;
+    auto at = [&](int64_t k) {
+        auto it = moved.find(k);
+        return it == moved.end() ? k : it->second;
+    };
+    std::vector<int64_t> out(G);
+    uint64_t st = seed;
+    for (int32_t j = 0; j < G; ++j) {
+        const int64_t k = j + (int64_t)(splitmix64_next(st) % (uint64_t)(N - j));
+        const int64_t vj = at(j), vk = at(k);
+        moved[j] = vk;
+        moved[k] = vj;
+        out[j] = vk;
+    }
+    return out;
+}
+
+}  // namespace
+
+struct gmm_model {
+    int device = 0;
+    int sms = 0;
+    int32_t D = 0, G = 0;
+    bool has_params = false;
+    bool ops_valid = false;
+    double *par[2] = {nullptr, nullptr};
+    size_t par_cap[2] = {0, 0};
+    int cur = 0;
+    // E-step operands
+    Operands op{};
+    float2 *op_sm = nullptr; size_t op_sm_cap = 0;
+    float *op_mu = nullptr; size_t op_mu_cap = 0;
+    float *op_c = nullptr; size_t op_c_cap = 0;
+    __nv_bfloat16 *op_B = nullptr; size_t op_B_cap = 0;
+    // global statistics
+    double *gstat = nullptr; size_t gstat_cap = 0;   // gmean | gvar_floored | wdist | wones  [4][D]
+    float *fstat = nullptr; size_t fstat_cap = 0;    // sw | center  [2][D]
+    bool has_center = false;
+    int32_t center_D = 0;
+    // workspace
+    double *partial = nullptr; size_t partial_cap = 0;
+    double *llp = nullptr; size_t llp_cap = 0;
+    double *lld = nullptr; size_t lld_cap = 0;
+    double *counts = nullptr; size_t counts_cap = 0;
+    int32_t *assign = nullptr; size_t assign_cap = 0;
+    float *xstage = nullptr; size_t xstage_cap = 0;
+    double *dstage = nullptr; size_t dstage_cap = 0;
+    int64_t *idx = nullptr; size_t idx_cap = 0;
+    unsigned long long *hist = nullptr; size_t hist_cap = 0;
+    DevStatus *status = nullptr;
+    std::vector<double> ll_hist;
+    // measurement hooks
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev;      // pairs around fused-pass launches (pending)
+    size_t ev_used = 0;
+    double pass_ms = 0.0;
+    long long pass_launches = 0;
+    long long launch_base = 0;
+
+    double *means() const { return par[cur]; }
+    double *gmean() const { return gstat; }
+    double *gvar() const { return gstat + D; }
+    double *wdist() const { return gstat + 2 * (size_t)D; }
+    double *wones() const { return gstat + 3 * (size_t)D; }
+    float *sw() const { return fstat; }
+    float *center() const { return fstat + D; }
+};
+
+namespace {
+
+// Event pair around one fused-pass launch when profiling is on.
+gmm_status prof_begin(gmm_model *m, cudaStream_t s, size_t *slot)
+{
+    if (!m->profiling) return GMM_OK;
+    if (m->ev_used + 2 > m->ev.size()) {
+        for (int k = 0; k < 64; ++k) {
+            cudaEvent_t e;
+            CK(cudaEventCreate(&e));
+            m->ev.push_back(e);
+        }
+    }
+    *slot = m->ev_used;
+    m->ev_used += 2;
+    CK(cudaEventRecord(m->ev[*slot], s));
+    return GMM_OK;
+}
+
+gmm_status prof_end(gmm_model *m, cudaStream_t s, size_t slot)
+{
+    if (!m->profiling) return GMM_OK;
+    CK(cudaEventRecord(m->ev[slot + 1], s));
+    return GMM_OK;
+}
+
+// After the stream has drained: add up the recorded pairs.
+gmm_status prof_collect(gmm_model *m)
+{
+    for (size_t k = 0; k + 1 < m->ev_used; k += 2) {
+        float ms = 0.f;
+        CK(cudaEventSynchronize(m->ev[k + 1]));
+        CK(cudaEventElapsedTime(&ms, m->ev[k], m->ev[k + 1]));
+        m->pass_ms += ms;
+        m->pass_launches += 1;
+    }
+    m->ev_used = 0;
+    return GMM_OK;
+}
+
+gmm_status ensure_shape(gmm_model *m, int32_t D, int32_t G)
+{
+    const size_t np = 2 * (size_t)G * D + G;
+    CK(grow(m->par[0], m->par_cap[0], np));
+    CK(grow(m->par[1], m->par_cap[1], np));
+    const int32_t KP = ((2 * D + 1) + 63) / 64 * 64;
+    CK(grow(m->op_sm, m->op_sm_cap, (size_t)G * D));
+    CK(grow(m->op_mu, m->op_mu_cap, (size_t)G * D));
+    CK(grow(m->op_c, m->op_c_cap, 3 * (size_t)G));
+    CK(grow(m->op_B, m->op_B_cap, 2 * (size_t)G * KP));
+    m->op.sm = m->op_sm;
+    m->op.mu = m->op_mu;
+    m->op.c = m->op_c;
+    m->op.c0 = m->op_c + G;
+    m->op.ctc = m->op_c + 2 * (size_t)G;
+    m->op.B = m->op_B;
+    m->op.Blo = m->op_B + (size_t)G * KP;
+    m->op.KP = KP;
+    if (m->D != D) m->has_center = false;
+    CK(grow(m->gstat, m->gstat_cap, 4 * (size_t)D));
+    CK(grow(m->fstat, m->fstat_cap, 2 * (size_t)D));
+    if (!m->status) CK(cudaMalloc(&m->status, sizeof(DevStatus)));
+    m->D = D;
+    m->G = G;
+    return GMM_OK;
+}
+
+// Device view of X: the caller's pointer if it is device memory, else a copy
+// in the model's staging buffer.
+gmm_status stage_x(gmm_model *m, const float *X, int64_t N, int32_t D, cudaStream_t s, const float **Xd)
+{
+    if (is_device_ptr(X)) { *Xd = X; return GMM_OK; }
+    CK(grow(m->xstage, m->xstage_cap, (size_t)N * D));
+    CK(cudaMemcpyAsync(m->xstage, X, sizeof(float) * (size_t)N * D, cudaMemcpyHostToDevice, s));
+    *Xd = m->xstage;
+    return GMM_OK;
+}
+
+gmm_status read_status(gmm_model *m, cudaStream_t s, DevStatus *out)
+{
+    CK(cudaMemcpyAsync(out, m->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return GMM_OK;
+}
+
+gmm_status run_global_stats(gmm_model *m, const float *Xd, int64_t N, double var_floor, int32_t dist,
+                            cudaStream_t s)
+{
+    const int grid = m->sms * 4;
+    CK(grow(m->partial, m->partial_cap, (size_t)grid * m->D));
+    CK(gmm::launch_global_stats(Xd, N, m->D, var_floor, dist, m->partial, grid, m->gmean(), m->gvar(),
+                                m->wdist(), m->sw(), m->center(), s));
+    m->has_center = true;
+    m->center_D = m->D;
+    return GMM_OK;
+}
+
+gmm_status run_kmeans(gmm_model *m, const float *Xd, int64_t N, int32_t km_iter, double var_floor,
+                      cudaStream_t s)
+{
+    const int32_t D = m->D, G = m->G, S = 1 + 2 * D;
+    const int grid = gmm::km_grid(D, G, m->sms);
+    CK(grow(m->partial, m->partial_cap, (size_t)grid * G * S));
+    CK(grow(m->assign, m->assign_cap, (size_t)N));
+    CK(grow(m->counts, m->counts_cap, (size_t)G));
+    for (int32_t it = 0; it < km_iter; ++it) {
+        int32_t np = 0;
+        size_t slot = 0;
+        gmm_status prc = prof_begin(m, s, &slot);
+        if (prc != GMM_OK) return prc;
+        CK(gmm::launch_km_pass(Xd, N, D, G, m->par[m->cur], m->wdist(), m->sw(), m->partial, grid, m->assign,
+                               m->status, &np, s));
+        if ((prc = prof_end(m, s, slot)) != GMM_OK) return prc;
+        CK(gmm::launch_km_finalize(m->partial, np, N, D, G, m->par[m->cur], var_floor, it == km_iter - 1,
+                                   m->counts, Xd, m->assign, m->gvar(), m->status, s));
+    }
+    return GMM_OK;
+}
+
+gmm_status run_prep(gmm_model *m, cudaStream_t s)
+{
+    const int build_tc = m->has_center && m->center_D == m->D;
+    CK(gmm::launch_em_prep(m->D, m->G, m->par[m->cur], m->op, m->has_center ? m->center() : nullptr, build_tc, s));
+    m->ops_valid = true;
+    return GMM_OK;
+}
+
+// em_iter EM iterations from par[cur]; iteration k reads par[(cur+k)&1] and
+// writes par[(cur+k+1)&1].  The status block tells which buffer is final.
+gmm_status run_em(gmm_model *m, const float *Xd, int64_t N, int32_t em_iter, double var_floor, double em_tol,
+                  int32_t prec, int32_t print, cudaStream_t s)
+{
+    const int32_t D = m->D, G = m->G, S = 1 + 2 * D;
+    const bool tc = prec == GMM_BF16 || prec == GMM_SPLIT_BF16;
+    if (prec == GMM_TF32) return fail(GMM_ERR_UNSUPPORTED, "prec TF32 is not implemented");
+    if (tc && !gmm::em_tc_supported(D, G))
+        return fail(GMM_ERR_UNSUPPORTED, "tensor-core E-step needs 2D+1 <= 128 and n_gaus <= 256 (D=%d, G=%d)", D, G);
+    if (!tc && !gmm::em_simt_supported(D, G))
+        return fail(GMM_ERR_UNSUPPORTED, "FP32 E-step: shared memory too small for D=%d, G=%d", D, G);
+    if (tc && !(m->has_center && m->center_D == D))
+        return fail(GMM_ERR_STATE, "tensor-core E-step needs the global centre (run learn or recompute_center)");
+    const int grid = tc ? gmm::em_tc_grid(m->sms) : gmm::em_simt_grid(D, G, m->sms);
+    CK(grow(m->partial, m->partial_cap, (size_t)grid * G * S));
+    CK(grow(m->llp, m->llp_cap, (size_t)grid));
+    CK(grow(m->lld, m->lld_cap, (size_t)(em_iter > 0 ? em_iter : 1)));
+    CK(gmm::launch_status_reset(m->status, s));
+    if (em_iter == 0) return GMM_OK;
+    const int base = m->cur;
+    CK(gmm::launch_em_prep(D, G, m->par[base], m->op, m->center(), tc ? 1 : (m->has_center && m->center_D == D), s));
+    for (int32_t k = 0; k < em_iter; ++k) {
+        gmm::EmPassArgs pa{Xd, N, D, G, m->op, m->center(), m->partial, m->llp, m->status, k};
+        size_t slot = 0;
+        gmm_status prc = prof_begin(m, s, &slot);
+        if (prc != GMM_OK) return prc;
+        if (tc) CK(gmm::launch_em_pass_tc(pa, grid, prec == GMM_SPLIT_BF16, s));
+        else CK(gmm::launch_em_pass_simt(pa, grid, s));
+        if ((prc = prof_end(m, s, slot)) != GMM_OK) return prc;
+        gmm::EmFinalizeArgs fa{m->partial, m->llp, grid, N, D, G, m->par[(base + k) & 1], m->par[(base + k + 1) & 1],
+                               var_floor, tc ? 1 : 0, m->op, m->center(), m->status, k, em_tol, m->lld,
+                               tc ? 1 : (m->has_center && m->center_D == D)};
+        CK(gmm::launch_em_finalize(fa, s));
+    }
+    DevStatus st;
+    gmm_status rc = read_status(m, s, &st);
+    if (rc != GMM_OK) return rc;
+    if ((rc = prof_collect(m)) != GMM_OK) return rc;
+    std::vector<double> ll(em_iter);
+    CK(cudaMemcpy(ll.data(), m->lld, sizeof(double) * em_iter, cudaMemcpyDeviceToHost));
+    if (st.code != 0) {
+        m->cur = (base + (st.fail_iter < 0 ? 0 : st.fail_iter)) & 1;
+        for (int k = 0; k < st.n_done && k < em_iter; ++k) m->ll_hist.push_back(ll[k]);
+        m->ops_valid = false;
+        return fail((gmm_status)st.code, "EM iteration %d produced a non-finite value", st.fail_iter);
+    }
+    m->cur = (base + st.n_done) & 1;
+    for (int k = 0; k < st.n_done; ++k) {
+        m->ll_hist.push_back(ll[k]);
+        if (print) fprintf(stderr, "gmm: EM iteration %d: mean log-likelihood %.10g\n", k + 1, ll[k]);
+    }
+    return GMM_OK;
+}
+
+gmm_status validate_x(const float *X, int64_t N, int32_t D)
+{
+    if (!X) return fail(GMM_ERR_ARG, "X is NULL");
+    if (N < 1) return fail(GMM_ERR_ARG, "N must be >= 1 (got %lld)", (long long)N);
+    if (D < 1 || D > GMM_MAX_DIMS) return fail(GMM_ERR_UNSUPPORTED, "D must be in [1, %d] (got %d)", GMM_MAX_DIMS, D);
+    return GMM_OK;
+}
+
+cudaStream_t as_stream(void *p) { return reinterpret_cast<cudaStream_t>(p); }
+
+}  // namespace
+
+extern "C" {
+
+const char *gmm_last_error(void) { return g_err.c_str(); }
+
+void gmm_default_opts(gmm_learn_opts *o)
+{
+    if (!o) return;
+    o->dist = GMM_MAHA;
+    o->seed_mode = GMM_RANDOM_SUBSET;
+    o->seed = 0;
+    o->em_tol = 0.0;
+    o->prec = GMM_FP32;
+    o->print = 0;
+    o->stream = nullptr;
+}
+
+gmm_status gmm_create(gmm_model **out)
+{
+    if (!out) return fail(GMM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    gmm_model *m = new (std::nothrow) gmm_model();
+    if (!m) return fail(GMM_ERR_OOM, "host allocation failed");
+    cudaError_t e = cudaGetDevice(&m->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&m->sms, cudaDevAttrMultiProcessorCount, m->device);
+    if (e == cudaSuccess) e = cudaMalloc(&m->status, sizeof(DevStatus));
+    if (e != cudaSuccess) {
+        delete m;
+        return fail(GMM_ERR_CUDA, "no usable CUDA device: %s", cudaGetErrorString(e));
+    }
+    *out = m;
+    return GMM_OK;
+}
+
+void gmm_destroy(gmm_model *m)
+{
+    if (!m) return;
+    for (cudaEvent_t e : m->ev) cudaEventDestroy(e);
+    void *bufs[] = {m->par[0], m->par[1], m->op_sm, m->op_mu, m->op_c, m->op_B, m->gstat, m->fstat,
+                    m->partial, m->llp, m->lld, m->counts, m->assign, m->xstage, m->dstage, m->idx,
+                    m->hist, m->status};
+    for (void *p : bufs)
+        if (p) cudaFree(p);
+    delete m;
+}
+
+gmm_status gmm_learn(gmm_model *m, const float *X, int64_t N, int32_t D, int32_t n_gaus, int32_t km_iter,
+                     int32_t em_iter, double var_floor, const gmm_learn_opts *opts)
+{
+    if (!m) return fail(GMM_ERR_ARG, "model is NULL");
+    gmm_learn_opts o;
+    gmm_default_opts(&o);
+    if (opts) o = *opts;
+    gmm_status rc = validate_x(X, N, D);
+    if (rc != GMM_OK) return rc;
+    if (n_gaus < 1 || (int64_t)n_gaus > N) return fail(GMM_ERR_ARG, "need 1 <= n_gaus <= N (n_gaus=%d, N=%lld)", n_gaus, (long long)N);
+    if (km_iter < 0 || em_iter < 0) return fail(GMM_ERR_ARG, "km_iter and em_iter must be >= 0");
+    if (!(var_floor >= 0.0) || !std::isfinite(var_floor)) return fail(GMM_ERR_ARG, "var_floor must be finite and >= 0");
+    if (o.dist != GMM_EUCL && o.dist != GMM_MAHA) return fail(GMM_ERR_ARG, "dist must be EUCL or MAHA");
+    if (o.seed_mode != GMM_KEEP_EXISTING && o.seed_mode != GMM_RANDOM_SUBSET) return fail(GMM_ERR_ARG, "bad seed_mode");
+    if (o.prec < GMM_FP32 || o.prec > GMM_SPLIT_BF16) return fail(GMM_ERR_ARG, "bad prec");
+    if (o.seed_mode == GMM_KEEP_EXISTING && !(m->has_params && m->D == D && m->G == n_gaus))
+        return fail(GMM_ERR_STATE, "keep_existing needs parameters of shape (%d, %d)", n_gaus, D);
+    cudaStream_t s = as_stream(o.stream);
+    if (o.seed_mode == GMM_RANDOM_SUBSET || m->D != D || m->G != n_gaus) {
+        rc = ensure_shape(m, D, n_gaus);
+        if (rc != GMM_OK) return rc;
+    }
+    const float *Xd = nullptr;
+    if ((rc = stage_x(m, X, N, D, s, &Xd)) != GMM_OK) return rc;
+    CK(gmm::launch_status_reset(m->status, s));
+    if ((rc = run_global_stats(m, Xd, N, var_floor, o.dist, s)) != GMM_OK) return rc;
+    if (o.seed_mode == GMM_RANDOM_SUBSET) {
+        std::vector<int64_t> idx = random_subset(N, n_gaus, o.seed);
+        CK(grow(m->idx, m->idx_cap, (size_t)n_gaus));
+        CK(cudaMemcpyAsync(m->idx, idx.data(), sizeof(int64_t) * n_gaus, cudaMemcpyHostToDevice, s));
+        m->cur = 0;
+        CK(gmm::launch_gather_seeds(Xd, D, n_gaus, m->idx, m->par[0], s));
+        CK(cudaStreamSynchronize(s));   // idx is a host vector
+        m->has_params = true;
+    }
+    m->ll_hist.clear();
+    if (km_iter > 0 && (rc = run_kmeans(m, Xd, N, km_iter, var_floor, s)) != GMM_OK) return rc;
+    if ((rc = run_em(m, Xd, N, em_iter, var_floor, o.em_tol, o.prec, o.print, s)) != GMM_OK) return rc;
+    if ((rc = run_prep(m, s)) != GMM_OK) return rc;
+    DevStatus st;
+    if ((rc = read_status(m, s, &st)) != GMM_OK) return rc;
+    if ((rc = prof_collect(m)) != GMM_OK) return rc;
+    if (st.code != 0) return fail((gmm_status)st.code, "learn failed with device status %d", st.code);
+    return GMM_OK;
+}
+
+gmm_status gmm_em_iterate(gmm_model *m, const float *X, int64_t N, int32_t n_iter, double var_floor, int32_t prec,
+                          int32_t recompute_center, void *stream)
+{
+    if (!m) return fail(GMM_ERR_ARG, "model is NULL");
+    if (!m->has_params) return fail(GMM_ERR_STATE, "model has no parameters");
+    gmm_status rc = validate_x(X, N, m->D);
+    if (rc != GMM_OK) return rc;
+    if (n_iter < 0 || !(var_floor >= 0.0) || !std::isfinite(var_floor)) return fail(GMM_ERR_ARG, "bad n_iter/var_floor");
+    if (prec < GMM_FP32 || prec > GMM_SPLIT_BF16) return fail(GMM_ERR_ARG, "bad prec");
+    cudaStream_t s = as_stream(stream);
+    const float *Xd = nullptr;
+    if ((rc = stage_x(m, X, N, m->D, s, &Xd)) != GMM_OK) return rc;
+    if (recompute_center || !(m->has_center && m->center_D == m->D)) {
+        CK(gmm::launch_status_reset(m->status, s));
+        if ((rc = run_global_stats(m, Xd, N, var_floor, GMM_MAHA, s)) != GMM_OK) return rc;
+    }
+    if ((rc = run_em(m, Xd, N, n_iter, var_floor, 0.0, prec, 0, s)) != GMM_OK) return rc;
+    return run_prep(m, s);
+}
+
+gmm_status gmm_kmeans(gmm_model *m, const float *X, int64_t N, int32_t km_iter, int32_t dist, double var_floor,
+                      int32_t *assign_out, void *stream)
+{
+    if (!m) return fail(GMM_ERR_ARG, "model is NULL");
+    if (!m->has_params) return fail(GMM_ERR_STATE, "model has no parameters (means to start from)");
+    gmm_status rc = validate_x(X, N, m->D);
+    if (rc != GMM_OK) return rc;
+    if (km_iter < 1) return fail(GMM_ERR_ARG, "km_iter must be >= 1");
+    if (dist != GMM_EUCL && dist != GMM_MAHA) return fail(GMM_ERR_ARG, "dist must be EUCL or MAHA");
+    if ((int64_t)m->G > N) return fail(GMM_ERR_ARG, "n_gaus > N");
+    if (!(var_floor >= 0.0) || !std::isfinite(var_floor)) return fail(GMM_ERR_ARG, "bad var_floor");
+    cudaStream_t s = as_stream(stream);
+    const float *Xd = nullptr;
+    if ((rc = stage_x(m, X, N, m->D, s, &Xd)) != GMM_OK) return rc;
+    CK(gmm::launch_status_reset(m->status, s));
+    if ((rc = run_global_stats(m, Xd, N, var_floor, dist, s)) != GMM_OK) return rc;
+    if ((rc = run_kmeans(m, Xd, N, km_iter, var_floor, s)) != GMM_OK) return rc;
+    if ((rc = run_prep(m, s)) != GMM_OK) return rc;
+    if (assign_out) {
+        CK(cudaMemcpyAsync(assign_out, m->assign, sizeof(int32_t) * (size_t)N, cudaMemcpyDefault, s));
+    }
+    DevStatus st;
+    if ((rc = read_status(m, s, &st)) != GMM_OK) return rc;
+    if ((rc = prof_collect(m)) != GMM_OK) return rc;
+    if (st.code != 0) return fail((gmm_status)st.code, "k-means failed with device status %d", st.code);
+    return GMM_OK;
+}
+
+gmm_status gmm_log_p(const gmm_model *mc, const float *X, int64_t N, int32_t g, double *out, void *stream)
+{
+    gmm_model *m = const_cast<gmm_model *>(mc);
+    if (!m || !out) return fail(GMM_ERR_ARG, "NULL argument");
+    if (!m->has_params) return fail(GMM_ERR_STATE, "model has no parameters");
+    gmm_status rc = validate_x(X, N, m->D);
+    if (rc != GMM_OK) return rc;
+    if (g < -1 || g >= m->G) return fail(GMM_ERR_ARG, "g out of range");
+    cudaStream_t s = as_stream(stream);
+    if (!m->ops_valid && (rc = run_prep(m, s)) != GMM_OK) return rc;
+    const float *Xd = nullptr;
+    if ((rc = stage_x(m, X, N, m->D, s, &Xd)) != GMM_OK) return rc;
+    double *od = out;
+    const bool dev_out = is_device_ptr(out);
+    if (!dev_out) {
+        CK(grow(m->dstage, m->dstage_cap, (size_t)N));
+        od = m->dstage;
+    }
+    CK(gmm::launch_log_p(Xd, N, m->D, m->G, m->op, g, od, s));
+    if (!dev_out) CK(cudaMemcpyAsync(out, od, sizeof(double) * (size_t)N, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return GMM_OK;
+}
+
+gmm_status gmm_avg_log_p(const gmm_model *mc, const float *X, int64_t N, int32_t g, double *out, void *stream)
+{
+    gmm_model *m = const_cast<gmm_model *>(mc);
+    if (!m || !out) return fail(GMM_ERR_ARG, "NULL argument");
+    if (!m->has_params) return fail(GMM_ERR_STATE, "model has no parameters");
+    gmm_status rc = validate_x(X, N, m->D);
+    if (rc != GMM_OK) return rc;
+    if (g < -1 || g >= m->G) return fail(GMM_ERR_ARG, "g out of range");
+    cudaStream_t s = as_stream(stream);
+    if (!m->ops_valid && (rc = run_prep(m, s)) != GMM_OK) return rc;
+    const float *Xd = nullptr;
+    if ((rc = stage_x(m, X, N, m->D, s, &Xd)) != GMM_OK) return rc;
+    CK(grow(m->dstage, m->dstage_cap, (size_t)N + 1));
+    CK(gmm::launch_log_p(Xd, N, m->D, m->G, m->op, g, m->dstage, s));
+    CK(gmm::launch_sum_fp64(m->dstage, N, m->dstage + N, s));
+    double sum = 0.0;
+    CK(cudaMemcpyAsync(&sum, m->dstage + N, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *out = sum / (double)N;
+    return GMM_OK;
+}
+
+static gmm_status assign_dev(gmm_model *m, const float *X, int64_t N, int32_t mode, cudaStream_t s, int32_t **ad)
+{
+    gmm_status rc = validate_x(X, N, m->D);
+    if (rc != GMM_OK) return rc;
+    if (mode != GMM_EUCL && mode != GMM_PROB) return fail(GMM_ERR_ARG, "assign mode must be EUCL or PROB");
+    if (!m->ops_valid && (rc = run_prep(m, s)) != GMM_OK) return rc;
+    const float *Xd = nullptr;
+    if ((rc = stage_x(m, X, N, m->D, s, &Xd)) != GMM_OK) return rc;
+    CK(grow(m->assign, m->assign_cap, (size_t)N));
+    // unit weights for the exact Euclidean recheck
+    std::vector<double> ones(m->D, 1.0);
+    CK(cudaMemcpyAsync(m->wones(), ones.data(), sizeof(double) * m->D, cudaMemcpyHostToDevice, s));
+    CK(gmm::launch_assign(Xd, N, m->D, m->G, m->par[m->cur], m->op, mode, m->assign, nullptr, m->wones(),
+                          m->status, s));
+    CK(cudaStreamSynchronize(s));   // `ones` is a host vector
+    *ad = m->assign;
+    return GMM_OK;
+}
+
+gmm_status gmm_assign(const gmm_model *mc, const float *X, int64_t N, int32_t mode, int32_t *out, void *stream)
+{
+    gmm_model *m = const_cast<gmm_model *>(mc);
+    if (!m || !out) return fail(GMM_ERR_ARG, "NULL argument");
+    if (!m->has_params) return fail(GMM_ERR_STATE, "model has no parameters");
+    cudaStream_t s = as_stream(stream);
+    int32_t *ad = nullptr;
+    gmm_status rc = assign_dev(m, X, N, mode, s, &ad);
+    if (rc != GMM_OK) return rc;
+    CK(cudaMemcpyAsync(out, ad, sizeof(int32_t) * (size_t)N, cudaMemcpyDefault, s));
+    CK(cudaStreamSynchronize(s));
+    return GMM_OK;
+}
+
+gmm_status gmm_raw_hist(const gmm_model *mc, const float *X, int64_t N, int32_t mode, int64_t *counts, void *stream)
+{
+    gmm_model *m = const_cast<gmm_model *>(mc);
+    if (!m || !counts) return fail(GMM_ERR_ARG, "NULL argument");
+    if (!m->has_params) return fail(GMM_ERR_STATE, "model has no parameters");
+    cudaStream_t s = as_stream(stream);
+    int32_t *ad = nullptr;
+    gmm_status rc = assign_dev(m, X, N, mode, s, &ad);
+    if (rc != GMM_OK) return rc;
+    CK(grow(m->hist, m->hist_cap, (size_t)m->G));
+    CK(gmm::launch_hist(ad, N, m->G, m->hist, s));
+    std::vector<unsigned long long> h(m->G);
+    CK(cudaMemcpyAsync(h.data(), m->hist, sizeof(unsigned long long) * m->G, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int g = 0; g < m->G; ++g) counts[g] = (int64_t)h[g];
+    return GMM_OK;
+}
+
+gmm_status gmm_norm_hist(const gmm_model *mc, const float *X, int64_t N, int32_t mode, double *hist, void *stream)
+{
+    if (!mc || !hist) return fail(GMM_ERR_ARG, "NULL argument");
+    std::vector<int64_t> c(mc->G > 0 ? mc->G : 1);
+    gmm_status rc = gmm_raw_hist(mc, X, N, mode, c.data(), stream);
+    if (rc != GMM_OK) return rc;
+    for (int g = 0; g < mc->G; ++g) hist[g] = (double)c[g] / (double)N;
+    return GMM_OK;
+}
+
+gmm_status gmm_get_params(const gmm_model *m, int32_t *D, int32_t *n_gaus, double *means, double *dcovs,
+                          double *hefts)
+{
+    if (!m) return fail(GMM_ERR_ARG, "model is NULL");
+    if (D) *D = m->has_params ? m->D : 0;
+    if (n_gaus) *n_gaus = m->has_params ? m->G : 0;
+    if (!m->has_params) return (means || dcovs || hefts) ? fail(GMM_ERR_STATE, "model has no parameters") : GMM_OK;
+    const size_t GD = (size_t)m->G * m->D;
+    const double *p = m->par[m->cur];
+    if (means) CK(cudaMemcpy(means, p, sizeof(double) * GD, cudaMemcpyDeviceToHost));
+    if (dcovs) CK(cudaMemcpy(dcovs, p + GD, sizeof(double) * GD, cudaMemcpyDeviceToHost));
+    if (hefts) CK(cudaMemcpy(hefts, p + 2 * GD, sizeof(double) * m->G, cudaMemcpyDeviceToHost));
+    return GMM_OK;
+}
+
+gmm_status gmm_set_params(gmm_model *m, int32_t D, int32_t n_gaus, const double *means, const double *dcovs,
+                          const double *hefts)
+{
+    if (!m || !means || !dcovs || !hefts) return fail(GMM_ERR_ARG, "NULL argument");
+    if (D < 1 || D > GMM_MAX_DIMS || n_gaus < 1) return fail(GMM_ERR_ARG, "bad shape (D=%d, n_gaus=%d)", D, n_gaus);
+    const size_t GD = (size_t)n_gaus * D;
+    for (size_t k = 0; k < GD; ++k)
+        if (!(dcovs[k] > 0.0) || !std::isfinite(dcovs[k]) || !std::isfinite(means[k]))
+            return fail(GMM_ERR_ARG, "dcovs must be finite and > 0, means finite");
+    for (int g = 0; g < n_gaus; ++g)
+        if (!(hefts[g] >= 0.0) || !std::isfinite(hefts[g])) return fail(GMM_ERR_ARG, "hefts must be finite and >= 0");
+    gmm_status rc = ensure_shape(m, D, n_gaus);
+    if (rc != GMM_OK) return rc;
+    m->cur = 0;
+    CK(cudaMemcpy(m->par[0], means, sizeof(double) * GD, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(m->par[0] + GD, dcovs, sizeof(double) * GD, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(m->par[0] + 2 * GD, hefts, sizeof(double) * n_gaus, cudaMemcpyHostToDevice));
+    m->has_params = true;
+    m->ops_valid = false;
+    m->ll_hist.clear();
+    return run_prep(m, nullptr);
+}
+
+gmm_status gmm_profile(gmm_model *m, int32_t enable)
+{
+    if (!m) return fail(GMM_ERR_ARG, "model is NULL");
+    m->profiling = enable != 0;
+    m->ev_used = 0;
+    m->pass_ms = 0.0;
+    m->pass_launches = 0;
+    m->launch_base = gmm::launches_total();
+    return GMM_OK;
+}
+
+gmm_status gmm_profile_read(const gmm_model *m, double *pass_ms, int64_t *pass_launches, int64_t *kernel_launches)
+{
+    if (!m) return fail(GMM_ERR_ARG, "model is NULL");
+    if (pass_ms) *pass_ms = m->pass_ms;
+    if (pass_launches) *pass_launches = m->pass_launches;
+    if (kernel_launches) *kernel_launches = gmm::launches_total() - m->launch_base;
+    return GMM_OK;
+}
+
+gmm_status gmm_get_stats(const gmm_model *m, double *ll_hist, int32_t cap, int32_t *n)
+{
+    if (!m) return fail(GMM_ERR_ARG, "model is NULL");
+    const int32_t k = (int32_t)m->ll_hist.size() < cap ? (int32_t)m->ll_hist.size() : cap;
+    for (int32_t i = 0; i < k; ++i) ll_hist[i] = m->ll_hist[i];
+    if (n) *n = k;
+    return GMM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,111 @@
+// Internal declarations shared by the CUDA translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "gmm_gb300.h"
+
+namespace gmm {
+
+constexpr double kLog2Pi = 1.83787706640934548356065947281123527;
+
+// Device-side status block, one per model.  Kernels never trap: they record
+// what went wrong here and return, and the host reads it after the stream
+// has drained.
+struct DevStatus {
+    int32_t code;        // 0 ok, else a gmm_status
+    int32_t halt;        // set on error: later kernels of the same call no-op
+    int32_t stop_after;  // last EM iteration to run (em_tol convergence)
+    int32_t n_done;      // EM iterations completed
+    int32_t fail_iter;   // iteration that produced a non-finite value
+    int32_t n_dead;      // dead means seen by the last k-means iteration
+    int32_t pad[2];
+};
+
+// Operands of the E-step derived from lambda (written by the prep/finalize
+// kernels, read by the fused passes and the inference kernels).
+struct Operands {
+    float2 *sm;          // [G][D]  (s, mu*s) with s = 1/sqrt(sigma^2)      (FP32 form)
+    float *mu;           // [G][D]  FP32 copy of the means: shift of the FP32 M-step
+    float *c;            // [G]     log w - D/2 log 2pi - 1/2 sum log sigma^2
+    float *c0;           // [G]     same without log w  (log_p(X, g))
+    __nv_bfloat16 *B;    // [G][KP] tensor-core E operand, K-major: hi part
+    __nv_bfloat16 *Blo;  // [G][KP] lo part (split-BF16)
+    float *ctc;          // [G]     constant of the centred tensor-core logits
+    int32_t KP;          // padded K of the tensor-core operand (multiple of 64)
+};
+
+struct EmPassArgs {
+    const float *X;
+    int64_t N;
+    int32_t D, G;
+    Operands op;
+    const float *center;     // [D] FP32 global mean (tensor-core centring)
+    double *partial;         // [grid][G][1+2D]
+    double *ll_partial;      // [grid]
+    DevStatus *status;
+    int32_t iter;
+};
+
+struct EmFinalizeArgs {
+    const double *partial;
+    const double *ll_partial;
+    int32_t n_partial;
+    int64_t N;
+    int32_t D, G;
+    const double *par_in;    // [G*D means | G*D dcovs | G hefts]
+    double *par_out;
+    double var_floor;
+    int32_t shift_mode;      // 0: per-Gaussian FP32 means (op.mu), 1: centre
+    Operands op;
+    const float *center;
+    DevStatus *status;
+    int32_t iter;
+    double em_tol;
+    double *ll_hist;         // device history
+    int32_t build_tc;        // also build the tensor-core operands
+};
+
+// Count of library kernels launched (process-wide, all models).
+void count_launches(int n);
+long long launches_total();
+
+// ---- launchers implemented in gmm_simt.cu
+cudaError_t launch_global_stats(const float *X, int64_t N, int32_t D, double var_floor, int32_t dist,
+                                double *partial, int32_t grid, double *gmean, double *gvar_floored,
+                                double *wdist, float *sw, float *center, cudaStream_t s);
+cudaError_t launch_gather_seeds(const float *X, int32_t D, int32_t G, const int64_t *idx,
+                                double *par, cudaStream_t s);
+cudaError_t launch_km_pass(const float *X, int64_t N, int32_t D, int32_t G, const double *par,
+                           const double *wdist, const float *sw, double *partial, int32_t grid,
+                           int32_t *assign, DevStatus *status, int32_t *n_partial, cudaStream_t s);
+cudaError_t launch_km_finalize(const double *partial, int32_t n_partial, int64_t N, int32_t D,
+                               int32_t G, double *par, double var_floor, int32_t final_iter,
+                               double *counts, const float *X, const int32_t *assign,
+                               const double *gvar_floored, DevStatus *status, cudaStream_t s);
+cudaError_t launch_em_prep(int32_t D, int32_t G, const double *par, Operands op, const float *center,
+                           int32_t build_tc, cudaStream_t s);
+cudaError_t launch_em_pass_simt(const EmPassArgs &a, int32_t grid, cudaStream_t s);
+cudaError_t launch_em_finalize(const EmFinalizeArgs &a, cudaStream_t s);
+cudaError_t launch_log_p(const float *X, int64_t N, int32_t D, int32_t G, Operands op, int32_t g,
+                         double *out, cudaStream_t s);
+cudaError_t launch_assign(const float *X, int64_t N, int32_t D, int32_t G, const double *par,
+                          Operands op, int32_t mode, int32_t *out, const float *sw_ones,
+                          const double *w_ones, DevStatus *status, cudaStream_t s);
+cudaError_t launch_status_reset(DevStatus *st, cudaStream_t s);
+cudaError_t launch_sum_fp64(const double *v, int64_t n, double *out, cudaStream_t s);
+cudaError_t launch_hist(const int32_t *a, int64_t N, int32_t G, unsigned long long *counts,
+                        cudaStream_t s);
+int em_simt_grid(int32_t D, int32_t G, int sms);
+int km_grid(int32_t D, int32_t G, int sms);
+size_t em_simt_smem(int32_t D, int32_t G);
+bool em_simt_supported(int32_t D, int32_t G);
+
+// ---- launchers implemented in gmm_em_tc.cu
+bool em_tc_supported(int32_t D, int32_t G);
+int em_tc_grid(int sms);
+cudaError_t launch_em_pass_tc(const EmPassArgs &a, int32_t grid, int32_t split, cudaStream_t s);
+
+}  // namespace gmm

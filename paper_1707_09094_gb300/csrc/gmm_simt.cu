@@ -1,0 +1,974 @@
+// CUDA-core kernels of the library: global statistics, k-means assignment +
+// accumulation, the plain FP32 fused EM pass, the FP64 reduce/update
+// ("finalize") kernels, operand preparation and inference.
+//
+// Data layout in HBM (row-major):
+//   X        float [N][D]
+//   lambda   double [G*D means | G*D dcovs | G hefts]   (ping-pong pair)
+//   partial  double [n_partial][G][1 + 2D]: per-CTA map results of Sec. 2.1
+//            (index 0 = L~_g, 1..D = sum l (x - shift), D+1..2D = sum l (x - shift)^2)
+// Every reduction over CTAs runs in CTA order in FP64, so results do not
+// depend on scheduling.
+#include <atomic>
+#include <cfloat>
+#include <cmath>
+
+#include "gmm_internal.cuh"
+
+namespace gmm {
+
+namespace {
+
+constexpr int kWarps = 8;
+constexpr int kEmThreads = kWarps * 32;
+constexpr int kTile = 32;      // samples per tile of the FP32 EM pass
+constexpr int kTP = kTile + 1; // padded row stride of the tile buffers
+constexpr int kKmThreads = 128;
+
+__device__ __forceinline__ bool em_skip(const DevStatus *st, int iter)
+{
+    return st->halt != 0 || iter > st->stop_after;
+}
+
+__device__ __forceinline__ float warp_max(float v)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Fixed-order block reduction of one double per thread (thread 0 returns it).
+__device__ double block_sum_d(double v, double *sh)
+{
+    int t = threadIdx.x;
+    sh[t] = v;
+    __syncthreads();
+    for (int s = blockDim.x >> 1; s > 0; s >>= 1) {
+        if (t < s) sh[t] += sh[t + s];
+        __syncthreads();
+    }
+    double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+__device__ void set_error(DevStatus *st, int code, int iter)
+{
+    if (atomicCAS(&st->code, 0, code) == 0) st->fail_iter = iter;
+    atomicExch(&st->halt, 1);
+}
+
+// ------------------------------------------------------------------------
+// Global per-dimension mean and variance (Eq. 20's global covariance).
+// Pass 1 sums x, pass 2 sums (x - mean)^2, both FP64 per CTA, CTA order.
+// blockDim = R*D: thread (r, d) walks rows r, r+R*grid, ... of column d.
+// ------------------------------------------------------------------------
+template <int PASS>
+__global__ void k_gstats(const float *__restrict__ X, int64_t N, int32_t D,
+                         const double *__restrict__ gmean, double *__restrict__ partial)
+{
+    extern __shared__ double shd[];
+    const int R = blockDim.x / D;
+    const int t = threadIdx.x;
+    double acc = 0.0;
+    if (t < R * D) {
+        const int d = t % D, r = t / D;
+        const double m = PASS == 2 ? gmean[d] : 0.0;
+        for (int64_t i = (int64_t)blockIdx.x * R + r; i < N; i += (int64_t)gridDim.x * R) {
+            double v = (double)X[i * D + d];
+            if (PASS == 1) acc += v;
+            else { double q = v - m; acc += q * q; }
+        }
+    }
+    shd[t] = acc;
+    __syncthreads();
+    if (t < D) {
+        double s = 0.0;
+        for (int r = 0; r < R; ++r) s += shd[r * D + t];
+        partial[(size_t)blockIdx.x * D + t] = s;
+    }
+}
+
+template <int PASS>
+__global__ void k_gstats_final(const double *__restrict__ partial, int n_partial, int64_t N, int32_t D,
+                               double var_floor, int32_t dist, double *gmean, double *gvar_floored,
+                               double *wdist, float *sw, float *center)
+{
+    int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= D) return;
+    double s = 0.0;
+    for (int c = 0; c < n_partial; ++c) s += partial[(size_t)c * D + d];
+    if (PASS == 1) {
+        gmean[d] = s / (double)N;
+        center[d] = (float)(s / (double)N);
+    } else {
+        double v = s / (double)N;
+        v = v > var_floor ? v : var_floor;
+        gvar_floored[d] = v;
+        double w = dist == GMM_MAHA ? 1.0 / v : 1.0;
+        wdist[d] = w;
+        sw[d] = (float)sqrt(w);
+    }
+}
+
+__global__ void k_gather_seeds(const float *__restrict__ X, int32_t D, int32_t G,
+                               const int64_t *__restrict__ idx, double *par)
+{
+    int g = blockIdx.x;
+    for (int d = threadIdx.x; d < D; d += blockDim.x) {
+        par[(size_t)g * D + d] = (double)X[idx[g] * D + d];
+        par[(size_t)G * D + (size_t)g * D + d] = 1.0;
+    }
+    if (threadIdx.x == 0) par[2 * (size_t)G * D + g] = 1.0 / (double)G;
+}
+
+// ------------------------------------------------------------------------
+// Nearest mean (Eq. 19) with an exact FP64 recheck of near ties.
+// FP32 distances use scaled coordinates xs = x*sqrt(w), cs = mu*sqrt(w).
+// Rounding bound of one FP32 distance d (x, mu rounded to FP32, t = xs - cs
+// rounded, FMA accumulation): |err| <= 2^-22 sqrt(2 d (|xs|^2 + |cs|^2))
+// + (D + 4) 2^-24 d.  If the runner-up minus its bound still exceeds the
+// winner plus its bound, the FP32 winner is the exact winner; otherwise all
+// Gaussians are re-evaluated in FP64 exactly as sum_d w_d (x_d - mu_d)^2 in
+// order d = 0..D-1 without fused operations, lowest index on exact ties.
+// ------------------------------------------------------------------------
+__device__ __forceinline__ float km_err(float d, float norms, int D)
+{
+    return 4.0f * (2.384185791015625e-07f * sqrtf(2.0f * d * norms) + (float)(D + 4) * 5.9604644775390625e-08f * d)
+           + 1e-30f;
+}
+
+__device__ int km_recheck_fp64(const float *__restrict__ x, int D, int G, const double *__restrict__ means,
+                               const double *__restrict__ w)
+{
+    double best = INFINITY;
+    int a = 0;
+    for (int g = 0; g < G; ++g) {
+        const double *mu = means + (size_t)g * D;
+        double acc = 0.0;
+        for (int d = 0; d < D; ++d) {
+            double t = __dsub_rn((double)x[d], mu[d]);
+            acc = __dadd_rn(acc, __dmul_rn(w[d], __dmul_rn(t, t)));
+        }
+        if (acc < best) { best = acc; a = g; }
+    }
+    return a;
+}
+
+struct KmArgs {
+    const float *X;
+    int64_t N;
+    int32_t D, DP, G, GS;
+    const double *means;   // lambda (means at the start of the iteration)
+    const double *w;       // [D] FP64 distance weights
+    const float *sw;       // [D] FP32 sqrt(w)
+    double *partial;       // [grid][G][1+2D]   (smem-acc mode) or [1][G][1+2D] (global mode)
+    int32_t *assign;
+    int32_t smem_acc;
+    const DevStatus *status;
+};
+
+// k-means map step (Sec. 3 with Sec. 2.1's chunking): each CTA takes a
+// contiguous chunk of samples; per sample the nearest mean (exact), then the
+// hard statistics count, sum(x - mu_old), sum((x - mu_old)^2) of its mean
+// (shifted by the FP32 old mean so that FP32 partial sums stay small).
+template <int DMAX>
+__global__ void __launch_bounds__(kKmThreads) k_km_pass(KmArgs a)
+{
+    extern __shared__ __align__(16) unsigned char km_smem[];
+    if (a.status->halt) return;
+    const int D = a.D, DP = a.DP, G = a.G, GS = a.GS;
+    float *cent = reinterpret_cast<float *>(km_smem);         // [GS][DP] scaled means
+    float *cnorm = cent + (size_t)GS * DP;                       // [GS]
+    float *S1 = cnorm + GS;                                      // [G][D]   (smem-acc)
+    float *S2 = S1 + (size_t)G * D;                              // [G][D]
+    int *cnt = reinterpret_cast<int *>(S2 + (size_t)G * D);      // [G]
+    __shared__ float s_nmax;
+    __shared__ float s_sw[GMM_MAX_DIMS];
+
+    for (int d = threadIdx.x; d < D; d += blockDim.x) s_sw[d] = a.sw[d];
+    if (a.smem_acc) {
+        for (int k = threadIdx.x; k < G * D; k += blockDim.x) { S1[k] = 0.f; S2[k] = 0.f; }
+        for (int g = threadIdx.x; g < G; g += blockDim.x) cnt[g] = 0;
+    }
+    __syncthreads();
+
+    const int64_t per = (a.N + gridDim.x - 1) / gridDim.x;
+    const int64_t i0 = (int64_t)blockIdx.x * per;
+    const int64_t i1 = min(a.N, i0 + per);
+    const bool one_slab = GS >= G;
+
+    auto load_slab = [&](int g0, int gs) {
+        for (int k = threadIdx.x; k < gs * DP; k += blockDim.x) {
+            int gg = k / DP, d = k - gg * DP;
+            cent[k] = d < D ? (float)(a.means[(size_t)(g0 + gg) * D + d] * (double)s_sw[d]) : 0.f;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_nmax = 0.f;
+        __syncthreads();
+        for (int gg = threadIdx.x; gg < gs; gg += blockDim.x) {
+            float n = 0.f;
+            for (int d = 0; d < D; ++d) n = fmaf(cent[gg * DP + d], cent[gg * DP + d], n);
+            cnorm[gg] = n;
+            atomicMax(reinterpret_cast<int *>(&s_nmax), __float_as_int(n));  // n >= 0
+        }
+        __syncthreads();
+    };
+    float nmax_all = 0.f;
+    if (one_slab) { load_slab(0, G); nmax_all = s_nmax; }
+    else {
+        // max norm over every mean, for the near-tie bound
+        for (int g0 = 0; g0 < G; g0 += GS) { load_slab(g0, min(GS, G - g0)); nmax_all = fmaxf(nmax_all, s_nmax); }
+    }
+
+    for (int64_t base = i0; base < i1; base += blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        const bool valid = i < i1;
+        float xr[DMAX];
+        float xs[DMAX];
+        float snorm = 0.f;
+#pragma unroll
+        for (int d = 0; d < DMAX; ++d) {
+            float v = (valid && d < D) ? a.X[i * D + d] : 0.f;
+            xr[d] = v;
+            xs[d] = d < D ? v * s_sw[d] : 0.f;
+            snorm = fmaf(xs[d], xs[d], snorm);
+        }
+        float b1 = INFINITY, b2 = INFINITY;
+        int a1 = 0;
+        for (int g0 = 0; g0 < G; g0 += GS) {
+            const int gs = min(GS, G - g0);
+            if (!one_slab) { __syncthreads(); load_slab(g0, gs); }
+            for (int gg = 0; gg < gs; ++gg) {
+                const float4 *c4 = reinterpret_cast<const float4 *>(cent + gg * DP);
+                float acc = 0.f;
+#pragma unroll
+                for (int q = 0; q < DMAX / 4; ++q) {
+                    if (q * 4 < DP) {
+                        float4 c = c4[q];
+                        float t0 = xs[4 * q] - c.x, t1 = xs[4 * q + 1] - c.y;
+                        float t2 = xs[4 * q + 2] - c.z, t3 = xs[4 * q + 3] - c.w;
+                        acc = fmaf(t0, t0, acc); acc = fmaf(t1, t1, acc);
+                        acc = fmaf(t2, t2, acc); acc = fmaf(t3, t3, acc);
+                    }
+                }
+                if (acc < b1) { b2 = b1; b1 = acc; a1 = g0 + gg; }
+                else if (acc < b2) { b2 = acc; }
+            }
+        }
+        if (!valid) continue;
+        const float norms = snorm + nmax_all;
+        int best = a1;
+        if (G > 1 && !(b2 - km_err(b2, norms, D) > b1 + km_err(b1, norms, D)))
+            best = km_recheck_fp64(a.X + i * D, D, G, a.means, a.w);
+        a.assign[i] = best;
+        const double *mu = a.means + (size_t)best * D;
+        if (a.smem_acc) {
+            atomicAdd(&cnt[best], 1);
+#pragma unroll
+            for (int d = 0; d < DMAX; ++d) {
+                if (d < D) {
+                    const float u = xr[d] - (float)mu[d];
+                    atomicAdd(&S1[best * D + d], u);
+                    atomicAdd(&S2[best * D + d], u * u);
+                }
+            }
+        } else {
+            double *P = a.partial + (size_t)best * (1 + 2 * D);
+            atomicAdd(P, 1.0);
+#pragma unroll
+            for (int d = 0; d < DMAX; ++d) {
+                if (d < D) {
+                    const double u = (double)(xr[d] - (float)mu[d]);
+                    atomicAdd(P + 1 + d, u);
+                    atomicAdd(P + 1 + D + d, u * u);
+                }
+            }
+        }
+    }
+    if (a.smem_acc) {
+        __syncthreads();
+        const int S = 1 + 2 * D;
+        double *P = a.partial + (size_t)blockIdx.x * G * S;
+        for (int k = threadIdx.x; k < G * S; k += blockDim.x) {
+            int g = k / S, j = k - g * S;
+            double v;
+            if (j == 0) v = (double)cnt[g];
+            else if (j <= D) v = (double)S1[g * D + j - 1];
+            else v = (double)S2[g * D + j - 1 - D];
+            P[k] = v;
+        }
+    }
+}
+
+// k-means reduce + update (Sec. 3 (ii); Eqs. 5-7 with Eq. 19 for the last
+// iteration).  One block per Gaussian, partials summed in CTA order.
+__global__ void k_km_finalize(const double *__restrict__ partial, int n_partial, int64_t N, int32_t D,
+                              int32_t G, double *par, double var_floor, int32_t final_iter,
+                              double *counts, const DevStatus *status)
+{
+    if (status->halt) return;
+    extern __shared__ double red[];   // [1+2D]
+    const int g = blockIdx.x, S = 1 + 2 * D;
+    for (int j = threadIdx.x; j < S; j += blockDim.x) {
+        double s = 0.0;
+        for (int c = 0; c < n_partial; ++c) s += partial[((size_t)c * G + g) * S + j];
+        red[j] = s;
+    }
+    __syncthreads();
+    const double cnt = red[0];
+    if (threadIdx.x == 0) counts[g] = cnt;
+    if (cnt > 0.0) {
+        double *means = par, *dcovs = par + (size_t)G * D, *hefts = par + 2 * (size_t)G * D;
+        for (int d = threadIdx.x; d < D; d += blockDim.x) {
+            const double shift = (double)(float)means[(size_t)g * D + d];
+            const double m1 = red[1 + d] / cnt;
+            if (final_iter) {
+                double v = red[1 + D + d] / cnt - m1 * m1;
+                dcovs[(size_t)g * D + d] = v > var_floor ? v : var_floor;
+            }
+            means[(size_t)g * D + d] = shift + m1;
+        }
+        if (final_iter && threadIdx.x == 0) hefts[g] = cnt / (double)N;
+    }
+}
+
+
+// Dead-mean resurrection (Sec. 3.1), reading documented in the oracle: the
+// most popular mean (largest count, lowest index) gives its lowest-index
+// samples, in increasing order, to the dead means in increasing index order
+// (cycling when there are more dead means than such samples).  Last
+// iteration: a dead mean gets the floored global variance and heft 1/N, and
+// the hefts are renormalised.  One block of 1024 threads.
+__global__ void __launch_bounds__(1024) k_km_dead_fix(const float *__restrict__ X,
+                                                      const int32_t *__restrict__ assign, int64_t N,
+                                                      int32_t D, int32_t G, double *par,
+                                                      const double *__restrict__ counts,
+                                                      const double *__restrict__ gvar_floored,
+                                                      int32_t final_iter, DevStatus *status)
+{
+    extern __shared__ int64_t members[];   // [G]
+    __shared__ int s_pop, s_ndead, s_found;
+    __shared__ int s_warp[32];
+    if (status->halt) return;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (tid == 0) {
+        int pop = 0, nd = 0;
+        for (int g = 0; g < G; ++g) {
+            if (counts[g] > counts[pop]) pop = g;
+            if (!(counts[g] > 0.0)) ++nd;
+        }
+        s_pop = pop; s_ndead = nd; s_found = 0;
+        status->n_dead = nd;
+    }
+    __syncthreads();
+    const int nd = s_ndead;
+    if (nd == 0) return;
+    const int pop = s_pop;
+    const int64_t n_pop = (int64_t)counts[pop];
+    int need = (int)min((int64_t)nd, n_pop);
+    // ordered scan of the assignments for the popular mean's first `need` samples
+    for (int64_t base = 0; base < N; base += blockDim.x) {
+        if (s_found >= need) break;
+        const int64_t i = base + tid;
+        const int f = (i < N && assign[i] == pop) ? 1 : 0;
+        const unsigned bal = __ballot_sync(0xffffffffu, f);
+        if (lane == 0) s_warp[wid] = __popc(bal);
+        __syncthreads();
+        int off = 0, tot = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { if (w < wid) off += s_warp[w]; tot += s_warp[w]; }
+        const int pos = s_found + off + __popc(bal & ((1u << lane) - 1u));
+        if (f && pos < need) members[pos] = i;
+        __syncthreads();
+        if (tid == 0) s_found += tot;
+        __syncthreads();
+    }
+    if (s_found < need) need = s_found;   // counts and assignments disagree: use what was found
+    if (need < 1) return;
+    double *means = par, *dcovs = par + (size_t)G * D, *hefts = par + 2 * (size_t)G * D;
+    int j = 0;
+    for (int g = 0; g < G; ++g) {
+        if (counts[g] > 0.0) continue;
+        const int64_t s = members[j % need];
+        ++j;
+        for (int d = tid; d < D; d += blockDim.x) {
+            means[(size_t)g * D + d] = (double)X[s * D + d];
+            if (final_iter) dcovs[(size_t)g * D + d] = gvar_floored[d];
+        }
+        if (final_iter && tid == 0) hefts[g] = 1.0 / (double)N;
+    }
+    if (final_iter) {
+        __syncthreads();
+        __shared__ double s_hsum;
+        if (tid == 0) {
+            double h = 0.0;
+            for (int g = 0; g < G; ++g) h += hefts[g];
+            s_hsum = h;
+        }
+        __syncthreads();
+        for (int g = tid; g < G; g += blockDim.x) hefts[g] /= s_hsum;
+    }
+}
+
+// ------------------------------------------------------------------------
+// Operands of the E-step from lambda (Eq. 15 with a diagonal covariance):
+//   FP32 form   l_g(x) = c_g - 1/2 sum_d (x_d s_gd - mu_gd s_gd)^2,
+//               s = 1/sigma, c_g = log w_g - D/2 log 2pi - 1/2 sum_d log sigma^2_gd
+//   tensor form the same expanded about the global centre m (x' = x - m,
+//               mu' = mu - m): l_g = ctc_g + sum_d x'^2 (-1/2 iv) + x' (mu' iv),
+//               ctc_g = c_g - 1/2 sum_d mu'^2 iv, packed K-major [G][KP] BF16
+//               (hi part, plus the lo part x - hi for split-BF16).
+// One block per Gaussian; called by k_em_prep and by k_em_finalize.
+// ------------------------------------------------------------------------
+__device__ void prep_operands(int g, int D, int G, const double *mu, const double *var, double w,
+                              const Operands &op, const float *center, int build_tc, double *sh)
+{
+    double lsum = 0.0, qsum = 0.0;
+    for (int d = threadIdx.x; d < D; d += blockDim.x) {
+        const double v = var[d], m = mu[d];
+        const double s = 1.0 / sqrt(v);
+        op.sm[(size_t)g * D + d] = make_float2((float)s, (float)(m * s));
+        op.mu[(size_t)g * D + d] = (float)m;
+        lsum += log(v);
+        if (build_tc) {
+            const double iv = 1.0 / v;
+            const double mc = m - (double)center[d];
+            qsum += mc * mc * iv;
+            const float b0 = (float)(-0.5 * iv), b1 = (float)(mc * iv);
+            const __nv_bfloat16 h0 = __float2bfloat16_rn(b0), h1 = __float2bfloat16_rn(b1);
+            op.B[(size_t)g * op.KP + d] = h0;
+            op.B[(size_t)g * op.KP + D + d] = h1;
+            op.Blo[(size_t)g * op.KP + d] = __float2bfloat16_rn((float)(-0.5 * iv - (double)__bfloat162float(h0)));
+            op.Blo[(size_t)g * op.KP + D + d] = __float2bfloat16_rn((float)(mc * iv - (double)__bfloat162float(h1)));
+        }
+    }
+    if (build_tc)
+        for (int k = 2 * D + threadIdx.x; k < op.KP; k += blockDim.x) {
+            op.B[(size_t)g * op.KP + k] = __float2bfloat16_rn(0.f);
+            op.Blo[(size_t)g * op.KP + k] = __float2bfloat16_rn(0.f);
+        }
+    lsum = block_sum_d(lsum, sh);
+    qsum = block_sum_d(qsum, sh);
+    if (threadIdx.x == 0) {
+        const double c0 = -0.5 * (double)D * kLog2Pi - 0.5 * lsum;
+        const double lw = log(w);
+        op.c[g] = (float)(lw + c0);
+        op.c0[g] = (float)c0;
+        if (build_tc) op.ctc[g] = (float)(lw + c0 - 0.5 * qsum);
+    }
+}
+
+__global__ void k_em_prep(int32_t D, int32_t G, const double *__restrict__ par, Operands op,
+                          const float *__restrict__ center, int32_t build_tc)
+{
+    __shared__ double sh[128];
+    const int g = blockIdx.x;
+    prep_operands(g, D, G, par + (size_t)g * D, par + (size_t)G * D + (size_t)g * D,
+                  par[2 * (size_t)G * D + g], op, center, build_tc, sh);
+}
+
+// ------------------------------------------------------------------------
+// Plain FP32 fused EM pass (the CUDA-core form): per 32-sample tile
+//   E  logits l_g(x_i) for every Gaussian (warp w: Gaussians g = w mod 8,
+//      lane = sample), into shared memory only;
+//   LSE warp-shuffle log-sum-exp per sample (Eqs. 16-18: max + sum of exp),
+//      log p(x_i) added to the CTA's FP64 log-likelihood, responsibilities
+//      l_{g,i} = exp(l_g - log p) (Eq. 3) written over the logits;
+//   M  thread-owned (g, d) pairs accumulate sum l (x - mu_f) and
+//      sum l (x - mu_f)^2 (Eqs. 9-11 shifted by the FP32 mean mu_f of the
+//      iteration start, which keeps FP32 sums small); FP32 in shared memory
+//      for the CTA's chunk, flushed once to the FP64 partial of the CTA.
+// Each CTA owns one contiguous chunk of tiles: the paper's thread t.
+// ------------------------------------------------------------------------
+template <int DMAX>
+__global__ void __launch_bounds__(kEmThreads, 1) k_em_pass_simt(EmPassArgs a)
+{
+    extern __shared__ __align__(16) float em_smem[];
+    if (em_skip(a.status, a.iter)) return;
+    const int D = a.D, G = a.G;
+    float *xT = em_smem;                          // [D][kTP]
+    float *L = xT + (size_t)D * kTP;              // [G][kTP]
+    float *S0 = L + (size_t)G * kTP;              // [G]
+    float *S1 = S0 + G;                           // [G*D]
+    float *S2 = S1 + (size_t)G * D;               // [G*D]
+    __shared__ double s_ll[kWarps];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+
+    for (int k = tid; k < G; k += kEmThreads) S0[k] = 0.f;
+    for (int k = tid; k < G * D; k += kEmThreads) { S1[k] = 0.f; S2[k] = 0.f; }
+
+    const int64_t ntiles = (a.N + kTile - 1) / kTile;
+    const int64_t t0 = ntiles * blockIdx.x / gridDim.x, t1 = ntiles * (blockIdx.x + 1) / gridDim.x;
+    double ll = 0.0;
+    for (int64_t tile = t0; tile < t1; ++tile) {
+        const int64_t i0 = tile * kTile;
+        const int n = (int)min((int64_t)kTile, a.N - i0);
+        __syncthreads();
+        const float *Xt = a.X + i0 * D;
+        for (int k = tid; k < kTile * D; k += kEmThreads) {
+            const int i = k / D, d = k - i * D;
+            xT[d * kTP + i] = i < n ? Xt[k] : 0.f;
+        }
+        __syncthreads();
+        // ---- E: logits
+        {
+            float xr[DMAX];
+#pragma unroll
+            for (int d = 0; d < DMAX; ++d) xr[d] = d < D ? xT[d * kTP + lane] : 0.f;
+            for (int g = w; g < G; g += kWarps) {
+                const float2 *p = a.op.sm + (size_t)g * D;
+                float acc = 0.f;
+#pragma unroll
+                for (int d = 0; d < DMAX; ++d) {
+                    if (d < D) {
+                        const float2 q = __ldg(p + d);
+                        const float t = fmaf(xr[d], q.x, -q.y);
+                        acc = fmaf(t, t, acc);
+                    }
+                }
+                L[g * kTP + lane] = fmaf(-0.5f, acc, __ldg(a.op.c + g));
+            }
+        }
+        __syncthreads();
+        // ---- LSE + responsibilities
+        for (int s = w; s < kTile; s += kWarps) {
+            float m = -INFINITY;
+            for (int g = lane; g < G; g += 32) m = fmaxf(m, L[g * kTP + s]);
+            m = warp_max(m);
+            float sum = 0.f;
+            for (int g = lane; g < G; g += 32) sum += __expf(L[g * kTP + s] - m);
+            sum = warp_sum(sum);
+            const float lse = m + logf(sum);
+            const bool ok = s < n;
+            for (int g = lane; g < G; g += 32) L[g * kTP + s] = ok ? __expf(L[g * kTP + s] - lse) : 0.f;
+            if (lane == 0 && ok) ll += (double)lse;
+        }
+        __syncthreads();
+        // ---- M: thread-owned (g, d) accumulators
+        for (int p = tid; p < G * D; p += kEmThreads) {
+            const int g = p / D, d = p - g * D;
+            const float mu = __ldg(a.op.mu + p);
+            const float *Lg = L + g * kTP;
+            const float *xd = xT + d * kTP;
+            float r1 = 0.f, r2 = 0.f;
+#pragma unroll 8
+            for (int i = 0; i < kTile; ++i) {
+                const float gm = Lg[i];
+                const float u = xd[i] - mu;
+                r1 = fmaf(gm, u, r1);
+                r2 = fmaf(gm * u, u, r2);
+            }
+            S1[p] += r1;
+            S2[p] += r2;
+        }
+        for (int g = tid; g < G; g += kEmThreads) {
+            float r0 = 0.f;
+            for (int i = 0; i < kTile; ++i) r0 += L[g * kTP + i];
+            S0[g] += r0;
+        }
+    }
+    __syncthreads();
+    const int S = 1 + 2 * D;
+    double *P = a.partial + (size_t)blockIdx.x * G * S;
+    for (int k = tid; k < G * S; k += kEmThreads) {
+        const int g = k / S, j = k - g * S;
+        P[k] = j == 0 ? (double)S0[g] : (j <= D ? (double)S1[g * D + j - 1] : (double)S2[g * D + j - 1 - D]);
+    }
+    if (lane == 0) s_ll[w] = ll;
+    __syncthreads();
+    if (tid == 0) {
+        double t = 0.0;
+        for (int k = 0; k < kWarps; ++k) t += s_ll[k];
+        a.ll_partial[blockIdx.x] = t;
+    }
+}
+
+// Log-likelihood reduce (CTA order) and the stopping rule: ll_hist[iter] =
+// log p(X | lambda_iter) / N; with em_tol > 0, iteration iter >= 1 whose gain
+// is below em_tol is the last one.
+__global__ void k_em_ll(const double *__restrict__ ll_partial, int n_partial, int64_t N, int32_t iter,
+                        double em_tol, double *ll_hist, DevStatus *status)
+{
+    if (em_skip(status, iter)) return;
+    if (threadIdx.x != 0) return;
+    double s = 0.0;
+    for (int c = 0; c < n_partial; ++c) s += ll_partial[c];
+    const double m = s / (double)N;
+    ll_hist[iter] = m;
+    if (!isfinite(m)) { set_error(status, GMM_ERR_NONFINITE, iter); return; }
+    status->n_done = iter + 1;
+    if (em_tol > 0.0 && iter >= 1 && m - ll_hist[iter - 1] < em_tol) status->stop_after = iter;
+}
+
+// EM reduce + update (Eqs. 12-14, Eq. 5; floor of Sec. 2.2), then the
+// operands of the next E-step.  One block per Gaussian; CTA-order FP64 sums.
+// A Gaussian whose L_g underflows keeps its mean and covariance (its heft is
+// L_g / N).  A non-finite result stops the call with GMM_ERR_NONFINITE and
+// leaves par_in (the last finite parameters) untouched.
+__global__ void k_em_finalize(EmFinalizeArgs a)
+{
+    extern __shared__ double red[];   // [1+2D]
+    __shared__ double sh[128];
+    __shared__ int s_bad;
+    const DevStatus *st = a.status;
+    if (st->halt || a.iter > st->stop_after) return;
+    const int g = blockIdx.x, D = a.D, G = a.G, S = 1 + 2 * D;
+    for (int j = threadIdx.x; j < S; j += blockDim.x) {
+        double s = 0.0;
+        for (int c = 0; c < a.n_partial; ++c) s += a.partial[((size_t)c * G + g) * S + j];
+        red[j] = s;
+    }
+    if (threadIdx.x == 0) s_bad = 0;
+    __syncthreads();
+    const double Lg = red[0];
+    const double *mi = a.par_in + (size_t)g * D, *vi = a.par_in + (size_t)G * D + (size_t)g * D;
+    double *mo = a.par_out + (size_t)g * D, *vo = a.par_out + (size_t)G * D + (size_t)g * D;
+    const double w = Lg / (double)a.N;
+    const bool live = Lg >= 1e-300;
+    for (int d = threadIdx.x; d < D; d += blockDim.x) {
+        double mu = mi[d], v = vi[d];
+        if (live) {
+            const double shift = a.shift_mode == 0 ? (double)a.op.mu[(size_t)g * D + d] : (double)a.center[d];
+            const double m1 = red[1 + d] / Lg;
+            mu = shift + m1;
+            v = red[1 + D + d] / Lg - m1 * m1;
+            v = v > a.var_floor ? v : a.var_floor;
+        }
+        if (!isfinite(mu) || !isfinite(v)) s_bad = 1;
+        mo[d] = mu;
+        vo[d] = v;
+    }
+    if (threadIdx.x == 0) {
+        a.par_out[2 * (size_t)G * D + g] = w;
+        if (!isfinite(w)) s_bad = 1;
+    }
+    __syncthreads();
+    if (s_bad) { if (threadIdx.x == 0) set_error(a.status, GMM_ERR_NONFINITE, a.iter); return; }
+    prep_operands(g, D, G, mo, vo, w, a.op, a.center, a.build_tc, sh);
+}
+
+// ------------------------------------------------------------------------
+// Inference (Sec. 4.1): log_p with the FP32 operands (online log-sum-exp per
+// thread, one sample per thread), and assign.
+// ------------------------------------------------------------------------
+template <int DMAX>
+__global__ void __launch_bounds__(128) k_log_p(const float *__restrict__ X, int64_t N, int32_t D, int32_t G,
+                                               Operands op, int32_t gsel, double *__restrict__ out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    float xr[DMAX];
+#pragma unroll
+    for (int d = 0; d < DMAX; ++d) xr[d] = d < D ? X[i * D + d] : 0.f;
+    auto logit = [&](int g) {
+        const float2 *p = op.sm + (size_t)g * D;
+        float acc = 0.f;
+#pragma unroll
+        for (int d = 0; d < DMAX; ++d)
+            if (d < D) { const float2 q = __ldg(p + d); const float t = fmaf(xr[d], q.x, -q.y); acc = fmaf(t, t, acc); }
+        return -0.5f * acc;
+    };
+    if (gsel >= 0) { out[i] = (double)logit(gsel) + (double)op.c0[gsel]; return; }
+    float m = -INFINITY, s = 0.f;
+    for (int g = 0; g < G; ++g) {
+        const float l = logit(g) + __ldg(op.c + g);
+        if (l > m) { s = s * __expf(m - l) + 1.f; m = l; }
+        else s += __expf(l - m);
+    }
+    out[i] = (double)m + log((double)s);
+}
+
+template <int DMAX>
+__global__ void __launch_bounds__(128) k_assign(const float *__restrict__ X, int64_t N, int32_t D, int32_t G,
+                                                const double *__restrict__ means, Operands op, int32_t mode,
+                                                int32_t *__restrict__ out, const double *__restrict__ w_ones)
+{
+    __shared__ float s_nmax;
+    if (threadIdx.x == 0) s_nmax = 0.f;
+    __syncthreads();
+    if (mode == GMM_EUCL) {
+        float nm = 0.f;
+        for (int g = threadIdx.x; g < G; g += blockDim.x) {
+            float n = 0.f;
+            for (int d = 0; d < D; ++d) { const float v = op.mu[(size_t)g * D + d]; n = fmaf(v, v, n); }
+            nm = fmaxf(nm, n);
+        }
+        atomicMax(reinterpret_cast<int *>(&s_nmax), __float_as_int(nm));
+        __syncthreads();
+    }
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    float xr[DMAX];
+    float snorm = 0.f;
+#pragma unroll
+    for (int d = 0; d < DMAX; ++d) { xr[d] = d < D ? X[i * D + d] : 0.f; snorm = fmaf(xr[d], xr[d], snorm); }
+    if (mode == GMM_EUCL) {
+        float b1 = INFINITY, b2 = INFINITY;
+        int a1 = 0;
+        for (int g = 0; g < G; ++g) {
+            const float *c = op.mu + (size_t)g * D;
+            float acc = 0.f;
+#pragma unroll
+            for (int d = 0; d < DMAX; ++d)
+                if (d < D) { const float t = xr[d] - __ldg(c + d); acc = fmaf(t, t, acc); }
+            if (acc < b1) { b2 = b1; b1 = acc; a1 = g; }
+            else if (acc < b2) b2 = acc;
+        }
+        const float norms = snorm + s_nmax;
+        int best = a1;
+        if (G > 1 && !(b2 - km_err(b2, norms, D) > b1 + km_err(b1, norms, D)))
+            best = km_recheck_fp64(X + i * D, D, G, means, w_ones);
+        out[i] = best;
+    } else {
+        float bl = -INFINITY;
+        int best = 0;
+        for (int g = 0; g < G; ++g) {
+            const float2 *p = op.sm + (size_t)g * D;
+            float acc = 0.f;
+#pragma unroll
+            for (int d = 0; d < DMAX; ++d)
+                if (d < D) { const float2 q = __ldg(p + d); const float t = fmaf(xr[d], q.x, -q.y); acc = fmaf(t, t, acc); }
+            const float l = fmaf(-0.5f, acc, __ldg(op.c + g));
+            if (l > bl) { bl = l; best = g; }
+        }
+        out[i] = best;
+    }
+}
+
+__global__ void k_status_reset(DevStatus *st)
+{
+    st->code = 0; st->halt = 0; st->stop_after = 0x7fffffff; st->n_done = 0;
+    st->fail_iter = -1; st->n_dead = 0;
+}
+
+__global__ void k_sum_fp64(const double *__restrict__ v, int64_t n, double *out)
+{
+    __shared__ double sh[1024];
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += v[i];
+    s = block_sum_d(s, sh);
+    if (threadIdx.x == 0) *out = s;
+}
+
+__global__ void k_hist(const int32_t *__restrict__ a, int64_t N, int32_t G, unsigned long long *counts)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) {
+        const int g = a[i];
+        if (g >= 0 && g < G) atomicAdd(counts + g, 1ull);
+    }
+}
+
+int dmax_for(int D) { return D <= 16 ? 16 : D <= 32 ? 32 : D <= 64 ? 64 : 128; }
+
+}  // namespace
+
+// ======================================================================== host
+static std::atomic<long long> g_launches{0};
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launches_total() { return g_launches.load(std::memory_order_relaxed); }
+
+size_t em_simt_smem(int32_t D, int32_t G)
+{
+    return sizeof(float) * ((size_t)D * kTP + (size_t)G * kTP + (size_t)G + 2 * (size_t)G * D);
+}
+
+bool em_simt_supported(int32_t D, int32_t G)
+{
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return D >= 1 && D <= GMM_MAX_DIMS && em_simt_smem(D, G) <= (size_t)optin;
+}
+
+int em_simt_grid(int32_t D, int32_t G, int sms)
+{
+    const size_t sm = em_simt_smem(D, G);
+    int per = (int)((200u * 1024u) / (sm + 2048));
+    per = per < 1 ? 1 : (per > 4 ? 4 : per);
+    return sms * per;
+}
+
+int km_grid(int32_t D, int32_t G, int sms)
+{
+    (void)D; (void)G;
+    return sms * 2;
+}
+
+cudaError_t launch_global_stats(const float *X, int64_t N, int32_t D, double var_floor, int32_t dist,
+                                double *partial, int32_t grid, double *gmean, double *gvar_floored,
+                                double *wdist, float *sw, float *center, cudaStream_t s)
+{
+    const int R = D >= 256 ? 1 : 256 / D;
+    const int threads = ((R * D + 31) / 32) * 32;
+    const size_t sm = sizeof(double) * threads;
+    k_gstats<1><<<grid, threads, sm, s>>>(X, N, D, nullptr, partial);
+    k_gstats_final<1><<<(D + 127) / 128, 128, 0, s>>>(partial, grid, N, D, var_floor, dist, gmean,
+                                                        gvar_floored, wdist, sw, center);
+    k_gstats<2><<<grid, threads, sm, s>>>(X, N, D, gmean, partial);
+    k_gstats_final<2><<<(D + 127) / 128, 128, 0, s>>>(partial, grid, N, D, var_floor, dist, gmean,
+                                                        gvar_floored, wdist, sw, center);
+    count_launches(4);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_seeds(const float *X, int32_t D, int32_t G, const int64_t *idx, double *par,
+                                cudaStream_t s)
+{
+    k_gather_seeds<<<G, 128, 0, s>>>(X, D, G, idx, par);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+static size_t km_slab_smem(int32_t D, int32_t G, int *GS_out, int *DP_out)
+{
+    const int DP = (D + 3) & ~3;
+    int GS = (int)((64 * 1024) / (sizeof(float) * (DP + 1)));
+    if (GS > G) GS = G;
+    if (GS < 1) GS = 1;
+    *GS_out = GS;
+    *DP_out = DP;
+    return sizeof(float) * ((size_t)GS * DP + GS);
+}
+
+cudaError_t launch_km_pass(const float *X, int64_t N, int32_t D, int32_t G, const double *par,
+                           const double *wdist, const float *sw, double *partial, int32_t grid,
+                           int32_t *assign, DevStatus *status, int32_t *n_partial, cudaStream_t s)
+{
+    int GS, DP;
+    size_t sm = km_slab_smem(D, G, &GS, &DP);
+    const size_t acc = sizeof(float) * 2 * (size_t)G * D + sizeof(int) * G;
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    KmArgs a{X, N, D, DP, G, GS, par, wdist, sw, partial, assign, 1, status};
+    *n_partial = grid;
+    if (sm + acc + 1024 <= (size_t)optin) {
+        sm += acc;
+    } else {
+        *n_partial = 1;
+        a.smem_acc = 0;
+        cudaError_t e = cudaMemsetAsync(partial, 0, sizeof(double) * (size_t)G * (1 + 2 * D), s);
+        if (e != cudaSuccess) return e;
+    }
+    const int dm = dmax_for(D);
+#define KM_LAUNCH(DM)                                                                              \
+    do {                                                                                           \
+        cudaFuncSetAttribute(k_km_pass<DM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
+        k_km_pass<DM><<<grid, kKmThreads, sm, s>>>(a);                                             \
+    } while (0)
+    if (dm == 16) KM_LAUNCH(16);
+    else if (dm == 32) KM_LAUNCH(32);
+    else if (dm == 64) KM_LAUNCH(64);
+    else KM_LAUNCH(128);
+#undef KM_LAUNCH
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_km_finalize(const double *partial, int32_t n_partial, int64_t N, int32_t D, int32_t G,
+                               double *par, double var_floor, int32_t final_iter, double *counts,
+                               const float *X, const int32_t *assign, const double *gvar_floored,
+                               DevStatus *status, cudaStream_t s)
+{
+    k_km_finalize<<<G, 128, sizeof(double) * (1 + 2 * D), s>>>(partial, n_partial, N, D, G, par, var_floor,
+                                                               final_iter, counts, status);
+    const size_t sm = sizeof(int64_t) * (size_t)G;
+    if (sm > 48 * 1024)
+        cudaFuncSetAttribute(k_km_dead_fix, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_km_dead_fix<<<1, 1024, sm, s>>>(X, assign, N, D, G, par, counts, gvar_floored, final_iter, status);
+    count_launches(2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_em_prep(int32_t D, int32_t G, const double *par, Operands op, const float *center,
+                           int32_t build_tc, cudaStream_t s)
+{
+    k_em_prep<<<G, 128, 0, s>>>(D, G, par, op, center, build_tc);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_em_pass_simt(const EmPassArgs &a, int32_t grid, cudaStream_t s)
+{
+    const size_t sm = em_simt_smem(a.D, a.G);
+    const int dm = dmax_for(a.D);
+#define EM_LAUNCH(DM)                                                                                   \
+    do {                                                                                                \
+        cudaFuncSetAttribute(k_em_pass_simt<DM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
+        k_em_pass_simt<DM><<<grid, kEmThreads, sm, s>>>(a);                                             \
+    } while (0)
+    if (dm == 16) EM_LAUNCH(16);
+    else if (dm == 32) EM_LAUNCH(32);
+    else if (dm == 64) EM_LAUNCH(64);
+    else EM_LAUNCH(128);
+#undef EM_LAUNCH
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_em_finalize(const EmFinalizeArgs &a, cudaStream_t s)
+{
+    k_em_ll<<<1, 32, 0, s>>>(a.ll_partial, a.n_partial, a.N, a.iter, a.em_tol, a.ll_hist, a.status);
+    k_em_finalize<<<a.G, 128, sizeof(double) * (1 + 2 * a.D), s>>>(a);
+    count_launches(2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_log_p(const float *X, int64_t N, int32_t D, int32_t G, Operands op, int32_t g,
+                         double *out, cudaStream_t s)
+{
+    const int blocks = (int)((N + 127) / 128);
+    const int dm = dmax_for(D);
+    if (dm == 16) k_log_p<16><<<blocks, 128, 0, s>>>(X, N, D, G, op, g, out);
+    else if (dm == 32) k_log_p<32><<<blocks, 128, 0, s>>>(X, N, D, G, op, g, out);
+    else if (dm == 64) k_log_p<64><<<blocks, 128, 0, s>>>(X, N, D, G, op, g, out);
+    else k_log_p<128><<<blocks, 128, 0, s>>>(X, N, D, G, op, g, out);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_assign(const float *X, int64_t N, int32_t D, int32_t G, const double *par, Operands op,
+                          int32_t mode, int32_t *out, const float *sw_ones, const double *w_ones,
+                          DevStatus *status, cudaStream_t s)
+{
+    (void)sw_ones; (void)status;
+    const int blocks = (int)((N + 127) / 128);
+    const int dm = dmax_for(D);
+    if (dm == 16) k_assign<16><<<blocks, 128, 0, s>>>(X, N, D, G, par, op, mode, out, w_ones);
+    else if (dm == 32) k_assign<32><<<blocks, 128, 0, s>>>(X, N, D, G, par, op, mode, out, w_ones);
+    else if (dm == 64) k_assign<64><<<blocks, 128, 0, s>>>(X, N, D, G, par, op, mode, out, w_ones);
+    else k_assign<128><<<blocks, 128, 0, s>>>(X, N, D, G, par, op, mode, out, w_ones);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_status_reset(DevStatus *st, cudaStream_t s)
+{
+    k_status_reset<<<1, 1, 0, s>>>(st);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sum_fp64(const double *v, int64_t n, double *out, cudaStream_t s)
+{
+    k_sum_fp64<<<1, 1024, 0, s>>>(v, n, out);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hist(const int32_t *a, int64_t N, int32_t G, unsigned long long *counts, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(unsigned long long) * G, s);
+    if (e != cudaSuccess) return e;
+    if (N > 0) k_hist<<<(int)((N + 255) / 256), 256, 0, s>>>(a, N, G, counts);
+    count_launches(N > 0 ? 1 : 0);
+    return cudaGetLastError();
+}
+
+}  // namespace gmm

@@ -1,0 +1,248 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs.
+
+Tolerances (the FP32 CUDA-core path):
+  k-means assignments  bit-exact, except samples whose two nearest oracle
+                       distances differ by < 1e-6 relative
+  EM parameters        1e-4 relative, with absolute floors 1e-4 * global std
+                       (means), 1e-4 * variance (dcovs), 1e-4 / G (hefts)
+  log-likelihoods      1e-6 relative (FP32 logits, FP64 sums)
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1707_09094_gb300 import GMM, GMM_EUCL, GMM_KEEP_EXISTING, GMM_MAHA, GMM_PROB, GmmError, synth
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1707_09094_gb300 import build
+    build.build()
+
+
+def dev(X):
+    return torch.from_numpy(np.ascontiguousarray(X)).cuda()
+
+
+def assert_params(got, ref, X, rtol=RTOL):
+    m, v, h = got
+    M, V, H = ref
+    gstd = X.astype(np.float64).std(axis=0)
+    G = M.shape[0]
+    np.testing.assert_allclose(m, M, rtol=rtol, atol=(rtol * gstd)[None, :])
+    np.testing.assert_allclose(v, V, rtol=rtol, atol=0)
+    np.testing.assert_allclose(h, H, rtol=rtol, atol=rtol / G)
+
+
+def near_tie_mask(b1, b2, rel=1e-6):
+    return (b2 - b1) < rel * np.maximum(np.abs(b2), 1e-300)
+
+
+def km_weights(X, dist, var_floor):
+    _, gv = oracle.global_stats(X)
+    gv = np.maximum(gv, var_floor)
+    return (1.0 / gv if dist == GMM_MAHA else np.ones_like(gv)), gv
+
+
+# ------------------------------------------------------------ seeding
+def test_random_subset_seeds_match_oracle():
+    X, _, _ = synth.make("c1", N=20000)
+    g = GMM().learn(dev(X), 8, km_iter=0, em_iter=0, seed=77)
+    m, v, h = g.get_params()
+    idx = oracle.seed_random_subset(X.shape[0], 8, 77)
+    np.testing.assert_array_equal(m, X[idx].astype(np.float64))
+    assert (v == 1.0).all() and np.allclose(h, 1 / 8)
+
+
+# ------------------------------------------------------------ k-means
+@pytest.mark.parametrize("dist", [GMM_MAHA, GMM_EUCL])
+@pytest.mark.parametrize("shape", [(100000, 10, 8), (5003, 13, 5), (129, 3, 3), (4097, 60, 37)])
+def test_kmeans_one_iteration_exact(shape, dist):
+    N, D, G = shape
+    X, _, _ = synth.make("c1", N=N, D=D, G=G, seed=11 + N)
+    seeds = synth.seeds_subset(X, G, 5)
+    w, gv = km_weights(X, dist, 1e-10)
+    M, V, H, A = oracle.kmeans(X, seeds, w, gv, 1, 1e-10)
+    _, b1, b2 = oracle.km_assign(X, seeds, w)
+    g = GMM().set_params(seeds, np.ones_like(seeds), np.full(G, 1.0 / G))
+    a = g.kmeans(dev(X), 1, dist_mode=dist).cpu().numpy()
+    ok = ~near_tie_mask(b1, b2)
+    np.testing.assert_array_equal(a[ok], A[ok])
+    if ok.all():
+        assert_params(g.get_params(), (M, V, H), X, rtol=1e-7)
+
+
+def test_kmeans_ten_iterations_c1():
+    X, _, _ = synth.make("c1")
+    seeds = synth.seeds_subset(X, 8, 9)
+    w, gv = km_weights(X, GMM_MAHA, 1e-10)
+    M, V, H, A = oracle.kmeans(X, seeds, w, gv, 10, 1e-10)
+    g = GMM().set_params(seeds, np.ones_like(seeds), np.full(8, 1.0 / 8))
+    a = g.kmeans(dev(X), 10).cpu().numpy()
+    # the last iteration's distances, from the oracle's means before it
+    Mprev = oracle.kmeans(X, seeds, w, gv, 9, 1e-10)[0]
+    _, b1, b2 = oracle.km_assign(X, Mprev, w)
+    ok = ~near_tie_mask(b1, b2)
+    np.testing.assert_array_equal(a[ok], A[ok])
+    assert_params(g.get_params(), (M, V, H), X)
+
+
+def test_kmeans_dead_mean_resurrection_gpu():
+    X = np.array([[0.0], [0.1], [0.2], [10.0], [10.1]], np.float32)
+    seeds = np.array([[0.1], [10.05], [1e6]])
+    g = GMM().set_params(seeds, np.ones_like(seeds), np.full(3, 1 / 3))
+    g.kmeans(dev(X), 1, dist_mode=GMM_EUCL, var_floor=1e-10)
+    w, gv = km_weights(X, GMM_EUCL, 1e-10)
+    M, V, H, A = oracle.kmeans(X, seeds, w, gv, 1, 1e-10)
+    m, v, h = g.get_params()
+    np.testing.assert_allclose(m, M, rtol=1e-12)
+    np.testing.assert_allclose(v, V, rtol=1e-6)
+    np.testing.assert_allclose(h, H, rtol=1e-15)
+
+
+# ------------------------------------------------------------ EM (FP32 form)
+def _start(X, G, seed):
+    seeds = synth.seeds_subset(X, G, seed)
+    w, gv = km_weights(X, GMM_MAHA, 1e-10)
+    return oracle.kmeans(X, seeds, w, gv, 5, 1e-10)[:3]
+
+
+@pytest.mark.parametrize("shape", [(100000, 10, 8), (7, 3, 2), (33, 1, 3), (1000, 13, 1), (2049, 60, 40),
+                                   (3001, 64, 17)])
+def test_em_iterations_match_oracle(shape):
+    N, D, G = shape
+    X, _, _ = synth.make("c1", N=N, D=D, G=G, seed=3 + N)
+    start = _start(X, G, 2) if G > 1 and N > 50 else (synth.seeds_subset(X, G, 1), np.ones((G, D)),
+                                                      np.full(G, 1.0 / G))
+    n_iter = 3
+    M, V, H, ll = oracle.em_iterate(X, *start, n_iter, 1e-10)
+    g = GMM().set_params(*start)
+    g.em_iterate(dev(X), n_iter, var_floor=1e-10, recompute_center=True)
+    assert_params(g.get_params(), (M, V, H), X)
+    np.testing.assert_allclose(g.ll_history(), ll, rtol=1e-6, atol=1e-6)
+
+
+def test_single_gaussian_closed_form_gpu():
+    rng = np.random.default_rng(4)
+    X = rng.normal(3.0, 2.0, (20011, 6)).astype(np.float32)
+    g = GMM().set_params(np.zeros((1, 6)), np.ones((1, 6)), np.ones(1))
+    g.em_iterate(dev(X), 1, recompute_center=True)
+    m, v, h = g.get_params()
+    Xd = X.astype(np.float64)
+    np.testing.assert_allclose(m[0], Xd.mean(axis=0), rtol=1e-6)
+    np.testing.assert_allclose(v[0], Xd.var(axis=0), rtol=1e-5)
+    assert h[0] == pytest.approx(1.0, abs=1e-12)
+
+
+def test_learn_end_to_end_c1_matches_oracle():
+    X, _, _ = synth.make("c1")
+    g = GMM().learn(dev(X), 8, km_iter=10, em_iter=10, seed=1001, var_floor=1e-10)
+    M, V, H, ll = oracle.learn(X, 8, seed=1001, km_iter=10, em_iter=10, var_floor=1e-10)
+    assert_params(g.get_params(), (M, V, H), X)
+    np.testing.assert_allclose(g.ll_history(), ll, rtol=1e-6)
+    assert (np.diff(g.ll_history()) >= -1e-6).all()
+
+
+def test_learn_accepts_host_input_and_em_tol():
+    X, _, _ = synth.make("c1", N=30000)
+    g = GMM().learn(X, 8, km_iter=5, em_iter=50, seed=3, em_tol=1e-6)
+    M, V, H, ll = oracle.learn(X, 8, seed=3, km_iter=5, em_iter=50, em_tol=1e-6)
+    assert len(g.ll_history()) == len(ll)
+    assert_params(g.get_params(), (M, V, H), X)
+
+
+def test_variance_floor_and_constant_dimension():
+    X, _, _ = synth.make("c1", N=20000)
+    X[:, 2] = 1.5
+    g = GMM().learn(dev(X), 8, km_iter=3, em_iter=3, seed=5, var_floor=1e-3)
+    _, v, _ = g.get_params()
+    assert (v >= 1e-3).all()
+    np.testing.assert_allclose(v[:, 2], 1e-3)
+
+
+def test_nonfinite_input_is_reported_and_model_kept():
+    X, _, _ = synth.make("c1", N=5000)
+    g = GMM().learn(dev(X), 4, km_iter=2, em_iter=2, seed=1)
+    before = g.get_params()
+    Xb = X.copy()
+    Xb[17, 3] = np.nan
+    with pytest.raises(GmmError) as e:
+        g.em_iterate(dev(Xb), 2)
+    assert e.value.status == -2
+    after = g.get_params()
+    for a, b in zip(before, after):
+        np.testing.assert_array_equal(a, b)
+
+
+def test_argument_errors():
+    X, _, _ = synth.make("c1", N=100)
+    with pytest.raises(GmmError) as e:
+        GMM().learn(dev(X), 101)
+    assert e.value.status == -1
+    with pytest.raises(GmmError) as e:
+        GMM().learn(dev(X), 4, seed_mode=GMM_KEEP_EXISTING)
+    assert e.value.status == -6
+
+
+# ------------------------------------------------------------ inference
+@pytest.mark.parametrize("shape", [(10000, 10, 8), (333, 60, 256), (65, 1, 1), (1000, 128, 5)])
+def test_log_p_and_assign_match_oracle(shape):
+    N, D, G = shape
+    X, _, mix = synth.make("c1", N=N, D=D, G=G, seed=21 + D)
+    m, v, h = mix.means, mix.stds ** 2, mix.hefts
+    g = GMM().set_params(m, v, h)
+    Xd = dev(X)
+    lp = g.log_p(Xd).cpu().numpy()
+    ref = oracle.log_p(X, m, v, h)
+    np.testing.assert_allclose(lp, ref, rtol=1e-6, atol=1e-5)
+    for k in (0, G - 1):
+        np.testing.assert_allclose(g.log_p(Xd, k).cpu().numpy(), oracle.log_p(X, m, v, h, g=k), rtol=1e-6, atol=1e-5)
+    assert g.avg_log_p(Xd) == pytest.approx(ref.mean(), rel=1e-6)
+    a_e = g.assign(Xd, GMM_EUCL).cpu().numpy()
+    _, b1, b2 = oracle.km_assign(X, m, np.ones(D))
+    ok = ~near_tie_mask(b1, b2)
+    np.testing.assert_array_equal(a_e[ok], oracle.assign(X, m, v, h, 0)[ok])
+    a_p = g.assign(Xd, GMM_PROB).cpu().numpy()
+    lt = np.stack([np.log(h[k]) + oracle.log_p(X, m, v, h, g=k) for k in range(G)], axis=1)
+    srt = np.sort(lt, axis=1)
+    ok = (srt[:, -1] - srt[:, -2]) > 1e-4 * np.abs(srt[:, -1]) + 1e-4 if G > 1 else np.ones(N, bool)
+    np.testing.assert_array_equal(a_p[ok], oracle.assign(X, m, v, h, 2)[ok])
+    hist = g.raw_hist(Xd, GMM_EUCL)
+    np.testing.assert_array_equal(hist, np.bincount(a_e, minlength=G))
+    np.testing.assert_allclose(g.norm_hist(Xd, GMM_EUCL), hist / N)
+
+
+# ------------------------------------------------------------ full size (c2)
+@pytest.fixture(scope="module")
+def c2():
+    X, lab, mix = synth.make("c2")
+    return X, dev(X), mix
+
+
+def test_c2_full_size_em_iteration_fp32(c2):
+    """One FP32 EM iteration at the benchmark's full size (N=2e6, D=60,
+    G=256), compared with the oracle run over the same data (MapReduce
+    chunks across the host cores)."""
+    X, Xd, mix = c2
+    start = (mix.means, mix.stds ** 2 * 1.2, mix.hefts)
+    start = tuple(np.array(a, dtype=np.float64) for a in start)
+    g = GMM().set_params(*start)
+    g.em_iterate(Xd, 1, recompute_center=True)
+    M, V, H, ll = oracle.em_iterate(X, *start, 1, 1e-10, n_chunks=max(oracle.num_threads(), 1) * 4)
+    assert_params(g.get_params(), (M, V, H), X)
+    np.testing.assert_allclose(g.ll_history(), ll, rtol=1e-6)
+
+
+def test_c2_full_size_log_p_sampled(c2):
+    X, Xd, mix = c2
+    m, v, h = mix.means, mix.stds ** 2, mix.hefts
+    g = GMM().set_params(m, v, h)
+    lp = g.log_p(Xd).cpu().numpy()
+    idx = np.random.default_rng(0).choice(X.shape[0], 4000, replace=False)
+    np.testing.assert_allclose(lp[idx], oracle.log_p(X[idx], m, v, h), rtol=1e-6, atol=1e-5)
