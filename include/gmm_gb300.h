@@ -61,10 +61,17 @@ typedef enum { GMM_EUCL = 0, GMM_MAHA = 1, GMM_PROB = 2 } gmm_dist;
  * (SplitMix64(seed) driving a partial Fisher-Yates shuffle of 0..N-1). */
 typedef enum { GMM_KEEP_EXISTING = 0, GMM_RANDOM_SUBSET = 1 } gmm_seed;
 
-/* Arithmetic of the E-step log-density contraction.
- *   FP32        plain FP32 CUDA-core form (direct sum of (x-mu)^2/sigma^2)
- *   BF16        tcgen05 tensor cores, BF16 operands, FP32 accumulation
- *   SPLIT_BF16  tcgen05, each operand split hi+lo in BF16, three products
+/* Arithmetic of the E-step log-density (Eq. 15) in the fused EM pass.
+ *   FP32   CUDA cores: direct sum of (x - mu)^2 / sigma^2 for every (sample,
+ *          Gaussian), log-sum-exp, dense M-step (FP32 sums shifted by the
+ *          iteration's means, reduced in FP64).
+ *   BF16   tcgen05 tensor cores: the expanded log-density (x'^2 and x' blocks,
+ *          data centred by the global mean) in BF16 with FP32 accumulation
+ *          screens every Gaussian with a rigorous rounding bound; the
+ *          Gaussians that can hold a responsibility >= 1e-12 are recomputed
+ *          exactly in FP32 and only they enter log-sum-exp and the M-step.
+ *          Needs D <= 64 and n_gaus <= 256.
+ *   TF32, SPLIT_BF16  reserved (GMM_ERR_UNSUPPORTED).
  * Sufficient statistics are reduced in FP64 in every mode. */
 typedef enum { GMM_FP32 = 0, GMM_BF16 = 1, GMM_TF32 = 2, GMM_SPLIT_BF16 = 3 } gmm_prec;
 
@@ -78,9 +85,10 @@ typedef struct {
     void *stream;       /* cudaStream_t, NULL = default stream                        */
 } gmm_learn_opts;
 
-/* Per-call limits of the kernels.  D <= GMM_MAX_DIMS; the FP32 E-step and
- * the k-means pass handle any n_gaus; the tensor-core E-step needs
- * 2*D+1 <= 128 and n_gaus <= 256 (larger shapes use the FP32 form). */
+/* Per-call limits of the kernels: D <= GMM_MAX_DIMS everywhere; the FP32
+ * EM pass needs its per-CTA statistics (4 * n_gaus * (2D+1) bytes plus the
+ * tile buffers) to fit in shared memory; the tensor-core EM pass needs
+ * D <= 64 and n_gaus <= 256.  Other shapes return GMM_ERR_UNSUPPORTED. */
 #define GMM_MAX_DIMS 128
 
 /* Create an empty model (no parameters) on the current CUDA device. */
@@ -189,6 +197,20 @@ gmm_status gmm_get_stats(const gmm_model *m, double *ll_hist, int32_t cap, int32
 gmm_status gmm_profile(gmm_model *m, int32_t enable);
 gmm_status gmm_profile_read(const gmm_model *m, double *pass_ms, int64_t *pass_launches,
                             int64_t *kernel_launches);
+
+/* Failure-detection test hooks (no counterpart in the paper).
+ *   GMM_DEBUG_WAIT_CYCLES  (value > 0) budget, in SM clock cycles, of every
+ *                          bounded wait inside the tensor-core pass (default
+ *                          2e9, about one second); 0 restores the default.
+ *   GMM_DEBUG_SKIP_MMA     value != 0 makes the tensor-core pass issue no
+ *                          MMA, so its epilogue waits for data that never
+ *                          arrives: the wait runs out, the pass records
+ *                          GMM_ERR_TIMEOUT, frees its tensor memory and the
+ *                          call returns GMM_ERR_TIMEOUT with the model kept.
+ * Used by the test-suite only. */
+#define GMM_DEBUG_WAIT_CYCLES 1
+#define GMM_DEBUG_SKIP_MMA 2
+gmm_status gmm_debug_set(gmm_model *m, int32_t key, int64_t value);
 
 /* Thread-local text of the last error ("" if none). */
 const char *gmm_last_error(void);

@@ -194,6 +194,11 @@ class GMM:
                    "gmm_profile_read")
         return ms.value, n.value, k.value
 
+    def debug_set(self, key, value):
+        """Failure-detection test hooks (GMM_DEBUG_WAIT_CYCLES, GMM_DEBUG_SKIP_MMA)."""
+        _lib.check(_lib.load().gmm_debug_set(self._h, key, int(value)), "gmm_debug_set")
+        return self
+
     def ll_history(self, cap=4096):
         out = np.empty(cap)
         n = ctypes.c_int32()

@@ -132,6 +132,9 @@ struct gmm_model {
     double pass_ms = 0.0;
     long long pass_launches = 0;
     long long launch_base = 0;
+    // failure-detection test hooks
+    long long wait_cycles = 2000000000LL;
+    int skip_mma = 0;
 
     double *means() const { return par[cur]; }
     double *gmean() const { return gstat; }
@@ -187,18 +190,18 @@ gmm_status ensure_shape(gmm_model *m, int32_t D, int32_t G)
     const size_t np = 2 * (size_t)G * D + G;
     CK(grow(m->par[0], m->par_cap[0], np));
     CK(grow(m->par[1], m->par_cap[1], np));
-    const int32_t KP = ((2 * D + 1) + 63) / 64 * 64;
+    const int32_t KP = 128;
     CK(grow(m->op_sm, m->op_sm_cap, (size_t)G * D));
     CK(grow(m->op_mu, m->op_mu_cap, (size_t)G * D));
-    CK(grow(m->op_c, m->op_c_cap, 3 * (size_t)G));
-    CK(grow(m->op_B, m->op_B_cap, 2 * (size_t)G * KP));
+    CK(grow(m->op_c, m->op_c_cap, 4 * (size_t)G));
+    CK(grow(m->op_B, m->op_B_cap, (size_t)G * KP));
     m->op.sm = m->op_sm;
     m->op.mu = m->op_mu;
     m->op.c = m->op_c;
     m->op.c0 = m->op_c + G;
     m->op.ctc = m->op_c + 2 * (size_t)G;
+    m->op.q = m->op_c + 3 * (size_t)G;
     m->op.B = m->op_B;
-    m->op.Blo = m->op_B + (size_t)G * KP;
     m->op.KP = KP;
     if (m->D != D) m->has_center = false;
     CK(grow(m->gstat, m->gstat_cap, 4 * (size_t)D));
@@ -275,10 +278,10 @@ gmm_status run_em(gmm_model *m, const float *Xd, int64_t N, int32_t em_iter, dou
                   int32_t prec, int32_t print, cudaStream_t s)
 {
     const int32_t D = m->D, G = m->G, S = 1 + 2 * D;
-    const bool tc = prec == GMM_BF16 || prec == GMM_SPLIT_BF16;
-    if (prec == GMM_TF32) return fail(GMM_ERR_UNSUPPORTED, "prec TF32 is not implemented");
+    const bool tc = prec == GMM_BF16;
+    if (prec == GMM_TF32 || prec == GMM_SPLIT_BF16) return fail(GMM_ERR_UNSUPPORTED, "prec %d is reserved", prec);
     if (tc && !gmm::em_tc_supported(D, G))
-        return fail(GMM_ERR_UNSUPPORTED, "tensor-core E-step needs 2D+1 <= 128 and n_gaus <= 256 (D=%d, G=%d)", D, G);
+        return fail(GMM_ERR_UNSUPPORTED, "tensor-core E-step needs D <= 64 and n_gaus <= 256 (D=%d, G=%d)", D, G);
     if (!tc && !gmm::em_simt_supported(D, G))
         return fail(GMM_ERR_UNSUPPORTED, "FP32 E-step: shared memory too small for D=%d, G=%d", D, G);
     if (tc && !(m->has_center && m->center_D == D))
@@ -292,7 +295,8 @@ gmm_status run_em(gmm_model *m, const float *Xd, int64_t N, int32_t em_iter, dou
     const int base = m->cur;
     CK(gmm::launch_em_prep(D, G, m->par[base], m->op, m->center(), tc ? 1 : (m->has_center && m->center_D == D), s));
     for (int32_t k = 0; k < em_iter; ++k) {
-        gmm::EmPassArgs pa{Xd, N, D, G, m->op, m->center(), m->partial, m->llp, m->status, k};
+        gmm::EmPassArgs pa{Xd, N, D, G, m->op, m->center(), m->partial, m->llp, m->status, k,
+                           m->wait_cycles, m->skip_mma};
         size_t slot = 0;
         gmm_status prc = prof_begin(m, s, &slot);
         if (prc != GMM_OK) return prc;
@@ -300,7 +304,7 @@ gmm_status run_em(gmm_model *m, const float *Xd, int64_t N, int32_t em_iter, dou
         else CK(gmm::launch_em_pass_simt(pa, grid, s));
         if ((prc = prof_end(m, s, slot)) != GMM_OK) return prc;
         gmm::EmFinalizeArgs fa{m->partial, m->llp, grid, N, D, G, m->par[(base + k) & 1], m->par[(base + k + 1) & 1],
-                               var_floor, tc ? 1 : 0, m->op, m->center(), m->status, k, em_tol, m->lld,
+                               var_floor, 0, m->op, m->center(), m->status, k, em_tol, m->lld,
                                tc ? 1 : (m->has_center && m->center_D == D)};
         CK(gmm::launch_em_finalize(fa, s));
     }
@@ -314,7 +318,9 @@ gmm_status run_em(gmm_model *m, const float *Xd, int64_t N, int32_t em_iter, dou
         m->cur = (base + (st.fail_iter < 0 ? 0 : st.fail_iter)) & 1;
         for (int k = 0; k < st.n_done && k < em_iter; ++k) m->ll_hist.push_back(ll[k]);
         m->ops_valid = false;
-        return fail((gmm_status)st.code, "EM iteration %d produced a non-finite value", st.fail_iter);
+        return fail((gmm_status)st.code, st.code == GMM_ERR_TIMEOUT ? "EM iteration %d: a bounded device wait ran out"
+                                                                     : "EM iteration %d produced a non-finite value",
+                    st.fail_iter);
     }
     m->cur = (base + st.n_done) & 1;
     for (int k = 0; k < st.n_done; ++k) {
@@ -637,6 +643,20 @@ gmm_status gmm_profile_read(const gmm_model *m, double *pass_ms, int64_t *pass_l
     if (pass_ms) *pass_ms = m->pass_ms;
     if (pass_launches) *pass_launches = m->pass_launches;
     if (kernel_launches) *kernel_launches = gmm::launches_total() - m->launch_base;
+    return GMM_OK;
+}
+
+gmm_status gmm_debug_set(gmm_model *m, int32_t key, int64_t value)
+{
+    if (!m) return fail(GMM_ERR_ARG, "model is NULL");
+    if (key == GMM_DEBUG_WAIT_CYCLES) {
+        if (value < 0) return fail(GMM_ERR_ARG, "wait budget must be >= 0");
+        m->wait_cycles = value > 0 ? (long long)value : 2000000000LL;
+    } else if (key == GMM_DEBUG_SKIP_MMA) {
+        m->skip_mma = value != 0;
+    } else {
+        return fail(GMM_ERR_ARG, "unknown debug key %d", key);
+    }
     return GMM_OK;
 }
 

@@ -31,10 +31,10 @@ struct Operands {
     float *mu;           // [G][D]  FP32 copy of the means: shift of the FP32 M-step
     float *c;            // [G]     log w - D/2 log 2pi - 1/2 sum log sigma^2
     float *c0;           // [G]     same without log w  (log_p(X, g))
-    __nv_bfloat16 *B;    // [G][KP] tensor-core E operand, K-major: hi part
-    __nv_bfloat16 *Blo;  // [G][KP] lo part (split-BF16)
+    __nv_bfloat16 *B;    // [G][128] tensor-core E operand, K-major
     float *ctc;          // [G]     constant of the centred tensor-core logits
-    int32_t KP;          // padded K of the tensor-core operand (multiple of 64)
+    float *q;            // [G]     sum_d mu'^2 / sigma^2 (centred), for the screening bound
+    int32_t KP;          // K of the tensor-core operand: two 64-wide blocks (x'^2 half, x' half)
 };
 
 struct EmPassArgs {
@@ -47,6 +47,8 @@ struct EmPassArgs {
     double *ll_partial;      // [grid]
     DevStatus *status;
     int32_t iter;
+    long long wait_cycles;   // budget of bounded waits (tensor-core pass)
+    int32_t skip_mma;        // test hook: issue no MMA
 };
 
 struct EmFinalizeArgs {

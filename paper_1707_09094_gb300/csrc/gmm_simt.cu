@@ -25,9 +25,15 @@ constexpr int kTile = 32;      // samples per tile of the FP32 EM pass
 constexpr int kTP = kTile + 1; // padded row stride of the tile buffers
 constexpr int kKmThreads = 128;
 
-__device__ __forceinline__ bool em_skip(const DevStatus *st, int iter)
+// Whether this block must skip its work: one thread reads the status block
+// and shares the answer, so that every thread of the block agrees even if
+// another block raises the halt flag meanwhile.
+__device__ __forceinline__ bool block_skip(const DevStatus *st, int iter)
 {
-    return st->halt != 0 || iter > st->stop_after;
+    __shared__ int s_skip;
+    if (threadIdx.x == 0) s_skip = (st->halt != 0 || iter > st->stop_after) ? 1 : 0;
+    __syncthreads();
+    return s_skip != 0;
 }
 
 __device__ __forceinline__ float warp_max(float v)
@@ -181,7 +187,7 @@ template <int DMAX>
 __global__ void __launch_bounds__(kKmThreads) k_km_pass(KmArgs a)
 {
     extern __shared__ __align__(16) unsigned char km_smem[];
-    if (a.status->halt) return;
+    if (block_skip(a.status, 0)) return;
     const int D = a.D, DP = a.DP, G = a.G, GS = a.GS;
     float *cent = reinterpret_cast<float *>(km_smem);         // [GS][DP] scaled means
     float *cnorm = cent + (size_t)GS * DP;                       // [GS]
@@ -312,7 +318,7 @@ __global__ void k_km_finalize(const double *__restrict__ partial, int n_partial,
                               int32_t G, double *par, double var_floor, int32_t final_iter,
                               double *counts, const DevStatus *status)
 {
-    if (status->halt) return;
+    if (block_skip(status, 0)) return;
     extern __shared__ double red[];   // [1+2D]
     const int g = blockIdx.x, S = 1 + 2 * D;
     for (int j = threadIdx.x; j < S; j += blockDim.x) {
@@ -355,7 +361,7 @@ __global__ void __launch_bounds__(1024) k_km_dead_fix(const float *__restrict__ 
     extern __shared__ int64_t members[];   // [G]
     __shared__ int s_pop, s_ndead, s_found;
     __shared__ int s_warp[32];
-    if (status->halt) return;
+    if (block_skip(status, 0)) return;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     if (tid == 0) {
         int pop = 0, nd = 0;
@@ -420,15 +426,18 @@ __global__ void __launch_bounds__(1024) k_km_dead_fix(const float *__restrict__ 
 //   FP32 form   l_g(x) = c_g - 1/2 sum_d (x_d s_gd - mu_gd s_gd)^2,
 //               s = 1/sigma, c_g = log w_g - D/2 log 2pi - 1/2 sum_d log sigma^2_gd
 //   tensor form the same expanded about the global centre m (x' = x - m,
-//               mu' = mu - m): l_g = ctc_g + sum_d x'^2 (-1/2 iv) + x' (mu' iv),
-//               ctc_g = c_g - 1/2 sum_d mu'^2 iv, packed K-major [G][KP] BF16
-//               (hi part, plus the lo part x - hi for split-BF16).
+//               mu' = mu - m): l_g = ctc_g + P1 + P2 with
+//               P1 = sum_d x'^2 (-1/2 iv_gd), P2 = sum_d x' (mu'_gd iv_gd),
+//               ctc_g = c_g - 1/2 q_g, q_g = sum_d mu'^2 iv; packed K-major
+//               [G][128] BF16: columns 0..63 hold -1/2 iv (the x'^2 block),
+//               64..127 hold mu' iv (the x' block), zero padded (D <= 64).
 // One block per Gaussian; called by k_em_prep and by k_em_finalize.
 // ------------------------------------------------------------------------
 __device__ void prep_operands(int g, int D, int G, const double *mu, const double *var, double w,
                               const Operands &op, const float *center, int build_tc, double *sh)
 {
     double lsum = 0.0, qsum = 0.0;
+    build_tc = build_tc && D <= 64;
     for (int d = threadIdx.x; d < D; d += blockDim.x) {
         const double v = var[d], m = mu[d];
         const double s = 1.0 / sqrt(v);
@@ -439,19 +448,13 @@ __device__ void prep_operands(int g, int D, int G, const double *mu, const doubl
             const double iv = 1.0 / v;
             const double mc = m - (double)center[d];
             qsum += mc * mc * iv;
-            const float b0 = (float)(-0.5 * iv), b1 = (float)(mc * iv);
-            const __nv_bfloat16 h0 = __float2bfloat16_rn(b0), h1 = __float2bfloat16_rn(b1);
-            op.B[(size_t)g * op.KP + d] = h0;
-            op.B[(size_t)g * op.KP + D + d] = h1;
-            op.Blo[(size_t)g * op.KP + d] = __float2bfloat16_rn((float)(-0.5 * iv - (double)__bfloat162float(h0)));
-            op.Blo[(size_t)g * op.KP + D + d] = __float2bfloat16_rn((float)(mc * iv - (double)__bfloat162float(h1)));
+            op.B[(size_t)g * 128 + d] = __float2bfloat16_rn((float)(-0.5 * iv));
+            op.B[(size_t)g * 128 + 64 + d] = __float2bfloat16_rn((float)(mc * iv));
         }
     }
     if (build_tc)
-        for (int k = 2 * D + threadIdx.x; k < op.KP; k += blockDim.x) {
-            op.B[(size_t)g * op.KP + k] = __float2bfloat16_rn(0.f);
-            op.Blo[(size_t)g * op.KP + k] = __float2bfloat16_rn(0.f);
-        }
+        for (int k = threadIdx.x; k < 128; k += blockDim.x)
+            if ((k & 63) >= D) op.B[(size_t)g * 128 + k] = __float2bfloat16_rn(0.f);
     lsum = block_sum_d(lsum, sh);
     qsum = block_sum_d(qsum, sh);
     if (threadIdx.x == 0) {
@@ -459,7 +462,10 @@ __device__ void prep_operands(int g, int D, int G, const double *mu, const doubl
         const double lw = log(w);
         op.c[g] = (float)(lw + c0);
         op.c0[g] = (float)c0;
-        if (build_tc) op.ctc[g] = (float)(lw + c0 - 0.5 * qsum);
+        if (build_tc) {
+            op.ctc[g] = (float)(lw + c0 - 0.5 * qsum);
+            op.q[g] = (float)qsum;
+        }
     }
 }
 
@@ -489,7 +495,7 @@ template <int DMAX>
 __global__ void __launch_bounds__(kEmThreads, 1) k_em_pass_simt(EmPassArgs a)
 {
     extern __shared__ __align__(16) float em_smem[];
-    if (em_skip(a.status, a.iter)) return;
+    if (block_skip(a.status, a.iter)) return;
     const int D = a.D, G = a.G;
     float *xT = em_smem;                          // [D][kTP]
     float *L = xT + (size_t)D * kTP;              // [G][kTP]
@@ -594,8 +600,8 @@ __global__ void __launch_bounds__(kEmThreads, 1) k_em_pass_simt(EmPassArgs a)
 __global__ void k_em_ll(const double *__restrict__ ll_partial, int n_partial, int64_t N, int32_t iter,
                         double em_tol, double *ll_hist, DevStatus *status)
 {
-    if (em_skip(status, iter)) return;
     if (threadIdx.x != 0) return;
+    if (status->halt != 0 || iter > status->stop_after) return;
     double s = 0.0;
     for (int c = 0; c < n_partial; ++c) s += ll_partial[c];
     const double m = s / (double)N;
@@ -615,8 +621,7 @@ __global__ void k_em_finalize(EmFinalizeArgs a)
     extern __shared__ double red[];   // [1+2D]
     __shared__ double sh[128];
     __shared__ int s_bad;
-    const DevStatus *st = a.status;
-    if (st->halt || a.iter > st->stop_after) return;
+    if (block_skip(a.status, a.iter)) return;
     const int g = blockIdx.x, D = a.D, G = a.G, S = 1 + 2 * D;
     for (int j = threadIdx.x; j < S; j += blockDim.x) {
         double s = 0.0;

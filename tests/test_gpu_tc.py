@@ -1,0 +1,118 @@
+"""GPU parity of the tensor-core (tcgen05) EM pass against the FP64 oracle and
+against the FP32 CUDA-core pass.
+
+The tensor-core pass screens Gaussians with BF16 products under a rigorous
+rounding bound and recomputes the survivors exactly in FP32, so it must meet
+the FP32 tolerances of test_gpu_parity.py (1e-4 relative on parameters, 1e-6
+on log-likelihoods); against the FP32 pass on the same data it agrees to
+FP32 summation-order noise.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1707_09094_gb300 import GMM, GMM_MAHA, GmmError, synth
+from paper_1707_09094_gb300._lib import GMM_DEBUG_SKIP_MMA, GMM_DEBUG_WAIT_CYCLES
+from test_gpu_parity import assert_close, assert_params, dev, km_weights
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1707_09094_gb300 import build
+    build.build()
+
+
+def _start(X, G, seed):
+    seeds = synth.seeds_subset(X, G, seed)
+    if G == 1 or X.shape[0] < 50:
+        return seeds, np.ones_like(seeds), np.full(G, 1.0 / G)
+    w, gv = km_weights(X, GMM_MAHA, 1e-10)
+    return oracle.kmeans(X, seeds, w, gv, 5, 1e-10)[:3]
+
+
+@pytest.mark.parametrize("shape", [(100000, 10, 8), (7, 3, 2), (33, 1, 3), (1000, 13, 1), (2049, 60, 40),
+                                   (3001, 64, 17), (20000, 60, 256), (129, 16, 16), (300, 5, 200)])
+def test_tc_em_matches_oracle(shape):
+    N, D, G = shape
+    X, _, _ = synth.make("c1", N=N, D=D, G=G, seed=3 + N)
+    start = _start(X, G, 2)
+    M, V, H, ll = oracle.em_iterate(X, *start, 3, 1e-10)
+    g = GMM().set_params(*start)
+    g.em_iterate(dev(X), 3, prec="bf16", recompute_center=True)
+    assert_params(g.get_params(), (M, V, H), X)
+    np.testing.assert_allclose(g.ll_history(), ll, rtol=1e-6, atol=1e-6)
+
+
+def test_tc_dense_fallback_many_candidates():
+    """Heavily overlapping Gaussians: every sample keeps more candidates than
+    the per-thread list holds, which exercises the exact dense path."""
+    rng = np.random.default_rng(3)
+    N, D, G = 4000, 8, 40
+    X = rng.normal(0, 1, (N, D)).astype(np.float32)
+    start = (rng.normal(0, 0.05, (G, D)), np.ones((G, D)), np.full(G, 1.0 / G))
+    M, V, H, ll = oracle.em_iterate(X, *start, 2, 1e-10)
+    g = GMM().set_params(*start)
+    g.em_iterate(dev(X), 2, prec="bf16", recompute_center=True)
+    assert_params(g.get_params(), (M, V, H), X)
+    np.testing.assert_allclose(g.ll_history(), ll, rtol=1e-6)
+
+
+def test_tc_learn_end_to_end_c1():
+    X, _, _ = synth.make("c1")
+    g = GMM().learn(dev(X), 8, km_iter=10, em_iter=10, seed=1001, prec="bf16")
+    M, V, H, ll = oracle.learn(X, 8, seed=1001, km_iter=10, em_iter=10)
+    assert_params(g.get_params(), (M, V, H), X)
+    np.testing.assert_allclose(g.ll_history(), ll, rtol=1e-6)
+
+
+def test_tc_matches_fp32_pass_at_full_size():
+    """N=2e6, D=60, N_G=256 (the benchmark's workload): 3 EM iterations in
+    each form from the same start agree to FP32 summation noise."""
+    X, _, mix = synth.make("c2")
+    Xd = dev(X)
+    start = (mix.means, mix.stds ** 2 * 1.2, mix.hefts)
+    a = GMM().set_params(*start)
+    a.em_iterate(Xd, 3, prec="fp32", recompute_center=True)
+    b = GMM().set_params(*start)
+    b.em_iterate(Xd, 3, prec="bf16", recompute_center=True)
+    ma, va, ha = a.get_params()
+    mb, vb, hb = b.get_params()
+    gstd = X.astype(np.float64).std(axis=0)
+    assert_close(mb, ma, 1e-5, (1e-5 * gstd)[None, :], "means")
+    assert_close(vb, va, 1e-5, (1e-5 * gstd ** 2)[None, :], "dcovs")
+    assert_close(hb, ha, 1e-5, 1e-5 / 256, "hefts")
+    np.testing.assert_allclose(b.ll_history(), a.ll_history(), rtol=1e-7)
+    # and the result is judged equal by the same evaluator
+    assert abs(a.avg_log_p(Xd) - b.avg_log_p(Xd)) < 1e-5
+
+
+def test_tc_bounded_wait_times_out_and_context_survives():
+    """Failure detection without a fault: the MMA issuer is told to issue
+    nothing, the epilogue's bounded wait runs out, the pass frees its tensor
+    memory and reports GMM_ERR_TIMEOUT; the model and the CUDA context stay
+    usable."""
+    X, _, _ = synth.make("c1", N=4096)
+    Xd = dev(X)
+    g = GMM().learn(Xd, 8, km_iter=2, em_iter=1, seed=1)
+    before = g.get_params()
+    g.debug_set(GMM_DEBUG_WAIT_CYCLES, 2_000_000).debug_set(GMM_DEBUG_SKIP_MMA, 1)
+    with pytest.raises(GmmError) as e:
+        g.em_iterate(Xd, 1, prec="bf16")
+    assert e.value.status == -4
+    for p, q in zip(before, g.get_params()):
+        np.testing.assert_array_equal(p, q)
+    g.debug_set(GMM_DEBUG_SKIP_MMA, 0).debug_set(GMM_DEBUG_WAIT_CYCLES, 0)
+    g.em_iterate(Xd, 1, prec="bf16")
+    torch.cuda.synchronize()
+    assert np.isfinite(g.ll_history()).all()
+
+
+def test_tc_rejects_unsupported_shapes():
+    X, _, _ = synth.make("c1", N=1000, D=70, G=4, seed=1)
+    g = GMM().set_params(X[:4].astype(np.float64), np.ones((4, 70)), np.full(4, 0.25))
+    with pytest.raises(GmmError) as e:
+        g.em_iterate(dev(X), 1, prec="bf16", recompute_center=True)
+    assert e.value.status == -7
