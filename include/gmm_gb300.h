@@ -212,6 +212,15 @@ gmm_status gmm_profile_read(const gmm_model *m, double *pass_ms, int64_t *pass_l
 #define GMM_DEBUG_SKIP_MMA 2
 gmm_status gmm_debug_set(gmm_model *m, int32_t key, int64_t value);
 
+/* Screening counters of the tensor-core pass, summed since the last
+ * gmm_profile(m, 1): GMM_STAT_SCREENED samples screened, GMM_STAT_KEPT
+ * (sample, Gaussian) pairs kept for the exact recompute, GMM_STAT_DENSE
+ * samples whose candidate list overflowed (exact pass over all Gaussians). */
+#define GMM_STAT_SCREENED 3
+#define GMM_STAT_KEPT 4
+#define GMM_STAT_DENSE 5
+gmm_status gmm_debug_get(const gmm_model *m, int32_t key, int64_t *value);
+
 /* Thread-local text of the last error ("" if none). */
 const char *gmm_last_error(void);
 

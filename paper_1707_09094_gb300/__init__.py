@@ -199,6 +199,15 @@ class GMM:
         _lib.check(_lib.load().gmm_debug_set(self._h, key, int(value)), "gmm_debug_set")
         return self
 
+    def screen_stats(self):
+        """(samples screened, candidates kept, dense fallbacks) of the tensor-core pass since profile()."""
+        out = []
+        for k in (_lib.GMM_STAT_SCREENED, _lib.GMM_STAT_KEPT, _lib.GMM_STAT_DENSE):
+            v = ctypes.c_int64()
+            _lib.check(_lib.load().gmm_debug_get(self._h, k, ctypes.byref(v)), "gmm_debug_get")
+            out.append(v.value)
+        return tuple(out)
+
     def ll_history(self, cap=4096):
         out = np.empty(cap)
         n = ctypes.c_int32()

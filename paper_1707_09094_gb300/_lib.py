@@ -18,6 +18,7 @@ GMM_EUCL, GMM_MAHA, GMM_PROB = 0, 1, 2
 GMM_KEEP_EXISTING, GMM_RANDOM_SUBSET = 0, 1
 GMM_FP32, GMM_BF16, GMM_TF32, GMM_SPLIT_BF16 = 0, 1, 2, 3
 GMM_DEBUG_WAIT_CYCLES, GMM_DEBUG_SKIP_MMA = 1, 2
+GMM_STAT_SCREENED, GMM_STAT_KEPT, GMM_STAT_DENSE = 3, 4, 5
 
 STATUS_NAMES = {0: "GMM_OK", -1: "GMM_ERR_ARG", -2: "GMM_ERR_NONFINITE", -3: "GMM_ERR_CUDA",
                 -4: "GMM_ERR_TIMEOUT", -5: "GMM_ERR_OOM", -6: "GMM_ERR_STATE", -7: "GMM_ERR_UNSUPPORTED"}
@@ -49,6 +50,7 @@ SIGNATURES = {
     "gmm_profile": (ctypes.c_int, [P, i32]),
     "gmm_profile_read": (ctypes.c_int, [P, ctypes.POINTER(f64), ctypes.POINTER(i64), ctypes.POINTER(i64)]),
     "gmm_debug_set": (ctypes.c_int, [P, i32, i64]),
+    "gmm_debug_get": (ctypes.c_int, [P, i32, ctypes.POINTER(i64)]),
     "gmm_last_error": (ctypes.c_char_p, []),
 }
 

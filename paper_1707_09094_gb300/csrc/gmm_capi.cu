@@ -135,6 +135,7 @@ struct gmm_model {
     // failure-detection test hooks
     long long wait_cycles = 2000000000LL;
     int skip_mma = 0;
+    unsigned long long *sstats = nullptr;   // screening counters (device, [3])
 
     double *means() const { return par[cur]; }
     double *gmean() const { return gstat; }
@@ -296,7 +297,7 @@ gmm_status run_em(gmm_model *m, const float *Xd, int64_t N, int32_t em_iter, dou
     CK(gmm::launch_em_prep(D, G, m->par[base], m->op, m->center(), tc ? 1 : (m->has_center && m->center_D == D), s));
     for (int32_t k = 0; k < em_iter; ++k) {
         gmm::EmPassArgs pa{Xd, N, D, G, m->op, m->center(), m->partial, m->llp, m->status, k,
-                           m->wait_cycles, m->skip_mma};
+                           m->wait_cycles, m->skip_mma, m->profiling ? m->sstats : nullptr};
         size_t slot = 0;
         gmm_status prc = prof_begin(m, s, &slot);
         if (prc != GMM_OK) return prc;
@@ -379,6 +380,7 @@ void gmm_destroy(gmm_model *m)
 {
     if (!m) return;
     for (cudaEvent_t e : m->ev) cudaEventDestroy(e);
+    if (m->sstats) cudaFree(m->sstats);
     void *bufs[] = {m->par[0], m->par[1], m->op_sm, m->op_mu, m->op_c, m->op_B, m->gstat, m->fstat,
                     m->partial, m->llp, m->lld, m->counts, m->assign, m->xstage, m->dstage, m->idx,
                     m->hist, m->status};
@@ -630,6 +632,8 @@ gmm_status gmm_profile(gmm_model *m, int32_t enable)
 {
     if (!m) return fail(GMM_ERR_ARG, "model is NULL");
     m->profiling = enable != 0;
+    if (!m->sstats) CK(cudaMalloc(&m->sstats, 3 * sizeof(unsigned long long)));
+    CK(cudaMemset(m->sstats, 0, 3 * sizeof(unsigned long long)));
     m->ev_used = 0;
     m->pass_ms = 0.0;
     m->pass_launches = 0;
@@ -657,6 +661,16 @@ gmm_status gmm_debug_set(gmm_model *m, int32_t key, int64_t value)
     } else {
         return fail(GMM_ERR_ARG, "unknown debug key %d", key);
     }
+    return GMM_OK;
+}
+
+gmm_status gmm_debug_get(const gmm_model *m, int32_t key, int64_t *value)
+{
+    if (!m || !value) return fail(GMM_ERR_ARG, "NULL argument");
+    if (key < GMM_STAT_SCREENED || key > GMM_STAT_DENSE) return fail(GMM_ERR_ARG, "unknown key %d", key);
+    unsigned long long v[3] = {0, 0, 0};
+    if (m->sstats) CK(cudaMemcpy(v, m->sstats, sizeof v, cudaMemcpyDeviceToHost));
+    *value = (int64_t)v[key - GMM_STAT_SCREENED];
     return GMM_OK;
 }
 

@@ -282,6 +282,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_em_pass_tc(TcArgs args)
     const uint32_t tmem = *tmem_slot;
 
     double ll = 0.0;
+    unsigned long long st_kept = 0, st_dense = 0, st_n = 0;
     if (warp == 8) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
@@ -394,6 +395,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_em_pass_tc(TcArgs args)
             float lx[kCap];
             float mh = -INFINITY, sh = 0.f;
             const bool dense = n > kCap;
+            if (valid) { st_n += 1; st_kept += (unsigned long long)n; st_dense += dense ? 1ull : 0ull; }
             if (!dense) {
 #pragma unroll
                 for (int k = 0; k < kCap; ++k) {
@@ -463,6 +465,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_em_pass_tc(TcArgs args)
     }
     double *red = reinterpret_cast<double *>(sbase + Ls.acc);   // statistics already flushed
     __syncthreads();
+    if (a.screen_stats && warp < 8) {
+        for (int o = 16; o > 0; o >>= 1) {
+            st_n += __shfl_xor_sync(0xffffffffu, st_n, o);
+            st_kept += __shfl_xor_sync(0xffffffffu, st_kept, o);
+            st_dense += __shfl_xor_sync(0xffffffffu, st_dense, o);
+        }
+        if (lane == 0) {
+            atomicAdd(a.screen_stats + 0, (warp < 4) ? st_n : 0ull);   // each sample counted once (half 0)
+            atomicAdd(a.screen_stats + 1, st_kept);
+            atomicAdd(a.screen_stats + 2, st_dense);
+        }
+    }
     for (int o = 16; o > 0; o >>= 1) ll += __shfl_xor_sync(0xffffffffu, ll, o);
     if (lane == 0) red[warp] = ll;
     __syncthreads();

@@ -49,6 +49,7 @@ struct EmPassArgs {
     int32_t iter;
     long long wait_cycles;   // budget of bounded waits (tensor-core pass)
     int32_t skip_mma;        // test hook: issue no MMA
+    unsigned long long *screen_stats;   // [3] screened, kept, dense (NULL = off)
 };
 
 struct EmFinalizeArgs {
