@@ -41,6 +41,7 @@ SIGNATURES = {
     "gmm_kmeans": (ctypes.c_int, [P, P, i64, i32, i32, f64, P, P]),
     "gmm_log_p": (ctypes.c_int, [P, P, i64, i32, P, P]),
     "gmm_avg_log_p": (ctypes.c_int, [P, P, i64, i32, ctypes.POINTER(f64), P]),
+    "gmm_avg_log_p_noalloc": (ctypes.c_int, [P, P, i64, i32, ctypes.POINTER(f64), P]),
     "gmm_assign": (ctypes.c_int, [P, P, i64, i32, P, P]),
     "gmm_raw_hist": (ctypes.c_int, [P, P, i64, i32, P, P]),
     "gmm_norm_hist": (ctypes.c_int, [P, P, i64, i32, P, P]),

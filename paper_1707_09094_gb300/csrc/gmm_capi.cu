@@ -529,6 +529,27 @@ gmm_status gmm_avg_log_p(const gmm_model *mc, const float *X, int64_t N, int32_t
     return GMM_OK;
 }
 
+gmm_status gmm_avg_log_p_noalloc(const gmm_model *mc, const float *X, int64_t N, int32_t g, double *out,
+                                 void *stream)
+{
+    gmm_model *m = const_cast<gmm_model *>(mc);
+    if (!m || !out) return fail(GMM_ERR_ARG, "NULL argument");
+    if (!m->has_params) return fail(GMM_ERR_STATE, "model has no parameters");
+    gmm_status rc = validate_x(X, N, m->D);
+    if (rc != GMM_OK) return rc;
+    if (g < -1 || g >= m->G) return fail(GMM_ERR_ARG, "g out of range");
+    if (!is_device_ptr(X)) return fail(GMM_ERR_ARG, "X must be device memory (this call stages nothing)");
+    if (N > gmm::avg_log_p_noalloc_max_n())
+        return fail(GMM_ERR_UNSUPPORTED, "N=%lld exceeds the allocation-free limit of %lld samples", (long long)N,
+                    (long long)gmm::avg_log_p_noalloc_max_n());
+    cudaStream_t s = as_stream(stream);
+    if (!m->ops_valid && (rc = run_prep(m, s)) != GMM_OK) return rc;
+    double sum = 0.0;
+    CK(gmm::launch_avg_log_p_noalloc(X, N, m->D, m->G, m->op, g, &sum, s));
+    *out = sum / (double)N;
+    return GMM_OK;
+}
+
 static gmm_status assign_dev(gmm_model *m, const float *X, int64_t N, int32_t mode, cudaStream_t s, int32_t **ad)
 {
     gmm_status rc = validate_x(X, N, m->D);

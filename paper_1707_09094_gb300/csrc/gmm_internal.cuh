@@ -101,6 +101,9 @@ cudaError_t launch_status_reset(DevStatus *st, cudaStream_t s);
 cudaError_t launch_sum_fp64(const double *v, int64_t n, double *out, cudaStream_t s);
 cudaError_t launch_hist(const int32_t *a, int64_t N, int32_t G, unsigned long long *counts,
                         cudaStream_t s);
+int64_t avg_log_p_noalloc_max_n();
+cudaError_t launch_avg_log_p_noalloc(const float *X, int64_t N, int32_t D, int32_t G, Operands op, int32_t g,
+                                     double *sum_host, cudaStream_t s);
 int em_simt_grid(int32_t D, int32_t G, int sms);
 int km_grid(int32_t D, int32_t G, int sms);
 size_t em_simt_smem(int32_t D, int32_t G);

@@ -10,6 +10,7 @@
 // Every reduction over CTAs runs in CTA order in FP64, so results do not
 // depend on scheduling.
 #include <atomic>
+#include <mutex>
 #include <cfloat>
 #include <cmath>
 
@@ -771,7 +772,98 @@ __global__ void k_hist(const int32_t *__restrict__ a, int64_t N, int32_t G, unsi
 
 int dmax_for(int D) { return D <= 16 ? 16 : D <= 32 ? 32 : D <= 64 ? 64 : 128; }
 
+// ------------------------------------------------------------------------
+// Allocation-free avg_log_p.  Scratch: one FP64 partial sum per 128-sample
+// block plus the grand total, in a fixed device array that every GPU loading
+// this library holds until the process exits (512 KiB + 8 B).  Every slot a
+// call reads is written by the same call, so nothing has to be cleared; two
+// calls whose kernels overlap on the GPU (different streams) race on it.
+// ------------------------------------------------------------------------
+constexpr int kNoAllocMaxBlocks = 65536;
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocMaxBlocks + 1];
+
+template <int DMAX>
+__global__ void __launch_bounds__(128) k_log_p_blocksum(const float *__restrict__ X, int64_t N, int32_t D, int32_t G,
+                                                        Operands op, int32_t gsel, double *__restrict__ partial)
+{
+    __shared__ double sh[128];
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double v = 0.0;
+    if (i < N) {
+        float xr[DMAX];
+#pragma unroll
+        for (int d = 0; d < DMAX; ++d) xr[d] = d < D ? X[i * D + d] : 0.f;
+        auto logit = [&](int g) {
+            const float2 *p = op.sm + (size_t)g * D;
+            float acc = 0.f;
+#pragma unroll
+            for (int d = 0; d < DMAX; ++d)
+                if (d < D) { const float2 q = __ldg(p + d); const float t = fmaf(xr[d], q.x, -q.y); acc = fmaf(t, t, acc); }
+            return -0.5f * acc;
+        };
+        if (gsel >= 0) {
+            v = (double)logit(gsel) + (double)op.c0[gsel];
+        } else {
+            float m = -INFINITY, s = 0.f;
+            for (int g = 0; g < G; ++g) {
+                const float l = logit(g) + __ldg(op.c + g);
+                if (l > m) { s = s * __expf(m - l) + 1.f; m = l; }
+                else s += __expf(l - m);
+            }
+            v = (double)m + log((double)s);
+        }
+    }
+    v = block_sum_d(v, sh);
+    if (threadIdx.x == 0) partial[blockIdx.x] = v;
+}
+
 }  // namespace
+
+// Device address of the scratch array on the current device.  The symbol's
+// host-side name is only a stand-in: the address has to be looked up once per
+// device, with that device current, before a kernel may be given it.
+static std::mutex g_noalloc_mu;
+static double *g_noalloc_dev[256] = {};
+
+static cudaError_t noalloc_scratch(double **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_dev[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_dev[dev] = static_cast<double *>(p);
+    }
+    *out = g_noalloc_dev[dev];
+    return cudaSuccess;
+}
+
+int64_t avg_log_p_noalloc_max_n() { return (int64_t)kNoAllocMaxBlocks * 128; }
+
+cudaError_t launch_avg_log_p_noalloc(const float *X, int64_t N, int32_t D, int32_t G, Operands op, int32_t g,
+                                     double *sum_host, cudaStream_t s)
+{
+    if (N < 1 || N > avg_log_p_noalloc_max_n()) return cudaErrorInvalidValue;
+    double *scratch = nullptr;
+    cudaError_t e = noalloc_scratch(&scratch);
+    if (e != cudaSuccess) return e;
+    const int blocks = (int)((N + 127) / 128);
+    const int dm = dmax_for(D);
+    if (dm == 16) k_log_p_blocksum<16><<<blocks, 128, 0, s>>>(X, N, D, G, op, g, scratch);
+    else if (dm == 32) k_log_p_blocksum<32><<<blocks, 128, 0, s>>>(X, N, D, G, op, g, scratch);
+    else if (dm == 64) k_log_p_blocksum<64><<<blocks, 128, 0, s>>>(X, N, D, G, op, g, scratch);
+    else k_log_p_blocksum<128><<<blocks, 128, 0, s>>>(X, N, D, G, op, g, scratch);
+    k_sum_fp64<<<1, 1024, 0, s>>>(scratch, blocks, scratch + kNoAllocMaxBlocks);
+    count_launches(2);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(sum_host, scratch + kNoAllocMaxBlocks, sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return e;
+    return cudaStreamSynchronize(s);
+}
 
 // ======================================================================== host
 static std::atomic<long long> g_launches{0};
