@@ -33,6 +33,8 @@
 #define ORC_ERR_OOM (-5)
 
 static const double ORC_LOG_2PI = 1.83787706640934548356065947281123527;
+/* Smallest responsibility sum L_g for which a Gaussian is re-estimated. */
+static const double ORC_MIN_RESP = 1e-8;
 
 /* ------------------------------------------------------------------------ */
 /* Log density of one diagonal Gaussian: Eq. 15 (log of Eq. 2) with the     */
@@ -342,8 +344,11 @@ int orc_kmeans(const float *X, int64_t N, int32_t D, int32_t G, const double *w,
  *   reduce: Eqs. 12-14 sum the chunks in order t = 1..N_T and divide;
  *   update: hefts by Eq. 5, variances by the one-pass form of Eq. 8 / Eq. 14,
  *           floored after the iteration (Sec. 2.2).
- * Reading for a Gaussian whose L_g underflows (< 1e-300): its heft becomes
- * L_g / N and its mean and covariance are kept (avoids 0/0).
+ * Reading for a Gaussian whose responsibility sum L_g is below 1e-8 (the
+ * paper is silent): its heft becomes L_g / N and its mean and covariance are
+ * kept.  Below that mass the re-estimate (Eqs. 13-14) is a ratio of sums of
+ * underflowing responsibilities that every precision resolves differently,
+ * while the Gaussian holds less than 1e-8 of one sample.
  * *mean_ll receives log p(X | lambda_old) / N, the likelihood of the
  * parameters the E-step used.
  */
@@ -402,7 +407,7 @@ static int orc_em_one(const float *X, int64_t N, int32_t D, int32_t G, double *m
     int rc = ORC_OK;
     for (int32_t g = 0; g < G; ++g) {
         hefts[g] = L[g] / (double)N;                                  /* Eq. 5 */
-        if (!(L[g] >= 1e-300)) continue;
+        if (!(L[g] >= ORC_MIN_RESP)) continue;
         for (int32_t d = 0; d < D; ++d) {
             double mu = M[(size_t)g * D + d] / L[g];                  /* Eq. 13 */
             double v = S[(size_t)g * D + d] / L[g] - mu * mu;         /* Eq. 14 */
@@ -474,7 +479,7 @@ int orc_em_step_twopass(const float *X, int64_t N, int32_t D, int32_t G, double 
         }
     for (int32_t g = 0; g < G; ++g) {
         hefts[g] = L[g] / (double)N;                                      /* Eq. 5 */
-        if (!(L[g] >= 1e-300)) continue;
+        if (!(L[g] >= ORC_MIN_RESP)) continue;
         for (int32_t d = 0; d < D; ++d) {
             double v = S[(size_t)g * D + d] / L[g];
             means[(size_t)g * D + d] = M[(size_t)g * D + d];

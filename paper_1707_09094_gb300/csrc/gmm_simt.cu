@@ -614,8 +614,9 @@ __global__ void k_em_ll(const double *__restrict__ ll_partial, int n_partial, in
 
 // EM reduce + update (Eqs. 12-14, Eq. 5; floor of Sec. 2.2), then the
 // operands of the next E-step.  One block per Gaussian; CTA-order FP64 sums.
-// A Gaussian whose L_g underflows keeps its mean and covariance (its heft is
-// L_g / N).  A non-finite result stops the call with GMM_ERR_NONFINITE and
+// A Gaussian whose responsibility sum L_g is below 1e-8 keeps its mean and
+// covariance (its heft is L_g / N): below that mass the re-estimate is a ratio
+// of underflowing sums.  A non-finite result stops the call with GMM_ERR_NONFINITE and
 // leaves par_in (the last finite parameters) untouched.
 __global__ void k_em_finalize(EmFinalizeArgs a)
 {
@@ -635,7 +636,7 @@ __global__ void k_em_finalize(EmFinalizeArgs a)
     const double *mi = a.par_in + (size_t)g * D, *vi = a.par_in + (size_t)G * D + (size_t)g * D;
     double *mo = a.par_out + (size_t)g * D, *vo = a.par_out + (size_t)G * D + (size_t)g * D;
     const double w = Lg / (double)a.N;
-    const bool live = Lg >= 1e-300;
+    const bool live = Lg >= 1e-8;   // below this mass the Gaussian keeps its parameters
     for (int d = threadIdx.x; d < D; d += blockDim.x) {
         double mu = mi[d], v = vi[d];
         if (live) {
