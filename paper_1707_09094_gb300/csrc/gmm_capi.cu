@@ -115,6 +115,7 @@ struct gmm_model {
     int32_t center_D = 0;
     // workspace
     double *partial = nullptr; size_t partial_cap = 0;
+    float *slab = nullptr; size_t slab_cap = 0;
     double *llp = nullptr; size_t llp_cap = 0;
     double *lld = nullptr; size_t lld_cap = 0;
     double *counts = nullptr; size_t counts_cap = 0;
@@ -289,6 +290,7 @@ gmm_status run_em(gmm_model *m, const float *Xd, int64_t N, int32_t em_iter, dou
         return fail(GMM_ERR_STATE, "tensor-core E-step needs the global centre (run learn or recompute_center)");
     const int grid = tc ? gmm::em_tc_grid(m->sms) : gmm::em_simt_grid(D, G, m->sms);
     CK(grow(m->partial, m->partial_cap, (size_t)grid * G * S));
+    if (tc) CK(grow(m->slab, m->slab_cap, gmm::em_tc_slab_floats(D, G, grid)));
     CK(grow(m->llp, m->llp_cap, (size_t)grid));
     CK(grow(m->lld, m->lld_cap, (size_t)(em_iter > 0 ? em_iter : 1)));
     CK(gmm::launch_status_reset(m->status, s));
@@ -301,7 +303,7 @@ gmm_status run_em(gmm_model *m, const float *Xd, int64_t N, int32_t em_iter, dou
         size_t slot = 0;
         gmm_status prc = prof_begin(m, s, &slot);
         if (prc != GMM_OK) return prc;
-        if (tc) CK(gmm::launch_em_pass_tc(pa, grid, prec == GMM_SPLIT_BF16, s));
+        if (tc) CK(gmm::launch_em_pass_tc(pa, m->slab, grid, s));
         else CK(gmm::launch_em_pass_simt(pa, grid, s));
         if ((prc = prof_end(m, s, slot)) != GMM_OK) return prc;
         gmm::EmFinalizeArgs fa{m->partial, m->llp, grid, N, D, G, m->par[(base + k) & 1], m->par[(base + k + 1) & 1],
@@ -382,7 +384,7 @@ void gmm_destroy(gmm_model *m)
     for (cudaEvent_t e : m->ev) cudaEventDestroy(e);
     if (m->sstats) cudaFree(m->sstats);
     void *bufs[] = {m->par[0], m->par[1], m->op_sm, m->op_mu, m->op_c, m->op_B, m->gstat, m->fstat,
-                    m->partial, m->llp, m->lld, m->counts, m->assign, m->xstage, m->dstage, m->idx,
+                    m->partial, m->slab, m->llp, m->lld, m->counts, m->assign, m->xstage, m->dstage, m->idx,
                     m->hist, m->status};
     for (void *p : bufs)
         if (p) cudaFree(p);

@@ -11,14 +11,20 @@
 //     |l~ - l| <= 2^-8 * 1.25 * sum_d (x'^2 iv/2 + |x' mu'| iv) + tiny terms,
 //     and by AM-GM sum_d |x' mu'| iv <= sum_d (x'^2 + mu'^2) iv / 2, so
 //     |l~ - l| <= K1 |P1| + k2_g with k2_g = 2^-8 * 1.25 * q_g / 2 + ...
-//     A Gaussian whose upper bound lies more than 27.7 nats below the best
-//     lower bound has responsibility < 1e-12 and is dropped.
-//  3. The few remaining candidates (about one per sample on speech-like data)
-//     get their log-density recomputed exactly in FP32 on the CUDA cores (the
-//     same formula as the FP32 form); log-sum-exp over them (Eqs. 16-18),
-//     responsibilities l_{g,i} (Eq. 3), and the M-step statistics (Eqs. 9-11,
-//     shifted by the FP32 mean of the iteration start) accumulated in shared
-//     memory.  Responsibilities never leave the SM.
+//     A Gaussian whose upper bound lies more than 45 nats below the best
+//     lower bound has responsibility < 3e-20 and is dropped; per Gaussian the
+//     dropped mass is below N * 3e-20, far under the 1e-8 responsibility sum
+//     below which the update keeps a Gaussian's parameters.
+//  3. The few remaining candidates (one to a few per sample on speech-like
+//     data) get their log-density recomputed exactly in FP32 on the CUDA
+//     cores, one warp per (sample, Gaussian) with lanes over dimensions;
+//     log-sum-exp over them (Eqs. 16-18), responsibilities l_{g,i} (Eq. 3),
+//     and the M-step statistics (Eqs. 9-11, shifted by the FP32 mean of the
+//     iteration start) reduced into the CTA's FP32 slab in L2 with
+//     fire-and-forget atomics.  Responsibilities are never stored.
+// Pipelining: A (the BF16 sample operand) and the FP32 sample tile (cp.async)
+// are double-buffered, so the MMAs of tile t+1 run while tile t is screened,
+// recomputed and accumulated.
 // Warp roles: warps 0-7 are the epilogue (warp w reads TMEM lanes 32*(w%4)..,
 // i.e. samples 32*(w%4).., Gaussians 128*(w/4)..), warp 8 allocates TMEM and
 // one of its threads issues the MMAs.  Every wait is bounded: on expiry the
@@ -35,9 +41,9 @@ namespace {
 constexpr int kEpiThreads = 256;
 constexpr int kThreads = kEpiThreads + 32;
 constexpr int kTM = 128;          // samples per tile = MMA M
-constexpr int kCap = 8;           // candidates per thread before the dense fallback
-constexpr float kScreenNats = 27.7f;
-constexpr float kK1 = 0.009765625f * 1.25f / 1.0f;   // 2^-7 * 1.25 (multiplies |P1|)
+constexpr int kCap = 16;          // candidates per (sample, half) before the dense fallback
+constexpr float kScreenNats = 45.0f;
+constexpr float kK1 = 0.009765625f * 1.25f;   // 2^-7 * 1.25 (multiplies |P1|)
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -151,58 +157,84 @@ __device__ __forceinline__ uint32_t sw128_off(int r, int c)
     return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4));
 }
 
-__device__ __forceinline__ uint32_t pack_bf16(float a, float b)
+
+__device__ __forceinline__ float warp_sum_f(float v)
 {
-    __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
-    return *reinterpret_cast<uint32_t *>(&v);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
 }
 
-// The FP32 log-density of the CUDA-core form, term for term.
-template <int DMAX>
-__device__ __forceinline__ float exact_logit(const float (&xr)[DMAX], const float2 *__restrict__ p, float c, int D)
+// Exact FP32 log-density of Gaussian g at one sample (the formula of the
+// CUDA-core form: c_g - 1/2 sum_d (x_d s_gd - mu_gd s_gd)^2), one warp, lanes
+// over dimensions; x is the sample's row in shared memory.
+__device__ __forceinline__ float warp_logit(const float *x, const float2 *__restrict__ p, float c, int D, int lane)
 {
     float acc = 0.f;
-#pragma unroll
-    for (int d = 0; d < DMAX; ++d) {
-        if (d < D) {
-            const float2 q = __ldg(p + d);
-            const float t = fmaf(xr[d], q.x, -q.y);
-            acc = fmaf(t, t, acc);
-        }
+    for (int d = lane; d < D; d += 32) {
+        const float2 q = __ldg(p + d);
+        const float t = fmaf(x[d], q.x, -q.y);
+        acc = fmaf(t, t, acc);
     }
-    return fmaf(-0.5f, acc, c);
+    return fmaf(-0.5f, warp_sum_f(acc), c);
 }
 
-template <int DMAX>
-__device__ __forceinline__ void load_row(float (&xr)[DMAX], const float *__restrict__ row, bool valid, int D)
+// M-step contribution of one (sample, Gaussian) pair with responsibility gm
+// (Eqs. 9-11, shifted by the FP32 mean mu_f): one warp, lanes over dimensions.
+__device__ __forceinline__ void warp_accumulate(float *slab_g, const float *x, const float *__restrict__ mu, float gm,
+                                                int D, int lane)
 {
-#pragma unroll
-    for (int d = 0; d < DMAX; ++d) xr[d] = (valid && d < D) ? __ldg(row + d) : 0.f;
+    if (lane == 0) atomicAdd(slab_g, gm);
+    for (int d = lane; d < D; d += 32) {
+        const float u = x[d] - __ldg(mu + d);
+        const float gu = gm * u;
+        atomicAdd(slab_g + 1 + d, gu);
+        atomicAdd(slab_g + 1 + D + d, gu * u);
+    }
 }
+
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 struct TcArgs {
     EmPassArgs a;
-    int32_t NG;   // Gaussians padded to a multiple of 16 (MMA N)
-    int32_t nk;   // K=16 steps per K block: ceil(D/16)
+    float *slab;      // [grid][G][1+2D] FP32 statistics of each CTA
+    int32_t NG;       // Gaussians padded to a multiple of 16 (MMA N)
+    int32_t nk;       // K=16 steps per K block: ceil(D/16)
+    int32_t x_al16;   // X is 16-byte aligned
 };
 
 struct TcSmem {
-    uint32_t B, A, acc, cst, ctr, xlo, xms, clist, bars, misc, total;
+    uint32_t B, A, X, xbytes, cst, ctr, cg, cl, cn, dms, xlo, xms, lse, bars, misc, total;
 };
 
 __host__ __device__ inline TcSmem tc_layout(int D, int G, int NG)
 {
+    (void)G;
     TcSmem L;
     uint32_t o = 0;
-    L.B = o; o += 2u * NG * 128u;                       // two K blocks of [NG][128 B]
-    L.A = o; o += kTM * 256u;                            // two K blocks of [128][128 B]
-    L.acc = o; o += 4u * (uint32_t)(G + 2 * G * D); o = (o + 15u) & ~15u;
-    if (o - L.acc < 128u) o = L.acc + 128u;              // also holds the 9 per-warp log-likelihoods
-    L.cst = o; o += 8u * NG;                             // (ctc, k2) per Gaussian
+    L.B = o; o += 2u * NG * 128u;                        // two K blocks of [NG][128 B]
+    L.A = o; o += 2u * kTM * 256u;                       // two buffers x two K blocks of [128][128 B]
+    L.xbytes = ((uint32_t)kTM * D * 4u + 15u) & ~15u;
+    L.X = o; o += 2u * L.xbytes;                         // two FP32 sample tiles
+    L.cst = o; o += 8u * NG;                             // (ctc + k2, k2) per Gaussian
     L.ctr = o; o += 4u * 64u;                            // centre
-    L.xlo = o; o += 4u * 2u * kTM;
-    L.xms = o; o += 8u * 2u * kTM;
-    L.clist = o; o += (uint32_t)kEpiThreads * kCap;
+    L.cg = o; o += (uint32_t)kEpiThreads * kCap;         // candidate Gaussian (local index)
+    o = (o + 15u) & ~15u;
+    L.cl = o; o += 4u * kEpiThreads * kCap;              // exact log-density, then responsibility
+    L.cn = o; o += 4u * kEpiThreads;                     // candidates per (sample, half)
+    L.dms = o; o += 8u * kEpiThreads;                    // dense path: (max, sum of exp)
+    L.xlo = o; o += 4u * kEpiThreads;
+    L.xms = o; o += 8u * kEpiThreads;
+    L.lse = o; o += 4u * kTM;
     o = (o + 7u) & ~7u;
     L.bars = o; o += 8u * 4u;
     L.misc = o; o += 16u;
@@ -210,7 +242,6 @@ __host__ __device__ inline TcSmem tc_layout(int D, int G, int NG)
     return L;
 }
 
-template <int DMAX>
 __global__ void __launch_bounds__(kThreads, 1) k_em_pass_tc(TcArgs args)
 {
     extern __shared__ __align__(1024) unsigned char tc_raw[];
@@ -219,31 +250,68 @@ __global__ void __launch_bounds__(kThreads, 1) k_em_pass_tc(TcArgs args)
     if (threadIdx.x == 0) s_skip = (a.status->halt != 0 || a.iter > a.status->stop_after) ? 1 : 0;
     __syncthreads();
     if (s_skip) return;   // uniform across the block
-    const int D = a.D, G = a.G, NG = args.NG, nk = args.nk;
+    const int D = a.D, G = a.G, NG = args.NG, nk = args.nk, S = 1 + 2 * a.D;
     const TcSmem Ls = tc_layout(D, G, NG);
     unsigned char *sbase = tc_raw + ((1024u - (smem_u32(tc_raw) & 1023u)) & 1023u);
     unsigned char *sB = sbase + Ls.B;
     unsigned char *sA = sbase + Ls.A;
-    float *S0 = reinterpret_cast<float *>(sbase + Ls.acc);
-    float *S1 = S0 + G;
-    float *S2 = S1 + (size_t)G * D;
+    float *sX = reinterpret_cast<float *>(sbase + Ls.X);
     float2 *cst = reinterpret_cast<float2 *>(sbase + Ls.cst);
     float *ctr = reinterpret_cast<float *>(sbase + Ls.ctr);
+    uint8_t *cg = reinterpret_cast<uint8_t *>(sbase + Ls.cg);
+    float *cl = reinterpret_cast<float *>(sbase + Ls.cl);
+    int *cn = reinterpret_cast<int *>(sbase + Ls.cn);
+    float2 *dms = reinterpret_cast<float2 *>(sbase + Ls.dms);
     float *xlo = reinterpret_cast<float *>(sbase + Ls.xlo);
     float2 *xms = reinterpret_cast<float2 *>(sbase + Ls.xms);
-    uint8_t *clist = reinterpret_cast<uint8_t *>(sbase + Ls.clist);
+    float *slse = reinterpret_cast<float *>(sbase + Ls.lse);
     uint64_t *bar_afull = reinterpret_cast<uint64_t *>(sbase + Ls.bars);
     uint64_t *bar_lfull = bar_afull + 1;
     uint64_t *bar_lfree = bar_afull + 2;
     uint64_t *bar_drain = bar_afull + 3;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sbase + Ls.misc);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(sbase + Ls.misc + 4);
+    float *slab = args.slab + (size_t)blockIdx.x * G * S;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long long budget = a.wait_cycles;
     const int64_t ntiles = (a.N + kTM - 1) / kTM;
     const int64_t t0 = ntiles * blockIdx.x / gridDim.x, t1 = ntiles * (blockIdx.x + 1) / gridDim.x;
     const int T = (int)(t1 - t0);
+
+    // FP32 sample tile `tile` -> X buffer b (cp.async, one commit group per call)
+    auto load_x = [&](int64_t tile, int b) {
+        const int64_t i0 = tile * kTM;
+        const int rows = (int)min((int64_t)kTM, a.N - i0);
+        const uint32_t bytes = (uint32_t)rows * D * 4u;
+        const char *src = reinterpret_cast<const char *>(a.X + i0 * D);
+        const uint32_t dst = smem_u32(sbase + Ls.X + b * Ls.xbytes);
+        uint32_t done = 0;
+        if (args.x_al16) {
+            const uint32_t n16 = bytes >> 4;
+            for (uint32_t k = tid; k < n16; k += kEpiThreads) cp_async16(dst + 16u * k, src + 16u * k);
+            done = n16 << 4;
+        }
+        for (uint32_t k = done / 4u + tid; k < bytes / 4u; k += kEpiThreads) cp_async4(dst + 4u * k, src + 4u * k);
+        cp_async_commit();
+    };
+    // BF16 operand A of tile `tile` -> A buffer b: row r = [x'^2 | x'] (K blocks 0 | 1), warp per row
+    auto build_a = [&](int64_t tile, int b) {
+        const int64_t i0 = tile * kTM;
+        unsigned char *ab = sA + b * (kTM * 256);
+        for (int r = warp; r < kTM; r += 8) {
+            const bool v = i0 + r < a.N;
+            const float *row = a.X + (i0 + r) * D;
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                const int d = lane + 32 * hh;
+                const float xc = (v && d < D) ? __ldg(row + d) - ctr[d] : 0.f;
+                const uint32_t off = sw128_off(r, d >> 3) + (uint32_t)((d & 7) * 2);
+                *reinterpret_cast<__nv_bfloat16 *>(ab + off) = __float2bfloat16_rn(xc * xc);
+                *reinterpret_cast<__nv_bfloat16 *>(ab + 16384 + off) = __float2bfloat16_rn(xc);
+            }
+        }
+    };
 
     if (tid == 0) {
         mbar_init(bar_afull, 1);
@@ -256,8 +324,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_em_pass_tc(TcArgs args)
         tmem_alloc(tmem_slot, 512);
         tmem_relinquish();
     } else {
-        for (int k = tid; k < G + 2 * G * D; k += kEpiThreads) S0[k] = 0.f;
-        // B operand: global [G][128] BF16 rows -> two swizzled K blocks
+        for (int k = tid; k < G * S; k += kEpiThreads) slab[k] = 0.f;
         for (int k = tid; k < NG * 16; k += kEpiThreads) {
             const int g = k >> 4, kb = (k >> 3) & 1, c = k & 7;
             uint4 v = make_uint4(0u, 0u, 0u, 0u);
@@ -276,10 +343,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_em_pass_tc(TcArgs args)
         }
         for (int d = tid; d < 64; d += kEpiThreads) ctr[d] = d < D ? __ldg(a.center + d) : 0.f;
     }
+    __syncthreads();   // centre in place for the first A
+    if (warp < 8 && T > 0) {
+        load_x(t0, 0);
+        build_a(t0, 0);
+        fence_proxy_async();
+    }
+    __threadfence();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    if (tid == 0 && T > 0) mbar_arrive(bar_afull);
 
     double ll = 0.0;
     unsigned long long st_kept = 0, st_dense = 0, st_n = 0;
@@ -293,9 +368,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_em_pass_tc(TcArgs args)
                 if (t > 0 && !mbar_wait(bar_lfree, (uint32_t)((t - 1) & 1), abort_flag, budget)) break;
                 tc_fence_after();
                 if (a.skip_mma) continue;   // test hook: the epilogue's wait must run out
+                const uint32_t ab = aS + (uint32_t)(t & 1) * (kTM * 256u);
                 for (int kb = 0; kb < 2; ++kb)
                     for (int kk = 0; kk < nk; ++kk)
-                        tc_mma(tmem + (uint32_t)(kb * 256), desc_k_sw128(aS + kb * 16384u + kk * 32u),
+                        tc_mma(tmem + (uint32_t)(kb * 256), desc_k_sw128(ab + kb * 16384u + kk * 32u),
                                desc_k_sw128(bS + (uint32_t)kb * NG * 128u + kk * 32u), idesc, kk > 0 ? 1u : 0u);
                 tc_commit(bar_lfull);
             }
@@ -310,39 +386,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_em_pass_tc(TcArgs args)
     } else {
         // ------------------------------------------------------------ epilogue
         const int q = warp & 3, h = warp >> 2;
-        const int s = 32 * q + lane;
+        const int s = 32 * q + lane;            // this thread's sample in the tile (TMEM lane)
         const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);
-        auto build_a = [&](int64_t tile) {
-            const int64_t i0 = tile * kTM;
-            const bool v = i0 + s < a.N;
-            float xr[DMAX];
-            load_row<DMAX>(xr, a.X + (i0 + s) * D, v, D);
-            uint32_t w[32];
-#pragma unroll
-            for (int d = 0; d < DMAX; d += 2) {
-                float x0 = (v && d < D) ? xr[d] - ctr[d] : 0.f;
-                float x1 = (v && d + 1 < D) ? xr[d + 1] - ctr[d + 1] : 0.f;
-                if (h == 0) { x0 *= x0; x1 *= x1; }
-                w[d >> 1] = pack_bf16(x0, x1);
-            }
-            unsigned char *rowp = sA + h * 16384;
-#pragma unroll
-            for (int c = 0; c < 8; ++c)
-                *reinterpret_cast<uint4 *>(rowp + sw128_off(s, c)) =
-                    make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
-        };
-        if (T > 0) build_a(t0);
-        fence_proxy_async();
-        epi_sync();
-        if (tid == 0 && T > 0) mbar_arrive(bar_afull);
-
         for (int t = 0; t < T; ++t) {
             const int64_t tile = t0 + t;
-            const int64_t i = tile * kTM + s;
-            const bool valid = i < a.N;
+            const int64_t i0 = tile * kTM;
+            const int nvalid = (int)min((int64_t)kTM, a.N - i0);
+            // ---- prefetch the next tile: FP32 rows (async) and its BF16 operand
+            if (t + 1 < T) {
+                load_x(tile + 1, (t + 1) & 1);
+                build_a(tile + 1, (t + 1) & 1);
+                fence_proxy_async();
+            } else {
+                cp_async_commit();
+            }
+            epi_sync();
+            if (tid == 0 && t + 1 < T) mbar_arrive(bar_afull);
+            // ---- pass 1: screening bounds from the two TMEM accumulators
             mbar_wait(bar_lfull, (uint32_t)(t & 1), abort_flag, budget);
             tc_fence_after();
-            // ---- pass 1: screening bounds from the two TMEM accumulators
             float ub[128];
             float lo = -INFINITY;
 #pragma unroll
@@ -368,15 +430,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_em_pass_tc(TcArgs args)
                 }
             }
             tc_fence_before();
-            xlo[h * kTM + s] = lo;
+            xlo[tid] = lo;
             epi_sync();
             if (tid == 0) mbar_arrive(bar_lfree);
             lo = fmaxf(xlo[s], xlo[kTM + s]);
-            // ---- pass 2: candidate list
+            // ---- pass 2: candidate list of this (sample, half)
             const float thr = lo - kScreenNats;
-            int n = 0;
-            uint8_t *my = clist + tid * kCap;
             const int gend = G - 128 * h;   // only real Gaussians (also when every bound is NaN/-inf)
+            int n = 0;
+            uint8_t *my = cg + tid * kCap;
 #pragma unroll
             for (int j = 0; j < 128; ++j) {
                 if (j < gend && ub[j] >= thr) {
@@ -384,87 +446,92 @@ __global__ void __launch_bounds__(kThreads, 1) k_em_pass_tc(TcArgs args)
                     ++n;
                 }
             }
-            // ---- next tile's A operand (E(t) has finished reading the buffer)
-            if (t + 1 < T) build_a(tile + 1);
-            fence_proxy_async();
+            if (s >= nvalid) n = 0;
+            cn[tid] = n;
+            if (s < nvalid) { st_n += (h == 0); st_kept += (unsigned long long)n; st_dense += n > kCap; }
+            cp_async_wait1();   // this tile's FP32 rows have landed
             epi_sync();
-            if (tid == 0 && t + 1 < T) mbar_arrive(bar_afull);
-            // ---- exact log-densities of the candidates, log-sum-exp, M-step
-            float xr[DMAX];
-            load_row<DMAX>(xr, a.X + i * D, valid, D);
-            float lx[kCap];
-            float mh = -INFINITY, sh = 0.f;
-            const bool dense = n > kCap;
-            if (valid) { st_n += 1; st_kept += (unsigned long long)n; st_dense += dense ? 1ull : 0ull; }
-            if (!dense) {
-#pragma unroll
-                for (int k = 0; k < kCap; ++k) {
-                    lx[k] = -INFINITY;
-                    if (k < n) {
-                        const int g = 128 * h + my[k];
-                        lx[k] = exact_logit<DMAX>(xr, a.op.sm + (size_t)g * D, __ldg(a.op.c + g), D);
-                        mh = fmaxf(mh, lx[k]);
+            const float *xt = sX + (t & 1) * (Ls.xbytes / 4u);
+            // ---- exact log-densities, one warp per (sample, candidate)
+            for (int j = 0; j < 32; ++j) {
+                const int slot = 32 * warp + j, ss = 32 * q + j;
+                const int nn = cn[slot];
+                const float *x = xt + ss * D;
+                if (nn <= kCap) {
+                    for (int k = 0; k < nn; ++k) {
+                        const int g = 128 * h + cg[slot * kCap + k];
+                        const float l = warp_logit(x, a.op.sm + (size_t)g * D, __ldg(a.op.c + g), D, lane);
+                        if (lane == 0) cl[slot * kCap + k] = l;
                     }
-                }
-#pragma unroll
-                for (int k = 0; k < kCap; ++k)
-                    if (k < n) sh += __expf(lx[k] - mh);
-            } else {
-                const int ge = min(G, 128 * h + 128);
-                for (int g = 128 * h; g < ge; ++g) {
-                    const float l = exact_logit<DMAX>(xr, a.op.sm + (size_t)g * D, __ldg(a.op.c + g), D);
-                    if (l > mh) { sh = sh * __expf(mh - l) + 1.f; mh = l; }
-                    else sh += __expf(l - mh);
+                } else {
+                    float m = -INFINITY, sm = 0.f;
+                    const int ge = min(G, 128 * h + 128);
+                    for (int g = 128 * h; g < ge; ++g) {
+                        const float l = warp_logit(x, a.op.sm + (size_t)g * D, __ldg(a.op.c + g), D, lane);
+                        if (l > m) { sm = sm * __expf(m - l) + 1.f; m = l; }
+                        else sm += __expf(l - m);
+                    }
+                    if (lane == 0) dms[slot] = make_float2(m, sm);
                 }
             }
-            xms[h * kTM + s] = make_float2(mh, sh);
+            epi_sync();
+            // ---- log-sum-exp per sample over both halves' candidates (Eqs. 16-18)
+            float mh = -INFINITY, sh = 0.f;
+            const float *myl = cl + tid * kCap;
+            if (n <= kCap) {
+                for (int k = 0; k < n; ++k) mh = fmaxf(mh, myl[k]);
+                for (int k = 0; k < n; ++k) sh += __expf(myl[k] - mh);
+            } else {
+                const float2 v = dms[tid];
+                mh = v.x;
+                sh = v.y;
+            }
+            xms[tid] = make_float2(mh, sh);
             epi_sync();
             const float2 o = xms[(1 - h) * kTM + s];
             const float M = fmaxf(mh, o.x);
-            const float S = (mh == -INFINITY ? 0.f : sh * __expf(mh - M)) + (o.x == -INFINITY ? 0.f : o.y * __expf(o.x - M));
-            const float lse = M + logf(S);
-            if (valid) {
-                if (h == 0) ll += (double)lse;
-                auto accumulate = [&](int g, float l) {
-                    const float gm = __expf(l - lse);
-                    if (!(gm > 0.f)) return;
-                    atomicAdd(&S0[g], gm);
-                    const float *mu = a.op.mu + (size_t)g * D;
-#pragma unroll
-                    for (int d = 0; d < DMAX; ++d) {
-                        if (d < D) {
-                            const float u = xr[d] - __ldg(mu + d);
-                            const float gu = gm * u;
-                            atomicAdd(&S1[g * D + d], gu);
-                            atomicAdd(&S2[g * D + d], gu * u);
-                        }
+            const float Ssum = (mh == -INFINITY ? 0.f : sh * __expf(mh - M)) + (o.x == -INFINITY ? 0.f : o.y * __expf(o.x - M));
+            const float lse = M + logf(Ssum);
+            if (s < nvalid && h == 0) {
+                ll += (double)lse;
+                slse[s] = lse;
+            }
+            if (n <= kCap)
+                for (int k = 0; k < n; ++k) cl[tid * kCap + k] = __expf(myl[k] - lse);   // Eq. 3
+            epi_sync();
+            // ---- M-step accumulation, one warp per (sample, candidate)
+            for (int j = 0; j < 32; ++j) {
+                const int slot = 32 * warp + j, ss = 32 * q + j;
+                const int nn = cn[slot];
+                const float *x = xt + ss * D;
+                if (nn <= kCap) {
+                    for (int k = 0; k < nn; ++k) {
+                        const int g = 128 * h + cg[slot * kCap + k];
+                        const float gm = cl[slot * kCap + k];
+                        if (gm > 0.f) warp_accumulate(slab + (size_t)g * S, x, a.op.mu + (size_t)g * D, gm, D, lane);
                     }
-                };
-                if (!dense) {
-#pragma unroll
-                    for (int k = 0; k < kCap; ++k)
-                        if (k < n) accumulate(128 * h + my[k], lx[k]);
                 } else {
+                    const float ls = slse[ss];
                     const int ge = min(G, 128 * h + 128);
-                    for (int g = 128 * h; g < ge; ++g)
-                        accumulate(g, exact_logit<DMAX>(xr, a.op.sm + (size_t)g * D, __ldg(a.op.c + g), D));
+                    for (int g = 128 * h; g < ge; ++g) {
+                        const float l = warp_logit(x, a.op.sm + (size_t)g * D, __ldg(a.op.c + g), D, lane);
+                        const float gm = __expf(l - ls);
+                        if (gm > 0.f) warp_accumulate(slab + (size_t)g * S, x, a.op.mu + (size_t)g * D, gm, D, lane);
+                    }
                 }
             }
+            epi_sync();
         }
         tc_fence_before();
     }
+    __threadfence();
     __syncthreads();
-    // ---- flush the CTA's statistics (same layout as the FP32 form)
+    // ---- the CTA's statistics (FP32 slab in L2) -> its FP64 partial
     if (warp < 8) {
-        const int S = 1 + 2 * D;
         double *P = a.partial + (size_t)blockIdx.x * G * S;
-        for (int k = tid; k < G * S; k += kEpiThreads) {
-            const int g = k / S, j = k - g * S;
-            P[k] = j == 0 ? (double)S0[g] : (j <= D ? (double)S1[g * D + j - 1] : (double)S2[g * D + j - 1 - D]);
-        }
+        for (int k = tid; k < G * S; k += kEpiThreads) P[k] = (double)__ldcg(slab + k);
     }
-    double *red = reinterpret_cast<double *>(sbase + Ls.acc);   // statistics already flushed
-    __syncthreads();
+    double *red = reinterpret_cast<double *>(sbase + Ls.cl);   // candidate storage is free now
     if (a.screen_stats && warp < 8) {
         for (int o = 16; o > 0; o >>= 1) {
             st_n += __shfl_xor_sync(0xffffffffu, st_n, o);
@@ -472,7 +539,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_em_pass_tc(TcArgs args)
             st_dense += __shfl_xor_sync(0xffffffffu, st_dense, o);
         }
         if (lane == 0) {
-            atomicAdd(a.screen_stats + 0, (warp < 4) ? st_n : 0ull);   // each sample counted once (half 0)
+            atomicAdd(a.screen_stats + 0, st_n);
             atomicAdd(a.screen_stats + 1, st_kept);
             atomicAdd(a.screen_stats + 2, st_dense);
         }
@@ -504,19 +571,20 @@ bool em_tc_supported(int32_t D, int32_t G)
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    return tc_layout(D, G, NG).total + 1024u <= (uint32_t)optin;
+    return tc_layout(D, G, NG).total + 1024u + 64u <= (uint32_t)optin;
 }
 
 int em_tc_grid(int sms) { return sms; }
 
-cudaError_t launch_em_pass_tc(const EmPassArgs &a, int32_t grid, int32_t split, cudaStream_t s)
+size_t em_tc_slab_floats(int32_t D, int32_t G, int grid) { return (size_t)grid * G * (1 + 2 * D); }
+
+cudaError_t launch_em_pass_tc(const EmPassArgs &a, float *slab, int32_t grid, cudaStream_t s)
 {
-    if (split) return cudaErrorNotSupported;
-    TcArgs t{a, (a.G + 15) / 16 * 16, (a.D + 15) / 16};
+    TcArgs t{a, slab, (a.G + 15) / 16 * 16, (a.D + 15) / 16, (reinterpret_cast<uintptr_t>(a.X) & 15u) == 0};
     const size_t sm = tc_layout(a.D, a.G, t.NG).total + 1024u;
-    cudaError_t e = cudaFuncSetAttribute(k_em_pass_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(k_em_pass_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_em_pass_tc<64><<<grid, kThreads, sm, s>>>(t);
+    k_em_pass_tc<<<grid, kThreads, sm, s>>>(t);
     count_launches(1);
     return cudaGetLastError();
 }

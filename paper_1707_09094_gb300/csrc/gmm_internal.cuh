@@ -112,6 +112,7 @@ bool em_simt_supported(int32_t D, int32_t G);
 // ---- launchers implemented in gmm_em_tc.cu
 bool em_tc_supported(int32_t D, int32_t G);
 int em_tc_grid(int sms);
-cudaError_t launch_em_pass_tc(const EmPassArgs &a, int32_t grid, int32_t split, cudaStream_t s);
+size_t em_tc_slab_floats(int32_t D, int32_t G, int grid);
+cudaError_t launch_em_pass_tc(const EmPassArgs &a, float *slab, int32_t grid, cudaStream_t s);
 
 }  // namespace gmm
