@@ -245,6 +245,11 @@ gmm_status gmm_debug_set(gmm_model *m, int32_t key, int64_t value);
 #define GMM_STAT_SCREENED 3
 #define GMM_STAT_KEPT 4
 #define GMM_STAT_DENSE 5
+/* GMM_STAT_PHASE0 + k (k = 0..7): SM cycles one epilogue thread of each CTA
+ * spent in phase k of a tile (0 prefetch, 1 barrier, 2 MMA wait, 3 screen,
+ * 4 candidates + sample-tile wait, 5 exact recompute, 6 log-sum-exp and
+ * M-step, 7 end-of-tile barrier), summed over CTAs. */
+#define GMM_STAT_PHASE0 6
 gmm_status gmm_debug_get(const gmm_model *m, int32_t key, int64_t *value);
 
 /* Thread-local text of the last error ("" if none). */

@@ -208,6 +208,15 @@ class GMM:
             out.append(v.value)
         return tuple(out)
 
+    def phase_cycles(self):
+        """Per-phase SM cycles of the tensor-core pass since profile() (summed over CTAs)."""
+        out = []
+        for k in range(8):
+            v = ctypes.c_int64()
+            _lib.check(_lib.load().gmm_debug_get(self._h, 6 + k, ctypes.byref(v)), "gmm_debug_get")
+            out.append(v.value)
+        return out
+
     def ll_history(self, cap=4096):
         out = np.empty(cap)
         n = ctypes.c_int32()

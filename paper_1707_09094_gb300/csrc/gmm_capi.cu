@@ -307,7 +307,7 @@ gmm_status run_em(gmm_model *m, const float *Xd, int64_t N, int32_t em_iter, dou
         else CK(gmm::launch_em_pass_simt(pa, grid, s));
         if ((prc = prof_end(m, s, slot)) != GMM_OK) return prc;
         gmm::EmFinalizeArgs fa{m->partial, m->llp, grid, N, D, G, m->par[(base + k) & 1], m->par[(base + k + 1) & 1],
-                               var_floor, 0, m->op, m->center(), m->status, k, em_tol, m->lld,
+                               var_floor, tc ? 1 : 0, m->op, m->center(), m->status, k, em_tol, m->lld,
                                tc ? 1 : (m->has_center && m->center_D == D)};
         CK(gmm::launch_em_finalize(fa, s));
     }
@@ -655,8 +655,8 @@ gmm_status gmm_profile(gmm_model *m, int32_t enable)
 {
     if (!m) return fail(GMM_ERR_ARG, "model is NULL");
     m->profiling = enable != 0;
-    if (!m->sstats) CK(cudaMalloc(&m->sstats, 3 * sizeof(unsigned long long)));
-    CK(cudaMemset(m->sstats, 0, 3 * sizeof(unsigned long long)));
+    if (!m->sstats) CK(cudaMalloc(&m->sstats, 11 * sizeof(unsigned long long)));
+    CK(cudaMemset(m->sstats, 0, 11 * sizeof(unsigned long long)));
     m->ev_used = 0;
     m->pass_ms = 0.0;
     m->pass_launches = 0;
@@ -690,8 +690,8 @@ gmm_status gmm_debug_set(gmm_model *m, int32_t key, int64_t value)
 gmm_status gmm_debug_get(const gmm_model *m, int32_t key, int64_t *value)
 {
     if (!m || !value) return fail(GMM_ERR_ARG, "NULL argument");
-    if (key < GMM_STAT_SCREENED || key > GMM_STAT_DENSE) return fail(GMM_ERR_ARG, "unknown key %d", key);
-    unsigned long long v[3] = {0, 0, 0};
+    if (key < GMM_STAT_SCREENED || key > GMM_STAT_PHASE0 + 7) return fail(GMM_ERR_ARG, "unknown key %d", key);
+    unsigned long long v[11] = {0};
     if (m->sstats) CK(cudaMemcpy(v, m->sstats, sizeof v, cudaMemcpyDeviceToHost));
     *value = (int64_t)v[key - GMM_STAT_SCREENED];
     return GMM_OK;

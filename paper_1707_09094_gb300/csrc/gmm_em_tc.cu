@@ -11,10 +11,11 @@
 //     |l~ - l| <= 2^-8 * 1.25 * sum_d (x'^2 iv/2 + |x' mu'| iv) + tiny terms,
 //     and by AM-GM sum_d |x' mu'| iv <= sum_d (x'^2 + mu'^2) iv / 2, so
 //     |l~ - l| <= K1 |P1| + k2_g with k2_g = 2^-8 * 1.25 * q_g / 2 + ...
-//     A Gaussian whose upper bound lies more than 45 nats below the best
-//     lower bound has responsibility < 3e-20 and is dropped; per Gaussian the
-//     dropped mass is below N * 3e-20, far under the 1e-8 responsibility sum
-//     below which the update keeps a Gaussian's parameters.
+//     A Gaussian whose upper bound lies more than T = ln(N * 1e9) nats below
+//     the best lower bound (35 nats at N = 2e6) has responsibility below
+//     1e-9 / N and is dropped: per Gaussian the dropped mass is below 1e-9,
+//     under the 1e-8 responsibility sum below which the update keeps a
+//     Gaussian's parameters.
 //  3. The few remaining candidates (one to a few per sample on speech-like
 //     data) get their log-density recomputed exactly in FP32 on the CUDA
 //     cores, one warp per (sample, Gaussian) with lanes over dimensions;
@@ -32,6 +33,8 @@
 // returns.
 #include <cuda_bf16.h>
 
+#include <cmath>
+
 #include "gmm_internal.cuh"
 
 namespace gmm {
@@ -42,7 +45,7 @@ constexpr int kEpiThreads = 256;
 constexpr int kThreads = kEpiThreads + 32;
 constexpr int kTM = 128;          // samples per tile = MMA M
 constexpr int kCap = 16;          // candidates per (sample, half) before the dense fallback
-constexpr float kScreenNats = 45.0f;
+constexpr int kNB = 8;            // candidates a warp recomputes at once
 constexpr float kK1 = 0.009765625f * 1.25f;   // 2^-7 * 1.25 (multiplies |P1|)
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -165,32 +168,53 @@ __device__ __forceinline__ float warp_sum_f(float v)
     return v;
 }
 
-// Exact FP32 log-density of Gaussian g at one sample (the formula of the
-// CUDA-core form: c_g - 1/2 sum_d (x_d s_gd - mu_gd s_gd)^2), one warp, lanes
-// over dimensions; x is the sample's row in shared memory.
-__device__ __forceinline__ float warp_logit(const float *x, const float2 *__restrict__ p, float c, int D, int lane)
+__device__ __forceinline__ float warp_max_f(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Exact FP32 log-density of one Gaussian at one sample by one thread (the
+// formula of the CUDA-core form: c_g - 1/2 sum_d (x_d s_gd - mu_gd s_gd)^2);
+// x is the sample's row in shared memory.  Used by the dense path.
+__device__ __forceinline__ float thread_logit(const float *x, const float2 *__restrict__ p, float c, int D)
 {
     float acc = 0.f;
-    for (int d = lane; d < D; d += 32) {
+    for (int d = 0; d < D; ++d) {
         const float2 q = __ldg(p + d);
         const float t = fmaf(x[d], q.x, -q.y);
         acc = fmaf(t, t, acc);
     }
-    return fmaf(-0.5f, warp_sum_f(acc), c);
+    return fmaf(-0.5f, acc, c);
 }
 
 // M-step contribution of one (sample, Gaussian) pair with responsibility gm
-// (Eqs. 9-11, shifted by the FP32 mean mu_f): one warp, lanes over dimensions.
-__device__ __forceinline__ void warp_accumulate(float *slab_g, const float *x, const float *__restrict__ mu, float gm,
-                                                int D, int lane)
+// (Eqs. 9-11 about the shift tc_shift of the BF16 operand row of g in shared
+// memory): one warp; lane k adds (gm u, gm u^2) for dimensions 2k and 2k+1 as
+// one 16-byte vector atomic (CUDA's float4 atomicAdd, compute capability
+// >= 9.0) into the CTA's slab row [S0, pad x3 | (S1_d, S2_d) for d < DP].
+__device__ __forceinline__ void smem_accumulate(float *slab_g, const float *x, const unsigned char *sB, int NG, int g,
+                                                const float *ctr, float gm, int D, int DP, int lane)
 {
-    if (lane == 0) atomicAdd(slab_g, gm);
-    for (int d = lane; d < D; d += 32) {
-        const float u = x[d] - __ldg(mu + d);
-        const float gu = gm * u;
-        atomicAdd(slab_g + 1 + d, gu);
-        atomicAdd(slab_g + 1 + D + d, gu * u);
+    if (2 * lane < DP) {
+        auto term = [&](int d, float &a1, float &a2) {
+            float u = 0.f;
+            if (d < D) {
+                const uint32_t off = sw128_off(g, d >> 3) + (uint32_t)((d & 7) * 2);
+                const __nv_bfloat16 b1 = *reinterpret_cast<const __nv_bfloat16 *>(sB + off);
+                const __nv_bfloat16 b2 = *reinterpret_cast<const __nv_bfloat16 *>(sB + (uint32_t)NG * 128u + off);
+                u = x[d] - tc_shift(ctr[d], b1, b2);
+            }
+            a1 = gm * u;
+            a2 = a1 * u;
+        };
+        float4 v;
+        term(2 * lane, v.x, v.y);
+        term(2 * lane + 1, v.z, v.w);
+        atomicAdd(reinterpret_cast<float4 *>(slab_g + 4 + 4 * lane), v);
     }
+    if (lane == 31) atomicAdd(slab_g, gm);
 }
 
 __device__ __forceinline__ void cp_async4(uint32_t dst, const void *src)
@@ -210,6 +234,7 @@ struct TcArgs {
     int32_t NG;       // Gaussians padded to a multiple of 16 (MMA N)
     int32_t nk;       // K=16 steps per K block: ceil(D/16)
     int32_t x_al16;   // X is 16-byte aligned
+    float screen;     // screening distance in nats, ln(N * 1e9)
 };
 
 struct TcSmem {
@@ -271,10 +296,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_em_pass_tc(TcArgs args)
     uint64_t *bar_drain = bar_afull + 3;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sbase + Ls.misc);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(sbase + Ls.misc + 4);
-    float *slab = args.slab + (size_t)blockIdx.x * G * S;
+    float *slab = args.slab + (size_t)blockIdx.x * G * (4 + 2 * ((a.D + 3) & ~3));
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long long budget = a.wait_cycles;
+    const int DP = (D + 3) & ~3, SP = 4 + 2 * DP;     // padded slab row
     const int64_t ntiles = (a.N + kTM - 1) / kTM;
     const int64_t t0 = ntiles * blockIdx.x / gridDim.x, t1 = ntiles * (blockIdx.x + 1) / gridDim.x;
     const int T = (int)(t1 - t0);
@@ -299,13 +325,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_em_pass_tc(TcArgs args)
     auto build_a = [&](int64_t tile, int b) {
         const int64_t i0 = tile * kTM;
         unsigned char *ab = sA + b * (kTM * 256);
-        for (int r = warp; r < kTM; r += 8) {
+#pragma unroll
+        for (int i = 0; i < kTM / 8; ++i) {
+            const int r = warp + 8 * i;
             const bool v = i0 + r < a.N;
             const float *row = a.X + (i0 + r) * D;
 #pragma unroll
             for (int hh = 0; hh < 2; ++hh) {
                 const int d = lane + 32 * hh;
-                const float xc = (v && d < D) ? __ldg(row + d) - ctr[d] : 0.f;
+                const float xc = (v && d < D) ? __ldcs(row + d) - ctr[d] : 0.f;
                 const uint32_t off = sw128_off(r, d >> 3) + (uint32_t)((d & 7) * 2);
                 *reinterpret_cast<__nv_bfloat16 *>(ab + off) = __float2bfloat16_rn(xc * xc);
                 *reinterpret_cast<__nv_bfloat16 *>(ab + 16384 + off) = __float2bfloat16_rn(xc);
@@ -324,7 +352,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_em_pass_tc(TcArgs args)
         tmem_alloc(tmem_slot, 512);
         tmem_relinquish();
     } else {
-        for (int k = tid; k < G * S; k += kEpiThreads) slab[k] = 0.f;
+        for (int k = tid; k < G * SP; k += kEpiThreads) slab[k] = 0.f;
         for (int k = tid; k < NG * 16; k += kEpiThreads) {
             const int g = k >> 4, kb = (k >> 3) & 1, c = k & 7;
             uint4 v = make_uint4(0u, 0u, 0u, 0u);
@@ -358,6 +386,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_em_pass_tc(TcArgs args)
 
     double ll = 0.0;
     unsigned long long st_kept = 0, st_dense = 0, st_n = 0;
+    unsigned long long tp[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // phase cycles (thread 0, profiling only)
+    long long tmark = clock64();
+    auto phase = [&](int k) {
+        const long long now = clock64();
+        tp[k] += (unsigned long long)(now - tmark);
+        tmark = now;
+    };
     if (warp == 8) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
@@ -400,11 +435,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_em_pass_tc(TcArgs args)
             } else {
                 cp_async_commit();
             }
+            phase(0);
             epi_sync();
             if (tid == 0 && t + 1 < T) mbar_arrive(bar_afull);
+            phase(1);
             // ---- pass 1: screening bounds from the two TMEM accumulators
             mbar_wait(bar_lfull, (uint32_t)(t & 1), abort_flag, budget);
             tc_fence_after();
+            phase(2);
             float ub[128];
             float lo = -INFINITY;
 #pragma unroll
@@ -430,12 +468,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_em_pass_tc(TcArgs args)
                 }
             }
             tc_fence_before();
+            phase(3);
             xlo[tid] = lo;
             epi_sync();
             if (tid == 0) mbar_arrive(bar_lfree);
             lo = fmaxf(xlo[s], xlo[kTM + s]);
             // ---- pass 2: candidate list of this (sample, half)
-            const float thr = lo - kScreenNats;
+            const float thr = lo - args.screen;
             const int gend = G - 128 * h;   // only real Gaussians (also when every bound is NaN/-inf)
             int n = 0;
             uint8_t *my = cg + tid * kCap;
@@ -451,29 +490,76 @@ __global__ void __launch_bounds__(kThreads, 1) k_em_pass_tc(TcArgs args)
             if (s < nvalid) { st_n += (h == 0); st_kept += (unsigned long long)n; st_dense += n > kCap; }
             cp_async_wait1();   // this tile's FP32 rows have landed
             epi_sync();
+            phase(4);
             const float *xt = sX + (t & 1) * (Ls.xbytes / 4u);
-            // ---- exact log-densities, one warp per (sample, candidate)
-            for (int j = 0; j < 32; ++j) {
-                const int slot = 32 * warp + j, ss = 32 * q + j;
-                const int nn = cn[slot];
-                const float *x = xt + ss * D;
-                if (nn <= kCap) {
-                    for (int k = 0; k < nn; ++k) {
-                        const int g = 128 * h + cg[slot * kCap + k];
-                        const float l = warp_logit(x, a.op.sm + (size_t)g * D, __ldg(a.op.c + g), D, lane);
-                        if (lane == 0) cl[slot * kCap + k] = l;
+            // ---- exact log-densities: one warp per (sample, candidate), kNB
+            // candidates at a time so that their parameter rows load together
+            const int my_n = cn[32 * warp + lane];
+            const unsigned dense_mask = __ballot_sync(0xffffffffu, my_n > kCap);
+            for (int r = 0; r < kCap; ++r) {
+                unsigned mask = __ballot_sync(0xffffffffu, my_n > r && my_n <= kCap);
+                while (mask) {
+                    int jj[kNB], gg[kNB];
+                    bool vv[kNB];
+#pragma unroll
+                    for (int u = 0; u < kNB; ++u) {
+                        vv[u] = mask != 0u;
+                        jj[u] = vv[u] ? __ffs(mask) - 1 : 0;
+                        if (vv[u]) mask &= mask - 1u;
+                        gg[u] = vv[u] ? 128 * h + cg[(32 * warp + jj[u]) * kCap + r] : 0;
                     }
-                } else {
-                    float m = -INFINITY, sm = 0.f;
-                    const int ge = min(G, 128 * h + 128);
-                    for (int g = 128 * h; g < ge; ++g) {
-                        const float l = warp_logit(x, a.op.sm + (size_t)g * D, __ldg(a.op.c + g), D, lane);
-                        if (l > m) { sm = sm * __expf(m - l) + 1.f; m = l; }
-                        else sm += __expf(l - m);
+                    float2 pp[kNB][2];
+                    float cc = 0.f;
+#pragma unroll
+                    for (int u = 0; u < kNB; ++u) {
+                        if (lane == u && vv[u]) cc = __ldg(a.op.c + gg[u]);
+#pragma unroll
+                        for (int hh = 0; hh < 2; ++hh) {
+                            const int d = lane + 32 * hh;
+                            pp[u][hh] = (vv[u] && d < D) ? __ldg(a.op.sm + (size_t)gg[u] * D + d) : make_float2(0.f, 0.f);
+                        }
                     }
-                    if (lane == 0) dms[slot] = make_float2(m, sm);
+                    float acc[kNB];
+#pragma unroll
+                    for (int u = 0; u < kNB; ++u) {
+                        const float *x = xt + (32 * q + jj[u]) * D;
+                        acc[u] = 0.f;
+#pragma unroll
+                        for (int hh = 0; hh < 2; ++hh) {
+                            const int d = lane + 32 * hh;
+                            if (vv[u] && d < D) {
+                                const float tt = fmaf(x[d], pp[u][hh].x, -pp[u][hh].y);
+                                acc[u] = fmaf(tt, tt, acc[u]);
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                        for (int u = 0; u < kNB; ++u) acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], o);
+                    // lane u writes candidate u (all lanes hold every reduced sum)
+#pragma unroll
+                    for (int u = 0; u < kNB; ++u)
+                        if (lane == u && vv[u]) cl[(32 * warp + jj[u]) * kCap + r] = fmaf(-0.5f, acc[u], cc);
                 }
             }
+            // dense slots (candidate list overflowed): lanes over Gaussians
+            for (unsigned dm = dense_mask; dm; dm &= dm - 1u) {
+                const int j = __ffs(dm) - 1;
+                const float *x = xt + (32 * q + j) * D;
+                float m = -INFINITY, sm = 0.f;
+                const int ge = min(G, 128 * h + 128);
+                for (int g = 128 * h + lane; g < ge; g += 32) {
+                    const float l = thread_logit(x, a.op.sm + (size_t)g * D, __ldg(a.op.c + g), D);
+                    if (l > m) { sm = sm * __expf(m - l) + 1.f; m = l; }
+                    else sm += __expf(l - m);
+                }
+                const float M = warp_max_f(m);
+                sm = (m == -INFINITY) ? 0.f : sm * __expf(m - M);
+                sm = warp_sum_f(sm);
+                if (lane == 0) dms[32 * warp + j] = make_float2(M, sm);
+            }
+            phase(5);
             epi_sync();
             // ---- log-sum-exp per sample over both halves' candidates (Eqs. 16-18)
             float mh = -INFINITY, sh = 0.f;
@@ -499,28 +585,44 @@ __global__ void __launch_bounds__(kThreads, 1) k_em_pass_tc(TcArgs args)
             if (n <= kCap)
                 for (int k = 0; k < n; ++k) cl[tid * kCap + k] = __expf(myl[k] - lse);   // Eq. 3
             epi_sync();
-            // ---- M-step accumulation, one warp per (sample, candidate)
-            for (int j = 0; j < 32; ++j) {
-                const int slot = 32 * warp + j, ss = 32 * q + j;
-                const int nn = cn[slot];
-                const float *x = xt + ss * D;
-                if (nn <= kCap) {
-                    for (int k = 0; k < nn; ++k) {
-                        const int g = 128 * h + cg[slot * kCap + k];
-                        const float gm = cl[slot * kCap + k];
-                        if (gm > 0.f) warp_accumulate(slab + (size_t)g * S, x, a.op.mu + (size_t)g * D, gm, D, lane);
-                    }
-                } else {
-                    const float ls = slse[ss];
-                    const int ge = min(G, 128 * h + 128);
-                    for (int g = 128 * h; g < ge; ++g) {
-                        const float l = warp_logit(x, a.op.sm + (size_t)g * D, __ldg(a.op.c + g), D, lane);
-                        const float gm = __expf(l - ls);
-                        if (gm > 0.f) warp_accumulate(slab + (size_t)g * S, x, a.op.mu + (size_t)g * D, gm, D, lane);
+            // ---- M-step accumulation: one warp per (sample, candidate), kNB at a
+            // time; the shift comes from the BF16 operand in shared memory
+            for (int r = 0; r < kCap; ++r) {
+                unsigned mask = __ballot_sync(0xffffffffu, my_n > r && my_n <= kCap);
+                while (mask) {
+#pragma unroll
+                    for (int u = 0; u < kNB; ++u) {
+                        if (!mask) break;
+                        const int j = __ffs(mask) - 1;
+                        mask &= mask - 1u;
+                        const int slot = 32 * warp + j;
+                        const int g = 128 * h + cg[slot * kCap + r];
+                        const float gm = cl[slot * kCap + r];
+                        if (gm > 0.f)
+                            smem_accumulate(slab + (size_t)g * SP, xt + (32 * q + j) * D, sB, NG, g, ctr, gm, D, DP, lane);
                     }
                 }
             }
+            for (unsigned dm = dense_mask; dm; dm &= dm - 1u) {
+                const int j = __ffs(dm) - 1;
+                const float *x = xt + (32 * q + j) * D;
+                const float ls = slse[32 * q + j];
+                const int ge = min(G, 128 * h + 128);
+                for (int g0 = 128 * h; g0 < ge; g0 += 32) {
+                    const int g = g0 + lane;
+                    const float gml = g < ge ? __expf(thread_logit(x, a.op.sm + (size_t)g * D, __ldg(a.op.c + g), D) - ls) : 0.f;
+                    unsigned live = __ballot_sync(0xffffffffu, gml > 0.f);
+                    while (live) {
+                        const int src = __ffs(live) - 1;
+                        live &= live - 1u;
+                        const float gmv = __shfl_sync(0xffffffffu, gml, src);
+                        smem_accumulate(slab + (size_t)(g0 + src) * SP, x, sB, NG, g0 + src, ctr, gmv, D, DP, lane);
+                    }
+                }
+            }
+            phase(6);
             epi_sync();
+            phase(7);
         }
         tc_fence_before();
     }
@@ -529,7 +631,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_em_pass_tc(TcArgs args)
     // ---- the CTA's statistics (FP32 slab in L2) -> its FP64 partial
     if (warp < 8) {
         double *P = a.partial + (size_t)blockIdx.x * G * S;
-        for (int k = tid; k < G * S; k += kEpiThreads) P[k] = (double)__ldcg(slab + k);
+        for (int k = tid; k < G * S; k += kEpiThreads) {
+            const int g = k / S, j = k - g * S;
+            const int src = j == 0 ? 0 : (j <= D ? 4 + 2 * (j - 1) : 4 + 2 * (j - 1 - D) + 1);
+            P[k] = (double)__ldcg(slab + (size_t)g * SP + src);
+        }
     }
     double *red = reinterpret_cast<double *>(sbase + Ls.cl);   // candidate storage is free now
     if (a.screen_stats && warp < 8) {
@@ -543,6 +649,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_em_pass_tc(TcArgs args)
             atomicAdd(a.screen_stats + 1, st_kept);
             atomicAdd(a.screen_stats + 2, st_dense);
         }
+        if (tid == 0)
+            for (int k = 0; k < 8; ++k) atomicAdd(a.screen_stats + 3 + k, tp[k]);
     }
     for (int o = 16; o > 0; o >>= 1) ll += __shfl_xor_sync(0xffffffffu, ll, o);
     if (lane == 0) red[warp] = ll;
@@ -576,11 +684,12 @@ bool em_tc_supported(int32_t D, int32_t G)
 
 int em_tc_grid(int sms) { return sms; }
 
-size_t em_tc_slab_floats(int32_t D, int32_t G, int grid) { return (size_t)grid * G * (1 + 2 * D); }
+size_t em_tc_slab_floats(int32_t D, int32_t G, int grid) { return (size_t)grid * G * (4 + 2 * ((D + 3) & ~3)); }
 
 cudaError_t launch_em_pass_tc(const EmPassArgs &a, float *slab, int32_t grid, cudaStream_t s)
 {
-    TcArgs t{a, slab, (a.G + 15) / 16 * 16, (a.D + 15) / 16, (reinterpret_cast<uintptr_t>(a.X) & 15u) == 0};
+    TcArgs t{a, slab, (a.G + 15) / 16 * 16, (a.D + 15) / 16, (reinterpret_cast<uintptr_t>(a.X) & 15u) == 0,
+             (float)std::log((double)a.N * 1e9)};
     const size_t sm = tc_layout(a.D, a.G, t.NG).total + 1024u;
     cudaError_t e = cudaFuncSetAttribute(k_em_pass_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
