@@ -226,6 +226,25 @@ def run_ours(args):
         return {"ms": ms, "wall_s": wall, "pass_ms": pass_ms, "pass_n": pass_n, "launches": launches,
                 "clocks": cs.summary()}
 
+    # k-means (Sec. 3) pass throughput and one whole learn(), reported beside the EM metric
+    km = GMM().set_params(*start)
+    km.kmeans(Xd, 1, return_assign=False)
+    km.set_params(*start)
+    km.profile(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    km.kmeans(Xd, 5, return_assign=False)
+    torch.cuda.synchronize()
+    km_wall = time.perf_counter() - t0
+    km_ms, km_n, _ = km.profile_read()
+    learn_t = []
+    for _ in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        GMM().learn(Xd, G, km_iter=10, em_iter=10, seed=1002, prec=args.forms[-1])
+        torch.cuda.synchronize()
+        learn_t.append(time.perf_counter() - t0)
+
     results = {}
     for prec in args.forms:
         if "error" in quality.get(prec, {}):
@@ -270,6 +289,9 @@ def run_ours(args):
         "clocks": r["clocks"],
         "e2e": {"value": world * units / (e2e["ms"] / args.steps * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": int(X.nbytes), "d2h_bytes_per_step": 8 + 32},
+        "kmeans": {"pass_ms": km_ms / max(km_n, 1), "units_per_s": units / (km_ms / max(km_n, 1) * 1e-3),
+                   "iterations_wall_ms": km_wall * 1e3 / 5},
+        "learn_10km_10em_s": min(learn_t),
         "forms": {p: {"value": world * units / (results[p]["ms"] / args.steps * 1e-3),
                       "ms_per_step": results[p]["ms"] / args.steps,
                       "pass_ms": results[p]["pass_ms"] / max(results[p]["pass_n"], 1),

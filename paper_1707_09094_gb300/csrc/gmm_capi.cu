@@ -250,15 +250,16 @@ gmm_status run_kmeans(gmm_model *m, const float *Xd, int64_t N, int32_t km_iter,
     const int32_t D = m->D, G = m->G, S = 1 + 2 * D;
     const int grid = gmm::km_grid(D, G, m->sms);
     CK(grow(m->partial, m->partial_cap, (size_t)grid * G * S));
+    CK(grow(m->slab, m->slab_cap, gmm::km_slab_floats(D, G, grid)));
     CK(grow(m->assign, m->assign_cap, (size_t)N));
     CK(grow(m->counts, m->counts_cap, (size_t)G));
     for (int32_t it = 0; it < km_iter; ++it) {
-        int32_t np = 0;
+        const int32_t np = grid;
         size_t slot = 0;
         gmm_status prc = prof_begin(m, s, &slot);
         if (prc != GMM_OK) return prc;
-        CK(gmm::launch_km_pass(Xd, N, D, G, m->par[m->cur], m->wdist(), m->sw(), m->partial, grid, m->assign,
-                               m->status, &np, s));
+        CK(gmm::launch_km_pass(Xd, N, D, G, m->par[m->cur], m->wdist(), m->sw(), m->slab, m->partial, grid,
+                               m->assign, m->status, s));
         if ((prc = prof_end(m, s, slot)) != GMM_OK) return prc;
         CK(gmm::launch_km_finalize(m->partial, np, N, D, G, m->par[m->cur], var_floor, it == km_iter - 1,
                                    m->counts, Xd, m->assign, m->gvar(), m->status, s));

@@ -95,8 +95,9 @@ cudaError_t launch_global_stats(const float *X, int64_t N, int32_t D, double var
 cudaError_t launch_gather_seeds(const float *X, int32_t D, int32_t G, const int64_t *idx,
                                 double *par, cudaStream_t s);
 cudaError_t launch_km_pass(const float *X, int64_t N, int32_t D, int32_t G, const double *par,
-                           const double *wdist, const float *sw, double *partial, int32_t grid,
-                           int32_t *assign, DevStatus *status, int32_t *n_partial, cudaStream_t s);
+                           const double *wdist, const float *sw, float *slab, double *partial, int32_t grid,
+                           int32_t *assign, DevStatus *status, cudaStream_t s);
+size_t km_slab_floats(int32_t D, int32_t G, int grid);
 cudaError_t launch_km_finalize(const double *partial, int32_t n_partial, int64_t N, int32_t D,
                                int32_t G, double *par, double var_floor, int32_t final_iter,
                                double *counts, const float *X, const int32_t *assign,

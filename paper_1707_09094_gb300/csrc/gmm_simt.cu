@@ -174,35 +174,34 @@ struct KmArgs {
     const double *means;   // lambda (means at the start of the iteration)
     const double *w;       // [D] FP64 distance weights
     const float *sw;       // [D] FP32 sqrt(w)
-    double *partial;       // [grid][G][1+2D]   (smem-acc mode) or [1][G][1+2D] (global mode)
+    float *slab;           // [grid][G][4 + 2*DP] FP32 per-CTA statistics (L2)
+    double *partial;       // [grid][G][1+2D] FP64 per-CTA statistics (output)
     int32_t *assign;
-    int32_t smem_acc;
     const DevStatus *status;
 };
 
 // k-means map step (Sec. 3 with Sec. 2.1's chunking): each CTA takes a
 // contiguous chunk of samples; per sample the nearest mean (exact), then the
-// hard statistics count, sum(x - mu_old), sum((x - mu_old)^2) of its mean
-// (shifted by the FP32 old mean so that FP32 partial sums stay small).
+// hard statistics count, sum(x - mu_old), sum((x - mu_old)^2) of its mean,
+// shifted by the FP32 old mean so that FP32 sums stay small.  The sums go to
+// the CTA's FP32 slab in L2 as 16-byte vector atomics, one per two dimensions
+// (row layout [count, pad x3 | (S1_d, S2_d) for d < DP]); at the end the CTA
+// converts its slab to its FP64 partial.  Shared memory holds only the means.
 template <int DMAX>
 __global__ void __launch_bounds__(kKmThreads) k_km_pass(KmArgs a)
 {
     extern __shared__ __align__(16) unsigned char km_smem[];
     if (block_skip(a.status, 0)) return;
-    const int D = a.D, DP = a.DP, G = a.G, GS = a.GS;
+    const int D = a.D, DP = a.DP, G = a.G, GS = a.GS, SP = 4 + 2 * DP;
     float *cent = reinterpret_cast<float *>(km_smem);         // [GS][DP] scaled means
     float *cnorm = cent + (size_t)GS * DP;                       // [GS]
-    float *S1 = cnorm + GS;                                      // [G][D]   (smem-acc)
-    float *S2 = S1 + (size_t)G * D;                              // [G][D]
-    int *cnt = reinterpret_cast<int *>(S2 + (size_t)G * D);      // [G]
     __shared__ float s_nmax;
     __shared__ float s_sw[GMM_MAX_DIMS];
+    float *slab = a.slab + (size_t)blockIdx.x * G * SP;
 
     for (int d = threadIdx.x; d < D; d += blockDim.x) s_sw[d] = a.sw[d];
-    if (a.smem_acc) {
-        for (int k = threadIdx.x; k < G * D; k += blockDim.x) { S1[k] = 0.f; S2[k] = 0.f; }
-        for (int g = threadIdx.x; g < G; g += blockDim.x) cnt[g] = 0;
-    }
+    for (int k = threadIdx.x; k < G * SP; k += blockDim.x) slab[k] = 0.f;
+    __threadfence();
     __syncthreads();
 
     const int64_t per = (a.N + gridDim.x - 1) / gridDim.x;
@@ -253,17 +252,18 @@ __global__ void __launch_bounds__(kKmThreads) k_km_pass(KmArgs a)
             if (!one_slab) { __syncthreads(); load_slab(g0, gs); }
             for (int gg = 0; gg < gs; ++gg) {
                 const float4 *c4 = reinterpret_cast<const float4 *>(cent + gg * DP);
-                float acc = 0.f;
+                float acc0 = 0.f, acc1 = 0.f;
 #pragma unroll
                 for (int q = 0; q < DMAX / 4; ++q) {
                     if (q * 4 < DP) {
                         float4 c = c4[q];
                         float t0 = xs[4 * q] - c.x, t1 = xs[4 * q + 1] - c.y;
                         float t2 = xs[4 * q + 2] - c.z, t3 = xs[4 * q + 3] - c.w;
-                        acc = fmaf(t0, t0, acc); acc = fmaf(t1, t1, acc);
-                        acc = fmaf(t2, t2, acc); acc = fmaf(t3, t3, acc);
+                        acc0 = fmaf(t0, t0, acc0); acc1 = fmaf(t1, t1, acc1);
+                        acc0 = fmaf(t2, t2, acc0); acc1 = fmaf(t3, t3, acc1);
                     }
                 }
+                const float acc = acc0 + acc1;
                 if (acc < b1) { b2 = b1; b1 = acc; a1 = g0 + gg; }
                 else if (acc < b2) { b2 = acc; }
             }
@@ -275,41 +275,25 @@ __global__ void __launch_bounds__(kKmThreads) k_km_pass(KmArgs a)
             best = km_recheck_fp64(a.X + i * D, D, G, a.means, a.w);
         a.assign[i] = best;
         const double *mu = a.means + (size_t)best * D;
-        if (a.smem_acc) {
-            atomicAdd(&cnt[best], 1);
+        float *sg = slab + (size_t)best * SP;
+        atomicAdd(sg, 1.f);
 #pragma unroll
-            for (int d = 0; d < DMAX; ++d) {
-                if (d < D) {
-                    const float u = xr[d] - (float)mu[d];
-                    atomicAdd(&S1[best * D + d], u);
-                    atomicAdd(&S2[best * D + d], u * u);
-                }
-            }
-        } else {
-            double *P = a.partial + (size_t)best * (1 + 2 * D);
-            atomicAdd(P, 1.0);
-#pragma unroll
-            for (int d = 0; d < DMAX; ++d) {
-                if (d < D) {
-                    const double u = (double)(xr[d] - (float)mu[d]);
-                    atomicAdd(P + 1 + d, u);
-                    atomicAdd(P + 1 + D + d, u * u);
-                }
+        for (int d = 0; d < DMAX; d += 2) {
+            if (d < D) {
+                const float u0 = xr[d] - (float)mu[d];
+                const float u1 = d + 1 < D ? xr[d + 1] - (float)mu[d + 1] : 0.f;
+                atomicAdd(reinterpret_cast<float4 *>(sg + 4 + 2 * d), make_float4(u0, u0 * u0, u1, u1 * u1));
             }
         }
     }
-    if (a.smem_acc) {
-        __syncthreads();
-        const int S = 1 + 2 * D;
-        double *P = a.partial + (size_t)blockIdx.x * G * S;
-        for (int k = threadIdx.x; k < G * S; k += blockDim.x) {
-            int g = k / S, j = k - g * S;
-            double v;
-            if (j == 0) v = (double)cnt[g];
-            else if (j <= D) v = (double)S1[g * D + j - 1];
-            else v = (double)S2[g * D + j - 1 - D];
-            P[k] = v;
-        }
+    __threadfence();
+    __syncthreads();
+    const int S = 1 + 2 * D;
+    double *P = a.partial + (size_t)blockIdx.x * G * S;
+    for (int k = threadIdx.x; k < G * S; k += blockDim.x) {
+        const int g = k / S, j = k - g * S;
+        const int src = j == 0 ? 0 : (j <= D ? 4 + 2 * (j - 1) : 4 + 2 * (j - 1 - D) + 1);
+        P[k] = (double)__ldcg(slab + (size_t)g * SP + src);
     }
 }
 
@@ -527,18 +511,28 @@ __global__ void __launch_bounds__(kEmThreads, 1) k_em_pass_simt(EmPassArgs a)
             float xr[DMAX];
 #pragma unroll
             for (int d = 0; d < DMAX; ++d) xr[d] = d < D ? xT[d * kTP + lane] : 0.f;
-            for (int g = w; g < G; g += kWarps) {
-                const float2 *p = a.op.sm + (size_t)g * D;
-                float acc = 0.f;
+            // four Gaussians per step: four independent FMA chains per thread
+            for (int g0 = w; g0 < G; g0 += 4 * kWarps) {
+                float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
                 for (int d = 0; d < DMAX; ++d) {
                     if (d < D) {
-                        const float2 q = __ldg(p + d);
-                        const float t = fmaf(xr[d], q.x, -q.y);
-                        acc = fmaf(t, t, acc);
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int g = g0 + u * kWarps;
+                            if (g < G) {
+                                const float2 q = __ldg(a.op.sm + (size_t)g * D + d);
+                                const float t = fmaf(xr[d], q.x, -q.y);
+                                acc[u] = fmaf(t, t, acc[u]);
+                            }
+                        }
                     }
                 }
-                L[g * kTP + lane] = fmaf(-0.5f, acc, __ldg(a.op.c + g));
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int g = g0 + u * kWarps;
+                    if (g < G) L[g * kTP + lane] = fmaf(-0.5f, acc[u], __ldg(a.op.c + g));
+                }
             }
         }
         __syncthreads();
@@ -557,21 +551,37 @@ __global__ void __launch_bounds__(kEmThreads, 1) k_em_pass_simt(EmPassArgs a)
         }
         __syncthreads();
         // ---- M: thread-owned (g, d) accumulators
-        for (int p = tid; p < G * D; p += kEmThreads) {
-            const int g = p / D, d = p - g * D;
-            const float mu = __ldg(a.op.mu + p);
-            const float *Lg = L + g * kTP;
-            const float *xd = xT + d * kTP;
-            float r1 = 0.f, r2 = 0.f;
-#pragma unroll 8
-            for (int i = 0; i < kTile; ++i) {
-                const float gm = Lg[i];
-                const float u = xd[i] - mu;
-                r1 = fmaf(gm, u, r1);
-                r2 = fmaf(gm * u, u, r2);
+        // four (g, d) pairs per step: eight independent FMA chains per thread
+        for (int p0 = tid; p0 < G * D; p0 += 4 * kEmThreads) {
+            int gq[4], dq[4];
+            float mu[4], r1[4], r2[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int p = min(p0 + u * kEmThreads, G * D - 1);
+                gq[u] = p / D;
+                dq[u] = p - gq[u] * D;
+                mu[u] = __ldg(a.op.mu + p);
+                r1[u] = 0.f;
+                r2[u] = 0.f;
             }
-            S1[p] += r1;
-            S2[p] += r2;
+#pragma unroll 4
+            for (int i = 0; i < kTile; ++i) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float gm = L[gq[u] * kTP + i];
+                    const float uu = xT[dq[u] * kTP + i] - mu[u];
+                    r1[u] = fmaf(gm, uu, r1[u]);
+                    r2[u] = fmaf(gm * uu, uu, r2[u]);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int p = p0 + u * kEmThreads;
+                if (p < G * D) {
+                    S1[p] += r1[u];
+                    S2[p] += r2[u];
+                }
+            }
         }
         for (int g = tid; g < G; g += kEmThreads) {
             float r0 = 0.f;
@@ -897,7 +907,7 @@ int em_simt_grid(int32_t D, int32_t G, int sms)
 int km_grid(int32_t D, int32_t G, int sms)
 {
     (void)D; (void)G;
-    return sms * 2;
+    return sms * 3;   // the means slab (<= 64 KB) lets three CTAs share an SM
 }
 
 cudaError_t launch_global_stats(const float *X, int64_t N, int32_t D, double var_floor, int32_t dist,
@@ -937,25 +947,12 @@ static size_t km_slab_smem(int32_t D, int32_t G, int *GS_out, int *DP_out)
 }
 
 cudaError_t launch_km_pass(const float *X, int64_t N, int32_t D, int32_t G, const double *par,
-                           const double *wdist, const float *sw, double *partial, int32_t grid,
-                           int32_t *assign, DevStatus *status, int32_t *n_partial, cudaStream_t s)
+                           const double *wdist, const float *sw, float *slab, double *partial, int32_t grid,
+                           int32_t *assign, DevStatus *status, cudaStream_t s)
 {
     int GS, DP;
-    size_t sm = km_slab_smem(D, G, &GS, &DP);
-    const size_t acc = sizeof(float) * 2 * (size_t)G * D + sizeof(int) * G;
-    int dev = 0, optin = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    KmArgs a{X, N, D, DP, G, GS, par, wdist, sw, partial, assign, 1, status};
-    *n_partial = grid;
-    if (sm + acc + 1024 <= (size_t)optin) {
-        sm += acc;
-    } else {
-        *n_partial = 1;
-        a.smem_acc = 0;
-        cudaError_t e = cudaMemsetAsync(partial, 0, sizeof(double) * (size_t)G * (1 + 2 * D), s);
-        if (e != cudaSuccess) return e;
-    }
+    const size_t sm = km_slab_smem(D, G, &GS, &DP);
+    KmArgs a{X, N, D, DP, G, GS, par, wdist, sw, slab, partial, assign, status};
     const int dm = dmax_for(D);
 #define KM_LAUNCH(DM)                                                                              \
     do {                                                                                           \
@@ -970,6 +967,8 @@ cudaError_t launch_km_pass(const float *X, int64_t N, int32_t D, int32_t G, cons
     count_launches(1);
     return cudaGetLastError();
 }
+
+size_t km_slab_floats(int32_t D, int32_t G, int grid) { return (size_t)grid * G * (4 + 2 * ((D + 3) & ~3)); }
 
 cudaError_t launch_km_finalize(const double *partial, int32_t n_partial, int64_t N, int32_t D, int32_t G,
                                double *par, double var_floor, int32_t final_iter, double *counts,
