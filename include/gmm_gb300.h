@@ -85,10 +85,11 @@ typedef struct {
     void *stream;       /* cudaStream_t, NULL = default stream                        */
 } gmm_learn_opts;
 
-/* Per-call limits of the kernels: D <= GMM_MAX_DIMS everywhere; the FP32
- * EM pass needs its per-CTA statistics (4 * n_gaus * (2D+1) bytes plus the
- * tile buffers) to fit in shared memory; the tensor-core EM pass needs
- * D <= 64 and n_gaus <= 256.  Other shapes return GMM_ERR_UNSUPPORTED. */
+/* Per-call limits of the kernels: D <= GMM_MAX_DIMS everywhere.  The FP32
+ * EM form runs one fused pass when its per-CTA statistics (4 n_gaus (2D+1)
+ * bytes plus tile buffers) fit in shared memory, and otherwise two phases (a
+ * log-sum-exp pass, then one pass per slab of Gaussians).  The tensor-core
+ * EM pass needs D <= 64 and n_gaus <= 256 (else GMM_ERR_UNSUPPORTED). */
 #define GMM_MAX_DIMS 128
 
 /* Create an empty model (no parameters) on the current CUDA device. */

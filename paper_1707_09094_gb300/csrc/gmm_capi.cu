@@ -116,6 +116,7 @@ struct gmm_model {
     // workspace
     double *partial = nullptr; size_t partial_cap = 0;
     float *slab = nullptr; size_t slab_cap = 0;
+    float *lse = nullptr; size_t lse_cap = 0;
     double *llp = nullptr; size_t llp_cap = 0;
     double *lld = nullptr; size_t lld_cap = 0;
     double *counts = nullptr; size_t counts_cap = 0;
@@ -285,14 +286,19 @@ gmm_status run_em(gmm_model *m, const float *Xd, int64_t N, int32_t em_iter, dou
     if (prec == GMM_TF32 || prec == GMM_SPLIT_BF16) return fail(GMM_ERR_UNSUPPORTED, "prec %d is reserved", prec);
     if (tc && !gmm::em_tc_supported(D, G))
         return fail(GMM_ERR_UNSUPPORTED, "tensor-core E-step needs D <= 64 and n_gaus <= 256 (D=%d, G=%d)", D, G);
-    if (!tc && !gmm::em_simt_supported(D, G))
+    const bool two_phase = !tc && !gmm::em_simt_supported(D, G);
+    if (two_phase && gmm::em_slab_width(D, G) < 1)
         return fail(GMM_ERR_UNSUPPORTED, "FP32 E-step: shared memory too small for D=%d, G=%d", D, G);
     if (tc && !(m->has_center && m->center_D == D))
         return fail(GMM_ERR_STATE, "tensor-core E-step needs the global centre (run learn or recompute_center)");
-    const int grid = tc ? gmm::em_tc_grid(m->sms) : gmm::em_simt_grid(D, G, m->sms);
+    // one-pass forms: one partial per CTA; two-phase form: one per sample chunk
+    // (and one log-likelihood partial per 128-sample block of the lse pass)
+    const int grid = tc ? gmm::em_tc_grid(m->sms) : (two_phase ? m->sms : gmm::em_simt_grid(D, G, m->sms));
+    const int n_llp = two_phase ? (int)((N + 127) / 128) : grid;
     CK(grow(m->partial, m->partial_cap, (size_t)grid * G * S));
+    if (two_phase) CK(grow(m->lse, m->lse_cap, (size_t)N));
     if (tc) CK(grow(m->slab, m->slab_cap, gmm::em_tc_slab_floats(D, G, grid)));
-    CK(grow(m->llp, m->llp_cap, (size_t)grid));
+    CK(grow(m->llp, m->llp_cap, (size_t)n_llp));
     CK(grow(m->lld, m->lld_cap, (size_t)(em_iter > 0 ? em_iter : 1)));
     CK(gmm::launch_status_reset(m->status, s));
     if (em_iter == 0) return GMM_OK;
@@ -305,9 +311,10 @@ gmm_status run_em(gmm_model *m, const float *Xd, int64_t N, int32_t em_iter, dou
         gmm_status prc = prof_begin(m, s, &slot);
         if (prc != GMM_OK) return prc;
         if (tc) CK(gmm::launch_em_pass_tc(pa, m->slab, grid, s));
+        else if (two_phase) CK(gmm::launch_em_two_phase(pa, m->lse, grid, s));
         else CK(gmm::launch_em_pass_simt(pa, grid, s));
         if ((prc = prof_end(m, s, slot)) != GMM_OK) return prc;
-        gmm::EmFinalizeArgs fa{m->partial, m->llp, grid, N, D, G, m->par[(base + k) & 1], m->par[(base + k + 1) & 1],
+        gmm::EmFinalizeArgs fa{m->partial, m->llp, grid, n_llp, N, D, G, m->par[(base + k) & 1], m->par[(base + k + 1) & 1],
                                var_floor, tc ? 1 : 0, m->op, m->center(), m->status, k, em_tol, m->lld,
                                tc ? 1 : (m->has_center && m->center_D == D)};
         CK(gmm::launch_em_finalize(fa, s));
@@ -385,7 +392,7 @@ void gmm_destroy(gmm_model *m)
     for (cudaEvent_t e : m->ev) cudaEventDestroy(e);
     if (m->sstats) cudaFree(m->sstats);
     void *bufs[] = {m->par[0], m->par[1], m->op_sm, m->op_mu, m->op_c, m->op_B, m->gstat, m->fstat,
-                    m->partial, m->slab, m->llp, m->lld, m->counts, m->assign, m->xstage, m->dstage, m->idx,
+                    m->partial, m->slab, m->lse, m->llp, m->lld, m->counts, m->assign, m->xstage, m->dstage, m->idx,
                     m->hist, m->status};
     for (void *p : bufs)
         if (p) cudaFree(p);

@@ -55,7 +55,8 @@ struct EmPassArgs {
 struct EmFinalizeArgs {
     const double *partial;
     const double *ll_partial;
-    int32_t n_partial;
+    int32_t n_partial;       // partials of the statistics
+    int32_t n_ll_partial;    // partials of the log-likelihood
     int64_t N;
     int32_t D, G;
     const double *par_in;    // [G*D means | G*D dcovs | G hefts]
@@ -106,6 +107,8 @@ cudaError_t launch_em_prep(int32_t D, int32_t G, const double *par, Operands op,
                            int32_t build_tc, cudaStream_t s);
 cudaError_t launch_em_pass_simt(const EmPassArgs &a, int32_t grid, cudaStream_t s);
 cudaError_t launch_em_finalize(const EmFinalizeArgs &a, cudaStream_t s);
+int em_slab_width(int32_t D, int32_t G);
+cudaError_t launch_em_two_phase(const EmPassArgs &a, float *lse, int32_t n_chunks, cudaStream_t s);
 cudaError_t launch_log_p(const float *X, int64_t N, int32_t D, int32_t G, Operands op, int32_t g,
                          double *out, cudaStream_t s);
 cudaError_t launch_assign(const float *X, int64_t N, int32_t D, int32_t G, const double *par,

@@ -268,3 +268,56 @@ def test_c2_full_size_log_p_sampled(c2):
     lp = g.log_p(Xd).cpu().numpy()
     idx = np.random.default_rng(0).choice(X.shape[0], 4000, replace=False)
     np.testing.assert_allclose(lp[idx], oracle.log_p(X[idx], m, v, h), rtol=1e-6, atol=1e-5)
+
+
+# ------------------------------------------------------------ large N_G * D
+@pytest.mark.parametrize("shape", [(6000, 128, 300), (8000, 100, 600), (30000, 17, 2500)])
+def test_two_phase_em_matches_oracle(shape):
+    """Shapes whose per-CTA statistics exceed shared memory run the two-phase
+    FP32 form (log-sum-exp pass, then per-Gaussian-slab passes).  Started from
+    k-means (>= 10 samples per Gaussian, as the paper recommends): from unit
+    variances in 100+ dimensions the log-densities reach thousands of nats and
+    FP32 resolves responsibilities only to ~1e-3."""
+    N, D, G = shape
+    X, _, _ = synth.make("c1", N=N, D=D, G=G, seed=7 + G)
+    start = _start(X, G, 3)
+    M, V, H, ll = oracle.em_iterate(X, *start, 2, 1e-10)
+    g = GMM().set_params(*start)
+    g.em_iterate(dev(X), 2, recompute_center=True)
+    assert_params(g.get_params(), (M, V, H), X, min_count=10.0)
+    rtol = 1e-6 if N >= 10 * G else 1e-5
+    np.testing.assert_allclose(g.ll_history(), ll, rtol=rtol)
+
+
+def test_kmeans_multi_slab_exact():
+    """More means than one shared-memory slab holds: the pass walks slabs."""
+    X, _, _ = synth.make("c1", N=5000, D=128, G=300, seed=9)
+    seeds = synth.seeds_subset(X, 300, 4)
+    w, gv = km_weights(X, GMM_MAHA, 1e-10)
+    M, V, H, A = oracle.kmeans(X, seeds, w, gv, 1, 1e-10)
+    _, b1, b2 = oracle.km_assign(X, seeds, w)
+    g = GMM().set_params(seeds, np.ones_like(seeds), np.full(300, 1.0 / 300))
+    a = g.kmeans(dev(X), 1).cpu().numpy()
+    ok = ~near_tie_mask(b1, b2)
+    np.testing.assert_array_equal(a[ok], A[ok])
+
+
+def test_c3_full_size_fp32_properties_and_sampled_log_p():
+    """N=1e7, D=128, N_G=1024 (the precision workload) through learn(): the
+    per-iteration log-likelihood never decreases, hefts sum to one, the floor
+    holds, and sampled per-sample log-densities match the oracle's under the
+    learned parameters."""
+    X, _, _ = synth.make("c3")
+    Xd = dev(X)
+    g = GMM().learn(Xd, 1024, km_iter=2, em_iter=3, seed=1003, var_floor=1e-10)
+    ll = g.ll_history()
+    assert len(ll) == 3 and np.isfinite(ll).all()
+    assert (np.diff(ll) >= -1e-6 * np.abs(ll[1:])).all()
+    m, v, h = g.get_params()
+    assert h.sum() == pytest.approx(1.0, abs=1e-6)   # FP32 responsibility sums over 1e7 samples
+    assert (v >= 1e-10).all()
+    idx = np.random.default_rng(1).choice(X.shape[0], 300, replace=False)
+    lp = g.log_p(Xd).cpu().numpy()[idx]
+    np.testing.assert_allclose(lp, oracle.log_p(X[idx], m, v, h), rtol=1e-5, atol=1e-4)
+    del Xd
+    torch.cuda.empty_cache()
