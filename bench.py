@@ -299,6 +299,8 @@ def run_ours(args):
                       "delta_ll_vs_fp32": (quality[p]["avg_log_p"] - ref_ll) if ref_ll is not None else None}
                   for p in results},
     }
+    if not args.no_batched:
+        line["batched_512"] = run_batched_leg()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, cores, sample = cpu_oracle_rate(X)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
@@ -307,6 +309,31 @@ def run_ours(args):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def run_batched_leg():
+    """Batched form: 512 independent fits (N log-uniform in [1000, 200000],
+    D in {13,39,64}, N_G in {8..128}), k-means(10) + EM(10) each, one call."""
+    import torch
+
+    from paper_1707_09094_gb300 import learn_batched, synth
+    Xs, Gs, units = [], [], 0
+    for j in range(512):
+        X, _, mix = synth.batched_fit(j)
+        Xs.append(torch.from_numpy(X).cuda())
+        Gs.append(mix.means.shape[0])
+        units += X.shape[0] * X.shape[1] * mix.means.shape[0]
+    learn_batched(Xs, Gs, km_iter=10, em_iter=10, seed=40000)     # autotunes this bucket
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    models = learn_batched(Xs, Gs, km_iter=10, em_iter=10, seed=40000)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    n_tot = int(sum(x.shape[0] for x in Xs))
+    return {"fits": 512, "samples": n_tot, "km_iter": 10, "em_iter": 10, "learn_s": dt,
+            "fits_per_s": 512 / dt, "units_per_iter": units,
+            "units_per_s_20_iters": 20 * units / dt,
+            "mean_final_ll": float(np.mean([m.ll_history()[-1] for m in models]))}
 
 
 def base_eval(base, g, Xd):
@@ -323,6 +350,7 @@ def main():
                     help="comma list of E-step forms; the last available one is the headline")
     ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per pass launch, if measured")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 512-fit batched leg")
     args = ap.parse_args()
     args.forms = [f for f in args.forms.split(",") if f]
     if args.impl == "reference":

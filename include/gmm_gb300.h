@@ -147,6 +147,24 @@ gmm_status gmm_kmeans(gmm_model *m, const float *X, int64_t N, int32_t km_iter, 
                       double var_floor, int32_t *assign_out, void *stream);
 
 /*
+ * Batched learn(): n_fits independent fits (their own X, N, D, n_gaus) with
+ * the same km_iter, em_iter, var_floor and opts, run as one CUDA graph whose
+ * data passes are persistent kernels over a work list of (fit, sample chunk)
+ * items (Sec. 2.1's chunks, scheduled largest first across all fits).  Fit f
+ * seeds with random_subset from opts->seed + f; arithmetic is the FP32 form
+ * with FP64 reductions, so each fit matches gmm_learn on its own data.  The
+ * chunk size and CTAs per SM of the EM pass are picked by an autotuner per
+ * shape bucket (timed on the first batch of that bucket; kept in memory and,
+ * if the environment variable GMM_AUTOTUNE_CACHE names a file, there).
+ * Requires 1 <= D <= 64 and 1 <= n_gaus <= min(N, 128) per fit; opts->prec
+ * must be GMM_FP32 and opts->seed_mode GMM_RANDOM_SUBSET.  X[f] may be host
+ * or device memory.  On return models[f] holds fit f's parameters and history.
+ */
+gmm_status gmm_learn_batched(gmm_model *const *models, int32_t n_fits, const float *const *X, const int64_t *N,
+                             const int32_t *D, const int32_t *n_gaus, int32_t km_iter, int32_t em_iter,
+                             double var_floor, const gmm_learn_opts *opts);
+
+/*
  * log_p(X) / log_p(X, g) of Sec. 4.1: out[i] = log p(x_i | lambda) (Eq. 16)
  * for g = -1, or log N(x_i | mu_g, Sigma_g) (Eq. 15, without the heft) for
  * 0 <= g < n_gaus.  out: double [N], host or device.

@@ -223,3 +223,26 @@ class GMM:
         _lib.check(_lib.load().gmm_get_stats(self._h, out.ctypes.data_as(ctypes.c_void_p), cap, ctypes.byref(n)),
                    "gmm_get_stats")
         return out[: n.value].copy()
+
+
+def learn_batched(Xs, n_gaus, km_iter=10, em_iter=10, var_floor=1e-10, dist_mode=GMM_MAHA, seed=0, em_tol=0.0,
+                  print_mode=False):
+    """Batched learn(): one GMM per array/tensor in Xs (fit f seeds from seed + f).
+    n_gaus is an int or a sequence.  Returns the list of fitted GMM objects."""
+    n = len(Xs)
+    gs = list(n_gaus) if hasattr(n_gaus, "__len__") else [int(n_gaus)] * n
+    models = [GMM() for _ in range(n)]
+    keep, ptrs, Ns, Ds = [], [], [], []
+    for X in Xs:
+        p, N, D, k = _as_input(X)
+        keep.append(k); ptrs.append(p.value); Ns.append(N); Ds.append(D)
+    arr = lambda t, v: (t * len(v))(*v)  # noqa: E731
+    o = _lib.gmm_learn_opts()
+    _lib.load().gmm_default_opts(ctypes.byref(o))
+    o.dist, o.seed, o.em_tol, o.print = dist_mode, seed & (2**64 - 1), em_tol, int(print_mode)
+    hs = arr(ctypes.c_void_p, [m._h.value for m in models])
+    _lib.check(_lib.load().gmm_learn_batched(hs, n, arr(ctypes.c_void_p, ptrs), arr(ctypes.c_int64, Ns),
+                                             arr(ctypes.c_int32, Ds), arr(ctypes.c_int32, gs), km_iter, em_iter,
+                                             var_floor, ctypes.byref(o)), "gmm_learn_batched")
+    del keep
+    return models

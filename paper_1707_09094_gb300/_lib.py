@@ -38,6 +38,7 @@ SIGNATURES = {
     "gmm_default_opts": (None, [ctypes.POINTER(gmm_learn_opts)]),
     "gmm_learn": (ctypes.c_int, [P, P, i64, i32, i32, i32, i32, f64, ctypes.POINTER(gmm_learn_opts)]),
     "gmm_em_iterate": (ctypes.c_int, [P, P, i64, i32, f64, i32, i32, P]),
+    "gmm_learn_batched": (ctypes.c_int, [P, i32, P, P, P, P, i32, i32, f64, ctypes.POINTER(gmm_learn_opts)]),
     "gmm_kmeans": (ctypes.c_int, [P, P, i64, i32, i32, f64, P, P]),
     "gmm_log_p": (ctypes.c_int, [P, P, i64, i32, P, P]),
     "gmm_avg_log_p": (ctypes.c_int, [P, P, i64, i32, ctypes.POINTER(f64), P]),

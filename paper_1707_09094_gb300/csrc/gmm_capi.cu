@@ -4,7 +4,13 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
+#include <cstdlib>
 #include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -715,3 +721,342 @@ gmm_status gmm_get_stats(const gmm_model *m, double *ll_hist, int32_t cap, int32
 }
 
 }  // extern "C"
+
+// ============================================================== batched form
+namespace {
+
+// Autotuner of the batched EM pass: per shape bucket (largest D rounded up to
+// 16, largest n_gaus rounded up to a power of two, log2 of the total sample
+// count) the fastest (samples per work item, CTAs per SM) among a fixed set of
+// candidates, timed with CUDA events on the real batch.  Results live in
+// memory and, when GMM_AUTOTUNE_CACHE names a file, are appended to / read
+// from it as lines "bucket chunk per_sm ms".
+std::mutex g_tune_mu;
+std::map<std::string, std::pair<int, int>> g_tune;
+bool g_tune_loaded = false;
+
+std::string tune_bucket(int dmax, int gmax, int64_t ntot)
+{
+    int gq = 1;
+    while (gq < gmax) gq <<= 1;
+    int nq = 0;
+    while ((int64_t(1) << (nq + 1)) <= ntot) ++nq;
+    std::ostringstream o;
+    o << "D" << ((dmax + 15) / 16 * 16) << "_G" << gq << "_N2^" << nq;
+    return o.str();
+}
+
+void tune_load()
+{
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char *path = std::getenv("GMM_AUTOTUNE_CACHE");
+    if (!path) return;
+    std::ifstream f(path);
+    std::string key;
+    int chunk, per_sm;
+    double ms;
+    while (f >> key >> chunk >> per_sm >> ms) g_tune[key] = {chunk, per_sm};
+}
+
+void tune_store(const std::string &key, int chunk, int per_sm, double ms)
+{
+    g_tune[key] = {chunk, per_sm};
+    const char *path = std::getenv("GMM_AUTOTUNE_CACHE");
+    if (!path) return;
+    std::ofstream f(path, std::ios::app);
+    f << key << " " << chunk << " " << per_sm << " " << ms << "\n";
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct BatchHost {
+    std::vector<gmm::BFit> fits;
+    std::vector<gmm::BItem> items;
+    std::vector<int32_t> order;
+    size_t partial_doubles = 0;
+};
+
+// Work items of `chunk` samples, grouped by fit; `order` lists them largest
+// first (the persistent kernels draw items in that order).
+void build_items(BatchHost &h, int chunk)
+{
+    h.items.clear();
+    h.partial_doubles = 0;
+    for (size_t f = 0; f < h.fits.size(); ++f) {
+        gmm::BFit &F = h.fits[f];
+        F.item0 = (int32_t)h.items.size();
+        const size_t pd = (size_t)F.G * (1 + 2 * F.D);
+        for (int64_t i0 = 0; i0 < F.N; i0 += chunk) {
+            gmm::BItem it{};
+            it.fit = (int32_t)f;
+            it.i0 = i0;
+            it.i1 = std::min<int64_t>(F.N, i0 + chunk);
+            it.poff = h.partial_doubles;
+            h.partial_doubles += pd;
+            h.items.push_back(it);
+        }
+        F.n_items = (int32_t)h.items.size() - F.item0;
+    }
+    h.order.resize(h.items.size());
+    for (size_t k = 0; k < h.items.size(); ++k) h.order[k] = (int32_t)k;
+    std::stable_sort(h.order.begin(), h.order.end(), [&](int32_t a, int32_t b) {
+        const gmm::BItem &A = h.items[a], &B = h.items[b];
+        const gmm::BFit &FA = h.fits[A.fit], &FB = h.fits[B.fit];
+        return (double)(A.i1 - A.i0) * FA.G * FA.D > (double)(B.i1 - B.i0) * FB.G * FB.D;
+    });
+}
+
+}  // namespace
+
+extern "C" gmm_status gmm_learn_batched(gmm_model *const *models, int32_t n_fits, const float *const *X,
+                                        const int64_t *N, const int32_t *D, const int32_t *n_gaus, int32_t km_iter,
+                                        int32_t em_iter, double var_floor, const gmm_learn_opts *opts)
+{
+    if (!models || !X || !N || !D || !n_gaus || n_fits < 1) return fail(GMM_ERR_ARG, "bad batch arguments");
+    gmm_learn_opts o;
+    gmm_default_opts(&o);
+    if (opts) o = *opts;
+    if (o.seed_mode != GMM_RANDOM_SUBSET) return fail(GMM_ERR_UNSUPPORTED, "batched learn seeds with random_subset");
+    if (o.prec != GMM_FP32) return fail(GMM_ERR_UNSUPPORTED, "batched learn runs the FP32 form");
+    if (o.dist != GMM_EUCL && o.dist != GMM_MAHA) return fail(GMM_ERR_ARG, "dist must be EUCL or MAHA");
+    if (km_iter < 0 || em_iter < 0 || !(var_floor >= 0.0) || !std::isfinite(var_floor))
+        return fail(GMM_ERR_ARG, "bad km_iter/em_iter/var_floor");
+    int dmax = 1, gmax = 1;
+    int64_t ntot = 0;
+    for (int f = 0; f < n_fits; ++f) {
+        if (!models[f] || !X[f]) return fail(GMM_ERR_ARG, "fit %d: NULL model or X", f);
+        if (D[f] < 1 || D[f] > 64) return fail(GMM_ERR_UNSUPPORTED, "fit %d: batched fits need 1 <= D <= 64", f);
+        if (n_gaus[f] < 1 || n_gaus[f] > 128 || (int64_t)n_gaus[f] > N[f])
+            return fail(GMM_ERR_ARG, "fit %d: need 1 <= n_gaus <= min(N, 128)", f);
+        dmax = std::max(dmax, D[f]);
+        gmax = std::max(gmax, n_gaus[f]);
+        ntot += N[f];
+    }
+    int dev = 0, sms = 0, optin = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    size_t em_sm = 0, km_sm = 0;
+    for (int f = 0; f < n_fits; ++f) {
+        em_sm = std::max(em_sm, gmm::b_em_smem(D[f], n_gaus[f]));
+        km_sm = std::max(km_sm, gmm::b_km_smem(D[f], n_gaus[f]));
+    }
+    const int km_per_sm = km_sm * 2 + 4096 <= (size_t)(228 * 1024) ? 2 : 1;
+    if (em_sm > (size_t)optin || km_sm > (size_t)optin) return fail(GMM_ERR_UNSUPPORTED, "batch shapes exceed shared memory");
+    CK(gmm::b_prepare(em_sm, km_sm));
+
+    // ---- device arena: per-fit buffers, descriptors, seeds, staged X
+    BatchHost h;
+    h.fits.resize(n_fits);
+    std::vector<size_t> off(n_fits);
+    size_t bytes = 0;
+    std::vector<std::vector<int64_t>> seeds(n_fits);
+    std::vector<bool> host_x(n_fits);
+    for (int f = 0; f < n_fits; ++f) {
+        const size_t G = n_gaus[f], Df = D[f], np = 2 * G * Df + G;
+        off[f] = bytes;
+        bytes += align_up(8 * np, 256) * 2 + align_up(8 * G * Df, 256) + align_up(4 * G * Df, 256) +
+                 align_up(4 * G, 256) + align_up(8 * Df, 256) * 2 + align_up(4 * Df, 256) * 2 + align_up(8 * G, 256) +
+                 align_up(4 * (size_t)N[f], 256) + align_up(8 * G, 256) + align_up(8 * (size_t)std::max(em_iter, 1), 256) +
+                 align_up(sizeof(gmm::BFitStatus), 256);
+        host_x[f] = !is_device_ptr(X[f]);
+        if (host_x[f]) bytes += align_up(4 * (size_t)N[f] * Df, 256);
+        seeds[f] = random_subset(N[f], n_gaus[f], o.seed + (uint64_t)f);
+    }
+    unsigned char *arena = nullptr;
+    CK(cudaMalloc(&arena, bytes ? bytes : 1));
+    struct ArenaGuard { unsigned char *p; ~ArenaGuard() { if (p) cudaFree(p); } } guard{arena};
+    cudaStream_t s = nullptr;
+    CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    struct StreamGuard { cudaStream_t s; ~StreamGuard() { if (s) cudaStreamDestroy(s); } } sguard{s};
+    std::vector<gmm::BFitStatus> st0(n_fits);
+    std::vector<int32_t> comp_fit, comp_g;
+    for (int f = 0; f < n_fits; ++f) {
+        const size_t G = n_gaus[f], Df = D[f], np = 2 * G * Df + G;
+        unsigned char *p = arena + off[f];
+        auto take = [&](size_t n) { unsigned char *q = p; p += align_up(n, 256); return q; };
+        gmm::BFit &F = h.fits[f];
+        F.N = N[f];
+        F.D = D[f];
+        F.G = n_gaus[f];
+        F.par = reinterpret_cast<double *>(take(8 * np));
+        F.par2 = reinterpret_cast<double *>(take(8 * np));
+        F.sm = reinterpret_cast<float2 *>(take(8 * G * Df));
+        F.mu = reinterpret_cast<float *>(take(4 * G * Df));
+        F.c = reinterpret_cast<float *>(take(4 * G));
+        F.gvar = reinterpret_cast<double *>(take(8 * Df));
+        F.w = reinterpret_cast<double *>(take(8 * Df));
+        F.sw = reinterpret_cast<float *>(take(4 * Df));
+        F.center = reinterpret_cast<float *>(take(4 * Df));
+        F.counts = reinterpret_cast<double *>(take(8 * G));
+        F.assign = reinterpret_cast<int32_t *>(take(4 * (size_t)N[f]));
+        int64_t *sidx = reinterpret_cast<int64_t *>(take(8 * G));
+        F.seed_idx = sidx;
+        F.ll_hist = reinterpret_cast<double *>(take(8 * (size_t)std::max(em_iter, 1)));
+        F.status = reinterpret_cast<gmm::BFitStatus *>(take(sizeof(gmm::BFitStatus)));
+        if (host_x[f]) {
+            float *xs = reinterpret_cast<float *>(take(4 * (size_t)N[f] * Df));
+            CK(cudaMemcpyAsync(xs, X[f], 4 * (size_t)N[f] * Df, cudaMemcpyHostToDevice, s));
+            F.X = xs;
+        } else {
+            F.X = X[f];
+        }
+        CK(cudaMemcpyAsync(sidx, seeds[f].data(), 8 * G, cudaMemcpyHostToDevice, s));
+        st0[f] = gmm::BFitStatus{0, 0, 0x7fffffff, 0, -1, {0, 0, 0}};
+        for (int g = 0; g < F.G; ++g) { comp_fit.push_back(f); comp_g.push_back(g); }
+    }
+    const int n_comp = (int)comp_fit.size();
+    // descriptors and tables in a second allocation (sized after items are known)
+    gmm::BFit *d_fits = nullptr;
+    int32_t *d_comp = nullptr;
+    int *d_counter = nullptr;
+    CK(cudaMalloc(&d_fits, sizeof(gmm::BFit) * n_fits));
+    struct FreeGuard { void *p; ~FreeGuard() { if (p) cudaFree(p); } } g1{d_fits};
+    CK(cudaMalloc(&d_comp, sizeof(int32_t) * 2 * n_comp));
+    FreeGuard g2{d_comp};
+    CK(cudaMalloc(&d_counter, sizeof(int)));
+    FreeGuard g3{d_counter};
+    CK(cudaMemcpyAsync(d_comp, comp_fit.data(), 4 * n_comp, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(d_comp + n_comp, comp_g.data(), 4 * n_comp, cudaMemcpyHostToDevice, s));
+    gmm::BItem *d_items = nullptr;
+    int32_t *d_order = nullptr;
+    double *d_partial = nullptr, *d_llp = nullptr;
+    size_t cap_items = 0, cap_partial = 0;
+    FreeGuard g4{nullptr}, g5{nullptr}, g6{nullptr}, g7{nullptr};
+    auto upload = [&](int chunk) -> gmm_status {
+        build_items(h, chunk);
+        if (h.items.size() > cap_items) {
+            if (d_items) cudaFree(d_items);
+            if (d_order) cudaFree(d_order);
+            if (d_llp) cudaFree(d_llp);
+            cap_items = h.items.size();
+            CK(cudaMalloc(&d_items, sizeof(gmm::BItem) * cap_items));
+            CK(cudaMalloc(&d_order, sizeof(int32_t) * cap_items));
+            CK(cudaMalloc(&d_llp, sizeof(double) * cap_items));
+            g4.p = d_items; g5.p = d_order; g6.p = d_llp;
+        }
+        if (h.partial_doubles > cap_partial) {
+            if (d_partial) cudaFree(d_partial);
+            cap_partial = h.partial_doubles;
+            CK(cudaMalloc(&d_partial, sizeof(double) * cap_partial));
+            g7.p = d_partial;
+        }
+        CK(cudaMemcpyAsync(d_items, h.items.data(), sizeof(gmm::BItem) * h.items.size(), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(d_order, h.order.data(), sizeof(int32_t) * h.items.size(), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(d_fits, h.fits.data(), sizeof(gmm::BFit) * n_fits, cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));   // host vectors are reused by the next call
+        return GMM_OK;
+    };
+    auto reset_status = [&]() -> gmm_status {
+        for (int f = 0; f < n_fits; ++f)
+            CK(cudaMemcpyAsync(h.fits[f].status, &st0[f], sizeof(gmm::BFitStatus), cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));
+        return GMM_OK;
+    };
+    gmm_status rc;
+
+    // ---- autotune the EM pass for this shape bucket
+    int chunk = 8192, per_sm = 1;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        tune_load();
+        const std::string key = tune_bucket(dmax, gmax, ntot);
+        auto hit = g_tune.find(key);
+        if (hit != g_tune.end()) {
+            chunk = hit->second.first;
+            per_sm = hit->second.second;
+        } else if (em_iter > 0) {
+            if ((rc = upload(8192)) != GMM_OK) return rc;
+            if ((rc = reset_status()) != GMM_OK) return rc;
+            CK(gmm::launch_b_gstats(d_fits, n_fits, var_floor, o.dist, s));
+            CK(gmm::launch_b_seed(d_fits, d_comp, d_comp + n_comp, n_comp, s));
+            CK(gmm::launch_b_em_prep(d_fits, d_comp, d_comp + n_comp, n_comp, s));
+            cudaEvent_t e0, e1;
+            CK(cudaEventCreate(&e0));
+            CK(cudaEventCreate(&e1));
+            double best = 1e300;
+            const int chunks[3] = {2048, 8192, 32768};
+            for (int ci = 0; ci < 3; ++ci)
+                for (int ps = 1; ps <= 2; ++ps) {
+                    if (ps == 2 && em_sm * 2 + 4096 > (size_t)(228 * 1024)) continue;
+                    if ((rc = upload(chunks[ci])) != GMM_OK) return rc;
+                    float ms = 0.f, tot = 0.f;
+                    for (int rep = 0; rep < 2; ++rep) {
+                        CK(cudaEventRecord(e0, s));
+                        CK(gmm::launch_b_em_pass(d_fits, d_items, d_order, (int)h.items.size(), d_counter, d_partial,
+                                                 d_llp, em_sm, sms * ps, 0, s));
+                        CK(cudaEventRecord(e1, s));
+                        CK(cudaEventSynchronize(e1));
+                        CK(cudaEventElapsedTime(&ms, e0, e1));
+                        if (rep) tot += ms;
+                    }
+                    if (tot < best) { best = tot; chunk = chunks[ci]; per_sm = ps; }
+                }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            tune_store(key, chunk, per_sm, best);
+        }
+    }
+
+    // ---- the whole fit as one CUDA graph
+    if ((rc = upload(chunk)) != GMM_OK) return rc;
+    if ((rc = reset_status()) != GMM_OK) return rc;
+    const int n_items = (int)h.items.size();
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    cudaError_t ce = cudaSuccess;
+    auto cap = [&](cudaError_t e) { if (ce == cudaSuccess) ce = e; };
+    cap(gmm::launch_b_gstats(d_fits, n_fits, var_floor, o.dist, s));
+    cap(gmm::launch_b_seed(d_fits, d_comp, d_comp + n_comp, n_comp, s));
+    for (int it = 0; it < km_iter; ++it)
+        cap(gmm::launch_b_km_iter(d_fits, n_fits, d_comp, d_comp + n_comp, n_comp, d_items, d_order, n_items,
+                                  d_counter, d_partial, km_sm, sms * km_per_sm, var_floor, it == km_iter - 1, s));
+    cap(gmm::launch_b_em_prep(d_fits, d_comp, d_comp + n_comp, n_comp, s));
+    for (int it = 0; it < em_iter; ++it) {
+        cap(gmm::launch_b_em_pass(d_fits, d_items, d_order, n_items, d_counter, d_partial, d_llp, em_sm, sms * per_sm,
+                                  it, s));
+        cap(gmm::launch_b_em_finish(d_fits, n_fits, d_comp, d_comp + n_comp, n_comp, d_items, d_partial, d_llp,
+                                    var_floor, o.em_tol, it, s));
+    }
+    cudaError_t ee = cudaStreamEndCapture(s, &graph);
+    if (ce != cudaSuccess) { if (graph) cudaGraphDestroy(graph); CK(ce); }
+    CK(ee);
+    struct GraphGuard { cudaGraph_t g; cudaGraphExec_t x; ~GraphGuard() { if (x) cudaGraphExecDestroy(x); if (g) cudaGraphDestroy(g); } } gg{graph, nullptr};
+    CK(cudaGraphInstantiate(&exec, graph, 0));
+    gg.x = exec;
+    CK(cudaGraphLaunch(exec, s));
+    CK(cudaStreamSynchronize(s));
+
+    // ---- results into the models
+    std::vector<gmm::BFitStatus> st(n_fits);
+    int32_t first_bad = -1;
+    for (int f = 0; f < n_fits; ++f) {
+        CK(cudaMemcpy(&st[f], h.fits[f].status, sizeof(gmm::BFitStatus), cudaMemcpyDeviceToHost));
+        gmm_model *m = models[f];
+        const gmm::BFit &F = h.fits[f];
+        if ((rc = ensure_shape(m, F.D, F.G)) != GMM_OK) return rc;
+        int done = st[f].code ? std::max(st[f].fail_iter, 0) : st[f].n_done;
+        const double *src = (done & 1) ? F.par2 : F.par;
+        const size_t np = 2 * (size_t)F.G * F.D + F.G;
+        CK(cudaMemcpy(m->par[0], src, 8 * np, cudaMemcpyDeviceToDevice));
+        m->cur = 0;
+        m->has_params = true;
+        m->ops_valid = false;
+        m->has_center = false;
+        std::vector<double> ll(std::max(st[f].n_done, 0));
+        if (!ll.empty()) CK(cudaMemcpy(ll.data(), F.ll_hist, 8 * ll.size(), cudaMemcpyDeviceToHost));
+        m->ll_hist = ll;
+        if (st[f].code && first_bad < 0) first_bad = f;
+        if (o.print)
+            for (size_t k = 0; k < ll.size(); ++k)
+                fprintf(stderr, "gmm: fit %d EM iteration %zu: mean log-likelihood %.10g\n", f, k + 1, ll[k]);
+    }
+    for (int f = 0; f < n_fits; ++f)
+        if ((rc = run_prep(models[f], nullptr)) != GMM_OK) return rc;
+    CK(cudaDeviceSynchronize());
+    if (first_bad >= 0)
+        return fail((gmm_status)st[first_bad].code, "fit %d failed at EM iteration %d", first_bad, st[first_bad].fail_iter);
+    return GMM_OK;
+}

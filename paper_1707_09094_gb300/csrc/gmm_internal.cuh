@@ -126,6 +126,49 @@ int km_grid(int32_t D, int32_t G, int sms);
 size_t em_simt_smem(int32_t D, int32_t G);
 bool em_simt_supported(int32_t D, int32_t G);
 
+// ---- batched form (gmm_batched.cu)
+struct BFitStatus {
+    int32_t code, halt, stop_after, n_done, fail_iter, pad[3];
+};
+
+struct BFit {
+    const float *X;
+    int64_t N;
+    int32_t D, G;
+    double *par, *par2;        // ping-pong [G*D means | G*D dcovs | G hefts]
+    float2 *sm;                // E-step operands
+    float *mu, *c;
+    double *gvar, *w;          // floored global variance, distance weights
+    float *sw, *center;
+    double *counts;
+    int32_t *assign;
+    const int64_t *seed_idx;
+    double *ll_hist;           // [em_iter]
+    BFitStatus *status;
+    int32_t item0, n_items;    // this fit's items are item0 .. item0+n_items-1
+};
+
+struct BItem {
+    int32_t fit, pad;
+    int64_t i0, i1;            // sample range of the item
+    size_t poff;               // offset of its FP64 partial [G][1+2D]
+};
+
+size_t b_em_smem(int D, int G);
+cudaError_t b_prepare(size_t em_smem, size_t km_smem);
+size_t b_km_smem(int D, int G);
+cudaError_t launch_b_gstats(BFit *fits, int n_fits, double var_floor, int dist, cudaStream_t s);
+cudaError_t launch_b_seed(BFit *fits, const int32_t *comp_fit, const int32_t *comp_g, int n_comp, cudaStream_t s);
+cudaError_t launch_b_km_iter(BFit *fits, int n_fits, const int32_t *comp_fit, const int32_t *comp_g, int n_comp,
+                             const BItem *items, const int32_t *order, int n_items, int *counter, double *partial,
+                             size_t smem, int grid, double var_floor, int final_iter, cudaStream_t s);
+cudaError_t launch_b_em_prep(BFit *fits, const int32_t *comp_fit, const int32_t *comp_g, int n_comp, cudaStream_t s);
+cudaError_t launch_b_em_pass(BFit *fits, const BItem *items, const int32_t *order, int n_items, int *counter,
+                             double *partial, double *llp, size_t smem, int grid, int iter, cudaStream_t s);
+cudaError_t launch_b_em_finish(BFit *fits, int n_fits, const int32_t *comp_fit, const int32_t *comp_g, int n_comp,
+                               const BItem *items, const double *partial, const double *llp, double var_floor,
+                               double em_tol, int iter, cudaStream_t s);
+
 // ---- launchers implemented in gmm_em_tc.cu
 bool em_tc_supported(int32_t D, int32_t G);
 int em_tc_grid(int sms);
