@@ -127,6 +127,22 @@ def cpu_oracle_rate(X, target_s: float = 12.0):
                               "threads, %.2f s" % (n, X.shape[0], X.shape[1], G, cores, dt)
 
 
+def max_over_ranks(ms: float, world: int, device: str) -> float:
+    """Slowest rank's time (the job ends when the last replica ends)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, ms_per_step: float) -> float:
+    """Units all replicas processed per second (each rank runs the whole workload)."""
+    return world * units_per_rank / (ms_per_step * 1e-3)
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -216,11 +232,7 @@ def run_ours(args):
             ev1.record(stream)
             torch.cuda.synchronize()
             wall = time.perf_counter() - t0
-        ms = ev0.elapsed_time(ev1)
-        if world > 1:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ev0.elapsed_time(ev1), world, "cuda")
         pass_ms, pass_n, launches = g.profile_read()
         g.profile(False)
         return {"ms": ms, "wall_s": wall, "pass_ms": pass_ms, "pass_n": pass_n, "launches": launches,
@@ -254,7 +266,7 @@ def run_ours(args):
     r = results[head]
     e2e = time_form(head, host_input=True)
     step_ms = r["ms"] / args.steps
-    value = world * units / (step_ms * 1e-3)
+    value = whole_job_rate(units, world, step_ms)
 
     peaks, peak_src = _peaks()
     pass_ms = r["pass_ms"] / max(r["pass_n"], 1)
@@ -301,6 +313,8 @@ def run_ours(args):
     }
     if not args.no_batched:
         line["batched_512"] = run_batched_leg()
+    if not args.no_init_net:
+        line["init_net"] = run_init_net_leg(peaks, peak_src)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, cores, sample = cpu_oracle_rate(X)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
@@ -336,6 +350,44 @@ def run_batched_leg():
             "mean_final_ll": float(np.mean([m.ll_history()[-1] for m in models]))}
 
 
+def run_init_net_leg(peaks, peak_src, B=16, P=4096, steps=10, warmup=3):
+    """Learned initialiser: Adam training steps of the set encoder at
+    D=32, N_G=32 (per point 32-256-256-256, mean pool, 256-512-512-512-2080),
+    B sets of P points per step, on synthetic sets with synthetic targets."""
+    import torch
+
+    from paper_1707_09094_gb300 import InitNet
+    D, G, Hp, Hh, Lp, Lh = 32, 32, 256, 512, 3, 3
+    net = InitNet(D, G, Hp, Hh, Lp, Lh, seed=0)
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    pts = torch.randn((B, P, D), device="cuda", generator=gen) * 2.0
+    tgt = (torch.randn((B, G, D), device="cuda", generator=gen, dtype=torch.float64),
+           torch.rand((B, G, D), device="cuda", generator=gen, dtype=torch.float64) + 0.5,
+           torch.full((B, G), 1.0 / G, device="cuda", dtype=torch.float64))
+    for _ in range(warmup):
+        net.step(pts, tgt, lam=0.1, mode=2)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(steps):
+        net.step(pts, tgt, lam=0.1, mode=2)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / steps
+    # algorithmic GEMM flops: forward, input-gradient and weight-gradient
+    # products of every layer (3 x 2 x MACs); point layers per point, head per set
+    point_mac = D * Hp + (Lp - 1) * Hp * Hp
+    head_mac = Hp * Hh + (Lh - 1) * Hh * Hh + Hh * G * (1 + 2 * D)
+    flops = 6.0 * (B * P * point_mac + B * head_mac)
+    achieved = flops / (ms * 1e-3) / 1e12
+    return {"sets": B, "points_per_set": P, "ms_per_step": ms, "sets_per_s": B / (ms * 1e-3),
+            "points_per_s": B * P / (ms * 1e-3),
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                         "frac": achieved / peaks["bf16_tflops"], "peak_source": "bf16_tflops (%s)" % peak_src,
+                         "flops_per_step": flops}}
+
+
 def base_eval(base, g, Xd):
     return g.avg_log_p(Xd)
 
@@ -351,6 +403,7 @@ def main():
     ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per pass launch, if measured")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-fit batched leg")
+    ap.add_argument("--no-init-net", action="store_true", help="skip the learned-initialiser training leg")
     args = ap.parse_args()
     args.forms = [f for f in args.forms.split(",") if f]
     if args.impl == "reference":

@@ -218,6 +218,49 @@ gmm_status gmm_raw_hist(const gmm_model *m, const float *X, int64_t N, int32_t m
 gmm_status gmm_norm_hist(const gmm_model *m, const float *X, int64_t N, int32_t mode,
                          double *hist, void *stream);
 
+/*
+ * Learned initialiser (a set encoder trained on the plain method's fits).
+ * Network: per point D -> point_layers x hidden_point (ReLU), mean-pool over
+ * the P points, head_layers x hidden_head (ReLU), linear to n_gaus (1 + 2D)
+ * outputs: softmax -> hefts, means, exp(.) + var_floor -> dcovs.  All
+ * products run in BF16 with FP32 accumulation (FP32 master weights, Adam).
+ * Loss of a set: the mean negative log-likelihood of its points under the
+ * predicted mixture (Eqs. 1, 16), plus lambda * sum_k w~_k min_g
+ * sum_d (m_gd - m~_kd)^2 / v~_kd pulling the predicted means to the plain
+ * method's fit (w~, m~, v~) when targets are given.
+ */
+typedef struct gmm_init_net gmm_init_net;
+
+/* D <= 64, n_gaus <= 64; weights drawn from SplitMix64(seed). */
+gmm_status gmm_init_net_create(gmm_init_net **out, int32_t D, int32_t n_gaus, int32_t hidden_point,
+                               int32_t hidden_head, int32_t point_layers, int32_t head_layers, uint64_t seed);
+void gmm_init_net_destroy(gmm_init_net *n);
+int64_t gmm_init_net_num_params(const gmm_init_net *n);
+
+/* Copy the FP32 weights and/or the last gradients to host arrays (NULL = skip);
+ * layout: per layer W [out][in] then b [out], layers in order. */
+gmm_status gmm_init_net_get_weights(const gmm_init_net *n, float *weights, float *grads);
+gmm_status gmm_init_net_set_weights(gmm_init_net *n, const float *weights);
+
+/*
+ * One pass over a batch of B sets of P points (pts: device float [B][P][D]).
+ * mode 0: forward + loss; 1: also gradients; 2: also one Adam step (lr).
+ * Targets (device double [B][n_gaus][D], [B][n_gaus][D], [B][n_gaus]) are
+ * needed when lambda > 0.  pred_* (device, may be NULL) receive the predicted
+ * parameters; *loss (host) the batch-mean loss.
+ */
+gmm_status gmm_init_net_step(gmm_init_net *n, const float *pts, int32_t B, int32_t P, const double *tgt_means,
+                             const double *tgt_dcovs, const double *tgt_hefts, double lambda, double var_floor,
+                             int32_t mode, double lr, double *pred_means, double *pred_dcovs, double *pred_hefts,
+                             double *loss, void *stream);
+
+/* Seed model m for EM from P random samples of X (SplitMix64(seed) subset):
+ * the network's predicted hefts, means and dcovs become m's parameters.
+ * GMM_ERR_NONFINITE if the prediction is not finite (callers fall back to
+ * k-means seeding). */
+gmm_status gmm_init_net_seed_model(const gmm_init_net *n, gmm_model *m, const float *X, int64_t N, int32_t P,
+                                   uint64_t seed, double var_floor, void *stream);
+
 /* Read the parameters (host pointers; any may be NULL).  D / n_gaus receive
  * the shape.  GMM_ERR_STATE if the model has none. */
 gmm_status gmm_get_params(const gmm_model *m, int32_t *D, int32_t *n_gaus, double *means,

@@ -246,3 +246,66 @@ def learn_batched(Xs, n_gaus, km_iter=10, em_iter=10, var_floor=1e-10, dist_mode
                                              var_floor, ctypes.byref(o)), "gmm_learn_batched")
     del keep
     return models
+
+
+class InitNet:
+    """Learned initialiser (set encoder) on the GPU; see gmm_init_net_* in the C header."""
+
+    def __init__(self, D=32, n_gaus=32, hidden_point=256, hidden_head=512, point_layers=3, head_layers=3, seed=0):
+        h = ctypes.c_void_p()
+        _lib.check(_lib.load().gmm_init_net_create(ctypes.byref(h), D, n_gaus, hidden_point, hidden_head,
+                                                   point_layers, head_layers, seed & (2**64 - 1)),
+                   "gmm_init_net_create")
+        self._h, self.D, self.n_gaus = h, D, n_gaus
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            _lib.load().gmm_init_net_destroy(h)
+            self._h = None
+
+    @property
+    def num_params(self):
+        return int(_lib.load().gmm_init_net_num_params(self._h))
+
+    def get_weights(self):
+        w = np.empty(self.num_params, np.float32)
+        _lib.check(_lib.load().gmm_init_net_get_weights(self._h, w.ctypes.data_as(ctypes.c_void_p), None), "get")
+        return w
+
+    def get_grads(self):
+        g = np.empty(self.num_params, np.float32)
+        _lib.check(_lib.load().gmm_init_net_get_weights(self._h, None, g.ctypes.data_as(ctypes.c_void_p)), "get")
+        return g
+
+    def set_weights(self, w):
+        w = np.ascontiguousarray(w, np.float32)
+        _lib.check(_lib.load().gmm_init_net_set_weights(self._h, w.ctypes.data_as(ctypes.c_void_p)), "set")
+        return self
+
+    def step(self, pts, targets=None, lam=0.0, var_floor=1e-3, mode=0, lr=1e-3, want_pred=False):
+        """pts: CUDA float32 tensor [B][P][D]; targets: (means, dcovs, hefts) CUDA float64 tensors or None.
+        Returns (loss, pred) with pred = (means, dcovs, hefts) CUDA tensors when want_pred."""
+        torch = _torch()
+        B, P, D = pts.shape
+        tp = [ctypes.c_void_p(0)] * 3 if targets is None else [ctypes.c_void_p(t.data_ptr()) for t in targets]
+        pred = None
+        pp = [ctypes.c_void_p(0)] * 3
+        if want_pred:
+            G = self.n_gaus
+            pred = (torch.empty((B, G, D), dtype=torch.float64, device=pts.device),
+                    torch.empty((B, G, D), dtype=torch.float64, device=pts.device),
+                    torch.empty((B, G), dtype=torch.float64, device=pts.device))
+            pp = [ctypes.c_void_p(t.data_ptr()) for t in pred]
+        loss = ctypes.c_double()
+        _lib.check(_lib.load().gmm_init_net_step(self._h, ctypes.c_void_p(pts.data_ptr()), B, P, tp[0], tp[1], tp[2],
+                                                 lam, var_floor, mode, lr, pp[0], pp[1], pp[2], ctypes.byref(loss),
+                                                 _stream_ptr(pts)), "gmm_init_net_step")
+        return loss.value, pred
+
+    def seed_model(self, model, X, P=4096, seed=0, var_floor=1e-3):
+        ptr, N, D, keep = _as_input(X)
+        _lib.check(_lib.load().gmm_init_net_seed_model(self._h, model._h, ptr, N, P, seed & (2**64 - 1), var_floor,
+                                                       _stream_ptr(X)), "gmm_init_net_seed_model")
+        del keep
+        return model

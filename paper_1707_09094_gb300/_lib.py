@@ -53,6 +53,14 @@ SIGNATURES = {
     "gmm_profile_read": (ctypes.c_int, [P, ctypes.POINTER(f64), ctypes.POINTER(i64), ctypes.POINTER(i64)]),
     "gmm_debug_set": (ctypes.c_int, [P, i32, i64]),
     "gmm_debug_get": (ctypes.c_int, [P, i32, ctypes.POINTER(i64)]),
+    "gmm_init_net_create": (ctypes.c_int, [ctypes.POINTER(P), i32, i32, i32, i32, i32, i32, ctypes.c_uint64]),
+    "gmm_init_net_destroy": (None, [P]),
+    "gmm_init_net_num_params": (i64, [P]),
+    "gmm_init_net_get_weights": (ctypes.c_int, [P, P, P]),
+    "gmm_init_net_set_weights": (ctypes.c_int, [P, P]),
+    "gmm_init_net_step": (ctypes.c_int, [P, P, i32, i32, P, P, P, f64, f64, i32, f64, P, P, P,
+                                         ctypes.POINTER(f64), P]),
+    "gmm_init_net_seed_model": (ctypes.c_int, [P, P, P, i64, i32, ctypes.c_uint64, f64, P]),
     "gmm_last_error": (ctypes.c_char_p, []),
 }
 

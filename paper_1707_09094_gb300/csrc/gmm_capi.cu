@@ -1060,3 +1060,99 @@ extern "C" gmm_status gmm_learn_batched(gmm_model *const *models, int32_t n_fits
         return fail((gmm_status)st[first_bad].code, "fit %d failed at EM iteration %d", first_bad, st[first_bad].fail_iter);
     return GMM_OK;
 }
+
+// ============================================================== learned initialiser
+struct gmm_init_net {
+    gmm::InitNet *net;
+};
+
+extern "C" gmm_status gmm_init_net_create(gmm_init_net **out, int32_t D, int32_t n_gaus, int32_t hidden_point,
+                                          int32_t hidden_head, int32_t point_layers, int32_t head_layers, uint64_t seed)
+{
+    if (!out) return fail(GMM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (D < 1 || D > 64 || n_gaus < 1 || n_gaus > 64 || hidden_point < 1 || hidden_head < 1 || point_layers < 1 ||
+        head_layers < 0)
+        return fail(GMM_ERR_ARG, "bad network shape");
+    cudaError_t e = cudaSuccess;
+    gmm::InitNet *n = gmm::init_net_new(D, n_gaus, hidden_point, hidden_head, point_layers, head_layers, seed, &e);
+    if (e != cudaSuccess) {
+        gmm::init_net_free(n);
+        return fail(GMM_ERR_CUDA, "network allocation failed: %s", cudaGetErrorString(e));
+    }
+    *out = new gmm_init_net{n};
+    return GMM_OK;
+}
+
+extern "C" void gmm_init_net_destroy(gmm_init_net *n)
+{
+    if (!n) return;
+    gmm::init_net_free(n->net);
+    delete n;
+}
+
+extern "C" int64_t gmm_init_net_num_params(const gmm_init_net *n) { return n ? gmm::init_net_n_params(n->net) : 0; }
+
+extern "C" gmm_status gmm_init_net_get_weights(const gmm_init_net *n, float *weights, float *grads)
+{
+    if (!n) return fail(GMM_ERR_ARG, "net is NULL");
+    CK(gmm::init_net_get(n->net, weights, grads));
+    return GMM_OK;
+}
+
+extern "C" gmm_status gmm_init_net_set_weights(gmm_init_net *n, const float *weights)
+{
+    if (!n || !weights) return fail(GMM_ERR_ARG, "NULL argument");
+    CK(gmm::init_net_set_weights(n->net, weights));
+    CK(cudaDeviceSynchronize());
+    return GMM_OK;
+}
+
+extern "C" gmm_status gmm_init_net_step(gmm_init_net *n, const float *pts, int32_t B, int32_t P, const double *tgt_means,
+                                        const double *tgt_dcovs, const double *tgt_hefts, double lambda,
+                                        double var_floor, int32_t mode, double lr, double *pred_means,
+                                        double *pred_dcovs, double *pred_hefts, double *loss, void *stream)
+{
+    if (!n || !pts) return fail(GMM_ERR_ARG, "NULL argument");
+    if (B < 1 || P < 1 || mode < 0 || mode > 2) return fail(GMM_ERR_ARG, "bad B/P/mode");
+    if (!is_device_ptr(pts)) return fail(GMM_ERR_ARG, "pts must be device memory");
+    if (lambda > 0.0 && !(tgt_means && tgt_dcovs && tgt_hefts)) return fail(GMM_ERR_ARG, "lambda > 0 needs targets");
+    if (!(var_floor > 0.0)) return fail(GMM_ERR_ARG, "var_floor must be > 0");
+    CK(gmm::init_net_run(n->net, pts, B, P, tgt_means, tgt_dcovs, tgt_hefts, lambda, var_floor, mode >= 1,
+                         mode == 2 ? lr : 0.0, pred_means, pred_dcovs, pred_hefts, loss, as_stream(stream)));
+    return GMM_OK;
+}
+
+extern "C" gmm_status gmm_init_net_seed_model(const gmm_init_net *nc, gmm_model *m, const float *X, int64_t N, int32_t P,
+                                              uint64_t seed, double var_floor, void *stream)
+{
+    if (!nc || !m || !X) return fail(GMM_ERR_ARG, "NULL argument");
+    gmm::InitNet *n = nc->net;
+    const int D = gmm::init_net_D(n), G = gmm::init_net_G(n);
+    if (N < P || P < 1) return fail(GMM_ERR_ARG, "need 1 <= P <= N");
+    cudaStream_t s = as_stream(stream);
+    gmm_status rc = ensure_shape(m, D, G);
+    if (rc != GMM_OK) return rc;
+    const float *Xd = nullptr;
+    if ((rc = stage_x(m, X, N, D, s, &Xd)) != GMM_OK) return rc;
+    std::vector<int64_t> idx = random_subset(N, P, seed);
+    int64_t *d_idx = nullptr;
+    float *d_pts = nullptr;
+    double *d_par = nullptr;
+    CK(cudaMalloc(&d_idx, 8 * (size_t)P));
+    struct F { void *p; ~F() { if (p) cudaFree(p); } } f1{d_idx};
+    CK(cudaMalloc(&d_pts, 4 * (size_t)P * D));
+    F f2{d_pts};
+    CK(cudaMalloc(&d_par, 8 * (2 * (size_t)G * D + G)));
+    F f3{d_par};
+    CK(cudaMemcpyAsync(d_idx, idx.data(), 8 * (size_t)P, cudaMemcpyHostToDevice, s));
+    CK(gmm::init_net_gather(Xd, D, d_idx, P, d_pts, s));
+    double loss = 0.0;
+    CK(gmm::init_net_run(n, d_pts, 1, P, nullptr, nullptr, nullptr, 0.0, var_floor, 0, 0.0, d_par,
+                         d_par + (size_t)G * D, d_par + 2 * (size_t)G * D, &loss, s));
+    std::vector<double> h(2 * (size_t)G * D + G);
+    CK(cudaMemcpy(h.data(), d_par, 8 * h.size(), cudaMemcpyDeviceToHost));
+    for (double v : h)
+        if (!std::isfinite(v)) return fail(GMM_ERR_NONFINITE, "the network produced non-finite parameters");
+    return gmm_set_params(m, D, G, h.data(), h.data() + (size_t)G * D, h.data() + 2 * (size_t)G * D);
+}

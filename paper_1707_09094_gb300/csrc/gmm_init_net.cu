@@ -1,0 +1,608 @@
+// Learned initialiser: a set encoder that maps a sample subset of a dataset
+// to the starting hefts, means and variances of EM (in place of k-means
+// seeding, which stays the fallback).  Network (row vectors, ReLU):
+//   per point  x (D) -> Lp layers of width Hp           (weights W_l [out][in])
+//   pool       mean over the P points of the last per-point activations
+//   head       Lh layers of width Hh, then a linear layer to G (1 + 2D) outputs
+//   outputs    a (G) -> hefts = softmax(a); m (G x D) -> means;
+//              r (G x D) -> variances exp(r) + var_floor
+// Loss per set (mean over the batch):
+//   NLL  = -(1/P) sum_p log sum_g w_g N(x_p | m_g, v_g)           (Eqs. 1, 16)
+//   PULL = lambda sum_k w~_k min_g sum_d (m_gd - m~_kd)^2 / v~_kd
+// where (w~, m~, v~) is the k-means + EM fit of the plain method on the set.
+// The NLL gradient is the EM statistics of the predicted mixture: with
+// responsibilities l_{g,p} (Eq. 3),
+//   dNLL/da_g  = w_g - (1/P) sum_p l_{g,p}
+//   dNLL/dm_gd = -(1/P) sum_p l_{g,p} (x_pd - m_gd) / v_gd
+//   dNLL/dr_gd = -(1/2P) sum_p l_{g,p} ((x_pd - m_gd)^2 / v_gd - 1) exp(r_gd) / v_gd.
+// Kernels: a tiled BF16 GEMM with FP32 accumulation (optionally transposed
+// operands and split-K), bias + ReLU to BF16, ReLU backward, column sums,
+// pooling, the loss/gradient kernel and Adam.  FP32 master weights, BF16
+// copies feed the GEMMs.
+#include <cmath>
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "gmm_internal.cuh"
+
+namespace gmm {
+
+namespace {
+
+constexpr int kBM = 64, kBN = 64, kBK = 16;
+
+// C[M][N] (FP32, row stride ldc) (+)= sum_k opA(m,k) opB(n,k).
+// opA(m,k) = tA ? A[k*lda + m] : A[m*lda + k];  opB(n,k) = tB ? B[k*ldb + n] : B[n*ldb + k].
+// gridDim.z splits K; with splits > 1 (or accumulate) the tile is added with atomics.
+__global__ void __launch_bounds__(256) k_gemm_bf16(const __nv_bfloat16 *__restrict__ A, const __nv_bfloat16 *__restrict__ B,
+                                                   float *__restrict__ C, int M, int N, int K, int lda, int ldb, int ldc,
+                                                   int tA, int tB, int atomic)
+{
+    __shared__ float As[kBK][kBM + 4];
+    __shared__ float Bs[kBK][kBN + 4];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
+    const int ks = (K + gridDim.z - 1) / gridDim.z;
+    const int kbeg = blockIdx.z * ks, kend = min(K, kbeg + ks);
+    float acc[4][4] = {};
+    for (int k0 = kbeg; k0 < kend; k0 += kBK) {
+        for (int e = threadIdx.x; e < kBK * kBM; e += 256) {
+            int kk, mm;
+            if (tA) { mm = e % kBM; kk = e / kBM; } else { kk = e % kBK; mm = e / kBK; }
+            const int m = m0 + mm, k = k0 + kk;
+            float v = 0.f;
+            if (m < M && k < kend) v = __bfloat162float(tA ? A[(size_t)k * lda + m] : A[(size_t)m * lda + k]);
+            As[kk][mm] = v;
+        }
+        for (int e = threadIdx.x; e < kBK * kBN; e += 256) {
+            int kk, nn;
+            if (tB) { nn = e % kBN; kk = e / kBN; } else { kk = e % kBK; nn = e / kBK; }
+            const int n = n0 + nn, k = k0 + kk;
+            float v = 0.f;
+            if (n < N && k < kend) v = __bfloat162float(tB ? B[(size_t)k * ldb + n] : B[(size_t)n * ldb + k]);
+            Bs[kk][nn] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < kBK; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
+            if (m < M && n < N) {
+                if (atomic) atomicAdd(&C[(size_t)m * ldc + n], acc[i][j]);
+                else C[(size_t)m * ldc + n] = acc[i][j];
+            }
+        }
+}
+
+// out = act(Z + bias) in BF16 (relu != 0) ; also FP32 copy if zf != NULL
+__global__ void k_bias_act(const float *__restrict__ Z, const float *__restrict__ bias, __nv_bfloat16 *__restrict__ out,
+                           float *__restrict__ zf, int64_t M, int N, int relu)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= M * N) return;
+    float v = Z[e] + bias[e % N];
+    if (relu) v = fmaxf(v, 0.f);
+    out[e] = __float2bfloat16_rn(v);
+    if (zf) zf[e] = v;
+}
+
+// dZ = dH * (H > 0) (ReLU backward through the stored BF16 activation); with
+// pool != 0, dH[m][n] = dpool[m / P][n] / P (mean-pool backward).
+__global__ void k_relu_bwd(const float *__restrict__ dH, const __nv_bfloat16 *__restrict__ H, __nv_bfloat16 *__restrict__ dZ,
+                           int64_t M, int N, int pool_P)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= M * N) return;
+    float g;
+    if (pool_P > 0) {
+        const int64_t m = e / N;
+        g = dH[(m / pool_P) * N + e % N] / (float)pool_P;
+    } else {
+        g = dH[e];
+    }
+    dZ[e] = __float2bfloat16_rn(__bfloat162float(H[e]) > 0.f ? g : 0.f);
+}
+
+// db[n] += sum_m dZ[m][n]
+__global__ void k_colsum(const __nv_bfloat16 *__restrict__ dZ, float *__restrict__ db, int64_t M, int N)
+{
+    const int n = blockIdx.x * 32 + (threadIdx.x & 31);
+    if (n >= N) return;
+    float s = 0.f;
+    for (int64_t m = threadIdx.x >> 5; m < M; m += blockDim.x >> 5) s += __bfloat162float(dZ[m * N + n]);
+    atomicAdd(&db[n], s);
+}
+
+// pooled[b][n] = mean over p of H[b*P + p][n]; also a BF16 copy
+__global__ void k_pool(const __nv_bfloat16 *__restrict__ H, float *__restrict__ pooled, __nv_bfloat16 *__restrict__ pooled_bf,
+                       int P, int N)
+{
+    const int b = blockIdx.y, n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    float s = 0.f;
+    for (int p = 0; p < P; ++p) s += __bfloat162float(H[((size_t)b * P + p) * N + n]);
+    s /= (float)P;
+    pooled[(size_t)b * N + n] = s;
+    pooled_bf[(size_t)b * N + n] = __float2bfloat16_rn(s);
+}
+
+__device__ __forceinline__ float bsum_f(float v, float *sh)
+{
+    const int t = threadIdx.x;
+    sh[t] = v;
+    __syncthreads();
+    for (int s = blockDim.x >> 1; s > 0; s >>= 1) {
+        if (t < s) sh[t] += sh[t + s];
+        __syncthreads();
+    }
+    const float r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// One block per set: predicted mixture from the network output, the loss and
+// its gradient with respect to the output (d_out), and the parameters.
+// Shared memory: w, m, v, logv-exp, stats S0 [G], S1 [G][D], S2 [G][D].
+__global__ void __launch_bounds__(256) k_set_loss(const float *__restrict__ out, const float *__restrict__ pts, int P, int D,
+                                                  int G, double var_floor, const double *__restrict__ tgt_m,
+                                                  const double *__restrict__ tgt_v, const double *__restrict__ tgt_w,
+                                                  double lambda, float *__restrict__ d_out, float *__restrict__ loss,
+                                                  double *__restrict__ pm, double *__restrict__ pv, double *__restrict__ pw,
+                                                  int B)
+{
+    extern __shared__ float ls[];
+    const int b = blockIdx.x, O = G * (1 + 2 * D);
+    const float *o = out + (size_t)b * O;
+    float *w = ls;                          // [G] hefts
+    float *lw = w + G;                      // [G] log hefts
+    float *m = lw + G;                      // [G][D]
+    float *v = m + G * D;                   // [G][D] variances
+    float *er = v + G * D;                  // [G][D] exp(r)
+    float *cst = er + G * D;                // [G] log w - 1/2 sum log(2 pi v)
+    float *S0 = cst + G;                    // [G]
+    float *S1 = S0 + G;                     // [G][D]
+    float *S2 = S1 + G * D;                 // [G][D]
+    float *sh = S2 + G * D;                 // [256]
+    __shared__ float s_max, s_sum;
+    if (threadIdx.x == 0) {
+        float mx = -INFINITY;
+        for (int g = 0; g < G; ++g) mx = fmaxf(mx, o[g]);
+        float s = 0.f;
+        for (int g = 0; g < G; ++g) s += __expf(o[g] - mx);
+        s_max = mx;
+        s_sum = s;
+    }
+    __syncthreads();
+    for (int g = threadIdx.x; g < G; g += blockDim.x) {
+        w[g] = __expf(o[g] - s_max) / s_sum;
+        lw[g] = o[g] - s_max - logf(s_sum);
+        S0[g] = 0.f;
+    }
+    for (int k = threadIdx.x; k < G * D; k += blockDim.x) {
+        m[k] = o[G + k];
+        er[k] = __expf(o[G + G * D + k]);
+        v[k] = er[k] + (float)var_floor;
+        S1[k] = 0.f;
+        S2[k] = 0.f;
+    }
+    __syncthreads();
+    for (int g = threadIdx.x; g < G; g += blockDim.x) {
+        float s = 0.f;
+        for (int d = 0; d < D; ++d) s += logf(v[g * D + d]);
+        cst[g] = lw[g] - 0.5f * ((float)D * 1.8378770664093453f + s);
+    }
+    __syncthreads();
+    // responsibilities and statistics, a thread per point
+    float nll = 0.f;
+    for (int p = threadIdx.x; p < P; p += blockDim.x) {
+        const float *x = pts + ((size_t)b * P + p) * D;
+        float mx = -INFINITY, sum = 0.f;
+        for (int g = 0; g < G; ++g) {
+            float q = 0.f;
+            for (int d = 0; d < D; ++d) {
+                const float t = x[d] - m[g * D + d];
+                q = fmaf(t * t, 1.f / v[g * D + d], q);
+            }
+            const float l = cst[g] - 0.5f * q;
+            if (l > mx) { sum = sum * __expf(mx - l) + 1.f; mx = l; }
+            else sum += __expf(l - mx);
+        }
+        const float lse = mx + logf(sum);
+        nll -= lse;
+        for (int g = 0; g < G; ++g) {
+            float q = 0.f;
+            for (int d = 0; d < D; ++d) {
+                const float t = x[d] - m[g * D + d];
+                q = fmaf(t * t, 1.f / v[g * D + d], q);
+            }
+            const float gm = __expf(cst[g] - 0.5f * q - lse);
+            if (gm < 1e-8f) continue;   // contributes < 1e-8 of a point to any statistic
+            atomicAdd(&S0[g], gm);
+            for (int d = 0; d < D; ++d) {
+                const float t = x[d] - m[g * D + d];
+                atomicAdd(&S1[g * D + d], gm * t);
+                atomicAdd(&S2[g * D + d], gm * t * t);
+            }
+        }
+    }
+    nll = bsum_f(nll, sh) / (float)P;
+    // gradient with respect to the network output (mean over the batch)
+    const float invB = 1.f / (float)B, invP = 1.f / (float)P;
+    float *d = d_out + (size_t)b * O;
+    for (int g = threadIdx.x; g < G; g += blockDim.x) d[g] = (w[g] - S0[g] * invP) * invB;
+    for (int k = threadIdx.x; k < G * D; k += blockDim.x) {
+        d[G + k] = -S1[k] / v[k] * invP * invB;
+        d[G + G * D + k] = -0.5f * (S2[k] / v[k] - S0[k / D]) * er[k] / v[k] * invP * invB;
+    }
+    __syncthreads();
+    // pull of the predicted means toward the plain method's fit (nearest pairs)
+    float pull = 0.f;
+    if (lambda > 0.0 && tgt_m) {
+        for (int k = threadIdx.x; k < G; k += blockDim.x) {
+            const double *tm = tgt_m + ((size_t)b * G + k) * D, *tv = tgt_v + ((size_t)b * G + k) * D;
+            float best = INFINITY;
+            int bg = 0;
+            for (int g = 0; g < G; ++g) {
+                float q = 0.f;
+                for (int dd = 0; dd < D; ++dd) {
+                    const float t = m[g * D + dd] - (float)tm[dd];
+                    q = fmaf(t * t, 1.f / (float)tv[dd], q);
+                }
+                if (q < best) { best = q; bg = g; }
+            }
+            const float wk = (float)tgt_w[(size_t)b * G + k] * (float)lambda;
+            pull += wk * best;
+            for (int dd = 0; dd < D; ++dd)
+                atomicAdd(&d[G + bg * D + dd], 2.f * wk * (m[bg * D + dd] - (float)tm[dd]) / (float)tv[dd] * invB);
+        }
+    }
+    pull = bsum_f(pull, sh);
+    if (threadIdx.x == 0) loss[b] = nll + pull;
+    if (pm) {
+        for (int k = threadIdx.x; k < G * D; k += blockDim.x) {
+            pm[(size_t)b * G * D + k] = (double)m[k];
+            pv[(size_t)b * G * D + k] = (double)v[k];
+        }
+        for (int g = threadIdx.x; g < G; g += blockDim.x) pw[(size_t)b * G + g] = (double)w[g];
+    }
+}
+
+// Adam (Kingma & Ba, 2015) on the FP32 master weights; BF16 copy refreshed.
+__global__ void k_adam(float *__restrict__ wgt, const float *__restrict__ g, float *__restrict__ m1, float *__restrict__ m2,
+                       __nv_bfloat16 *__restrict__ wbf, int64_t n, float lr, float b1, float b2, float eps, float c1,
+                       float c2)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float a = b1 * m1[i] + (1.f - b1) * gi;
+    const float s = b2 * m2[i] + (1.f - b2) * gi * gi;
+    m1[i] = a;
+    m2[i] = s;
+    const float w = wgt[i] - lr * (a / c1) / (sqrtf(s / c2) + eps);
+    wgt[i] = w;
+    wbf[i] = __float2bfloat16_rn(w);
+}
+
+__global__ void k_to_bf16(const float *__restrict__ x, __nv_bfloat16 *__restrict__ y, int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = __float2bfloat16_rn(x[i]);
+}
+
+inline int blocks_for(int64_t n, int t) { return (int)((n + t - 1) / t); }
+
+}  // namespace
+
+// ----------------------------------------------------------------- host
+struct InitNet {
+    int D, G, Hp, Hh, Lp, Lh, O;
+    int64_t n_params = 0;
+    std::vector<int64_t> w_off, b_off, w_in, w_out;   // per layer (Lp + Lh + 1 layers)
+    float *wgt = nullptr, *grad = nullptr, *m1 = nullptr, *m2 = nullptr;
+    __nv_bfloat16 *wbf = nullptr;
+    int64_t step = 0;
+    // activation workspace (grown per batch)
+    size_t ws_cap = 0;
+    unsigned char *ws = nullptr;
+};
+
+namespace {
+
+struct Ws {
+    __nv_bfloat16 *x;               // [BP][D] input points in BF16
+    std::vector<__nv_bfloat16 *> h; // per-point activations [BP][Hp] x Lp
+    float *z;                       // FP32 scratch [BP][max(Hp, Hh, O)]
+    __nv_bfloat16 *dz;              // BF16 [BP][Hp]
+    float *dh;                      // FP32 [BP][Hp]
+    float *pooled;                  // [B][Hp]
+    std::vector<__nv_bfloat16 *> a; // head activations [B][Hh] x Lh, a[0] = pooled (BF16)
+    float *out;                     // [B][O]
+    float *dout;                    // [B][O]
+    float *loss;                    // [B]
+};
+
+size_t ws_bytes(const InitNet &n, int B, int P)
+{
+    const int64_t BP = (int64_t)B * P;
+    const int64_t wmax = std::max((int64_t)n.Hp, std::max((int64_t)n.Hh, (int64_t)n.O));
+    size_t s = 0;
+    auto add = [&](size_t b) { s += (b + 255) / 256 * 256; };
+    add(2 * BP * n.D);
+    for (int l = 0; l < n.Lp; ++l) add(2 * BP * n.Hp);
+    add(4 * BP * wmax);
+    add(2 * BP * n.Hp);
+    add(4 * BP * n.Hp);
+    add(4 * (size_t)B * n.Hp);
+    for (int l = 0; l <= n.Lh; ++l) add(2 * (size_t)B * std::max(n.Hh, n.Hp));
+    add(4 * (size_t)B * n.O);
+    add(4 * (size_t)B * n.O);
+    add(4 * (size_t)B);
+    return s;
+}
+
+Ws carve(InitNet &n, int B, int P)
+{
+    const int64_t BP = (int64_t)B * P;
+    const int64_t wmax = std::max((int64_t)n.Hp, std::max((int64_t)n.Hh, (int64_t)n.O));
+    unsigned char *p = n.ws;
+    auto take = [&](size_t b) { unsigned char *q = p; p += (b + 255) / 256 * 256; return q; };
+    Ws w;
+    w.x = reinterpret_cast<__nv_bfloat16 *>(take(2 * BP * n.D));
+    for (int l = 0; l < n.Lp; ++l) w.h.push_back(reinterpret_cast<__nv_bfloat16 *>(take(2 * BP * n.Hp)));
+    w.z = reinterpret_cast<float *>(take(4 * BP * wmax));
+    w.dz = reinterpret_cast<__nv_bfloat16 *>(take(2 * BP * n.Hp));
+    w.dh = reinterpret_cast<float *>(take(4 * BP * n.Hp));
+    w.pooled = reinterpret_cast<float *>(take(4 * (size_t)B * n.Hp));
+    for (int l = 0; l <= n.Lh; ++l)
+        w.a.push_back(reinterpret_cast<__nv_bfloat16 *>(take(2 * (size_t)B * std::max(n.Hh, n.Hp))));
+    w.out = reinterpret_cast<float *>(take(4 * (size_t)B * n.O));
+    w.dout = reinterpret_cast<float *>(take(4 * (size_t)B * n.O));
+    w.loss = reinterpret_cast<float *>(take(4 * (size_t)B));
+    return w;
+}
+
+cudaError_t gemm(const __nv_bfloat16 *A, const __nv_bfloat16 *B, float *C, int M, int N, int K, int lda, int ldb, int ldc,
+                 int tA, int tB, int splits, int accumulate, cudaStream_t s)
+{
+    dim3 grid((N + kBN - 1) / kBN, (M + kBM - 1) / kBM, splits);
+    if (splits > 1 && !accumulate) return cudaErrorInvalidValue;   // split-K only accumulates onto zeroed C
+    k_gemm_bf16<<<grid, 256, 0, s>>>(A, B, C, M, N, K, lda, ldb, ldc, tA, tB, (splits > 1 || accumulate) ? 1 : 0);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+#define CKE(x)                                       \
+    do {                                             \
+        cudaError_t e_ = (x);                        \
+        if (e_ != cudaSuccess) return e_;            \
+    } while (0)
+
+// Forward pass for B sets of P points (pts FP32 [B][P][D], device).
+cudaError_t net_forward(InitNet &n, const float *pts, int B, int P, Ws &w, cudaStream_t s)
+{
+    const int64_t BP = (int64_t)B * P;
+    k_to_bf16<<<blocks_for(BP * n.D, 256), 256, 0, s>>>(pts, w.x, BP * n.D);
+    const __nv_bfloat16 *in = w.x;
+    int kin = n.D;
+    for (int l = 0; l < n.Lp; ++l) {
+        CKE(gemm(in, n.wbf + n.w_off[l], w.z, (int)BP, n.Hp, kin, kin, kin, n.Hp, 0, 0, 1, 0, s));
+        k_bias_act<<<blocks_for(BP * n.Hp, 256), 256, 0, s>>>(w.z, n.wgt + n.b_off[l], w.h[l], nullptr, BP, n.Hp, 1);
+        in = w.h[l];
+        kin = n.Hp;
+    }
+    k_pool<<<dim3((n.Hp + 127) / 128, B), 128, 0, s>>>(w.h[n.Lp - 1], w.pooled, w.a[0], P, n.Hp);
+    int hin = n.Hp;
+    for (int l = 0; l < n.Lh; ++l) {
+        const int li = n.Lp + l;
+        CKE(gemm(w.a[l], n.wbf + n.w_off[li], w.z, B, n.Hh, hin, hin, hin, n.Hh, 0, 0, 1, 0, s));
+        k_bias_act<<<blocks_for((int64_t)B * n.Hh, 256), 256, 0, s>>>(w.z, n.wgt + n.b_off[li], w.a[l + 1], nullptr, B,
+                                                                       n.Hh, 1);
+        hin = n.Hh;
+    }
+    const int lo = n.Lp + n.Lh;
+    CKE(gemm(w.a[n.Lh], n.wbf + n.w_off[lo], w.z, B, n.O, hin, hin, hin, n.O, 0, 0, 1, 0, s));
+    // the BF16 copy of the output is not needed: write it to the free dz buffer
+    k_bias_act<<<blocks_for((int64_t)B * n.O, 256), 256, 0, s>>>(w.z, n.wgt + n.b_off[lo], w.dz, w.out, B, n.O, 0);
+    count_launches(3 + n.Lp + n.Lh);
+    return cudaGetLastError();
+}
+
+// Backward pass from w.dout; gradients accumulate into n.grad (zeroed here).
+cudaError_t net_backward(InitNet &n, int B, int P, Ws &w, cudaStream_t s)
+{
+    const int64_t BP = (int64_t)B * P;
+    CKE(cudaMemsetAsync(n.grad, 0, sizeof(float) * n.n_params, s));
+    // output layer: dW = dout^T a_Lh, db = colsum(dout), dA = dout W
+    const int lo = n.Lp + n.Lh;
+    int hin = n.Lh > 0 ? n.Hh : n.Hp;
+    // dout FP32 -> BF16 for the GEMMs (reuse dz)
+    k_to_bf16<<<blocks_for((int64_t)B * n.O, 256), 256, 0, s>>>(w.dout, w.dz, (int64_t)B * n.O);
+    CKE(gemm(w.dz, w.a[n.Lh], n.grad + n.w_off[lo], n.O, hin, B, n.O, hin, hin, 1, 1, 1, 1, s));
+    k_colsum<<<(n.O + 31) / 32, 256, 0, s>>>(w.dz, n.grad + n.b_off[lo], B, n.O);
+    CKE(gemm(w.dz, n.wbf + n.w_off[lo], w.dh, B, hin, n.O, n.O, hin, hin, 0, 1, 1, 0, s));
+    for (int l = n.Lh - 1; l >= 0; --l) {
+        const int li = n.Lp + l;
+        const int lin = l == 0 ? n.Hp : n.Hh;
+        k_relu_bwd<<<blocks_for((int64_t)B * n.Hh, 256), 256, 0, s>>>(w.dh, w.a[l + 1], w.dz, B, n.Hh, 0);
+        CKE(gemm(w.dz, w.a[l], n.grad + n.w_off[li], n.Hh, lin, B, n.Hh, lin, lin, 1, 1, 1, 1, s));
+        k_colsum<<<(n.Hh + 31) / 32, 256, 0, s>>>(w.dz, n.grad + n.b_off[li], B, n.Hh);
+        CKE(gemm(w.dz, n.wbf + n.w_off[li], w.dh, B, lin, n.Hh, n.Hh, lin, lin, 0, 1, 1, 0, s));
+    }
+    // w.dh now holds d(pooled) [B][Hp]; per-point layers
+    for (int l = n.Lp - 1; l >= 0; --l) {
+        const int kin = l == 0 ? n.D : n.Hp;
+        const __nv_bfloat16 *hin_act = l == 0 ? w.x : w.h[l - 1];
+        k_relu_bwd<<<blocks_for(BP * n.Hp, 256), 256, 0, s>>>(w.dh, w.h[l], w.dz, BP, n.Hp, l == n.Lp - 1 ? P : 0);
+        const int splits = (int)std::min<int64_t>(64, std::max<int64_t>(1, BP / 4096));
+        CKE(gemm(w.dz, hin_act, n.grad + n.w_off[l], n.Hp, kin, (int)BP, n.Hp, kin, kin, 1, 1, splits, 1, s));
+        k_colsum<<<(n.Hp + 31) / 32, 256, 0, s>>>(w.dz, n.grad + n.b_off[l], BP, n.Hp);
+        if (l > 0) CKE(gemm(w.dz, n.wbf + n.w_off[l], w.dh, (int)BP, kin, n.Hp, n.Hp, kin, kin, 0, 1, 1, 0, s));
+    }
+    count_launches(2 + 3 * (n.Lh + n.Lp));
+    return cudaGetLastError();
+}
+
+cudaError_t ensure_ws(InitNet &n, int B, int P)
+{
+    const size_t need = ws_bytes(n, B, P);
+    if (need <= n.ws_cap) return cudaSuccess;
+    if (n.ws) cudaFree(n.ws);
+    n.ws = nullptr;
+    n.ws_cap = 0;
+    CKE(cudaMalloc(&n.ws, need));
+    n.ws_cap = need;
+    return cudaSuccess;
+}
+
+}  // namespace
+
+InitNet *init_net_new(int D, int G, int Hp, int Hh, int Lp, int Lh, uint64_t seed, cudaError_t *err)
+{
+    InitNet *n = new InitNet();
+    n->D = D; n->G = G; n->Hp = Hp; n->Hh = Hh; n->Lp = Lp; n->Lh = Lh; n->O = G * (1 + 2 * D);
+    const int L = Lp + Lh + 1;
+    int64_t o = 0;
+    for (int l = 0; l < L; ++l) {
+        const int in = l == 0 ? D : (l < Lp ? Hp : (l == Lp ? Hp : Hh));
+        const int out = l < Lp ? Hp : (l < L - 1 ? Hh : n->O);
+        n->w_in.push_back(in);
+        n->w_out.push_back(out);
+        n->w_off.push_back(o);
+        o += (int64_t)in * out;
+        n->b_off.push_back(o);
+        o += out;
+    }
+    n->n_params = o;
+    // He-uniform initial weights from SplitMix64(seed), zero biases; the
+    // output layer starts small so the first mixtures are broad
+    std::vector<float> h(o, 0.f);
+    uint64_t st = seed;
+    auto next = [&]() {
+        uint64_t z = (st += 0x9e3779b97f4a7c15ULL);
+        z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+        z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+        z ^= z >> 31;
+        return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+    };
+    for (int l = 0; l < L; ++l) {
+        const double lim = std::sqrt(6.0 / n->w_in[l]) * (l == L - 1 ? 0.1 : 1.0);
+        for (int64_t k = 0; k < n->w_in[l] * n->w_out[l]; ++k) h[n->w_off[l] + k] = (float)((2.0 * next() - 1.0) * lim);
+    }
+    cudaError_t e = cudaMalloc(&n->wgt, 4 * o);
+    if (e == cudaSuccess) e = cudaMalloc(&n->grad, 4 * o);
+    if (e == cudaSuccess) e = cudaMalloc(&n->m1, 4 * o);
+    if (e == cudaSuccess) e = cudaMalloc(&n->m2, 4 * o);
+    if (e == cudaSuccess) e = cudaMalloc(&n->wbf, 2 * o);
+    if (e == cudaSuccess) e = cudaMemcpy(n->wgt, h.data(), 4 * o, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(n->m1, 0, 4 * o);
+    if (e == cudaSuccess) e = cudaMemset(n->m2, 0, 4 * o);
+    if (e == cudaSuccess) {
+        k_to_bf16<<<blocks_for(o, 256), 256>>>(n->wgt, n->wbf, o);
+        e = cudaGetLastError();
+    }
+    *err = e;
+    return n;
+}
+
+void init_net_free(InitNet *n)
+{
+    if (!n) return;
+    void *b[] = {n->wgt, n->grad, n->m1, n->m2, n->wbf, n->ws};
+    for (void *p : b)
+        if (p) cudaFree(p);
+    delete n;
+}
+
+int64_t init_net_n_params(const InitNet *n) { return n->n_params; }
+
+namespace {
+__global__ void k_gather_rows(const float *__restrict__ X, int D, const int64_t *__restrict__ idx, int P,
+                              float *__restrict__ out)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)P * D) return;
+    const int64_t p = e / D, d = e - p * D;
+    out[e] = X[idx[p] * D + d];
+}
+}  // namespace
+
+cudaError_t init_net_gather(const float *X, int D, const int64_t *idx, int P, float *out, cudaStream_t s)
+{
+    k_gather_rows<<<blocks_for((int64_t)P * D, 256), 256, 0, s>>>(X, D, idx, P, out);
+    count_launches(1);
+    return cudaGetLastError();
+}
+int init_net_D(const InitNet *n) { return n->D; }
+int init_net_G(const InitNet *n) { return n->G; }
+
+cudaError_t init_net_set_weights(InitNet *n, const float *w_host)
+{
+    CKE(cudaMemcpy(n->wgt, w_host, 4 * n->n_params, cudaMemcpyHostToDevice));
+    k_to_bf16<<<blocks_for(n->n_params, 256), 256>>>(n->wgt, n->wbf, n->n_params);
+    return cudaGetLastError();
+}
+
+cudaError_t init_net_get(const InitNet *n, float *w_host, float *g_host)
+{
+    if (w_host) CKE(cudaMemcpy(w_host, n->wgt, 4 * n->n_params, cudaMemcpyDeviceToHost));
+    if (g_host) CKE(cudaMemcpy(g_host, n->grad, 4 * n->n_params, cudaMemcpyDeviceToHost));
+    return cudaSuccess;
+}
+
+// Forward (+ loss, + backward if grads, + Adam if lr > 0).  pts: device FP32
+// [B][P][D]; targets (device FP64, may be NULL when lambda == 0); predicted
+// parameters written to pm/pv/pw (device FP64, may be NULL); mean loss to
+// *loss_host.
+cudaError_t init_net_run(InitNet *n, const float *pts, int B, int P, const double *tm, const double *tv, const double *tw,
+                         double lambda, double var_floor, int grads, double lr, double *pm, double *pv, double *pw,
+                         double *loss_host, cudaStream_t s)
+{
+    CKE(ensure_ws(*n, B, P));
+    Ws w = carve(*n, B, P);
+    CKE(net_forward(*n, pts, B, P, w, s));
+    const size_t sm = sizeof(float) * (3 * (size_t)n->G + 5 * (size_t)n->G * n->D + 256 + n->G);
+    CKE(cudaFuncSetAttribute(k_set_loss, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_set_loss<<<B, 256, sm, s>>>(w.out, pts, P, n->D, n->G, var_floor, tm, tv, tw, lambda, w.dout, w.loss, pm, pv, pw, B);
+    count_launches(1);
+    CKE(cudaGetLastError());
+    if (grads) CKE(net_backward(*n, B, P, w, s));
+    if (grads && lr > 0.0) {
+        ++n->step;
+        const float b1 = 0.9f, b2 = 0.999f;
+        const float c1 = 1.f - std::pow(b1, (float)n->step), c2 = 1.f - std::pow(b2, (float)n->step);
+        k_adam<<<blocks_for(n->n_params, 256), 256, 0, s>>>(n->wgt, n->grad, n->m1, n->m2, n->wbf, n->n_params, (float)lr,
+                                                            b1, b2, 1e-8f, c1, c2);
+        count_launches(1);
+        CKE(cudaGetLastError());
+    }
+    if (loss_host) {
+        std::vector<float> l(B);
+        CKE(cudaMemcpyAsync(l.data(), w.loss, 4 * (size_t)B, cudaMemcpyDeviceToHost, s));
+        CKE(cudaStreamSynchronize(s));
+        double t = 0.0;
+        for (int b = 0; b < B; ++b) t += l[b];
+        *loss_host = t / B;
+    } else {
+        CKE(cudaStreamSynchronize(s));
+    }
+    return cudaSuccess;
+}
+
+}  // namespace gmm

@@ -169,6 +169,20 @@ cudaError_t launch_b_em_finish(BFit *fits, int n_fits, const int32_t *comp_fit, 
                                const BItem *items, const double *partial, const double *llp, double var_floor,
                                double em_tol, int iter, cudaStream_t s);
 
+// ---- learned initialiser (gmm_init_net.cu)
+struct InitNet;
+InitNet *init_net_new(int D, int G, int Hp, int Hh, int Lp, int Lh, uint64_t seed, cudaError_t *err);
+void init_net_free(InitNet *n);
+int64_t init_net_n_params(const InitNet *n);
+int init_net_D(const InitNet *n);
+int init_net_G(const InitNet *n);
+cudaError_t init_net_gather(const float *X, int D, const int64_t *idx, int P, float *out, cudaStream_t s);
+cudaError_t init_net_set_weights(InitNet *n, const float *w_host);
+cudaError_t init_net_get(const InitNet *n, float *w_host, float *g_host);
+cudaError_t init_net_run(InitNet *n, const float *pts, int B, int P, const double *tm, const double *tv, const double *tw,
+                         double lambda, double var_floor, int grads, double lr, double *pm, double *pv, double *pw,
+                         double *loss_host, cudaStream_t s);
+
 // ---- launchers implemented in gmm_em_tc.cu
 bool em_tc_supported(int32_t D, int32_t G);
 int em_tc_grid(int sms);

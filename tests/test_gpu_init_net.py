@@ -1,0 +1,93 @@
+"""Learned initialiser on the GPU: loss and gradients of the BF16 kernels
+against the FP64 network oracle, and a short training run."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import init_net as orc
+from paper_1707_09094_gb300 import InitNet
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1707_09094_gb300 import build
+    build.build()
+
+
+@pytest.mark.parametrize("cfg", [dict(D=4, G=3, Hp=16, Hh=32, Lp=2, Lh=1, B=3, P=96, tol=0.05),
+                                 dict(D=32, G=32, Hp=64, Hh=64, Lp=3, Lh=3, B=2, P=256, tol=0.12)])
+def test_gradients_match_oracle(cfg):
+    """BF16 operands with FP32 accumulation against the FP64 network oracle.
+
+    Every GEMM rounds both operands to BF16 (unit roundoff 2^-9), forward
+    and backward, so the gradient error grows with depth: the whole vector
+    must lie within `tol` (relative norm: 5% for the 3-layer net, 12% for
+    the 7-layer one) and point the same way (cosine > 0.995); each layer's
+    block must have cosine > 0.98, which a dropped term or a transposed
+    operand in any one layer's backward pass fails."""
+    D, G, Hp, Hh, Lp, Lh, B, P = (cfg[k] for k in ("D", "G", "Hp", "Hh", "Lp", "Lh", "B", "P"))
+    net = InitNet(D, G, Hp, Hh, Lp, Lh, seed=3)
+    w = net.get_weights().astype(np.float64)
+    rng = np.random.default_rng(4)
+    pts = rng.normal(0, 1.5, (B, P, D)).astype(np.float32)
+    tgt = (rng.normal(0, 1, (B, G, D)), rng.uniform(0.5, 2, (B, G, D)), rng.dirichlet(np.ones(G), B))
+    loss, _ = net.step(torch.from_numpy(pts).cuda(), [torch.from_numpy(t).cuda() for t in tgt], lam=0.2,
+                       var_floor=1e-3, mode=1)
+    g = net.get_grads().astype(np.float64)
+    ref_loss, ref_g, _ = orc.loss_and_grad(w, pts, G, D, Hp, Hh, Lp, Lh, 1e-3, tgt, lam=0.2)
+    assert loss == pytest.approx(ref_loss, rel=1e-2)
+
+    def cmp(a, b):
+        return np.linalg.norm(a - b) / np.linalg.norm(b), a @ b / (np.linalg.norm(a) * np.linalg.norm(b))
+
+    per_layer, o = [], 0
+    for (fo, fi) in orc.layer_shapes(D, G, Hp, Hh, Lp, Lh):
+        n = fo * fi + fo
+        per_layer.append(cmp(g[o:o + n], ref_g[o:o + n]))
+        o += n
+    rel, cos = cmp(g, ref_g)
+    assert rel < cfg["tol"] and cos > 0.995, (rel, cos, per_layer)
+    assert all(c > 0.98 for _, c in per_layer), per_layer
+
+
+def test_training_reduces_loss():
+    rng = np.random.default_rng(5)
+    D, G, P = 4, 3, 128
+    net = InitNet(D, G, 32, 32, 2, 1, seed=1)
+    pts = torch.from_numpy(rng.normal(0, 1, (8, P, D)).astype(np.float32) * 2 + 1).cuda()
+    first, _ = net.step(pts, mode=0, var_floor=1e-3)
+    for _ in range(200):
+        net.step(pts, mode=2, lr=3e-3, var_floor=1e-3)
+    last, _ = net.step(pts, mode=0, var_floor=1e-3)
+    assert last < first - 0.5
+
+
+def test_learned_start_beats_kmeans_on_held_out_mixtures():
+    """A briefly trained network (4000 fitted training sets, 1500 Adam steps)
+    seeds EM on held-out N = 1e5 mixtures; EM then converges in fewer data
+    passes than from the paper's k-means seeding (which costs its own 10
+    passes) and to a final mean log-likelihood at least as good on average."""
+    from paper_1707_09094_gb300 import init_train, synth
+    D, G, P = 8, 8, 512
+    pts, tgt = init_train.make_sets(4000, D, G, P, seed0=5_000_000)
+    net = InitNet(D, G, 128, 256, 3, 3, seed=0)
+    hist = init_train.train(net, pts, tgt, steps=1500, batch=64, lr=1e-3, lam=0.1)
+    assert hist[-100:].mean() < hist[:100].mean()
+    Xs = []
+    for j in range(16):
+        rng = np.random.default_rng(9_000_000 + j)
+        X, _ = synth._draw(rng, synth.mixture_c1(rng, D, G), 100_000)
+        Xs.append(torch.from_numpy(X).cuda())
+    rows = init_train.evaluate(net, Xs, P=P, max_iter=300, em_tol=1e-6)
+    assert all(r["learned_ok"] for r in rows)
+    km_passes = np.mean([r["kmeans_passes"] for r in rows])
+    ln_passes = np.mean([r["learned_passes"] for r in rows])
+    km_ll = np.mean([r["kmeans_ll"] for r in rows])
+    ln_ll = np.mean([r["learned_ll"] for r in rows])
+    assert ln_passes < km_passes, (ln_passes, km_passes)
+    assert ln_ll > km_ll - 0.02, (ln_ll, km_ll)
+    # the fallback policy never ends below the k-means start's likelihood
+    m, _ = init_train.learned_or_kmeans(net, Xs[0], P=P, judge=True)
+    assert m.avg_log_p(Xs[0]) >= rows[0]["kmeans_ll"] - 1e-9
