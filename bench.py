@@ -96,10 +96,11 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def make_data():
+def make_data(n=None):
+    """The c2 workload (N = 2,000,000, D = 60, N_G = 256), or its first n samples."""
     from paper_1707_09094_gb300 import synth
     X, _, _ = synth.make("c2")
-    return X
+    return X if n is None else np.ascontiguousarray(X[:n])
 
 
 def cpu_oracle_rate(X, target_s: float = 12.0):
@@ -184,7 +185,7 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     build.build()
-    X = make_data()
+    X = make_data(args.n)
     Xd = torch.from_numpy(X).cuda()
     N, D = X.shape
     G = G_FULL
@@ -234,9 +235,18 @@ def run_ours(args):
             wall = time.perf_counter() - t0
         ms = max_over_ranks(ev0.elapsed_time(ev1), world, "cuda")
         pass_ms, pass_n, launches = g.profile_read()
+        extra = {}
+        if prec == "bf16":
+            cyc = g.phase_cycles()
+            tot = max(sum(cyc), 1)
+            names = ["prefetch_next_tile", "sync_a_ready", "wait_mma", "screen_pass1", "candidates",
+                     "exact_recompute", "lse_and_m_step", "tail_sync"]
+            n_scr, kept, dense = g.screen_stats()
+            extra = {"phase_share": {k: c / tot for k, c in zip(names, cyc)},
+                     "candidates_per_sample": kept / max(n_scr, 1), "dense_fallbacks": dense}
         g.profile(False)
         return {"ms": ms, "wall_s": wall, "pass_ms": pass_ms, "pass_n": pass_n, "launches": launches,
-                "clocks": cs.summary()}
+                "clocks": cs.summary(), **extra}
 
     # k-means (Sec. 3) pass throughput and one whole learn(), reported beside the EM metric
     km = GMM().set_params(*start)
@@ -291,8 +301,8 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "split_bf16": "bf16"}[head],
         "data": "synthetic",
-        "config": {"workload": "c2 EM iteration (fused E+M pass + FP64 reduce/update): N=2000000 D=60 N_G=256, "
-                               "k-means-initialised, E-step %s" % head,
+        "config": {"workload": "c2 EM iteration (fused E+M pass + FP64 reduce/update): N=%d D=60 N_G=256, "
+                               "k-means-initialised, E-step %s" % (N, head),
                    "N": N, "D": D, "N_G": G, "form": head,
                    "l2": "inputs larger than L2 (X = %.0f MB)" % (X.nbytes / 1e6),
                    "parallelism": "replicas" if world > 1 else "single"},
@@ -308,7 +318,9 @@ def run_ours(args):
                       "ms_per_step": results[p]["ms"] / args.steps,
                       "pass_ms": results[p]["pass_ms"] / max(results[p]["pass_n"], 1),
                       "avg_log_p_after_10_em": quality[p]["avg_log_p"],
-                      "delta_ll_vs_fp32": (quality[p]["avg_log_p"] - ref_ll) if ref_ll is not None else None}
+                      "delta_ll_vs_fp32": (quality[p]["avg_log_p"] - ref_ll) if ref_ll is not None else None,
+                      **{k: results[p][k] for k in ("phase_share", "candidates_per_sample", "dense_fallbacks")
+                         if k in results[p]}}
                   for p in results},
     }
     if not args.no_batched:
@@ -404,6 +416,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-fit batched leg")
     ap.add_argument("--no-init-net", action="store_true", help="skip the learned-initialiser training leg")
+    ap.add_argument("--n", type=int, default=None,
+                    help="time on the first n samples only (profiling captures); the default is the full workload")
     args = ap.parse_args()
     args.forms = [f for f in args.forms.split(",") if f]
     if args.impl == "reference":
