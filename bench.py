@@ -239,10 +239,9 @@ def run_ours(args):
         if prec == "bf16":
             cyc = g.phase_cycles()
             tot = max(sum(cyc), 1)
-            names = ["prefetch_next_tile", "sync_a_ready", "wait_mma", "screen_pass1", "candidates",
-                     "exact_recompute", "lse_and_m_step", "tail_sync"]
+            names = ["build_next_operand", "sync_operand_ready", "wait_mma", "screen_pass1", "candidate_lists"]
             n_scr, kept, dense = g.screen_stats()
-            extra = {"phase_share": {k: c / tot for k, c in zip(names, cyc)},
+            extra = {"screen_phase_share": {k: c / tot for k, c in zip(names, cyc)},
                      "candidates_per_sample": kept / max(n_scr, 1), "dense_fallbacks": dense}
         g.profile(False)
         return {"ms": ms, "wall_s": wall, "pass_ms": pass_ms, "pass_n": pass_n, "launches": launches,
@@ -319,7 +318,7 @@ def run_ours(args):
                       "pass_ms": results[p]["pass_ms"] / max(results[p]["pass_n"], 1),
                       "avg_log_p_after_10_em": quality[p]["avg_log_p"],
                       "delta_ll_vs_fp32": (quality[p]["avg_log_p"] - ref_ll) if ref_ll is not None else None,
-                      **{k: results[p][k] for k in ("phase_share", "candidates_per_sample", "dense_fallbacks")
+                      **{k: results[p][k] for k in ("screen_phase_share", "candidates_per_sample", "dense_fallbacks")
                          if k in results[p]}}
                   for p in results},
     }

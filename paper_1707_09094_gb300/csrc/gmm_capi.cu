@@ -122,6 +122,7 @@ struct gmm_model {
     // workspace
     double *partial = nullptr; size_t partial_cap = 0;
     float *slab = nullptr; size_t slab_cap = 0;
+    unsigned char *tclist = nullptr; size_t tclist_cap = 0;   // tensor-core pass: per-sample records
     float *lse = nullptr; size_t lse_cap = 0;
     double *llp = nullptr; size_t llp_cap = 0;
     double *lld = nullptr; size_t lld_cap = 0;
@@ -303,7 +304,7 @@ gmm_status run_em(gmm_model *m, const float *Xd, int64_t N, int32_t em_iter, dou
     const int n_llp = two_phase ? (int)((N + 127) / 128) : grid;
     CK(grow(m->partial, m->partial_cap, (size_t)grid * G * S));
     if (two_phase) CK(grow(m->lse, m->lse_cap, (size_t)N));
-    if (tc) CK(grow(m->slab, m->slab_cap, gmm::em_tc_slab_floats(D, G, grid)));
+    if (tc) CK(grow(m->tclist, m->tclist_cap, gmm::em_tc_list_bytes(N)));
     CK(grow(m->llp, m->llp_cap, (size_t)n_llp));
     CK(grow(m->lld, m->lld_cap, (size_t)(em_iter > 0 ? em_iter : 1)));
     CK(gmm::launch_status_reset(m->status, s));
@@ -316,12 +317,12 @@ gmm_status run_em(gmm_model *m, const float *Xd, int64_t N, int32_t em_iter, dou
         size_t slot = 0;
         gmm_status prc = prof_begin(m, s, &slot);
         if (prc != GMM_OK) return prc;
-        if (tc) CK(gmm::launch_em_pass_tc(pa, m->slab, grid, s));
+        if (tc) CK(gmm::launch_em_pass_tc(pa, gmm::em_tc_lists(m->tclist, N), grid, grid, s));
         else if (two_phase) CK(gmm::launch_em_two_phase(pa, m->lse, grid, s));
         else CK(gmm::launch_em_pass_simt(pa, grid, s));
         if ((prc = prof_end(m, s, slot)) != GMM_OK) return prc;
         gmm::EmFinalizeArgs fa{m->partial, m->llp, grid, n_llp, N, D, G, m->par[(base + k) & 1], m->par[(base + k + 1) & 1],
-                               var_floor, tc ? 1 : 0, m->op, m->center(), m->status, k, em_tol, m->lld,
+                               var_floor, 0, m->op, m->center(), m->status, k, em_tol, m->lld,
                                tc ? 1 : (m->has_center && m->center_D == D)};
         CK(gmm::launch_em_finalize(fa, s));
     }
@@ -399,7 +400,7 @@ void gmm_destroy(gmm_model *m)
     if (m->sstats) cudaFree(m->sstats);
     void *bufs[] = {m->par[0], m->par[1], m->op_sm, m->op_mu, m->op_c, m->op_B, m->gstat, m->fstat,
                     m->partial, m->slab, m->lse, m->llp, m->lld, m->counts, m->assign, m->xstage, m->dstage, m->idx,
-                    m->hist, m->status};
+                    m->hist, m->status, m->tclist};
     for (void *p : bufs)
         if (p) cudaFree(p);
     delete m;

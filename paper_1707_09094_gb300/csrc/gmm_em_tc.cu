@@ -1,36 +1,35 @@
-// Tensor-core (tcgen05, sm_103a) fused EM pass.
+// Tensor-core (tcgen05, sm_103a) EM pass in three kernels.
 //
-// Per 128-sample tile of the CTA's contiguous chunk (the paper's thread t):
-//  1. E-step contraction on the tensor cores, BF16 operands, FP32 accumulators
-//     in TMEM, split into the two halves of the expanded log-density (Eq. 15
-//     expanded about the global centre m, x' = x - m, mu' = mu - m):
+//  1. k_em_screen_tc -- per 128-sample tile of the CTA's chunk, the E-step
+//     contraction on the tensor cores, BF16 operands, FP32 accumulators in
+//     TMEM, split into the two halves of the log-density (Eq. 15) expanded
+//     about the global centre m (x' = x - m, mu' = mu - m):
 //        P1[i][g] = sum_d x'^2 (-1/2 iv_gd)      (K block 0, TMEM columns 0..255)
 //        P2[i][g] = sum_d x'   (mu'_gd iv_gd)    (K block 1, TMEM columns 256..511)
-//     so l~_g(x_i) = ctc_g + P1 + P2 approximates log w_g N(x_i|g).
-//  2. Screening with a rigorous bound: with BF16 rounding of both operands,
-//     |l~ - l| <= 2^-8 * 1.25 * sum_d (x'^2 iv/2 + |x' mu'| iv) + tiny terms,
-//     and by AM-GM sum_d |x' mu'| iv <= sum_d (x'^2 + mu'^2) iv / 2, so
-//     |l~ - l| <= K1 |P1| + k2_g with k2_g = 2^-8 * 1.25 * q_g / 2 + ...
+//     so l~_g(x_i) = ctc_g + P1 + P2 approximates log w_g N(x_i|g).  With
+//     BF16 rounding of both operands, |l~ - l| <= 2^-8 * 1.25 *
+//     sum_d (x'^2 iv/2 + |x' mu'| iv) + tiny terms, and by AM-GM
+//     sum_d |x' mu'| iv <= sum_d (x'^2 + mu'^2) iv / 2, so
+//     |l~ - l| <= K1 |P1| + k2_g with k2_g = 2^-8 * 1.25 * q_g / 2 + ....
 //     A Gaussian whose upper bound lies more than T = ln(N * 1e9) nats below
-//     the best lower bound (35 nats at N = 2e6) has responsibility below
-//     1e-9 / N and is dropped: per Gaussian the dropped mass is below 1e-9,
-//     under the 1e-8 responsibility sum below which the update keeps a
-//     Gaussian's parameters.
-//  3. The few remaining candidates (one to a few per sample on speech-like
-//     data) get their log-density recomputed exactly in FP32 on the CUDA
-//     cores, one warp per (sample, Gaussian) with lanes over dimensions;
-//     log-sum-exp over them (Eqs. 16-18), responsibilities l_{g,i} (Eq. 3),
-//     and the M-step statistics (Eqs. 9-11, shifted by the FP32 mean of the
-//     iteration start) reduced into the CTA's FP32 slab in L2 with
-//     fire-and-forget atomics.  Responsibilities are never stored.
-// Pipelining: A (the BF16 sample operand) and the FP32 sample tile (cp.async)
-// are double-buffered, so the MMAs of tile t+1 run while tile t is screened,
-// recomputed and accumulated.
-// Warp roles: warps 0-7 are the epilogue (warp w reads TMEM lanes 32*(w%4)..,
-// i.e. samples 32*(w%4).., Gaussians 128*(w/4)..), warp 8 allocates TMEM and
-// one of its threads issues the MMAs.  Every wait is bounded: on expiry the
-// CTA records GMM_ERR_TIMEOUT, stops issuing work, drains, frees TMEM and
-// returns.
+//     the best lower bound has responsibility below 1e-9 / N and is dropped
+//     (per Gaussian the dropped mass is below 1e-9, under the 1e-8
+//     responsibility sum below which the update keeps a Gaussian's
+//     parameters).  Output per (sample, half of the Gaussians): the list of
+//     surviving Gaussians (at most kTcCap, else the half is marked dense).
+//  2. k_em_exact -- one warp per sample, lanes over dimensions, the
+//     parameters in shared memory: the exact FP32 log-density of every
+//     candidate (the formula of the CUDA-core form), of every Gaussian of a
+//     dense half; log-sum-exp (Eqs. 16-18), log p(x_i) into the CTA's FP64
+//     log-likelihood, responsibilities l_{g,i} (Eq. 3) of the candidates.
+//  3. k_em_mstep_lists -- one CTA per (sample chunk, half of the Gaussians),
+//     the paper's thread t: per 256-sample tile the (sample, Gaussian) pairs
+//     are counting-sorted by Gaussian, and the warp that owns a Gaussian sums
+//     l, l (x - mu_f), l (x - mu_f)^2 over its pairs in registers (Eqs. 9-11,
+//     shifted by the FP32 mean mu_f of the iteration start) and adds them to
+//     the CTA's FP32 statistics in shared memory (no atomics on them); the
+//     chunk's statistics go to its FP64 partial once.
+// Responsibilities exist only for the surviving pairs (a few per sample).
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -44,9 +43,11 @@ namespace {
 constexpr int kEpiThreads = 256;
 constexpr int kThreads = kEpiThreads + 32;
 constexpr int kTM = 128;          // samples per tile = MMA M
-constexpr int kCap = 16;          // candidates per (sample, half) before the dense fallback
-constexpr int kNB = 8;            // candidates a warp recomputes at once
+constexpr int kCap = kTcCap;      // candidates per (sample, half) before the dense fallback
 constexpr float kK1 = 0.009765625f * 1.25f;   // 2^-7 * 1.25 (multiplies |P1|)
+constexpr int kExThreads = 1024;  // exact-recompute kernel: 32 warps, one sample per warp at a time
+constexpr int kMsThreads = 512;   // M-step kernel: 16 warps
+constexpr int kMsTile = 256;      // samples per M-step tile
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -175,91 +176,37 @@ __device__ __forceinline__ float warp_max_f(float v)
     return v;
 }
 
-// Exact FP32 log-density of one Gaussian at one sample by one thread (the
-// formula of the CUDA-core form: c_g - 1/2 sum_d (x_d s_gd - mu_gd s_gd)^2);
-// x is the sample's row in shared memory.  Used by the dense path.
-__device__ __forceinline__ float thread_logit(const float *x, const float2 *__restrict__ p, float c, int D)
-{
-    float acc = 0.f;
-    for (int d = 0; d < D; ++d) {
-        const float2 q = __ldg(p + d);
-        const float t = fmaf(x[d], q.x, -q.y);
-        acc = fmaf(t, t, acc);
-    }
-    return fmaf(-0.5f, acc, c);
-}
 
-// M-step contribution of one (sample, Gaussian) pair with responsibility gm
-// (Eqs. 9-11 about the shift tc_shift of the BF16 operand row of g in shared
-// memory): one warp; lane k adds (gm u, gm u^2) for dimensions 2k and 2k+1 as
-// one 16-byte vector atomic (CUDA's float4 atomicAdd, compute capability
-// >= 9.0) into the CTA's slab row [S0, pad x3 | (S1_d, S2_d) for d < DP].
-__device__ __forceinline__ void smem_accumulate(float *slab_g, const float *x, const unsigned char *sB, int NG, int g,
-                                                const float *ctr, float gm, int D, int DP, int lane)
+__device__ __forceinline__ bool skip_block(const DevStatus *st, int iter)
 {
-    if (2 * lane < DP) {
-        auto term = [&](int d, float &a1, float &a2) {
-            float u = 0.f;
-            if (d < D) {
-                const uint32_t off = sw128_off(g, d >> 3) + (uint32_t)((d & 7) * 2);
-                const __nv_bfloat16 b1 = *reinterpret_cast<const __nv_bfloat16 *>(sB + off);
-                const __nv_bfloat16 b2 = *reinterpret_cast<const __nv_bfloat16 *>(sB + (uint32_t)NG * 128u + off);
-                u = x[d] - tc_shift(ctr[d], b1, b2);
-            }
-            a1 = gm * u;
-            a2 = a1 * u;
-        };
-        float4 v;
-        term(2 * lane, v.x, v.y);
-        term(2 * lane + 1, v.z, v.w);
-        atomicAdd(reinterpret_cast<float4 *>(slab_g + 4 + 4 * lane), v);
-    }
-    if (lane == 31) atomicAdd(slab_g, gm);
+    __shared__ int s_skip;
+    if (threadIdx.x == 0) s_skip = (st->halt != 0 || iter > st->stop_after) ? 1 : 0;
+    __syncthreads();
+    return s_skip != 0;
 }
-
-__device__ __forceinline__ void cp_async4(uint32_t dst, const void *src)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 struct TcArgs {
     EmPassArgs a;
-    float *slab;      // [grid][G][1+2D] FP32 statistics of each CTA
+    TcLists L;
     int32_t NG;       // Gaussians padded to a multiple of 16 (MMA N)
     int32_t nk;       // K=16 steps per K block: ceil(D/16)
-    int32_t x_al16;   // X is 16-byte aligned
     float screen;     // screening distance in nats, ln(N * 1e9)
 };
 
 struct TcSmem {
-    uint32_t B, A, X, xbytes, cst, ctr, cg, cl, cn, dms, xlo, xms, lse, bars, misc, total;
+    uint32_t B, A, cst, ctr, cg, xlo, bars, misc, total;
 };
 
-__host__ __device__ inline TcSmem tc_layout(int D, int G, int NG)
+__host__ __device__ inline TcSmem tc_layout(int NG)
 {
-    (void)G;
     TcSmem L;
     uint32_t o = 0;
     L.B = o; o += 2u * NG * 128u;                        // two K blocks of [NG][128 B]
     L.A = o; o += 2u * kTM * 256u;                       // two buffers x two K blocks of [128][128 B]
-    L.xbytes = ((uint32_t)kTM * D * 4u + 15u) & ~15u;
-    L.X = o; o += 2u * L.xbytes;                         // two FP32 sample tiles
-    L.cst = o; o += 8u * NG;                             // (ctc + k2, k2) per Gaussian
+    L.cst = o; o += 8u * NG;                             // (ctc, k2) per Gaussian
     L.ctr = o; o += 4u * 64u;                            // centre
-    L.cg = o; o += (uint32_t)kEpiThreads * kCap;         // candidate Gaussian (local index)
-    o = (o + 15u) & ~15u;
-    L.cl = o; o += 4u * kEpiThreads * kCap;              // exact log-density, then responsibility
-    L.cn = o; o += 4u * kEpiThreads;                     // candidates per (sample, half)
-    L.dms = o; o += 8u * kEpiThreads;                    // dense path: (max, sum of exp)
-    L.xlo = o; o += 4u * kEpiThreads;
-    L.xms = o; o += 8u * kEpiThreads;
-    L.lse = o; o += 4u * kTM;
+    L.cg = o; o += (uint32_t)kEpiThreads * kCap;         // candidate list staging, 16 B per thread
+    L.xlo = o; o += 4u * kEpiThreads;                    // best lower bound per (sample, half)
     o = (o + 7u) & ~7u;
     L.bars = o; o += 8u * 4u;
     L.misc = o; o += 16u;
@@ -267,65 +214,47 @@ __host__ __device__ inline TcSmem tc_layout(int D, int G, int NG)
     return L;
 }
 
-__global__ void __launch_bounds__(kThreads, 1) k_em_pass_tc(TcArgs args)
+// ------------------------------------------------------------------------
+// 1. Screening on the tensor cores.  Warp roles: warps 0-7 are the epilogue
+// (warp w reads TMEM lanes 32*(w%4).., i.e. samples 32*(w%4).., Gaussians
+// 128*(w/4)..), warp 8 allocates TMEM and one of its threads issues the
+// MMAs.  The BF16 sample operand is double-buffered, so the MMAs of tile
+// t+1 run while tile t is screened.  Every wait is bounded: on expiry the
+// CTA records GMM_ERR_TIMEOUT, stops issuing work, drains, frees TMEM and
+// returns.
+// ------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads, 1) k_em_screen_tc(TcArgs args)
 {
     extern __shared__ __align__(1024) unsigned char tc_raw[];
     const EmPassArgs &a = args.a;
-    __shared__ int s_skip;
-    if (threadIdx.x == 0) s_skip = (a.status->halt != 0 || a.iter > a.status->stop_after) ? 1 : 0;
-    __syncthreads();
-    if (s_skip) return;   // uniform across the block
-    const int D = a.D, G = a.G, NG = args.NG, nk = args.nk, S = 1 + 2 * a.D;
-    const TcSmem Ls = tc_layout(D, G, NG);
+    if (skip_block(a.status, a.iter)) return;   // uniform across the block
+    const int D = a.D, G = a.G, NG = args.NG, nk = args.nk;
+    const TcSmem Ls = tc_layout(NG);
     unsigned char *sbase = tc_raw + ((1024u - (smem_u32(tc_raw) & 1023u)) & 1023u);
     unsigned char *sB = sbase + Ls.B;
     unsigned char *sA = sbase + Ls.A;
-    float *sX = reinterpret_cast<float *>(sbase + Ls.X);
     float2 *cst = reinterpret_cast<float2 *>(sbase + Ls.cst);
     float *ctr = reinterpret_cast<float *>(sbase + Ls.ctr);
     uint8_t *cg = reinterpret_cast<uint8_t *>(sbase + Ls.cg);
-    float *cl = reinterpret_cast<float *>(sbase + Ls.cl);
-    int *cn = reinterpret_cast<int *>(sbase + Ls.cn);
-    float2 *dms = reinterpret_cast<float2 *>(sbase + Ls.dms);
     float *xlo = reinterpret_cast<float *>(sbase + Ls.xlo);
-    float2 *xms = reinterpret_cast<float2 *>(sbase + Ls.xms);
-    float *slse = reinterpret_cast<float *>(sbase + Ls.lse);
     uint64_t *bar_afull = reinterpret_cast<uint64_t *>(sbase + Ls.bars);
     uint64_t *bar_lfull = bar_afull + 1;
     uint64_t *bar_lfree = bar_afull + 2;
     uint64_t *bar_drain = bar_afull + 3;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sbase + Ls.misc);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(sbase + Ls.misc + 4);
-    float *slab = args.slab + (size_t)blockIdx.x * G * (4 + 2 * ((a.D + 3) & ~3));
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long long budget = a.wait_cycles;
-    const int DP = (D + 3) & ~3, SP = 4 + 2 * DP;     // padded slab row
     const int64_t ntiles = (a.N + kTM - 1) / kTM;
     const int64_t t0 = ntiles * blockIdx.x / gridDim.x, t1 = ntiles * (blockIdx.x + 1) / gridDim.x;
     const int T = (int)(t1 - t0);
 
-    // FP32 sample tile `tile` -> X buffer b (cp.async, one commit group per call)
-    auto load_x = [&](int64_t tile, int b) {
-        const int64_t i0 = tile * kTM;
-        const int rows = (int)min((int64_t)kTM, a.N - i0);
-        const uint32_t bytes = (uint32_t)rows * D * 4u;
-        const char *src = reinterpret_cast<const char *>(a.X + i0 * D);
-        const uint32_t dst = smem_u32(sbase + Ls.X + b * Ls.xbytes);
-        uint32_t done = 0;
-        if (args.x_al16) {
-            const uint32_t n16 = bytes >> 4;
-            for (uint32_t k = tid; k < n16; k += kEpiThreads) cp_async16(dst + 16u * k, src + 16u * k);
-            done = n16 << 4;
-        }
-        for (uint32_t k = done / 4u + tid; k < bytes / 4u; k += kEpiThreads) cp_async4(dst + 4u * k, src + 4u * k);
-        cp_async_commit();
-    };
     // BF16 operand A of tile `tile` -> A buffer b: row r = [x'^2 | x'] (K blocks 0 | 1), warp per row
     auto build_a = [&](int64_t tile, int b) {
         const int64_t i0 = tile * kTM;
         unsigned char *ab = sA + b * (kTM * 256);
-#pragma unroll
+#pragma unroll 4
         for (int i = 0; i < kTM / 8; ++i) {
             const int r = warp + 8 * i;
             const bool v = i0 + r < a.N;
@@ -352,7 +281,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_em_pass_tc(TcArgs args)
         tmem_alloc(tmem_slot, 512);
         tmem_relinquish();
     } else {
-        for (int k = tid; k < G * SP; k += kEpiThreads) slab[k] = 0.f;
         for (int k = tid; k < NG * 16; k += kEpiThreads) {
             const int g = k >> 4, kb = (k >> 3) & 1, c = k & 7;
             uint4 v = make_uint4(0u, 0u, 0u, 0u);
@@ -373,18 +301,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_em_pass_tc(TcArgs args)
     }
     __syncthreads();   // centre in place for the first A
     if (warp < 8 && T > 0) {
-        load_x(t0, 0);
         build_a(t0, 0);
         fence_proxy_async();
     }
-    __threadfence();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     if (tid == 0 && T > 0) mbar_arrive(bar_afull);
 
-    double ll = 0.0;
     unsigned long long st_kept = 0, st_dense = 0, st_n = 0;
     unsigned long long tp[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // phase cycles (thread 0, profiling only)
     long long tmark = clock64();
@@ -423,17 +348,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_em_pass_tc(TcArgs args)
         const int q = warp & 3, h = warp >> 2;
         const int s = 32 * q + lane;            // this thread's sample in the tile (TMEM lane)
         const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);
+        uint8_t *my = cg + tid * kCap;
         for (int t = 0; t < T; ++t) {
             const int64_t tile = t0 + t;
             const int64_t i0 = tile * kTM;
             const int nvalid = (int)min((int64_t)kTM, a.N - i0);
-            // ---- prefetch the next tile: FP32 rows (async) and its BF16 operand
+            // ---- the next tile's BF16 operand
             if (t + 1 < T) {
-                load_x(tile + 1, (t + 1) & 1);
                 build_a(tile + 1, (t + 1) & 1);
                 fence_proxy_async();
-            } else {
-                cp_async_commit();
             }
             phase(0);
             epi_sync();
@@ -473,11 +396,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_em_pass_tc(TcArgs args)
             epi_sync();
             if (tid == 0) mbar_arrive(bar_lfree);
             lo = fmaxf(xlo[s], xlo[kTM + s]);
-            // ---- pass 2: candidate list of this (sample, half)
+            // ---- pass 2: candidate list of this (sample, half) -> global
             const float thr = lo - args.screen;
             const int gend = G - 128 * h;   // only real Gaussians (also when every bound is NaN/-inf)
             int n = 0;
-            uint8_t *my = cg + tid * kCap;
 #pragma unroll
             for (int j = 0; j < 128; ++j) {
                 if (j < gend && ub[j] >= thr) {
@@ -485,159 +407,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_em_pass_tc(TcArgs args)
                     ++n;
                 }
             }
-            if (s >= nvalid) n = 0;
-            cn[tid] = n;
-            if (s < nvalid) { st_n += (h == 0); st_kept += (unsigned long long)n; st_dense += n > kCap; }
-            cp_async_wait1();   // this tile's FP32 rows have landed
-            epi_sync();
+            if (s < nvalid) {
+                const int64_t rec = (i0 + s) * 2 + h;
+                args.L.cnt[rec] = (uint8_t)min(n, 255);
+                if (n > 0 && n <= kCap)
+                    reinterpret_cast<uint4 *>(args.L.cand)[rec] = *reinterpret_cast<const uint4 *>(my);
+                st_n += (h == 0);
+                st_kept += (unsigned long long)n;
+                st_dense += n > kCap;
+            }
             phase(4);
-            const float *xt = sX + (t & 1) * (Ls.xbytes / 4u);
-            // ---- exact log-densities: one warp per (sample, candidate), kNB
-            // candidates at a time so that their parameter rows load together
-            const int my_n = cn[32 * warp + lane];
-            const unsigned dense_mask = __ballot_sync(0xffffffffu, my_n > kCap);
-            for (int r = 0; r < kCap; ++r) {
-                unsigned mask = __ballot_sync(0xffffffffu, my_n > r && my_n <= kCap);
-                while (mask) {
-                    int jj[kNB], gg[kNB];
-                    bool vv[kNB];
-#pragma unroll
-                    for (int u = 0; u < kNB; ++u) {
-                        vv[u] = mask != 0u;
-                        jj[u] = vv[u] ? __ffs(mask) - 1 : 0;
-                        if (vv[u]) mask &= mask - 1u;
-                        gg[u] = vv[u] ? 128 * h + cg[(32 * warp + jj[u]) * kCap + r] : 0;
-                    }
-                    float2 pp[kNB][2];
-                    float cc = 0.f;
-#pragma unroll
-                    for (int u = 0; u < kNB; ++u) {
-                        if (lane == u && vv[u]) cc = __ldg(a.op.c + gg[u]);
-#pragma unroll
-                        for (int hh = 0; hh < 2; ++hh) {
-                            const int d = lane + 32 * hh;
-                            pp[u][hh] = (vv[u] && d < D) ? __ldg(a.op.sm + (size_t)gg[u] * D + d) : make_float2(0.f, 0.f);
-                        }
-                    }
-                    float acc[kNB];
-#pragma unroll
-                    for (int u = 0; u < kNB; ++u) {
-                        const float *x = xt + (32 * q + jj[u]) * D;
-                        acc[u] = 0.f;
-#pragma unroll
-                        for (int hh = 0; hh < 2; ++hh) {
-                            const int d = lane + 32 * hh;
-                            if (vv[u] && d < D) {
-                                const float tt = fmaf(x[d], pp[u][hh].x, -pp[u][hh].y);
-                                acc[u] = fmaf(tt, tt, acc[u]);
-                            }
-                        }
-                    }
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-                        for (int u = 0; u < kNB; ++u) acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], o);
-                    // lane u writes candidate u (all lanes hold every reduced sum)
-#pragma unroll
-                    for (int u = 0; u < kNB; ++u)
-                        if (lane == u && vv[u]) cl[(32 * warp + jj[u]) * kCap + r] = fmaf(-0.5f, acc[u], cc);
-                }
-            }
-            // dense slots (candidate list overflowed): lanes over Gaussians
-            for (unsigned dm = dense_mask; dm; dm &= dm - 1u) {
-                const int j = __ffs(dm) - 1;
-                const float *x = xt + (32 * q + j) * D;
-                float m = -INFINITY, sm = 0.f;
-                const int ge = min(G, 128 * h + 128);
-                for (int g = 128 * h + lane; g < ge; g += 32) {
-                    const float l = thread_logit(x, a.op.sm + (size_t)g * D, __ldg(a.op.c + g), D);
-                    if (l > m) { sm = sm * __expf(m - l) + 1.f; m = l; }
-                    else sm += __expf(l - m);
-                }
-                const float M = warp_max_f(m);
-                sm = (m == -INFINITY) ? 0.f : sm * __expf(m - M);
-                sm = warp_sum_f(sm);
-                if (lane == 0) dms[32 * warp + j] = make_float2(M, sm);
-            }
-            phase(5);
-            epi_sync();
-            // ---- log-sum-exp per sample over both halves' candidates (Eqs. 16-18)
-            float mh = -INFINITY, sh = 0.f;
-            const float *myl = cl + tid * kCap;
-            if (n <= kCap) {
-                for (int k = 0; k < n; ++k) mh = fmaxf(mh, myl[k]);
-                for (int k = 0; k < n; ++k) sh += __expf(myl[k] - mh);
-            } else {
-                const float2 v = dms[tid];
-                mh = v.x;
-                sh = v.y;
-            }
-            xms[tid] = make_float2(mh, sh);
-            epi_sync();
-            const float2 o = xms[(1 - h) * kTM + s];
-            const float M = fmaxf(mh, o.x);
-            const float Ssum = (mh == -INFINITY ? 0.f : sh * __expf(mh - M)) + (o.x == -INFINITY ? 0.f : o.y * __expf(o.x - M));
-            const float lse = M + logf(Ssum);
-            if (s < nvalid && h == 0) {
-                ll += (double)lse;
-                slse[s] = lse;
-            }
-            if (n <= kCap)
-                for (int k = 0; k < n; ++k) cl[tid * kCap + k] = __expf(myl[k] - lse);   // Eq. 3
-            epi_sync();
-            // ---- M-step accumulation: one warp per (sample, candidate), kNB at a
-            // time; the shift comes from the BF16 operand in shared memory
-            for (int r = 0; r < kCap; ++r) {
-                unsigned mask = __ballot_sync(0xffffffffu, my_n > r && my_n <= kCap);
-                while (mask) {
-#pragma unroll
-                    for (int u = 0; u < kNB; ++u) {
-                        if (!mask) break;
-                        const int j = __ffs(mask) - 1;
-                        mask &= mask - 1u;
-                        const int slot = 32 * warp + j;
-                        const int g = 128 * h + cg[slot * kCap + r];
-                        const float gm = cl[slot * kCap + r];
-                        if (gm > 0.f)
-                            smem_accumulate(slab + (size_t)g * SP, xt + (32 * q + j) * D, sB, NG, g, ctr, gm, D, DP, lane);
-                    }
-                }
-            }
-            for (unsigned dm = dense_mask; dm; dm &= dm - 1u) {
-                const int j = __ffs(dm) - 1;
-                const float *x = xt + (32 * q + j) * D;
-                const float ls = slse[32 * q + j];
-                const int ge = min(G, 128 * h + 128);
-                for (int g0 = 128 * h; g0 < ge; g0 += 32) {
-                    const int g = g0 + lane;
-                    const float gml = g < ge ? __expf(thread_logit(x, a.op.sm + (size_t)g * D, __ldg(a.op.c + g), D) - ls) : 0.f;
-                    unsigned live = __ballot_sync(0xffffffffu, gml > 0.f);
-                    while (live) {
-                        const int src = __ffs(live) - 1;
-                        live &= live - 1u;
-                        const float gmv = __shfl_sync(0xffffffffu, gml, src);
-                        smem_accumulate(slab + (size_t)(g0 + src) * SP, x, sB, NG, g0 + src, ctr, gmv, D, DP, lane);
-                    }
-                }
-            }
-            phase(6);
-            epi_sync();
-            phase(7);
         }
         tc_fence_before();
     }
-    __threadfence();
     __syncthreads();
-    // ---- the CTA's statistics (FP32 slab in L2) -> its FP64 partial
-    if (warp < 8) {
-        double *P = a.partial + (size_t)blockIdx.x * G * S;
-        for (int k = tid; k < G * S; k += kEpiThreads) {
-            const int g = k / S, j = k - g * S;
-            const int src = j == 0 ? 0 : (j <= D ? 4 + 2 * (j - 1) : 4 + 2 * (j - 1 - D) + 1);
-            P[k] = (double)__ldcg(slab + (size_t)g * SP + src);
-        }
-    }
-    double *red = reinterpret_cast<double *>(sbase + Ls.cl);   // candidate storage is free now
     if (a.screen_stats && warp < 8) {
         for (int o = 16; o > 0; o >>= 1) {
             st_n += __shfl_xor_sync(0xffffffffu, st_n, o);
@@ -652,22 +435,315 @@ __global__ void __launch_bounds__(kThreads, 1) k_em_pass_tc(TcArgs args)
         if (tid == 0)
             for (int k = 0; k < 8; ++k) atomicAdd(a.screen_stats + 3 + k, tp[k]);
     }
-    for (int o = 16; o > 0; o >>= 1) ll += __shfl_xor_sync(0xffffffffu, ll, o);
-    if (lane == 0) red[warp] = ll;
-    __syncthreads();
-    if (tid == 0) {
-        double tot = 0.0;
-        for (int w = 0; w < 9; ++w) tot += red[w];
-        a.ll_partial[blockIdx.x] = tot;
-        if (*abort_flag) {
-            if (atomicCAS(&a.status->code, 0, (int)GMM_ERR_TIMEOUT) == 0) a.status->fail_iter = a.iter;
-            atomicExch(&a.status->halt, 1);
-        }
+    if (tid == 0 && *abort_flag) {
+        if (atomicCAS(&a.status->code, 0, (int)GMM_ERR_TIMEOUT) == 0) a.status->fail_iter = a.iter;
+        atomicExch(&a.status->halt, 1);
     }
     if (warp == 8) {
         tc_fence_after();
         tmem_dealloc(tmem, 512);
     }
+}
+
+// ------------------------------------------------------------------------
+// 2. Exact log-densities, log-sum-exp and responsibilities of the screened
+// candidates.  One CTA per SM, the FP32 operands (s, mu s) and c in shared
+// memory; each warp takes one sample at a time, lanes over dimensions
+// (D <= 64: dimensions lane and lane + 32).  Lane L of the warp holds the
+// candidate in slot L & 15 of half L >> 4.
+// ------------------------------------------------------------------------
+__global__ void __launch_bounds__(kExThreads, 1) k_em_exact(EmPassArgs a, TcLists L)
+{
+    extern __shared__ __align__(16) unsigned char ex_raw[];
+    if (skip_block(a.status, a.iter)) return;
+    const int D = a.D, G = a.G;
+    float2 *psm = reinterpret_cast<float2 *>(ex_raw);                  // [G][D]
+    float *pc = reinterpret_cast<float *>(psm + (size_t)G * D);        // [G]
+    float *xbuf = pc + ((G + 3) & ~3);                                 // [32 warps][64]
+    __shared__ double s_ll[32];
+    for (int k = threadIdx.x; k < G * D; k += blockDim.x) psm[k] = __ldg(a.op.sm + k);
+    for (int g = threadIdx.x; g < G; g += blockDim.x) pc[g] = __ldg(a.op.c + g);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *xw = xbuf + warp * 64;
+    const int64_t lo = a.N * blockIdx.x / gridDim.x, hi = a.N * (blockIdx.x + 1) / gridDim.x;
+    double ll = 0.0;
+    for (int64_t i = lo + warp; i < hi; i += kExThreads / 32) {
+        const float *row = a.X + i * D;
+        const float x0 = lane < D ? __ldg(row + lane) : 0.f;
+        const float x1 = lane + 32 < D ? __ldg(row + 32 + lane) : 0.f;
+        const int hL = lane >> 4, k = lane & 15;
+        const int cnt2 = *reinterpret_cast<const uint16_t *>(L.cnt + 2 * i);
+        const int n0 = cnt2 & 255, n1 = cnt2 >> 8;
+        const int nh = hL ? n1 : n0;
+        const bool valid = nh <= kCap && k < nh;
+        const int g = valid ? 128 * hL + L.cand[i * 32 + lane] : 0;
+        float logit = -INFINITY;
+        unsigned mask = __ballot_sync(0xffffffffu, valid);
+        while (mask) {
+            int src[4], gg[4];
+            bool vv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                vv[u] = mask != 0u;
+                src[u] = vv[u] ? __ffs(mask) - 1 : 0;
+                if (vv[u]) mask &= mask - 1u;
+                gg[u] = __shfl_sync(0xffffffffu, g, src[u]);
+            }
+            float acc[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float2 *p = psm + (size_t)gg[u] * D;
+                float r = 0.f;
+                if (lane < D) { const float2 q = p[lane]; const float t = fmaf(x0, q.x, -q.y); r = t * t; }
+                if (lane + 32 < D) { const float2 q = p[lane + 32]; const float t = fmaf(x1, q.x, -q.y); r = fmaf(t, t, r); }
+                acc[u] = r;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], o);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (vv[u] && lane == src[u]) logit = fmaf(-0.5f, acc[u], pc[gg[u]]);
+        }
+        // dense halves (more than kCap candidates): every Gaussian of the
+        // half, lanes over Gaussians, online max / sum of exp per lane
+        float dm = -INFINITY, ds = 0.f;
+        if (n0 > kCap || n1 > kCap) {
+            if (lane < D) xw[lane] = x0;
+            if (lane + 32 < D) xw[lane + 32] = x1;
+            __syncwarp();
+            for (int hh = 0; hh < 2; ++hh) {
+                if ((hh ? n1 : n0) <= kCap) continue;
+                const int ge = min(G, 128 * hh + 128);
+                for (int gd = 128 * hh + lane; gd < ge; gd += 32) {
+                    const float2 *p = psm + (size_t)gd * D;
+                    float r = 0.f;
+                    for (int d = 0; d < D; ++d) {
+                        const float2 q = p[d];
+                        const float t = fmaf(xw[d], q.x, -q.y);
+                        r = fmaf(t, t, r);
+                    }
+                    const float l = fmaf(-0.5f, r, pc[gd]);
+                    if (l > dm) { ds = ds * __expf(dm - l) + 1.f; dm = l; }
+                    else ds += __expf(l - dm);
+                }
+            }
+            __syncwarp();
+        }
+        // log-sum-exp over the candidates and the dense halves (Eqs. 16-18)
+        const float M = warp_max_f(fmaxf(logit, dm));
+        float e = (logit == -INFINITY) ? 0.f : __expf(logit - M);
+        if (dm != -INFINITY) e += ds * __expf(dm - M);
+        const float lse = M + logf(warp_sum_f(e));
+        if (valid) L.gam[i * 32 + lane] = __expf(logit - lse);   // Eq. 3
+        if (lane == 0) {
+            L.lse[i] = lse;
+            ll += (double)lse;
+        }
+    }
+    if (lane == 0) s_ll[warp] = ll;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < kExThreads / 32; ++w) tot += s_ll[w];
+        a.ll_partial[blockIdx.x] = tot;
+    }
+}
+
+// ------------------------------------------------------------------------
+// 3. M-step statistics from the responsibility lists.  CTA b handles
+// sample chunk b / 2 and half b % 2 of the Gaussians (at most 128).
+// Shared memory: the chunk's FP32 statistics [128][1 + 2D] (S0 | S1_d |
+// S2_d, shifted by mu_f), the per-tile bins of the counting sort.
+// ------------------------------------------------------------------------
+struct MsSmem {
+    uint32_t slab, cnt, off, fill, pairs, scand, sn, dl, dn, xw, total;
+};
+
+__host__ __device__ inline MsSmem ms_layout(int D)
+{
+    MsSmem L;
+    uint32_t o = 0;
+    L.slab = o; o += 4u * 128u * (uint32_t)(1 + 2 * D);
+    L.cnt = o; o += 4u * 128u;
+    L.off = o; o += 4u * 132u;
+    L.fill = o; o += 4u * 128u;
+    L.scand = o; o += 16u * kMsTile;
+    L.pairs = o; o += 2u * kMsTile * kCap;
+    L.sn = o; o += (uint32_t)kMsTile;
+    L.dl = o; o += 4u * kMsTile;
+    L.dn = o; o += 16u;
+    L.xw = o; o += 4u * 64u;
+    L.total = o;
+    return L;
+}
+
+__global__ void __launch_bounds__(kMsThreads, 2) k_em_mstep_lists(EmPassArgs a, TcLists L)
+{
+    extern __shared__ __align__(16) unsigned char ms_raw[];
+    if (skip_block(a.status, a.iter)) return;
+    const int D = a.D, G = a.G, S = 1 + 2 * D;
+    const int h = blockIdx.x & 1, chunk = blockIdx.x >> 1, nchunks = gridDim.x >> 1;
+    const int GH = max(0, min(128, G - 128 * h));
+    if (GH == 0) return;
+    const MsSmem Ls = ms_layout(D);
+    float *slab = reinterpret_cast<float *>(ms_raw + Ls.slab);
+    int *bcnt = reinterpret_cast<int *>(ms_raw + Ls.cnt);
+    int *boff = reinterpret_cast<int *>(ms_raw + Ls.off);
+    int *bfill = reinterpret_cast<int *>(ms_raw + Ls.fill);
+    uint4 *scand = reinterpret_cast<uint4 *>(ms_raw + Ls.scand);
+    uint16_t *pairs = reinterpret_cast<uint16_t *>(ms_raw + Ls.pairs);
+    uint8_t *sn = reinterpret_cast<uint8_t *>(ms_raw + Ls.sn);
+    int *dl = reinterpret_cast<int *>(ms_raw + Ls.dl);
+    int *dn = reinterpret_cast<int *>(ms_raw + Ls.dn);
+    float *xw = reinterpret_cast<float *>(ms_raw + Ls.xw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int k = tid; k < 128 * S; k += kMsThreads) slab[k] = 0.f;
+    const int64_t lo = a.N * chunk / nchunks, hi = a.N * (chunk + 1) / nchunks;
+    const uint8_t *ccnt = L.cnt;
+    for (int64_t i0 = lo; i0 < hi; i0 += kMsTile) {
+        const int nt = (int)min((int64_t)kMsTile, hi - i0);
+        if (tid < 128) { bcnt[tid] = 0; bfill[tid] = 0; }
+        if (tid == 0) *dn = 0;
+        __syncthreads();
+        // ---- this half's list of each sample of the tile; histogram by Gaussian
+        if (tid < nt) {
+            const int64_t rec = (i0 + tid) * 2 + h;
+            const int n = ccnt[rec];
+            sn[tid] = (uint8_t)n;
+            if (n > kCap) {
+                dl[atomicAdd(dn, 1)] = tid;
+            } else if (n > 0) {
+                scand[tid] = reinterpret_cast<const uint4 *>(L.cand)[rec];
+                const uint8_t *cb = reinterpret_cast<const uint8_t *>(scand + tid);
+                for (int k = 0; k < n; ++k) atomicAdd(&bcnt[cb[k]], 1);
+            }
+        }
+        __syncthreads();
+        // ---- exclusive scan of the 128 bins (warp 0, four bins per lane)
+        if (warp == 0) {
+            const int4 v = reinterpret_cast<const int4 *>(bcnt)[lane];
+            const int tot = v.x + v.y + v.z + v.w;
+            int inc = tot;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            const int ex = inc - tot;
+            boff[4 * lane] = ex;
+            boff[4 * lane + 1] = ex + v.x;
+            boff[4 * lane + 2] = ex + v.x + v.y;
+            boff[4 * lane + 3] = ex + v.x + v.y + v.z;
+            if (lane == 31) boff[128] = inc;
+        }
+        __syncthreads();
+        // ---- scatter the pairs (sample << 4 | slot) into their bins
+        if (tid < nt) {
+            const int n = sn[tid];
+            if (n > 0 && n <= kCap) {
+                const uint8_t *cb = reinterpret_cast<const uint8_t *>(scand + tid);
+                for (int k = 0; k < n; ++k) {
+                    const int gl = cb[k];
+                    pairs[boff[gl] + atomicAdd(&bfill[gl], 1)] = (uint16_t)((tid << 4) | k);
+                }
+            }
+        }
+        __syncthreads();
+        // ---- warp w owns Gaussians w, w + 16, ...: sums in registers, then
+        // one read-modify-write of its rows of the CTA's statistics
+        for (int gl = warp; gl < GH; gl += kMsThreads / 32) {
+            const int pb = boff[gl], pe = boff[gl + 1];
+            if (pb == pe) continue;
+            const int g = 128 * h + gl;
+            const float m0 = lane < D ? __ldg(a.op.mu + (size_t)g * D + lane) : 0.f;
+            const float m1 = lane + 32 < D ? __ldg(a.op.mu + (size_t)g * D + 32 + lane) : 0.f;
+            float s0 = 0.f, a1 = 0.f, a2 = 0.f, b1 = 0.f, b2 = 0.f;
+            for (int p = pb; p < pe; ++p) {
+                const int pr = pairs[p];
+                const int64_t i = i0 + (pr >> 4);
+                const float gm = __ldg(L.gam + i * 32 + 16 * h + (pr & 15));
+                const float *row = a.X + i * D;
+                if (lane < D) {
+                    const float u = __ldg(row + lane) - m0;
+                    const float v = gm * u;
+                    a1 += v;
+                    a2 = fmaf(v, u, a2);
+                }
+                if (lane + 32 < D) {
+                    const float u = __ldg(row + 32 + lane) - m1;
+                    const float v = gm * u;
+                    b1 += v;
+                    b2 = fmaf(v, u, b2);
+                }
+                s0 += gm;
+            }
+            float *sg = slab + (size_t)gl * S;
+            if (lane == 0) sg[0] += s0;
+            if (lane < D) { sg[1 + lane] += a1; sg[1 + D + lane] += a2; }
+            if (lane + 32 < D) { sg[33 + lane] += b1; sg[33 + D + lane] += b2; }
+        }
+        __syncthreads();
+        // ---- dense (sample, half) records: warp 0 recomputes every
+        // Gaussian of the half exactly and adds the responsibilities > 0
+        if (warp == 0) {
+            const int nd = *dn;
+            for (int r = 0; r < nd; ++r) {
+                const int64_t i = i0 + dl[r];
+                const float *row = a.X + i * D;
+                const float x0 = lane < D ? __ldg(row + lane) : 0.f;
+                const float x1 = lane + 32 < D ? __ldg(row + 32 + lane) : 0.f;
+                if (lane < D) xw[lane] = x0;
+                if (lane + 32 < D) xw[lane + 32] = x1;
+                __syncwarp();
+                const float ls = __ldg(L.lse + i);
+                for (int gb = 0; gb < GH; gb += 32) {
+                    const int gl = gb + lane;
+                    float gm = 0.f;
+                    if (gl < GH) {
+                        const float2 *p = a.op.sm + (size_t)(128 * h + gl) * D;
+                        float acc = 0.f;
+                        for (int d = 0; d < D; ++d) {
+                            const float2 q = __ldg(p + d);
+                            const float t = fmaf(xw[d], q.x, -q.y);
+                            acc = fmaf(t, t, acc);
+                        }
+                        gm = __expf(fmaf(-0.5f, acc, __ldg(a.op.c + 128 * h + gl)) - ls);
+                    }
+                    unsigned live = __ballot_sync(0xffffffffu, gm > 0.f);
+                    while (live) {
+                        const int src = __ffs(live) - 1;
+                        live &= live - 1u;
+                        const float gv = __shfl_sync(0xffffffffu, gm, src);
+                        const int gg = gb + src;
+                        const size_t gidx = (size_t)(128 * h + gg) * D;
+                        float *sg = slab + (size_t)gg * S;
+                        if (lane < D) {
+                            const float u = x0 - __ldg(a.op.mu + gidx + lane);
+                            const float v = gv * u;
+                            sg[1 + lane] += v;
+                            sg[1 + D + lane] = fmaf(v, u, sg[1 + D + lane]);
+                        }
+                        if (lane + 32 < D) {
+                            const float u = x1 - __ldg(a.op.mu + gidx + 32 + lane);
+                            const float v = gv * u;
+                            sg[33 + lane] += v;
+                            sg[33 + D + lane] = fmaf(v, u, sg[33 + D + lane]);
+                        }
+                        if (lane == 0) sg[0] += gv;
+                        __syncwarp();
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+    }
+    // ---- the chunk's statistics of this half -> its FP64 partial
+    double *P = a.partial + ((size_t)chunk * G + 128 * h) * S;
+    for (int k = tid; k < GH * S; k += kMsThreads) P[k] = (double)slab[k];
 }
 
 }  // namespace
@@ -679,22 +755,48 @@ bool em_tc_supported(int32_t D, int32_t G)
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    return tc_layout(D, G, NG).total + 1024u + 64u <= (uint32_t)optin;
+    const size_t ex = (size_t)G * D * 8u + 4u * (size_t)((G + 3) & ~3) + 32u * 64u * 4u;
+    return tc_layout(NG).total + 1024u + 64u <= (uint32_t)optin && ex <= (size_t)optin &&
+           ms_layout(D).total <= (uint32_t)optin;
 }
 
 int em_tc_grid(int sms) { return sms; }
 
-size_t em_tc_slab_floats(int32_t D, int32_t G, int grid) { return (size_t)grid * G * (4 + 2 * ((D + 3) & ~3)); }
+size_t em_tc_list_bytes(int64_t N) { return (size_t)N * (32u + 2u + 128u + 4u) + 1024u; }
 
-cudaError_t launch_em_pass_tc(const EmPassArgs &a, float *slab, int32_t grid, cudaStream_t s)
+TcLists em_tc_lists(void *base, int64_t N)
 {
-    TcArgs t{a, slab, (a.G + 15) / 16 * 16, (a.D + 15) / 16, (reinterpret_cast<uintptr_t>(a.X) & 15u) == 0,
-             (float)std::log((double)a.N * 1e9)};
-    const size_t sm = tc_layout(a.D, a.G, t.NG).total + 1024u;
-    cudaError_t e = cudaFuncSetAttribute(k_em_pass_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    unsigned char *p = static_cast<unsigned char *>(base);
+    TcLists L;
+    L.gam = reinterpret_cast<float *>(p);                 // [N][2][16] FP32 (16-byte aligned rows)
+    p += (size_t)N * 128u;
+    L.cand = p;                                           // [N][2][16] Gaussian index within the half
+    p += (size_t)N * 32u;
+    L.lse = reinterpret_cast<float *>(p);                 // [N]
+    p += (size_t)N * 4u;
+    L.cnt = p;                                            // [N][2] candidates (> kTcCap: dense)
+    return L;
+}
+
+cudaError_t launch_em_pass_tc(const EmPassArgs &a, const TcLists &L, int32_t grid, int32_t ms_chunks, cudaStream_t s)
+{
+    TcArgs t{a, L, (a.G + 15) / 16 * 16, (a.D + 15) / 16, (float)std::log((double)a.N * 1e9)};
+    const size_t sm1 = tc_layout(t.NG).total + 1024u;
+    cudaError_t e = cudaFuncSetAttribute(k_em_screen_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
     if (e != cudaSuccess) return e;
-    k_em_pass_tc<<<grid, kThreads, sm, s>>>(t);
-    count_launches(1);
+    k_em_screen_tc<<<grid, kThreads, sm1, s>>>(t);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const size_t sm2 = (size_t)a.G * a.D * 8u + 4u * (size_t)((a.G + 3) & ~3) + 32u * 64u * 4u;
+    if ((e = cudaFuncSetAttribute(k_em_exact, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2)) != cudaSuccess)
+        return e;
+    k_em_exact<<<grid, kExThreads, sm2, s>>>(a, L);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const size_t sm3 = ms_layout(a.D).total;
+    if ((e = cudaFuncSetAttribute(k_em_mstep_lists, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3)) !=
+        cudaSuccess)
+        return e;
+    k_em_mstep_lists<<<2 * ms_chunks, kMsThreads, sm3, s>>>(a, L);
+    count_launches(3);
     return cudaGetLastError();
 }
 

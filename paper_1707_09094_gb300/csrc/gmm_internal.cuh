@@ -184,9 +184,17 @@ cudaError_t init_net_run(InitNet *n, const float *pts, int B, int P, const doubl
                          double *loss_host, cudaStream_t s);
 
 // ---- launchers implemented in gmm_em_tc.cu
+constexpr int kTcCap = 16;   // candidates per (sample, half of the Gaussians) before the dense fallback
+struct TcLists {             // per-sample records between the three kernels of the tensor-core pass
+    float *gam;              // [N][2][kTcCap] responsibilities of the candidates
+    uint8_t *cand;           // [N][2][kTcCap] candidate Gaussian (index within its half)
+    float *lse;              // [N] log p(x_i)
+    uint8_t *cnt;            // [N][2] candidates per half (> kTcCap: every Gaussian of the half)
+};
 bool em_tc_supported(int32_t D, int32_t G);
 int em_tc_grid(int sms);
-size_t em_tc_slab_floats(int32_t D, int32_t G, int grid);
-cudaError_t launch_em_pass_tc(const EmPassArgs &a, float *slab, int32_t grid, cudaStream_t s);
+size_t em_tc_list_bytes(int64_t N);
+TcLists em_tc_lists(void *base, int64_t N);
+cudaError_t launch_em_pass_tc(const EmPassArgs &a, const TcLists &L, int32_t grid, int32_t ms_chunks, cudaStream_t s);
 
 }  // namespace gmm
