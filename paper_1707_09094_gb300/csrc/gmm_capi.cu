@@ -304,7 +304,7 @@ gmm_status run_em(gmm_model *m, const float *Xd, int64_t N, int32_t em_iter, dou
     const int n_llp = two_phase ? (int)((N + 127) / 128) : grid;
     CK(grow(m->partial, m->partial_cap, (size_t)grid * G * S));
     if (two_phase) CK(grow(m->lse, m->lse_cap, (size_t)N));
-    if (tc) CK(grow(m->tclist, m->tclist_cap, gmm::em_tc_list_bytes(N)));
+    if (tc) CK(grow(m->tclist, m->tclist_cap, gmm::em_tc_list_bytes(N, grid)));
     CK(grow(m->llp, m->llp_cap, (size_t)n_llp));
     CK(grow(m->lld, m->lld_cap, (size_t)(em_iter > 0 ? em_iter : 1)));
     CK(gmm::launch_status_reset(m->status, s));
@@ -317,7 +317,7 @@ gmm_status run_em(gmm_model *m, const float *Xd, int64_t N, int32_t em_iter, dou
         size_t slot = 0;
         gmm_status prc = prof_begin(m, s, &slot);
         if (prc != GMM_OK) return prc;
-        if (tc) CK(gmm::launch_em_pass_tc(pa, gmm::em_tc_lists(m->tclist, N), grid, grid, s));
+        if (tc) CK(gmm::launch_em_pass_tc(pa, gmm::em_tc_lists(m->tclist, N, grid), grid, grid, s));
         else if (two_phase) CK(gmm::launch_em_two_phase(pa, m->lse, grid, s));
         else CK(gmm::launch_em_pass_simt(pa, grid, s));
         if ((prc = prof_end(m, s, slot)) != GMM_OK) return prc;

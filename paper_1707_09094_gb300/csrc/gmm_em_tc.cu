@@ -46,8 +46,7 @@ constexpr int kTM = 128;          // samples per tile = MMA M
 constexpr int kCap = kTcCap;      // candidates per (sample, half) before the dense fallback
 constexpr float kK1 = 0.009765625f * 1.25f;   // 2^-7 * 1.25 (multiplies |P1|)
 constexpr int kExThreads = 1024;  // exact-recompute kernel: 32 warps, one sample per warp at a time
-constexpr int kMsThreads = 512;   // M-step kernel: 16 warps
-constexpr int kMsTile = 256;      // samples per M-step tile
+constexpr int kMsThreads = 1024;  // M-step kernel: 32 warps
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -169,12 +168,6 @@ __device__ __forceinline__ float warp_sum_f(float v)
     return v;
 }
 
-__device__ __forceinline__ float warp_max_f(float v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
 
 
 __device__ __forceinline__ bool skip_block(const DevStatus *st, int iter)
@@ -446,306 +439,695 @@ __global__ void __launch_bounds__(kThreads, 1) k_em_screen_tc(TcArgs args)
 }
 
 // ------------------------------------------------------------------------
-// 2. Exact log-densities, log-sum-exp and responsibilities of the screened
-// candidates.  One CTA per SM, the FP32 operands (s, mu s) and c in shared
-// memory; each warp takes one sample at a time, lanes over dimensions
-// (D <= 64: dimensions lane and lane + 32).  Lane L of the warp holds the
-// candidate in slot L & 15 of half L >> 4.
+// Bulk (untiled TMA) copies global -> shared, completing on an mbarrier.
+// Addresses 16-byte aligned, sizes multiples of 16 bytes.
 // ------------------------------------------------------------------------
-__global__ void __launch_bounds__(kExThreads, 1) k_em_exact(EmPassArgs a, TcLists L)
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
 {
-    extern __shared__ __align__(16) unsigned char ex_raw[];
-    if (skip_block(a.status, a.iter)) return;
-    const int D = a.D, G = a.G;
-    float2 *psm = reinterpret_cast<float2 *>(ex_raw);                  // [G][D]
-    float *pc = reinterpret_cast<float *>(psm + (size_t)G * D);        // [G]
-    float *xbuf = pc + ((G + 3) & ~3);                                 // [32 warps][64]
-    __shared__ double s_ll[32];
-    for (int k = threadIdx.x; k < G * D; k += blockDim.x) psm[k] = __ldg(a.op.sm + k);
-    for (int g = threadIdx.x; g < G; g += blockDim.x) pc[g] = __ldg(a.op.c + g);
-    __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float *xw = xbuf + warp * 64;
-    const int64_t lo = a.N * blockIdx.x / gridDim.x, hi = a.N * (blockIdx.x + 1) / gridDim.x;
-    double ll = 0.0;
-    for (int64_t i = lo + warp; i < hi; i += kExThreads / 32) {
-        const float *row = a.X + i * D;
-        const float x0 = lane < D ? __ldg(row + lane) : 0.f;
-        const float x1 = lane + 32 < D ? __ldg(row + 32 + lane) : 0.f;
-        const int hL = lane >> 4, k = lane & 15;
-        const int cnt2 = *reinterpret_cast<const uint16_t *>(L.cnt + 2 * i);
-        const int n0 = cnt2 & 255, n1 = cnt2 >> 8;
-        const int nh = hL ? n1 : n0;
-        const bool valid = nh <= kCap && k < nh;
-        const int g = valid ? 128 * hL + L.cand[i * 32 + lane] : 0;
-        float logit = -INFINITY;
-        unsigned mask = __ballot_sync(0xffffffffu, valid);
-        while (mask) {
-            int src[4], gg[4];
-            bool vv[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                vv[u] = mask != 0u;
-                src[u] = vv[u] ? __ffs(mask) - 1 : 0;
-                if (vv[u]) mask &= mask - 1u;
-                gg[u] = __shfl_sync(0xffffffffu, g, src[u]);
-            }
-            float acc[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const float2 *p = psm + (size_t)gg[u] * D;
-                float r = 0.f;
-                if (lane < D) { const float2 q = p[lane]; const float t = fmaf(x0, q.x, -q.y); r = t * t; }
-                if (lane + 32 < D) { const float2 q = p[lane + 32]; const float t = fmaf(x1, q.x, -q.y); r = fmaf(t, t, r); }
-                acc[u] = r;
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-                for (int u = 0; u < 4; ++u) acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], o);
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (vv[u] && lane == src[u]) logit = fmaf(-0.5f, acc[u], pc[gg[u]]);
-        }
-        // dense halves (more than kCap candidates): every Gaussian of the
-        // half, lanes over Gaussians, online max / sum of exp per lane
-        float dm = -INFINITY, ds = 0.f;
-        if (n0 > kCap || n1 > kCap) {
-            if (lane < D) xw[lane] = x0;
-            if (lane + 32 < D) xw[lane + 32] = x1;
-            __syncwarp();
-            for (int hh = 0; hh < 2; ++hh) {
-                if ((hh ? n1 : n0) <= kCap) continue;
-                const int ge = min(G, 128 * hh + 128);
-                for (int gd = 128 * hh + lane; gd < ge; gd += 32) {
-                    const float2 *p = psm + (size_t)gd * D;
-                    float r = 0.f;
-                    for (int d = 0; d < D; ++d) {
-                        const float2 q = p[d];
-                        const float t = fmaf(xw[d], q.x, -q.y);
-                        r = fmaf(t, t, r);
-                    }
-                    const float l = fmaf(-0.5f, r, pc[gd]);
-                    if (l > dm) { ds = ds * __expf(dm - l) + 1.f; dm = l; }
-                    else ds += __expf(l - dm);
-                }
-            }
-            __syncwarp();
-        }
-        // log-sum-exp over the candidates and the dense halves (Eqs. 16-18)
-        const float M = warp_max_f(fmaxf(logit, dm));
-        float e = (logit == -INFINITY) ? 0.f : __expf(logit - M);
-        if (dm != -INFINITY) e += ds * __expf(dm - M);
-        const float lse = M + logf(warp_sum_f(e));
-        if (valid) L.gam[i * 32 + lane] = __expf(logit - lse);   // Eq. 3
-        if (lane == 0) {
-            L.lse[i] = lse;
-            ll += (double)lse;
-        }
-    }
-    if (lane == 0) s_ll[warp] = ll;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double tot = 0.0;
-        for (int w = 0; w < kExThreads / 32; ++w) tot += s_ll[w];
-        a.ll_partial[blockIdx.x] = tot;
-    }
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
 }
 
-// ------------------------------------------------------------------------
-// 3. M-step statistics from the responsibility lists.  CTA b handles
-// sample chunk b / 2 and half b % 2 of the Gaussians (at most 128).
-// Shared memory: the chunk's FP32 statistics [128][1 + 2D] (S0 | S1_d |
-// S2_d, shifted by mu_f), the per-tile bins of the counting sort.
-// ------------------------------------------------------------------------
-struct MsSmem {
-    uint32_t slab, cnt, off, fill, pairs, scand, sn, dl, dn, xw, total;
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+constexpr int kST = 128;   // samples per staged tile of the exact and M-step kernels
+
+// A staged tile is copied by the bulk engine when it is a whole tile of a
+// 16-byte-aligned X; the last, partial tile (or an unaligned X) is copied by
+// the threads themselves.
+__device__ __forceinline__ bool tile_is_bulk(int64_t i0, int64_t N, int x_al16)
+{
+    return x_al16 && i0 + kST <= N;
+}
+
+// Bounded wait on a staged tile: true when it landed.  On expiry the status
+// word records GMM_ERR_TIMEOUT (the block then stops consuming tiles).
+__device__ __forceinline__ bool stage_wait(uint64_t *bar, uint32_t parity, long long budget, volatile int *abort_flag)
+{
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*abort_flag) return false;
+        if (clock64() - t0 > budget) { *abort_flag = 1; return false; }
+    }
+    return true;
+}
+
+struct ExArgs {
+    EmPassArgs a;
+    TcLists L;
+    float screen;     // ln(N * 1e9): responsibilities below exp(-screen) are dropped
+    int32_t x_al16;
+    int32_t wp;       // exact kernel: pair slots per warp (a multiple of 32)
 };
 
-__host__ __device__ inline MsSmem ms_layout(int D)
+struct ExSmem {
+    uint32_t ps, pm, pc, X[2], cand[2], cnt[2], wl, wg, ws, bars, misc, total;
+};
+
+// The operands s = 1/sigma and mu s are two [G][DS] arrays with an odd row
+// stride DS, so lanes reading different Gaussians at one d hit distinct banks.
+__host__ __device__ inline int ex_stride(int D) { return D | 1; }
+
+__host__ __device__ inline ExSmem ex_layout(int D, int G, int wp)
 {
-    MsSmem L;
+    ExSmem L;
+    const uint32_t DS = (uint32_t)ex_stride(D);
     uint32_t o = 0;
-    L.slab = o; o += 4u * 128u * (uint32_t)(1 + 2 * D);
-    L.cnt = o; o += 4u * 128u;
-    L.off = o; o += 4u * 132u;
-    L.fill = o; o += 4u * 128u;
-    L.scand = o; o += 16u * kMsTile;
-    L.pairs = o; o += 2u * kMsTile * kCap;
-    L.sn = o; o += (uint32_t)kMsTile;
-    L.dl = o; o += 4u * kMsTile;
-    L.dn = o; o += 16u;
-    L.xw = o; o += 4u * 64u;
+    L.ps = o; o += 4u * (uint32_t)G * DS;
+    L.pm = o; o += 4u * (uint32_t)G * DS;
+    L.pc = o; o += 4u * (uint32_t)G;
+    o = (o + 127u) & ~127u;
+    for (int b = 0; b < 2; ++b) {
+        L.X[b] = o; o += ((4u * kST * (uint32_t)D) + 127u) & ~127u;
+        L.cand[b] = o; o += 32u * kST;
+        L.cnt[b] = o; o += 2u * kST;
+    }
+    L.wl = o; o += 4u * 32u * (uint32_t)wp;
+    L.wg = o; o += 32u * (uint32_t)wp;
+    L.ws = o; o += 32u * (uint32_t)wp;
+    L.bars = o; o += 16u;
+    L.misc = o; o += 16u;
     L.total = o;
     return L;
 }
 
-__global__ void __launch_bounds__(kMsThreads, 2) k_em_mstep_lists(EmPassArgs a, TcLists L)
+// ------------------------------------------------------------------------
+// 2. Exact log-densities, log-sum-exp and responsibilities of the screened
+// candidates.  One CTA per SM owns a contiguous run of 128-sample tiles; the
+// FP32 operands (s, mu s) and c sit in shared memory, and each tile's
+// samples, candidate lists and counts are staged by bulk copies two tiles
+// ahead.  Warp w takes samples 4w..4w+3 of a tile, with no block barrier
+// inside the tile:
+//  * its (sample, Gaussian) pairs -- the screened candidates, or every
+//    Gaussian of a dense half -- one lane per pair, each lane the whole
+//    exact FP32 log-density over D (the formula of the CUDA-core form);
+//  * eight lanes per sample: log-sum-exp (Eqs. 16-18), log p(x_i) into the
+//    CTA's FP64 log-likelihood, and the pairs whose responsibility (Eq. 3)
+//    is at least exp(-screen) -- the screen's own bound: every dropped pair
+//    carries less than 1e-9 / N -- kept in pair order: the first kTcKeep in
+//    the sample's record, the rest in the CTA's spill list.
+// Four samples with more than kWarpPairs pairs (dense halves) are done one
+// sample at a time, lanes over dimensions, to the same results.
+// ------------------------------------------------------------------------
+__global__ void __launch_bounds__(kExThreads, 1) k_em_exact(ExArgs args)
 {
-    extern __shared__ __align__(16) unsigned char ms_raw[];
+    extern __shared__ __align__(128) unsigned char ex_raw[];
+    const EmPassArgs &a = args.a;
+    const TcLists &L = args.L;
+    if (skip_block(a.status, a.iter)) return;
+    const int D = a.D, G = a.G, DS = ex_stride(D);
+    const int WP = args.wp;
+    const ExSmem Ls = ex_layout(D, G, WP);
+    float *pss = reinterpret_cast<float *>(ex_raw + Ls.ps);
+    float *pms = reinterpret_cast<float *>(ex_raw + Ls.pm);
+    float *pc = reinterpret_cast<float *>(ex_raw + Ls.pc);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(ex_raw + Ls.bars);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(ex_raw + Ls.misc);
+    int *nspill = reinterpret_cast<int *>(ex_raw + Ls.misc + 4);
+    __shared__ double s_ll[32];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    float *wl = reinterpret_cast<float *>(ex_raw + Ls.wl) + warp * WP;
+    uint8_t *wg = ex_raw + Ls.wg + warp * WP;
+    uint8_t *wsm = ex_raw + Ls.ws + warp * WP;
+    const int64_t ntiles = (a.N + kST - 1) / kST;
+    const int64_t t0 = ntiles * blockIdx.x / gridDim.x, t1 = ntiles * (blockIdx.x + 1) / gridDim.x;
+    const float keep = -args.screen;
+    int64_t *sp_ig = L.sp_ig + (size_t)blockIdx.x * kTcSpill;
+    float *sp_gam = L.sp_gam + (size_t)blockIdx.x * kTcSpill;
+
+    auto issue = [&](int64_t tile, int b) {   // thread 0 only
+        const int64_t i0 = tile * kST;
+        const uint32_t xb = 4u * kST * (uint32_t)D;
+        const uint32_t bo = (uint32_t)b * (Ls.X[1] - Ls.X[0]);
+        fence_proxy_async();
+        mbar_expect_tx(bars + b, xb + 32u * kST + 2u * kST);
+        bulk_g2s(ex_raw + Ls.X[0] + bo, a.X + i0 * D, xb, bars + b);
+        bulk_g2s(ex_raw + Ls.cand[0] + bo, L.cand + i0 * 32, 32u * kST, bars + b);
+        bulk_g2s(ex_raw + Ls.cnt[0] + bo, L.cnt + i0 * 2, 2u * kST, bars + b);
+    };
+    // one kept pair of sample i at rank r (pair order): record slot or spill
+    auto put = [&](int64_t i, int r, int g, float gam, int spill_base, bool spill_ok) {
+        if (r < kTcKeep) {
+            L.gam[i * kTcKeep + r] = gam;
+            L.kg[i * kTcKeep + r] = (uint8_t)g;
+        } else if (spill_base >= 0) {
+            const int e = spill_base + r - kTcKeep;
+            if (e < kTcSpill) {
+                sp_ig[e] = i * 256 + g;
+                sp_gam[e] = spill_ok ? gam : 0.f;   // a failed reservation leaves null entries
+            }
+        }
+    };
+
+    if (tid == 0) {
+        mbar_init(bars, 1);
+        mbar_init(bars + 1, 1);
+        *abort_flag = 0;
+        *nspill = 0;
+        fence_mbar_init();
+    }
+    for (int k = tid; k < G * D; k += kExThreads) {
+        const int g = k / D, d = k - g * D;
+        const float2 v = __ldg(a.op.sm + k);
+        pss[g * DS + d] = v.x;
+        pms[g * DS + d] = v.y;
+    }
+    for (int g = tid; g < G; g += kExThreads) pc[g] = __ldg(a.op.c + g);
+    __syncthreads();
+    if (tid == 0)
+        for (int k = 0; k < 2 && t0 + k < t1; ++k)
+            if (tile_is_bulk((t0 + k) * kST, a.N, args.x_al16)) issue(t0 + k, k);
+    double ll = 0.0;
+    uint32_t use0 = 0u, use1 = 0u;
+    const int j8 = lane & 7, k8 = lane >> 3;     // eight lanes per sample in the finish step
+    for (int64_t t = t0; t < t1; ++t) {
+        const int b = (int)((t - t0) & 1);
+        const int64_t i0 = t * kST;
+        const int nv = (int)min((int64_t)kST, a.N - i0);
+        const uint32_t bo = (uint32_t)b * (Ls.X[1] - Ls.X[0]);
+        float *xs = reinterpret_cast<float *>(ex_raw + Ls.X[0] + bo);
+        uint8_t *cs = ex_raw + Ls.cand[0] + bo;
+        uint8_t *ns = ex_raw + Ls.cnt[0] + bo;
+        if (tile_is_bulk(i0, a.N, args.x_al16)) {
+            if (stage_wait(bars + b, (b ? use1 : use0) & 1u, a.wait_cycles, abort_flag)) {
+                if (b) ++use1; else ++use0;
+            }
+        } else {
+            for (int k = tid; k < nv * D; k += kExThreads) xs[k] = __ldg(a.X + i0 * D + k);
+            for (int k = tid; k < nv * 32; k += kExThreads) cs[k] = L.cand[i0 * 32 + k];
+            for (int k = tid; k < nv * 2; k += kExThreads) ns[k] = L.cnt[i0 * 2 + k];
+        }
+        __syncthreads();
+        if (*abort_flag) break;   // uniform: nothing sets the flag between the barrier and here
+        const int sb = 4 * warp;  // this warp's first sample in the tile
+        // ---- pairs of the four samples: counts, offsets (lanes 0..3)
+        int n0 = 0, n1 = 0, c0 = 0, c1 = 0;
+        if (lane < 4 && sb + lane < nv) {
+            n0 = ns[2 * (sb + lane)];
+            n1 = ns[2 * (sb + lane) + 1];
+            c0 = n0 > kCap ? min(128, G) : n0;
+            c1 = n1 > kCap ? max(0, min(128, G - 128)) : n1;
+        }
+        const int tot = c0 + c1;
+        const int t_0 = __shfl_sync(0xffffffffu, tot, 0), t_1 = __shfl_sync(0xffffffffu, tot, 1);
+        const int t_2 = __shfl_sync(0xffffffffu, tot, 2), t_3 = __shfl_sync(0xffffffffu, tot, 3);
+        const int o1 = t_0, o2 = o1 + t_1, o3 = o2 + t_2, T = o3 + t_3;
+        if (T <= WP) {
+            // ---- lay the pairs out, one lane per pair
+            for (int p = lane; p < T; p += 32) {
+                const int k = (p >= o1) + (p >= o2) + (p >= o3);
+                const int j = p - (k == 0 ? 0 : (k == 1 ? o1 : (k == 2 ? o2 : o3)));
+                wsm[p] = (uint8_t)k;
+                wg[p] = (uint8_t)j;   // rank within the sample for now
+            }
+            __syncwarp();
+            for (int p = lane; p < T; p += 32) {
+                const int k = wsm[p], j = wg[p];
+                const int si = sb + k;
+                const int m0 = ns[2 * si], m1 = ns[2 * si + 1];
+                const int d0 = m0 > kCap ? min(128, G) : m0;
+                int g;
+                if (j < d0) g = m0 > kCap ? j : cs[si * 32 + j];
+                else g = 128 + (m1 > kCap ? j - d0 : cs[si * 32 + 16 + (j - d0)]);
+                // ---- exact log-density of the pair over all D
+                const float *xr = xs + si * D;
+                const float *qs = pss + g * DS, *qm = pms + g * DS;
+                float r0 = 0.f, r1 = 0.f;
+                int d = 0;
+                for (; d + 1 < D; d += 2) {
+                    const float ta = fmaf(xr[d], qs[d], -qm[d]);
+                    const float tb = fmaf(xr[d + 1], qs[d + 1], -qm[d + 1]);
+                    r0 = fmaf(ta, ta, r0);
+                    r1 = fmaf(tb, tb, r1);
+                }
+                if (d < D) {
+                    const float ta = fmaf(xr[d], qs[d], -qm[d]);
+                    r0 = fmaf(ta, ta, r0);
+                }
+                wl[p] = fmaf(-0.5f, r0 + r1, pc[g]);
+                wg[p] = (uint8_t)g;
+            }
+            __syncwarp();
+            // ---- eight lanes per sample: log-sum-exp, kept pairs in order
+            const int si = sb + k8;
+            const int pb = k8 == 0 ? 0 : (k8 == 1 ? o1 : (k8 == 2 ? o2 : o3));
+            const int pn = (k8 == 0 ? o1 : (k8 == 1 ? o2 : (k8 == 2 ? o3 : T))) - pb;
+            float M = -INFINITY;
+            for (int q = j8; q < pn; q += 8) M = fmaxf(M, wl[pb + q]);
+#pragma unroll
+            for (int o = 4; o > 0; o >>= 1) M = fmaxf(M, __shfl_xor_sync(0xffffffffu, M, o));
+            float Ssum = 0.f;
+            if (M != -INFINITY)
+                for (int q = j8; q < pn; q += 8) Ssum += __expf(wl[pb + q] - M);
+#pragma unroll
+            for (int o = 4; o > 0; o >>= 1) Ssum += __shfl_xor_sync(0xffffffffu, Ssum, o);
+            const float lse = M + logf(Ssum);
+            // kept pairs: ranks by rounds of eight, in pair order
+            int m = 0;
+            const int rounds = (pn + 7) >> 3;
+            const int rmax = __reduce_max_sync(0xffffffffu, rounds);
+            for (int r = 0; r < rmax; ++r) {
+                const int q = 8 * r + j8;
+                const float rl = q < pn ? wl[pb + q] - lse : -INFINITY;
+                const bool kp = q < pn && rl >= keep;
+                const unsigned bal = __ballot_sync(0xffffffffu, kp);
+                const unsigned grp = (bal >> (8 * k8)) & 0xFFu;
+                if (kp) {
+                    const int rank = m + __popc(grp & ((1u << j8) - 1u));
+                    if (rank < kTcKeep) put(i0 + si, rank, wg[pb + q], __expf(rl), -1, true);
+                }
+                m += __popc(grp);
+            }
+            // spill: reserve the CTA list's slots for ranks >= kTcKeep
+            int sbase = -1;
+            bool sok = true;
+            if (j8 == 0 && si < nv && m > kTcKeep) {
+                sbase = atomicAdd(nspill, m - kTcKeep);
+                sok = sbase + (m - kTcKeep) <= kTcSpill;
+            }
+            sbase = __shfl_sync(0xffffffffu, sbase, 8 * k8);
+            sok = __shfl_sync(0xffffffffu, (int)sok, 8 * k8) != 0;
+            if (__any_sync(0xffffffffu, sbase >= 0)) {   // warp-uniform
+                int mm = 0;
+                for (int r = 0; r < rmax; ++r) {
+                    const int q = 8 * r + j8;
+                    const float rl = q < pn ? wl[pb + q] - lse : -INFINITY;
+                    const bool kp = q < pn && rl >= keep;
+                    const unsigned grp = (__ballot_sync(0xffffffffu, kp) >> (8 * k8)) & 0xFFu;
+                    if (kp && sbase >= 0) {
+                        const int rank = mm + __popc(grp & ((1u << j8) - 1u));
+                        if (rank >= kTcKeep) put(i0 + si, rank, wg[pb + q], __expf(rl), sbase, sok);
+                    }
+                    mm += __popc(grp);
+                }
+            }
+            if (j8 == 0 && si < nv) {
+                L.km[i0 + si] = (uint8_t)(m > kTcKeep ? (sok ? kTcKeep : 255) : m);
+                L.lse[i0 + si] = lse;
+                ll += (double)lse;
+            }
+            __syncwarp();
+        } else {
+            // ---- more pairs than the warp's slots (dense halves): one sample
+            // at a time, one lane per pair in rounds of 32, two passes
+            for (int k = 0; k < 4; ++k) {
+                const int si = sb + k;
+                if (si >= nv) break;
+                const float *xr = xs + si * D;
+                const int m0 = ns[2 * si], m1 = ns[2 * si + 1];
+                const int d0 = m0 > kCap ? min(128, G) : m0;
+                const int cnt = d0 + (m1 > kCap ? max(0, min(128, G - 128)) : m1);
+                auto gsel = [&](int j) -> int {
+                    if (j < d0) return m0 > kCap ? j : cs[si * 32 + j];
+                    return 128 + (m1 > kCap ? j - d0 : cs[si * 32 + 16 + (j - d0)]);
+                };
+                auto logit = [&](int g) -> float {
+                    const float *qs = pss + g * DS, *qm = pms + g * DS;
+                    float r0 = 0.f;
+                    for (int d = 0; d < D; ++d) {
+                        const float tt = fmaf(xr[d], qs[d], -qm[d]);
+                        r0 = fmaf(tt, tt, r0);
+                    }
+                    return fmaf(-0.5f, r0, pc[g]);
+                };
+                // pass 1: online max / sum of exp per lane, then over the warp
+                float mx = -INFINITY, sm = 0.f;
+                for (int j = lane; j < cnt; j += 32) {
+                    const float l = logit(gsel(j));
+                    if (l > mx) { sm = sm * __expf(mx - l) + 1.f; mx = l; }
+                    else sm += __expf(l - mx);
+                }
+                float M = mx;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) M = fmaxf(M, __shfl_xor_sync(0xffffffffu, M, o));
+                float Ssum = (mx == -INFINITY) ? 0.f : sm * __expf(mx - M);
+                Ssum = warp_sum_f(Ssum);
+                const float lse = M + logf(Ssum);
+                // pass 2: kept pairs in pair order
+                int m = 0;
+                for (int j0 = 0; j0 < cnt; j0 += 32) {
+                    const int j = j0 + lane;
+                    const float rl = j < cnt ? logit(gsel(j)) - lse : -INFINITY;
+                    m += __popc(__ballot_sync(0xffffffffu, j < cnt && rl >= keep));
+                }
+                int sbase = -1;
+                bool sok = true;
+                if (lane == 0 && m > kTcKeep) {
+                    sbase = atomicAdd(nspill, m - kTcKeep);
+                    sok = sbase + (m - kTcKeep) <= kTcSpill;
+                }
+                sbase = __shfl_sync(0xffffffffu, sbase, 0);
+                sok = __shfl_sync(0xffffffffu, (int)sok, 0) != 0;
+                int r = 0;
+                for (int j0 = 0; j0 < cnt; j0 += 32) {
+                    const int j = j0 + lane;
+                    const int g = j < cnt ? gsel(j) : 0;
+                    const float rl = j < cnt ? logit(g) - lse : -INFINITY;
+                    const bool kp = j < cnt && rl >= keep;
+                    const unsigned bal = __ballot_sync(0xffffffffu, kp);
+                    if (kp) put(i0 + si, r + __popc(bal & ((1u << lane) - 1u)), g, __expf(rl), sbase, sok);
+                    r += __popc(bal);
+                }
+                if (lane == 0) {
+                    L.km[i0 + si] = (uint8_t)(m > kTcKeep ? (sok ? kTcKeep : 255) : m);
+                    L.lse[i0 + si] = lse;
+                    ll += (double)lse;
+                }
+            }
+        }
+        __syncthreads();   // every warp is done with buffer b
+        if (tid == 0 && t + 2 < t1 && tile_is_bulk((t + 2) * kST, a.N, args.x_al16)) issue(t + 2, b);
+    }
+    // drain: no bulk copy may still be writing into shared memory at exit
+    if (tid == 0)
+        for (int bb = 0; bb < 2; ++bb) {
+            uint32_t issued = 0;
+            for (int64_t t = t0 + bb; t < t1; t += 2)
+                if (tile_is_bulk(t * kST, a.N, args.x_al16)) ++issued;
+            const uint32_t used = bb ? use1 : use0;
+            const long long d0 = clock64();
+            for (uint32_t u = used; u < issued; ++u)
+                while (!mbar_try_wait(bars + bb, u & 1u) && clock64() - d0 < a.wait_cycles) {
+                }
+        }
+    for (int o = 16; o > 0; o >>= 1) ll += __shfl_xor_sync(0xffffffffu, ll, o);
+    if (lane == 0) s_ll[warp] = ll;
+    __syncthreads();
+    if (tid == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < kExThreads / 32; ++w) tot += s_ll[w];
+        a.ll_partial[blockIdx.x] = tot;
+        L.sp_n[blockIdx.x] = min(*nspill, kTcSpill);
+        if (*abort_flag) {
+            if (atomicCAS(&a.status->code, 0, (int)GMM_ERR_TIMEOUT) == 0) a.status->fail_iter = a.iter;
+            atomicExch(&a.status->halt, 1);
+        }
+    }
+}
+
+// ------------------------------------------------------------------------
+// 3. M-step statistics from the compacted responsibility records.  CTA b
+// owns the same run of 128-sample tiles as CTA b of the exact kernel (the
+// paper's thread t) and the FP32 statistics [G][1 + 2D] (S0 | S1_d | S2_d,
+// shifted by the FP32 means mu_f) of its samples in shared memory.  Each
+// tile's samples and records are staged by bulk copies two tiles ahead; its
+// (sample, Gaussian) pairs are counting-sorted by Gaussian, and the warp that
+// owns a Gaussian (g = warp + 32 k; its mu_f row in registers for the whole
+// kernel) sums its pairs in registers and adds them to the Gaussian's row:
+// no atomics on the statistics.  Then the CTA's spill list (kept pairs
+// beyond kTcKeep) is added with shared-memory atomics, and the samples the
+// spill list had no room for are recomputed over every Gaussian.
+// ------------------------------------------------------------------------
+struct MsSmem {
+    uint32_t slab, cnt, off, fill, pairs, X[2], kg[2], gam[2], km[2], ovl, misc, bars, total;
+};
+
+__host__ __device__ inline MsSmem ms_layout(int D, int G)
+{
+    MsSmem L;
+    uint32_t o = 0;
+    L.slab = o; o += 4u * (uint32_t)G * (uint32_t)(1 + 2 * D);
+    o = (o + 15u) & ~15u;
+    L.cnt = o; o += 4u * 256u;
+    L.off = o; o += 4u * 260u;
+    L.fill = o; o += 4u * 256u;
+    L.pairs = o; o += 2u * kST * kTcKeep;
+    o = (o + 127u) & ~127u;
+    for (int b = 0; b < 2; ++b) {
+        L.X[b] = o; o += ((4u * kST * (uint32_t)D) + 127u) & ~127u;
+        L.gam[b] = o; o += 4u * kST * kTcKeep;
+        L.kg[b] = o; o += (uint32_t)kST * kTcKeep;
+        L.km[b] = o; o += (uint32_t)kST;
+    }
+    L.ovl = o; o += 4u * kST;
+    L.misc = o; o += 16u;
+    L.bars = o; o += 16u;
+    L.total = o;
+    return L;
+}
+
+__global__ void __launch_bounds__(kMsThreads, 1) k_em_mstep_lists(ExArgs args)
+{
+    extern __shared__ __align__(128) unsigned char ms_raw[];
+    const EmPassArgs &a = args.a;
+    const TcLists &L = args.L;
     if (skip_block(a.status, a.iter)) return;
     const int D = a.D, G = a.G, S = 1 + 2 * D;
-    const int h = blockIdx.x & 1, chunk = blockIdx.x >> 1, nchunks = gridDim.x >> 1;
-    const int GH = max(0, min(128, G - 128 * h));
-    if (GH == 0) return;
-    const MsSmem Ls = ms_layout(D);
+    const MsSmem Ls = ms_layout(D, G);
     float *slab = reinterpret_cast<float *>(ms_raw + Ls.slab);
     int *bcnt = reinterpret_cast<int *>(ms_raw + Ls.cnt);
     int *boff = reinterpret_cast<int *>(ms_raw + Ls.off);
     int *bfill = reinterpret_cast<int *>(ms_raw + Ls.fill);
-    uint4 *scand = reinterpret_cast<uint4 *>(ms_raw + Ls.scand);
     uint16_t *pairs = reinterpret_cast<uint16_t *>(ms_raw + Ls.pairs);
-    uint8_t *sn = reinterpret_cast<uint8_t *>(ms_raw + Ls.sn);
-    int *dl = reinterpret_cast<int *>(ms_raw + Ls.dl);
-    int *dn = reinterpret_cast<int *>(ms_raw + Ls.dn);
-    float *xw = reinterpret_cast<float *>(ms_raw + Ls.xw);
+    int *ovl = reinterpret_cast<int *>(ms_raw + Ls.ovl);
+    int *novl = reinterpret_cast<int *>(ms_raw + Ls.misc);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(ms_raw + Ls.misc + 4);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(ms_raw + Ls.bars);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    for (int k = tid; k < 128 * S; k += kMsThreads) slab[k] = 0.f;
-    const int64_t lo = a.N * chunk / nchunks, hi = a.N * (chunk + 1) / nchunks;
-    const uint8_t *ccnt = L.cnt;
-    for (int64_t i0 = lo; i0 < hi; i0 += kMsTile) {
-        const int nt = (int)min((int64_t)kMsTile, hi - i0);
-        if (tid < 128) { bcnt[tid] = 0; bfill[tid] = 0; }
-        if (tid == 0) *dn = 0;
-        __syncthreads();
-        // ---- this half's list of each sample of the tile; histogram by Gaussian
-        if (tid < nt) {
-            const int64_t rec = (i0 + tid) * 2 + h;
-            const int n = ccnt[rec];
-            sn[tid] = (uint8_t)n;
-            if (n > kCap) {
-                dl[atomicAdd(dn, 1)] = tid;
-            } else if (n > 0) {
-                scand[tid] = reinterpret_cast<const uint4 *>(L.cand)[rec];
-                const uint8_t *cb = reinterpret_cast<const uint8_t *>(scand + tid);
-                for (int k = 0; k < n; ++k) atomicAdd(&bcnt[cb[k]], 1);
+    const int64_t ntiles = (a.N + kST - 1) / kST;
+    const int64_t t0 = ntiles * blockIdx.x / gridDim.x, t1 = ntiles * (blockIdx.x + 1) / gridDim.x;
+    const float keep = -args.screen;
+
+    // shifts of the Gaussians this warp owns (g = warp + 32 k), kept in registers
+    float mu0[8], mu1[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int g = warp + 32 * k;
+        mu0[k] = (g < G && lane < D) ? __ldg(a.op.mu + (size_t)g * D + lane) : 0.f;
+        mu1[k] = (g < G && lane + 32 < D) ? __ldg(a.op.mu + (size_t)g * D + 32 + lane) : 0.f;
+    }
+    // one pair (responsibility gv of Gaussian g at sample row x0|x1) with atomics
+    auto add_atomic = [&](int g, float gv, float x0, float x1) {
+        float *sg = slab + (size_t)g * S;
+        if (lane < D) {
+            const float u = x0 - __ldg(a.op.mu + (size_t)g * D + lane);
+            const float v = gv * u;
+            atomicAdd(sg + 1 + lane, v);
+            atomicAdd(sg + 1 + D + lane, v * u);
+        }
+        if (lane + 32 < D) {
+            const float u = x1 - __ldg(a.op.mu + (size_t)g * D + 32 + lane);
+            const float v = gv * u;
+            atomicAdd(sg + 33 + lane, v);
+            atomicAdd(sg + 33 + D + lane, v * u);
+        }
+        if (lane == 0) atomicAdd(sg, gv);
+    };
+
+    auto issue = [&](int64_t tile, int b) {   // thread 0 only
+        const int64_t i0 = tile * kST;
+        const uint32_t xb = 4u * kST * (uint32_t)D;
+        const uint32_t bo = (uint32_t)b * (Ls.X[1] - Ls.X[0]);
+        fence_proxy_async();
+        mbar_expect_tx(bars + b, xb + 5u * kST * kTcKeep + kST);
+        bulk_g2s(ms_raw + Ls.X[0] + bo, a.X + i0 * D, xb, bars + b);
+        bulk_g2s(ms_raw + Ls.gam[0] + bo, L.gam + i0 * kTcKeep, 4u * kST * kTcKeep, bars + b);
+        bulk_g2s(ms_raw + Ls.kg[0] + bo, L.kg + i0 * kTcKeep, (uint32_t)kST * kTcKeep, bars + b);
+        bulk_g2s(ms_raw + Ls.km[0] + bo, L.km + i0, (uint32_t)kST, bars + b);
+    };
+    if (tid == 0) {
+        mbar_init(bars, 1);
+        mbar_init(bars + 1, 1);
+        *abort_flag = 0;
+        *novl = 0;
+        fence_mbar_init();
+    }
+    for (int k = tid; k < G * S; k += kMsThreads) slab[k] = 0.f;
+    for (int k = tid; k < 256; k += kMsThreads) { bcnt[k] = 0; bfill[k] = 0; }
+    __syncthreads();
+    if (tid == 0)
+        for (int k = 0; k < 2 && t0 + k < t1; ++k)
+            if (tile_is_bulk((t0 + k) * kST, a.N, args.x_al16)) issue(t0 + k, k);
+    uint32_t use0 = 0u, use1 = 0u;
+    for (int64_t t = t0; t < t1; ++t) {
+        const int b = (int)((t - t0) & 1);
+        const int64_t i0 = t * kST;
+        const int nv = (int)min((int64_t)kST, a.N - i0);
+        const uint32_t bo = (uint32_t)b * (Ls.X[1] - Ls.X[0]);
+        float *xs = reinterpret_cast<float *>(ms_raw + Ls.X[0] + bo);
+        float *gms = reinterpret_cast<float *>(ms_raw + Ls.gam[0] + bo);
+        uint8_t *kgs = ms_raw + Ls.kg[0] + bo;
+        uint8_t *kms = ms_raw + Ls.km[0] + bo;
+        if (tile_is_bulk(i0, a.N, args.x_al16)) {
+            if (stage_wait(bars + b, (b ? use1 : use0) & 1u, a.wait_cycles, abort_flag)) {
+                if (b) ++use1; else ++use0;
+            }
+        } else {
+            for (int k = tid; k < nv * D; k += kMsThreads) xs[k] = __ldg(a.X + i0 * D + k);
+            for (int k = tid; k < nv; k += kMsThreads) {
+                const int m = L.km[i0 + k];
+                kms[k] = (uint8_t)m;
+                for (int j = 0; j < kTcKeep && m <= kTcKeep && j < m; ++j) {
+                    kgs[k * kTcKeep + j] = L.kg[(i0 + k) * kTcKeep + j];
+                    gms[k * kTcKeep + j] = L.gam[(i0 + k) * kTcKeep + j];
+                }
             }
         }
         __syncthreads();
-        // ---- exclusive scan of the 128 bins (warp 0, four bins per lane)
+        if (*abort_flag) break;   // uniform: nothing sets the flag between the barrier and here
+        // ---- histogram of the tile's pairs by Gaussian
+        for (int e = tid; e < nv * kTcKeep; e += kMsThreads) {
+            const int si = e / kTcKeep, slot = e - si * kTcKeep;
+            const int m = kms[si];
+            if (m == 255) {
+                if (slot == 0) ovl[atomicAdd(novl, 1)] = si;
+            } else if (slot < m) {
+                atomicAdd(&bcnt[kgs[e]], 1);
+            }
+        }
+        __syncthreads();
+        // ---- exclusive scan of the 256 bins (warp 0, eight bins per lane)
         if (warp == 0) {
-            const int4 v = reinterpret_cast<const int4 *>(bcnt)[lane];
-            const int tot = v.x + v.y + v.z + v.w;
+            int v[8], tot = 0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) { v[j] = bcnt[8 * lane + j]; tot += v[j]; }
             int inc = tot;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const int y = __shfl_up_sync(0xffffffffu, inc, o);
                 if (lane >= o) inc += y;
             }
-            const int ex = inc - tot;
-            boff[4 * lane] = ex;
-            boff[4 * lane + 1] = ex + v.x;
-            boff[4 * lane + 2] = ex + v.x + v.y;
-            boff[4 * lane + 3] = ex + v.x + v.y + v.z;
-            if (lane == 31) boff[128] = inc;
+            int run = inc - tot;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) { boff[8 * lane + j] = run; run += v[j]; }
+            if (lane == 31) boff[256] = inc;
         }
         __syncthreads();
-        // ---- scatter the pairs (sample << 4 | slot) into their bins
-        if (tid < nt) {
-            const int n = sn[tid];
-            if (n > 0 && n <= kCap) {
-                const uint8_t *cb = reinterpret_cast<const uint8_t *>(scand + tid);
-                for (int k = 0; k < n; ++k) {
-                    const int gl = cb[k];
-                    pairs[boff[gl] + atomicAdd(&bfill[gl], 1)] = (uint16_t)((tid << 4) | k);
-                }
+        // ---- scatter the pairs (sample * kTcKeep + slot) into their bins
+        for (int e = tid; e < nv * kTcKeep; e += kMsThreads) {
+            const int si = e / kTcKeep, slot = e - si * kTcKeep;
+            const int m = kms[si];
+            if (m != 255 && slot < m) {
+                const int g = kgs[e];
+                pairs[boff[g] + atomicAdd(&bfill[g], 1)] = (uint16_t)e;
             }
         }
         __syncthreads();
-        // ---- warp w owns Gaussians w, w + 16, ...: sums in registers, then
-        // one read-modify-write of its rows of the CTA's statistics
-        for (int gl = warp; gl < GH; gl += kMsThreads / 32) {
-            const int pb = boff[gl], pe = boff[gl + 1];
-            if (pb == pe) continue;
-            const int g = 128 * h + gl;
-            const float m0 = lane < D ? __ldg(a.op.mu + (size_t)g * D + lane) : 0.f;
-            const float m1 = lane + 32 < D ? __ldg(a.op.mu + (size_t)g * D + 32 + lane) : 0.f;
-            float s0 = 0.f, a1 = 0.f, a2 = 0.f, b1 = 0.f, b2 = 0.f;
-            for (int p = pb; p < pe; ++p) {
-                const int pr = pairs[p];
-                const int64_t i = i0 + (pr >> 4);
-                const float gm = __ldg(L.gam + i * 32 + 16 * h + (pr & 15));
-                const float *row = a.X + i * D;
-                if (lane < D) {
-                    const float u = __ldg(row + lane) - m0;
-                    const float v = gm * u;
-                    a1 += v;
-                    a2 = fmaf(v, u, a2);
-                }
-                if (lane + 32 < D) {
-                    const float u = __ldg(row + 32 + lane) - m1;
-                    const float v = gm * u;
-                    b1 += v;
-                    b2 = fmaf(v, u, b2);
-                }
-                s0 += gm;
-            }
-            float *sg = slab + (size_t)gl * S;
-            if (lane == 0) sg[0] += s0;
-            if (lane < D) { sg[1 + lane] += a1; sg[1 + D + lane] += a2; }
-            if (lane + 32 < D) { sg[33 + lane] += b1; sg[33 + D + lane] += b2; }
-        }
-        __syncthreads();
-        // ---- dense (sample, half) records: warp 0 recomputes every
-        // Gaussian of the half exactly and adds the responsibilities > 0
-        if (warp == 0) {
-            const int nd = *dn;
-            for (int r = 0; r < nd; ++r) {
-                const int64_t i = i0 + dl[r];
-                const float *row = a.X + i * D;
-                const float x0 = lane < D ? __ldg(row + lane) : 0.f;
-                const float x1 = lane + 32 < D ? __ldg(row + 32 + lane) : 0.f;
-                if (lane < D) xw[lane] = x0;
-                if (lane + 32 < D) xw[lane + 32] = x1;
-                __syncwarp();
-                const float ls = __ldg(L.lse + i);
-                for (int gb = 0; gb < GH; gb += 32) {
-                    const int gl = gb + lane;
-                    float gm = 0.f;
-                    if (gl < GH) {
-                        const float2 *p = a.op.sm + (size_t)(128 * h + gl) * D;
-                        float acc = 0.f;
-                        for (int d = 0; d < D; ++d) {
-                            const float2 q = __ldg(p + d);
-                            const float t = fmaf(xw[d], q.x, -q.y);
-                            acc = fmaf(t, t, acc);
-                        }
-                        gm = __expf(fmaf(-0.5f, acc, __ldg(a.op.c + 128 * h + gl)) - ls);
-                    }
-                    unsigned live = __ballot_sync(0xffffffffu, gm > 0.f);
-                    while (live) {
-                        const int src = __ffs(live) - 1;
-                        live &= live - 1u;
-                        const float gv = __shfl_sync(0xffffffffu, gm, src);
-                        const int gg = gb + src;
-                        const size_t gidx = (size_t)(128 * h + gg) * D;
-                        float *sg = slab + (size_t)gg * S;
+        // ---- warp w owns Gaussians w + 32 k: sums in registers, then one
+        // read-modify-write of the Gaussian's row
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int g = warp + 32 * k;
+            if (g < G) {
+                const int pb = boff[g], pe = boff[g + 1];
+                if (pb < pe) {
+                    float s0 = 0.f, a1 = 0.f, a2 = 0.f, b1 = 0.f, b2 = 0.f;
+                    for (int p = pb; p < pe; ++p) {
+                        const int e = pairs[p];
+                        const float gm = gms[e];
+                        const float *xr = xs + (e / kTcKeep) * D;
                         if (lane < D) {
-                            const float u = x0 - __ldg(a.op.mu + gidx + lane);
-                            const float v = gv * u;
-                            sg[1 + lane] += v;
-                            sg[1 + D + lane] = fmaf(v, u, sg[1 + D + lane]);
+                            const float u = xr[lane] - mu0[k];
+                            const float v = gm * u;
+                            a1 += v;
+                            a2 = fmaf(v, u, a2);
                         }
                         if (lane + 32 < D) {
-                            const float u = x1 - __ldg(a.op.mu + gidx + 32 + lane);
-                            const float v = gv * u;
-                            sg[33 + lane] += v;
-                            sg[33 + D + lane] = fmaf(v, u, sg[33 + D + lane]);
+                            const float u = xr[lane + 32] - mu1[k];
+                            const float v = gm * u;
+                            b1 += v;
+                            b2 = fmaf(v, u, b2);
                         }
-                        if (lane == 0) sg[0] += gv;
-                        __syncwarp();
+                        s0 += gm;
                     }
+                    float *sg = slab + (size_t)g * S;
+                    if (lane == 0) sg[0] += s0;
+                    if (lane < D) { sg[1 + lane] += a1; sg[1 + D + lane] += a2; }
+                    if (lane + 32 < D) { sg[33 + lane] += b1; sg[33 + D + lane] += b2; }
                 }
-                __syncwarp();
             }
         }
         __syncthreads();
+        // ---- samples the spill list had no room for: every Gaussian, one
+        // warp per sample, shared-memory atomics (never taken in practice)
+        const int nd = *novl;
+        for (int r = warp; r < nd; r += kMsThreads / 32) {
+            const int si = ovl[r];
+            const float *xr = xs + si * D;
+            const float x0 = lane < D ? xr[lane] : 0.f;
+            const float x1 = lane + 32 < D ? xr[lane + 32] : 0.f;
+            const float ls = __ldg(L.lse + i0 + si);
+            for (int g = 0; g < G; ++g) {
+                const float2 *pp = a.op.sm + (size_t)g * D;
+                float acc = 0.f;
+                if (lane < D) { const float2 q = __ldg(pp + lane); const float tt = fmaf(x0, q.x, -q.y); acc = tt * tt; }
+                if (lane + 32 < D) { const float2 q = __ldg(pp + 32 + lane); const float tt = fmaf(x1, q.x, -q.y); acc = fmaf(tt, tt, acc); }
+                acc = warp_sum_f(acc);
+                const float rl = fmaf(-0.5f, acc, __ldg(a.op.c + g)) - ls;
+                if (rl >= keep) add_atomic(g, __expf(rl), x0, x1);   // the same rule as the kept pairs
+            }
+        }
+        for (int k = tid; k < 256; k += kMsThreads) { bcnt[k] = 0; bfill[k] = 0; }
+        __syncthreads();   // every warp is done with buffer b, the bins and the list
+        if (tid == 0) {
+            *novl = 0;
+            if (t + 2 < t1 && tile_is_bulk((t + 2) * kST, a.N, args.x_al16)) issue(t + 2, b);
+        }
     }
-    // ---- the chunk's statistics of this half -> its FP64 partial
-    double *P = a.partial + ((size_t)chunk * G + 128 * h) * S;
-    for (int k = tid; k < GH * S; k += kMsThreads) P[k] = (double)slab[k];
+    // drain: no bulk copy may still be writing into shared memory at exit
+    if (tid == 0)
+        for (int bb = 0; bb < 2; ++bb) {
+            uint32_t issued = 0;
+            for (int64_t t = t0 + bb; t < t1; t += 2)
+                if (tile_is_bulk(t * kST, a.N, args.x_al16)) ++issued;
+            const uint32_t used = bb ? use1 : use0;
+            const long long d0 = clock64();
+            for (uint32_t u = used; u < issued; ++u)
+                while (!mbar_try_wait(bars + bb, u & 1u) && clock64() - d0 < a.wait_cycles) {
+                }
+        }
+    __syncthreads();
+    // ---- the spill list of this CTA's samples (kept pairs beyond kTcKeep)
+    if (!*abort_flag) {
+        const int ns = L.sp_n[blockIdx.x];
+        const int64_t *sp_ig = L.sp_ig + (size_t)blockIdx.x * kTcSpill;
+        const float *sp_gam = L.sp_gam + (size_t)blockIdx.x * kTcSpill;
+        for (int e = warp; e < ns; e += kMsThreads / 32) {
+            const float gv = sp_gam[e];
+            if (!(gv > 0.f)) continue;
+            const int64_t ig = sp_ig[e];
+            const int64_t i = ig >> 8;
+            const int g = (int)(ig & 255);
+            const float *xr = a.X + i * D;
+            add_atomic(g, gv, lane < D ? __ldg(xr + lane) : 0.f, lane + 32 < D ? __ldg(xr + 32 + lane) : 0.f);
+        }
+    }
+    __syncthreads();
+    // ---- the CTA's statistics -> its FP64 partial
+    double *P = a.partial + (size_t)blockIdx.x * G * S;
+    for (int k = tid; k < G * S; k += kMsThreads) P[k] = (double)slab[k];
+    if (tid == 0 && *abort_flag) {
+        if (atomicCAS(&a.status->code, 0, (int)GMM_ERR_TIMEOUT) == 0) a.status->fail_iter = a.iter;
+        atomicExch(&a.status->halt, 1);
+    }
 }
 
+}  // namespace
+
+namespace {
+int optin_smem()
+{
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return optin;
+}
+// pair slots per warp of the exact kernel: what shared memory leaves, up to 256
+int ex_wp(int D, int G)
+{
+    const long long rest = (long long)optin_smem() - 2048 - (long long)ex_layout(D, G, 0).total;
+    const long long wp = rest / (6 * 32);
+    return (int)(wp >= 256 ? 256 : (wp / 32) * 32);
+}
 }  // namespace
 
 bool em_tc_supported(int32_t D, int32_t G)
@@ -755,47 +1137,62 @@ bool em_tc_supported(int32_t D, int32_t G)
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const size_t ex = (size_t)G * D * 8u + 4u * (size_t)((G + 3) & ~3) + 32u * 64u * 4u;
-    return tc_layout(NG).total + 1024u + 64u <= (uint32_t)optin && ex <= (size_t)optin &&
-           ms_layout(D).total <= (uint32_t)optin;
+    // dynamic layouts plus the kernels' static shared memory
+    return tc_layout(NG).total + 1024u + 2048u <= (uint32_t)optin && ex_wp(D, G) >= 32 &&
+           ms_layout(D, G).total + 2048u <= (uint32_t)optin;
 }
 
 int em_tc_grid(int sms) { return sms; }
 
-size_t em_tc_list_bytes(int64_t N) { return (size_t)N * (32u + 2u + 128u + 4u) + 1024u; }
+namespace {
+size_t al256(size_t n) { return (n + 255u) & ~(size_t)255u; }
+}
 
-TcLists em_tc_lists(void *base, int64_t N)
+size_t em_tc_list_bytes(int64_t N, int grid)
 {
+    const size_t n = (size_t)N, sp = (size_t)grid * kTcSpill;
+    return al256(4u * n * kTcKeep) + al256(n * kTcKeep) + al256(32u * n) + al256(4u * n) + al256(2u * n) +
+           al256(n) + al256(8u * sp) + al256(4u * sp) + al256(4u * (size_t)grid) + 256u;
+}
+
+TcLists em_tc_lists(void *base, int64_t N, int grid)
+{
+    const size_t n = (size_t)N, sp = (size_t)grid * kTcSpill;
     unsigned char *p = static_cast<unsigned char *>(base);
     TcLists L;
-    L.gam = reinterpret_cast<float *>(p);                 // [N][2][16] FP32 (16-byte aligned rows)
-    p += (size_t)N * 128u;
-    L.cand = p;                                           // [N][2][16] Gaussian index within the half
-    p += (size_t)N * 32u;
-    L.lse = reinterpret_cast<float *>(p);                 // [N]
-    p += (size_t)N * 4u;
-    L.cnt = p;                                            // [N][2] candidates (> kTcCap: dense)
+    L.gam = reinterpret_cast<float *>(p);       p += al256(4u * n * kTcKeep);
+    L.kg = p;                                   p += al256(n * kTcKeep);
+    L.cand = p;                                 p += al256(32u * n);
+    L.lse = reinterpret_cast<float *>(p);       p += al256(4u * n);
+    L.cnt = p;                                  p += al256(2u * n);
+    L.km = p;                                   p += al256(n);
+    L.sp_ig = reinterpret_cast<int64_t *>(p);   p += al256(8u * sp);
+    L.sp_gam = reinterpret_cast<float *>(p);    p += al256(4u * sp);
+    L.sp_n = reinterpret_cast<int32_t *>(p);
     return L;
 }
 
-cudaError_t launch_em_pass_tc(const EmPassArgs &a, const TcLists &L, int32_t grid, int32_t ms_chunks, cudaStream_t s)
+cudaError_t launch_em_pass_tc(const EmPassArgs &a, const TcLists &L, int32_t grid, int32_t ms_grid, cudaStream_t s)
 {
-    TcArgs t{a, L, (a.G + 15) / 16 * 16, (a.D + 15) / 16, (float)std::log((double)a.N * 1e9)};
+    const float scr = (float)std::log((double)a.N * 1e9);
+    TcArgs t{a, L, (a.G + 15) / 16 * 16, (a.D + 15) / 16, scr};
     const size_t sm1 = tc_layout(t.NG).total + 1024u;
     cudaError_t e = cudaFuncSetAttribute(k_em_screen_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
     if (e != cudaSuccess) return e;
     k_em_screen_tc<<<grid, kThreads, sm1, s>>>(t);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const size_t sm2 = (size_t)a.G * a.D * 8u + 4u * (size_t)((a.G + 3) & ~3) + 32u * 64u * 4u;
+    const int al = (reinterpret_cast<uintptr_t>(a.X) & 15u) == 0;
+    ExArgs x{a, L, scr, al, ex_wp(a.D, a.G)};
+    const size_t sm2 = ex_layout(a.D, a.G, x.wp).total;
     if ((e = cudaFuncSetAttribute(k_em_exact, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2)) != cudaSuccess)
         return e;
-    k_em_exact<<<grid, kExThreads, sm2, s>>>(a, L);
+    k_em_exact<<<grid, kExThreads, sm2, s>>>(x);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const size_t sm3 = ms_layout(a.D).total;
+    const size_t sm3 = ms_layout(a.D, a.G).total;
     if ((e = cudaFuncSetAttribute(k_em_mstep_lists, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3)) !=
         cudaSuccess)
         return e;
-    k_em_mstep_lists<<<2 * ms_chunks, kMsThreads, sm3, s>>>(a, L);
+    k_em_mstep_lists<<<ms_grid, kMsThreads, sm3, s>>>(x);
     count_launches(3);
     return cudaGetLastError();
 }

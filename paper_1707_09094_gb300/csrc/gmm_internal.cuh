@@ -185,16 +185,23 @@ cudaError_t init_net_run(InitNet *n, const float *pts, int B, int P, const doubl
 
 // ---- launchers implemented in gmm_em_tc.cu
 constexpr int kTcCap = 16;   // candidates per (sample, half of the Gaussians) before the dense fallback
+constexpr int kTcKeep = 16;  // responsibilities kept per sample before the full-recompute fallback
 struct TcLists {             // per-sample records between the three kernels of the tensor-core pass
-    float *gam;              // [N][2][kTcCap] responsibilities of the candidates
-    uint8_t *cand;           // [N][2][kTcCap] candidate Gaussian (index within its half)
+    float *gam;              // [N][kTcKeep] responsibilities that matter (compacted)
+    uint8_t *kg;             // [N][kTcKeep] their Gaussians (N_G <= 256)
+    uint8_t *cand;           // [N][2][kTcCap] screened candidates (index within the half)
     float *lse;              // [N] log p(x_i)
     uint8_t *cnt;            // [N][2] candidates per half (> kTcCap: every Gaussian of the half)
+    uint8_t *km;             // [N] kept responsibilities in the record (255: recompute every Gaussian)
+    int64_t *sp_ig;          // [grid][kTcSpill] kept pairs beyond kTcKeep: sample * 256 + Gaussian
+    float *sp_gam;           //                  and their responsibilities (0: unused entry)
+    int32_t *sp_n;           // [grid] entries of each CTA's spill list
 };
+constexpr int kTcSpill = 16384;   // spill entries per CTA
 bool em_tc_supported(int32_t D, int32_t G);
 int em_tc_grid(int sms);
-size_t em_tc_list_bytes(int64_t N);
-TcLists em_tc_lists(void *base, int64_t N);
+size_t em_tc_list_bytes(int64_t N, int grid);
+TcLists em_tc_lists(void *base, int64_t N, int grid);
 cudaError_t launch_em_pass_tc(const EmPassArgs &a, const TcLists &L, int32_t grid, int32_t ms_chunks, cudaStream_t s);
 
 }  // namespace gmm

@@ -64,6 +64,22 @@ def test_tc_dense_fallback_many_candidates():
     np.testing.assert_allclose(g.ll_history(), ll, rtol=1e-6)
 
 
+def test_tc_spill_list_full_falls_back_to_recompute():
+    """Every sample keeps ~40 responsibilities: 16 go to its record, the rest
+    to its CTA's spill list; at N = 150,000 the lists overflow and the
+    samples without room are recomputed over every Gaussian in the M-step.
+    All three routes must give the oracle's iteration."""
+    rng = np.random.default_rng(4)
+    N, D, G = 150_000, 8, 40
+    X = rng.normal(0, 1, (N, D)).astype(np.float32)
+    start = (rng.normal(0, 0.05, (G, D)), np.ones((G, D)), np.full(G, 1.0 / G))
+    M, V, H, ll = oracle.em_iterate(X, *start, 2, 1e-10)
+    g = GMM().set_params(*start)
+    g.em_iterate(dev(X), 2, prec="bf16", recompute_center=True)
+    assert_params(g.get_params(), (M, V, H), X)
+    np.testing.assert_allclose(g.ll_history(), ll, rtol=1e-6)
+
+
 def test_tc_learn_end_to_end_c1():
     X, _, _ = synth.make("c1")
     g = GMM().learn(dev(X), 8, km_iter=10, em_iter=10, seed=1001, prec="bf16")
@@ -119,3 +135,25 @@ def test_tc_rejects_unsupported_shapes():
     with pytest.raises(GmmError) as e:
         g.em_iterate(dev(X), 1, prec="bf16", recompute_center=True)
     assert e.value.status == -7
+
+
+def test_tc_unaligned_input_matches_aligned():
+    """The staged kernels copy whole 128-sample tiles with the bulk engine
+    only when X is 16-byte aligned; an X that starts 4 bytes into its buffer
+    takes the per-thread copy for every tile and must give the same results
+    (same arithmetic; only the order of FP32 additions within a Gaussian's
+    bin may differ)."""
+    X, _, _ = synth.make("c1", N=50_000, seed=21)
+    flat = torch.zeros(X.size + 1, dtype=torch.float32, device="cuda")
+    flat[1:] = torch.from_numpy(X.ravel()).cuda()
+    Xu = flat[1:].view(X.shape)
+    assert Xu.data_ptr() % 16 == 4
+    Xa = dev(X)
+    start = GMM().learn(Xa, 8, km_iter=5, em_iter=0, seed=3).get_params()
+    a = GMM().set_params(*start)
+    a.em_iterate(Xa, 3, prec="bf16", recompute_center=True)
+    b = GMM().set_params(*start)
+    b.em_iterate(Xu, 3, prec="bf16", recompute_center=True)
+    np.testing.assert_allclose(a.ll_history(), b.ll_history(), rtol=1e-7)
+    for p, q in zip(a.get_params(), b.get_params()):
+        np.testing.assert_allclose(p, q, rtol=1e-6, atol=1e-9)
