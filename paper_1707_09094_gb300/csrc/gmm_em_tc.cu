@@ -40,7 +40,7 @@ namespace gmm {
 
 namespace {
 
-constexpr int kEpiThreads = 256;
+constexpr int kEpiThreads = 512;  // screening kernel: 16 epilogue warps
 constexpr int kThreads = kEpiThreads + 32;
 constexpr int kTM = 128;          // samples per tile = MMA M
 constexpr int kCap = kTcCap;      // candidates per (sample, half) before the dense fallback
@@ -90,7 +90,7 @@ __device__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_fl
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 512;" ::: "memory"); }
 
 __device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols)
 {
@@ -178,266 +178,6 @@ __device__ __forceinline__ bool skip_block(const DevStatus *st, int iter)
     return s_skip != 0;
 }
 
-struct TcArgs {
-    EmPassArgs a;
-    TcLists L;
-    int32_t NG;       // Gaussians padded to a multiple of 16 (MMA N)
-    int32_t nk;       // K=16 steps per K block: ceil(D/16)
-    float screen;     // screening distance in nats, ln(N * 1e9)
-};
-
-struct TcSmem {
-    uint32_t B, A, cst, ctr, cg, xlo, bars, misc, total;
-};
-
-__host__ __device__ inline TcSmem tc_layout(int NG)
-{
-    TcSmem L;
-    uint32_t o = 0;
-    L.B = o; o += 2u * NG * 128u;                        // two K blocks of [NG][128 B]
-    L.A = o; o += 2u * kTM * 256u;                       // two buffers x two K blocks of [128][128 B]
-    L.cst = o; o += 8u * NG;                             // (ctc, k2) per Gaussian
-    L.ctr = o; o += 4u * 64u;                            // centre
-    L.cg = o; o += (uint32_t)kEpiThreads * kCap;         // candidate list staging, 16 B per thread
-    L.xlo = o; o += 4u * kEpiThreads;                    // best lower bound per (sample, half)
-    o = (o + 7u) & ~7u;
-    L.bars = o; o += 8u * 4u;
-    L.misc = o; o += 16u;
-    L.total = o;
-    return L;
-}
-
-// ------------------------------------------------------------------------
-// 1. Screening on the tensor cores.  Warp roles: warps 0-7 are the epilogue
-// (warp w reads TMEM lanes 32*(w%4).., i.e. samples 32*(w%4).., Gaussians
-// 128*(w/4)..), warp 8 allocates TMEM and one of its threads issues the
-// MMAs.  The BF16 sample operand is double-buffered, so the MMAs of tile
-// t+1 run while tile t is screened.  Every wait is bounded: on expiry the
-// CTA records GMM_ERR_TIMEOUT, stops issuing work, drains, frees TMEM and
-// returns.
-// ------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads, 1) k_em_screen_tc(TcArgs args)
-{
-    extern __shared__ __align__(1024) unsigned char tc_raw[];
-    const EmPassArgs &a = args.a;
-    if (skip_block(a.status, a.iter)) return;   // uniform across the block
-    const int D = a.D, G = a.G, NG = args.NG, nk = args.nk;
-    const TcSmem Ls = tc_layout(NG);
-    unsigned char *sbase = tc_raw + ((1024u - (smem_u32(tc_raw) & 1023u)) & 1023u);
-    unsigned char *sB = sbase + Ls.B;
-    unsigned char *sA = sbase + Ls.A;
-    float2 *cst = reinterpret_cast<float2 *>(sbase + Ls.cst);
-    float *ctr = reinterpret_cast<float *>(sbase + Ls.ctr);
-    uint8_t *cg = reinterpret_cast<uint8_t *>(sbase + Ls.cg);
-    float *xlo = reinterpret_cast<float *>(sbase + Ls.xlo);
-    uint64_t *bar_afull = reinterpret_cast<uint64_t *>(sbase + Ls.bars);
-    uint64_t *bar_lfull = bar_afull + 1;
-    uint64_t *bar_lfree = bar_afull + 2;
-    uint64_t *bar_drain = bar_afull + 3;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sbase + Ls.misc);
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(sbase + Ls.misc + 4);
-
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const long long budget = a.wait_cycles;
-    const int64_t ntiles = (a.N + kTM - 1) / kTM;
-    const int64_t t0 = ntiles * blockIdx.x / gridDim.x, t1 = ntiles * (blockIdx.x + 1) / gridDim.x;
-    const int T = (int)(t1 - t0);
-
-    // BF16 operand A of tile `tile` -> A buffer b: row r = [x'^2 | x'] (K blocks 0 | 1), warp per row
-    auto build_a = [&](int64_t tile, int b) {
-        const int64_t i0 = tile * kTM;
-        unsigned char *ab = sA + b * (kTM * 256);
-#pragma unroll 4
-        for (int i = 0; i < kTM / 8; ++i) {
-            const int r = warp + 8 * i;
-            const bool v = i0 + r < a.N;
-            const float *row = a.X + (i0 + r) * D;
-#pragma unroll
-            for (int hh = 0; hh < 2; ++hh) {
-                const int d = lane + 32 * hh;
-                const float xc = (v && d < D) ? __ldcs(row + d) - ctr[d] : 0.f;
-                const uint32_t off = sw128_off(r, d >> 3) + (uint32_t)((d & 7) * 2);
-                *reinterpret_cast<__nv_bfloat16 *>(ab + off) = __float2bfloat16_rn(xc * xc);
-                *reinterpret_cast<__nv_bfloat16 *>(ab + 16384 + off) = __float2bfloat16_rn(xc);
-            }
-        }
-    };
-
-    if (tid == 0) {
-        mbar_init(bar_afull, 1);
-        mbar_init(bar_lfull, 1);
-        mbar_init(bar_lfree, 1);
-        mbar_init(bar_drain, 1);
-        *abort_flag = 0;
-    }
-    if (warp == 8) {
-        tmem_alloc(tmem_slot, 512);
-        tmem_relinquish();
-    } else {
-        for (int k = tid; k < NG * 16; k += kEpiThreads) {
-            const int g = k >> 4, kb = (k >> 3) & 1, c = k & 7;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (g < G) v = __ldg(reinterpret_cast<const uint4 *>(a.op.B + (size_t)g * 128 + kb * 64) + c);
-            *reinterpret_cast<uint4 *>(sB + (uint32_t)kb * NG * 128u + sw128_off(g, c)) = v;
-        }
-        for (int g = tid; g < NG; g += kEpiThreads) {
-            if (g < G) {
-                const float ct = __ldg(a.op.ctc + g);
-                // 2^-8 * 1.25 * q/2  +  2^-21 |ctc|  +  1e-4
-                const float k2 = 0.00390625f * 1.25f * 0.5f * __ldg(a.op.q + g) + 4.76837158203125e-07f * fabsf(ct) + 1e-4f;
-                cst[g] = make_float2(ct, k2);
-            } else {
-                cst[g] = make_float2(-INFINITY, 0.f);
-            }
-        }
-        for (int d = tid; d < 64; d += kEpiThreads) ctr[d] = d < D ? __ldg(a.center + d) : 0.f;
-    }
-    __syncthreads();   // centre in place for the first A
-    if (warp < 8 && T > 0) {
-        build_a(t0, 0);
-        fence_proxy_async();
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = *tmem_slot;
-    if (tid == 0 && T > 0) mbar_arrive(bar_afull);
-
-    unsigned long long st_kept = 0, st_dense = 0, st_n = 0;
-    unsigned long long tp[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // phase cycles (thread 0, profiling only)
-    long long tmark = clock64();
-    auto phase = [&](int k) {
-        const long long now = clock64();
-        tp[k] += (unsigned long long)(now - tmark);
-        tmark = now;
-    };
-    if (warp == 8) {
-        // ------------------------------------------------------------ MMA issuer
-        if (lane == 0) {
-            const uint32_t idesc = idesc_bf16(kTM, NG);
-            const uint32_t aS = smem_u32(sA), bS = smem_u32(sB);
-            for (int t = 0; t < T; ++t) {
-                if (!mbar_wait(bar_afull, (uint32_t)(t & 1), abort_flag, budget)) break;
-                if (t > 0 && !mbar_wait(bar_lfree, (uint32_t)((t - 1) & 1), abort_flag, budget)) break;
-                tc_fence_after();
-                if (a.skip_mma) continue;   // test hook: the epilogue's wait must run out
-                const uint32_t ab = aS + (uint32_t)(t & 1) * (kTM * 256u);
-                for (int kb = 0; kb < 2; ++kb)
-                    for (int kk = 0; kk < nk; ++kk)
-                        tc_mma(tmem + (uint32_t)(kb * 256), desc_k_sw128(ab + kb * 16384u + kk * 32u),
-                               desc_k_sw128(bS + (uint32_t)kb * NG * 128u + kk * 32u), idesc, kk > 0 ? 1u : 0u);
-                tc_commit(bar_lfull);
-            }
-            // drain: every MMA issued above must be complete before TMEM is
-            // freed, so this wait ignores the abort flag (it is still bounded)
-            tc_commit(bar_drain);
-            const long long d0 = clock64();
-            while (!mbar_try_wait(bar_drain, 0u) && clock64() - d0 < budget) {
-            }
-        }
-        __syncwarp();
-    } else {
-        // ------------------------------------------------------------ epilogue
-        const int q = warp & 3, h = warp >> 2;
-        const int s = 32 * q + lane;            // this thread's sample in the tile (TMEM lane)
-        const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);
-        uint8_t *my = cg + tid * kCap;
-        for (int t = 0; t < T; ++t) {
-            const int64_t tile = t0 + t;
-            const int64_t i0 = tile * kTM;
-            const int nvalid = (int)min((int64_t)kTM, a.N - i0);
-            // ---- the next tile's BF16 operand
-            if (t + 1 < T) {
-                build_a(tile + 1, (t + 1) & 1);
-                fence_proxy_async();
-            }
-            phase(0);
-            epi_sync();
-            if (tid == 0 && t + 1 < T) mbar_arrive(bar_afull);
-            phase(1);
-            // ---- pass 1: screening bounds from the two TMEM accumulators
-            mbar_wait(bar_lfull, (uint32_t)(t & 1), abort_flag, budget);
-            tc_fence_after();
-            phase(2);
-            float ub[128];
-            float lo = -INFINITY;
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                const int g0 = 128 * h + 16 * c;
-                if (g0 < NG) {
-                    uint32_t p1[16], p2[16];
-                    tmem_ld16(tl + (uint32_t)g0, p1);
-                    tmem_ld16(tl + 256u + (uint32_t)g0, p2);
-                    tmem_wait_ld();
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const float P1 = __uint_as_float(p1[j]), P2 = __uint_as_float(p2[j]);
-                        const float2 k = cst[g0 + j];
-                        const float l = (P1 + P2) + k.x;
-                        const float e = fmaf(fabsf(P1), kK1, k.y);
-                        ub[16 * c + j] = l + e;
-                        lo = fmaxf(lo, l - e);
-                    }
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) ub[16 * c + j] = -INFINITY;
-                }
-            }
-            tc_fence_before();
-            phase(3);
-            xlo[tid] = lo;
-            epi_sync();
-            if (tid == 0) mbar_arrive(bar_lfree);
-            lo = fmaxf(xlo[s], xlo[kTM + s]);
-            // ---- pass 2: candidate list of this (sample, half) -> global
-            const float thr = lo - args.screen;
-            const int gend = G - 128 * h;   // only real Gaussians (also when every bound is NaN/-inf)
-            int n = 0;
-#pragma unroll
-            for (int j = 0; j < 128; ++j) {
-                if (j < gend && ub[j] >= thr) {
-                    if (n < kCap) my[n] = (uint8_t)j;
-                    ++n;
-                }
-            }
-            if (s < nvalid) {
-                const int64_t rec = (i0 + s) * 2 + h;
-                args.L.cnt[rec] = (uint8_t)min(n, 255);
-                if (n > 0 && n <= kCap)
-                    reinterpret_cast<uint4 *>(args.L.cand)[rec] = *reinterpret_cast<const uint4 *>(my);
-                st_n += (h == 0);
-                st_kept += (unsigned long long)n;
-                st_dense += n > kCap;
-            }
-            phase(4);
-        }
-        tc_fence_before();
-    }
-    __syncthreads();
-    if (a.screen_stats && warp < 8) {
-        for (int o = 16; o > 0; o >>= 1) {
-            st_n += __shfl_xor_sync(0xffffffffu, st_n, o);
-            st_kept += __shfl_xor_sync(0xffffffffu, st_kept, o);
-            st_dense += __shfl_xor_sync(0xffffffffu, st_dense, o);
-        }
-        if (lane == 0) {
-            atomicAdd(a.screen_stats + 0, st_n);
-            atomicAdd(a.screen_stats + 1, st_kept);
-            atomicAdd(a.screen_stats + 2, st_dense);
-        }
-        if (tid == 0)
-            for (int k = 0; k < 8; ++k) atomicAdd(a.screen_stats + 3 + k, tp[k]);
-    }
-    if (tid == 0 && *abort_flag) {
-        if (atomicCAS(&a.status->code, 0, (int)GMM_ERR_TIMEOUT) == 0) a.status->fail_iter = a.iter;
-        atomicExch(&a.status->halt, 1);
-    }
-    if (warp == 8) {
-        tc_fence_after();
-        tmem_dealloc(tmem, 512);
-    }
-}
-
 // ------------------------------------------------------------------------
 // Bulk (untiled TMA) copies global -> shared, completing on an mbarrier.
 // Addresses 16-byte aligned, sizes multiples of 16 bytes.
@@ -479,6 +219,322 @@ __device__ __forceinline__ bool stage_wait(uint64_t *bar, uint32_t parity, long 
         if (clock64() - t0 > budget) { *abort_flag = 1; return false; }
     }
     return true;
+}
+
+struct TcArgs {
+    EmPassArgs a;
+    TcLists L;
+    int32_t NG;       // Gaussians padded to a multiple of 16 (MMA N)
+    int32_t nk;       // K=16 steps per K block: ceil(D/16)
+    float screen;     // screening distance in nats, ln(N * 1e9)
+    int32_t x_al16;   // X is 16-byte aligned: whole tiles are staged by bulk copies
+};
+
+struct TcSmem {
+    uint32_t B, A, X, xstride, cst, ctr, cg, xlo, cn, bars, misc, total;
+};
+
+__host__ __device__ inline TcSmem tc_layout(int D, int NG)
+{
+    TcSmem L;
+    uint32_t o = 0;
+    L.B = o; o += 2u * NG * 128u;                        // two K blocks of [NG][128 B]
+    L.A = o; o += 2u * kTM * 256u;                       // two buffers x two K blocks of [128][128 B]
+    L.xstride = ((4u * kTM * (uint32_t)D) + 127u) & ~127u;
+    L.X = o; o += 2u * L.xstride;                        // two staged FP32 sample tiles
+    L.cst = o; o += 8u * NG;                             // (ctc, k2) per Gaussian
+    L.ctr = o; o += 4u * 64u;                            // centre
+    L.cg = o; o += (uint32_t)kEpiThreads * kCap;         // candidate list staging, 16 B per thread
+    L.xlo = o; o += 4u * kEpiThreads;                    // best lower bound per (sample, quarter)
+    L.cn = o; o += 4u * kEpiThreads;                     // candidates per (sample, quarter)
+    o = (o + 7u) & ~7u;
+    L.bars = o; o += 8u * 6u;
+    L.misc = o; o += 16u;
+    L.total = o;
+    return L;
+}
+
+// ------------------------------------------------------------------------
+// 1. Screening on the tensor cores.  Warp roles: warps 0-15 are the
+// epilogue (warp w reads TMEM lanes 32*(w%4).., i.e. samples 32*(w%4)..,
+// and Gaussians 64*(w/4)..64*(w/4)+63 of both accumulators), warp 16
+// allocates TMEM and one of its threads issues the MMAs.  Each FP32 sample
+// tile is staged by a bulk copy three tiles ahead; the BF16 operand of tile
+// t+1 is built from it (double-buffered) while the MMAs of tile t+1 follow
+// the screening of tile t.  Output per (sample, half of the Gaussians): the
+// candidates of its two quarters merged into one list of at most kTcCap,
+// else the half is marked dense.  Every wait is bounded: on expiry the CTA
+// records GMM_ERR_TIMEOUT, stops issuing work, drains, frees TMEM and returns.
+// ------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads, 1) k_em_screen_tc(TcArgs args)
+{
+    extern __shared__ __align__(1024) unsigned char tc_raw[];
+    const EmPassArgs &a = args.a;
+    if (skip_block(a.status, a.iter)) return;   // uniform across the block
+    const int D = a.D, G = a.G, NG = args.NG, nk = args.nk;
+    const TcSmem Ls = tc_layout(D, NG);
+    unsigned char *sbase = tc_raw + ((1024u - (smem_u32(tc_raw) & 1023u)) & 1023u);
+    unsigned char *sB = sbase + Ls.B;
+    unsigned char *sA = sbase + Ls.A;
+    float2 *cst = reinterpret_cast<float2 *>(sbase + Ls.cst);
+    float *ctr = reinterpret_cast<float *>(sbase + Ls.ctr);
+    uint8_t *cg = reinterpret_cast<uint8_t *>(sbase + Ls.cg);
+    float *xlo = reinterpret_cast<float *>(sbase + Ls.xlo);
+    int *cn = reinterpret_cast<int *>(sbase + Ls.cn);
+    uint64_t *bar_afull = reinterpret_cast<uint64_t *>(sbase + Ls.bars);
+    uint64_t *bar_lfull = bar_afull + 1;
+    uint64_t *bar_lfree = bar_afull + 2;
+    uint64_t *bar_drain = bar_afull + 3;
+    uint64_t *bar_x = bar_afull + 4;   // [2] staged sample tiles
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sbase + Ls.misc);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(sbase + Ls.misc + 4);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long budget = a.wait_cycles;
+    const int64_t ntiles = (a.N + kTM - 1) / kTM;
+    const int64_t t0 = ntiles * blockIdx.x / gridDim.x, t1 = ntiles * (blockIdx.x + 1) / gridDim.x;
+    const int T = (int)(t1 - t0);
+    uint32_t xuse0 = 0u, xuse1 = 0u;   // consumed bulk tiles per buffer (epilogue threads)
+    uint32_t xiss0 = 0u, xiss1 = 0u;   // issued bulk tiles per buffer (thread 0)
+
+    auto issue_x = [&](int64_t tile) {   // thread 0 only; buffer tile & 1
+        const int b = (int)(tile & 1);
+        if (b) ++xiss1; else ++xiss0;
+        const uint32_t xb = 4u * kTM * (uint32_t)D;
+        fence_proxy_async();
+        mbar_expect_tx(bar_x + b, xb);
+        bulk_g2s(sbase + Ls.X + (uint32_t)b * Ls.xstride, a.X + tile * kTM * D, xb, bar_x + b);
+    };
+    // BF16 operand A of tile `tile` -> A buffer b: row r = [x'^2 | x'] (K
+    // blocks 0 | 1), warp per row, from the staged tile (or from global for
+    // a tile that is not staged)
+    auto build_a = [&](int64_t tile, int b) {
+        const int64_t i0 = tile * kTM;
+        unsigned char *ab = sA + b * (kTM * 256);
+        const bool staged = tile_is_bulk(i0, a.N, args.x_al16);
+        if (staged) {
+            const int xb = (int)(tile & 1);
+            if (stage_wait(bar_x + xb, (xb ? xuse1 : xuse0) & 1u, budget, abort_flag)) {
+                if (xb) ++xuse1; else ++xuse0;
+            }
+        }
+        const float *xt = reinterpret_cast<const float *>(sbase + Ls.X + (uint32_t)(tile & 1) * Ls.xstride);
+#pragma unroll 2
+        for (int i = 0; i < kTM / 16; ++i) {
+            const int r = warp + 16 * i;
+            const bool v = i0 + r < a.N;
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                const int d = lane + 32 * hh;
+                float xv = 0.f;
+                if (v && d < D) xv = staged ? xt[r * D + d] : __ldg(a.X + (i0 + r) * D + d);
+                const float xc = (v && d < D) ? xv - ctr[d] : 0.f;
+                const uint32_t off = sw128_off(r, d >> 3) + (uint32_t)((d & 7) * 2);
+                *reinterpret_cast<__nv_bfloat16 *>(ab + off) = __float2bfloat16_rn(xc * xc);
+                *reinterpret_cast<__nv_bfloat16 *>(ab + 16384 + off) = __float2bfloat16_rn(xc);
+            }
+        }
+    };
+
+    if (tid == 0) {
+        for (int k = 0; k < 6; ++k) mbar_init(bar_afull + k, 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 16) {
+        tmem_alloc(tmem_slot, 512);
+        tmem_relinquish();
+    } else {
+        for (int k = tid; k < NG * 16; k += kEpiThreads) {
+            const int g = k >> 4, kb = (k >> 3) & 1, c = k & 7;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (g < G) v = __ldg(reinterpret_cast<const uint4 *>(a.op.B + (size_t)g * 128 + kb * 64) + c);
+            *reinterpret_cast<uint4 *>(sB + (uint32_t)kb * NG * 128u + sw128_off(g, c)) = v;
+        }
+        for (int g = tid; g < NG; g += kEpiThreads) {
+            if (g < G) {
+                const float ct = __ldg(a.op.ctc + g);
+                // 2^-8 * 1.25 * q/2  +  2^-21 |ctc|  +  1e-4
+                const float k2 = 0.00390625f * 1.25f * 0.5f * __ldg(a.op.q + g) + 4.76837158203125e-07f * fabsf(ct) + 1e-4f;
+                cst[g] = make_float2(ct, k2);
+            } else {
+                cst[g] = make_float2(-INFINITY, 0.f);
+            }
+        }
+        for (int d = tid; d < 64; d += kEpiThreads) ctr[d] = d < D ? __ldg(a.center + d) : 0.f;
+    }
+    __syncthreads();   // barriers initialised, centre in place
+    if (tid == 0)
+        for (int k = 0; k < 2 && k < T; ++k)
+            if (tile_is_bulk((t0 + k) * kTM, a.N, args.x_al16)) issue_x(t0 + k);
+    if (warp < 16 && T > 0) {
+        build_a(t0, 0);
+        fence_proxy_async();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    if (tid == 0 && T > 0) {
+        mbar_arrive(bar_afull);
+        if (2 < T && tile_is_bulk((t0 + 2) * kTM, a.N, args.x_al16)) issue_x(t0 + 2);
+    }
+
+    unsigned long long st_kept = 0, st_dense = 0, st_n = 0;
+    unsigned long long tp[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // phase cycles (thread 0, profiling only)
+    long long tmark = clock64();
+    auto phase = [&](int k) {
+        const long long now = clock64();
+        tp[k] += (unsigned long long)(now - tmark);
+        tmark = now;
+    };
+    if (warp == 16) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16(kTM, NG);
+            const uint32_t aS = smem_u32(sA), bS = smem_u32(sB);
+            for (int t = 0; t < T; ++t) {
+                if (!mbar_wait(bar_afull, (uint32_t)(t & 1), abort_flag, budget)) break;
+                if (t > 0 && !mbar_wait(bar_lfree, (uint32_t)((t - 1) & 1), abort_flag, budget)) break;
+                tc_fence_after();
+                if (a.skip_mma) continue;   // test hook: the epilogue's wait must run out
+                const uint32_t ab = aS + (uint32_t)(t & 1) * (kTM * 256u);
+                for (int kb = 0; kb < 2; ++kb)
+                    for (int kk = 0; kk < nk; ++kk)
+                        tc_mma(tmem + (uint32_t)(kb * 256), desc_k_sw128(ab + kb * 16384u + kk * 32u),
+                               desc_k_sw128(bS + (uint32_t)kb * NG * 128u + kk * 32u), idesc, kk > 0 ? 1u : 0u);
+                tc_commit(bar_lfull);
+            }
+            // drain: every MMA issued above must be complete before TMEM is
+            // freed, so this wait ignores the abort flag (it is still bounded)
+            tc_commit(bar_drain);
+            const long long d0 = clock64();
+            while (!mbar_try_wait(bar_drain, 0u) && clock64() - d0 < budget) {
+            }
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------------------ epilogue
+        const int q = warp & 3, c = warp >> 2;  // lane quadrant, Gaussian quarter
+        const int s = 32 * q + lane;            // this thread's sample in the tile (TMEM lane)
+        const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);
+        uint8_t *my = cg + tid * kCap;
+        for (int t = 0; t < T; ++t) {
+            const int64_t tile = t0 + t;
+            const int64_t i0 = tile * kTM;
+            const int nvalid = (int)min((int64_t)kTM, a.N - i0);
+            // ---- the next tile's BF16 operand
+            if (t + 1 < T) {
+                build_a(tile + 1, (t + 1) & 1);
+                fence_proxy_async();
+            }
+            phase(0);
+            epi_sync();
+            if (tid == 0) {
+                if (t + 1 < T) mbar_arrive(bar_afull);
+                // the staged buffer of tile t+1 is free again: tile t+3 goes there
+                if (t + 3 < T && tile_is_bulk((tile + 3) * kTM, a.N, args.x_al16)) issue_x(tile + 3);
+            }
+            phase(1);
+            // ---- pass 1: screening bounds from the two TMEM accumulators
+            mbar_wait(bar_lfull, (uint32_t)(t & 1), abort_flag, budget);
+            tc_fence_after();
+            phase(2);
+            float ub[64];
+            float lo = -INFINITY;
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) {
+                const int g0 = 64 * c + 16 * cc;
+                if (g0 < NG) {
+                    uint32_t p1[16], p2[16];
+                    tmem_ld16(tl + (uint32_t)g0, p1);
+                    tmem_ld16(tl + 256u + (uint32_t)g0, p2);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const float P1 = __uint_as_float(p1[j]), P2 = __uint_as_float(p2[j]);
+                        const float2 k = cst[g0 + j];
+                        const float l = (P1 + P2) + k.x;
+                        const float e = fmaf(fabsf(P1), kK1, k.y);
+                        ub[16 * cc + j] = l + e;
+                        lo = fmaxf(lo, l - e);
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) ub[16 * cc + j] = -INFINITY;
+                }
+            }
+            tc_fence_before();
+            phase(3);
+            xlo[tid] = lo;
+            epi_sync();
+            if (tid == 0) mbar_arrive(bar_lfree);
+            lo = fmaxf(fmaxf(xlo[s], xlo[kTM + s]), fmaxf(xlo[2 * kTM + s], xlo[3 * kTM + s]));
+            // ---- pass 2: candidate list of this (sample, quarter)
+            const float thr = lo - args.screen;
+            const int gend = G - 64 * c;   // only real Gaussians (also when every bound is NaN/-inf)
+            int n = 0;
+#pragma unroll
+            for (int j = 0; j < 64; ++j) {
+                if (j < gend && ub[j] >= thr) {
+                    if (n < kCap) my[n] = (uint8_t)j;
+                    ++n;
+                }
+            }
+            cn[tid] = n;
+            epi_sync();
+            // ---- the two quarters of a half -> one record (threads of even quarters)
+            if ((c & 1) == 0 && s < nvalid) {
+                const int h = c >> 1;
+                const int nb = cn[tid + 128];
+                const int tot = n + nb;
+                const int64_t rec = (i0 + s) * 2 + h;
+                args.L.cnt[rec] = (uint8_t)(n > kCap || nb > kCap ? 255 : min(tot, 255));
+                if (tot > 0 && tot <= kCap) {
+                    const uint8_t *yb = cg + (tid + 128) * kCap;
+                    for (int k = 0; k < nb; ++k) my[n + k] = (uint8_t)(64 + yb[k]);
+                    reinterpret_cast<uint4 *>(args.L.cand)[rec] = *reinterpret_cast<const uint4 *>(my);
+                }
+                st_n += (h == 0);
+                st_kept += (unsigned long long)tot;
+                st_dense += tot > kCap;
+            }
+            phase(4);
+        }
+        tc_fence_before();
+    }
+    __syncthreads();
+    // drain: no bulk copy may still be writing into shared memory at exit
+    if (tid == 0)
+        for (int bb = 0; bb < 2; ++bb) {
+            const uint32_t issued = bb ? xiss1 : xiss0, used = bb ? xuse1 : xuse0;
+            const long long d0 = clock64();
+            for (uint32_t u = used; u < issued; ++u)
+                while (!mbar_try_wait(bar_x + bb, u & 1u) && clock64() - d0 < budget) {
+                }
+        }
+    if (a.screen_stats && warp < 16) {
+        for (int o = 16; o > 0; o >>= 1) {
+            st_n += __shfl_xor_sync(0xffffffffu, st_n, o);
+            st_kept += __shfl_xor_sync(0xffffffffu, st_kept, o);
+            st_dense += __shfl_xor_sync(0xffffffffu, st_dense, o);
+        }
+        if (lane == 0) {
+            atomicAdd(a.screen_stats + 0, st_n);
+            atomicAdd(a.screen_stats + 1, st_kept);
+            atomicAdd(a.screen_stats + 2, st_dense);
+        }
+        if (tid == 0)
+            for (int k = 0; k < 8; ++k) atomicAdd(a.screen_stats + 3 + k, tp[k]);
+    }
+    if (tid == 0 && *abort_flag) {
+        if (atomicCAS(&a.status->code, 0, (int)GMM_ERR_TIMEOUT) == 0) a.status->fail_iter = a.iter;
+        atomicExch(&a.status->halt, 1);
+    }
+    if (warp == 16) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 512);
+    }
 }
 
 struct ExArgs {
@@ -564,10 +620,12 @@ __global__ void __launch_bounds__(kExThreads, 1) k_em_exact(ExArgs args)
     int64_t *sp_ig = L.sp_ig + (size_t)blockIdx.x * kTcSpill;
     float *sp_gam = L.sp_gam + (size_t)blockIdx.x * kTcSpill;
 
+    uint32_t iss0 = 0u, iss1 = 0u;   // issued bulk tiles per buffer (thread 0)
     auto issue = [&](int64_t tile, int b) {   // thread 0 only
         const int64_t i0 = tile * kST;
         const uint32_t xb = 4u * kST * (uint32_t)D;
         const uint32_t bo = (uint32_t)b * (Ls.X[1] - Ls.X[0]);
+        if (b) ++iss1; else ++iss0;
         fence_proxy_async();
         mbar_expect_tx(bars + b, xb + 32u * kST + 2u * kST);
         bulk_g2s(ex_raw + Ls.X[0] + bo, a.X + i0 * D, xb, bars + b);
@@ -810,9 +868,7 @@ __global__ void __launch_bounds__(kExThreads, 1) k_em_exact(ExArgs args)
     // drain: no bulk copy may still be writing into shared memory at exit
     if (tid == 0)
         for (int bb = 0; bb < 2; ++bb) {
-            uint32_t issued = 0;
-            for (int64_t t = t0 + bb; t < t1; t += 2)
-                if (tile_is_bulk(t * kST, a.N, args.x_al16)) ++issued;
+            const uint32_t issued = bb ? iss1 : iss0;
             const uint32_t used = bb ? use1 : use0;
             const long long d0 = clock64();
             for (uint32_t u = used; u < issued; ++u)
@@ -923,10 +979,12 @@ __global__ void __launch_bounds__(kMsThreads, 1) k_em_mstep_lists(ExArgs args)
         if (lane == 0) atomicAdd(sg, gv);
     };
 
+    uint32_t iss0 = 0u, iss1 = 0u;   // issued bulk tiles per buffer (thread 0)
     auto issue = [&](int64_t tile, int b) {   // thread 0 only
         const int64_t i0 = tile * kST;
         const uint32_t xb = 4u * kST * (uint32_t)D;
         const uint32_t bo = (uint32_t)b * (Ls.X[1] - Ls.X[0]);
+        if (b) ++iss1; else ++iss0;
         fence_proxy_async();
         mbar_expect_tx(bars + b, xb + 5u * kST * kTcKeep + kST);
         bulk_g2s(ms_raw + Ls.X[0] + bo, a.X + i0 * D, xb, bars + b);
@@ -1076,9 +1134,7 @@ __global__ void __launch_bounds__(kMsThreads, 1) k_em_mstep_lists(ExArgs args)
     // drain: no bulk copy may still be writing into shared memory at exit
     if (tid == 0)
         for (int bb = 0; bb < 2; ++bb) {
-            uint32_t issued = 0;
-            for (int64_t t = t0 + bb; t < t1; t += 2)
-                if (tile_is_bulk(t * kST, a.N, args.x_al16)) ++issued;
+            const uint32_t issued = bb ? iss1 : iss0;
             const uint32_t used = bb ? use1 : use0;
             const long long d0 = clock64();
             for (uint32_t u = used; u < issued; ++u)
@@ -1138,7 +1194,7 @@ bool em_tc_supported(int32_t D, int32_t G)
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     // dynamic layouts plus the kernels' static shared memory
-    return tc_layout(NG).total + 1024u + 2048u <= (uint32_t)optin && ex_wp(D, G) >= 32 &&
+    return tc_layout(D, NG).total + 1024u + 2048u <= (uint32_t)optin && ex_wp(D, G) >= 32 &&
            ms_layout(D, G).total + 2048u <= (uint32_t)optin;
 }
 
@@ -1175,13 +1231,13 @@ TcLists em_tc_lists(void *base, int64_t N, int grid)
 cudaError_t launch_em_pass_tc(const EmPassArgs &a, const TcLists &L, int32_t grid, int32_t ms_grid, cudaStream_t s)
 {
     const float scr = (float)std::log((double)a.N * 1e9);
-    TcArgs t{a, L, (a.G + 15) / 16 * 16, (a.D + 15) / 16, scr};
-    const size_t sm1 = tc_layout(t.NG).total + 1024u;
+    const int al = (reinterpret_cast<uintptr_t>(a.X) & 15u) == 0;
+    TcArgs t{a, L, (a.G + 15) / 16 * 16, (a.D + 15) / 16, scr, al};
+    const size_t sm1 = tc_layout(a.D, t.NG).total + 1024u;
     cudaError_t e = cudaFuncSetAttribute(k_em_screen_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
     if (e != cudaSuccess) return e;
     k_em_screen_tc<<<grid, kThreads, sm1, s>>>(t);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const int al = (reinterpret_cast<uintptr_t>(a.X) & 15u) == 0;
     ExArgs x{a, L, scr, al, ex_wp(a.D, a.G)};
     const size_t sm2 = ex_layout(a.D, a.G, x.wp).total;
     if ((e = cudaFuncSetAttribute(k_em_exact, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2)) != cudaSuccess)
