@@ -546,11 +546,12 @@ struct ExArgs {
 };
 
 struct ExSmem {
-    uint32_t ps, pm, pc, X[2], cand[2], cnt[2], wl, wg, ws, bars, misc, total;
+    uint32_t psm, pc, X[2], cand[2], cnt[2], wl, wg, ws, bars, misc, total;
 };
 
-// The operands s = 1/sigma and mu s are two [G][DS] arrays with an odd row
-// stride DS, so lanes reading different Gaussians at one d hit distinct banks.
+// The operands (s = 1/sigma, mu s) are one [G][DS] float2 array with an odd
+// row stride DS, so lanes reading different Gaussians at one d spread over
+// the banks.
 __host__ __device__ inline int ex_stride(int D) { return D | 1; }
 
 __host__ __device__ inline ExSmem ex_layout(int D, int G, int wp)
@@ -558,8 +559,7 @@ __host__ __device__ inline ExSmem ex_layout(int D, int G, int wp)
     ExSmem L;
     const uint32_t DS = (uint32_t)ex_stride(D);
     uint32_t o = 0;
-    L.ps = o; o += 4u * (uint32_t)G * DS;
-    L.pm = o; o += 4u * (uint32_t)G * DS;
+    L.psm = o; o += 8u * (uint32_t)G * DS;
     L.pc = o; o += 4u * (uint32_t)G;
     o = (o + 127u) & ~127u;
     for (int b = 0; b < 2; ++b) {
@@ -603,8 +603,7 @@ __global__ void __launch_bounds__(kExThreads, 1) k_em_exact(ExArgs args)
     const int D = a.D, G = a.G, DS = ex_stride(D);
     const int WP = args.wp;
     const ExSmem Ls = ex_layout(D, G, WP);
-    float *pss = reinterpret_cast<float *>(ex_raw + Ls.ps);
-    float *pms = reinterpret_cast<float *>(ex_raw + Ls.pm);
+    float2 *psm = reinterpret_cast<float2 *>(ex_raw + Ls.psm);
     float *pc = reinterpret_cast<float *>(ex_raw + Ls.pc);
     uint64_t *bars = reinterpret_cast<uint64_t *>(ex_raw + Ls.bars);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(ex_raw + Ls.misc);
@@ -655,9 +654,7 @@ __global__ void __launch_bounds__(kExThreads, 1) k_em_exact(ExArgs args)
     }
     for (int k = tid; k < G * D; k += kExThreads) {
         const int g = k / D, d = k - g * D;
-        const float2 v = __ldg(a.op.sm + k);
-        pss[g * DS + d] = v.x;
-        pms[g * DS + d] = v.y;
+        psm[g * DS + d] = __ldg(a.op.sm + k);
     }
     for (int g = tid; g < G; g += kExThreads) pc[g] = __ldg(a.op.c + g);
     __syncthreads();
@@ -718,18 +715,23 @@ __global__ void __launch_bounds__(kExThreads, 1) k_em_exact(ExArgs args)
                 else g = 128 + (m1 > kCap ? j - d0 : cs[si * 32 + 16 + (j - d0)]);
                 // ---- exact log-density of the pair over all D
                 const float *xr = xs + si * D;
-                const float *qs = pss + g * DS, *qm = pms + g * DS;
+                const float2 *q = psm + g * DS;
                 float r0 = 0.f, r1 = 0.f;
-                int d = 0;
-                for (; d + 1 < D; d += 2) {
-                    const float ta = fmaf(xr[d], qs[d], -qm[d]);
-                    const float tb = fmaf(xr[d + 1], qs[d + 1], -qm[d + 1]);
-                    r0 = fmaf(ta, ta, r0);
-                    r1 = fmaf(tb, tb, r1);
-                }
-                if (d < D) {
-                    const float ta = fmaf(xr[d], qs[d], -qm[d]);
-                    r0 = fmaf(ta, ta, r0);
+                if ((D & 1) == 0) {   // the row is 8-byte aligned: two dimensions per load
+                    const float2 *x2 = reinterpret_cast<const float2 *>(xr);
+#pragma unroll 4
+                    for (int d2 = 0; d2 < D / 2; ++d2) {
+                        const float2 xv = x2[d2], qa = q[2 * d2], qb = q[2 * d2 + 1];
+                        const float ta = fmaf(xv.x, qa.x, -qa.y), tb = fmaf(xv.y, qb.x, -qb.y);
+                        r0 = fmaf(ta, ta, r0);
+                        r1 = fmaf(tb, tb, r1);
+                    }
+                } else {
+                    for (int d = 0; d < D; ++d) {
+                        const float2 qa = q[d];
+                        const float ta = fmaf(xr[d], qa.x, -qa.y);
+                        r0 = fmaf(ta, ta, r0);
+                    }
                 }
                 wl[p] = fmaf(-0.5f, r0 + r1, pc[g]);
                 wg[p] = (uint8_t)g;
@@ -809,10 +811,11 @@ __global__ void __launch_bounds__(kExThreads, 1) k_em_exact(ExArgs args)
                     return 128 + (m1 > kCap ? j - d0 : cs[si * 32 + 16 + (j - d0)]);
                 };
                 auto logit = [&](int g) -> float {
-                    const float *qs = pss + g * DS, *qm = pms + g * DS;
+                    const float2 *q = psm + g * DS;
                     float r0 = 0.f;
                     for (int d = 0; d < D; ++d) {
-                        const float tt = fmaf(xr[d], qs[d], -qm[d]);
+                        const float2 qa = q[d];
+                        const float tt = fmaf(xr[d], qa.x, -qa.y);
                         r0 = fmaf(tt, tt, r0);
                     }
                     return fmaf(-0.5f, r0, pc[g]);
