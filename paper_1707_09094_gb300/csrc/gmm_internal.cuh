@@ -62,7 +62,7 @@ struct EmFinalizeArgs {
     const double *par_in;    // [G*D means | G*D dcovs | G hefts]
     double *par_out;
     double var_floor;
-    int32_t shift_mode;      // 0: per-Gaussian FP32 means (op.mu), 1: tc_shift of the BF16 operand
+    int32_t shift_mode;      // reserved (0): the statistics are shifted by the FP32 means op.mu
     Operands op;
     const float *center;
     DevStatus *status;
@@ -71,19 +71,6 @@ struct EmFinalizeArgs {
     double *ll_hist;         // device history
     int32_t build_tc;        // also build the tensor-core operands
 };
-
-// Shift of the tensor-core pass's M-step sums for Gaussian g, dimension d:
-// the global centre plus the mean recovered from the two BF16 operand
-// entries (mu' iv) / (2 * (1/2) iv).  Any constant near the mean keeps the
-// FP32 sums of (x - shift) small; this one is already in shared memory.  The
-// pass and the reduce/update kernel evaluate it with the same correctly
-// rounded FP32 operations, so both see the same value.
-__device__ __forceinline__ float tc_shift(float center, __nv_bfloat16 b1, __nv_bfloat16 b2)
-{
-    const float f1 = __bfloat162float(b1), f2 = __bfloat162float(b2);
-    if (f1 == 0.f) return center;
-    return __fadd_rn(center, __fdiv_rn(f2, __fmul_rn(-2.f, f1)));
-}
 
 // Count of library kernels launched (process-wide, all models).
 void count_launches(int n);

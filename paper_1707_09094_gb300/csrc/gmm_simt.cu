@@ -805,9 +805,7 @@ __global__ void k_em_finalize(EmFinalizeArgs a)
     for (int d = threadIdx.x; d < D; d += blockDim.x) {
         double mu = mi[d], v = vi[d];
         if (live) {
-            const double shift = a.shift_mode == 0
-                                     ? (double)a.op.mu[(size_t)g * D + d]
-                                     : (double)tc_shift(a.center[d], a.op.B[(size_t)g * 128 + d], a.op.B[(size_t)g * 128 + 64 + d]);
+            const double shift = (double)a.op.mu[(size_t)g * D + d];   // the passes' FP32 shift
             const double m1 = red[1 + d] / Lg;
             mu = shift + m1;
             v = red[1 + D + d] / Lg - m1 * m1;
