@@ -297,6 +297,166 @@ __global__ void __launch_bounds__(kKmThreads) k_km_pass(KmArgs a)
     }
 }
 
+// Tiled form of the k-means map step for D <= 64 (one CTA per SM, its
+// contiguous chunk of samples).  Shared memory holds the scaled means
+// cs = mu sqrt(w) with an odd row stride, the chunk's FP32 statistics
+// [G][1 + 2D] (count, sum(x - mu_f), sum((x - mu_f)^2), shifted by the FP32
+// old mean mu_f), and a 64-sample tile of raw and scaled rows.  Warp w takes
+// samples 4w..4w+3 of the tile, lane l the means l, l+32, ... (up to 8):
+// 32 FP32 distances per thread in registers, the direct form
+// sum_d (xs_d - cs_d)^2 with the rounding bound of km_err.  A sample whose
+// runner-up is not provably behind is re-decided in FP64 by the whole warp,
+// one mean per lane, in the oracle's operation order, lowest index on exact
+// ties.  The statistics go to shared memory with atomics (one mean per
+// sample), and the chunk's FP32 statistics to its FP64 partial at the end.
+constexpr int kKmTileThreads = 512;
+constexpr int kKmTileS = 64;   // samples per tile
+
+__host__ __device__ inline int km_tile_cs(int D) { return D | 1; }
+
+__host__ __device__ inline size_t km_tile_smem(int D, int G)
+{
+    const size_t cs = (size_t)km_tile_cs(D);
+    return sizeof(float) * ((size_t)G * cs + (size_t)G + (size_t)G * (1 + 2 * D) + 2u * kKmTileS * 64u + 64u) + 64u;
+}
+
+__global__ void __launch_bounds__(kKmTileThreads, 1) k_km_tile(KmArgs a)
+{
+    extern __shared__ __align__(16) unsigned char kmt_smem[];
+    if (block_skip(a.status, 0)) return;
+    const int D = a.D, G = a.G, CS = km_tile_cs(D), S = 1 + 2 * D;
+    float *cent = reinterpret_cast<float *>(kmt_smem);        // [G][CS]
+    float *cnorm = cent + (size_t)G * CS;                       // [G]
+    float *slab = cnorm + G;                                    // [G][S]
+    float *xr = slab + (size_t)G * S;                           // [64][64] raw rows
+    float *xsc = xr + kKmTileS * 64;                            // [64][64] scaled rows
+    float *swd = xsc + kKmTileS * 64;                           // [64] sqrt(w)
+    __shared__ float s_nmax;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int d = tid; d < 64; d += kKmTileThreads) swd[d] = d < D ? a.sw[d] : 0.f;
+    for (int k = tid; k < G * S; k += kKmTileThreads) slab[k] = 0.f;
+    if (tid == 0) s_nmax = 0.f;
+    __syncthreads();
+    for (int k = tid; k < G * D; k += kKmTileThreads) {
+        const int g = k / D, d = k - g * D;
+        cent[g * CS + d] = (float)(a.means[k] * (double)swd[d]);
+    }
+    __syncthreads();
+    for (int g = tid; g < G; g += kKmTileThreads) {
+        float n = 0.f;
+        for (int d = 0; d < D; ++d) n = fmaf(cent[g * CS + d], cent[g * CS + d], n);
+        cnorm[g] = n;
+        atomicMax(reinterpret_cast<int *>(&s_nmax), __float_as_int(n));   // n >= 0
+    }
+    __syncthreads();
+    const float nmax_all = s_nmax;
+    const int64_t i0 = a.N * blockIdx.x / gridDim.x, i1 = a.N * (blockIdx.x + 1) / gridDim.x;
+    const int nj = (G + 31) / 32;
+    for (int64_t base = i0; base < i1; base += kKmTileS) {
+        const int nv = (int)min((int64_t)kKmTileS, i1 - base);
+        for (int k = tid; k < nv * D; k += kKmTileThreads) {
+            const int r = k / D, d = k - r * D;
+            const float v = __ldg(a.X + base * D + k);
+            xr[r * 64 + d] = v;
+            xsc[r * 64 + d] = v * swd[d];
+        }
+        __syncthreads();
+        const int sb = 4 * warp;
+        if (sb < nv) {
+            float acc[4][8];
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[k][j] = 0.f;
+            for (int d = 0; d < D; ++d) {
+                float xv[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) xv[k] = xsc[(sb + k) * 64 + d];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    if (j < nj) {
+                        const int g = lane + 32 * j;
+                        const float c = g < G ? cent[g * CS + d] : 0.f;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const float t = xv[k] - c;
+                            acc[k][j] = fmaf(t, t, acc[k][j]);
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int si = sb + k;   // warp-uniform
+                // best and runner-up over this lane's means, then over the warp
+                float b1 = INFINITY, b2 = INFINITY;
+                int a1 = 0x7fffffff;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int g = lane + 32 * j;
+                    if (j < nj && g < G) {
+                        const float v = acc[k][j];
+                        if (v < b1) { b2 = b1; b1 = v; a1 = g; }
+                        else if (v < b2) { b2 = v; }
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float ob1 = __shfl_xor_sync(0xffffffffu, b1, o);
+                    const float ob2 = __shfl_xor_sync(0xffffffffu, b2, o);
+                    const int oa1 = __shfl_xor_sync(0xffffffffu, a1, o);
+                    const bool take = ob1 < b1 || (ob1 == b1 && oa1 < a1);
+                    const float nb2 = take ? fminf(b1, ob2) : fminf(ob1, b2);
+                    if (take) { b1 = ob1; a1 = oa1; }
+                    b2 = nb2;
+                }
+                if (si >= nv) continue;
+                float sn = 0.f;
+                for (int d = lane; d < D; d += 32) sn = fmaf(xsc[si * 64 + d], xsc[si * 64 + d], sn);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) sn += __shfl_xor_sync(0xffffffffu, sn, o);
+                const float norms = sn + nmax_all;
+                int best = a1;
+                if (G > 1 && !(b2 - km_err(b2, norms, D) > b1 + km_err(b1, norms, D))) {
+                    // FP64 re-decision, one mean per lane, oracle order
+                    double bv = INFINITY;
+                    int bi = 0x7fffffff;
+                    for (int g = lane; g < G; g += 32) {
+                        const double *mu = a.means + (size_t)g * D;
+                        double accd = 0.0;
+                        for (int d = 0; d < D; ++d) {
+                            const double t = __dsub_rn((double)xr[si * 64 + d], mu[d]);
+                            accd = __dadd_rn(accd, __dmul_rn(a.w[d], __dmul_rn(t, t)));
+                        }
+                        if (accd < bv) { bv = accd; bi = g; }
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                        if (ov < bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+                    }
+                    best = bi;
+                }
+                const int64_t i = base + si;
+                if (lane == 0) a.assign[i] = best;
+                // statistics of the mean this sample joins
+                float *sg = slab + (size_t)best * S;
+                const double *mu = a.means + (size_t)best * D;
+                for (int d = lane; d < D; d += 32) {
+                    const float u = xr[si * 64 + d] - (float)mu[d];
+                    atomicAdd(sg + 1 + d, u);
+                    atomicAdd(sg + 1 + D + d, u * u);
+                }
+                if (lane == 0) atomicAdd(sg, 1.f);
+            }
+        }
+        __syncthreads();   // the tile buffers are reused
+    }
+    double *P = a.partial + (size_t)blockIdx.x * G * S;
+    for (int k = tid; k < G * S; k += kKmTileThreads) P[k] = (double)slab[k];
+}
+
 // k-means reduce + update (Sec. 3 (ii); Eqs. 5-7 with Eq. 19 for the last
 // iteration).  One block per Gaussian, partials summed in CTA order.
 __global__ void k_km_finalize(const double *__restrict__ partial, int n_partial, int64_t N, int32_t D,
@@ -1057,10 +1217,19 @@ int em_simt_grid(int32_t D, int32_t G, int sms)
     return sms * per;
 }
 
+static bool km_tile_fits(int32_t D, int32_t G)
+{
+    if (D > 64 || G > 256) return false;   // 8 means per lane
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return km_tile_smem(D, G) + 2048u <= (size_t)optin;
+}
+
 int km_grid(int32_t D, int32_t G, int sms)
 {
-    (void)D; (void)G;
-    return sms * 3;   // the means slab (<= 64 KB) lets three CTAs share an SM
+    if (km_tile_fits(D, G)) return sms;   // tiled form: one CTA per SM
+    return sms * 3;                       // the means slab (<= 64 KB) lets three CTAs share an SM
 }
 
 cudaError_t launch_global_stats(const float *X, int64_t N, int32_t D, double var_floor, int32_t dist,
@@ -1106,6 +1275,13 @@ cudaError_t launch_km_pass(const float *X, int64_t N, int32_t D, int32_t G, cons
     int GS, DP;
     const size_t sm = km_slab_smem(D, G, &GS, &DP);
     KmArgs a{X, N, D, DP, G, GS, par, wdist, sw, slab, partial, assign, status};
+    if (km_tile_fits(D, G)) {
+        const size_t smt = km_tile_smem(D, G);
+        cudaFuncSetAttribute(k_km_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smt);
+        k_km_tile<<<grid, kKmTileThreads, smt, s>>>(a);
+        count_launches(1);
+        return cudaGetLastError();
+    }
     const int dm = dmax_for(D);
 #define KM_LAUNCH(DM)                                                                              \
     do {                                                                                           \
