@@ -297,29 +297,38 @@ __global__ void __launch_bounds__(kKmThreads) k_km_pass(KmArgs a)
     }
 }
 
-// Tiled form of the k-means map step for D <= 64 (one CTA per SM, its
-// contiguous chunk of samples).  Shared memory holds the scaled means
-// cs = mu sqrt(w) with an odd row stride, the chunk's FP32 statistics
-// [G][1 + 2D] (count, sum(x - mu_f), sum((x - mu_f)^2), shifted by the FP32
-// old mean mu_f), and a 64-sample tile of raw and scaled rows.  Warp w takes
-// samples 4w..4w+3 of the tile, lane l the means l, l+32, ... (up to 8):
-// 32 FP32 distances per thread in registers, the direct form
-// sum_d (xs_d - cs_d)^2 with the rounding bound of km_err.  A sample whose
-// runner-up is not provably behind is re-decided in FP64 by the whole warp,
-// one mean per lane, in the oracle's operation order, lowest index on exact
-// ties.  The statistics go to shared memory with atomics (one mean per
-// sample), and the chunk's FP32 statistics to its FP64 partial at the end.
+// Tiled form of the k-means map step for D <= 64, N_G <= 256 (one CTA per
+// SM, its contiguous chunk of samples).  With scaled coordinates
+// xs = x sqrt(w), cs = mu sqrt(w) the nearest mean minimises the expanded
+// score s_g = |cs_g|^2 - 2 xs.cs_g (the distance minus the common |xs|^2):
+// one FMA per (sample, mean, dimension).  Shared memory holds the scaled
+// means with an odd row stride, their squared norms, the chunk's FP32
+// statistics [G][1 + 2D] (count, sum(x - mu_f), sum((x - mu_f)^2), shifted
+// by the FP32 old mean mu_f) and a 128-sample tile of scaled rows.  Warp w
+// takes samples 8w..8w+7 of the tile, lane l the means l, l+32, ...: 64
+// scores per thread in registers.
+// Rounding bound of a computed score (xs, cs each within 3u of the exact
+// scaled values, u = 2^-24; FMA accumulation over D terms; the final
+// subtraction): |s~ - s| <= (D + 8) u (|cs|^2 + 2 |xs| |cs|) to first order,
+// taken here with a factor 2 and the largest |cs|^2 of all means.  If the
+// runner-up minus the winner exceeds twice that bound the FP32 winner is the
+// exact winner; otherwise the whole warp re-decides in FP64, one mean per
+// lane, as sum_d w_d (x_d - mu_d)^2 in order d = 0..D-1 without fused
+// operations, lowest index on exact ties (the oracle's definition).  The
+// statistics go to shared memory with atomics (one mean per sample), and
+// the chunk's FP32 statistics to its FP64 partial at the end.
 constexpr int kKmTileThreads = 512;
-constexpr int kKmTileS = 64;   // samples per tile
+constexpr int kKmTileS = 128;   // samples per tile: 16 warps x 8
 
 __host__ __device__ inline int km_tile_cs(int D) { return D | 1; }
 
 __host__ __device__ inline size_t km_tile_smem(int D, int G)
 {
     const size_t cs = (size_t)km_tile_cs(D);
-    return sizeof(float) * ((size_t)G * cs + (size_t)G + (size_t)G * (1 + 2 * D) + 2u * kKmTileS * 64u + 64u) + 64u;
+    return sizeof(float) * ((size_t)G * cs + (size_t)G + (size_t)G * (1 + 2 * D) + (size_t)kKmTileS * 64u + 64u) + 64u;
 }
 
+template <int NJ>   // means per lane: ceil(N_G / 32) rounded up to a power of two
 __global__ void __launch_bounds__(kKmTileThreads, 1) k_km_tile(KmArgs a)
 {
     extern __shared__ __align__(16) unsigned char kmt_smem[];
@@ -328,8 +337,7 @@ __global__ void __launch_bounds__(kKmTileThreads, 1) k_km_tile(KmArgs a)
     float *cent = reinterpret_cast<float *>(kmt_smem);        // [G][CS]
     float *cnorm = cent + (size_t)G * CS;                       // [G]
     float *slab = cnorm + G;                                    // [G][S]
-    float *xr = slab + (size_t)G * S;                           // [64][64] raw rows
-    float *xsc = xr + kKmTileS * 64;                            // [64][64] scaled rows
+    float *xsc = slab + (size_t)G * S;                          // [128][64] scaled rows
     float *swd = xsc + kKmTileS * 64;                           // [64] sqrt(w)
     __shared__ float s_nmax;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -349,56 +357,55 @@ __global__ void __launch_bounds__(kKmTileThreads, 1) k_km_tile(KmArgs a)
         atomicMax(reinterpret_cast<int *>(&s_nmax), __float_as_int(n));   // n >= 0
     }
     __syncthreads();
-    const float nmax_all = s_nmax;
+    const float nmax = s_nmax;
+    const float kE = 2.0f * (float)(D + 8) * 5.9604644775390625e-08f;
     const int64_t i0 = a.N * blockIdx.x / gridDim.x, i1 = a.N * (blockIdx.x + 1) / gridDim.x;
-    const int nj = (G + 31) / 32;
+    float cn[NJ];
+    int ro[NJ];   // row offsets; lanes past the last mean read its row (their score is +inf)
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+        const int g = lane + 32 * j;
+        cn[j] = g < G ? cnorm[g] : INFINITY;
+        ro[j] = min(g, G - 1) * CS;
+    }
     for (int64_t base = i0; base < i1; base += kKmTileS) {
         const int nv = (int)min((int64_t)kKmTileS, i1 - base);
         for (int k = tid; k < nv * D; k += kKmTileThreads) {
             const int r = k / D, d = k - r * D;
-            const float v = __ldg(a.X + base * D + k);
-            xr[r * 64 + d] = v;
-            xsc[r * 64 + d] = v * swd[d];
+            xsc[r * 64 + d] = __ldg(a.X + base * D + k) * swd[d];
         }
         __syncthreads();
-        const int sb = 4 * warp;
+        const int sb = 8 * warp;
         if (sb < nv) {
-            float acc[4][8];
+            float acc[8][NJ];
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
+            for (int k = 0; k < 8; ++k)
 #pragma unroll
-                for (int j = 0; j < 8; ++j) acc[k][j] = 0.f;
+                for (int j = 0; j < NJ; ++j) acc[k][j] = 0.f;
+            const float *xrow = xsc + sb * 64;
+#pragma unroll 2
             for (int d = 0; d < D; ++d) {
-                float xv[4];
+                float xv[8], c[NJ];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) xv[k] = xsc[(sb + k) * 64 + d];
+                for (int k = 0; k < 8; ++k) xv[k] = xrow[k * 64 + d];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    if (j < nj) {
-                        const int g = lane + 32 * j;
-                        const float c = g < G ? cent[g * CS + d] : 0.f;
+                for (int j = 0; j < NJ; ++j) c[j] = cent[ro[j] + d];
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            const float t = xv[k] - c;
-                            acc[k][j] = fmaf(t, t, acc[k][j]);
-                        }
-                    }
-                }
+                for (int k = 0; k < 8; ++k)
+#pragma unroll
+                    for (int j = 0; j < NJ; ++j) acc[k][j] = fmaf(xv[k], c[j], acc[k][j]);
             }
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
+            for (int k = 0; k < 8; ++k) {
                 const int si = sb + k;   // warp-uniform
-                // best and runner-up over this lane's means, then over the warp
                 float b1 = INFINITY, b2 = INFINITY;
                 int a1 = 0x7fffffff;
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
+                for (int j = 0; j < NJ; ++j) {
+                    const float v = fmaf(-2.f, acc[k][j], cn[j]);
                     const int g = lane + 32 * j;
-                    if (j < nj && g < G) {
-                        const float v = acc[k][j];
-                        if (v < b1) { b2 = b1; b1 = v; a1 = g; }
-                        else if (v < b2) { b2 = v; }
-                    }
+                    if (v < b1) { b2 = b1; b1 = v; a1 = g; }
+                    else if (v < b2) { b2 = v; }
                 }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
@@ -412,12 +419,14 @@ __global__ void __launch_bounds__(kKmTileThreads, 1) k_km_tile(KmArgs a)
                 }
                 if (si >= nv) continue;
                 float sn = 0.f;
-                for (int d = lane; d < D; d += 32) sn = fmaf(xsc[si * 64 + d], xsc[si * 64 + d], sn);
+                for (int d = lane; d < D; d += 32) sn = fmaf(xrow[k * 64 + d], xrow[k * 64 + d], sn);
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) sn += __shfl_xor_sync(0xffffffffu, sn, o);
-                const float norms = sn + nmax_all;
+                const float E = kE * (nmax + 2.f * sqrtf(sn * nmax)) + 1e-30f;
+                const int64_t i = base + si;
+                const float *x = a.X + i * D;
                 int best = a1;
-                if (G > 1 && !(b2 - km_err(b2, norms, D) > b1 + km_err(b1, norms, D))) {
+                if (G > 1 && !(b2 - b1 > 2.f * E)) {
                     // FP64 re-decision, one mean per lane, oracle order
                     double bv = INFINITY;
                     int bi = 0x7fffffff;
@@ -425,7 +434,7 @@ __global__ void __launch_bounds__(kKmTileThreads, 1) k_km_tile(KmArgs a)
                         const double *mu = a.means + (size_t)g * D;
                         double accd = 0.0;
                         for (int d = 0; d < D; ++d) {
-                            const double t = __dsub_rn((double)xr[si * 64 + d], mu[d]);
+                            const double t = __dsub_rn((double)__ldg(x + d), mu[d]);
                             accd = __dadd_rn(accd, __dmul_rn(a.w[d], __dmul_rn(t, t)));
                         }
                         if (accd < bv) { bv = accd; bi = g; }
@@ -438,20 +447,19 @@ __global__ void __launch_bounds__(kKmTileThreads, 1) k_km_tile(KmArgs a)
                     }
                     best = bi;
                 }
-                const int64_t i = base + si;
                 if (lane == 0) a.assign[i] = best;
                 // statistics of the mean this sample joins
                 float *sg = slab + (size_t)best * S;
                 const double *mu = a.means + (size_t)best * D;
                 for (int d = lane; d < D; d += 32) {
-                    const float u = xr[si * 64 + d] - (float)mu[d];
+                    const float u = __ldg(x + d) - (float)mu[d];
                     atomicAdd(sg + 1 + d, u);
                     atomicAdd(sg + 1 + D + d, u * u);
                 }
                 if (lane == 0) atomicAdd(sg, 1.f);
             }
         }
-        __syncthreads();   // the tile buffers are reused
+        __syncthreads();   // the tile buffer is reused
     }
     double *P = a.partial + (size_t)blockIdx.x * G * S;
     for (int k = tid; k < G * S; k += kKmTileThreads) P[k] = (double)slab[k];
@@ -1277,8 +1285,16 @@ cudaError_t launch_km_pass(const float *X, int64_t N, int32_t D, int32_t G, cons
     KmArgs a{X, N, D, DP, G, GS, par, wdist, sw, slab, partial, assign, status};
     if (km_tile_fits(D, G)) {
         const size_t smt = km_tile_smem(D, G);
-        cudaFuncSetAttribute(k_km_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smt);
-        k_km_tile<<<grid, kKmTileThreads, smt, s>>>(a);
+#define KMT_LAUNCH(NJ)                                                                              \
+    do {                                                                                            \
+        cudaFuncSetAttribute(k_km_tile<NJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smt); \
+        k_km_tile<NJ><<<grid, kKmTileThreads, smt, s>>>(a);                                         \
+    } while (0)
+        if (G <= 32) KMT_LAUNCH(1);
+        else if (G <= 64) KMT_LAUNCH(2);
+        else if (G <= 128) KMT_LAUNCH(4);
+        else KMT_LAUNCH(8);
+#undef KMT_LAUNCH
         count_launches(1);
         return cudaGetLastError();
     }
