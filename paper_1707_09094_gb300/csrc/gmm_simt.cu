@@ -312,7 +312,8 @@ __global__ void __launch_bounds__(kKmThreads) k_km_pass(KmArgs a)
 // subtraction): |s~ - s| <= (D + 8) u (|cs|^2 + 2 |xs| |cs|) to first order,
 // taken here with a factor 2 and the largest |cs|^2 of all means.  If the
 // runner-up minus the winner exceeds twice that bound the FP32 winner is the
-// exact winner; otherwise the whole warp re-decides in FP64, one mean per
+// exact winner; otherwise the means whose score is within twice the bound of
+// the best (no other mean can win) are re-decided in FP64, each on its own
 // lane, as sum_d w_d (x_d - mu_d)^2 in order d = 0..D-1 without fused
 // operations, lowest index on exact ties (the oracle's definition).  The
 // statistics go to shared memory with atomics (one mean per sample), and
@@ -427,17 +428,24 @@ __global__ void __launch_bounds__(kKmTileThreads, 1) k_km_tile(KmArgs a)
                 const float *x = a.X + i * D;
                 int best = a1;
                 if (G > 1 && !(b2 - b1 > 2.f * E)) {
-                    // FP64 re-decision, one mean per lane, oracle order
+                    // FP64 re-decision among the means whose score is within 2E
+                    // of the best (every other mean is provably farther), each on
+                    // its own lane in the oracle's operation order
                     double bv = INFINITY;
                     int bi = 0x7fffffff;
-                    for (int g = lane; g < G; g += 32) {
-                        const double *mu = a.means + (size_t)g * D;
-                        double accd = 0.0;
-                        for (int d = 0; d < D; ++d) {
-                            const double t = __dsub_rn((double)__ldg(x + d), mu[d]);
-                            accd = __dadd_rn(accd, __dmul_rn(a.w[d], __dmul_rn(t, t)));
+                    const float lim = b1 + 2.f * E;
+#pragma unroll
+                    for (int j = 0; j < NJ; ++j) {
+                        const int g = lane + 32 * j;
+                        if (g < G && fmaf(-2.f, acc[k][j], cn[j]) <= lim) {
+                            const double *mu = a.means + (size_t)g * D;
+                            double accd = 0.0;
+                            for (int d = 0; d < D; ++d) {
+                                const double t = __dsub_rn((double)__ldg(x + d), mu[d]);
+                                accd = __dadd_rn(accd, __dmul_rn(a.w[d], __dmul_rn(t, t)));
+                            }
+                            if (accd < bv || (accd == bv && g < bi)) { bv = accd; bi = g; }
                         }
-                        if (accd < bv) { bv = accd; bi = g; }
                     }
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) {
