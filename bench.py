@@ -310,8 +310,7 @@ def run_ours(args):
         "clocks": r["clocks"],
         "e2e": {"value": world * units / (e2e["ms"] / args.steps * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": int(X.nbytes), "d2h_bytes_per_step": 8 + 32},
-        "kmeans": {"pass_ms": km_ms / max(km_n, 1), "units_per_s": units / (km_ms / max(km_n, 1) * 1e-3),
-                   "iterations_wall_ms": km_wall * 1e3 / 5},
+        "kmeans": kmeans_line(km_ms / max(km_n, 1), km_wall * 1e3 / 5, units, peaks, peak_src),
         "learn_10km_10em_s": min(learn_t),
         "forms": {p: {"value": world * units / (results[p]["ms"] / args.steps * 1e-3),
                       "ms_per_step": results[p]["ms"] / args.steps,
@@ -334,6 +333,17 @@ def run_ours(args):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def kmeans_line(pass_ms, wall_ms, units, peaks, peak_src):
+    """k-means map pass: 1 FMA per (i, g, d) (the expanded score), FP32 FMA-bound."""
+    peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    achieved = 2.0 * units / (pass_ms * 1e-3) / 1e12
+    return {"pass_ms": pass_ms, "units_per_s": units / (pass_ms * 1e-3), "iterations_wall_ms": wall_ms,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak,
+                         "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (%s clock)" %
+                                        (peaks.get("sm_max_mhz", 2070.0), peak_src)}}
 
 
 def run_batched_leg():
