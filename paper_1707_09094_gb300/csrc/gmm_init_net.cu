@@ -119,14 +119,22 @@ __global__ void k_relu_bwd(const float *__restrict__ dH, const __nv_bfloat16 *__
     dZ[e] = __float2bfloat16_rn(__bfloat162float(H[e]) > 0.f ? g : 0.f);
 }
 
-// db[n] += sum_m dZ[m][n]
+// db[n] += sum_m dZ[m][n]; blocks over (32 columns, a stride of rows)
 __global__ void k_colsum(const __nv_bfloat16 *__restrict__ dZ, float *__restrict__ db, int64_t M, int N)
 {
-    const int n = blockIdx.x * 32 + (threadIdx.x & 31);
-    if (n >= N) return;
+    __shared__ float part[8][33];
+    const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;   // 256 threads: 8 rows at a time
+    const int n = blockIdx.x * 32 + lane;
     float s = 0.f;
-    for (int64_t m = threadIdx.x >> 5; m < M; m += blockDim.x >> 5) s += __bfloat162float(dZ[m * N + n]);
-    atomicAdd(&db[n], s);
+    if (n < N)
+        for (int64_t m = (int64_t)blockIdx.y * 8 + wy; m < M; m += (int64_t)gridDim.y * 8) s += __bfloat162float(dZ[m * N + n]);
+    part[wy][lane] = s;
+    __syncthreads();
+    if (wy == 0 && n < N) {
+        float t = 0.f;
+        for (int k = 0; k < 8; ++k) t += part[k][lane];
+        atomicAdd(&db[n], t);
+    }
 }
 
 // pooled[b][n] = mean over p of H[b*P + p][n]; also a BF16 copy
@@ -156,99 +164,141 @@ __device__ __forceinline__ float bsum_f(float v, float *sh)
     return r;
 }
 
-// One block per set: predicted mixture from the network output, the loss and
-// its gradient with respect to the output (d_out), and the parameters.
-// Shared memory: w, m, v, logv-exp, stats S0 [G], S1 [G][D], S2 [G][D].
-__global__ void __launch_bounds__(256) k_set_loss(const float *__restrict__ out, const float *__restrict__ pts, int P, int D,
-                                                  int G, double var_floor, const double *__restrict__ tgt_m,
-                                                  const double *__restrict__ tgt_v, const double *__restrict__ tgt_w,
-                                                  double lambda, float *__restrict__ d_out, float *__restrict__ loss,
-                                                  double *__restrict__ pm, double *__restrict__ pv, double *__restrict__ pw,
-                                                  int B)
+// Loss of each set and its gradient with respect to the network output, in
+// three steps (lp = per-set mixture, st = per-set statistics, FP32):
+//  k_loss_prep   one block per set: hefts w = softmax(a), constants
+//                cst_g = log w_g - 1/2 sum_d log(2 pi v_gd), means m, inverse
+//                variances iv = 1/v with v = exp(r) + var_floor, and exp(r);
+//                zeroes the statistics and the NLL.
+//  k_loss_chunk  one block per (set, 128 points): log-densities and log-sum-
+//                exp of each point (Eqs. 15-16), responsibilities (Eq. 3) in
+//                shared memory, then the statistics S0_g = sum l, S1_gd =
+//                sum l (x - m), S2_gd = sum l (x - m)^2 as a dense reduction
+//                over the block's points, added to the set's totals.
+//  k_loss_grad   one block per set: dNLL/d(a, m, r) from the statistics, the
+//                pull of the predicted means toward the plain method's fit,
+//                the loss, and optionally the predicted mixture in FP64.
+constexpr int kLossPts = 128;
+
+__global__ void k_loss_prep(const float *__restrict__ out, int D, int G, double var_floor, float *__restrict__ lp,
+                            float *__restrict__ st, float *__restrict__ nll)
 {
-    extern __shared__ float ls[];
-    const int b = blockIdx.x, O = G * (1 + 2 * D);
+    const int b = blockIdx.x, O = G * (1 + 2 * D), LP = 2 * G + 3 * G * D, ST = G + 2 * G * D;
     const float *o = out + (size_t)b * O;
-    float *w = ls;                          // [G] hefts
-    float *lw = w + G;                      // [G] log hefts
-    float *m = lw + G;                      // [G][D]
-    float *v = m + G * D;                   // [G][D] variances
-    float *er = v + G * D;                  // [G][D] exp(r)
-    float *cst = er + G * D;                // [G] log w - 1/2 sum log(2 pi v)
-    float *S0 = cst + G;                    // [G]
-    float *S1 = S0 + G;                     // [G][D]
-    float *S2 = S1 + G * D;                 // [G][D]
-    float *sh = S2 + G * D;                 // [256]
-    __shared__ float s_max, s_sum;
+    float *w = lp + (size_t)b * LP, *cst = w + G, *m = cst + G, *iv = m + G * D, *er = iv + G * D;
+    __shared__ float s_max, s_lsum;
     if (threadIdx.x == 0) {
         float mx = -INFINITY;
         for (int g = 0; g < G; ++g) mx = fmaxf(mx, o[g]);
-        float s = 0.f;
-        for (int g = 0; g < G; ++g) s += __expf(o[g] - mx);
+        float sm = 0.f;
+        for (int g = 0; g < G; ++g) sm += __expf(o[g] - mx);
         s_max = mx;
-        s_sum = s;
+        s_lsum = logf(sm);
+        nll[b] = 0.f;
     }
     __syncthreads();
-    for (int g = threadIdx.x; g < G; g += blockDim.x) {
-        w[g] = __expf(o[g] - s_max) / s_sum;
-        lw[g] = o[g] - s_max - logf(s_sum);
-        S0[g] = 0.f;
-    }
     for (int k = threadIdx.x; k < G * D; k += blockDim.x) {
         m[k] = o[G + k];
-        er[k] = __expf(o[G + G * D + k]);
-        v[k] = er[k] + (float)var_floor;
-        S1[k] = 0.f;
-        S2[k] = 0.f;
+        const float e = __expf(o[G + G * D + k]);
+        er[k] = e;
+        iv[k] = 1.f / (e + (float)var_floor);
     }
+    for (int k = threadIdx.x; k < ST; k += blockDim.x) st[(size_t)b * ST + k] = 0.f;
     __syncthreads();
     for (int g = threadIdx.x; g < G; g += blockDim.x) {
-        float s = 0.f;
-        for (int d = 0; d < D; ++d) s += logf(v[g * D + d]);
-        cst[g] = lw[g] - 0.5f * ((float)D * 1.8378770664093453f + s);
+        const float lw = o[g] - s_max - s_lsum;
+        w[g] = __expf(lw);
+        float sl = 0.f;
+        for (int d = 0; d < D; ++d) sl += logf(iv[g * D + d]);   // = -sum log v
+        cst[g] = lw - 0.5f * ((float)D * 1.8378770664093453f - sl);
     }
+}
+
+__global__ void __launch_bounds__(kLossPts) k_loss_chunk(const float *__restrict__ pts, int P, int D, int G,
+                                                         const float *__restrict__ lp, float *__restrict__ st,
+                                                         float *__restrict__ nll)
+{
+    extern __shared__ float lsm[];
+    const int b = blockIdx.x, p0 = blockIdx.y * kLossPts, np = min(kLossPts, P - p0);
+    const int LP = 2 * G + 3 * G * D, ST = G + 2 * G * D, GS = G + 1, XS = D | 1;   // odd row strides
+    float *cst = lsm;                    // [G]
+    float *m = cst + G;                  // [G][D]
+    float *iv = m + G * D;               // [G][D]
+    float *x = iv + G * D;               // [128][XS]
+    float *gam = x + kLossPts * XS;      // [128][G + 1]
+    float *red = gam + kLossPts * GS;    // [128]
+    const float *lpb = lp + (size_t)b * LP;
+    for (int k = threadIdx.x; k < G; k += kLossPts) cst[k] = lpb[G + k];
+    for (int k = threadIdx.x; k < 2 * G * D; k += kLossPts) m[k] = lpb[2 * G + k];   // m then iv
+    for (int k = threadIdx.x; k < np * D; k += kLossPts) x[(k / D) * XS + k % D] = pts[((size_t)b * P + p0) * D + k];
     __syncthreads();
-    // responsibilities and statistics, a thread per point
-    float nll = 0.f;
-    for (int p = threadIdx.x; p < P; p += blockDim.x) {
-        const float *x = pts + ((size_t)b * P + p) * D;
-        float mx = -INFINITY, sum = 0.f;
+    float nl = 0.f;
+    const int p = threadIdx.x;
+    if (p < np) {
+        const float *xp = x + p * XS;
+        float mx = -INFINITY, sm = 0.f;
         for (int g = 0; g < G; ++g) {
             float q = 0.f;
             for (int d = 0; d < D; ++d) {
-                const float t = x[d] - m[g * D + d];
-                q = fmaf(t * t, 1.f / v[g * D + d], q);
+                const float t = xp[d] - m[g * D + d];
+                q = fmaf(t * t, iv[g * D + d], q);
             }
-            const float l = cst[g] - 0.5f * q;
-            if (l > mx) { sum = sum * __expf(mx - l) + 1.f; mx = l; }
-            else sum += __expf(l - mx);
+            const float l = fmaf(-0.5f, q, cst[g]);
+            gam[p * GS + g] = l;
+            if (l > mx) { sm = sm * __expf(mx - l) + 1.f; mx = l; }
+            else sm += __expf(l - mx);
         }
-        const float lse = mx + logf(sum);
-        nll -= lse;
-        for (int g = 0; g < G; ++g) {
-            float q = 0.f;
-            for (int d = 0; d < D; ++d) {
-                const float t = x[d] - m[g * D + d];
-                q = fmaf(t * t, 1.f / v[g * D + d], q);
-            }
-            const float gm = __expf(cst[g] - 0.5f * q - lse);
-            if (gm < 1e-8f) continue;   // contributes < 1e-8 of a point to any statistic
-            atomicAdd(&S0[g], gm);
-            for (int d = 0; d < D; ++d) {
-                const float t = x[d] - m[g * D + d];
-                atomicAdd(&S1[g * D + d], gm * t);
-                atomicAdd(&S2[g * D + d], gm * t * t);
-            }
-        }
+        const float lse = mx + logf(sm);
+        nl = -lse;
+        for (int g = 0; g < G; ++g) gam[p * GS + g] = __expf(gam[p * GS + g] - lse);   // Eq. 3
     }
-    nll = bsum_f(nll, sh) / (float)P;
-    // gradient with respect to the network output (mean over the batch)
+    red[threadIdx.x] = nl;
+    __syncthreads();
+    for (int h = kLossPts / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(&nll[b], red[0]);
+    // statistics of the block's points: threads over (g, d)
+    float *stb = st + (size_t)b * ST;
+    for (int k = threadIdx.x; k < G * D; k += kLossPts) {
+        const int g = k / D, d = k - g * D;
+        const float mg = m[k];
+        float s1 = 0.f, s2 = 0.f;
+        for (int q = 0; q < np; ++q) {
+            const float t = x[q * XS + d] - mg;
+            const float v = gam[q * GS + g] * t;
+            s1 += v;
+            s2 = fmaf(v, t, s2);
+        }
+        atomicAdd(&stb[G + k], s1);
+        atomicAdd(&stb[G + G * D + k], s2);
+    }
+    for (int g = threadIdx.x; g < G; g += kLossPts) {
+        float s0 = 0.f;
+        for (int q = 0; q < np; ++q) s0 += gam[q * GS + g];
+        atomicAdd(&stb[g], s0);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_loss_grad(const float *__restrict__ lp, const float *__restrict__ st,
+                                                   const float *__restrict__ nll, int P, int D, int G, double var_floor,
+                                                   const double *__restrict__ tgt_m, const double *__restrict__ tgt_v,
+                                                   const double *__restrict__ tgt_w, double lambda,
+                                                   float *__restrict__ d_out, float *__restrict__ loss,
+                                                   double *__restrict__ pm, double *__restrict__ pv,
+                                                   double *__restrict__ pw, int B)
+{
+    __shared__ float sh[256];
+    const int b = blockIdx.x, O = G * (1 + 2 * D), LP = 2 * G + 3 * G * D, ST = G + 2 * G * D;
+    const float *w = lp + (size_t)b * LP, *m = w + 2 * G, *iv = m + G * D, *er = iv + G * D;
+    const float *S0 = st + (size_t)b * ST, *S1 = S0 + G, *S2 = S1 + G * D;
     const float invB = 1.f / (float)B, invP = 1.f / (float)P;
     float *d = d_out + (size_t)b * O;
     for (int g = threadIdx.x; g < G; g += blockDim.x) d[g] = (w[g] - S0[g] * invP) * invB;
     for (int k = threadIdx.x; k < G * D; k += blockDim.x) {
-        d[G + k] = -S1[k] / v[k] * invP * invB;
-        d[G + G * D + k] = -0.5f * (S2[k] / v[k] - S0[k / D]) * er[k] / v[k] * invP * invB;
+        d[G + k] = -S1[k] * iv[k] * invP * invB;
+        d[G + G * D + k] = -0.5f * (S2[k] * iv[k] - S0[k / D]) * er[k] * iv[k] * invP * invB;
     }
     __syncthreads();
     // pull of the predicted means toward the plain method's fit (nearest pairs)
@@ -273,11 +323,11 @@ __global__ void __launch_bounds__(256) k_set_loss(const float *__restrict__ out,
         }
     }
     pull = bsum_f(pull, sh);
-    if (threadIdx.x == 0) loss[b] = nll + pull;
+    if (threadIdx.x == 0) loss[b] = nll[b] * invP + pull;
     if (pm) {
         for (int k = threadIdx.x; k < G * D; k += blockDim.x) {
             pm[(size_t)b * G * D + k] = (double)m[k];
-            pv[(size_t)b * G * D + k] = (double)v[k];
+            pv[(size_t)b * G * D + k] = (double)er[k] + var_floor;
         }
         for (int g = threadIdx.x; g < G; g += blockDim.x) pw[(size_t)b * G + g] = (double)w[g];
     }
@@ -336,6 +386,9 @@ struct Ws {
     float *out;                     // [B][O]
     float *dout;                    // [B][O]
     float *loss;                    // [B]
+    float *lpar;                    // [B][2G + 3GD] predicted mixture for the loss
+    float *lst;                     // [B][G + 2GD] statistics of the loss
+    float *lnll;                    // [B] NLL sums
 };
 
 size_t ws_bytes(const InitNet &n, int B, int P)
@@ -353,6 +406,9 @@ size_t ws_bytes(const InitNet &n, int B, int P)
     for (int l = 0; l <= n.Lh; ++l) add(2 * (size_t)B * std::max(n.Hh, n.Hp));
     add(4 * (size_t)B * n.O);
     add(4 * (size_t)B * n.O);
+    add(4 * (size_t)B);
+    add(4 * (size_t)B * (2 * n.G + 3 * (size_t)n.G * n.D));
+    add(4 * (size_t)B * (n.G + 2 * (size_t)n.G * n.D));
     add(4 * (size_t)B);
     return s;
 }
@@ -375,6 +431,9 @@ Ws carve(InitNet &n, int B, int P)
     w.out = reinterpret_cast<float *>(take(4 * (size_t)B * n.O));
     w.dout = reinterpret_cast<float *>(take(4 * (size_t)B * n.O));
     w.loss = reinterpret_cast<float *>(take(4 * (size_t)B));
+    w.lpar = reinterpret_cast<float *>(take(4 * (size_t)B * (2 * n.G + 3 * (size_t)n.G * n.D)));
+    w.lst = reinterpret_cast<float *>(take(4 * (size_t)B * (n.G + 2 * (size_t)n.G * n.D)));
+    w.lnll = reinterpret_cast<float *>(take(4 * (size_t)B));
     return w;
 }
 
@@ -435,14 +494,14 @@ cudaError_t net_backward(InitNet &n, int B, int P, Ws &w, cudaStream_t s)
     // dout FP32 -> BF16 for the GEMMs (reuse dz)
     k_to_bf16<<<blocks_for((int64_t)B * n.O, 256), 256, 0, s>>>(w.dout, w.dz, (int64_t)B * n.O);
     CKE(gemm(w.dz, w.a[n.Lh], n.grad + n.w_off[lo], n.O, hin, B, n.O, hin, hin, 1, 1, 1, 1, s));
-    k_colsum<<<(n.O + 31) / 32, 256, 0, s>>>(w.dz, n.grad + n.b_off[lo], B, n.O);
+    k_colsum<<<dim3((n.O + 31) / 32, 1), 256, 0, s>>>(w.dz, n.grad + n.b_off[lo], B, n.O);
     CKE(gemm(w.dz, n.wbf + n.w_off[lo], w.dh, B, hin, n.O, n.O, hin, hin, 0, 1, 1, 0, s));
     for (int l = n.Lh - 1; l >= 0; --l) {
         const int li = n.Lp + l;
         const int lin = l == 0 ? n.Hp : n.Hh;
         k_relu_bwd<<<blocks_for((int64_t)B * n.Hh, 256), 256, 0, s>>>(w.dh, w.a[l + 1], w.dz, B, n.Hh, 0);
         CKE(gemm(w.dz, w.a[l], n.grad + n.w_off[li], n.Hh, lin, B, n.Hh, lin, lin, 1, 1, 1, 1, s));
-        k_colsum<<<(n.Hh + 31) / 32, 256, 0, s>>>(w.dz, n.grad + n.b_off[li], B, n.Hh);
+        k_colsum<<<dim3((n.Hh + 31) / 32, 1), 256, 0, s>>>(w.dz, n.grad + n.b_off[li], B, n.Hh);
         CKE(gemm(w.dz, n.wbf + n.w_off[li], w.dh, B, lin, n.Hh, n.Hh, lin, lin, 0, 1, 1, 0, s));
     }
     // w.dh now holds d(pooled) [B][Hp]; per-point layers
@@ -452,7 +511,8 @@ cudaError_t net_backward(InitNet &n, int B, int P, Ws &w, cudaStream_t s)
         k_relu_bwd<<<blocks_for(BP * n.Hp, 256), 256, 0, s>>>(w.dh, w.h[l], w.dz, BP, n.Hp, l == n.Lp - 1 ? P : 0);
         const int splits = (int)std::min<int64_t>(64, std::max<int64_t>(1, BP / 4096));
         CKE(gemm(w.dz, hin_act, n.grad + n.w_off[l], n.Hp, kin, (int)BP, n.Hp, kin, kin, 1, 1, splits, 1, s));
-        k_colsum<<<(n.Hp + 31) / 32, 256, 0, s>>>(w.dz, n.grad + n.b_off[l], BP, n.Hp);
+        k_colsum<<<dim3((n.Hp + 31) / 32, (unsigned)std::min<int64_t>(256, (BP + 255) / 256)), 256, 0, s>>>(
+            w.dz, n.grad + n.b_off[l], BP, n.Hp);
         if (l > 0) CKE(gemm(w.dz, n.wbf + n.w_off[l], w.dh, (int)BP, kin, n.Hp, n.Hp, kin, kin, 0, 1, 1, 0, s));
     }
     count_launches(2 + 3 * (n.Lh + n.Lp));
@@ -577,10 +637,14 @@ cudaError_t init_net_run(InitNet *n, const float *pts, int B, int P, const doubl
     CKE(ensure_ws(*n, B, P));
     Ws w = carve(*n, B, P);
     CKE(net_forward(*n, pts, B, P, w, s));
-    const size_t sm = sizeof(float) * (3 * (size_t)n->G + 5 * (size_t)n->G * n->D + 256 + n->G);
-    CKE(cudaFuncSetAttribute(k_set_loss, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_set_loss<<<B, 256, sm, s>>>(w.out, pts, P, n->D, n->G, var_floor, tm, tv, tw, lambda, w.dout, w.loss, pm, pv, pw, B);
-    count_launches(1);
+    k_loss_prep<<<B, 256, 0, s>>>(w.out, n->D, n->G, var_floor, w.lpar, w.lst, w.lnll);
+    const size_t sm = sizeof(float) * ((size_t)n->G + 2 * (size_t)n->G * n->D + (size_t)kLossPts * (n->D | 1) +
+                                       (size_t)kLossPts * (n->G + 1) + kLossPts);
+    CKE(cudaFuncSetAttribute(k_loss_chunk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_loss_chunk<<<dim3(B, (P + kLossPts - 1) / kLossPts), kLossPts, sm, s>>>(pts, P, n->D, n->G, w.lpar, w.lst, w.lnll);
+    k_loss_grad<<<B, 256, 0, s>>>(w.lpar, w.lst, w.lnll, P, n->D, n->G, var_floor, tm, tv, tw, lambda, w.dout, w.loss,
+                                  pm, pv, pw, B);
+    count_launches(3);
     CKE(cudaGetLastError());
     if (grads) CKE(net_backward(*n, B, P, w, s));
     if (grads && lr > 0.0) {
