@@ -25,10 +25,13 @@
 #include <vector>
 
 #include "gmm_internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace gmm {
 
 namespace {
+
+using namespace ptx;
 
 constexpr int kBM = 64, kBN = 64, kBK = 16;
 
@@ -90,6 +93,179 @@ __global__ void __launch_bounds__(256) k_gemm_bf16(const __nv_bfloat16 *__restri
         }
 }
 
+// ------------------------------------------------------------------------
+// Tensor-core GEMM (tcgen05, BF16 operands, FP32 accumulators in TMEM) for
+// the per-point layers: D[M][N] = sum_k A[m][k] B[n][k], A and B row-major
+// with K contiguous (K-major), rows a multiple of 8 elements apart.  A CTA
+// owns a 128 x BN tile; K advances in 64-wide blocks staged by cp.async into
+// 128-byte-swizzled shared memory (two stages), one thread issues the four
+// K=16 MMAs of a block and commits them to the stage's mbarrier.  Rows or K
+// beyond the operands are zero-filled.  Epilogues (tcgen05.ld, a warp per 32
+// rows): 0 FP32 atomics into C (split-K along grid z), 1 bias + ReLU to BF16,
+// 2 gradient masked by a stored activation (ReLU backward) to BF16.
+// ------------------------------------------------------------------------
+struct TcGemm {
+    const __nv_bfloat16 *A, *B;
+    int M, N, K, lda, ldb;
+    int kb_split;                // 64-wide K blocks per CTA along grid z
+    int mode;
+    float *C; int ldc;
+    const float *bias;
+    __nv_bfloat16 *out; int ldo;
+    const __nv_bfloat16 *ref; int ldr;
+    long long budget;            // cycles of a bounded wait
+    int *err;                    // set when a wait runs out
+};
+
+__device__ __forceinline__ void cp_async16_zf(uint32_t dst, const void *src, int bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+
+template <int BN>
+__global__ void __launch_bounds__(128, 1) k_gemm_tc(TcGemm g)
+{
+    extern __shared__ __align__(1024) unsigned char gt_raw[];
+    unsigned char *sb = gt_raw + ((1024u - (smem_u32(gt_raw) & 1023u)) & 1023u);
+    constexpr uint32_t kStage = 16384u + (uint32_t)BN * 128u;
+    constexpr uint32_t kCols = BN < 32 ? 32 : BN;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sb + 2 * kStage);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(sb + 2 * kStage + 16);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(sb + 2 * kStage + 20);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * 128, n0 = blockIdx.y * BN;
+    const int nkb_all = (g.K + 63) / 64;
+    const int kb0 = blockIdx.z * g.kb_split, nkb = min(nkb_all, kb0 + g.kb_split) - kb0;
+    if (nkb <= 0) return;   // uniform
+    if (tid == 0) {
+        mbar_init(bars, 1);
+        mbar_init(bars + 1, 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        tmem_alloc(tslot, kCols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    auto load = [&](int kb, int st) {
+        unsigned char *sa = sb + st * kStage, *sbb = sa + 16384;
+        const int k0 = kb * 64;
+        for (int e = tid; e < 128 * 8; e += 128) {
+            const int r = e >> 3, c = e & 7, m = m0 + r, k = k0 + 8 * c;
+            const bool ok = m < g.M && k < g.K;
+            cp_async16_zf(smem_u32(sa + sw128_off(r, c)), ok ? g.A + (size_t)m * g.lda + k : g.A, ok ? 16 : 0);
+        }
+        for (int e = tid; e < BN * 8; e += 128) {
+            const int r = e >> 3, c = e & 7, n = n0 + r, k = k0 + 8 * c;
+            const bool ok = n < g.N && k < g.K;
+            cp_async16_zf(smem_u32(sbb + sw128_off(r, c)), ok ? g.B + (size_t)n * g.ldb + k : g.B, ok ? 16 : 0);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    const uint32_t idesc = idesc_bf16(128, BN);
+    load(kb0, 0);
+    for (int i = 0; i < nkb; ++i) {
+        const int st = i & 1;
+        if (i + 1 < nkb) {
+            // the other stage was read by the MMAs of block i-1
+            if (i >= 1) mbar_wait(bars + ((i + 1) & 1), (uint32_t)(((i - 1) >> 1) & 1), abort_flag, g.budget);
+            load(kb0 + i + 1, (i + 1) & 1);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t a = smem_u32(sb + st * kStage), b = a + 16384u;
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+                tc_mma(tmem, desc_k_sw128(a + kk * 32u), desc_k_sw128(b + kk * 32u), idesc, (i > 0 || kk > 0) ? 1u : 0u);
+            tc_commit(bars + st);
+        }
+    }
+    // every MMA has completed once the last block's commit has arrived
+    if (!mbar_wait(bars + ((nkb - 1) & 1), (uint32_t)(((nkb - 1) >> 1) & 1), abort_flag, g.budget)) {
+        // bounded drain (ignores the abort flag) before the memory is freed
+        const long long d0 = clock64();
+        while (!mbar_try_wait(bars + ((nkb - 1) & 1), (uint32_t)(((nkb - 1) >> 1) & 1)) && clock64() - d0 < g.budget) {
+        }
+        if (tid == 0) atomicExch(g.err, 1);
+    }
+    tc_fence_after();
+    const int row = m0 + 32 * warp + lane;
+    const uint32_t tl = tmem + ((uint32_t)(32 * warp) << 16);
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+        uint32_t r[16];
+        tmem_ld16(tl + (uint32_t)c0, r);
+        tmem_wait_ld();
+        const int nb = n0 + c0;
+        if (row >= g.M || nb >= g.N) continue;
+        const bool full = nb + 16 <= g.N;
+        if (g.mode == 0) {
+            float *c = g.C + (size_t)row * g.ldc + nb;
+            if (full && (g.ldc & 3) == 0 && (reinterpret_cast<uintptr_t>(c) & 15u) == 0) {
+#pragma unroll
+                for (int j = 0; j < 16; j += 4)
+                    atomicAdd(reinterpret_cast<float4 *>(c + j),
+                              make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]), __uint_as_float(r[j + 2]),
+                                          __uint_as_float(r[j + 3])));
+            } else {
+                for (int j = 0; j < 16 && nb + j < g.N; ++j) atomicAdd(c + j, __uint_as_float(r[j]));
+            }
+        } else {
+            __nv_bfloat16 v[16];
+            if (g.mode == 1) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    v[j] = __float2bfloat16_rn(fmaxf(__uint_as_float(r[j]) + (nb + j < g.N ? g.bias[nb + j] : 0.f), 0.f));
+            } else {
+                const __nv_bfloat16 *h = g.ref + (size_t)row * g.ldr + nb;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const float hv = (nb + j < g.N) ? __bfloat162float(h[j]) : 0.f;
+                    v[j] = __float2bfloat16_rn(hv > 0.f ? __uint_as_float(r[j]) : 0.f);
+                }
+            }
+            __nv_bfloat16 *o = g.out + (size_t)row * g.ldo + nb;
+            if (full && (g.ldo & 7) == 0 && (reinterpret_cast<uintptr_t>(o) & 15u) == 0) {
+                reinterpret_cast<uint4 *>(o)[0] = *reinterpret_cast<const uint4 *>(v);
+                reinterpret_cast<uint4 *>(o)[1] = *reinterpret_cast<const uint4 *>(v + 8);
+            } else {
+                for (int j = 0; j < 16 && nb + j < g.N; ++j) o[j] = v[j];
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, kCols);
+}
+
+// out[c][r] = in[r][c] for a BF16 [R][C] matrix (32 x 32 tiles)
+__global__ void k_transpose_bf16(const __nv_bfloat16 *__restrict__ in, __nv_bfloat16 *__restrict__ out, int64_t R, int C)
+{
+    __shared__ __nv_bfloat16 t[32][34];
+    const int64_t r0 = (int64_t)blockIdx.y * 32;
+    const int c0 = blockIdx.x * 32;
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int64_t r = r0 + k;
+        const int c = c0 + threadIdx.x;
+        if (r < R && c < C) t[k][threadIdx.x] = in[r * C + c];
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int c = c0 + k;
+        const int64_t r = r0 + threadIdx.x;
+        if (r < R && c < C) out[(int64_t)c * R + r] = t[threadIdx.x][k];
+    }
+}
+
 // out = act(Z + bias) in BF16 (relu != 0) ; also FP32 copy if zf != NULL
 __global__ void k_bias_act(const float *__restrict__ Z, const float *__restrict__ bias, __nv_bfloat16 *__restrict__ out,
                            float *__restrict__ zf, int64_t M, int N, int relu)
@@ -137,17 +313,26 @@ __global__ void k_colsum(const __nv_bfloat16 *__restrict__ dZ, float *__restrict
     }
 }
 
-// pooled[b][n] = mean over p of H[b*P + p][n]; also a BF16 copy
+// pooled[b][n] = mean over p of H[b*P + p][n]; also a BF16 copy.  A block
+// per (32 columns, set): eight warps take every eighth point, then reduce.
 __global__ void k_pool(const __nv_bfloat16 *__restrict__ H, float *__restrict__ pooled, __nv_bfloat16 *__restrict__ pooled_bf,
                        int P, int N)
 {
-    const int b = blockIdx.y, n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= N) return;
+    __shared__ float part[8][33];
+    const int b = blockIdx.y, lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+    const int n = blockIdx.x * 32 + lane;
     float s = 0.f;
-    for (int p = 0; p < P; ++p) s += __bfloat162float(H[((size_t)b * P + p) * N + n]);
-    s /= (float)P;
-    pooled[(size_t)b * N + n] = s;
-    pooled_bf[(size_t)b * N + n] = __float2bfloat16_rn(s);
+    if (n < N)
+        for (int p = wy; p < P; p += 8) s += __bfloat162float(H[((size_t)b * P + p) * N + n]);
+    part[wy][lane] = s;
+    __syncthreads();
+    if (wy == 0 && n < N) {
+        float t = 0.f;
+        for (int k = 0; k < 8; ++k) t += part[k][lane];
+        t /= (float)P;
+        pooled[(size_t)b * N + n] = t;
+        pooled_bf[(size_t)b * N + n] = __float2bfloat16_rn(t);
+    }
 }
 
 __device__ __forceinline__ float bsum_f(float v, float *sh)
@@ -367,6 +552,7 @@ struct InitNet {
     std::vector<int64_t> w_off, b_off, w_in, w_out;   // per layer (Lp + Lh + 1 layers)
     float *wgt = nullptr, *grad = nullptr, *m1 = nullptr, *m2 = nullptr;
     __nv_bfloat16 *wbf = nullptr;
+    int *err = nullptr;             // device flag: a bounded wait of a tensor-core GEMM ran out
     int64_t step = 0;
     // activation workspace (grown per batch)
     size_t ws_cap = 0;
@@ -386,6 +572,10 @@ struct Ws {
     float *out;                     // [B][O]
     float *dout;                    // [B][O]
     float *loss;                    // [B]
+    __nv_bfloat16 *dz2;             // BF16 [BP][Hp] second gradient buffer (tensor-core backward)
+    __nv_bfloat16 *dzT;             // BF16 [Hp][BP] transposed gradient
+    __nv_bfloat16 *inT;             // BF16 [max(D, Hp)][BP] transposed layer input
+    __nv_bfloat16 *wT;              // BF16 [max(D, Hp)][Hp] transposed weights
     float *lpar;                    // [B][2G + 3GD] predicted mixture for the loss
     float *lst;                     // [B][G + 2GD] statistics of the loss
     float *lnll;                    // [B] NLL sums
@@ -407,6 +597,11 @@ size_t ws_bytes(const InitNet &n, int B, int P)
     add(4 * (size_t)B * n.O);
     add(4 * (size_t)B * n.O);
     add(4 * (size_t)B);
+    const int64_t kmax = std::max(n.D, n.Hp);
+    add(2 * BP * n.Hp);
+    add(2 * BP * n.Hp);
+    add(2 * BP * kmax);
+    add(2 * (size_t)kmax * n.Hp);
     add(4 * (size_t)B * (2 * n.G + 3 * (size_t)n.G * n.D));
     add(4 * (size_t)B * (n.G + 2 * (size_t)n.G * n.D));
     add(4 * (size_t)B);
@@ -431,6 +626,11 @@ Ws carve(InitNet &n, int B, int P)
     w.out = reinterpret_cast<float *>(take(4 * (size_t)B * n.O));
     w.dout = reinterpret_cast<float *>(take(4 * (size_t)B * n.O));
     w.loss = reinterpret_cast<float *>(take(4 * (size_t)B));
+    const int64_t kmax = std::max(n.D, n.Hp);
+    w.dz2 = reinterpret_cast<__nv_bfloat16 *>(take(2 * BP * n.Hp));
+    w.dzT = reinterpret_cast<__nv_bfloat16 *>(take(2 * BP * n.Hp));
+    w.inT = reinterpret_cast<__nv_bfloat16 *>(take(2 * BP * kmax));
+    w.wT = reinterpret_cast<__nv_bfloat16 *>(take(2 * (size_t)kmax * n.Hp));
     w.lpar = reinterpret_cast<float *>(take(4 * (size_t)B * (2 * n.G + 3 * (size_t)n.G * n.D)));
     w.lst = reinterpret_cast<float *>(take(4 * (size_t)B * (n.G + 2 * (size_t)n.G * n.D)));
     w.lnll = reinterpret_cast<float *>(take(4 * (size_t)B));
@@ -443,6 +643,48 @@ cudaError_t gemm(const __nv_bfloat16 *A, const __nv_bfloat16 *B, float *C, int M
     dim3 grid((N + kBN - 1) / kBN, (M + kBM - 1) / kBM, splits);
     if (splits > 1 && !accumulate) return cudaErrorInvalidValue;   // split-K only accumulates onto zeroed C
     k_gemm_bf16<<<grid, 256, 0, s>>>(A, B, C, M, N, K, lda, ldb, ldc, tA, tB, (splits > 1 || accumulate) ? 1 : 0);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+bool tc_usable(const void *A, const void *B, int K, int lda, int ldb)
+{
+    return ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15u) == 0 && K % 8 == 0 &&
+           lda % 8 == 0 && ldb % 8 == 0;
+}
+
+// D = A B^T on the tensor cores (see k_gemm_tc); splits > 1 only with mode 0
+cudaError_t gemm_tc(const __nv_bfloat16 *A, const __nv_bfloat16 *B, int64_t M, int N, int K, int lda, int ldb, int mode,
+                    float *C, int ldc, const float *bias, __nv_bfloat16 *out, int ldo, const __nv_bfloat16 *ref,
+                    int ldr, int splits, int *err, cudaStream_t s)
+{
+    const int nkb = (K + 63) / 64;
+    splits = std::max(1, std::min(splits, nkb));
+    const int kb_split = (nkb + splits - 1) / splits;
+    const int gz = (nkb + kb_split - 1) / kb_split;
+    TcGemm g{A, B, (int)M, N, K, lda, ldb, kb_split, mode, C, ldc, bias, out, ldo, ref, ldr, 2000000000LL, err};
+    const int BN = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
+    const size_t sm = 2 * (16384 + (size_t)BN * 128) + 64 + 1024;
+    const dim3 grid((unsigned)((M + 127) / 128), (unsigned)((N + BN - 1) / BN), (unsigned)gz);
+#define GTC(BNV)                                                                                           \
+    do {                                                                                                   \
+        cudaError_t e_ = cudaFuncSetAttribute(k_gemm_tc<BNV>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                              (int)sm);                                                    \
+        if (e_ != cudaSuccess) return e_;                                                                  \
+        k_gemm_tc<BNV><<<grid, 128, sm, s>>>(g);                                                           \
+    } while (0)
+    if (BN == 32) GTC(32);
+    else if (BN == 64) GTC(64);
+    else if (BN == 128) GTC(128);
+    else GTC(256);
+#undef GTC
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t transpose_bf16(const __nv_bfloat16 *in, __nv_bfloat16 *out, int64_t R, int C, cudaStream_t s)
+{
+    k_transpose_bf16<<<dim3((unsigned)((C + 31) / 32), (unsigned)((R + 31) / 32)), dim3(32, 8), 0, s>>>(in, out, R, C);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -461,12 +703,19 @@ cudaError_t net_forward(InitNet &n, const float *pts, int B, int P, Ws &w, cudaS
     const __nv_bfloat16 *in = w.x;
     int kin = n.D;
     for (int l = 0; l < n.Lp; ++l) {
-        CKE(gemm(in, n.wbf + n.w_off[l], w.z, (int)BP, n.Hp, kin, kin, kin, n.Hp, 0, 0, 1, 0, s));
-        k_bias_act<<<blocks_for(BP * n.Hp, 256), 256, 0, s>>>(w.z, n.wgt + n.b_off[l], w.h[l], nullptr, BP, n.Hp, 1);
+        const __nv_bfloat16 *W = n.wbf + n.w_off[l];
+        if (tc_usable(in, W, kin, kin, kin)) {
+            // tensor cores, bias + ReLU + BF16 in the epilogue
+            CKE(gemm_tc(in, W, BP, n.Hp, kin, kin, kin, 1, nullptr, 0, n.wgt + n.b_off[l], w.h[l], n.Hp, nullptr, 0, 1,
+                        n.err, s));
+        } else {
+            CKE(gemm(in, W, w.z, (int)BP, n.Hp, kin, kin, kin, n.Hp, 0, 0, 1, 0, s));
+            k_bias_act<<<blocks_for(BP * n.Hp, 256), 256, 0, s>>>(w.z, n.wgt + n.b_off[l], w.h[l], nullptr, BP, n.Hp, 1);
+        }
         in = w.h[l];
         kin = n.Hp;
     }
-    k_pool<<<dim3((n.Hp + 127) / 128, B), 128, 0, s>>>(w.h[n.Lp - 1], w.pooled, w.a[0], P, n.Hp);
+    k_pool<<<dim3((n.Hp + 31) / 32, B), 256, 0, s>>>(w.h[n.Lp - 1], w.pooled, w.a[0], P, n.Hp);
     int hin = n.Hp;
     for (int l = 0; l < n.Lh; ++l) {
         const int li = n.Lp + l;
@@ -504,16 +753,36 @@ cudaError_t net_backward(InitNet &n, int B, int P, Ws &w, cudaStream_t s)
         k_colsum<<<dim3((n.Hh + 31) / 32, 1), 256, 0, s>>>(w.dz, n.grad + n.b_off[li], B, n.Hh);
         CKE(gemm(w.dz, n.wbf + n.w_off[li], w.dh, B, lin, n.Hh, n.Hh, lin, lin, 0, 1, 1, 0, s));
     }
-    // w.dh now holds d(pooled) [B][Hp]; per-point layers
+    // w.dh now holds d(pooled) [B][Hp]; per-point layers.  cur = dLoss/dZ_l in BF16.
+    __nv_bfloat16 *cur = w.dz, *nxt = w.dz2;
+    k_relu_bwd<<<blocks_for(BP * n.Hp, 256), 256, 0, s>>>(w.dh, w.h[n.Lp - 1], cur, BP, n.Hp, P);
     for (int l = n.Lp - 1; l >= 0; --l) {
         const int kin = l == 0 ? n.D : n.Hp;
         const __nv_bfloat16 *hin_act = l == 0 ? w.x : w.h[l - 1];
-        k_relu_bwd<<<blocks_for(BP * n.Hp, 256), 256, 0, s>>>(w.dh, w.h[l], w.dz, BP, n.Hp, l == n.Lp - 1 ? P : 0);
-        const int splits = (int)std::min<int64_t>(64, std::max<int64_t>(1, BP / 4096));
-        CKE(gemm(w.dz, hin_act, n.grad + n.w_off[l], n.Hp, kin, (int)BP, n.Hp, kin, kin, 1, 1, splits, 1, s));
+        const __nv_bfloat16 *W = n.wbf + n.w_off[l];
+        // dW_l = cur^T in_l: a reduction over the B*P points, split along K
+        if (BP % 8 == 0 && tc_usable(w.dzT, w.inT, (int)BP, (int)BP, (int)BP)) {
+            CKE(transpose_bf16(cur, w.dzT, BP, n.Hp, s));
+            CKE(transpose_bf16(hin_act, w.inT, BP, kin, s));
+            CKE(gemm_tc(w.dzT, w.inT, n.Hp, kin, (int)BP, (int)BP, (int)BP, 0, n.grad + n.w_off[l], kin, nullptr, nullptr,
+                        0, nullptr, 0, 64, n.err, s));
+        } else {
+            const int splits = (int)std::min<int64_t>(64, std::max<int64_t>(1, BP / 4096));
+            CKE(gemm(cur, hin_act, n.grad + n.w_off[l], n.Hp, kin, (int)BP, n.Hp, kin, kin, 1, 1, splits, 1, s));
+        }
         k_colsum<<<dim3((n.Hp + 31) / 32, (unsigned)std::min<int64_t>(256, (BP + 255) / 256)), 256, 0, s>>>(
-            w.dz, n.grad + n.b_off[l], BP, n.Hp);
-        if (l > 0) CKE(gemm(w.dz, n.wbf + n.w_off[l], w.dh, (int)BP, kin, n.Hp, n.Hp, kin, kin, 0, 1, 1, 0, s));
+            cur, n.grad + n.b_off[l], BP, n.Hp);
+        if (l == 0) break;
+        // dZ_{l-1} = (cur W_l) masked by ReLU'(h_{l-1})
+        if (tc_usable(cur, w.wT, n.Hp, n.Hp, n.Hp)) {
+            CKE(transpose_bf16(W, w.wT, n.Hp, kin, s));
+            CKE(gemm_tc(cur, w.wT, BP, kin, n.Hp, n.Hp, n.Hp, 2, nullptr, 0, nullptr, nxt, kin, w.h[l - 1], kin, 1, n.err,
+                        s));
+            std::swap(cur, nxt);
+        } else {
+            CKE(gemm(cur, W, w.dh, (int)BP, kin, n.Hp, n.Hp, kin, kin, 0, 1, 1, 0, s));
+            k_relu_bwd<<<blocks_for(BP * n.Hp, 256), 256, 0, s>>>(w.dh, w.h[l - 1], cur, BP, n.Hp, 0);
+        }
     }
     count_launches(2 + 3 * (n.Lh + n.Lp));
     return cudaGetLastError();
@@ -570,6 +839,8 @@ InitNet *init_net_new(int D, int G, int Hp, int Hh, int Lp, int Lh, uint64_t see
     if (e == cudaSuccess) e = cudaMalloc(&n->m1, 4 * o);
     if (e == cudaSuccess) e = cudaMalloc(&n->m2, 4 * o);
     if (e == cudaSuccess) e = cudaMalloc(&n->wbf, 2 * o);
+    if (e == cudaSuccess) e = cudaMalloc(&n->err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(n->err, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemcpy(n->wgt, h.data(), 4 * o, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(n->m1, 0, 4 * o);
     if (e == cudaSuccess) e = cudaMemset(n->m2, 0, 4 * o);
@@ -584,7 +855,7 @@ InitNet *init_net_new(int D, int G, int Hp, int Hh, int Lp, int Lh, uint64_t see
 void init_net_free(InitNet *n)
 {
     if (!n) return;
-    void *b[] = {n->wgt, n->grad, n->m1, n->m2, n->wbf, n->ws};
+    void *b[] = {n->wgt, n->grad, n->m1, n->m2, n->wbf, n->ws, n->err};
     for (void *p : b)
         if (p) cudaFree(p);
     delete n;
@@ -656,6 +927,8 @@ cudaError_t init_net_run(InitNet *n, const float *pts, int B, int P, const doubl
         count_launches(1);
         CKE(cudaGetLastError());
     }
+    int herr = 0;
+    CKE(cudaMemcpyAsync(&herr, n->err, sizeof(int), cudaMemcpyDeviceToHost, s));
     if (loss_host) {
         std::vector<float> l(B);
         CKE(cudaMemcpyAsync(l.data(), w.loss, 4 * (size_t)B, cudaMemcpyDeviceToHost, s));
@@ -665,6 +938,10 @@ cudaError_t init_net_run(InitNet *n, const float *pts, int B, int P, const doubl
         *loss_host = t / B;
     } else {
         CKE(cudaStreamSynchronize(s));
+    }
+    if (herr) {
+        cudaMemsetAsync(n->err, 0, sizeof(int), s);
+        return cudaErrorLaunchTimeout;   // a bounded wait of a tensor-core GEMM ran out
     }
     return cudaSuccess;
 }
