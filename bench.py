@@ -29,6 +29,11 @@ sys.path.insert(0, ROOT)
 METRIC = "EM iters/sec (N·N_G·D/s) at D=60,N_G=256; BF16-TC vs FP32 at stated ΔLL"
 UNIT = "N·N_G·D/s"
 N_FULL, D_FULL, G_FULL = 2_000_000, 60, 256
+# DRAM bytes (read + write) of one tensor-core EM pass on the full workload:
+# ncu dram__bytes of the screen, exact and M-step kernels at N = 1,000,000
+# (961 MB, profiles/em_pass_tc_c2_1m_ncu.md), scaled by the samples (traffic
+# grows in proportion).  Re-measure whenever those kernels change.
+TC_PASS_TRAFFIC = 961.0e6 * 2
 
 
 def _peaks():
@@ -292,7 +297,7 @@ def run_ours(args):
         roof = {"bound": "tensor", "achieved": flops / (pass_ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
                 "peak_source": "bf16_tflops (%s)" % peak_src}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = args.traffic
+    roof["traffic"] = (args.traffic * N / N_FULL if args.traffic and head == "bf16" else None)
     roof["kernel_ms"] = pass_ms
 
     line = {
@@ -421,7 +426,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--forms", default="fp32,bf16",
                     help="comma list of E-step forms; the last available one is the headline")
-    ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per pass launch, if measured")
+    ap.add_argument("--traffic", type=float, default=TC_PASS_TRAFFIC,
+                    help="DRAM bytes of one headline pass (ncu), per pass; 0 = not measured")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-fit batched leg")
     ap.add_argument("--no-init-net", action="store_true", help="skip the learned-initialiser training leg")

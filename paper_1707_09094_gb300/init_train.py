@@ -116,3 +116,77 @@ def learned_or_kmeans(net: InitNet, X, P: int = 4096, em_iter: int = 300, em_tol
     if not ok or base.avg_log_p(X) > g.avg_log_p(X):
         return base, "kmeans"
     return g, "learned"
+
+
+def step_bench(B: int = 16, P: int = 4096, D: int = 32, G: int = 32, steps: int = 10, warmup: int = 3):
+    """Time Adam training steps of the set encoder (per point D-256-256-256,
+    mean pool, 256-512-512-512-G(1+2D)) on synthetic sets; returns ms/step."""
+    import torch
+    net = InitNet(D, G, 256, 512, 3, 3, seed=0)
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    pts = torch.randn((B, P, D), device="cuda", generator=gen) * 2.0
+    tgt = (torch.randn((B, G, D), device="cuda", generator=gen, dtype=torch.float64),
+           torch.rand((B, G, D), device="cuda", generator=gen, dtype=torch.float64) + 0.5,
+           torch.full((B, G), 1.0 / G, device="cuda", dtype=torch.float64))
+    for _ in range(warmup):
+        net.step(pts, tgt, lam=0.1, mode=2)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(steps):
+        net.step(pts, tgt, lam=0.1, mode=2)
+    ev1.record()
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1) / max(steps, 1)
+
+
+def _main(argv=None):
+    import argparse
+    import json
+    ap = argparse.ArgumentParser(prog="python -m paper_1707_09094_gb300.init_train")
+    sub = ap.add_subparsers(dest="cmd", required=True)
+    b = sub.add_parser("step-bench", help="time training steps")
+    b.add_argument("--sets", type=int, default=16)
+    b.add_argument("--points", type=int, default=4096)
+    b.add_argument("--steps", type=int, default=10)
+    b.add_argument("--warmup", type=int, default=3)
+    t = sub.add_parser("train", help="train on fitted synthetic sets, evaluate against k-means seeding")
+    t.add_argument("--D", type=int, default=8)
+    t.add_argument("--G", type=int, default=8)
+    t.add_argument("--points", type=int, default=512)
+    t.add_argument("--sets", type=int, default=4000)
+    t.add_argument("--steps", type=int, default=1500)
+    t.add_argument("--eval", type=int, default=16)
+    t.add_argument("--eval-n", type=int, default=100_000)
+    t.add_argument("--save", default=None, help="write the trained weights (float32 .npy)")
+    a = ap.parse_args(argv)
+    from . import build
+    build.build()
+    if a.cmd == "step-bench":
+        ms = step_bench(a.sets, a.points, steps=a.steps, warmup=a.warmup)
+        print(json.dumps({"ms_per_step": ms, "sets": a.sets, "points_per_set": a.points}))
+        return 0
+    import torch
+    pts, tgt = make_sets(a.sets, a.D, a.G, a.points, seed0=5_000_000)
+    net = InitNet(a.D, a.G, 128, 256, 3, 3, seed=0)
+    hist = train(net, pts, tgt, steps=a.steps)
+    Xs = []
+    for j in range(a.eval):
+        rng = np.random.default_rng(9_000_000 + j)
+        X, _ = synth._draw(rng, synth.mixture_c1(rng, a.D, a.G), a.eval_n)
+        Xs.append(torch.from_numpy(X).cuda())
+    rows = evaluate(net, Xs, P=a.points)
+    km = np.array([r["kmeans_ll"] for r in rows])
+    ln = np.array([r["learned_ll"] for r in rows])
+    print(json.dumps({"loss_first": float(hist[:50].mean()), "loss_last": float(hist[-50:].mean()),
+                      "passes_kmeans": float(np.mean([r["kmeans_passes"] for r in rows])),
+                      "passes_learned": float(np.mean([r["learned_passes"] for r in rows])),
+                      "ll_kmeans": float(km.mean()), "ll_learned": float(ln.mean()),
+                      "ll_judged": float(np.maximum(km, ln).mean())}))
+    if a.save:
+        np.save(a.save, net.get_weights())
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(_main())
