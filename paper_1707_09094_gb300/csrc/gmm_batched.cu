@@ -338,6 +338,7 @@ __global__ void __launch_bounds__(kBThreads) k_b_em_pass(BFit *fits, const BItem
     extern __shared__ __align__(16) float bsm[];
     __shared__ int s_item;
     __shared__ double s_ll[kBWarps];
+    __shared__ int s_nact;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     while (true) {
         const int k = next_item(counter, &s_item);
@@ -352,6 +353,9 @@ __global__ void __launch_bounds__(kBThreads) k_b_em_pass(BFit *fits, const BItem
         float *S0 = L + (size_t)G * kBTP;         // [G]
         float *S1 = S0 + G;                       // [G*D]
         float *S2 = S1 + (size_t)G * D;           // [G*D]
+        int *act = reinterpret_cast<int *>(S2 + (size_t)G * D);   // [G] Gaussians that matter in the tile
+        // the single-fit rule: responsibilities below 1e-9 / N are left out
+        const float keep = (float)(1e-9 / (double)f.N);
         for (int k = tid; k < G; k += kBThreads) S0[k] = 0.f;
         for (int k = tid; k < G * D; k += kBThreads) { S1[k] = 0.f; S2[k] = 0.f; }
         double ll = 0.0;
@@ -404,16 +408,25 @@ __global__ void __launch_bounds__(kBThreads) k_b_em_pass(BFit *fits, const BItem
                 for (int g = lane; g < G; g += 32) L[g * kBTP + s] = ok ? __expf(L[g * kBTP + s] - lse) : 0.f;
                 if (lane == 0 && ok) ll += (double)lse;
             }
+            if (tid == 0) s_nact = 0;
             __syncthreads();
-            for (int p0 = tid; p0 < G * D; p0 += 4 * kBThreads) {
+            for (int g = tid; g < G; g += kBThreads) {
+                float mx = 0.f;
+                for (int i = 0; i < kBT; ++i) mx = fmaxf(mx, L[g * kBTP + i]);
+                if (mx >= keep) act[atomicAdd(&s_nact, 1)] = g;
+            }
+            __syncthreads();
+            const int na = s_nact;
+            for (int p0 = tid; p0 < na * D; p0 += 4 * kBThreads) {
                 int gq[4], dq[4];
                 float mu[4], r1[4], r2[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const int p = min(p0 + u * kBThreads, G * D - 1);
-                    gq[u] = p / D;
-                    dq[u] = p - gq[u] * D;
-                    mu[u] = __ldg(f.mu + p);
+                    const int p = min(p0 + u * kBThreads, na * D - 1);
+                    const int ga = p / D;
+                    gq[u] = act[ga];
+                    dq[u] = p - ga * D;
+                    mu[u] = __ldg(f.mu + (size_t)gq[u] * D + dq[u]);
                     r1[u] = 0.f;
                     r2[u] = 0.f;
                 }
@@ -430,10 +443,15 @@ __global__ void __launch_bounds__(kBThreads) k_b_em_pass(BFit *fits, const BItem
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int p = p0 + u * kBThreads;
-                    if (p < G * D) { S1[p] += r1[u]; S2[p] += r2[u]; }
+                    if (p < na * D) {
+                        const int q = gq[u] * D + dq[u];
+                        S1[q] += r1[u];
+                        S2[q] += r2[u];
+                    }
                 }
             }
-            for (int g = tid; g < G; g += kBThreads) {
+            for (int kk = tid; kk < na; kk += kBThreads) {
+                const int g = act[kk];
                 float r0 = 0.f;
                 for (int i = 0; i < kBT; ++i) r0 += L[g * kBTP + i];
                 S0[g] += r0;
@@ -523,7 +541,7 @@ __global__ void __launch_bounds__(128) k_b_em_finalize(BFit *fits, const int32_t
 
 size_t b_em_smem(int D, int G)
 {
-    return sizeof(float) * ((size_t)D * kBTP + (size_t)G * kBTP + G + 2 * (size_t)G * D);
+    return sizeof(float) * ((size_t)D * kBTP + (size_t)G * kBTP + G + 2 * (size_t)G * D) + sizeof(int) * (size_t)G;
 }
 
 size_t b_km_smem(int D, int G)

@@ -663,8 +663,14 @@ __global__ void __launch_bounds__(kEmThreads, 1) k_em_pass_simt(EmPassArgs a)
     float *S0 = L + (size_t)G * kTP;              // [G]
     float *S1 = S0 + G;                           // [G*D]
     float *S2 = S1 + (size_t)G * D;               // [G*D]
+    int *act = reinterpret_cast<int *>(S2 + (size_t)G * D);   // [G] Gaussians that matter in the tile
     __shared__ double s_ll[kWarps];
+    __shared__ int s_nact;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    // responsibilities below 1e-9 / N (the tensor-core form's rule) carry less
+    // than 1e-9 per Gaussian in total: a Gaussian none of whose tile
+    // responsibilities reaches it is left out of the tile's M-step
+    const float keep = (float)(1e-9 / (double)a.N);
 
     for (int k = tid; k < G; k += kEmThreads) S0[k] = 0.f;
     for (int k = tid; k < G * D; k += kEmThreads) { S1[k] = 0.f; S2[k] = 0.f; }
@@ -725,18 +731,27 @@ __global__ void __launch_bounds__(kEmThreads, 1) k_em_pass_simt(EmPassArgs a)
             for (int g = lane; g < G; g += 32) L[g * kTP + s] = ok ? __expf(L[g * kTP + s] - lse) : 0.f;
             if (lane == 0 && ok) ll += (double)lse;
         }
+        if (tid == 0) s_nact = 0;
         __syncthreads();
-        // ---- M: thread-owned (g, d) accumulators
+        for (int g = tid; g < G; g += kEmThreads) {
+            float mx = 0.f;
+            for (int i = 0; i < kTile; ++i) mx = fmaxf(mx, L[g * kTP + i]);
+            if (mx >= keep) act[atomicAdd(&s_nact, 1)] = g;
+        }
+        __syncthreads();
+        const int na = s_nact;
+        // ---- M: thread-owned (g, d) accumulators over the Gaussians that matter
         // four (g, d) pairs per step: eight independent FMA chains per thread
-        for (int p0 = tid; p0 < G * D; p0 += 4 * kEmThreads) {
+        for (int p0 = tid; p0 < na * D; p0 += 4 * kEmThreads) {
             int gq[4], dq[4];
             float mu[4], r1[4], r2[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const int p = min(p0 + u * kEmThreads, G * D - 1);
-                gq[u] = p / D;
-                dq[u] = p - gq[u] * D;
-                mu[u] = __ldg(a.op.mu + p);
+                const int p = min(p0 + u * kEmThreads, na * D - 1);
+                const int ga = p / D;
+                gq[u] = act[ga];
+                dq[u] = p - ga * D;
+                mu[u] = __ldg(a.op.mu + (size_t)gq[u] * D + dq[u]);
                 r1[u] = 0.f;
                 r2[u] = 0.f;
             }
@@ -753,13 +768,15 @@ __global__ void __launch_bounds__(kEmThreads, 1) k_em_pass_simt(EmPassArgs a)
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int p = p0 + u * kEmThreads;
-                if (p < G * D) {
-                    S1[p] += r1[u];
-                    S2[p] += r2[u];
+                if (p < na * D) {
+                    const int q = gq[u] * D + dq[u];
+                    S1[q] += r1[u];
+                    S2[q] += r2[u];
                 }
             }
         }
-        for (int g = tid; g < G; g += kEmThreads) {
+        for (int k = tid; k < na; k += kEmThreads) {
+            const int g = act[k];
             float r0 = 0.f;
             for (int i = 0; i < kTile; ++i) r0 += L[g * kTP + i];
             S0[g] += r0;
@@ -1214,7 +1231,7 @@ long long launches_total() { return g_launches.load(std::memory_order_relaxed); 
 
 size_t em_simt_smem(int32_t D, int32_t G)
 {
-    return sizeof(float) * ((size_t)D * kTP + (size_t)G * kTP + (size_t)G + 2 * (size_t)G * D);
+    return sizeof(float) * ((size_t)D * kTP + (size_t)G * kTP + (size_t)G + 2 * (size_t)G * D) + sizeof(int) * (size_t)G;
 }
 
 bool em_simt_supported(int32_t D, int32_t G)
