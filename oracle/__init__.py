@@ -22,7 +22,7 @@ _lock = threading.Lock()
 _lib = None
 
 DIST_EUCL, DIST_MAHA, DIST_PROB = 0, 1, 2
-SEED_KEEP_EXISTING, SEED_RANDOM_SUBSET = 0, 1
+SEED_KEEP_EXISTING, SEED_RANDOM_SUBSET, SEED_STATIC_SUBSET, SEED_STATIC_SPREAD, SEED_RANDOM_SPREAD = 0, 1, 2, 3, 4
 
 
 def build(force: bool = False) -> str:
@@ -53,6 +53,8 @@ def _load():
                 "orc_posteriors": (ctypes.c_int, [P, i64, i32, i32, P, P, P, P]),
                 "orc_global_stats": (ctypes.c_int, [P, i64, i32, P, P]),
                 "orc_seed_random_subset": (ctypes.c_int, [i64, i32, u64, P]),
+                "orc_seed_static_subset": (ctypes.c_int, [i64, i32, P]),
+                "orc_seed_spread": (ctypes.c_int, [P, i64, i32, i32, P, i64, P]),
                 "orc_km_dist": (f64, [P, P, P, i32]),
                 "orc_km_assign": (ctypes.c_int, [P, i64, i32, i32, P, P, P, P, P]),
                 "orc_kmeans": (ctypes.c_int, [P, i64, i32, i32, P, P, P, P, P, i32, f64, P]),
@@ -147,6 +149,22 @@ def seed_random_subset(N: int, G: int, seed: int):
     idx = np.empty(G, np.int64)
     _check(_load().orc_seed_random_subset(N, G, ctypes.c_uint64(seed & (2**64 - 1)), _p(idx)),
            "seed_random_subset")
+    return idx
+
+
+def seed_static_subset(N: int, G: int):
+    idx = np.empty(G, np.int64)
+    _check(_load().orc_seed_static_subset(N, G, _p(idx)), "seed_static_subset")
+    return idx
+
+
+def seed_spread(X, G: int, w, first: int):
+    """Farthest-first traversal from sample `first` (static_spread / random_spread)."""
+    X = _x(X)
+    N, D = X.shape
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    idx = np.empty(G, np.int64)
+    _check(_load().orc_seed_spread(_p(X), N, D, G, _p(w), first, _p(idx)), "seed_spread")
     return idx
 
 

@@ -196,6 +196,55 @@ int orc_seed_random_subset(int64_t N, int32_t G, uint64_t seed, int64_t *idx_out
     return ORC_OK;
 }
 
+double orc_km_dist(const float *x, const double *mu, const double *w, int32_t D);
+
+/* static_subset (Sec. 4.1, seed_mode): "a subset of the training samples
+ * (repeatable)".  Reading: N_G samples at evenly spaced indices
+ * floor(g * N / N_G), g = 0..N_G-1 -- repeatable and free of random numbers. */
+int orc_seed_static_subset(int64_t N, int32_t G, int64_t *idx_out)
+{
+    if (G < 1 || (int64_t)G > N) return ORC_ERR_ARG;
+    for (int32_t g = 0; g < G; ++g) idx_out[g] = (int64_t)(((__int128)g * N) / G);
+    return ORC_OK;
+}
+
+/* static_spread / random_spread (Sec. 4.1, seed_mode): "a maximally spread
+ * subset of training samples", repeatable or from a random start, inspired
+ * by k-means++.  Reading: greedy farthest-first traversal.  The first seed is
+ * sample `first`; each next seed is the sample whose distance (Eq. 20 with
+ * the k-means weights w: Mahalanobis or Euclidean, in the order of
+ * orc_km_dist) to its nearest chosen seed is largest, the lowest index on an
+ * exact tie; chosen samples are never chosen again (so the seeds are
+ * distinct even when samples repeat). */
+int orc_seed_spread(const float *X, int64_t N, int32_t D, int32_t G, const double *w, int64_t first,
+                    int64_t *idx_out)
+{
+    if (G < 1 || (int64_t)G > N || first < 0 || first >= N) return ORC_ERR_ARG;
+    double *mind = (double *)malloc(sizeof(double) * (size_t)N);
+    double *mu = (double *)malloc(sizeof(double) * (size_t)D);
+    if (!mind || !mu) { free(mind); free(mu); return ORC_ERR_OOM; }
+    for (int64_t i = 0; i < N; ++i) mind[i] = INFINITY;
+    int64_t cur = first;
+    for (int32_t g = 0; g < G; ++g) {
+        idx_out[g] = cur;
+        mind[cur] = -1.0;   /* chosen */
+        if (g + 1 == G) break;
+        for (int32_t d = 0; d < D; ++d) mu[d] = (double)X[(size_t)cur * D + d];
+        int64_t best = -1;
+        double bv = -INFINITY;
+        for (int64_t i = 0; i < N; ++i) {
+            if (mind[i] < 0.0) continue;
+            double dd = orc_km_dist(X + (size_t)i * D, mu, w, D);
+            if (dd < mind[i]) mind[i] = dd;
+            if (mind[i] > bv) { bv = mind[i]; best = i; }
+        }
+        cur = best;
+    }
+    free(mind);
+    free(mu);
+    return ORC_OK;
+}
+
 /* ------------------------------------------------------------------------ */
 /* k-means (Sec. 3): the hard-assignment special case of EM, Eq. 19.         */
 /* ------------------------------------------------------------------------ */
@@ -522,7 +571,8 @@ int orc_assign(const float *X, int64_t N, int32_t D, int32_t G, const double *me
 /*
  * learn(data, n_gaus, dist_mode, seed_mode, km_iter, em_iter, var_floor)
  * (Sec. 4.1).  dist_mode: 0 eucl, 1 maha.  seed_mode: 0 keep_existing (the
- * given means/dcovs/hefts are the start), 1 random_subset (seed).
+ * given means/dcovs/hefts are the start), 1 random_subset (seed), 2
+ * static_subset, 3 static_spread, 4 random_spread (seed).
  * Flow: global statistics (Mahalanobis weights, floored) -> seeds -> k-means
  * (if km_iter > 0) -> EM (em_iter iterations).  With km_iter == 0 and
  * random_subset the start is the plain initialisation of Sec. 3 first
@@ -535,7 +585,7 @@ int orc_learn(const float *X, int64_t N, int32_t D, int32_t G, int32_t dist_mode
 {
     if (N < 1 || D < 1 || G < 1 || (int64_t)G > N || km_iter < 0 || em_iter < 0 ||
         !(var_floor >= 0.0) || (dist_mode != 0 && dist_mode != 1) ||
-        (seed_mode != 0 && seed_mode != 1))
+        seed_mode < 0 || seed_mode > 4)
         return ORC_ERR_ARG;
     double *gm = (double *)malloc(sizeof(double) * D), *gv = (double *)malloc(sizeof(double) * D);
     double *w = (double *)malloc(sizeof(double) * D);
@@ -546,10 +596,16 @@ int orc_learn(const float *X, int64_t N, int32_t D, int32_t G, int32_t dist_mode
         w[d] = dist_mode == 1 ? 1.0 / gv[d] : 1.0;
     }
     int rc = ORC_OK;
-    if (seed_mode == 1) {
+    if (seed_mode != 0) {
         int64_t *idx = (int64_t *)malloc(sizeof(int64_t) * G);
         if (!idx) { free(gm); free(gv); free(w); return ORC_ERR_OOM; }
-        rc = orc_seed_random_subset(N, G, seed, idx);
+        if (seed_mode == 1) rc = orc_seed_random_subset(N, G, seed, idx);
+        else if (seed_mode == 2) rc = orc_seed_static_subset(N, G, idx);
+        else {
+            int64_t first = 0;   /* static_spread: sample 0; random_spread: random_subset's first draw */
+            if (seed_mode == 4) rc = orc_seed_random_subset(N, 1, seed, &first);
+            if (rc == ORC_OK) rc = orc_seed_spread(X, N, D, G, w, first, idx);
+        }
         for (int32_t g = 0; g < G && rc == ORC_OK; ++g) {
             for (int32_t d = 0; d < D; ++d) {
                 means[(size_t)g * D + d] = (double)X[(size_t)idx[g] * D + d];

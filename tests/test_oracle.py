@@ -352,3 +352,52 @@ def test_learn_rejects_bad_arguments():
         oracle.learn(X, 6)
     with pytest.raises(RuntimeError):
         oracle.learn(X, 2, var_floor=-1.0)
+
+
+# ------------------------------------------------------------ seed modes (Sec. 4.1)
+def test_static_subset_is_evenly_spaced():
+    idx = oracle.seed_static_subset(10, 4)
+    np.testing.assert_array_equal(idx, [0, 2, 5, 7])   # floor(g * 10 / 4)
+    idx = oracle.seed_static_subset(7, 7)
+    np.testing.assert_array_equal(idx, np.arange(7))
+
+
+def test_spread_is_farthest_first_on_a_line():
+    """Points 0..9 on a line, unit weights: from 0 the farthest is 9; then 4
+    and 5 are both 4 away from their nearest seed and the lower index wins."""
+    X = np.arange(10, dtype=np.float32)[:, None]
+    np.testing.assert_array_equal(oracle.seed_spread(X, 3, np.ones(1), 0), [0, 9, 4])
+    np.testing.assert_array_equal(oracle.seed_spread(X, 4, np.ones(1), 6), [6, 0, 3, 9])
+
+
+def test_spread_matches_bruteforce_and_weights():
+    rng = np.random.default_rng(8)
+    X = rng.normal(0, 1, (60, 3)).astype(np.float32) * np.array([1.0, 5.0, 0.2], np.float32)
+    w = 1.0 / np.array([1.0, 25.0, 0.04])
+    idx = oracle.seed_spread(X, 7, w, 11)
+    chosen = [11]
+    Xd = X.astype(np.float64)
+    while len(chosen) < 7:
+        d = np.min(((Xd[:, None, :] - Xd[None, chosen, :]) ** 2 * w).sum(2), axis=1)
+        d[chosen] = -1.0
+        chosen.append(int(np.argmax(d)))   # argmax returns the lowest index of the maximum
+    np.testing.assert_array_equal(idx, chosen)
+    # duplicates: seeds stay distinct when fewer distinct points than seeds exist
+    Xr = np.repeat(np.array([[0.0], [1.0]], np.float32), 3, axis=0)
+    idx = oracle.seed_spread(Xr, 4, np.ones(1), 0)
+    assert len(set(idx.tolist())) == 4
+
+
+def test_learn_seed_modes_place_means_on_samples():
+    X, _, _ = synth.make("c1", N=5000)
+    for mode in (oracle.SEED_STATIC_SUBSET, oracle.SEED_STATIC_SPREAD, oracle.SEED_RANDOM_SPREAD):
+        M, V, H, _ = oracle.learn(X, 8, seed_mode=mode, seed=5, km_iter=0, em_iter=0)
+        rows = {tuple(r) for r in X.astype(np.float64)}
+        assert all(tuple(m) in rows for m in M)
+        np.testing.assert_array_equal(V, np.ones_like(V))
+    # random_spread starts where random_subset's first draw lands
+    _, gv = oracle.global_stats(X)
+    M, _, _, _ = oracle.learn(X, 8, seed_mode=oracle.SEED_RANDOM_SPREAD, seed=5, km_iter=0, em_iter=0)
+    first = oracle.seed_random_subset(X.shape[0], 1, 5)[0]
+    idx = oracle.seed_spread(X, 8, 1.0 / np.maximum(gv, 1e-10), first)
+    np.testing.assert_array_equal(M, X[idx].astype(np.float64))
