@@ -58,8 +58,20 @@ typedef enum { GMM_EUCL = 0, GMM_MAHA = 1, GMM_PROB = 2 } gmm_dist;
 
 /* Seeding (Sec. 4.1 `seed_mode`): KEEP_EXISTING starts from the model's
  * parameters; RANDOM_SUBSET takes n_gaus distinct random samples as means
- * (SplitMix64(seed) driving a partial Fisher-Yates shuffle of 0..N-1). */
-typedef enum { GMM_KEEP_EXISTING = 0, GMM_RANDOM_SUBSET = 1 } gmm_seed;
+ * (SplitMix64(seed) driving a partial Fisher-Yates shuffle of 0..N-1);
+ * STATIC_SUBSET the samples floor(g N / n_gaus) (repeatable); STATIC_SPREAD
+ * and RANDOM_SPREAD a maximally spread subset: greedy farthest-first under the
+ * k-means distance (dist), lowest index on ties, starting at sample 0 or at
+ * RANDOM_SUBSET's first draw for `seed` (N_G passes over X, FP64 distances).
+ * With km_iter = 0 the seeds are the means, with unit variances and uniform
+ * hefts. */
+typedef enum {
+    GMM_KEEP_EXISTING = 0,
+    GMM_RANDOM_SUBSET = 1,
+    GMM_STATIC_SUBSET = 2,
+    GMM_STATIC_SPREAD = 3,
+    GMM_RANDOM_SPREAD = 4
+} gmm_seed;
 
 /* Arithmetic of the E-step log-density (Eq. 15) in the fused EM pass.
  *   FP32   CUDA cores: direct sum of (x - mu)^2 / sigma^2 for every (sample,

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libgmm_gb300.so")
 GMM_OK, GMM_ERR_ARG, GMM_ERR_NONFINITE, GMM_ERR_CUDA = 0, -1, -2, -3
 GMM_ERR_TIMEOUT, GMM_ERR_OOM, GMM_ERR_STATE, GMM_ERR_UNSUPPORTED = -4, -5, -6, -7
 GMM_EUCL, GMM_MAHA, GMM_PROB = 0, 1, 2
-GMM_KEEP_EXISTING, GMM_RANDOM_SUBSET = 0, 1
+GMM_KEEP_EXISTING, GMM_RANDOM_SUBSET, GMM_STATIC_SUBSET, GMM_STATIC_SPREAD, GMM_RANDOM_SPREAD = 0, 1, 2, 3, 4
 GMM_FP32, GMM_BF16, GMM_TF32, GMM_SPLIT_BF16 = 0, 1, 2, 3
 GMM_DEBUG_WAIT_CYCLES, GMM_DEBUG_SKIP_MMA = 1, 2
 GMM_STAT_SCREENED, GMM_STAT_KEPT, GMM_STAT_DENSE = 3, 4, 5

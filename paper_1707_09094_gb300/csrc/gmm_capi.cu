@@ -123,6 +123,7 @@ struct gmm_model {
     double *partial = nullptr; size_t partial_cap = 0;
     float *slab = nullptr; size_t slab_cap = 0;
     unsigned char *tclist = nullptr; size_t tclist_cap = 0;   // tensor-core pass: per-sample records
+    double *spread = nullptr; size_t spread_cap = 0;          // spread seeding: distances + block partials
     float *lse = nullptr; size_t lse_cap = 0;
     double *llp = nullptr; size_t llp_cap = 0;
     double *lld = nullptr; size_t lld_cap = 0;
@@ -400,7 +401,7 @@ void gmm_destroy(gmm_model *m)
     if (m->sstats) cudaFree(m->sstats);
     void *bufs[] = {m->par[0], m->par[1], m->op_sm, m->op_mu, m->op_c, m->op_B, m->gstat, m->fstat,
                     m->partial, m->slab, m->lse, m->llp, m->lld, m->counts, m->assign, m->xstage, m->dstage, m->idx,
-                    m->hist, m->status, m->tclist};
+                    m->hist, m->status, m->tclist, m->spread};
     for (void *p : bufs)
         if (p) cudaFree(p);
     delete m;
@@ -419,12 +420,12 @@ gmm_status gmm_learn(gmm_model *m, const float *X, int64_t N, int32_t D, int32_t
     if (km_iter < 0 || em_iter < 0) return fail(GMM_ERR_ARG, "km_iter and em_iter must be >= 0");
     if (!(var_floor >= 0.0) || !std::isfinite(var_floor)) return fail(GMM_ERR_ARG, "var_floor must be finite and >= 0");
     if (o.dist != GMM_EUCL && o.dist != GMM_MAHA) return fail(GMM_ERR_ARG, "dist must be EUCL or MAHA");
-    if (o.seed_mode != GMM_KEEP_EXISTING && o.seed_mode != GMM_RANDOM_SUBSET) return fail(GMM_ERR_ARG, "bad seed_mode");
+    if (o.seed_mode < GMM_KEEP_EXISTING || o.seed_mode > GMM_RANDOM_SPREAD) return fail(GMM_ERR_ARG, "bad seed_mode");
     if (o.prec < GMM_FP32 || o.prec > GMM_SPLIT_BF16) return fail(GMM_ERR_ARG, "bad prec");
     if (o.seed_mode == GMM_KEEP_EXISTING && !(m->has_params && m->D == D && m->G == n_gaus))
         return fail(GMM_ERR_STATE, "keep_existing needs parameters of shape (%d, %d)", n_gaus, D);
     cudaStream_t s = as_stream(o.stream);
-    if (o.seed_mode == GMM_RANDOM_SUBSET || m->D != D || m->G != n_gaus) {
+    if (o.seed_mode != GMM_KEEP_EXISTING || m->D != D || m->G != n_gaus) {
         rc = ensure_shape(m, D, n_gaus);
         if (rc != GMM_OK) return rc;
     }
@@ -432,10 +433,23 @@ gmm_status gmm_learn(gmm_model *m, const float *X, int64_t N, int32_t D, int32_t
     if ((rc = stage_x(m, X, N, D, s, &Xd)) != GMM_OK) return rc;
     CK(gmm::launch_status_reset(m->status, s));
     if ((rc = run_global_stats(m, Xd, N, var_floor, o.dist, s)) != GMM_OK) return rc;
-    if (o.seed_mode == GMM_RANDOM_SUBSET) {
-        std::vector<int64_t> idx = random_subset(N, n_gaus, o.seed);
+    if (o.seed_mode != GMM_KEEP_EXISTING) {
+        std::vector<int64_t> idx;
+        if (o.seed_mode == GMM_RANDOM_SUBSET) {
+            idx = random_subset(N, n_gaus, o.seed);
+        } else if (o.seed_mode == GMM_STATIC_SUBSET) {
+            for (int32_t g = 0; g < n_gaus; ++g) idx.push_back((int64_t)(((__int128)g * N) / n_gaus));
+        } else {   // spread: the first seed here, the rest on the device
+            idx.assign((size_t)n_gaus, 0);
+            idx[0] = o.seed_mode == GMM_STATIC_SPREAD ? 0 : random_subset(N, 1, o.seed)[0];
+        }
         CK(grow(m->idx, m->idx_cap, (size_t)n_gaus));
         CK(cudaMemcpyAsync(m->idx, idx.data(), sizeof(int64_t) * n_gaus, cudaMemcpyHostToDevice, s));
+        if (o.seed_mode == GMM_STATIC_SPREAD || o.seed_mode == GMM_RANDOM_SPREAD) {
+            const int blocks = 2 * m->sms;
+            CK(grow(m->spread, m->spread_cap, (size_t)N + 2u * blocks));
+            CK(gmm::launch_spread_seeds(Xd, N, D, n_gaus, m->wdist(), m->idx, m->spread, blocks, s));
+        }
         m->cur = 0;
         CK(gmm::launch_gather_seeds(Xd, D, n_gaus, m->idx, m->par[0], s));
         CK(cudaStreamSynchronize(s));   // idx is a host vector

@@ -170,6 +170,11 @@ cudaError_t init_net_run(InitNet *n, const float *pts, int B, int P, const doubl
                          double lambda, double var_floor, int grads, double lr, double *pm, double *pv, double *pw,
                          double *loss_host, cudaStream_t s);
 
+// Spread seeding: idx[0] set by the caller, idx[1..G-1] written on the device;
+// work holds N + 2 * blocks doubles.
+cudaError_t launch_spread_seeds(const float *X, int64_t N, int32_t D, int32_t G, const double *w, int64_t *idx,
+                                double *work, int32_t blocks, cudaStream_t s);
+
 // ---- launchers implemented in gmm_em_tc.cu
 constexpr int kTcCap = 16;   // candidates per (sample, half of the Gaussians) before the dense fallback
 constexpr int kTcKeep = 16;  // responsibilities kept per sample before the full-recompute fallback

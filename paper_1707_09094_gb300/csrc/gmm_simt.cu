@@ -1224,6 +1224,81 @@ cudaError_t launch_avg_log_p_noalloc(const float *X, int64_t N, int32_t D, int32
     return cudaStreamSynchronize(s);
 }
 
+// ------------------------------------------------------------------------
+// Spread seeding (static_spread / random_spread, Sec. 4.1): greedy
+// farthest-first traversal.  Pass g marks seed idx[g] as chosen (mind = -1),
+// lowers every other sample's distance to its nearest seed by its distance to
+// idx[g] (Eq. 20 with the k-means weights, FP64, d = 0..D-1 without fused
+// operations: the oracle's order) and reduces the largest (lowest index on a
+// tie) per block; the pick kernel reduces the blocks in order into idx[g+1].
+// ------------------------------------------------------------------------
+struct SpreadArgs {
+    const float *X;
+    int64_t N;
+    int32_t D;
+    const double *w;
+    int64_t *idx;
+    double *mind;      // [N]
+    double *pv;        // [blocks] best distance per block
+    int64_t *pi;       // [blocks] its sample
+    int32_t g;
+    int32_t init;
+};
+
+__global__ void __launch_bounds__(256) k_spread_pass(SpreadArgs a)
+{
+    __shared__ double sv[256];
+    __shared__ int64_t si[256];
+    const int64_t cur = a.idx[a.g];
+    const float *xc = a.X + cur * a.D;
+    double bv = -INFINITY;
+    int64_t bi = INT64_MAX;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += (int64_t)gridDim.x * blockDim.x) {
+        double md = a.init ? INFINITY : a.mind[i];
+        if (i == cur) {
+            md = -1.0;
+        } else if (md >= 0.0) {
+            const float *x = a.X + i * a.D;
+            double acc = 0.0;
+            for (int d = 0; d < a.D; ++d) {
+                const double t = __dsub_rn((double)x[d], (double)xc[d]);
+                acc = __dadd_rn(acc, __dmul_rn(a.w[d], __dmul_rn(t, t)));
+            }
+            if (acc < md) md = acc;
+        }
+        a.mind[i] = md;
+        if (md >= 0.0 && (md > bv || (md == bv && i < bi))) { bv = md; bi = i; }
+    }
+    sv[threadIdx.x] = bv;
+    si[threadIdx.x] = bi;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+            const double ov = sv[threadIdx.x + h];
+            const int64_t oi = si[threadIdx.x + h];
+            if (ov > sv[threadIdx.x] || (ov == sv[threadIdx.x] && oi < si[threadIdx.x])) {
+                sv[threadIdx.x] = ov;
+                si[threadIdx.x] = oi;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        a.pv[blockIdx.x] = sv[0];
+        a.pi[blockIdx.x] = si[0];
+    }
+}
+
+__global__ void k_spread_pick(SpreadArgs a, int nb)
+{
+    if (threadIdx.x != 0) return;
+    double bv = -INFINITY;
+    int64_t bi = INT64_MAX;
+    for (int b = 0; b < nb; ++b)
+        if (a.pv[b] > bv || (a.pv[b] == bv && a.pi[b] < bi)) { bv = a.pv[b]; bi = a.pi[b]; }
+    a.idx[a.g + 1] = bi;
+}
+
 // ======================================================================== host
 static std::atomic<long long> g_launches{0};
 void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
@@ -1478,4 +1553,20 @@ cudaError_t launch_hist(const int32_t *a, int64_t N, int32_t G, unsigned long lo
     return cudaGetLastError();
 }
 
+}  // namespace gmm
+
+namespace gmm {
+cudaError_t launch_spread_seeds(const float *X, int64_t N, int32_t D, int32_t G, const double *w, int64_t *idx,
+                                double *work, int32_t blocks, cudaStream_t s)
+{
+    SpreadArgs a{X, N, D, w, idx, work, work + N, reinterpret_cast<int64_t *>(work + N + blocks), 0, 1};
+    for (int32_t g = 0; g + 1 < G; ++g) {
+        a.g = g;
+        a.init = g == 0;
+        k_spread_pass<<<blocks, 256, 0, s>>>(a);
+        k_spread_pick<<<1, 32, 0, s>>>(a, blocks);
+    }
+    count_launches(2 * (G > 1 ? G - 1 : 0));
+    return cudaGetLastError();
+}
 }  // namespace gmm

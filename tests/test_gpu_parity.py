@@ -321,3 +321,35 @@ def test_c3_full_size_fp32_properties_and_sampled_log_p():
     np.testing.assert_allclose(lp, oracle.log_p(X[idx], m, v, h), rtol=1e-5, atol=1e-4)
     del Xd
     torch.cuda.empty_cache()
+
+
+# ------------------------------------------------------------ other seed modes (Sec. 4.1)
+@pytest.mark.parametrize("dist", [GMM_MAHA, GMM_EUCL])
+@pytest.mark.parametrize("mode", ["static_subset", "static_spread", "random_spread"])
+def test_seed_modes_match_oracle(mode, dist):
+    """The same seed samples as the oracle (the spread modes' FP64 distances
+    are taken in the oracle's order, so the farthest-first choices agree
+    exactly), then a short learn from them within the FP32 tolerances."""
+    from paper_1707_09094_gb300 import GMM_RANDOM_SPREAD, GMM_STATIC_SPREAD, GMM_STATIC_SUBSET
+    sm = {"static_subset": GMM_STATIC_SUBSET, "static_spread": GMM_STATIC_SPREAD,
+          "random_spread": GMM_RANDOM_SPREAD}[mode]
+    X, _, _ = synth.make("c1", N=20000, seed=31)
+    g = GMM().learn(dev(X), 8, dist_mode=dist, seed_mode=sm, km_iter=0, em_iter=0, seed=11)
+    M, V, H, _ = oracle.learn(X, 8, dist_mode=dist, seed_mode=sm, seed=11, km_iter=0, em_iter=0)
+    m, v, h = g.get_params()
+    np.testing.assert_array_equal(m, M)
+    np.testing.assert_array_equal(v, V)
+    np.testing.assert_array_equal(h, H)
+    g2 = GMM().learn(dev(X), 8, dist_mode=dist, seed_mode=sm, km_iter=3, em_iter=3, seed=11)
+    M2, V2, H2, ll = oracle.learn(X, 8, dist_mode=dist, seed_mode=sm, seed=11, km_iter=3, em_iter=3)
+    assert_params(g2.get_params(), (M2, V2, H2), X, min_count=10.0)
+    np.testing.assert_allclose(g2.ll_history(), ll, rtol=1e-6)
+
+
+def test_spread_seeds_many_gaussians():
+    X, _, _ = synth.make("c1", N=200_000, D=10, G=64, seed=32)
+    from paper_1707_09094_gb300 import GMM_STATIC_SPREAD
+    g = GMM().learn(dev(X), 64, seed_mode=GMM_STATIC_SPREAD, km_iter=0, em_iter=0)
+    _, gv = oracle.global_stats(X)
+    idx = oracle.seed_spread(X, 64, 1.0 / np.maximum(gv, 1e-10), 0)
+    np.testing.assert_array_equal(g.get_params()[0], X[idx].astype(np.float64))
