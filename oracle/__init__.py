@@ -64,6 +64,7 @@ def _load():
                 "orc_learn": (ctypes.c_int, [P, i64, i32, i32, i32, i32, u64, i32, i32, f64, f64,
                                              i32, P, P, P, P, P]),
                 "orc_num_threads": (ctypes.c_int, []),
+                "orc_generate": (ctypes.c_int, [P, P, P, i32, i32, i64, u64, P, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -166,6 +167,19 @@ def seed_spread(X, G: int, w, first: int):
     idx = np.empty(G, np.int64)
     _check(_load().orc_seed_spread(_p(X), N, D, G, _p(w), first, _p(idx)), "seed_spread")
     return idx
+
+
+def generate(means, dcovs, hefts, N: int, seed: int = 0):
+    """M.generate(N) of Sec. 4.1: (X float32 [N][D], labels int32 [N])."""
+    means = np.ascontiguousarray(means, dtype=np.float64)
+    dcovs = np.ascontiguousarray(dcovs, dtype=np.float64)
+    hefts = np.ascontiguousarray(hefts, dtype=np.float64)
+    G, D = means.shape
+    X = np.empty((N, D), np.float32)
+    lab = np.empty(N, np.int32)
+    _check(_load().orc_generate(_p(means), _p(dcovs), _p(hefts), G, D, N, ctypes.c_uint64(seed & (2**64 - 1)),
+                                _p(X), _p(lab)), "generate")
+    return X, lab
 
 
 def km_dist(x, mu, w) -> float:

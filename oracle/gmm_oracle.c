@@ -634,3 +634,56 @@ int orc_num_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------ */
+/* generate (Sec. 4.1, M.generate(N)): N random samples of the model.       */
+/* Reading (the paper gives no generator): uniforms from SplitMix64 used as  */
+/* a counter-based generator -- output k for seed s is the SplitMix64 mix of */
+/* s + (k + 1) * 0x9e3779b97f4a7c15, i.e. the k-th output of a generator     */
+/* started at state s -- as u = ((r >> 11) + 0.5) 2^-53 in (0, 1).  Sample i */
+/* uses outputs i*K .. i*K + K - 1, K = 1 + 2 ceil(D / 2): the first picks  */
+/* the Gaussian (the first g with u < cumulative heft / total heft, else the */
+/* last), then pairs (u1, u2) give Box-Muller normals sqrt(-2 ln u1) (cos,   */
+/* sin)(2 pi u2) for dimensions 2j, 2j+1; x = mean + sqrt(dcov) z, stored as */
+/* float.                                                                    */
+/* ------------------------------------------------------------------------ */
+static double orc_counter_uniform(uint64_t seed, uint64_t k)
+{
+    uint64_t z = seed + (k + 1) * 0x9e3779b97f4a7c15ULL;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    z ^= z >> 31;
+    return ((double)(z >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+}
+
+int orc_generate(const double *means, const double *dcovs, const double *hefts, int32_t G, int32_t D,
+                 int64_t N, uint64_t seed, float *out, int32_t *labels)
+{
+    if (G < 1 || D < 1 || N < 0) return ORC_ERR_ARG;
+    double tot = 0.0;
+    for (int32_t g = 0; g < G; ++g) tot += hefts[g];
+    const int64_t K = 1 + 2 * (int64_t)((D + 1) / 2);
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int64_t i = 0; i < N; ++i) {
+        const uint64_t k0 = (uint64_t)(i * K);
+        const double u = orc_counter_uniform(seed, k0);
+        int32_t lab = G - 1;
+        double c = 0.0;
+        for (int32_t g = 0; g < G; ++g) {
+            c += hefts[g];
+            if (u < c / tot) { lab = g; break; }
+        }
+        if (labels) labels[i] = lab;
+        for (int32_t j = 0; 2 * j < D; ++j) {
+            const double u1 = orc_counter_uniform(seed, k0 + 1 + 2 * (uint64_t)j);
+            const double u2 = orc_counter_uniform(seed, k0 + 2 + 2 * (uint64_t)j);
+            const double r = sqrt(-2.0 * log(u1));
+            for (int32_t h = 0; h < 2 && 2 * j + h < D; ++h) {
+                const int32_t d = 2 * j + h;
+                const double z = r * (h == 0 ? cos(two_pi * u2) : sin(two_pi * u2));
+                out[(size_t)i * D + d] = (float)(means[(size_t)lab * D + d] + sqrt(dcovs[(size_t)lab * D + d]) * z);
+            }
+        }
+    }
+    return ORC_OK;
+}

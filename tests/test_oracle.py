@@ -401,3 +401,32 @@ def test_learn_seed_modes_place_means_on_samples():
     first = oracle.seed_random_subset(X.shape[0], 1, 5)[0]
     idx = oracle.seed_spread(X, 8, 1.0 / np.maximum(gv, 1e-10), first)
     np.testing.assert_array_equal(M, X[idx].astype(np.float64))
+
+
+# ------------------------------------------------------------ generate (Sec. 4.1)
+def test_generate_matches_the_model_statistics():
+    """Samples of a known mixture: label frequencies within 5 sigma of the
+    hefts, per-component sample means and variances within 5 standard errors
+    of the model's (normal theory), and the first uniform equals SplitMix64's
+    first output from the seed (the published generator)."""
+    rng = np.random.default_rng(3)
+    G, D, N = 3, 5, 200_000
+    means = rng.normal(0, 3, (G, D))
+    dcovs = rng.uniform(0.5, 2.0, (G, D))
+    hefts = np.array([0.5, 0.3, 0.2])
+    X, lab = oracle.generate(means, dcovs, hefts, N, seed=0)
+    freq = np.bincount(lab, minlength=G) / N
+    assert np.all(np.abs(freq - hefts) < 5 * np.sqrt(hefts * (1 - hefts) / N))
+    for g in range(G):
+        xs = X[lab == g].astype(np.float64)
+        n = xs.shape[0]
+        assert np.all(np.abs(xs.mean(0) - means[g]) < 5 * np.sqrt(dcovs[g] / n))
+        assert np.all(np.abs(xs.var(0) - dcovs[g]) < 5 * dcovs[g] * np.sqrt(2.0 / n))
+    # the label of sample 0 follows from SplitMix64's first output for seed 0
+    with open(os.path.join(HERE, "golden", "splitmix64_seed0.txt")) as f:
+        first = [int(l.strip(), 16) for l in f if l.strip() and not l.startswith("#")][0]
+    u = ((first >> 11) + 0.5) / 2.0 ** 53
+    assert lab[0] == int(np.searchsorted(np.cumsum(hefts), u, side="right"))
+    # deterministic
+    X2, lab2 = oracle.generate(means, dcovs, hefts, 1000, seed=0)
+    np.testing.assert_array_equal(X2, X[:1000])
