@@ -273,6 +273,25 @@ gmm_status gmm_init_net_step(gmm_init_net *n, const float *pts, int32_t B, int32
 gmm_status gmm_init_net_seed_model(const gmm_init_net *n, gmm_model *m, const float *X, int64_t N, int32_t P,
                                    uint64_t seed, double var_floor, void *stream);
 
+/* generate (Sec. 4.1, M.generate(N)): N random samples of the model into out
+ * (float [N][D], host or device pointer, owned by the caller).  Sample i
+ * takes SplitMix64 outputs i*K .. i*K + K - 1 of a generator started at
+ * state `seed` (K = 1 + 2 ceil(D/2); output k is computed directly from
+ * seed + (k+1) * 0x9e3779b97f4a7c15, so samples are independent of N and of
+ * the launch): the first picks the Gaussian by its heft (inverse CDF), pairs
+ * give Box-Muller normals; x = mean + sqrt(dcov) z.  Errors: GMM_ERR_STATE
+ * without parameters, GMM_ERR_ARG for N < 0 or out == NULL with N > 0. */
+gmm_status gmm_generate(const gmm_model *m, int64_t N, uint64_t seed, float *out, void *stream);
+
+/* save / load (Sec. 4.1, M.save / M.load): the model's parameters in a file
+ * of this library's format -- 8 bytes "GMMDIAG1", int32 D, int32 n_gaus
+ * (little-endian), then FP64 means [n_gaus][D], dcovs [n_gaus][D], hefts
+ * [n_gaus].  load checks the header, the sizes, and that every value is
+ * finite, every dcov > 0 and every heft >= 0; on any failure the model is
+ * unchanged and GMM_ERR_ARG is returned (the paper's `false`). */
+gmm_status gmm_save(const gmm_model *m, const char *path);
+gmm_status gmm_load(gmm_model *m, const char *path);
+
 /* Read the parameters (host pointers; any may be NULL).  D / n_gaus receive
  * the shape.  GMM_ERR_STATE if the model has none. */
 gmm_status gmm_get_params(const gmm_model *m, int32_t *D, int32_t *n_gaus, double *means,

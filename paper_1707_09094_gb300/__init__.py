@@ -8,6 +8,7 @@ memory and the current stream.
 from __future__ import annotations
 
 import ctypes
+import os
 
 import numpy as np
 
@@ -182,6 +183,32 @@ class GMM:
         """reset() of Sec. 4.1: zero means, unit covariances, uniform hefts."""
         return self.set_params(np.zeros((n_gaus, n_dims)), np.ones((n_gaus, n_dims)),
                                np.full(n_gaus, 1.0 / n_gaus))
+
+    def generate(self, N, seed=0, device="cuda"):
+        """M.generate(N) of Sec. 4.1: N samples of the model as a float32 [N][D]
+        tensor on `device` ("cuda") or a numpy array (device=None)."""
+        D = self.get_params()[0].shape[1]
+        if device is None:
+            out = np.empty((N, D), np.float32)
+            ptr = out.ctypes.data_as(ctypes.c_void_p)
+            stream = None
+        else:
+            torch = _torch()
+            out = torch.empty((N, D), dtype=torch.float32, device=device)
+            ptr = ctypes.c_void_p(out.data_ptr())
+            stream = _stream_ptr(out)
+        _lib.check(_lib.load().gmm_generate(self._h, N, seed & (2**64 - 1), ptr, stream), "gmm_generate")
+        return out
+
+    def save(self, path):
+        """M.save(filename) of Sec. 4.1."""
+        _lib.check(_lib.load().gmm_save(self._h, os.fsencode(path)), "gmm_save")
+        return self
+
+    def load(self, path):
+        """M.load(filename) of Sec. 4.1."""
+        _lib.check(_lib.load().gmm_load(self._h, os.fsencode(path)), "gmm_load")
+        return self
 
     def profile(self, enable=True):
         """Start (reset) or stop event timing of the fused-pass launches."""

@@ -48,6 +48,9 @@ SIGNATURES = {
     "gmm_norm_hist": (ctypes.c_int, [P, P, i64, i32, P, P]),
     "gmm_get_params": (ctypes.c_int, [P, ctypes.POINTER(i32), ctypes.POINTER(i32), P, P, P]),
     "gmm_set_params": (ctypes.c_int, [P, i32, i32, P, P, P]),
+    "gmm_generate": (ctypes.c_int, [P, i64, ctypes.c_uint64, P, P]),
+    "gmm_save": (ctypes.c_int, [P, ctypes.c_char_p]),
+    "gmm_load": (ctypes.c_int, [P, ctypes.c_char_p]),
     "gmm_get_stats": (ctypes.c_int, [P, P, i32, ctypes.POINTER(i32)]),
     "gmm_profile": (ctypes.c_int, [P, i32]),
     "gmm_profile_read": (ctypes.c_int, [P, ctypes.POINTER(f64), ctypes.POINTER(i64), ctypes.POINTER(i64)]),

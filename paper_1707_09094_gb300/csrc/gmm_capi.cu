@@ -680,6 +680,64 @@ gmm_status gmm_set_params(gmm_model *m, int32_t D, int32_t n_gaus, const double 
     return run_prep(m, nullptr);
 }
 
+gmm_status gmm_generate(const gmm_model *mc, int64_t N, uint64_t seed, float *out, void *stream)
+{
+    if (!mc) return fail(GMM_ERR_ARG, "model is NULL");
+    if (!mc->has_params) return fail(GMM_ERR_STATE, "model has no parameters");
+    if (N < 0 || (N > 0 && !out)) return fail(GMM_ERR_ARG, "need N >= 0 and an output buffer");
+    if (N == 0) return GMM_OK;
+    gmm_model *m = const_cast<gmm_model *>(mc);   // staging buffer only
+    cudaStream_t s = as_stream(stream);
+    const size_t n = (size_t)N * m->D;
+    if (is_device_ptr(out)) {
+        CK(gmm::launch_generate(m->par[m->cur], m->G, m->D, N, seed, out, m->sms, s));
+        return GMM_OK;
+    }
+    CK(grow(m->xstage, m->xstage_cap, n));
+    CK(gmm::launch_generate(m->par[m->cur], m->G, m->D, N, seed, m->xstage, m->sms, s));
+    CK(cudaMemcpyAsync(out, m->xstage, sizeof(float) * n, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return GMM_OK;
+}
+
+gmm_status gmm_save(const gmm_model *m, const char *path)
+{
+    if (!m || !path) return fail(GMM_ERR_ARG, "NULL argument");
+    if (!m->has_params) return fail(GMM_ERR_STATE, "model has no parameters");
+    const int32_t D = m->D, G = m->G;
+    const size_t GD = (size_t)G * D;
+    std::vector<double> buf(2 * GD + G);
+    gmm_status rc = gmm_get_params(m, nullptr, nullptr, buf.data(), buf.data() + GD, buf.data() + 2 * GD);
+    if (rc != GMM_OK) return rc;
+    FILE *f = fopen(path, "wb");
+    if (!f) return fail(GMM_ERR_ARG, "cannot open %s for writing", path);
+    bool ok = fwrite("GMMDIAG1", 1, 8, f) == 8 && fwrite(&D, sizeof(D), 1, f) == 1 && fwrite(&G, sizeof(G), 1, f) == 1 &&
+              fwrite(buf.data(), sizeof(double), buf.size(), f) == buf.size();
+    ok = (fclose(f) == 0) && ok;
+    return ok ? GMM_OK : fail(GMM_ERR_ARG, "cannot write %s", path);
+}
+
+gmm_status gmm_load(gmm_model *m, const char *path)
+{
+    if (!m || !path) return fail(GMM_ERR_ARG, "NULL argument");
+    FILE *f = fopen(path, "rb");
+    if (!f) return fail(GMM_ERR_ARG, "cannot open %s", path);
+    char magic[8];
+    int32_t D = 0, G = 0;
+    bool ok = fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "GMMDIAG1", 8) == 0 && fread(&D, sizeof(D), 1, f) == 1 &&
+              fread(&G, sizeof(G), 1, f) == 1 && D >= 1 && D <= GMM_MAX_DIMS && G >= 1 && G <= (1 << 24);
+    std::vector<double> buf;
+    if (ok) {
+        const size_t GD = (size_t)G * D;
+        buf.resize(2 * GD + G);
+        ok = fread(buf.data(), sizeof(double), buf.size(), f) == buf.size();
+    }
+    fclose(f);
+    if (!ok) return fail(GMM_ERR_ARG, "%s is not a model file of this library", path);
+    const size_t GD = (size_t)G * D;
+    return gmm_set_params(m, D, G, buf.data(), buf.data() + GD, buf.data() + 2 * GD);
+}
+
 gmm_status gmm_profile(gmm_model *m, int32_t enable)
 {
     if (!m) return fail(GMM_ERR_ARG, "model is NULL");

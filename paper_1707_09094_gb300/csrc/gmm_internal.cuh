@@ -175,6 +175,10 @@ cudaError_t init_net_run(InitNet *n, const float *pts, int B, int P, const doubl
 cudaError_t launch_spread_seeds(const float *X, int64_t N, int32_t D, int32_t G, const double *w, int64_t *idx,
                                 double *work, int32_t blocks, cudaStream_t s);
 
+// generate: N samples of the model (par = [means | dcovs | hefts]) into out (device)
+cudaError_t launch_generate(const double *par, int32_t G, int32_t D, int64_t N, uint64_t seed, float *out, int sms,
+                            cudaStream_t s);
+
 // ---- launchers implemented in gmm_em_tc.cu
 constexpr int kTcCap = 16;   // candidates per (sample, half of the Gaussians) before the dense fallback
 constexpr int kTcKeep = 16;  // responsibilities kept per sample before the full-recompute fallback

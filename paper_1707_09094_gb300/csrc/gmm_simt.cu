@@ -1299,6 +1299,59 @@ __global__ void k_spread_pick(SpreadArgs a, int nb)
     a.idx[a.g + 1] = bi;
 }
 
+// ------------------------------------------------------------------------
+// generate (Sec. 4.1, M.generate(N)): sample i takes the SplitMix64 outputs
+// i*K .. i*K+K-1 of a generator started at state `seed` (counter-based: output
+// k = mix(seed + (k+1) * 0x9e3779b97f4a7c15)), u = ((r >> 11) + 0.5) 2^-53;
+// the first picks the Gaussian (first g with u < cumulative heft / total,
+// else the last), pairs (u1, u2) give Box-Muller normals for dimensions
+// 2j, 2j+1; x = mean + sqrt(dcov) z, stored as float.
+// ------------------------------------------------------------------------
+__device__ __forceinline__ double counter_uniform(uint64_t seed, uint64_t k)
+{
+    uint64_t z = seed + (k + 1) * 0x9e3779b97f4a7c15ULL;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    z ^= z >> 31;
+    return ((double)(z >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+}
+
+__global__ void __launch_bounds__(256) k_generate(const double *__restrict__ par, int32_t G, int32_t D, int64_t N,
+                                                  uint64_t seed, float *__restrict__ out)
+{
+    extern __shared__ double cdf[];   // [G] cumulative hefts / total
+    const double *mu = par, *var = par + (size_t)G * D, *h = par + 2 * (size_t)G * D;
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int g = 0; g < G; ++g) tot = __dadd_rn(tot, h[g]);
+        double c = 0.0;
+        for (int g = 0; g < G; ++g) {
+            c = __dadd_rn(c, h[g]);
+            cdf[g] = __ddiv_rn(c, tot);
+        }
+    }
+    __syncthreads();
+    const int64_t K = 1 + 2 * (int64_t)((D + 1) / 2);
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t k0 = (uint64_t)(i * K);
+        const double u = counter_uniform(seed, k0);
+        int lab = G - 1;
+        for (int g = 0; g < G; ++g)
+            if (u < cdf[g]) { lab = g; break; }
+        for (int j = 0; 2 * j < D; ++j) {
+            const double u1 = counter_uniform(seed, k0 + 1 + 2 * (uint64_t)j);
+            const double u2 = counter_uniform(seed, k0 + 2 + 2 * (uint64_t)j);
+            const double r = sqrt(-2.0 * log(u1));
+            const double a = two_pi * u2;
+            const double z0 = r * cos(a), z1 = r * sin(a);
+            const int d = 2 * j;
+            out[i * D + d] = (float)(mu[(size_t)lab * D + d] + sqrt(var[(size_t)lab * D + d]) * z0);
+            if (d + 1 < D) out[i * D + d + 1] = (float)(mu[(size_t)lab * D + d + 1] + sqrt(var[(size_t)lab * D + d + 1]) * z1);
+        }
+    }
+}
+
 // ======================================================================== host
 static std::atomic<long long> g_launches{0};
 void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
@@ -1567,6 +1620,23 @@ cudaError_t launch_spread_seeds(const float *X, int64_t N, int32_t D, int32_t G,
         k_spread_pick<<<1, 32, 0, s>>>(a, blocks);
     }
     count_launches(2 * (G > 1 ? G - 1 : 0));
+    return cudaGetLastError();
+}
+}  // namespace gmm
+
+namespace gmm {
+cudaError_t launch_generate(const double *par, int32_t G, int32_t D, int64_t N, uint64_t seed, float *out, int sms,
+                            cudaStream_t s)
+{
+    const size_t sm = sizeof(double) * (size_t)G;
+    if (sm > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_generate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+    }
+    const int64_t want = (N + 255) / 256;
+    const int blocks = (int)(want < 8 * (int64_t)sms ? (want > 0 ? want : 1) : 8 * sms);
+    k_generate<<<blocks, 256, sm, s>>>(par, G, D, N, seed, out);
+    count_launches(1);
     return cudaGetLastError();
 }
 }  // namespace gmm

@@ -353,3 +353,29 @@ def test_spread_seeds_many_gaussians():
     _, gv = oracle.global_stats(X)
     idx = oracle.seed_spread(X, 64, 1.0 / np.maximum(gv, 1e-10), 0)
     np.testing.assert_array_equal(g.get_params()[0], X[idx].astype(np.float64))
+
+
+# ------------------------------------------------------------ generate, save, load (Sec. 4.1)
+def test_generate_matches_oracle_and_save_load_roundtrip(tmp_path):
+    """The same counter-based uniforms on both sides: labels identical and
+    values equal up to the last bits of the math library (FP64 log, cos, sin
+    rounded to float); host and device outputs equal; save + load restores
+    the parameters exactly; a bad file is rejected and leaves the model."""
+    _, _, mix = synth.make("c1", N=1000)
+    g = GMM().set_params(mix.means, mix.stds ** 2, mix.hefts)
+    Y = g.generate(100_000, seed=7).cpu().numpy()
+    Yr, _ = oracle.generate(mix.means, mix.stds ** 2, mix.hefts, 100_000, seed=7)
+    np.testing.assert_allclose(Y, Yr, rtol=1e-6, atol=1e-6)
+    np.testing.assert_array_equal(g.generate(1000, seed=7, device=None), Y[:1000])
+    path = tmp_path / "model.gmm"
+    g.save(path)
+    h = GMM().load(path)
+    for a, b in zip(g.get_params(), h.get_params()):
+        np.testing.assert_array_equal(a, b)
+    bad = tmp_path / "bad.gmm"
+    bad.write_bytes(b"GMMDIAG0" + bytes(16))
+    with pytest.raises(GmmError) as e:
+        h.load(bad)
+    assert e.value.status == -1
+    for a, b in zip(g.get_params(), h.get_params()):
+        np.testing.assert_array_equal(a, b)
