@@ -157,3 +157,18 @@ def test_tc_unaligned_input_matches_aligned():
     np.testing.assert_allclose(a.ll_history(), b.ll_history(), rtol=1e-7)
     # FP32 addition order: 1e-6 relative, with a floor of 1e-6 of the data's scale
     assert_params(b.get_params(), a.get_params(), X, rtol=1e-6)
+
+
+def test_tc_and_fp32_converge_alike_under_em_tol():
+    """Convergence-driven runs (em_tol = 1e-6, at most 250 iterations) on two
+    Table-1-shaped synthetic sets: the tensor-core form stops within a few
+    iterations of the FP32 form (their mean-LL gains differ by FP32 noise
+    where they cross em_tol) and at the same mean log-likelihood."""
+    for r, (N, D, G) in enumerate([(6497, 11, 30), (37749, 32, 50)]):
+        rng = np.random.default_rng(2100 + r)
+        X, _ = synth._draw(rng, synth.mixture_c1(rng, D, G), N)
+        Xd = dev(X)
+        a = GMM().learn(Xd, G, km_iter=10, em_iter=250, em_tol=1e-6, seed=5, prec="fp32")
+        b = GMM().learn(Xd, G, km_iter=10, em_iter=250, em_tol=1e-6, seed=5, prec="bf16")
+        assert abs(len(a.ll_history()) - len(b.ll_history())) <= 3   # the stop test sees LL gains near em_tol
+        assert abs(a.avg_log_p(Xd) - b.avg_log_p(Xd)) < 1e-5
