@@ -52,15 +52,17 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, interval_ms: int = 20):
         self.index = index
+        self.interval_ms = interval_ms
         self.proc = None
-        self.lines = []
+        self.lines = []          # (arrival time, line)
+        self.window = None       # (t0, t1): only samples that arrive inside count
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.interval_ms)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -70,7 +72,11 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def mark(self, t0, t1):
+        """The timed region, in time.perf_counter() seconds."""
+        self.window = (t0, t1)
 
     def __exit__(self, *a):
         if self.proc:
@@ -83,7 +89,9 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ts, ln in self.lines:
+            if self.window and not (self.window[0] <= ts <= self.window[1]):
+                continue
             p = [x.strip() for x in ln.split(",")]
             if len(p) < 9:
                 continue
@@ -221,23 +229,26 @@ def run_ours(args):
     def time_form(prec, host_input=False):
         g = em_model()
         Xin = X if not host_input else torch.from_numpy(X).pin_memory()
-        for _ in range(args.warmup):
+        with ClockSampler(local) as cs:   # started before the warm-up: sampling is live when timing starts
+            for _ in range(args.warmup):
+                g.set_params(*start)
+                g.em_iterate(Xin if host_input else Xd, 1, prec=prec)
             g.set_params(*start)
-            g.em_iterate(Xin if host_input else Xd, 1, prec=prec)
-        g.set_params(*start)
-        g.profile(True)
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-        with ClockSampler(local) as cs:
+            g.profile(True)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            if world > 1:
+                dist.barrier()
+            torch.cuda.synchronize()
             ev0.record(stream)
             t0 = time.perf_counter()
             for _ in range(args.steps):
                 g.em_iterate(Xin if host_input else Xd, 1, prec=prec)
             ev1.record(stream)
             torch.cuda.synchronize()
-            wall = time.perf_counter() - t0
+            t1 = time.perf_counter()
+            wall = t1 - t0
+            cs.mark(t0, t1)
+            time.sleep(2.5 * cs.interval_ms / 1e3)   # let the last samples of the window arrive
         ms = max_over_ranks(ev0.elapsed_time(ev1), world, "cuda")
         pass_ms, pass_n, launches = g.profile_read()
         extra = {}
@@ -455,7 +466,7 @@ def base_eval(base, g, Xd):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--forms", default="fp32,bf16",
