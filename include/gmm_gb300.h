@@ -75,13 +75,16 @@ typedef enum {
 
 /* Arithmetic of the E-step log-density (Eq. 15) in the fused EM pass.
  *   FP32   CUDA cores: direct sum of (x - mu)^2 / sigma^2 for every (sample,
- *          Gaussian), log-sum-exp, dense M-step (FP32 sums shifted by the
- *          iteration's means, reduced in FP64).
+ *          Gaussian), log-sum-exp, M-step (FP32 sums shifted by the
+ *          iteration's means, reduced in FP64) over the Gaussians holding a
+ *          responsibility >= 1e-9 / N somewhere in a 32-sample tile.
  *   BF16   tcgen05 tensor cores: the expanded log-density (x'^2 and x' blocks,
  *          data centred by the global mean) in BF16 with FP32 accumulation
  *          screens every Gaussian with a rigorous rounding bound; the
- *          Gaussians that can hold a responsibility >= 1e-12 are recomputed
- *          exactly in FP32 and only they enter log-sum-exp and the M-step.
+ *          Gaussians that can hold a responsibility >= 1e-9 / N are
+ *          recomputed exactly in FP32, and those whose exact responsibility
+ *          reaches 1e-9 / N enter log-sum-exp and the M-step.  (For every
+ *          Gaussian the responsibility left out sums to less than 1e-9.)
  *          Needs D <= 64 and n_gaus <= 256.
  *   TF32, SPLIT_BF16  reserved (GMM_ERR_UNSUPPORTED).
  * Sufficient statistics are reduced in FP64 in every mode. */
@@ -334,14 +337,15 @@ gmm_status gmm_debug_set(gmm_model *m, int32_t key, int64_t value);
 /* Screening counters of the tensor-core pass, summed since the last
  * gmm_profile(m, 1): GMM_STAT_SCREENED samples screened, GMM_STAT_KEPT
  * (sample, Gaussian) pairs kept for the exact recompute, GMM_STAT_DENSE
- * samples whose candidate list overflowed (exact pass over all Gaussians). */
+ * (sample, half of the Gaussians) lists that overflowed (exact pass over
+ * every Gaussian of the half). */
 #define GMM_STAT_SCREENED 3
 #define GMM_STAT_KEPT 4
 #define GMM_STAT_DENSE 5
 /* GMM_STAT_PHASE0 + k (k = 0..7): SM cycles one epilogue thread of each CTA
- * spent in phase k of a tile (0 prefetch, 1 barrier, 2 MMA wait, 3 screen,
- * 4 candidates + sample-tile wait, 5 exact recompute, 6 log-sum-exp and
- * M-step, 7 end-of-tile barrier), summed over CTAs. */
+ * of the screening kernel spent in phase k of a tile (0 building the next
+ * tile's BF16 operand, 1 barrier, 2 MMA wait, 3 screening bounds, 4 candidate
+ * lists and their records; 5-7 unused), summed over CTAs. */
 #define GMM_STAT_PHASE0 6
 gmm_status gmm_debug_get(const gmm_model *m, int32_t key, int64_t *value);
 
