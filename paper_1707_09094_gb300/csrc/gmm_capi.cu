@@ -124,6 +124,8 @@ struct gmm_model {
     float *slab = nullptr; size_t slab_cap = 0;
     unsigned char *tclist = nullptr; size_t tclist_cap = 0;   // tensor-core pass: per-sample records
     double *spread = nullptr; size_t spread_cap = 0;          // spread seeding: distances + block partials
+    cudaStream_t cstream = nullptr;                           // host-input copies that overlap the first pass
+    std::vector<cudaEvent_t> cev;                             // [0] start, [1..] chunk copies
     float *lse = nullptr; size_t lse_cap = 0;
     double *llp = nullptr; size_t llp_cap = 0;
     double *lld = nullptr; size_t lld_cap = 0;
@@ -284,10 +286,18 @@ gmm_status run_prep(gmm_model *m, cudaStream_t s)
     return GMM_OK;
 }
 
+// Host X arriving in sample chunks (tile-aligned bounds, one copy event per
+// chunk): the first EM iteration runs its pass chunk by chunk, each after its
+// copy, so the copies of later chunks overlap the pass over earlier ones.
+struct ChunkPlan {
+    std::vector<int64_t> bounds;     // C + 1 sample bounds
+    std::vector<cudaEvent_t> ready;  // C events recorded on the copy stream
+};
+
 // em_iter EM iterations from par[cur]; iteration k reads par[(cur+k)&1] and
 // writes par[(cur+k+1)&1].  The status block tells which buffer is final.
 gmm_status run_em(gmm_model *m, const float *Xd, int64_t N, int32_t em_iter, double var_floor, double em_tol,
-                  int32_t prec, int32_t print, cudaStream_t s)
+                  int32_t prec, int32_t print, cudaStream_t s, const ChunkPlan *cp = nullptr)
 {
     const int32_t D = m->D, G = m->G, S = 1 + 2 * D;
     const bool tc = prec == GMM_BF16;
@@ -302,27 +312,38 @@ gmm_status run_em(gmm_model *m, const float *Xd, int64_t N, int32_t em_iter, dou
     // one-pass forms: one partial per CTA; two-phase form: one per sample chunk
     // (and one log-likelihood partial per 128-sample block of the lse pass)
     const int grid = tc ? gmm::em_tc_grid(m->sms) : (two_phase ? m->sms : gmm::em_simt_grid(D, G, m->sms));
+    if (two_phase && cp) {   // the two-phase form makes two passes: all of X first
+        CK(cudaStreamWaitEvent(s, cp->ready.back(), 0));
+        cp = nullptr;
+    }
+    const int nch = cp ? (int)cp->ready.size() : 1;
     const int n_llp = two_phase ? (int)((N + 127) / 128) : grid;
-    CK(grow(m->partial, m->partial_cap, (size_t)grid * G * S));
+    CK(grow(m->partial, m->partial_cap, (size_t)nch * grid * G * S));
     if (two_phase) CK(grow(m->lse, m->lse_cap, (size_t)N));
     if (tc) CK(grow(m->tclist, m->tclist_cap, gmm::em_tc_list_bytes(N, grid)));
-    CK(grow(m->llp, m->llp_cap, (size_t)n_llp));
+    CK(grow(m->llp, m->llp_cap, (size_t)nch * n_llp));
     CK(grow(m->lld, m->lld_cap, (size_t)(em_iter > 0 ? em_iter : 1)));
     CK(gmm::launch_status_reset(m->status, s));
     if (em_iter == 0) return GMM_OK;
     const int base = m->cur;
     CK(gmm::launch_em_prep(D, G, m->par[base], m->op, m->center(), tc ? 1 : (m->has_center && m->center_D == D), s));
     for (int32_t k = 0; k < em_iter; ++k) {
-        gmm::EmPassArgs pa{Xd, N, D, G, m->op, m->center(), m->partial, m->llp, m->status, k,
-                           m->wait_cycles, m->skip_mma, m->profiling ? m->sstats : nullptr};
+        const int chunks = (k == 0 && cp) ? nch : 1;
         size_t slot = 0;
         gmm_status prc = prof_begin(m, s, &slot);
         if (prc != GMM_OK) return prc;
-        if (tc) CK(gmm::launch_em_pass_tc(pa, gmm::em_tc_lists(m->tclist, N, grid), grid, grid, s));
-        else if (two_phase) CK(gmm::launch_em_two_phase(pa, m->lse, grid, s));
-        else CK(gmm::launch_em_pass_simt(pa, grid, s));
+        for (int c = 0; c < chunks; ++c) {
+            const int64_t b0 = chunks > 1 ? cp->bounds[c] : 0, b1 = chunks > 1 ? cp->bounds[c + 1] : N;
+            if (chunks > 1) CK(cudaStreamWaitEvent(s, cp->ready[c], 0));
+            gmm::EmPassArgs pa{Xd + b0 * D, b1 - b0, D, G, m->op, m->center(), m->partial + (size_t)c * grid * G * S,
+                               m->llp + (size_t)c * n_llp, m->status, k, m->wait_cycles, m->skip_mma,
+                               m->profiling ? m->sstats : nullptr, N};
+            if (tc) CK(gmm::launch_em_pass_tc(pa, gmm::em_tc_lists(m->tclist, b1 - b0, grid), grid, grid, s));
+            else if (two_phase) CK(gmm::launch_em_two_phase(pa, m->lse, grid, s));
+            else CK(gmm::launch_em_pass_simt(pa, grid, s));
+        }
         if ((prc = prof_end(m, s, slot)) != GMM_OK) return prc;
-        gmm::EmFinalizeArgs fa{m->partial, m->llp, grid, n_llp, N, D, G, m->par[(base + k) & 1], m->par[(base + k + 1) & 1],
+        gmm::EmFinalizeArgs fa{m->partial, m->llp, chunks * grid, chunks * n_llp, N, D, G, m->par[(base + k) & 1], m->par[(base + k + 1) & 1],
                                var_floor, 0, m->op, m->center(), m->status, k, em_tol, m->lld,
                                tc ? 1 : (m->has_center && m->center_D == D)};
         CK(gmm::launch_em_finalize(fa, s));
@@ -398,6 +419,8 @@ void gmm_destroy(gmm_model *m)
 {
     if (!m) return;
     for (cudaEvent_t e : m->ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : m->cev) cudaEventDestroy(e);
+    if (m->cstream) cudaStreamDestroy(m->cstream);
     if (m->sstats) cudaFree(m->sstats);
     void *bufs[] = {m->par[0], m->par[1], m->op_sm, m->op_mu, m->op_c, m->op_B, m->gstat, m->fstat,
                     m->partial, m->slab, m->lse, m->llp, m->lld, m->counts, m->assign, m->xstage, m->dstage, m->idx,
@@ -477,12 +500,40 @@ gmm_status gmm_em_iterate(gmm_model *m, const float *X, int64_t N, int32_t n_ite
     if (prec < GMM_FP32 || prec > GMM_SPLIT_BF16) return fail(GMM_ERR_ARG, "bad prec");
     cudaStream_t s = as_stream(stream);
     const float *Xd = nullptr;
-    if ((rc = stage_x(m, X, N, m->D, s, &Xd)) != GMM_OK) return rc;
-    if (recompute_center || !(m->has_center && m->center_D == m->D)) {
+    const bool need_center = recompute_center || !(m->has_center && m->center_D == m->D);
+    ChunkPlan plan;
+    constexpr int kChunks = 4;
+    if (!is_device_ptr(X) && !need_center && n_iter >= 1 && N >= (int64_t)kChunks * 65536) {
+        // host X in four tile-aligned chunks on a copy stream; the first
+        // iteration's pass follows them chunk by chunk
+        const size_t D = (size_t)m->D;
+        CK(grow(m->xstage, m->xstage_cap, (size_t)N * D));
+        if (!m->cstream) CK(cudaStreamCreateWithFlags(&m->cstream, cudaStreamNonBlocking));
+        while (m->cev.size() < kChunks + 1) {
+            cudaEvent_t e;
+            CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            m->cev.push_back(e);
+        }
+        CK(cudaEventRecord(m->cev[0], s));               // earlier work on s that reads xstage
+        CK(cudaStreamWaitEvent(m->cstream, m->cev[0], 0));
+        for (int c = 0; c <= kChunks; ++c) plan.bounds.push_back(c == kChunks ? N : (N * c / kChunks) / 128 * 128);
+        for (int c = 0; c < kChunks; ++c) {
+            const int64_t b0 = plan.bounds[c], b1 = plan.bounds[c + 1];
+            CK(cudaMemcpyAsync(m->xstage + b0 * D, X + b0 * D, sizeof(float) * (size_t)(b1 - b0) * D,
+                               cudaMemcpyHostToDevice, m->cstream));
+            CK(cudaEventRecord(m->cev[1 + c], m->cstream));
+            plan.ready.push_back(m->cev[1 + c]);
+        }
+        Xd = m->xstage;   // the first pass waits for each chunk; the last wait covers every later use
+    } else if ((rc = stage_x(m, X, N, m->D, s, &Xd)) != GMM_OK) {
+        return rc;
+    }
+    if (need_center) {
         CK(gmm::launch_status_reset(m->status, s));
         if ((rc = run_global_stats(m, Xd, N, var_floor, GMM_MAHA, s)) != GMM_OK) return rc;
     }
-    if ((rc = run_em(m, Xd, N, n_iter, var_floor, 0.0, prec, 0, s)) != GMM_OK) return rc;
+    if ((rc = run_em(m, Xd, N, n_iter, var_floor, 0.0, prec, 0, s, plan.ready.empty() ? nullptr : &plan)) != GMM_OK)
+        return rc;
     return run_prep(m, s);
 }
 

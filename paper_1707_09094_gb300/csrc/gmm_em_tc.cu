@@ -1104,7 +1104,7 @@ TcLists em_tc_lists(void *base, int64_t N, int grid)
 
 cudaError_t launch_em_pass_tc(const EmPassArgs &a, const TcLists &L, int32_t grid, int32_t ms_grid, cudaStream_t s)
 {
-    const float scr = (float)std::log((double)a.N * 1e9);
+    const float scr = (float)std::log((double)(a.N_total > a.N ? a.N_total : a.N) * 1e9);
     const int al = (reinterpret_cast<uintptr_t>(a.X) & 15u) == 0;
     TcArgs t{a, L, (a.G + 15) / 16 * 16, (a.D + 15) / 16, scr, al};
     const size_t sm1 = tc_layout(a.D, t.NG).total + 1024u;

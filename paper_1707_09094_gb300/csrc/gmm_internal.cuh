@@ -50,6 +50,7 @@ struct EmPassArgs {
     long long wait_cycles;   // budget of bounded waits (tensor-core pass)
     int32_t skip_mma;        // test hook: issue no MMA
     unsigned long long *screen_stats;   // [3] screened, kept, dense (NULL = off)
+    int64_t N_total;         // samples of the whole iteration (N of one chunk when X arrives in chunks)
 };
 
 struct EmFinalizeArgs {

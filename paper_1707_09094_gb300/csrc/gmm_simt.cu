@@ -670,7 +670,7 @@ __global__ void __launch_bounds__(kEmThreads, 1) k_em_pass_simt(EmPassArgs a)
     // responsibilities below 1e-9 / N (the tensor-core form's rule) carry less
     // than 1e-9 per Gaussian in total: a Gaussian none of whose tile
     // responsibilities reaches it is left out of the tile's M-step
-    const float keep = (float)(1e-9 / (double)a.N);
+    const float keep = (float)(1e-9 / (double)(a.N_total > a.N ? a.N_total : a.N));
 
     for (int k = tid; k < G; k += kEmThreads) S0[k] = 0.f;
     for (int k = tid; k < G * D; k += kEmThreads) { S1[k] = 0.f; S2[k] = 0.f; }

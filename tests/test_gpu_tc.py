@@ -172,3 +172,24 @@ def test_tc_and_fp32_converge_alike_under_em_tol():
         b = GMM().learn(Xd, G, km_iter=10, em_iter=250, em_tol=1e-6, seed=5, prec="bf16")
         assert abs(len(a.ll_history()) - len(b.ll_history())) <= 3   # the stop test sees LL gains near em_tol
         assert abs(a.avg_log_p(Xd) - b.avg_log_p(Xd)) < 1e-5
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_host_input_in_chunks_matches_device_input(prec):
+    """Host X of >= 262,144 samples reaches the GPU in four chunks whose copies
+    overlap the first EM iteration's pass; the result equals the device-input
+    run up to FP32 addition order, over several iterations."""
+    X, _, _ = synth.make("c1", N=300_001, seed=41)
+    Xd = dev(X)
+    start = GMM().learn(Xd, 8, km_iter=3, em_iter=0, seed=2).get_params()
+    a = GMM().set_params(*start)
+    a.em_iterate(Xd, 0, recompute_center=True)
+    a.em_iterate(Xd, 3, prec=prec)
+    b = GMM().set_params(*start)
+    b.em_iterate(Xd, 0, recompute_center=True)
+    Xh = torch.from_numpy(X).pin_memory()
+    b.em_iterate(Xh, 3, prec=prec)
+    b.em_iterate(X, 2, prec=prec)            # pageable host memory too
+    a.em_iterate(Xd, 2, prec=prec)
+    np.testing.assert_allclose(b.ll_history(), a.ll_history(), rtol=1e-7)
+    assert_params(b.get_params(), a.get_params(), X, rtol=1e-6)
