@@ -420,10 +420,12 @@ struct ExSmem {
     uint32_t psm, pc, X[2], cand[2], cnt[2], wl, wg, ws, bars, misc, total;
 };
 
-// The operands (s = 1/sigma, mu s) are one [G][DS] float2 array with an odd
-// row stride DS, so lanes reading different Gaussians at one d spread over
-// the banks.
-__host__ __device__ inline int ex_stride(int D) { return D | 1; }
+// The operands (s = 1/sigma, mu s) are one [G][DS] float2 array whose row
+// stride DS is the smallest value >= D with DS = 2 (mod 4): rows start on
+// 16-byte boundaries (two dimensions per 128-bit load) and DS/2 is odd, so
+// the eight lanes of one 128-bit load phase that read different Gaussians at
+// one d hit different banks.
+__host__ __device__ inline int ex_stride(int D) { return D + ((6 - (D & 3)) & 3); }
 
 __host__ __device__ inline ExSmem ex_layout(int D, int G, int wp)
 {
@@ -588,7 +590,20 @@ __global__ void __launch_bounds__(kExThreads, 1) k_em_exact(ExArgs args)
                 const float *xr = xs + si * D;
                 const float2 *q = psm + g * DS;
                 float r0 = 0.f, r1 = 0.f;
-                if ((D & 1) == 0) {   // the row is 8-byte aligned: two dimensions per load
+                if ((D & 3) == 0) {   // 16-byte aligned rows: four dimensions per three 128-bit loads
+                    const float4 *x4 = reinterpret_cast<const float4 *>(xr);
+                    const float4 *q4 = reinterpret_cast<const float4 *>(q);
+#pragma unroll 3
+                    for (int d4 = 0; d4 < D / 4; ++d4) {
+                        const float4 xv = x4[d4], qa = q4[2 * d4], qb = q4[2 * d4 + 1];
+                        const float ta = fmaf(xv.x, qa.x, -qa.y), tb = fmaf(xv.y, qa.z, -qa.w);
+                        const float tc = fmaf(xv.z, qb.x, -qb.y), td = fmaf(xv.w, qb.z, -qb.w);
+                        r0 = fmaf(ta, ta, r0);
+                        r1 = fmaf(tb, tb, r1);
+                        r0 = fmaf(tc, tc, r0);
+                        r1 = fmaf(td, td, r1);
+                    }
+                } else if ((D & 1) == 0) {   // 8-byte aligned rows: two dimensions per load
                     const float2 *x2 = reinterpret_cast<const float2 *>(xr);
 #pragma unroll 4
                     for (int d2 = 0; d2 < D / 2; ++d2) {
