@@ -647,6 +647,25 @@ cudaError_t gemm(const __nv_bfloat16 *A, const __nv_bfloat16 *B, float *C, int M
     return cudaGetLastError();
 }
 
+#define CKE_(x)                                      \
+    do {                                             \
+        cudaError_t e_ = (x);                        \
+        if (e_ != cudaSuccess) return e_;            \
+    } while (0)
+
+// C[M][N] (row stride N) = op(A) op(B)^T for the head layers (M = sets, a few
+// dozen rows): split along K until the grid fills the GPU; the split parts
+// are added with atomics onto the zeroed C.
+cudaError_t gemm_small(const __nv_bfloat16 *A, const __nv_bfloat16 *B, float *C, int M, int N, int K, int lda, int ldb,
+                       int tA, int tB, cudaStream_t s)
+{
+    const int tiles = ((N + kBN - 1) / kBN) * ((M + kBM - 1) / kBM);
+    const int splits = std::max(1, std::min((K + kBK * 4 - 1) / (kBK * 4), (304 + tiles - 1) / tiles));
+    if (splits == 1) return gemm(A, B, C, M, N, K, lda, ldb, N, tA, tB, 1, 0, s);
+    CKE_(cudaMemsetAsync(C, 0, sizeof(float) * (size_t)M * N, s));
+    return gemm(A, B, C, M, N, K, lda, ldb, N, tA, tB, splits, 1, s);
+}
+
 bool tc_usable(const void *A, const void *B, int K, int lda, int ldb)
 {
     return ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15u) == 0 && K % 8 == 0 &&
@@ -719,13 +738,13 @@ cudaError_t net_forward(InitNet &n, const float *pts, int B, int P, Ws &w, cudaS
     int hin = n.Hp;
     for (int l = 0; l < n.Lh; ++l) {
         const int li = n.Lp + l;
-        CKE(gemm(w.a[l], n.wbf + n.w_off[li], w.z, B, n.Hh, hin, hin, hin, n.Hh, 0, 0, 1, 0, s));
+        CKE(gemm_small(w.a[l], n.wbf + n.w_off[li], w.z, B, n.Hh, hin, hin, hin, 0, 0, s));
         k_bias_act<<<blocks_for((int64_t)B * n.Hh, 256), 256, 0, s>>>(w.z, n.wgt + n.b_off[li], w.a[l + 1], nullptr, B,
                                                                        n.Hh, 1);
         hin = n.Hh;
     }
     const int lo = n.Lp + n.Lh;
-    CKE(gemm(w.a[n.Lh], n.wbf + n.w_off[lo], w.z, B, n.O, hin, hin, hin, n.O, 0, 0, 1, 0, s));
+    CKE(gemm_small(w.a[n.Lh], n.wbf + n.w_off[lo], w.z, B, n.O, hin, hin, hin, 0, 0, s));
     // the BF16 copy of the output is not needed: write it to the free dz buffer
     k_bias_act<<<blocks_for((int64_t)B * n.O, 256), 256, 0, s>>>(w.z, n.wgt + n.b_off[lo], w.dz, w.out, B, n.O, 0);
     count_launches(3 + n.Lp + n.Lh);
@@ -744,14 +763,14 @@ cudaError_t net_backward(InitNet &n, int B, int P, Ws &w, cudaStream_t s)
     k_to_bf16<<<blocks_for((int64_t)B * n.O, 256), 256, 0, s>>>(w.dout, w.dz, (int64_t)B * n.O);
     CKE(gemm(w.dz, w.a[n.Lh], n.grad + n.w_off[lo], n.O, hin, B, n.O, hin, hin, 1, 1, 1, 1, s));
     k_colsum<<<dim3((n.O + 31) / 32, 1), 256, 0, s>>>(w.dz, n.grad + n.b_off[lo], B, n.O);
-    CKE(gemm(w.dz, n.wbf + n.w_off[lo], w.dh, B, hin, n.O, n.O, hin, hin, 0, 1, 1, 0, s));
+    CKE(gemm_small(w.dz, n.wbf + n.w_off[lo], w.dh, B, hin, n.O, n.O, hin, 0, 1, s));
     for (int l = n.Lh - 1; l >= 0; --l) {
         const int li = n.Lp + l;
         const int lin = l == 0 ? n.Hp : n.Hh;
         k_relu_bwd<<<blocks_for((int64_t)B * n.Hh, 256), 256, 0, s>>>(w.dh, w.a[l + 1], w.dz, B, n.Hh, 0);
         CKE(gemm(w.dz, w.a[l], n.grad + n.w_off[li], n.Hh, lin, B, n.Hh, lin, lin, 1, 1, 1, 1, s));
         k_colsum<<<dim3((n.Hh + 31) / 32, 1), 256, 0, s>>>(w.dz, n.grad + n.b_off[li], B, n.Hh);
-        CKE(gemm(w.dz, n.wbf + n.w_off[li], w.dh, B, lin, n.Hh, n.Hh, lin, lin, 0, 1, 1, 0, s));
+        CKE(gemm_small(w.dz, n.wbf + n.w_off[li], w.dh, B, lin, n.Hh, n.Hh, lin, 0, 1, s));
     }
     // w.dh now holds d(pooled) [B][Hp]; per-point layers.  cur = dLoss/dZ_l in BF16.
     __nv_bfloat16 *cur = w.dz, *nxt = w.dz2;
