@@ -486,25 +486,33 @@ __global__ void __launch_bounds__(256) k_loss_grad(const float *__restrict__ lp,
         d[G + G * D + k] = -0.5f * (S2[k] * iv[k] - S0[k / D]) * er[k] * iv[k] * invP * invB;
     }
     __syncthreads();
-    // pull of the predicted means toward the plain method's fit (nearest pairs)
+    // pull of the predicted means toward the plain method's fit (nearest pairs);
+    // the set's targets go to shared memory once (means, inverse variances)
     float pull = 0.f;
     if (lambda > 0.0 && tgt_m) {
+        extern __shared__ float tsm[];   // [G][D] target means, [G][D] 1 / target variances
+        float *tmf = tsm, *tif = tsm + G * D;
+        for (int k = threadIdx.x; k < G * D; k += blockDim.x) {
+            tmf[k] = (float)tgt_m[(size_t)b * G * D + k];
+            tif[k] = 1.f / (float)tgt_v[(size_t)b * G * D + k];
+        }
+        __syncthreads();
         for (int k = threadIdx.x; k < G; k += blockDim.x) {
-            const double *tm = tgt_m + ((size_t)b * G + k) * D, *tv = tgt_v + ((size_t)b * G + k) * D;
+            const float *tm = tmf + k * D, *ti = tif + k * D;
             float best = INFINITY;
             int bg = 0;
             for (int g = 0; g < G; ++g) {
                 float q = 0.f;
                 for (int dd = 0; dd < D; ++dd) {
-                    const float t = m[g * D + dd] - (float)tm[dd];
-                    q = fmaf(t * t, 1.f / (float)tv[dd], q);
+                    const float t = m[g * D + dd] - tm[dd];
+                    q = fmaf(t * t, ti[dd], q);
                 }
                 if (q < best) { best = q; bg = g; }
             }
             const float wk = (float)tgt_w[(size_t)b * G + k] * (float)lambda;
             pull += wk * best;
             for (int dd = 0; dd < D; ++dd)
-                atomicAdd(&d[G + bg * D + dd], 2.f * wk * (m[bg * D + dd] - (float)tm[dd]) / (float)tv[dd] * invB);
+                atomicAdd(&d[G + bg * D + dd], 2.f * wk * (m[bg * D + dd] - tm[dd]) * ti[dd] * invB);
         }
     }
     pull = bsum_f(pull, sh);
@@ -932,8 +940,10 @@ cudaError_t init_net_run(InitNet *n, const float *pts, int B, int P, const doubl
                                        (size_t)kLossPts * (n->G + 1) + kLossPts);
     CKE(cudaFuncSetAttribute(k_loss_chunk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     k_loss_chunk<<<dim3(B, (P + kLossPts - 1) / kLossPts), kLossPts, sm, s>>>(pts, P, n->D, n->G, w.lpar, w.lst, w.lnll);
-    k_loss_grad<<<B, 256, 0, s>>>(w.lpar, w.lst, w.lnll, P, n->D, n->G, var_floor, tm, tv, tw, lambda, w.dout, w.loss,
-                                  pm, pv, pw, B);
+    const size_t smg = sizeof(float) * 2 * (size_t)n->G * n->D;
+    if (smg > 48 * 1024) CKE(cudaFuncSetAttribute(k_loss_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smg));
+    k_loss_grad<<<B, 256, smg, s>>>(w.lpar, w.lst, w.lnll, P, n->D, n->G, var_floor, tm, tv, tw, lambda, w.dout, w.loss,
+                                    pm, pv, pw, B);
     count_launches(3);
     CKE(cudaGetLastError());
     if (grads) CKE(net_backward(*n, B, P, w, s));
