@@ -263,17 +263,25 @@ def run_ours(args):
         return {"ms": ms, "wall_s": wall, "pass_ms": pass_ms, "pass_n": pass_n, "launches": launches,
                 "clocks": cs.summary(), **extra}
 
-    # k-means (Sec. 3) pass throughput and one whole learn(), reported beside the EM metric
-    km = GMM().set_params(*start)
-    km.kmeans(Xd, 1, return_assign=False)
-    km.set_params(*start)
-    km.profile(True)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    km.kmeans(Xd, 5, return_assign=False)
-    torch.cuda.synchronize()
-    km_wall = time.perf_counter() - t0
-    km_ms, km_n, _ = km.profile_read()
+    # k-means (Sec. 3) pass throughput, both forms, and one whole learn(), reported beside the EM metric
+    from paper_1707_09094_gb300._lib import GMM_DEBUG_KM_FORM
+
+    def km_time(form):
+        km = GMM().set_params(*start)
+        km.debug_set(GMM_DEBUG_KM_FORM, form)
+        km.kmeans(Xd, 1, return_assign=False)
+        km.set_params(*start)
+        km.profile(True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        km.kmeans(Xd, 5, return_assign=False)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        ms, n, _ = km.profile_read()
+        return ms / max(n, 1), wall * 1e3 / 5, km.km_screen_stats()
+
+    km_tc = km_time(0)
+    km_cc = km_time(1)
     learn_t = []
     for _ in range(2):
         torch.cuda.synchronize()
@@ -326,7 +334,7 @@ def run_ours(args):
         "clocks": r["clocks"],
         "e2e": {"value": world * units / (e2e["ms"] / args.steps * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": int(X.nbytes), "d2h_bytes_per_step": 8 + 32},
-        "kmeans": kmeans_line(km_ms / max(km_n, 1), km_wall * 1e3 / 5, units, peaks, peak_src),
+        "kmeans": kmeans_line(km_tc, km_cc, units, N * (D + 1) * 4, peaks, peak_src),
         "learn_10km_10em_s": min(learn_t),
         "forms": {p: {"value": world * units / (results[p]["ms"] / args.steps * 1e-3),
                       "ms_per_step": results[p]["ms"] / args.steps,
@@ -385,15 +393,29 @@ def run_table1_leg(em_tol=1e-6, max_iter=250):
     return {"em_tol": em_tol, "max_em_iter": max_iter, "runs": rows}
 
 
-def kmeans_line(pass_ms, wall_ms, units, peaks, peak_src):
-    """k-means map pass: 1 FMA per (i, g, d) (the expanded score), FP32 FMA-bound."""
-    peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-    achieved = 2.0 * units / (pass_ms * 1e-3) / 1e12
-    return {"pass_ms": pass_ms, "units_per_s": units / (pass_ms * 1e-3), "iterations_wall_ms": wall_ms,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak,
-                         "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (%s clock)" %
-                                        (peaks.get("sm_max_mhz", 2070.0), peak_src)}}
+def kmeans_line(tc, cc, units, bytes_alg, peaks, peak_src):
+    """k-means map pass (operands, assignment, sorted statistics), per form.
+    Algorithmic work: 1 MAC per (i, g, d) (the expanded score x.mu) and the
+    bytes X once + one assignment per sample.  The tensor-core form issues 3
+    BF16 MMAs per MAC (split operands); the CUDA-core form 1 FP32 FMA."""
+    (tc_ms, tc_wall, (scr, dfr, f64)), (cc_ms, cc_wall, _) = tc, cc
+    tens = peaks["bf16_tflops"]
+    alu = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    return {"form": "tensor cores: split-BF16 screen, exact FP32/FP64 decision of the rest",
+            "pass_ms": tc_ms, "units_per_s": units / (tc_ms * 1e-3), "iterations_wall_ms": tc_wall,
+            "deferred_per_sample": dfr / max(scr, 1), "fp64_per_sample": f64 / max(scr, 1),
+            "roofline": {"bound": "tensor", "achieved": 2.0 * units / (tc_ms * 1e-3) / 1e12, "peak": tens,
+                         "unit": "TFLOP/s", "frac": 2.0 * units / (tc_ms * 1e-3) / 1e12 / tens,
+                         "peak_source": "bf16_tflops (%s); algorithmic 2 flop per (i, g, d)" % peak_src},
+            "hbm": {"achieved": bytes_alg / (tc_ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": bytes_alg / (tc_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                    "note": "algorithmic bytes: X once + one int32 assignment per sample"},
+            "cuda_core_form": {"pass_ms": cc_ms, "iterations_wall_ms": cc_wall,
+                               "roofline": {"bound": "alu", "achieved": 2.0 * units / (cc_ms * 1e-3) / 1e12,
+                                            "peak": alu, "unit": "TFLOP/s",
+                                            "frac": 2.0 * units / (cc_ms * 1e-3) / 1e12 / alu,
+                                            "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz"
+                                                           % peaks.get("sm_max_mhz", 2070.0)}}}
 
 
 def run_batched_leg():

@@ -332,6 +332,11 @@ gmm_status gmm_profile_read(const gmm_model *m, double *pass_ms, int64_t *pass_l
  * Used by the test-suite only. */
 #define GMM_DEBUG_WAIT_CYCLES 1
 #define GMM_DEBUG_SKIP_MMA 2
+/*   GMM_DEBUG_KM_FORM      0 (default): k-means assigns on the tensor cores
+ *                          where D <= 64 and N_G <= 256 (same assignments:
+ *                          both forms decide the nearest mean exactly);
+ *                          1: on the CUDA cores. */
+#define GMM_DEBUG_KM_FORM 3
 gmm_status gmm_debug_set(gmm_model *m, int32_t key, int64_t value);
 
 /* Screening counters of the tensor-core pass, summed since the last
@@ -347,6 +352,13 @@ gmm_status gmm_debug_set(gmm_model *m, int32_t key, int64_t value);
  * tile's BF16 operand, 1 barrier, 2 MMA wait, 3 screening bounds, 4 candidate
  * lists and their records; 5-7 unused), summed over CTAs. */
 #define GMM_STAT_PHASE0 6
+/* Tensor-core k-means, summed over its passes: GMM_STAT_KM_SCREENED samples
+ * screened, GMM_STAT_KM_DEFERRED samples the screen left with more than one
+ * candidate (decided by exact FP32 distances), GMM_STAT_KM_FP64 samples
+ * re-decided in FP64. */
+#define GMM_STAT_KM_SCREENED 14
+#define GMM_STAT_KM_DEFERRED 15
+#define GMM_STAT_KM_FP64 16
 gmm_status gmm_debug_get(const gmm_model *m, int32_t key, int64_t *value);
 
 /* Thread-local text of the last error ("" if none). */

@@ -223,7 +223,7 @@ class GMM:
         return ms.value, n.value, k.value
 
     def debug_set(self, key, value):
-        """Failure-detection test hooks (GMM_DEBUG_WAIT_CYCLES, GMM_DEBUG_SKIP_MMA)."""
+        """Test hooks (GMM_DEBUG_WAIT_CYCLES, GMM_DEBUG_SKIP_MMA, GMM_DEBUG_KM_FORM)."""
         _lib.check(_lib.load().gmm_debug_set(self._h, key, int(value)), "gmm_debug_set")
         return self
 
@@ -231,6 +231,16 @@ class GMM:
         """(samples screened, candidates kept, dense fallbacks) of the tensor-core pass since profile()."""
         out = []
         for k in (_lib.GMM_STAT_SCREENED, _lib.GMM_STAT_KEPT, _lib.GMM_STAT_DENSE):
+            v = ctypes.c_int64()
+            _lib.check(_lib.load().gmm_debug_get(self._h, k, ctypes.byref(v)), "gmm_debug_get")
+            out.append(v.value)
+        return tuple(out)
+
+    def km_screen_stats(self):
+        """(samples screened, deferred to the exact FP32 decision, re-decided in FP64) of the
+        tensor-core k-means since profile()."""
+        out = []
+        for k in (_lib.GMM_STAT_KM_SCREENED, _lib.GMM_STAT_KM_DEFERRED, _lib.GMM_STAT_KM_FP64):
             v = ctypes.c_int64()
             _lib.check(_lib.load().gmm_debug_get(self._h, k, ctypes.byref(v)), "gmm_debug_get")
             out.append(v.value)

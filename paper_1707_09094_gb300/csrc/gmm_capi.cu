@@ -22,6 +22,11 @@ using gmm::Operands;
 
 namespace {
 
+// Device counters of gmm_profile: words 0-10 the EM screening kernel's,
+// words 11-13 the tensor-core k-means pass's (screened, deferred, FP64).
+constexpr int kStatWords = 14;
+constexpr int kStatKm = 11;
+
 thread_local std::string g_err;
 
 gmm_status fail(gmm_status st, const char *fmt, ...)
@@ -123,6 +128,7 @@ struct gmm_model {
     double *partial = nullptr; size_t partial_cap = 0;
     float *slab = nullptr; size_t slab_cap = 0;
     unsigned char *tclist = nullptr; size_t tclist_cap = 0;   // tensor-core pass: per-sample records
+    unsigned char *kmop = nullptr; size_t kmop_cap = 0;       // tensor-core k-means operands
     double *spread = nullptr; size_t spread_cap = 0;          // spread seeding: distances + block partials
     cudaStream_t cstream = nullptr;                           // host-input copies that overlap the first pass
     std::vector<cudaEvent_t> cev;                             // [0] start, [1..] chunk copies
@@ -147,7 +153,8 @@ struct gmm_model {
     // failure-detection test hooks
     long long wait_cycles = 2000000000LL;
     int skip_mma = 0;
-    unsigned long long *sstats = nullptr;   // screening counters (device, [3])
+    int km_form = 0;                        // 0: tensor cores where supported, 1: CUDA cores
+    unsigned long long *sstats = nullptr;   // screening counters (device, [kStatWords])
 
     double *means() const { return par[cur]; }
     double *gmean() const { return gstat; }
@@ -259,9 +266,16 @@ gmm_status run_kmeans(gmm_model *m, const float *Xd, int64_t N, int32_t km_iter,
                       cudaStream_t s)
 {
     const int32_t D = m->D, G = m->G, S = 1 + 2 * D;
-    const int grid = gmm::km_grid(D, G, m->sms);
+    const bool tc = m->km_form == 0 && m->has_center && m->center_D == D && gmm::km_tc_supported(D, G);
+    const int grid = tc ? m->sms : gmm::km_grid(D, G, m->sms);
     CK(grow(m->partial, m->partial_cap, (size_t)grid * G * S));
-    CK(grow(m->slab, m->slab_cap, gmm::km_slab_floats(D, G, grid)));
+    if (tc) {
+        CK(grow(m->tclist, m->tclist_cap, gmm::em_tc_list_bytes(N, grid)));
+        CK(grow(m->kmop, m->kmop_cap, gmm::km_tc_ops_bytes(D, G)));
+        m->ops_valid = false;   // the pass writes the FP32 means into the E-step operands
+    } else {
+        CK(grow(m->slab, m->slab_cap, gmm::km_slab_floats(D, G, grid)));
+    }
     CK(grow(m->assign, m->assign_cap, (size_t)N));
     CK(grow(m->counts, m->counts_cap, (size_t)G));
     for (int32_t it = 0; it < km_iter; ++it) {
@@ -269,8 +283,14 @@ gmm_status run_kmeans(gmm_model *m, const float *Xd, int64_t N, int32_t km_iter,
         size_t slot = 0;
         gmm_status prc = prof_begin(m, s, &slot);
         if (prc != GMM_OK) return prc;
-        CK(gmm::launch_km_pass(Xd, N, D, G, m->par[m->cur], m->wdist(), m->sw(), m->slab, m->partial, grid,
-                               m->assign, m->status, s));
+        if (tc)
+            CK(gmm::launch_km_pass_tc(Xd, N, D, G, m->par[m->cur], m->wdist(), m->sw(), m->center(),
+                                      gmm::km_tc_ops(m->kmop, D, G), m->op, m->partial, grid, m->assign,
+                                      gmm::em_tc_lists(m->tclist, N, grid), m->status, m->wait_cycles,
+                                      m->profiling ? m->sstats + kStatKm : nullptr, s));
+        else
+            CK(gmm::launch_km_pass(Xd, N, D, G, m->par[m->cur], m->wdist(), m->sw(), m->slab, m->partial, grid,
+                                   m->assign, m->status, s));
         if ((prc = prof_end(m, s, slot)) != GMM_OK) return prc;
         CK(gmm::launch_km_finalize(m->partial, np, N, D, G, m->par[m->cur], var_floor, it == km_iter - 1,
                                    m->counts, Xd, m->assign, m->gvar(), m->status, s));
@@ -424,7 +444,7 @@ void gmm_destroy(gmm_model *m)
     if (m->sstats) cudaFree(m->sstats);
     void *bufs[] = {m->par[0], m->par[1], m->op_sm, m->op_mu, m->op_c, m->op_B, m->gstat, m->fstat,
                     m->partial, m->slab, m->lse, m->llp, m->lld, m->counts, m->assign, m->xstage, m->dstage, m->idx,
-                    m->hist, m->status, m->tclist, m->spread};
+                    m->hist, m->status, m->tclist, m->kmop, m->spread};
     for (void *p : bufs)
         if (p) cudaFree(p);
     delete m;
@@ -793,8 +813,8 @@ gmm_status gmm_profile(gmm_model *m, int32_t enable)
 {
     if (!m) return fail(GMM_ERR_ARG, "model is NULL");
     m->profiling = enable != 0;
-    if (!m->sstats) CK(cudaMalloc(&m->sstats, 11 * sizeof(unsigned long long)));
-    CK(cudaMemset(m->sstats, 0, 11 * sizeof(unsigned long long)));
+    if (!m->sstats) CK(cudaMalloc(&m->sstats, kStatWords * sizeof(unsigned long long)));
+    CK(cudaMemset(m->sstats, 0, kStatWords * sizeof(unsigned long long)));
     m->ev_used = 0;
     m->pass_ms = 0.0;
     m->pass_launches = 0;
@@ -819,6 +839,9 @@ gmm_status gmm_debug_set(gmm_model *m, int32_t key, int64_t value)
         m->wait_cycles = value > 0 ? (long long)value : 2000000000LL;
     } else if (key == GMM_DEBUG_SKIP_MMA) {
         m->skip_mma = value != 0;
+    } else if (key == GMM_DEBUG_KM_FORM) {
+        if (value < 0 || value > 1) return fail(GMM_ERR_ARG, "k-means form must be 0 or 1");
+        m->km_form = (int)value;
     } else {
         return fail(GMM_ERR_ARG, "unknown debug key %d", key);
     }
@@ -828,8 +851,8 @@ gmm_status gmm_debug_set(gmm_model *m, int32_t key, int64_t value)
 gmm_status gmm_debug_get(const gmm_model *m, int32_t key, int64_t *value)
 {
     if (!m || !value) return fail(GMM_ERR_ARG, "NULL argument");
-    if (key < GMM_STAT_SCREENED || key > GMM_STAT_PHASE0 + 7) return fail(GMM_ERR_ARG, "unknown key %d", key);
-    unsigned long long v[11] = {0};
+    if (key < GMM_STAT_SCREENED || key >= GMM_STAT_SCREENED + kStatWords) return fail(GMM_ERR_ARG, "unknown key %d", key);
+    unsigned long long v[kStatWords] = {0};
     if (m->sstats) CK(cudaMemcpy(v, m->sstats, sizeof v, cudaMemcpyDeviceToHost));
     *value = (int64_t)v[key - GMM_STAT_SCREENED];
     return GMM_OK;

@@ -1097,7 +1097,7 @@ size_t em_tc_list_bytes(int64_t N, int grid)
 {
     const size_t n = (size_t)N, sp = (size_t)grid * kTcSpill;
     return al256(4u * n * kTcKeep) + al256(n * kTcKeep) + al256(32u * n) + al256(4u * n) + al256(2u * n) +
-           al256(n) + al256(8u * sp) + al256(4u * sp) + al256(4u * (size_t)grid) + 256u;
+           al256(n) + al256(8u * sp) + al256(4u * sp) + al256(4u * (size_t)grid) + al256(4u * n) + 256u;
 }
 
 TcLists em_tc_lists(void *base, int64_t N, int grid)
@@ -1113,7 +1113,8 @@ TcLists em_tc_lists(void *base, int64_t N, int grid)
     L.km = p;                                   p += al256(n);
     L.sp_ig = reinterpret_cast<int64_t *>(p);   p += al256(8u * sp);
     L.sp_gam = reinterpret_cast<float *>(p);    p += al256(4u * sp);
-    L.sp_n = reinterpret_cast<int32_t *>(p);
+    L.sp_n = reinterpret_cast<int32_t *>(p);    p += al256(4u * (size_t)grid);
+    L.defer = reinterpret_cast<int32_t *>(p);
     return L;
 }
 
@@ -1139,6 +1140,18 @@ cudaError_t launch_em_pass_tc(const EmPassArgs &a, const TcLists &L, int32_t gri
         return e;
     k_em_mstep_lists<<<ms_grid, kMsThreads, sm3, s>>>(x);
     count_launches(3);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mstep_records(const EmPassArgs &a, const TcLists &L, int32_t grid, cudaStream_t s)
+{
+    const int al = (reinterpret_cast<uintptr_t>(a.X) & 15u) == 0;
+    ExArgs x{a, L, 0.f, al, 0};
+    const size_t sm3 = ms_layout(a.D, a.G).total;
+    cudaError_t e = cudaFuncSetAttribute(k_em_mstep_lists, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3);
+    if (e != cudaSuccess) return e;
+    k_em_mstep_lists<<<grid, kMsThreads, sm3, s>>>(x);
+    count_launches(1);
     return cudaGetLastError();
 }
 

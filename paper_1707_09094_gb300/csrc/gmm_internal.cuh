@@ -193,8 +193,29 @@ struct TcLists {             // per-sample records between the three kernels of 
     int64_t *sp_ig;          // [grid][kTcSpill] kept pairs beyond kTcKeep: sample * 256 + Gaussian
     float *sp_gam;           //                  and their responsibilities (0: unused entry)
     int32_t *sp_n;           // [grid] entries of each CTA's spill list
+    int32_t *defer;          // [N] k-means: samples left to the exact decision (CTA b's in its own sample range)
 };
 constexpr int kTcSpill = 16384;   // spill entries per CTA
+
+// Tensor-core k-means operands, rebuilt from the FP64 means every iteration.
+struct KmTcOps {
+    __nv_bfloat16 *B;        // [G][128] c' = (mu - m) sqrt(w) split as BF16 hi (0..63) | lo (64..127)
+    float *cn;               // [G] |c'|^2
+    float *cs;               // [G][D] mu sqrt(w) (FP32, uncentred: the exact FP32 distance)
+    float *ncs;              // [G] |mu sqrt(w)|^2
+};
+bool km_tc_supported(int32_t D, int32_t G);
+size_t km_tc_ops_bytes(int32_t D, int32_t G);
+KmTcOps km_tc_ops(void *base, int32_t D, int32_t G);
+// One k-means iteration's map step on the tensor cores: operands, assignment
+// (assign[N] and one-pair records in L), sorted statistics into partial
+// [grid][G][1 + 2D] (shifted by the FP32 means written to mu_f).
+cudaError_t launch_km_pass_tc(const float *X, int64_t N, int32_t D, int32_t G, const double *means,
+                              const double *w, const float *sw, const float *center, KmTcOps o, Operands op,
+                              double *partial, int32_t grid, int32_t *assign, const TcLists &L, DevStatus *status,
+                              long long wait_cycles, unsigned long long *stats, cudaStream_t s);
+// The sorted M-step kernel of the tensor-core EM pass on records already in L.
+cudaError_t launch_mstep_records(const EmPassArgs &a, const TcLists &L, int32_t grid, cudaStream_t s);
 bool em_tc_supported(int32_t D, int32_t G);
 int em_tc_grid(int sms);
 size_t em_tc_list_bytes(int64_t N, int grid);
