@@ -1143,16 +1143,4 @@ cudaError_t launch_em_pass_tc(const EmPassArgs &a, const TcLists &L, int32_t gri
     return cudaGetLastError();
 }
 
-cudaError_t launch_mstep_records(const EmPassArgs &a, const TcLists &L, int32_t grid, cudaStream_t s)
-{
-    const int al = (reinterpret_cast<uintptr_t>(a.X) & 15u) == 0;
-    ExArgs x{a, L, 0.f, al, 0};
-    const size_t sm3 = ms_layout(a.D, a.G).total;
-    cudaError_t e = cudaFuncSetAttribute(k_em_mstep_lists, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3);
-    if (e != cudaSuccess) return e;
-    k_em_mstep_lists<<<grid, kMsThreads, sm3, s>>>(x);
-    count_launches(1);
-    return cudaGetLastError();
-}
-
 }  // namespace gmm

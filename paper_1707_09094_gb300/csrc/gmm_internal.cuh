@@ -208,14 +208,13 @@ bool km_tc_supported(int32_t D, int32_t G);
 size_t km_tc_ops_bytes(int32_t D, int32_t G);
 KmTcOps km_tc_ops(void *base, int32_t D, int32_t G);
 // One k-means iteration's map step on the tensor cores: operands, assignment
-// (assign[N] and one-pair records in L), sorted statistics into partial
-// [grid][G][1 + 2D] (shifted by the FP32 means written to mu_f).
+// (assign[N]; L holds the screen's candidate lists), statistics into partial
+// [grid][G][1 + 2D] (shifted by the FP32 means written to op.mu).
 cudaError_t launch_km_pass_tc(const float *X, int64_t N, int32_t D, int32_t G, const double *means,
                               const double *w, const float *sw, const float *center, KmTcOps o, Operands op,
                               double *partial, int32_t grid, int32_t *assign, const TcLists &L, DevStatus *status,
                               long long wait_cycles, unsigned long long *stats, cudaStream_t s);
-// The sorted M-step kernel of the tensor-core EM pass on records already in L.
-cudaError_t launch_mstep_records(const EmPassArgs &a, const TcLists &L, int32_t grid, cudaStream_t s);
+
 bool em_tc_supported(int32_t D, int32_t G);
 int em_tc_grid(int sms);
 size_t em_tc_list_bytes(int64_t N, int grid);

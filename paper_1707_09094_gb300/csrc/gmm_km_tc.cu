@@ -35,10 +35,9 @@
 //     win are re-decided in FP64 in the definition's own operation order
 //     (lowest index on exact ties); more than 32 candidates, or none (a
 //     non-finite sample), re-decide every mean in FP64.
-// The assignment goes to assign[i] and, as a one-pair record
-// (responsibility 1), to the sorted M-step kernel of the tensor-core EM
-// pass, which sums count, sum(x - mu_f), sum((x - mu_f)^2) per mean into the
-// CTA's FP64 partial: the statistics of Eqs. 5-7.
+//  4. k_km_stats -- from the assignment, count, sum(x - mu_f) and
+//     sum((x - mu_f)^2) per mean into each CTA's FP64 partial: the sums of
+//     Eqs. 5-7.
 #include <cuda_bf16.h>
 
 #include <climits>
@@ -300,13 +299,7 @@ __global__ void __launch_bounds__(kThr, 1) k_km_screen_tc(KmTcArgs a)
             if (lane == 0) xnb[r] = make_float2(sqrtf(ss), ss);
         }
     };
-    // the decided mean of sample i: assign[] and its one-pair record
-    auto put = [&](int64_t i, int g) {
-        a.assign[i] = g;
-        L.kg[i * kTcKeep] = (uint8_t)g;
-        L.gam[i * kTcKeep] = 1.f;
-        L.km[i] = 1;
-    };
+    auto put = [&](int64_t i, int g) { a.assign[i] = g; };
 
     if (tid == 0) {
         for (int k = 0; k < 9; ++k) mbar_init(bar_afull + k, 1);
@@ -600,7 +593,6 @@ __global__ void __launch_bounds__(kThr, 1) k_km_screen_tc(KmTcArgs a)
                 while (!mbar_try_wait(bar_x + bb, u & 1u) && clock64() - d0 < budget) {
                 }
         }
-        L.sp_n[blockIdx.x] = 0;   // no spilled pairs: one pair per sample
         if (a.stats) {
             atomicAdd(a.stats + 1, (unsigned long long)*namb);
             atomicAdd(a.stats + 2, (unsigned long long)*n64);
@@ -616,6 +608,178 @@ __global__ void __launch_bounds__(kThr, 1) k_km_screen_tc(KmTcArgs a)
     }
 }
 
+// ------------------------------------------------------------------------
+// 4. Statistics of the assignment: count, sum(x - mu_f), sum((x - mu_f)^2)
+// per mean (the sums of Eqs. 5-7, shifted by the FP32 mean mu_f of the
+// iteration start).  One CTA per SM over a contiguous run of 128-sample
+// tiles, staged (samples and assignments) by bulk copies kStBufs tiles
+// ahead; the shifts in shared memory.  Warp w owns the means g = w + 32 k
+// and keeps their FP32 sums in registers for the whole run (lanes over
+// dimensions): per tile it finds its samples with four ballots over the
+// staged assignments and adds each to the sums of its mean.  No atomics and
+// one barrier per tile; the sums go to the CTA's FP64 partial at the end.
+// ------------------------------------------------------------------------
+constexpr int kStThreads = 1024;
+constexpr int kStBufs = 4;
+
+struct StArgs {
+    const float *X;
+    int64_t N;
+    int32_t D, G;
+    const int32_t *assign;
+    const float *mu_f;     // [G][D] FP32 means (the shift)
+    double *partial;       // [grid][G][1 + 2D]
+    DevStatus *status;
+    long long wait_cycles;
+    int32_t x_al16;
+};
+
+struct StSmem {
+    uint32_t mu, cnt, X[kStBufs], asg[kStBufs], bars, misc, total;
+};
+
+__host__ __device__ inline StSmem st_layout(int D, int G)
+{
+    StSmem L;
+    uint32_t o = 0;
+    L.mu = o; o += 4u * (uint32_t)G * (uint32_t)D;
+    L.cnt = o; o += 4u * (uint32_t)G;
+    o = (o + 127u) & ~127u;
+    for (int b = 0; b < kStBufs; ++b) {
+        L.X[b] = o; o += ((4u * kTM * (uint32_t)D) + 127u) & ~127u;
+        L.asg[b] = o; o += 4u * kTM;
+    }
+    L.bars = o; o += 8u * kStBufs;
+    L.misc = o; o += 16u;
+    L.total = o;
+    return L;
+}
+
+__global__ void __launch_bounds__(kStThreads, 1) k_km_stats(StArgs a)
+{
+    extern __shared__ __align__(128) unsigned char st_raw[];
+    if (km_skip(a.status)) return;
+    const int D = a.D, G = a.G, S = 1 + 2 * D;
+    const StSmem Ls = st_layout(D, G);
+    float *mus = reinterpret_cast<float *>(st_raw + Ls.mu);
+    int *scnt = reinterpret_cast<int *>(st_raw + Ls.cnt);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(st_raw + Ls.bars);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(st_raw + Ls.misc);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t ntiles = (a.N + kTM - 1) / kTM;
+    const int64_t t0 = ntiles * blockIdx.x / gridDim.x, t1 = ntiles * (blockIdx.x + 1) / gridDim.x;
+    uint32_t iss = 0u;   // bulk tiles issued (thread 0); tile t0 + k goes to buffer k % kStBufs
+    auto issue = [&](int64_t tile) {   // thread 0 only
+        const int b = (int)((tile - t0) % kStBufs);
+        const uint32_t xb = 4u * kTM * (uint32_t)D;
+        ++iss;
+        fence_proxy_async();
+        mbar_expect_tx(bars + b, xb + 4u * kTM);
+        bulk_g2s(st_raw + Ls.X[b], a.X + tile * kTM * D, xb, bars + b);
+        bulk_g2s(st_raw + Ls.asg[b], a.assign + tile * kTM, 4u * kTM, bars + b);
+    };
+    for (int k = tid; k < G * D; k += kStThreads) mus[k] = __ldg(a.mu_f + k);
+    for (int k = tid; k < G; k += kStThreads) scnt[k] = 0;
+    if (tid == 0) {
+        for (int b = 0; b < kStBufs; ++b) mbar_init(bars + b, 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0)
+        for (int k = 0; k < kStBufs && t0 + k < t1; ++k)
+            if (tile_bulk((t0 + k) * kTM, a.N, a.x_al16)) issue(t0 + k);
+    // sums of the owned means (k-th: g = warp + 32 k), dimensions lane and
+    // lane + 32; the counts in shared memory
+    float s1a[8], s1b[8], s2a[8], s2b[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s1a[k] = s1b[k] = s2a[k] = s2b[k] = 0.f;
+    auto add = [&](int k, const float *xr, const float *mr) {
+        const float u0 = lane < D ? xr[lane] - mr[lane] : 0.f;
+        const float u1 = lane + 32 < D ? xr[lane + 32] - mr[lane + 32] : 0.f;
+        s1a[k] += u0;
+        s2a[k] = fmaf(u0, u0, s2a[k]);
+        s1b[k] += u1;
+        s2b[k] = fmaf(u1, u1, s2b[k]);
+    };
+    int64_t tend = t1;   // first tile not consumed (an abort leaves later copies pending)
+    for (int64_t t = t0; t < t1; ++t) {
+        const int b = (int)((t - t0) % kStBufs);
+        const uint32_t use = (uint32_t)((t - t0) / kStBufs);
+        const int64_t i0 = t * kTM;
+        const int nv = (int)min((int64_t)kTM, a.N - i0);
+        float *xs = reinterpret_cast<float *>(st_raw + Ls.X[b]);
+        int32_t *as = reinterpret_cast<int32_t *>(st_raw + Ls.asg[b]);
+        if (tile_bulk(i0, a.N, a.x_al16)) {
+            x_wait(bars + b, use & 1u, a.wait_cycles, abort_flag);
+        } else {
+            for (int k = tid; k < nv * D; k += kStThreads) xs[k] = __ldg(a.X + i0 * D + k);
+            for (int k = tid; k < nv; k += kStThreads) as[k] = __ldg(a.assign + i0 + k);
+            __syncthreads();
+        }
+        // a tile whose copy did not land (the wait ran out) is not read
+        const bool skip = __any_sync(0xffffffffu, *abort_flag != 0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int g = !skip && 32 * q + lane < nv ? as[32 * q + lane] : -1;
+            const bool mine = g >= 0 && g < G && (g & 31) == warp;
+            unsigned m = __ballot_sync(0xffffffffu, mine);
+            if (mine) atomicAdd(&scnt[g], 1);
+            while (m) {
+                const int src = __ffs(m) - 1;
+                m &= m - 1u;
+                const int gs = __shfl_sync(0xffffffffu, g, src);
+                const float *xr = xs + (32 * q + src) * D;
+                const float *mr = mus + gs * D;
+                switch (gs >> 5) {   // warp-uniform: the sums stay in registers
+                case 0: add(0, xr, mr); break;
+                case 1: add(1, xr, mr); break;
+                case 2: add(2, xr, mr); break;
+                case 3: add(3, xr, mr); break;
+                case 4: add(4, xr, mr); break;
+                case 5: add(5, xr, mr); break;
+                case 6: add(6, xr, mr); break;
+                default: add(7, xr, mr); break;
+                }
+            }
+        }
+        if (__syncthreads_or(*abort_flag != 0)) {   // uniform
+            tend = t;
+            break;
+        }
+        // buffer b is free again
+        if (tid == 0 && t + kStBufs < t1 && tile_bulk((t + kStBufs) * kTM, a.N, a.x_al16)) issue(t + kStBufs);
+    }
+    __syncthreads();
+    // drain: no bulk copy may still be writing into shared memory at exit.
+    // Bulk tiles are issued in order (tiles t0 .. t0 + iss - 1); those from
+    // tend on were not consumed.
+    if (tid == 0) {
+        const long long d0 = clock64();
+        for (int64_t t = tend; t < t0 + (int64_t)iss; ++t) {
+            const int b = (int)((t - t0) % kStBufs);
+            const uint32_t use = (uint32_t)((t - t0) / kStBufs);
+            while (!mbar_try_wait(bars + b, use & 1u) && clock64() - d0 < a.wait_cycles) {
+            }
+        }
+    }
+    double *P = a.partial + (size_t)blockIdx.x * G * S;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int g = warp + 32 * k;
+        if (g < G) {
+            double *pg = P + (size_t)g * S;
+            if (lane == 0) pg[0] = (double)scnt[g];
+            if (lane < D) { pg[1 + lane] = (double)s1a[k]; pg[1 + D + lane] = (double)s2a[k]; }
+            if (lane + 32 < D) { pg[33 + lane] = (double)s1b[k]; pg[33 + D + lane] = (double)s2b[k]; }
+        }
+    }
+    if (tid == 0 && *abort_flag) {
+        if (atomicCAS(&a.status->code, 0, (int)GMM_ERR_TIMEOUT) == 0) a.status->fail_iter = 0;
+        atomicExch(&a.status->halt, 1);
+    }
+}
+
 }  // namespace
 
 bool km_tc_supported(int32_t D, int32_t G)
@@ -625,7 +789,7 @@ bool km_tc_supported(int32_t D, int32_t G)
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const int NG = (G + 15) / 16 * 16;
-    return km_layout(D, NG).total + 1024u + 1024u <= (uint32_t)optin;
+    return km_layout(D, NG).total + 1024u + 1024u <= (uint32_t)optin && st_layout(D, G).total + 1024u <= (uint32_t)optin;
 }
 
 namespace {
@@ -669,19 +833,13 @@ cudaError_t launch_km_pass_tc(const float *X, int64_t N, int32_t D, int32_t G, c
         return e;
     k_km_screen_tc<<<grid, kThr, sm, s>>>(k);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    count_launches(2);
-    EmPassArgs pa{};
-    pa.X = X;
-    pa.N = N;
-    pa.D = D;
-    pa.G = G;
-    pa.op = op;
-    pa.partial = partial;
-    pa.status = status;
-    pa.iter = 0;
-    pa.wait_cycles = wait_cycles;
-    pa.N_total = N;
-    return launch_mstep_records(pa, L, grid, s);
+    StArgs st{X, N, D, G, assign, op.mu, partial, status, wait_cycles, k.x_al16};
+    const size_t sm4 = st_layout(D, G).total;
+    if ((e = cudaFuncSetAttribute(k_km_stats, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm4)) != cudaSuccess)
+        return e;
+    k_km_stats<<<grid, kStThreads, sm4, s>>>(st);
+    count_launches(3);
+    return cudaGetLastError();
 }
 
 }  // namespace gmm

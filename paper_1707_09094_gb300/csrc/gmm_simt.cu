@@ -483,8 +483,17 @@ __global__ void k_km_finalize(const double *__restrict__ partial, int n_partial,
     extern __shared__ double red[];   // [1+2D]
     const int g = blockIdx.x, S = 1 + 2 * D;
     for (int j = threadIdx.x; j < S; j += blockDim.x) {
+        // partials summed in CTA order; eight loads in flight at a time
         double s = 0.0;
-        for (int c = 0; c < n_partial; ++c) s += partial[((size_t)c * G + g) * S + j];
+        int c = 0;
+        for (; c + 8 <= n_partial; c += 8) {
+            double v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = partial[((size_t)(c + u) * G + g) * S + j];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) s += v[u];
+        }
+        for (; c < n_partial; ++c) s += partial[((size_t)c * G + g) * S + j];
         red[j] = s;
     }
     __syncthreads();
@@ -524,16 +533,38 @@ __global__ void __launch_bounds__(1024) k_km_dead_fix(const float *__restrict__ 
     __shared__ int s_warp[32];
     if (block_skip(status, 0)) return;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    if (tid == 0) {
-        int pop = 0, nd = 0;
-        for (int g = 0; g < G; ++g) {
-            if (counts[g] > counts[pop]) pop = g;
-            if (!(counts[g] > 0.0)) ++nd;
+    // most populous mean (lowest index among equal counts) and dead means, block-wide
+    {
+        double best = -1.0;
+        int pop = 0x7fffffff, nd = 0;
+        for (int g = tid; g < G; g += blockDim.x) {
+            const double c = counts[g];
+            if (c > best) { best = c; pop = g; }   // ascending g: the first of equal counts
+            nd += !(c > 0.0);
         }
-        s_pop = pop; s_ndead = nd; s_found = 0;
-        status->n_dead = nd;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int op = __shfl_xor_sync(0xffffffffu, pop, o);
+            if (ob > best || (ob == best && op < pop)) { best = ob; pop = op; }
+            nd += __shfl_xor_sync(0xffffffffu, nd, o);
+        }
+        __shared__ double s_best[32];
+        __shared__ int s_popw[32], s_ndw[32];
+        if (lane == 0) { s_best[wid] = best; s_popw[wid] = pop; s_ndw[wid] = nd; }
+        __syncthreads();
+        if (tid == 0) {
+            double b = -1.0;
+            int p = 0x7fffffff, n = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                if (s_best[w] > b || (s_best[w] == b && s_popw[w] < p)) { b = s_best[w]; p = s_popw[w]; }
+                n += s_ndw[w];
+            }
+            s_pop = p == 0x7fffffff ? 0 : p; s_ndead = n; s_found = 0;
+            status->n_dead = n;
+        }
+        __syncthreads();
     }
-    __syncthreads();
     const int nd = s_ndead;
     if (nd == 0) return;
     const int pop = s_pop;
