@@ -99,6 +99,7 @@ struct TcArgs {
     int32_t nk;       // K=16 steps per K block: ceil(D/16)
     float screen;     // screening distance in nats, ln(N * 1e9)
     int32_t x_al16;   // X is 16-byte aligned: whole tiles are staged by bulk copies
+    int32_t x_v2;     // D even and X 8-byte aligned: rows are read two dimensions at a time
 };
 
 struct TcSmem {
@@ -113,11 +114,11 @@ __host__ __device__ inline TcSmem tc_layout(int D, int NG)
     L.A = o; o += 2u * kTM * 256u;                       // two buffers x two K blocks of [128][128 B]
     L.xstride = ((4u * kTM * (uint32_t)D) + 127u) & ~127u;
     L.X = o; o += 2u * L.xstride;                        // two staged FP32 sample tiles
-    L.cst = o; o += 8u * NG;                             // (ctc, k2) per Gaussian
+    L.cst = o; o += 8u * NG;                             // ctc - k2 [NG] | ctc + k2 [NG]
     L.ctr = o; o += 4u * 64u;                            // centre
     L.cg = o; o += (uint32_t)kEpiThreads * kCap;         // candidate list staging, 16 B per thread
     L.xlo = o; o += 4u * kEpiThreads;                    // best lower bound per (sample, quarter)
-    L.cn = o; o += 4u * kEpiThreads;                     // candidates per (sample, quarter)
+    L.cn = o; o += 8u * kEpiThreads;                     // candidate bit mask per (sample, quarter)
     o = (o + 7u) & ~7u;
     L.bars = o; o += 8u * 6u;
     L.misc = o; o += 16u;
@@ -147,11 +148,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_em_screen_tc(TcArgs args)
     unsigned char *sbase = tc_raw + ((1024u - (smem_u32(tc_raw) & 1023u)) & 1023u);
     unsigned char *sB = sbase + Ls.B;
     unsigned char *sA = sbase + Ls.A;
-    float2 *cst = reinterpret_cast<float2 *>(sbase + Ls.cst);
+    float *clb = reinterpret_cast<float *>(sbase + Ls.cst);   // lower-bound constant per Gaussian
+    float *cub = clb + NG;                                       // upper-bound constant
     float *ctr = reinterpret_cast<float *>(sbase + Ls.ctr);
     uint8_t *cg = reinterpret_cast<uint8_t *>(sbase + Ls.cg);
     float *xlo = reinterpret_cast<float *>(sbase + Ls.xlo);
-    int *cn = reinterpret_cast<int *>(sbase + Ls.cn);
+    uint2 *cm = reinterpret_cast<uint2 *>(sbase + Ls.cn);
     uint64_t *bar_afull = reinterpret_cast<uint64_t *>(sbase + Ls.bars);
     uint64_t *bar_lfull = bar_afull + 1;
     uint64_t *bar_lfree = bar_afull + 2;
@@ -179,6 +181,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_em_screen_tc(TcArgs args)
     // BF16 operand A of tile `tile` -> A buffer b: row r = [x'^2 | x'] (K
     // blocks 0 | 1), warp per row, from the staged tile (or from global for
     // a tile that is not staged)
+    // Rows r = warp + 16 i share r & 7, so a lane's swizzled column offset
+    // (two dimensions per lane) is the same in every row it writes.
+    const uint32_t colo = ((uint32_t)((lane >> 2) ^ (warp & 7)) << 4) | (uint32_t)((lane & 3) * 4);
+    const uint32_t rowo = (uint32_t)(warp >> 3) * 1024u + (uint32_t)(warp & 7) * 128u;
     auto build_a = [&](int64_t tile, int b) {
         const int64_t i0 = tile * kTM;
         unsigned char *ab = sA + b * (kTM * 256);
@@ -190,20 +196,27 @@ __global__ void __launch_bounds__(kThreads, 1) k_em_screen_tc(TcArgs args)
             }
         }
         const float *xt = reinterpret_cast<const float *>(sbase + Ls.X + (uint32_t)(tile & 1) * Ls.xstride);
-#pragma unroll 2
+        const int d0 = 2 * lane;
+        const float2 c2 = reinterpret_cast<const float2 *>(ctr)[lane];   // 0 past D
+#pragma unroll 4
         for (int i = 0; i < kTM / 16; ++i) {
             const int r = warp + 16 * i;
-            const bool v = i0 + r < a.N;
-#pragma unroll
-            for (int hh = 0; hh < 2; ++hh) {
-                const int d = lane + 32 * hh;
-                float xv = 0.f;
-                if (v && d < D) xv = staged ? xt[r * D + d] : __ldg(a.X + (i0 + r) * D + d);
-                const float xc = (v && d < D) ? xv - ctr[d] : 0.f;
-                const uint32_t off = sw128_off(r, d >> 3) + (uint32_t)((d & 7) * 2);
-                *reinterpret_cast<__nv_bfloat16 *>(ab + off) = __float2bfloat16_rn(xc * xc);
-                *reinterpret_cast<__nv_bfloat16 *>(ab + 16384 + off) = __float2bfloat16_rn(xc);
+            float x0 = 0.f, x1 = 0.f;
+            if (i0 + r < a.N && d0 < D) {
+                const float *src = staged ? xt + r * D + d0 : a.X + (i0 + r) * D + d0;
+                if (args.x_v2) {   // D even and X 8-byte aligned
+                    const float2 p = staged ? *reinterpret_cast<const float2 *>(src)
+                                            : __ldg(reinterpret_cast<const float2 *>(src));
+                    x0 = p.x - c2.x;
+                    x1 = p.y - c2.y;
+                } else {
+                    x0 = (staged ? src[0] : __ldg(src)) - c2.x;
+                    if (d0 + 1 < D) x1 = (staged ? src[1] : __ldg(src + 1)) - c2.y;
+                }
             }
+            const uint32_t off = rowo + 2048u * (uint32_t)i + colo;
+            *reinterpret_cast<__nv_bfloat162 *>(ab + off) = __floats2bfloat162_rn(x0 * x0, x1 * x1);
+            *reinterpret_cast<__nv_bfloat162 *>(ab + 16384 + off) = __floats2bfloat162_rn(x0, x1);
         }
     };
 
@@ -227,9 +240,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_em_screen_tc(TcArgs args)
                 const float ct = __ldg(a.op.ctc + g);
                 // 2^-8 * 1.25 * q/2  +  2^-21 |ctc|  +  1e-4
                 const float k2 = 0.00390625f * 1.25f * 0.5f * __ldg(a.op.q + g) + 4.76837158203125e-07f * fabsf(ct) + 1e-4f;
-                cst[g] = make_float2(ct, k2);
+                clb[g] = ct - k2;
+                cub[g] = ct + k2;
             } else {
-                cst[g] = make_float2(-INFINITY, 0.f);
+                clb[g] = -INFINITY;
+                cub[g] = -INFINITY;
             }
         }
         for (int d = tid; d < 64; d += kEpiThreads) ctr[d] = d < D ? __ldg(a.center + d) : 0.f;
@@ -311,8 +326,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_em_screen_tc(TcArgs args)
             mbar_wait(bar_lfull, (uint32_t)(t & 1), abort_flag, budget);
             tc_fence_after();
             phase(2);
+            // P1 = sum x'^2 (-iv/2) is a sum of non-positive products, so |P1| = -P1
+            // and the bounds l -+ e are linear in (P1, P2):
+            //   lb = (1 + K1) P1 + P2 + (ctc - k2),  ub = (1 - K1) P1 + P2 + (ctc + k2)
+            // evaluated two Gaussians per packed FP32 instruction
             float ub[64];
             float lo = -INFINITY;
+            const float2 kp = make_float2(1.f + kK1, 1.f + kK1), km = make_float2(1.f - kK1, 1.f - kK1);
 #pragma unroll
             for (int cc = 0; cc < 4; ++cc) {
                 const int g0 = 64 * c + 16 * cc;
@@ -322,13 +342,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_em_screen_tc(TcArgs args)
                     tmem_ld16(tl + 256u + (uint32_t)g0, p2);
                     tmem_wait_ld();
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const float P1 = __uint_as_float(p1[j]), P2 = __uint_as_float(p2[j]);
-                        const float2 k = cst[g0 + j];
-                        const float l = (P1 + P2) + k.x;
-                        const float e = fmaf(fabsf(P1), kK1, k.y);
-                        ub[16 * cc + j] = l + e;
-                        lo = fmaxf(lo, l - e);
+                    for (int j = 0; j < 16; j += 4) {
+                        const float4 cl = *reinterpret_cast<const float4 *>(clb + g0 + j);
+                        const float4 cu = *reinterpret_cast<const float4 *>(cub + g0 + j);
+                        const float2 x1a = make_float2(__uint_as_float(p1[j]), __uint_as_float(p1[j + 1]));
+                        const float2 x1b = make_float2(__uint_as_float(p1[j + 2]), __uint_as_float(p1[j + 3]));
+                        const float2 x2a = make_float2(__uint_as_float(p2[j]), __uint_as_float(p2[j + 1]));
+                        const float2 x2b = make_float2(__uint_as_float(p2[j + 2]), __uint_as_float(p2[j + 3]));
+                        const float2 la = __fadd2_rn(__ffma2_rn(x1a, kp, x2a), make_float2(cl.x, cl.y));
+                        const float2 lb = __fadd2_rn(__ffma2_rn(x1b, kp, x2b), make_float2(cl.z, cl.w));
+                        const float2 ua = __fadd2_rn(__ffma2_rn(x1a, km, x2a), make_float2(cu.x, cu.y));
+                        const float2 ubb = __fadd2_rn(__ffma2_rn(x1b, km, x2b), make_float2(cu.z, cu.w));
+                        lo = fmaxf(lo, fmaxf(fmaxf(la.x, la.y), fmaxf(lb.x, lb.y)));
+                        ub[16 * cc + j] = ua.x;
+                        ub[16 * cc + j + 1] = ua.y;
+                        ub[16 * cc + j + 2] = ubb.x;
+                        ub[16 * cc + j + 3] = ubb.y;
                     }
                 } else {
 #pragma unroll
@@ -341,29 +370,33 @@ __global__ void __launch_bounds__(kThreads, 1) k_em_screen_tc(TcArgs args)
             epi_sync();
             if (tid == 0) mbar_arrive(bar_lfree);
             lo = fmaxf(fmaxf(xlo[s], xlo[kTM + s]), fmaxf(xlo[2 * kTM + s], xlo[3 * kTM + s]));
-            // ---- pass 2: candidate list of this (sample, quarter)
+            // ---- pass 2: candidate list of this (sample, quarter), as a bit mask first
             const float thr = lo - args.screen;
             const int gend = G - 64 * c;   // only real Gaussians (also when every bound is NaN/-inf)
-            int n = 0;
+            uint32_t m0 = 0u, m1 = 0u;
 #pragma unroll
-            for (int j = 0; j < 64; ++j) {
-                if (j < gend && ub[j] >= thr) {
-                    if (n < kCap) my[n] = (uint8_t)j;
-                    ++n;
-                }
+            for (int j = 0; j < 32; ++j) {
+                if (ub[j] >= thr) m0 |= 1u << j;
+                if (ub[32 + j] >= thr) m1 |= 1u << j;
             }
-            cn[tid] = n;
+            m0 &= gend >= 32 ? 0xffffffffu : (gend > 0 ? (1u << gend) - 1u : 0u);
+            m1 &= gend >= 64 ? 0xffffffffu : (gend > 32 ? (1u << (gend - 32)) - 1u : 0u);
+            cm[tid] = make_uint2(m0, m1);
             epi_sync();
             // ---- the two quarters of a half -> one record (threads of even quarters)
             if ((c & 1) == 0 && s < nvalid) {
                 const int h = c >> 1;
-                const int nb = cn[tid + 128];
+                const uint2 pm = cm[tid + 128];
+                const int n = __popc(m0) + __popc(m1), nb = __popc(pm.x) + __popc(pm.y);
                 const int tot = n + nb;
                 const int64_t rec = (i0 + s) * 2 + h;
-                args.L.cnt[rec] = (uint8_t)(n > kCap || nb > kCap ? 255 : min(tot, 255));
+                args.L.cnt[rec] = (uint8_t)(n > kCap || nb > kCap ? 255 : tot);
                 if (tot > 0 && tot <= kCap) {
-                    const uint8_t *yb = cg + (tid + 128) * kCap;
-                    for (int k = 0; k < nb; ++k) my[n + k] = (uint8_t)(64 + yb[k]);
+                    int k = 0;
+                    for (uint32_t m = m0; m != 0u; m &= m - 1u) my[k++] = (uint8_t)(__ffs(m) - 1);
+                    for (uint32_t m = m1; m != 0u; m &= m - 1u) my[k++] = (uint8_t)(31 + __ffs(m));
+                    for (uint32_t m = pm.x; m != 0u; m &= m - 1u) my[k++] = (uint8_t)(63 + __ffs(m));
+                    for (uint32_t m = pm.y; m != 0u; m &= m - 1u) my[k++] = (uint8_t)(95 + __ffs(m));
                     reinterpret_cast<uint4 *>(args.L.cand)[rec] = *reinterpret_cast<const uint4 *>(my);
                 }
                 st_n += (h == 0);
@@ -1122,7 +1155,8 @@ cudaError_t launch_em_pass_tc(const EmPassArgs &a, const TcLists &L, int32_t gri
 {
     const float scr = (float)std::log((double)(a.N_total > a.N ? a.N_total : a.N) * 1e9);
     const int al = (reinterpret_cast<uintptr_t>(a.X) & 15u) == 0;
-    TcArgs t{a, L, (a.G + 15) / 16 * 16, (a.D + 15) / 16, scr, al};
+    TcArgs t{a, L, (a.G + 15) / 16 * 16, (a.D + 15) / 16, scr, al,
+             (a.D % 2 == 0 && (reinterpret_cast<uintptr_t>(a.X) & 7u) == 0) ? 1 : 0};
     const size_t sm1 = tc_layout(a.D, t.NG).total + 1024u;
     cudaError_t e = cudaFuncSetAttribute(k_em_screen_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
     if (e != cudaSuccess) return e;
