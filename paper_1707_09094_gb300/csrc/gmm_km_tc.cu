@@ -702,8 +702,8 @@ __global__ void __launch_bounds__(kStThreads, 1) k_km_stats(StArgs a)
         s1b[k] += u1;
         s2b[k] = fmaf(u1, u1, s2b[k]);
     };
-    int64_t tend = t1;   // first tile not consumed (an abort leaves later copies pending)
-    for (int64_t t = t0; t < t1; ++t) {
+    // tile t: wait for its copy (or copy it here), then each warp adds its samples
+    auto process = [&](int64_t t) {
         const int b = (int)((t - t0) % kStBufs);
         const uint32_t use = (uint32_t)((t - t0) / kStBufs);
         const int64_t i0 = t * kTM;
@@ -715,7 +715,7 @@ __global__ void __launch_bounds__(kStThreads, 1) k_km_stats(StArgs a)
         } else {
             for (int k = tid; k < nv * D; k += kStThreads) xs[k] = __ldg(a.X + i0 * D + k);
             for (int k = tid; k < nv; k += kStThreads) as[k] = __ldg(a.assign + i0 + k);
-            __syncthreads();
+            __syncthreads();   // uniform: every thread processes the same tiles
         }
         // a tile whose copy did not land (the wait ran out) is not read
         const bool skip = __any_sync(0xffffffffu, *abort_flag != 0);
@@ -743,12 +743,20 @@ __global__ void __launch_bounds__(kStThreads, 1) k_km_stats(StArgs a)
                 }
             }
         }
+    };
+    // two tiles between barriers (fewer waits on the slowest warp)
+    int64_t tend = t1;   // first tile not consumed (an abort leaves later copies pending)
+    for (int64_t t = t0; t < t1; t += 2) {
+        process(t);
+        if (t + 1 < t1) process(t + 1);
         if (__syncthreads_or(*abort_flag != 0)) {   // uniform
             tend = t;
             break;
         }
-        // buffer b is free again
-        if (tid == 0 && t + kStBufs < t1 && tile_bulk((t + kStBufs) * kTM, a.N, a.x_al16)) issue(t + kStBufs);
+        // the buffers of tiles t and t+1 are free again
+        if (tid == 0)
+            for (int64_t u = t + kStBufs; u < t + kStBufs + 2 && u < t1; ++u)
+                if (tile_bulk(u * kTM, a.N, a.x_al16)) issue(u);
     }
     __syncthreads();
     // drain: no bulk copy may still be writing into shared memory at exit.

@@ -70,11 +70,49 @@ __device__ void set_error(DevStatus *st, int code, int iter)
     atomicExch(&st->halt, 1);
 }
 
+// p[0] + p[stride] + ... + p[(n-1) stride], added in that order, with eight
+// loads in flight at a time
+__device__ __forceinline__ double sum_in_order(const double *__restrict__ p, int n, size_t stride)
+{
+    double s = 0.0;
+    int c = 0;
+    for (; c + 8 <= n; c += 8) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = p[(size_t)(c + u) * stride];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s += v[u];
+    }
+    for (; c < n; ++c) s += p[(size_t)c * stride];
+    return s;
+}
+
 // ------------------------------------------------------------------------
 // Global per-dimension mean and variance (Eq. 20's global covariance).
-// Pass 1 sums x, pass 2 sums (x - mean)^2, both FP64 per CTA, CTA order.
-// blockDim = R*D: thread (r, d) walks rows r, r+R*grid, ... of column d.
+// Pass 1 sums x, pass 2 sums (x - mean)^2.  Each thread keeps an unevaluated
+// float-float sum (hi + lo, about 44 significant bits: Knuth's error-free
+// two-sum with renormalisation), so the pass runs on the FP32 pipes at HBM
+// speed; the per-thread sums are combined in FP64 per CTA, then in CTA
+// order.  blockDim = R*D: thread (r, d) walks rows r, r+R*grid, ... of
+// column d.
 // ------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// (hi, lo) += (v, ve), renormalised so that |lo| <= ulp(hi) / 2
+__device__ __forceinline__ void ff_add(float &hi, float &lo, float v, float ve)
+{
+    float s, e;
+    two_sum(hi, v, s, e);
+    e = __fadd_rn(e, __fadd_rn(lo, ve));
+    hi = __fadd_rn(s, e);
+    lo = __fsub_rn(e, __fsub_rn(hi, s));
+}
+
 template <int PASS>
 __global__ void k_gstats(const float *__restrict__ X, int64_t N, int32_t D,
                          const double *__restrict__ gmean, double *__restrict__ partial)
@@ -82,17 +120,27 @@ __global__ void k_gstats(const float *__restrict__ X, int64_t N, int32_t D,
     extern __shared__ double shd[];
     const int R = blockDim.x / D;
     const int t = threadIdx.x;
-    double acc = 0.0;
+    float hi = 0.f, lo = 0.f;
     if (t < R * D) {
         const int d = t % D, r = t / D;
         const double m = PASS == 2 ? gmean[d] : 0.0;
+        const float mh = (float)m, ml = (float)(m - (double)mh);   // m = mh + ml to ~2^-48
         for (int64_t i = (int64_t)blockIdx.x * R + r; i < N; i += (int64_t)gridDim.x * R) {
-            double v = (double)X[i * D + d];
-            if (PASS == 1) acc += v;
-            else { double q = v - m; acc += q * q; }
+            const float v = X[i * D + d];
+            if (PASS == 1) {
+                ff_add(hi, lo, v, 0.f);
+            } else {
+                float q, qe;
+                two_sum(v, -mh, q, qe);          // v - mh exactly
+                qe = __fsub_rn(qe, ml);          // (q, qe) = v - m
+                const float p = __fmul_rn(q, q);
+                float pe = __fmaf_rn(q, q, -p);  // q*q - p exactly
+                pe = __fmaf_rn(__fadd_rn(q, q), qe, pe);
+                ff_add(hi, lo, p, pe);
+            }
         }
     }
-    shd[t] = acc;
+    shd[t] = (double)hi + (double)lo;
     __syncthreads();
     if (t < D) {
         double s = 0.0;
@@ -102,14 +150,23 @@ __global__ void k_gstats(const float *__restrict__ X, int64_t N, int32_t D,
 }
 
 template <int PASS>
-__global__ void k_gstats_final(const double *__restrict__ partial, int n_partial, int64_t N, int32_t D,
-                               double var_floor, int32_t dist, double *gmean, double *gvar_floored,
-                               double *wdist, float *sw, float *center)
+__global__ void __launch_bounds__(128) k_gstats_final(const double *__restrict__ partial, int n_partial, int64_t N,
+                                                      int32_t D, double var_floor, int32_t dist, double *gmean,
+                                                      double *gvar_floored, double *wdist, float *sw, float *center)
 {
-    int d = blockIdx.x * blockDim.x + threadIdx.x;
-    if (d >= D) return;
+    // one block per dimension: strided partial sums, then a fixed-order tree
+    __shared__ double red[128];
+    const int d = blockIdx.x, t = threadIdx.x;
     double s = 0.0;
-    for (int c = 0; c < n_partial; ++c) s += partial[(size_t)c * D + d];
+    for (int c = t; c < n_partial; c += 128) s += partial[(size_t)c * D + d];
+    red[t] = s;
+    __syncthreads();
+    for (int w = 64; w > 0; w >>= 1) {
+        if (t < w) red[t] += red[t + w];
+        __syncthreads();
+    }
+    if (t != 0) return;
+    s = red[0];
     if (PASS == 1) {
         gmean[d] = s / (double)N;
         center[d] = (float)(s / (double)N);
@@ -482,20 +539,7 @@ __global__ void k_km_finalize(const double *__restrict__ partial, int n_partial,
     if (block_skip(status, 0)) return;
     extern __shared__ double red[];   // [1+2D]
     const int g = blockIdx.x, S = 1 + 2 * D;
-    for (int j = threadIdx.x; j < S; j += blockDim.x) {
-        // partials summed in CTA order; eight loads in flight at a time
-        double s = 0.0;
-        int c = 0;
-        for (; c + 8 <= n_partial; c += 8) {
-            double v[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = partial[((size_t)(c + u) * G + g) * S + j];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) s += v[u];
-        }
-        for (; c < n_partial; ++c) s += partial[((size_t)c * G + g) * S + j];
-        red[j] = s;
-    }
+    for (int j = threadIdx.x; j < S; j += blockDim.x) red[j] = sum_in_order(partial + (size_t)g * S + j, n_partial, (size_t)G * S);
     __syncthreads();
     const double cnt = red[0];
     if (threadIdx.x == 0) counts[g] = cnt;
@@ -992,8 +1036,7 @@ __global__ void k_em_ll(const double *__restrict__ ll_partial, int n_partial, in
 {
     if (threadIdx.x != 0) return;
     if (status->halt != 0 || iter > status->stop_after) return;
-    double s = 0.0;
-    for (int c = 0; c < n_partial; ++c) s += ll_partial[c];
+    const double s = sum_in_order(ll_partial, n_partial, 1);
     const double m = s / (double)N;
     ll_hist[iter] = m;
     if (!isfinite(m)) { set_error(status, GMM_ERR_NONFINITE, iter); return; }
@@ -1014,11 +1057,7 @@ __global__ void k_em_finalize(EmFinalizeArgs a)
     __shared__ int s_bad;
     if (block_skip(a.status, a.iter)) return;
     const int g = blockIdx.x, D = a.D, G = a.G, S = 1 + 2 * D;
-    for (int j = threadIdx.x; j < S; j += blockDim.x) {
-        double s = 0.0;
-        for (int c = 0; c < a.n_partial; ++c) s += a.partial[((size_t)c * G + g) * S + j];
-        red[j] = s;
-    }
+    for (int j = threadIdx.x; j < S; j += blockDim.x) red[j] = sum_in_order(a.partial + (size_t)g * S + j, a.n_partial, (size_t)G * S);
     if (threadIdx.x == 0) s_bad = 0;
     __syncthreads();
     const double Lg = red[0];
@@ -1432,11 +1471,11 @@ cudaError_t launch_global_stats(const float *X, int64_t N, int32_t D, double var
     const int threads = ((R * D + 31) / 32) * 32;
     const size_t sm = sizeof(double) * threads;
     k_gstats<1><<<grid, threads, sm, s>>>(X, N, D, nullptr, partial);
-    k_gstats_final<1><<<(D + 127) / 128, 128, 0, s>>>(partial, grid, N, D, var_floor, dist, gmean,
-                                                        gvar_floored, wdist, sw, center);
+    k_gstats_final<1><<<D, 128, 0, s>>>(partial, grid, N, D, var_floor, dist, gmean, gvar_floored, wdist, sw,
+                                         center);
     k_gstats<2><<<grid, threads, sm, s>>>(X, N, D, gmean, partial);
-    k_gstats_final<2><<<(D + 127) / 128, 128, 0, s>>>(partial, grid, N, D, var_floor, dist, gmean,
-                                                        gvar_floored, wdist, sw, center);
+    k_gstats_final<2><<<D, 128, 0, s>>>(partial, grid, N, D, var_floor, dist, gmean, gvar_floored, wdist, sw,
+                                         center);
     count_launches(4);
     return cudaGetLastError();
 }
