@@ -603,22 +603,36 @@ __global__ void __launch_bounds__(kExThreads, 1) k_em_exact(ExArgs args)
         const int t_2 = __shfl_sync(0xffffffffu, tot, 2), t_3 = __shfl_sync(0xffffffffu, tot, 3);
         const int o1 = t_0, o2 = o1 + t_1, o3 = o2 + t_2, T = o3 + t_3;
         if (T <= WP) {
-            // ---- lay the pairs out, one lane per pair
-            for (int p = lane; p < T; p += 32) {
-                const int k = (p >= o1) + (p >= o2) + (p >= o3);
-                const int j = p - (k == 0 ? 0 : (k == 1 ? o1 : (k == 2 ? o2 : o3)));
-                wsm[p] = (uint8_t)k;
-                wg[p] = (uint8_t)j;   // rank within the sample for now
-            }
-            __syncwarp();
-            for (int p = lane; p < T; p += 32) {
-                const int k = wsm[p], j = wg[p];
-                const int si = sb + k;
-                const int m0 = ns[2 * si], m1 = ns[2 * si + 1];
-                const int d0 = m0 > kCap ? min(128, G) : m0;
-                int g;
-                if (j < d0) g = m0 > kCap ? j : cs[si * 32 + j];
-                else g = 128 + (m1 > kCap ? j - d0 : cs[si * 32 + 16 + (j - d0)]);
+            // ---- one lane per pair, in rounds of 32 pairs.  Within a round the
+            // pairs are dealt to lanes in the order (rank among the pairs with
+            // the same g mod 8, g mod 8): the eight lanes of a 128-bit load
+            // phase then mostly read operand rows in distinct bank groups.
+            for (int p0 = 0; p0 < T; p0 += 32) {
+                const int pl = p0 + lane;
+                int sil = 0, gl = 0;
+                if (pl < T) {
+                    const int k = (pl >= o1) + (pl >= o2) + (pl >= o3);
+                    const int j = pl - (k == 0 ? 0 : (k == 1 ? o1 : (k == 2 ? o2 : o3)));
+                    sil = sb + k;
+                    const int m0 = ns[2 * sil], m1 = ns[2 * sil + 1];
+                    const int d0 = m0 > kCap ? min(128, G) : m0;
+                    if (j < d0) gl = m0 > kCap ? j : cs[sil * 32 + j];
+                    else gl = 128 + (m1 > kCap ? j - d0 : cs[sil * 32 + 16 + (j - d0)]);
+                }
+                const int key = pl < T ? (gl & 7) : 8;   // lanes past the last pair sort last
+                const int rk = __popc(__match_any_sync(0xffffffffu, key) & ((1u << lane) - 1u));
+                int pos = 0;
+#pragma unroll
+                for (int kk = 0; kk < 9; ++kk) {
+                    const int ck = __popc(__ballot_sync(0xffffffffu, key == kk));
+                    pos += min(ck, rk) + (kk < key && ck > rk ? 1 : 0);
+                }
+                wsm[p0 + pos] = (uint8_t)lane;   // p0 + 31 < WP: T <= WP and WP is a multiple of 32
+                __syncwarp();
+                const int src = wsm[p0 + lane];
+                const int p = p0 + src;
+                const int si = __shfl_sync(0xffffffffu, sil, src), g = __shfl_sync(0xffffffffu, gl, src);
+                if (p >= T) continue;
                 // ---- exact log-density of the pair over all D
                 const float *xr = xs + si * D;
                 const float2 *q = psm + g * DS;
