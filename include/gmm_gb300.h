@@ -286,6 +286,16 @@ gmm_status gmm_init_net_seed_model(const gmm_init_net *n, gmm_model *m, const fl
  * without parameters, GMM_ERR_ARG for N < 0 or out == NULL with N > 0. */
 gmm_status gmm_generate(const gmm_model *m, int64_t N, uint64_t seed, float *out, void *stream);
 
+/* FP64 sample data (the double-precision input of the paper's gmm_diag,
+ * Sec. 4.1).  The library computes on FP32 samples: gmm_x_from_f64 rounds
+ * X64[0..count) to the nearest FP32 values (ties to even) into X32[0..count),
+ * on `stream` (NULL = the default stream), and X32 is then passed to any call
+ * that takes X.  Both pointers are device memory owned by the caller; a host
+ * array is converted on the host instead.  Values beyond the FP32 range become
+ * +-inf, which the calls that take X report as GMM_ERR_NONFINITE.
+ * GMM_ERR_ARG for count < 0, a NULL or host pointer (count > 0). */
+gmm_status gmm_x_from_f64(const double *X64, int64_t count, float *X32, void *stream);
+
 /* save / load (Sec. 4.1, M.save / M.load): the model's parameters in a file
  * of this library's format -- 8 bytes "GMMDIAG1", int32 D, int32 n_gaus
  * (little-endian), then FP64 means [n_gaus][D], dcovs [n_gaus][D], hefts

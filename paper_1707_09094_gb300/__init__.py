@@ -33,12 +33,22 @@ def _stream_ptr(X):
 
 
 def _as_input(X):
-    """(pointer, N, D, keepalive) for a float32 [N][D] tensor/array."""
+    """(pointer, N, D, keepalive) for a float32 [N][D] tensor/array.  FP64
+    samples (the paper's double input) are rounded to FP32: CUDA tensors by
+    the library's conversion kernel, host data on the host."""
     torch = _torch()
     if isinstance(X, torch.Tensor):
-        if X.dtype != torch.float32 or X.dim() != 2:
-            raise ValueError("X must be a float32 [N][D] tensor")
+        if X.dim() != 2 or X.dtype not in (torch.float32, torch.float64):
+            raise ValueError("X must be a float32 or float64 [N][D] tensor")
         X = X.contiguous()
+        if X.dtype == torch.float64:
+            if not X.is_cuda:
+                return _as_input(X.numpy())
+            X32 = torch.empty(X.shape, dtype=torch.float32, device=X.device)
+            _lib.check(_lib.load().gmm_x_from_f64(ctypes.c_void_p(X.data_ptr()), X.numel(),
+                                                  ctypes.c_void_p(X32.data_ptr()), _stream_ptr(X)),
+                       "gmm_x_from_f64")
+            X = X32
         return ctypes.c_void_p(X.data_ptr()), X.shape[0], X.shape[1], X
     A = np.ascontiguousarray(X, dtype=np.float32)
     if A.ndim != 2:

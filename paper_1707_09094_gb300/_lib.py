@@ -50,6 +50,7 @@ SIGNATURES = {
     "gmm_get_params": (ctypes.c_int, [P, ctypes.POINTER(i32), ctypes.POINTER(i32), P, P, P]),
     "gmm_set_params": (ctypes.c_int, [P, i32, i32, P, P, P]),
     "gmm_generate": (ctypes.c_int, [P, i64, ctypes.c_uint64, P, P]),
+    "gmm_x_from_f64": (ctypes.c_int, [P, i64, P, P]),
     "gmm_save": (ctypes.c_int, [P, ctypes.c_char_p]),
     "gmm_load": (ctypes.c_int, [P, ctypes.c_char_p]),
     "gmm_get_stats": (ctypes.c_int, [P, P, i32, ctypes.POINTER(i32)]),

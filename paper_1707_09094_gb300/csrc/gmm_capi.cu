@@ -771,6 +771,20 @@ gmm_status gmm_generate(const gmm_model *mc, int64_t N, uint64_t seed, float *ou
     return GMM_OK;
 }
 
+gmm_status gmm_x_from_f64(const double *X64, int64_t count, float *X32, void *stream)
+{
+    if (count < 0) return fail(GMM_ERR_ARG, "count must be >= 0");
+    if (count == 0) return GMM_OK;
+    if (!X64 || !X32) return fail(GMM_ERR_ARG, "NULL pointer");
+    if (!is_device_ptr(X64) || !is_device_ptr(X32))
+        return fail(GMM_ERR_ARG, "gmm_x_from_f64 takes device memory (convert host arrays on the host)");
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CK(gmm::launch_f64_to_f32(X64, count, X32, sms, as_stream(stream)));
+    return GMM_OK;
+}
+
 gmm_status gmm_save(const gmm_model *m, const char *path)
 {
     if (!m || !path) return fail(GMM_ERR_ARG, "NULL argument");

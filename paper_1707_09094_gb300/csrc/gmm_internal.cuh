@@ -111,6 +111,7 @@ cudaError_t launch_avg_log_p_noalloc(const float *X, int64_t N, int32_t D, int32
                                      double *sum_host, cudaStream_t s);
 int em_simt_grid(int32_t D, int32_t G, int sms);
 int km_grid(int32_t D, int32_t G, int sms);
+cudaError_t launch_f64_to_f32(const double *in, int64_t n, float *out, int sms, cudaStream_t s);
 size_t em_simt_smem(int32_t D, int32_t G);
 bool em_simt_supported(int32_t D, int32_t G);
 

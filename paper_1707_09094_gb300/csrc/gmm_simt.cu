@@ -1695,6 +1695,22 @@ cudaError_t launch_spread_seeds(const float *X, int64_t N, int32_t D, int32_t G,
 }  // namespace gmm
 
 namespace gmm {
+namespace {
+__global__ void k_f64_to_f32(const double *__restrict__ in, int64_t n, float *__restrict__ out)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        out[k] = __double2float_rn(in[k]);
+}
+}  // namespace
+
+cudaError_t launch_f64_to_f32(const double *in, int64_t n, float *out, int sms, cudaStream_t s)
+{
+    const int64_t blocks = (n + 255) / 256;
+    k_f64_to_f32<<<(int)(blocks < 8 * sms ? (blocks > 0 ? blocks : 1) : 8 * sms), 256, 0, s>>>(in, n, out);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_generate(const double *par, int32_t G, int32_t D, int64_t N, uint64_t seed, float *out, int sms,
                             cudaStream_t s)
 {

@@ -379,3 +379,34 @@ def test_generate_matches_oracle_and_save_load_roundtrip(tmp_path):
     assert e.value.status == -1
     for a, b in zip(g.get_params(), h.get_params()):
         np.testing.assert_array_equal(a, b)
+
+
+# ------------------------------------------------------------ FP64 sample data
+def test_fp64_samples_round_to_fp32_on_the_device():
+    """The paper's double input: CUDA float64 samples are rounded to nearest
+    FP32 by the library's kernel (compared bit for bit with numpy's rounding,
+    including overflow to inf and subnormals), and a fit on them equals the
+    fit on the rounded samples."""
+    import ctypes
+    from paper_1707_09094_gb300 import _lib
+    rng = np.random.default_rng(1)
+    v = np.concatenate([rng.normal(0, 3, 10000), [1e300, -1e300, 1e-310, 3.4e38, 1.0 + 2.0 ** -30, np.nan]])
+    t = torch.from_numpy(v).cuda()
+    out = torch.empty(v.size, dtype=torch.float32, device="cuda")
+    _lib.check(_lib.load().gmm_x_from_f64(ctypes.c_void_p(t.data_ptr()), v.size, ctypes.c_void_p(out.data_ptr()),
+                                          ctypes.c_void_p(0)), "gmm_x_from_f64")
+    torch.cuda.synchronize()
+    with np.errstate(over="ignore"):
+        ref = v.astype(np.float32)
+    got = out.cpu().numpy()
+    fin = ~np.isnan(ref)
+    np.testing.assert_array_equal(got[fin].view(np.uint32), ref[fin].view(np.uint32))
+    assert np.isnan(got[~fin]).all()
+
+    X, _, _ = synth.make("c1", N=20000)
+    X64 = X.astype(np.float64) + rng.normal(0, 1e-6, X.shape)
+    X32 = X64.astype(np.float32)
+    M, V, H, ll = oracle.learn(X32, 8, seed=5, km_iter=3, em_iter=3, var_floor=1e-10)
+    for Xin in (torch.from_numpy(X64).cuda(), X64):
+        g = GMM().learn(Xin, 8, km_iter=3, em_iter=3, seed=5, var_floor=1e-10)
+        assert_params(g.get_params(), (M, V, H), X32)
