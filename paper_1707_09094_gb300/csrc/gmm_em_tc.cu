@@ -329,8 +329,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_em_screen_tc(TcArgs args)
             // P1 = sum x'^2 (-iv/2) is a sum of non-positive products, so |P1| = -P1
             // and the bounds l -+ e are linear in (P1, P2):
             //   lb = (1 + K1) P1 + P2 + (ctc - k2),  ub = (1 - K1) P1 + P2 + (ctc + k2)
-            // evaluated two Gaussians per packed FP32 instruction
-            float ub[64];
+            // evaluated two Gaussians per packed FP32 instruction.  Pass 1 takes
+            // the best lower bound; pass 2 reads the accumulators again for the
+            // upper bounds (the MMAs of the next tile wait for this tile's pass 2).
             float lo = -INFINITY;
             const float2 kp = make_float2(1.f + kK1, 1.f + kK1), km = make_float2(1.f - kK1, 1.f - kK1);
 #pragma unroll
@@ -344,45 +345,61 @@ __global__ void __launch_bounds__(kThreads, 1) k_em_screen_tc(TcArgs args)
 #pragma unroll
                     for (int j = 0; j < 16; j += 4) {
                         const float4 cl = *reinterpret_cast<const float4 *>(clb + g0 + j);
-                        const float4 cu = *reinterpret_cast<const float4 *>(cub + g0 + j);
-                        const float2 x1a = make_float2(__uint_as_float(p1[j]), __uint_as_float(p1[j + 1]));
-                        const float2 x1b = make_float2(__uint_as_float(p1[j + 2]), __uint_as_float(p1[j + 3]));
-                        const float2 x2a = make_float2(__uint_as_float(p2[j]), __uint_as_float(p2[j + 1]));
-                        const float2 x2b = make_float2(__uint_as_float(p2[j + 2]), __uint_as_float(p2[j + 3]));
-                        const float2 la = __fadd2_rn(__ffma2_rn(x1a, kp, x2a), make_float2(cl.x, cl.y));
-                        const float2 lb = __fadd2_rn(__ffma2_rn(x1b, kp, x2b), make_float2(cl.z, cl.w));
-                        const float2 ua = __fadd2_rn(__ffma2_rn(x1a, km, x2a), make_float2(cu.x, cu.y));
-                        const float2 ubb = __fadd2_rn(__ffma2_rn(x1b, km, x2b), make_float2(cu.z, cu.w));
+                        const float2 la = __fadd2_rn(
+                            __ffma2_rn(make_float2(__uint_as_float(p1[j]), __uint_as_float(p1[j + 1])), kp,
+                                       make_float2(__uint_as_float(p2[j]), __uint_as_float(p2[j + 1]))),
+                            make_float2(cl.x, cl.y));
+                        const float2 lb = __fadd2_rn(
+                            __ffma2_rn(make_float2(__uint_as_float(p1[j + 2]), __uint_as_float(p1[j + 3])), kp,
+                                       make_float2(__uint_as_float(p2[j + 2]), __uint_as_float(p2[j + 3]))),
+                            make_float2(cl.z, cl.w));
                         lo = fmaxf(lo, fmaxf(fmaxf(la.x, la.y), fmaxf(lb.x, lb.y)));
-                        ub[16 * cc + j] = ua.x;
-                        ub[16 * cc + j + 1] = ua.y;
-                        ub[16 * cc + j + 2] = ubb.x;
-                        ub[16 * cc + j + 3] = ubb.y;
                     }
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) ub[16 * cc + j] = -INFINITY;
                 }
             }
-            tc_fence_before();
             phase(3);
             xlo[tid] = lo;
             epi_sync();
-            if (tid == 0) mbar_arrive(bar_lfree);
             lo = fmaxf(fmaxf(xlo[s], xlo[kTM + s]), fmaxf(xlo[2 * kTM + s], xlo[3 * kTM + s]));
             // ---- pass 2: candidate list of this (sample, quarter), as a bit mask first
             const float thr = lo - args.screen;
             const int gend = G - 64 * c;   // only real Gaussians (also when every bound is NaN/-inf)
             uint32_t m0 = 0u, m1 = 0u;
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                if (ub[j] >= thr) m0 |= 1u << j;
-                if (ub[32 + j] >= thr) m1 |= 1u << j;
+            for (int cc = 0; cc < 4; ++cc) {
+                const int g0 = 64 * c + 16 * cc;
+                if (g0 < NG) {
+                    uint32_t p1[16], p2[16];
+                    tmem_ld16(tl + (uint32_t)g0, p1);
+                    tmem_ld16(tl + 256u + (uint32_t)g0, p2);
+                    tmem_wait_ld();
+                    uint32_t bits = 0u;
+#pragma unroll
+                    for (int j = 0; j < 16; j += 4) {
+                        const float4 cu = *reinterpret_cast<const float4 *>(cub + g0 + j);
+                        const float2 ua = __fadd2_rn(
+                            __ffma2_rn(make_float2(__uint_as_float(p1[j]), __uint_as_float(p1[j + 1])), km,
+                                       make_float2(__uint_as_float(p2[j]), __uint_as_float(p2[j + 1]))),
+                            make_float2(cu.x, cu.y));
+                        const float2 ubb = __fadd2_rn(
+                            __ffma2_rn(make_float2(__uint_as_float(p1[j + 2]), __uint_as_float(p1[j + 3])), km,
+                                       make_float2(__uint_as_float(p2[j + 2]), __uint_as_float(p2[j + 3]))),
+                            make_float2(cu.z, cu.w));
+                        if (ua.x >= thr) bits |= 1u << j;
+                        if (ua.y >= thr) bits |= 1u << (j + 1);
+                        if (ubb.x >= thr) bits |= 1u << (j + 2);
+                        if (ubb.y >= thr) bits |= 1u << (j + 3);
+                    }
+                    if (cc < 2) m0 |= bits << (16 * cc);
+                    else m1 |= bits << (16 * (cc - 2));
+                }
             }
+            tc_fence_before();
             m0 &= gend >= 32 ? 0xffffffffu : (gend > 0 ? (1u << gend) - 1u : 0u);
             m1 &= gend >= 64 ? 0xffffffffu : (gend > 32 ? (1u << (gend - 32)) - 1u : 0u);
             cm[tid] = make_uint2(m0, m1);
             epi_sync();
+            if (tid == 0) mbar_arrive(bar_lfree);   // every thread's TMEM reads of this tile are done
             // ---- the two quarters of a half -> one record (threads of even quarters)
             if ((c & 1) == 0 && s < nvalid) {
                 const int h = c >> 1;
