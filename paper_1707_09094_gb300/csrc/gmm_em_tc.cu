@@ -6,29 +6,34 @@
 //     about the global centre m (x' = x - m, mu' = mu - m):
 //        P1[i][g] = sum_d x'^2 (-1/2 iv_gd)      (K block 0, TMEM columns 0..255)
 //        P2[i][g] = sum_d x'   (mu'_gd iv_gd)    (K block 1, TMEM columns 256..511)
-//     so l~_g(x_i) = ctc_g + P1 + P2 approximates log w_g N(x_i|g).  With
-//     BF16 rounding of both operands, |l~ - l| <= 2^-8 * 1.25 *
-//     sum_d (x'^2 iv/2 + |x' mu'| iv) + tiny terms, and by AM-GM
-//     sum_d |x' mu'| iv <= sum_d (x'^2 + mu'^2) iv / 2, so
-//     |l~ - l| <= K1 |P1| + k2_g with k2_g = 2^-8 * 1.25 * q_g / 2 + ....
+//     so l~_g(x_i) = ctc_g + P1 + P2 approximates log w_g N(x_i|g).  Each
+//     operand rounded to BF16 (8-bit significand) is within 2^-8 of its FP32
+//     value, so each product is within 2^-7 + 2^-16 of the exact one; the
+//     FP32 accumulation of 64 exact products adds at most 64 * 2^-23 of the
+//     sum of their magnitudes.  Hence
+//        |l~ - l| <= 2^-7 * 1.01 * sum_d (x'^2 iv/2 + |x' mu'| iv) + tiny terms,
+//     and by AM-GM sum_d |x' mu'| iv <= sum_d (x'^2 + mu'^2) iv / 2 = |P1| + q_g/2
+//     (q_g = sum_d mu'^2 iv), so |l~ - l| <= K1 |P1| + k2_g with
+//     K1 = 2^-6 * 1.25 and k2_g = 2^-7 * 1.25 * q_g / 2 + 2^-21 |ctc_g| + 1e-4.
 //     A Gaussian whose upper bound lies more than T = ln(N * 1e9) nats below
 //     the best lower bound has responsibility below 1e-9 / N and is dropped
 //     (per Gaussian the dropped mass is below 1e-9, under the 1e-8
 //     responsibility sum below which the update keeps a Gaussian's
 //     parameters).  Output per (sample, half of the Gaussians): the list of
 //     surviving Gaussians (at most kTcCap, else the half is marked dense).
-//  2. k_em_exact -- one warp per sample, lanes over dimensions, the
-//     parameters in shared memory: the exact FP32 log-density of every
-//     candidate (the formula of the CUDA-core form), of every Gaussian of a
-//     dense half; log-sum-exp (Eqs. 16-18), log p(x_i) into the CTA's FP64
-//     log-likelihood, responsibilities l_{g,i} (Eq. 3) of the candidates.
-//  3. k_em_mstep_lists -- one CTA per (sample chunk, half of the Gaussians),
-//     the paper's thread t: per 256-sample tile the (sample, Gaussian) pairs
-//     are counting-sorted by Gaussian, and the warp that owns a Gaussian sums
-//     l, l (x - mu_f), l (x - mu_f)^2 over its pairs in registers (Eqs. 9-11,
-//     shifted by the FP32 mean mu_f of the iteration start) and adds them to
-//     the CTA's FP32 statistics in shared memory (no atomics on them); the
-//     chunk's statistics go to its FP64 partial once.
+//  2. k_em_exact -- one CTA per SM over a contiguous run of 128-sample tiles,
+//     the FP32 operands in shared memory, one lane per (sample, candidate)
+//     pair: the exact FP32 log-density of every candidate (the formula of
+//     the CUDA-core form), of every Gaussian of a dense half; log-sum-exp
+//     (Eqs. 16-18), log p(x_i) into the CTA's FP64 log-likelihood,
+//     responsibilities l_{g,i} (Eq. 3) of the candidates that matter.
+//  3. k_em_mstep_lists -- the same CTA runs (the paper's thread t): per
+//     128-sample tile the (sample, Gaussian) pairs are counting-sorted by
+//     Gaussian, and the warp that owns a Gaussian sums l, l (x - mu_f),
+//     l (x - mu_f)^2 over its pairs in registers (Eqs. 9-11, shifted by the
+//     FP32 mean mu_f of the iteration start) and adds them to the CTA's FP32
+//     statistics in shared memory (no atomics on them); the chunk's
+//     statistics go to its FP64 partial once.
 // Responsibilities exist only for the surviving pairs (a few per sample).
 #include <cuda_bf16.h>
 
@@ -47,7 +52,7 @@ constexpr int kEpiThreads = 512;  // screening kernel: 16 epilogue warps
 constexpr int kThreads = kEpiThreads + 32;
 constexpr int kTM = 128;          // samples per tile = MMA M
 constexpr int kCap = kTcCap;      // candidates per (sample, half) before the dense fallback
-constexpr float kK1 = 0.009765625f * 1.25f;   // 2^-7 * 1.25 (multiplies |P1|)
+constexpr float kK1 = 0.015625f * 1.25f;      // 2^-6 * 1.25 (multiplies |P1|)
 constexpr int kExThreads = 1024;  // exact-recompute kernel: 32 warps, one sample per warp at a time
 constexpr int kMsThreads = 1024;  // M-step kernel: 32 warps
 
@@ -238,8 +243,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_em_screen_tc(TcArgs args)
         for (int g = tid; g < NG; g += kEpiThreads) {
             if (g < G) {
                 const float ct = __ldg(a.op.ctc + g);
-                // 2^-8 * 1.25 * q/2  +  2^-21 |ctc|  +  1e-4
-                const float k2 = 0.00390625f * 1.25f * 0.5f * __ldg(a.op.q + g) + 4.76837158203125e-07f * fabsf(ct) + 1e-4f;
+                // 2^-7 * 1.25 * q/2  +  2^-21 |ctc|  +  1e-4
+                const float k2 = 0.0078125f * 1.25f * 0.5f * __ldg(a.op.q + g) + 4.76837158203125e-07f * fabsf(ct) + 1e-4f;
                 clb[g] = ct - k2;
                 cub[g] = ct + k2;
             } else {
