@@ -359,8 +359,9 @@ gmm_status gmm_debug_set(gmm_model *m, int32_t key, int64_t value);
 #define GMM_STAT_DENSE 5
 /* GMM_STAT_PHASE0 + k (k = 0..7): SM cycles one epilogue thread of each CTA
  * of the screening kernel spent in phase k of a tile (0 building the next
- * tile's BF16 operand, 1 barrier, 2 MMA wait, 3 screening bounds, 4 candidate
- * lists and their records; 5-7 unused), summed over CTAs. */
+ * tile's BF16 operand, 1 barrier, 2 MMA wait, 3 lower bounds (first read of
+ * the accumulators), 4 upper bounds and candidate masks (second read) and the
+ * records; 5-7 unused), summed over CTAs. */
 #define GMM_STAT_PHASE0 6
 /* Tensor-core k-means, summed over its passes: GMM_STAT_KM_SCREENED samples
  * screened, GMM_STAT_KM_DEFERRED samples the screen left with more than one
