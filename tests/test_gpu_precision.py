@@ -1,0 +1,66 @@
+"""Precision report: the error of every result of one EM iteration against the
+FP64 oracle, per E-step form, on a prefix of the c2 workload (N = 50,000,
+D = 60, N_G = 256) from a k-means start.
+
+Results compared: log p(x_i) of the updated model (lse_i), the mean
+log-likelihood of the iteration, and the updated means, variances and
+weights (the sufficient statistics S0, S1, S2 enter only through them).  The
+relative errors are printed (pytest -s) and held to the parity tolerances:
+1e-4 on parameters (floors 1e-4 * global std / variance / 1 / N_G), 1e-6 on
+the mean log-likelihood, and 3 (1e-5 + 1e-6 |log p|) on each log p(x_i): the
+FP32 evaluation sums log-density terms of a few hundred nats (u * 500 is
+3e-5)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1707_09094_gb300 import GMM, GMM_MAHA, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1707_09094_gb300 import build
+    build.build()
+
+
+def rel_err(got, ref, floor):
+    got, ref = np.asarray(got, np.float64), np.asarray(ref, np.float64)
+    return float(np.max(np.abs(got - ref) / (np.abs(ref) + floor)))
+
+
+def test_precision_report_c2_prefix():
+    X, _, _ = synth.make("c2", N=50000)
+    G = 256
+    _, gv = oracle.global_stats(X)
+    gv = np.maximum(gv, 1e-10)
+    seeds = synth.seeds_subset(X, G, 7)
+    start = oracle.kmeans(X, seeds, 1.0 / gv, gv, 3, 1e-10)[:3]
+    M, V, H, ll = oracle.em_iterate(X, *start, 1, 1e-10)
+    lp_ref = oracle.log_p(X, M, V, H)
+    gstd = np.sqrt(X.astype(np.float64).var(axis=0))
+    Xd = torch.from_numpy(X).cuda()
+    rows = []
+    for prec in ("fp32", "bf16"):
+        g = GMM().set_params(*start)
+        g.em_iterate(Xd, 1, prec=prec, recompute_center=True)
+        m, v, h = g.get_params()
+        lp = g.log_p(Xd).cpu().numpy()
+        r = {"form": prec,
+             "means": rel_err(m, M, gstd[None, :]),
+             "dcovs": rel_err(v, V, gstd[None, :] ** 2),
+             "hefts": rel_err(h, H, 1.0 / G),
+             "LL": abs(g.ll_history()[0] - ll[0]) / abs(ll[0]),
+             "log p(x_i)": rel_err(lp, lp_ref, 1.0),
+             "log p limit": float(np.max(np.abs(lp - lp_ref) / (1e-5 + 1e-6 * np.abs(lp_ref))))}
+        rows.append(r)
+        k = int(np.argmax(np.abs(lp - lp_ref) / (1e-5 + 1e-6 * np.abs(lp_ref))))
+        print("\n%s worst log p: got %.9g ref %.9g" % (prec, lp[k], lp_ref[k]))
+        assert r["means"] <= 1e-4 and r["dcovs"] <= 1e-4 and r["hefts"] <= 1e-4, r
+        assert r["LL"] <= 1e-6 and r["log p limit"] <= 3.0, r
+    keys = ["means", "dcovs", "hefts", "LL", "log p(x_i)"]
+    print("\n| form | " + " | ".join(keys) + " |\n|---|" + "---:|" * len(keys))
+    for r in rows:
+        print("| %s | " % r["form"] + " | ".join("%.1e" % r[k] for k in keys) + " |")
