@@ -257,6 +257,13 @@ int64_t gmm_init_net_num_params(const gmm_init_net *n);
 gmm_status gmm_init_net_get_weights(const gmm_init_net *n, float *weights, float *grads);
 gmm_status gmm_init_net_set_weights(gmm_init_net *n, const float *weights);
 
+/* Training checkpoint: Adam's first and second moments (host float arrays of
+ * num_params, the weights' layout; NULL = skip on get) and its step count
+ * (the bias corrections use it).  With the weights, this resumes training
+ * where it stopped.  GMM_ERR_ARG for NULL pointers (set) or step < 0. */
+gmm_status gmm_init_net_get_adam(const gmm_init_net *n, float *m1, float *m2, int64_t *step);
+gmm_status gmm_init_net_set_adam(gmm_init_net *n, const float *m1, const float *m2, int64_t step);
+
 /*
  * One pass over a batch of B sets of P points (pts: device float [B][P][D]).
  * mode 0: forward + loss; 1: also gradients; 2: also one Adam step (lr).

@@ -331,6 +331,31 @@ class InitNet:
         _lib.check(_lib.load().gmm_init_net_set_weights(self._h, w.ctypes.data_as(ctypes.c_void_p)), "set")
         return self
 
+    def get_state(self):
+        """Training checkpoint: weights, Adam moments and step count."""
+        n = self.num_params
+        m1, m2, t = np.empty(n, np.float32), np.empty(n, np.float32), ctypes.c_int64()
+        _lib.check(_lib.load().gmm_init_net_get_adam(self._h, m1.ctypes.data_as(ctypes.c_void_p),
+                                                     m2.ctypes.data_as(ctypes.c_void_p), ctypes.byref(t)),
+                   "gmm_init_net_get_adam")
+        return {"weights": self.get_weights(), "adam_m1": m1, "adam_m2": m2, "adam_step": t.value}
+
+    def set_state(self, state):
+        self.set_weights(state["weights"])
+        m1 = np.ascontiguousarray(state["adam_m1"], np.float32)
+        m2 = np.ascontiguousarray(state["adam_m2"], np.float32)
+        _lib.check(_lib.load().gmm_init_net_set_adam(self._h, m1.ctypes.data_as(ctypes.c_void_p),
+                                                     m2.ctypes.data_as(ctypes.c_void_p), int(state["adam_step"])),
+                   "gmm_init_net_set_adam")
+        return self
+
+    def save_checkpoint(self, path):
+        np.savez(path, **self.get_state())
+
+    def load_checkpoint(self, path):
+        with np.load(path) as z:
+            return self.set_state({k: z[k] for k in z.files})
+
     def step(self, pts, targets=None, lam=0.0, var_floor=1e-3, mode=0, lr=1e-3, want_pred=False):
         """pts: CUDA float32 tensor [B][P][D]; targets: (means, dcovs, hefts) CUDA float64 tensors or None.
         Returns (loss, pred) with pred = (means, dcovs, hefts) CUDA tensors when want_pred."""

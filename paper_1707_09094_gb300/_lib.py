@@ -63,6 +63,8 @@ SIGNATURES = {
     "gmm_init_net_num_params": (i64, [P]),
     "gmm_init_net_get_weights": (ctypes.c_int, [P, P, P]),
     "gmm_init_net_set_weights": (ctypes.c_int, [P, P]),
+    "gmm_init_net_get_adam": (ctypes.c_int, [P, P, P, P]),
+    "gmm_init_net_set_adam": (ctypes.c_int, [P, P, P, i64]),
     "gmm_init_net_step": (ctypes.c_int, [P, P, i32, i32, P, P, P, f64, f64, i32, f64, P, P, P,
                                          ctypes.POINTER(f64), P]),
     "gmm_init_net_seed_model": (ctypes.c_int, [P, P, P, i64, i32, ctypes.c_uint64, f64, P]),

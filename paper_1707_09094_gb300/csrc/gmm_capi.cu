@@ -1261,6 +1261,21 @@ extern "C" gmm_status gmm_init_net_get_weights(const gmm_init_net *n, float *wei
     return GMM_OK;
 }
 
+extern "C" gmm_status gmm_init_net_get_adam(const gmm_init_net *n, float *m1, float *m2, int64_t *step)
+{
+    if (!n) return fail(GMM_ERR_ARG, "net is NULL");
+    CK(gmm::init_net_get_adam(n->net, m1, m2, step));
+    return GMM_OK;
+}
+
+extern "C" gmm_status gmm_init_net_set_adam(gmm_init_net *n, const float *m1, const float *m2, int64_t step)
+{
+    if (!n || !m1 || !m2) return fail(GMM_ERR_ARG, "NULL argument");
+    if (step < 0) return fail(GMM_ERR_ARG, "step must be >= 0");
+    CK(gmm::init_net_set_adam(n->net, m1, m2, step));
+    return GMM_OK;
+}
+
 extern "C" gmm_status gmm_init_net_set_weights(gmm_init_net *n, const float *weights)
 {
     if (!n || !weights) return fail(GMM_ERR_ARG, "NULL argument");

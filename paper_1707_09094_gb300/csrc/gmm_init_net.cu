@@ -917,6 +917,22 @@ cudaError_t init_net_set_weights(InitNet *n, const float *w_host)
     return cudaGetLastError();
 }
 
+cudaError_t init_net_get_adam(const InitNet *n, float *m1_host, float *m2_host, int64_t *step)
+{
+    if (m1_host) CKE(cudaMemcpy(m1_host, n->m1, 4 * n->n_params, cudaMemcpyDeviceToHost));
+    if (m2_host) CKE(cudaMemcpy(m2_host, n->m2, 4 * n->n_params, cudaMemcpyDeviceToHost));
+    if (step) *step = n->step;
+    return cudaSuccess;
+}
+
+cudaError_t init_net_set_adam(InitNet *n, const float *m1_host, const float *m2_host, int64_t step)
+{
+    CKE(cudaMemcpy(n->m1, m1_host, 4 * n->n_params, cudaMemcpyHostToDevice));
+    CKE(cudaMemcpy(n->m2, m2_host, 4 * n->n_params, cudaMemcpyHostToDevice));
+    n->step = step;
+    return cudaSuccess;
+}
+
 cudaError_t init_net_get(const InitNet *n, float *w_host, float *g_host)
 {
     if (w_host) CKE(cudaMemcpy(w_host, n->wgt, 4 * n->n_params, cudaMemcpyDeviceToHost));

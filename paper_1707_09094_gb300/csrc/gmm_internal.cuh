@@ -168,6 +168,8 @@ int init_net_G(const InitNet *n);
 cudaError_t init_net_gather(const float *X, int D, const int64_t *idx, int P, float *out, cudaStream_t s);
 cudaError_t init_net_set_weights(InitNet *n, const float *w_host);
 cudaError_t init_net_get(const InitNet *n, float *w_host, float *g_host);
+cudaError_t init_net_get_adam(const InitNet *n, float *m1_host, float *m2_host, int64_t *step);
+cudaError_t init_net_set_adam(InitNet *n, const float *m1_host, const float *m2_host, int64_t step);
 cudaError_t init_net_run(InitNet *n, const float *pts, int B, int P, const double *tm, const double *tv, const double *tw,
                          double lambda, double var_floor, int grads, double lr, double *pm, double *pv, double *pw,
                          double *loss_host, cudaStream_t s);
