@@ -31,8 +31,8 @@ UNIT = "N·N_G·D/s"
 N_FULL, D_FULL, G_FULL = 2_000_000, 60, 256
 # DRAM bytes (read + write) of one tensor-core EM pass on the full workload:
 # ncu dram__bytes of the screen, exact and M-step kernels at N = 1,000,000
-# (948 MB, profiles/em_pass_tc_c2_1m_ncu.md), scaled by the samples (traffic
-# grows in proportion).  Re-measure whenever those kernels change.
+# (948 MB in one capture), scaled by the samples (traffic grows in
+# proportion).  Re-measure whenever those kernels change.
 TC_PASS_TRAFFIC = 948.4e6 * 2
 
 

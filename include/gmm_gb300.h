@@ -195,10 +195,10 @@ gmm_status gmm_avg_log_p(const gmm_model *m, const float *X, int64_t N, int32_t 
  * gmm_avg_log_p_noalloc: the same value as gmm_avg_log_p (mean of log_p over
  * X) for callers that must not allocate device memory.  The paper has no
  * counterpart: it exists for code that cannot call cudaMalloc at the moment
- * it needs the number -- for example while a stream is being captured into a
- * CUDA graph (allocation is not a capturable operation), inside a framework
- * whose caching allocator owns all free device memory, or in a service that
- * fixes its memory footprint up front.  gmm_avg_log_p stages a per-sample
+ * it needs the number -- for example inside a framework whose caching
+ * allocator already holds all free device memory (a cudaMalloc would fail or
+ * force the framework to release its cache), or in a service that fixes its
+ * memory footprint up front.  gmm_avg_log_p stages a per-sample
  * buffer of N doubles in the model; this entry point instead reduces per
  * 128-sample block into a fixed array of 65537 doubles (512 KiB) compiled
  * into the library, which every GPU that loads the library keeps until the
@@ -208,8 +208,11 @@ gmm_status gmm_avg_log_p(const gmm_model *m, const float *X, int64_t N, int32_t 
  *        returns GMM_ERR_UNSUPPORTED.
  *   out  host double, written on return (the call synchronises `stream`).
  * The first call on each device looks up the device address of the array
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  All calls share the array and every call
+ * (cudaGetSymbolAddress, with that device current) and keeps it for the
+ * life of the process; make that first call before any stream capture.  A
+ * cudaDeviceReset (or any other teardown of the device's primary context)
+ * invalidates the kept address: this entry point must not be called after
+ * one.  All calls share the array and every call
  * overwrites the slots it reads, so nothing needs clearing; calls whose
  * kernels overlap on the GPU (concurrent streams or threads) race on it and
  * must be serialised by the caller.

@@ -60,6 +60,8 @@ def _load():
                 "orc_kmeans": (ctypes.c_int, [P, i64, i32, i32, P, P, P, P, P, i32, f64, P]),
                 "orc_em_iterate": (ctypes.c_int, [P, i64, i32, i32, P, P, P, i32, f64, f64, i32, P, P]),
                 "orc_em_step_twopass": (ctypes.c_int, [P, i64, i32, i32, P, P, P, f64]),
+                "orc_em_fp32_budget": (ctypes.c_int, [P, i64, i32, i32, P, P, P, f64, i32, i32, i32, f64, P, P,
+                                                      P, P]),
                 "orc_assign": (ctypes.c_int, [P, i64, i32, i32, P, P, P, i32, P]),
                 "orc_learn": (ctypes.c_int, [P, i64, i32, i32, i32, i32, u64, i32, i32, f64, f64,
                                              i32, P, P, P, P, P]),
@@ -229,6 +231,43 @@ def em_iterate(X, means, dcovs, hefts, em_iter: int, var_floor: float, em_tol: f
                                 em_iter, var_floor, em_tol, n_chunks, _p(ll), ctypes.byref(nd))
     _check(rc, "em_iterate")
     return m, v, h, ll[: nd.value]
+
+
+def fp32_accumulations(N: int, chunk: int = 0) -> int:
+    """Upper bound on the FP32 additions into one statistics accumulator of an
+    EM pass over N samples: at least 128 sample chunks (one per SM or more)
+    of 32-sample tiles, each tile first summed over up to 128 terms.  `chunk`
+    > 0 bounds the samples of one chunk instead (the batched form's items)."""
+    per_chunk = chunk if chunk > 0 else -(-N // 128)
+    return -(-per_chunk // 32) + 128
+
+
+def em_fp32_budget(X, means, dcovs, hefts, var_floor: float, n_acc: int = 0, n_lse: int = 0,
+                   drop: float = 1e-9, n_chunks: int = 0):
+    """One EM iteration from (means, dcovs, hefts) and the FP32 error budget of
+    each new parameter (see orc_em_fp32_budget).  n_acc: FP32 additions into
+    one statistics accumulator (default fp32_accumulations(N)); n_lse: the
+    longest chain of FP32 additions in one log-sum-exp (default G + 8, any
+    order).  Returns (means, dcovs, hefts, mean_ll, (b_means, b_dcovs, b_hefts))."""
+    X = _x(X)
+    N, D = X.shape
+    m = np.array(means, dtype=np.float64, order="C", copy=True)
+    v = np.array(dcovs, dtype=np.float64, order="C", copy=True)
+    h = np.array(hefts, dtype=np.float64, order="C", copy=True)
+    G = m.shape[0]
+    bm = np.zeros((G, D), np.float64)
+    bv = np.zeros((G, D), np.float64)
+    bw = np.zeros(G, np.float64)
+    ll = ctypes.c_double()
+    if n_chunks <= 0:
+        n_chunks = max(num_threads(), 1) * (4 if N >= 100_000 else 1)
+    if n_acc <= 0:
+        n_acc = fp32_accumulations(N)
+    if n_lse <= 0:
+        n_lse = G + 8
+    _check(_load().orc_em_fp32_budget(_p(X), N, D, G, _p(m), _p(v), _p(h), var_floor, n_chunks, n_acc, n_lse, drop,
+                                      ctypes.byref(ll), _p(bm), _p(bv), _p(bw)), "em_fp32_budget")
+    return m, v, h, ll.value, (bm, bv, bw)
 
 
 def em_step_twopass(X, means, dcovs, hefts, var_floor: float):

@@ -33,8 +33,6 @@
 #define ORC_ERR_OOM (-5)
 
 static const double ORC_LOG_2PI = 1.83787706640934548356065947281123527;
-/* Smallest responsibility sum L_g for which a Gaussian is re-estimated. */
-static const double ORC_MIN_RESP = 1e-8;
 
 /* ------------------------------------------------------------------------ */
 /* Log density of one diagonal Gaussian: Eq. 15 (log of Eq. 2) with the     */
@@ -393,11 +391,10 @@ int orc_kmeans(const float *X, int64_t N, int32_t D, int32_t G, const double *w,
  *   reduce: Eqs. 12-14 sum the chunks in order t = 1..N_T and divide;
  *   update: hefts by Eq. 5, variances by the one-pass form of Eq. 8 / Eq. 14,
  *           floored after the iteration (Sec. 2.2).
- * Reading for a Gaussian whose responsibility sum L_g is below 1e-8 (the
- * paper is silent): its heft becomes L_g / N and its mean and covariance are
- * kept.  Below that mass the re-estimate (Eqs. 13-14) is a ratio of sums of
- * underflowing responsibilities that every precision resolves differently,
- * while the Gaussian holds less than 1e-8 of one sample.
+ * Eqs. 12-14 define the new mean and covariance for every L_g > 0, and so
+ * does this function.  Reading for L_g == 0 (every responsibility underflowed;
+ * the paper is silent): the heft becomes 0 and the mean and covariance are
+ * kept, which only avoids 0/0.
  * *mean_ll receives log p(X | lambda_old) / N, the likelihood of the
  * parameters the E-step used.
  */
@@ -456,7 +453,7 @@ static int orc_em_one(const float *X, int64_t N, int32_t D, int32_t G, double *m
     int rc = ORC_OK;
     for (int32_t g = 0; g < G; ++g) {
         hefts[g] = L[g] / (double)N;                                  /* Eq. 5 */
-        if (!(L[g] >= ORC_MIN_RESP)) continue;
+        if (!(L[g] > 0.0)) continue;                                  /* 0/0 guard only */
         for (int32_t d = 0; d < D; ++d) {
             double mu = M[(size_t)g * D + d] / L[g];                  /* Eq. 13 */
             double v = S[(size_t)g * D + d] / L[g] - mu * mu;         /* Eq. 14 */
@@ -528,7 +525,7 @@ int orc_em_step_twopass(const float *X, int64_t N, int32_t D, int32_t G, double 
         }
     for (int32_t g = 0; g < G; ++g) {
         hefts[g] = L[g] / (double)N;                                      /* Eq. 5 */
-        if (!(L[g] >= ORC_MIN_RESP)) continue;
+        if (!(L[g] > 0.0)) continue;                                      /* 0/0 guard only */
         for (int32_t d = 0; d < D; ++d) {
             double v = S[(size_t)g * D + d] / L[g];
             means[(size_t)g * D + d] = M[(size_t)g * D + d];
@@ -536,6 +533,154 @@ int orc_em_step_twopass(const float *X, int64_t N, int32_t D, int32_t G, double 
         }
     }
     free(post); free(L); free(M); free(S);
+    return ORC_OK;
+}
+
+/*
+ * One EM iteration (exactly orc_em_iterate with em_iter = 1, var_floor and
+ * n_chunks as there) together with a bound on how far an FP32 evaluation of
+ * the same iteration may land from it.  This is a parity tolerance, not part
+ * of the method: the CUDA library evaluates the E-step of Eq. 15 in FP32 as
+ *     l~ = fl(c_g) - 1/2 sum_d fl(x_d s_d - m_d)^2,  s = fl(1/sigma), m = fl(mu/sigma),
+ * forms log p (Eq. 16) and l_{g,i} (Eq. 3) with FP32 exp/log, leaves out
+ * responsibilities whose total per Gaussian is below `drop`, and sums
+ * Eqs. 9-11 in FP32 about the FP32 start means f (at most n_acc additions into
+ * any FP32 accumulator) before the FP64 reduce of Eqs. 12-14.
+ * First-order bounds with u = 2^-24, from the exact FP64 quantities
+ * t_d = (x_d - mu_d) / sigma_d and a_d = (|x_d| + |mu_d|) / sigma_d:
+ *   logit   e_ig = u (|c_g| + |l_ig| + sum_d |t_d| a_d + (1 + D/2) sum_d t_d^2)
+ *   log p   E_i = sum_h l_hi e_ih carried from the logits, and its own rounding
+ *           r_i = sum_h l_hi u |l_ih - max_h l_ih| + (n_lse + 8) u + u |log p_i| + 2^-20 + G drop / N
+ *           (n_lse: the longest chain of FP32 additions in the sum of Eq. 16)
+ *   l_{g,i} relative error, since log l_{g,i} = l_ig - log p_i moves by
+ *           (1 - l_gi) dl_ig - sum_{h != g} l_hi dl_ih plus the roundings:
+ *           delta_ig = (E_i - l_gi e_ig) + (1 - l_gi) e_ig + r_i + u |l_ig - log p_i| + 2^-21
+ * and, with rho = n_acc u, L_g, mu', v' the new parameters and R_gd the largest
+ * |x_id - mu'_gd|:
+ *   b_w[g]    = (sum_i l delta + drop + rho L_g) / N
+ *   b_mu[g,d] = (sum_i l delta |x - mu'| + drop R + 2 rho sum_i l |x - f|) / L_g
+ *   b_var[g,d]= (sum_i l delta |(x - mu')^2 - v'| + drop (R^2 + v')
+ *                + 2 rho (sum_i l (x - f)^2 + 2 |mu' - f| sum_i l |x - f|)) / L_g
+ * (the first terms are the first-order change of a weighted mean / variance
+ * when each weight l_{g,i} moves by a relative delta_ig).  A Gaussian with
+ * L_g == 0 gets zero bounds (its parameters are kept on both sides).
+ * means/dcovs/hefts are updated in place; *mean_ll as in orc_em_iterate.
+ */
+int orc_em_fp32_budget(const float *X, int64_t N, int32_t D, int32_t G, double *means, double *dcovs,
+                       double *hefts, double var_floor, int32_t n_chunks, int32_t n_acc, int32_t n_lse, double drop,
+                       double *mean_ll, double *b_mu, double *b_var, double *b_w)
+{
+    if (N < 1 || D < 1 || G < 1 || n_chunks < 1 || n_acc < 1 || n_lse < 1 || !(drop >= 0.0)) return ORC_ERR_ARG;
+    const double u = 1.0 / 16777216.0;
+    size_t GD = (size_t)G * D;
+    double *m0 = (double *)malloc(sizeof(double) * GD), *v0 = (double *)malloc(sizeof(double) * GD);
+    double *h0 = (double *)malloc(sizeof(double) * (size_t)G);
+    if (!m0 || !v0 || !h0) { free(m0); free(v0); free(h0); return ORC_ERR_OOM; }
+    memcpy(m0, means, sizeof(double) * GD);
+    memcpy(v0, dcovs, sizeof(double) * GD);
+    memcpy(h0, hefts, sizeof(double) * (size_t)G);
+    int rc = orc_em_one(X, N, D, G, means, dcovs, hefts, var_floor, n_chunks, mean_ll);
+    if (rc != ORC_OK) { free(m0); free(v0); free(h0); return rc; }
+
+    /* per Gaussian of the start: sigma_gd and the constant of Eq. 15 */
+    double *sd = (double *)malloc(sizeof(double) * GD), *cst = (double *)malloc(sizeof(double) * (size_t)G);
+    /* per chunk: Bw [G], Bm, Bv, Am, Av, R [G][D] */
+    size_t per = (size_t)G + 5 * GD;
+    double *acc = (double *)calloc((size_t)n_chunks * per, sizeof(double));
+    if (!acc || !sd || !cst) { free(acc); free(sd); free(cst); free(m0); free(v0); free(h0); return ORC_ERR_OOM; }
+    for (int32_t g = 0; g < G; ++g) {
+        cst[g] = log(h0[g]) - 0.5 * (double)D * ORC_LOG_2PI;
+        for (int32_t d = 0; d < D; ++d) {
+            sd[(size_t)g * D + d] = sqrt(v0[(size_t)g * D + d]);
+            cst[g] -= 0.5 * log(v0[(size_t)g * D + d]);
+        }
+    }
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static, 1)
+#endif
+    for (int32_t t = 0; t < n_chunks; ++t) {
+        int64_t i0 = (int64_t)((double)N * t / n_chunks);
+        int64_t i1 = (int64_t)((double)N * (t + 1) / n_chunks);
+        double *Bw = acc + (size_t)t * per, *Bm = Bw + G, *Bv = Bm + GD, *Am = Bv + GD, *Av = Am + GD, *R = Av + GD;
+        double *l = (double *)malloc(sizeof(double) * (size_t)G);
+        double *e = (double *)malloc(sizeof(double) * (size_t)G);
+        for (int64_t i = i0; i < i1; ++i) {
+            const float *x = X + (size_t)i * D;
+            double mx = -INFINITY;
+            for (int32_t g = 0; g < G; ++g) {
+                const double *mu = m0 + (size_t)g * D, *sg = sd + (size_t)g * D;
+                double t2 = 0.0, ta = 0.0;
+                for (int32_t d = 0; d < D; ++d) {
+                    double td = ((double)x[d] - mu[d]) / sg[d];
+                    t2 += td * td;
+                    ta += fabs(td) * (fabs((double)x[d]) + fabs(mu[d])) / sg[d];
+                }
+                l[g] = cst[g] - 0.5 * t2;                       /* Eq. 15 */
+                e[g] = l[g] == -INFINITY ? 0.0 : u * (fabs(cst[g]) + fabs(l[g]) + ta + (1.0 + 0.5 * (double)D) * t2);
+                if (l[g] > mx) mx = l[g];
+            }
+            if (mx == -INFINITY) continue;
+            double se = 0.0;
+            for (int32_t g = 0; g < G; ++g) se += exp(l[g] - mx);
+            const double lse = mx + log(se);                    /* Eq. 16 */
+            /* E = sum_h l_h e_h (the logit errors carried into log p), rnd = the
+             * rounding of log p itself */
+            double E = 0.0, rnd = (double)(n_lse + 8) * u + u * fabs(lse) + 1.0 / 1048576.0 + (double)G * drop / (double)N;
+            for (int32_t g = 0; g < G; ++g)
+                if (l[g] > -INFINITY) {
+                    const double gam = exp(l[g] - lse);
+                    E += gam * e[g];
+                    rnd += gam * u * fabs(l[g] - mx);
+                }
+            for (int32_t g = 0; g < G; ++g) {
+                const double gam = exp(l[g] - lse);
+                const double *mu1 = means + (size_t)g * D, *v1 = dcovs + (size_t)g * D;
+                for (int32_t d = 0; d < D; ++d) {
+                    double r = fabs((double)x[d] - mu1[d]);
+                    if (r > R[(size_t)g * D + d]) R[(size_t)g * D + d] = r;
+                }
+                if (gam == 0.0) continue;
+                /* log l_{g,i} = l_g - log p: its logit error enters with weight
+                 * 1 - gam, the others' through log p */
+                const double del = (E - gam * e[g]) + (1.0 - gam) * e[g] + rnd + u * fabs(l[g] - lse) + 1.0 / 2097152.0;
+                const double gd = gam * del;
+                Bw[g] += gd;
+                for (int32_t d = 0; d < D; ++d) {
+                    const double xd = (double)x[d];
+                    const double r = xd - mu1[d];
+                    const double q = xd - (double)(float)m0[(size_t)g * D + d];
+                    Bm[(size_t)g * D + d] += gd * fabs(r);
+                    Bv[(size_t)g * D + d] += gd * fabs(r * r - v1[d]);
+                    Am[(size_t)g * D + d] += gam * fabs(q);
+                    Av[(size_t)g * D + d] += gam * (q * q);
+                }
+            }
+        }
+        free(l);
+        free(e);
+    }
+    /* reduce the chunks (R by maximum) and form the bounds */
+    double *tot = (double *)calloc(per, sizeof(double));
+    if (!tot) { free(acc); free(sd); free(cst); free(m0); free(v0); free(h0); return ORC_ERR_OOM; }
+    for (int32_t t = 0; t < n_chunks; ++t) {
+        const double *src = acc + (size_t)t * per;
+        for (size_t k = 0; k < (size_t)G + 4 * GD; ++k) tot[k] += src[k];
+        for (size_t k = (size_t)G + 4 * GD; k < per; ++k) if (src[k] > tot[k]) tot[k] = src[k];
+    }
+    const double *Bw = tot, *Bm = Bw + G, *Bv = Bm + GD, *Am = Bv + GD, *Av = Am + GD, *R = Av + GD;
+    const double rho = (double)n_acc * u;
+    for (int32_t g = 0; g < G; ++g) {
+        const double L = hefts[g] * (double)N;
+        b_w[g] = (Bw[g] + drop + rho * L) / (double)N;
+        for (int32_t d = 0; d < D; ++d) {
+            const size_t k = (size_t)g * D + d;
+            if (!(L > 0.0)) { b_mu[k] = 0.0; b_var[k] = 0.0; continue; }
+            const double sh = fabs(means[k] - (double)(float)m0[k]);
+            b_mu[k] = (Bm[k] + drop * R[k] + 2.0 * rho * Am[k]) / L;
+            b_var[k] = (Bv[k] + drop * (R[k] * R[k] + dcovs[k]) + 2.0 * rho * (Av[k] + 2.0 * sh * Am[k])) / L;
+        }
+    }
+    free(tot); free(acc); free(sd); free(cst); free(m0); free(v0); free(h0);
     return ORC_OK;
 }
 

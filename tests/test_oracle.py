@@ -225,6 +225,83 @@ def test_zero_responsibility_component_keeps_parameters():
     assert h[1] == 0.0 and h[0] == pytest.approx(1.0)
 
 
+def test_tiny_responsibility_component_is_reestimated():
+    """Eqs. 12-14 define the update for every L_g > 0: a Gaussian holding only
+    ~1e-20 of one sample's responsibility still gets the responsibility-
+    weighted mean and variance of the samples (only L_g == 0 keeps them)."""
+    X = np.random.default_rng(12).normal(0, 1, (500, 1)).astype(np.float32)
+    m0 = np.array([[0.0], [12.0]])
+    v0 = np.array([[1.0], [1.0]])
+    h0 = np.array([0.5, 0.5])
+    post = oracle.posteriors(X, m0, v0, h0)[:, 1]
+    L = post.sum()
+    assert 0.0 < L < 1e-8
+    m, v, h, _ = oracle.em_iterate(X, m0, v0, h0, 1, 1e-10)
+    x = X[:, 0].astype(np.float64)
+    mu = (post * x).sum() / L
+    np.testing.assert_allclose(m[1, 0], mu, rtol=1e-10)
+    np.testing.assert_allclose(v[1, 0], max((post * (x - mu) ** 2).sum() / L, 1e-10), rtol=1e-6)
+    assert h[1] == pytest.approx(L / 500, rel=1e-12)
+
+
+def _fp32_em_emulation(X, means, dcovs, hefts, var_floor):
+    """An EM iteration evaluated the way an FP32 E-step does it (numpy float32:
+    l = c - 1/2 sum (x s - m)^2 with s = 1/sigma, m = mu/sigma, float32
+    log-sum-exp, responsibilities and statistics sums about the float32 start
+    means), then the FP64 update of Eqs. 12-14."""
+    f32 = np.float32
+    G, D = means.shape
+    s = (1.0 / np.sqrt(dcovs)).astype(f32)
+    mm = (means / np.sqrt(dcovs)).astype(f32)
+    c = (np.log(hefts) - 0.5 * D * np.log(2 * np.pi) - 0.5 * np.log(dcovs).sum(1)).astype(f32)
+    x = X.astype(f32)
+    t = x[:, None, :] * s[None] - mm[None]
+    l = c[None] - f32(0.5) * (t * t).sum(2, dtype=f32)
+    mx = l.max(1, keepdims=True)
+    lse = mx[:, 0] + np.log(np.exp(l - mx).sum(1, dtype=f32))
+    gam = np.exp(l - lse[:, None])
+    f = means.astype(f32)
+    q = x[:, None, :] - f[None]
+    S0 = gam.sum(0, dtype=f32).astype(np.float64)
+    S1 = (gam[:, :, None] * q).sum(0, dtype=f32).astype(np.float64)
+    S2 = (gam[:, :, None] * q * q).sum(0, dtype=f32).astype(np.float64)
+    live = S0 >= 1e-8          # vanishing mass: mean and covariance kept (as the library does)
+    Sd = np.where(live, S0, 1.0)[:, None]
+    mu = np.where(live[:, None], f.astype(np.float64) + S1 / Sd, means)
+    var = np.where(live[:, None], np.maximum(S2 / Sd - (S1 / Sd) ** 2, var_floor), dcovs)
+    return mu, var, S0 / X.shape[0], float(lse.astype(np.float64).mean()), live
+
+
+@pytest.mark.parametrize("kind", ["c2", "overlap"])
+def test_fp32_budget_covers_an_fp32_emulation(kind):
+    """The parity budget (orc_em_fp32_budget) bounds what an FP32 evaluation
+    of the iteration actually does: an independent numpy float32 emulation
+    lands inside it for every parameter of every Gaussian, including the
+    weakly supported ones, while on the c2-like case (a start near the
+    fit) the budget of the well supported Gaussians stays below the 1e-4
+    parity tolerance, i.e. it widens nothing there."""
+    if kind == "c2":
+        X, _, mix = synth.make("c2", N=4000, G=64)
+        start = (mix.means, mix.stds ** 2 * 1.2, mix.hefts)
+    else:
+        rng = np.random.default_rng(5)
+        X = rng.normal(0, 1, (3000, 6)).astype(np.float32)
+        start = (rng.normal(0, 1.5, (12, 6)), rng.uniform(0.2, 2, (12, 6)), rng.dirichlet(np.ones(12)))
+    M, V, H, ll, (bm, bv, bw) = oracle.em_fp32_budget(X, *start, 1e-10)
+    m, v, h, ll32, live = _fp32_em_emulation(X, *start, 1e-10)
+    assert np.all(np.abs(m - M)[live] <= 2 * bm[live] + 1e-12)
+    assert np.all(np.abs(v - V)[live] <= 2 * bv[live] + 1e-12)
+    assert np.all(np.abs(h - H) <= 2 * bw + 1e-15)
+    assert abs(ll32 - ll) <= 1e-6 * abs(ll)
+    if kind != "c2":
+        return
+    L = H * X.shape[0]
+    big = L >= 100
+    assert big.any()
+    assert (bm[big] <= 1e-4 * (np.abs(M[big]) + X.std(0))).all()
+    assert (bv[big] <= 1e-4 * V[big]).all()
+
+
 # ------------------------------------------------------- Sec. 3 (k-means)
 def test_km_assign_bruteforce():
     rng = np.random.default_rng(11)
@@ -282,6 +359,27 @@ def test_kmeans_dead_mean_resurrection():
     # lowest index keeps mean 0 for x=0? mean0 = 0.1, mean2 = 0.0)
     m2, _, _, a2 = oracle.kmeans(X, m, w, gv, 1, 1e-10)
     assert a2[0] == 2 and (a2[3:] == 1).all()
+
+
+def test_kmeans_dead_means_cycle_over_the_popular_members():
+    """More dead means than samples of the most popular mean: the dead means,
+    in increasing index, take its samples in increasing index and start over
+    (reading of Sec. 3.1); after the last iteration each gets the floored
+    global variance and heft 1/N, and the hefts are renormalised."""
+    X = np.array([[0.0], [0.1], [10.0], [10.1], [20.0], [20.1]], np.float32)
+    seeds = np.array([[0.05], [10.05], [20.05], [1e6], [2e6], [3e6]])
+    gv = np.array([64.0])
+    m, v, h, a = oracle.kmeans(X, seeds, np.ones(1), gv, 1, 1e-10)
+    np.testing.assert_array_equal(a, [0, 0, 1, 1, 2, 2])
+    # popular = mean 0 (count 2, lowest index among the ties); dead 3, 4, 5
+    # take samples 0, 1, 0
+    np.testing.assert_array_equal(m[3:, 0], X[[0, 1, 0], 0].astype(np.float64))
+    np.testing.assert_allclose(m[:3, 0], [np.float32(0.0) / 2 + np.float32(0.1) / 2,
+                                          (np.float64(np.float32(10.0)) + np.float64(np.float32(10.1))) / 2,
+                                          (np.float64(np.float32(20.0)) + np.float64(np.float32(20.1))) / 2],
+                               rtol=1e-15)
+    assert (v[3:, 0] == 64.0).all()
+    np.testing.assert_allclose(h, np.array([2, 2, 2, 1, 1, 1]) / 9.0, rtol=1e-15)
 
 
 def test_random_subset_seeding_pins_splitmix64():

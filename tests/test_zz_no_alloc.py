@@ -1,9 +1,10 @@
 """gmm_avg_log_p_noalloc: the allocation-free variant of gmm_avg_log_p, for
-callers that cannot call cudaMalloc (a stream being captured into a CUDA
-graph, a framework allocator that owns all free device memory, a service
-with a fixed memory footprint).  It must return what gmm_avg_log_p returns,
-on consecutive calls, through the C ABI.  This file is collected last so that
-a run that stops at its first failure has run every other test before it."""
+callers that cannot call cudaMalloc when they need the value (a framework
+whose caching allocator already holds all free device memory, a service with
+a fixed memory footprint).  It must return what gmm_avg_log_p returns, on
+consecutive calls, through the C ABI, without changing the device's free
+memory.  This file is collected last so that a run that stops at its first
+failure has run every other test before it."""
 import ctypes
 
 import numpy as np
@@ -50,6 +51,43 @@ def test_noalloc_matches_avg_log_p_on_two_calls(shape):
             st, v = _noalloc(g, Xd, k)
             assert st == 0, _lib.load().gmm_last_error()
             assert v == pytest.approx(ref, rel=1e-12, abs=1e-12)
+
+
+def test_noalloc_first_on_a_fresh_model_allocates_nothing():
+    """Called before anything else on a new model (nothing staged yet), the
+    entry point still returns gmm_avg_log_p's value, and the device's free
+    memory is the same before and after each later call.  (The first call may
+    see the driver load the kernels' code; that is the driver's, so memory is
+    compared across the calls after it.)"""
+    X, _, mix = synth.make("c1", N=50_000, D=20, G=16, seed=3)
+    Xd = torch.from_numpy(X).cuda()
+    torch.cuda.synchronize()
+    g = GMM().set_params(mix.means, mix.stds ** 2, mix.hefts)
+    st, first = _noalloc(g, Xd)
+    assert st == 0, _lib.load().gmm_last_error()
+    for _ in range(3):
+        free0 = torch.cuda.mem_get_info()[0]
+        st, v = _noalloc(g, Xd)
+        free1 = torch.cuda.mem_get_info()[0]
+        assert st == 0 and v == first
+        assert free1 == free0
+    assert first == pytest.approx(_reference(g, Xd), rel=1e-12, abs=1e-12)
+
+
+def test_noalloc_at_the_size_limit():
+    """N = 8,388,608 fills all 65,536 block slots of the array: still the
+    value of gmm_avg_log_p, twice in a row."""
+    N = 8_388_608
+    rng = np.random.default_rng(8)
+    X = torch.from_numpy(rng.normal(0.5, 2.0, (N, 1)).astype(np.float32)).cuda()
+    g = GMM().set_params(np.array([[0.0], [1.0]]), np.array([[1.0], [4.0]]), np.array([0.3, 0.7]))
+    ref = _reference(g, X)
+    for _ in range(2):
+        st, v = _noalloc(g, X)
+        assert st == 0, _lib.load().gmm_last_error()
+        assert v == pytest.approx(ref, rel=1e-12, abs=1e-12)
+    del X
+    torch.cuda.empty_cache()
 
 
 def test_noalloc_rejects_host_input_and_oversize():
