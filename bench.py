@@ -116,10 +116,33 @@ def make_data(n=None):
     return X if n is None else np.ascontiguousarray(X[:n])
 
 
-def cpu_oracle_rate(X, target_s: float = 12.0):
-    """FP64 oracle EM iteration (MapReduce chunks over the host cores) on a
-    bounded prefix of the workload; returns (units/s, cores, sample text)."""
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "cpu part")):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def cpu_oracle_rate(X, target_s: float = 12.0, threads: int = 0):
+    """FP64 oracle EM iteration (MapReduce chunks over `threads` host cores,
+    0 = all) on a bounded prefix of the workload; returns (units/s, cores,
+    sample text)."""
     import oracle
+    all_cores = oracle.num_threads() if threads == 0 else None
+    if threads:
+        oracle.set_threads(threads)
     cores = oracle.num_threads()
     G = G_FULL
     rng = np.random.default_rng(5)
@@ -137,8 +160,45 @@ def cpu_oracle_rate(X, target_s: float = 12.0):
             break
         n = min(X.shape[0], int(n * max(2.0, target_s / 4 / max(dt, 1e-3))))
     units = n * G * X.shape[1]
+    del all_cores
     return units / dt, cores, "1 FP64 EM iteration on the first %d of %d samples (D=%d, N_G=%d), %d OpenMP " \
                               "threads, %.2f s" % (n, X.shape[0], X.shape[1], G, cores, dt)
+
+
+def cpu_e1_learn(threads: int, n: int):
+    """The paper's speed-up workload E1 (N=1e6, D=100, N_G=100; 10 k-means +
+    10 EM iterations, Sec. 5.1) by the FP64 oracle on `threads` host cores,
+    timed on the first n samples of a seeded c1-style mixture of that shape
+    and scaled to N=1e6 (both phases are linear in N)."""
+    import oracle
+
+    from paper_1707_09094_gb300 import synth
+    N, D, G = E1_SHAPE
+    rng = np.random.default_rng(2000 + len(TABLE1_SHAPES))
+    X, _ = synth._draw(rng, synth.mixture_c1(rng, D, G), n)
+    oracle.set_threads(threads)
+    t0 = time.perf_counter()
+    oracle.learn(X, G, seed=1, km_iter=10, em_iter=10, n_chunks=max(threads, 1) * 4)
+    dt = time.perf_counter() - t0
+    return {"threads": threads, "samples_timed": n, "timed_s": dt, "learn_s_scaled_to_1e6": dt * N / n}
+
+
+def cpu_baseline_line(X, rate_cores, cores, sample):
+    """The oracle on the host: all cores (the headline figure), one core, the
+    CPU model, and the E1 learn time beside the paper's own E1 numbers."""
+    import oracle
+    r1, _, s1 = cpu_oracle_rate(X, target_s=8.0, threads=1)
+    e1_all = cpu_e1_learn(cores, 60_000)
+    e1_one = cpu_e1_learn(1, 12_000)
+    oracle.set_threads(cores)
+    return {"value": rate_cores, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+            "cpu_model": cpu_model(),
+            "one_core": {"value": r1, "unit": UNIT, "sample": s1},
+            "e1_learn": {"all_cores": e1_all, "one_core": e1_one,
+                         "paper_s": {"1_thread": 272.0, "16_threads": 27.0,
+                                     "paper_hardware": "2x Xeon E5-2620 v4, 16 cores (FP64, Armadillo gmm_diag)"},
+                         "note": "10 k-means + 10 EM iterations at N=1e6, D=100, N_G=100, timed on a prefix and "
+                                 "scaled by N"}}
 
 
 def max_over_ranks(ms: float, world: int, device: str) -> float:
@@ -298,6 +358,7 @@ def run_ours(args):
     head = args.forms[-1] if args.forms[-1] in results else "fp32"
     r = results[head]
     e2e = time_form(head, host_input=True)
+    h2d_gbs = plain_copy_gbs(X, Xd)
     step_ms = r["ms"] / args.steps
     value = whole_job_rate(units, world, step_ms)
 
@@ -333,7 +394,11 @@ def run_ours(args):
         "gpu_launches": int(r["launches"]),
         "clocks": r["clocks"],
         "e2e": {"value": world * units / (e2e["ms"] / args.steps * 1e-3), "unit": UNIT,
-                "h2d_bytes_per_step": int(X.nbytes), "d2h_bytes_per_step": 8 + 32},
+                "h2d_bytes_per_step": int(X.nbytes), "d2h_bytes_per_step": 8 + 32,
+                "ms_per_step": e2e["ms"] / args.steps,
+                "plain_h2d_copy_gbs": h2d_gbs,
+                "plain_h2d_copy_ms": X.nbytes / (h2d_gbs * 1e9) * 1e3,
+                "note": "plain_h2d_copy: one cudaMemcpyAsync of the same pinned X, the copy engine's rate here"},
         "kmeans": kmeans_line(km_tc, km_cc, units, N * (D + 1) * 4, peaks, peak_src),
         "learn_10km_10em_s": min(learn_t),
         "forms": {p: {"value": world * units / (results[p]["ms"] / args.steps * 1e-3),
@@ -349,11 +414,12 @@ def run_ours(args):
         line["batched_512"] = run_batched_leg()
     if not args.no_init_net:
         line["init_net"] = run_init_net_leg(peaks, peak_src)
+        line["init_net_c5"] = run_init_net_c5_leg()
     if not args.no_table1:
         line["table1_em_tol"] = run_table1_leg()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, cores, sample = cpu_oracle_rate(X)
-        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        line["cpu_baseline"] = cpu_baseline_line(X, rate, cores, sample)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -479,6 +545,37 @@ def run_init_net_leg(peaks, peak_src, B=16, P=4096, steps=10, warmup=3):
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
                          "frac": achieved / peaks["bf16_tflops"], "peak_source": "bf16_tflops (%s)" % peak_src,
                          "flops_per_step": flops}}
+
+
+def plain_copy_gbs(X, Xd, reps=5):
+    """Host-to-device rate of one plain copy of the pinned workload (the
+    bound of the e2e step's input transfer)."""
+    import torch
+    Xh = torch.from_numpy(X).pin_memory()
+    stream = torch.cuda.current_stream()
+    best = float("inf")
+    for _ in range(reps):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        Xd.copy_(Xh, non_blocking=True)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        best = min(best, ev0.elapsed_time(ev1))
+    return X.nbytes / (best * 1e-3) / 1e9
+
+
+def run_init_net_c5_leg(n_train=32768, epochs=2.0, n_eval=16):
+    """The learned-initialiser workload at its shape (D=32, N_G=32, 4096
+    points per set), scaled down to fit the bench: n_train mixtures fitted by
+    the plain method (batched k-means 10 + EM 10), Adam for `epochs`, then
+    n_eval held-out mixtures of N = 1e6 fitted to convergence three ways
+    (k-means seeding; the network's start; the network's means as k-means
+    seeds with 3 iterations).  Paired means: data passes, final mean LL."""
+    from paper_1707_09094_gb300 import init_train
+    r = init_train.c5_experiment(n_train=n_train, epochs=epochs, n_eval=n_eval, eval_n=1_000_000, lr=3e-3,
+                                 lam=1.0, hybrid_km=3)
+    return {k: v for k, v in r.items() if k != "rows"}
 
 
 def base_eval(base, g, Xd):

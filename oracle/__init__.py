@@ -66,6 +66,7 @@ def _load():
                 "orc_learn": (ctypes.c_int, [P, i64, i32, i32, i32, i32, u64, i32, i32, f64, f64,
                                              i32, P, P, P, P, P]),
                 "orc_num_threads": (ctypes.c_int, []),
+                "orc_set_threads": (None, [i32]),
                 "orc_generate": (ctypes.c_int, [P, P, P, i32, i32, i64, u64, P, P]),
             }
             for name, (res, args) in sig.items():
@@ -100,6 +101,11 @@ def _check(rc, what):
 
 def num_threads() -> int:
     return int(_load().orc_num_threads())
+
+
+def set_threads(n: int) -> None:
+    """OpenMP threads of the MapReduce loops (the CPU-baseline timing only)."""
+    _load().orc_set_threads(int(n))
 
 
 def log_gauss(x, mu, dcov) -> float:

