@@ -364,7 +364,7 @@ gmm_status run_em(gmm_model *m, const float *Xd, int64_t N, int32_t em_iter, dou
         }
         if ((prc = prof_end(m, s, slot)) != GMM_OK) return prc;
         gmm::EmFinalizeArgs fa{m->partial, m->llp, chunks * grid, chunks * n_llp, N, D, G, m->par[(base + k) & 1], m->par[(base + k + 1) & 1],
-                               var_floor, tc ? gmm::em_tc_shift_mode() : 0, m->op, m->center(), m->status, k, em_tol, m->lld,
+                               var_floor, 0, m->op, m->center(), m->status, k, em_tol, m->lld,
                                tc ? 1 : (m->has_center && m->center_D == D)};
         CK(gmm::launch_em_finalize(fa, s));
     }

@@ -1125,341 +1125,6 @@ __global__ void __launch_bounds__(kMsThreads, 1) k_em_mstep_lists(ExArgs args)
     }
 }
 
-// ------------------------------------------------------------------------
-// 2'. Exact log-densities, log-sum-exp, responsibilities and M-step
-// statistics of the screened candidates in one kernel (in place of 2 and 3:
-// X is read once more instead of twice, and no per-sample record of
-// responsibilities exists).  One CTA of 32 warps per SM owns a contiguous run
-// of 64-sample tiles (the paper's chunk of one thread, Sec. 2.1).  Shared
-// memory holds the FP32 operands (s, mu s) and c_g of every Gaussian; each
-// tile's samples, candidate lists and counts are staged by bulk copies two
-// tiles ahead.  Per tile:
-//  A. warp per sample, lanes over the dimensions (d = lane, lane + 32): the
-//     exact log-density c_g - 1/2 sum_d t_d^2, t_d = x_d s_gd - mu_gd s_gd
-//     (Eq. 15, the formula of the CUDA-core form), of each candidate, four
-//     candidates at a time (their sums reduced across the warp in six
-//     shuffles); log p(x_i) by log-sum-exp (Eqs. 16-18) into the tile's
-//     log p array and the CTA's FP64 log-likelihood; the sample is queued
-//     under each of its candidate Gaussians;
-//  B. warp w owns Gaussians w + 32 k and keeps their statistics in tensor
-//     memory: for each sample queued under an owned Gaussian it computes
-//     the log-density again, the responsibility l = exp(l_g - log p) (Eq. 3),
-//     and -- if l is at least exp(-screen), the screen's own rule: a dropped
-//     pair carries less than 1e-9 / N -- adds l, l t_d, l t_d^2 (Eqs. 9-11 in
-//     the standardized coordinates t of the iteration start; the update maps
-//     them back, Eqs. 12-14: mu' = (mu s + S1 / L) / s,
-//     sigma'^2 = (S2 / L - (S1 / L)^2) / s^2).  No two warps add to the same
-//     sum, so no atomics touch the statistics.
-// Every kFlush tiles (and at the end) the FP32 sums are added to float-float
-// totals, so an FP32 sum adds at most 64 + kFlush terms.
-// ------------------------------------------------------------------------
-constexpr bool kTcFused = false;          // the pass runs 1 + 2' (true) or 1 + 2 + 3 (false)
-constexpr int kFxThreads = 1024;
-constexpr int kFxWarps = kFxThreads / 32;
-constexpr int kFT = 64;                    // samples per tile
-constexpr int kFOwn = 256 / kFxWarps;      // Gaussians owned per warp (G <= 256)
-constexpr int kFlush = 16;                 // tiles between flushes of the tensor-memory sums
-
-struct FxSmem {
-    uint32_t ops, opc, X[2], cand[2], cnt[2], qs, qn, lse, s0, bars, misc, total;
-};
-
-__host__ __device__ inline FxSmem fx_layout(int D, int G)
-{
-    FxSmem L;
-    uint32_t o = 0;
-    L.ops = o; o += 8u * (uint32_t)G * (uint32_t)D;
-    L.opc = o; o += 4u * (uint32_t)G;
-    o = (o + 127u) & ~127u;
-    for (int b = 0; b < 2; ++b) {
-        L.X[b] = o; o += ((4u * kFT * (uint32_t)D) + 127u) & ~127u;
-        L.cand[b] = o; o += 32u * kFT;
-        L.cnt[b] = o; o += ((2u * kFT) + 127u) & ~127u;
-    }
-    L.qs = o; o += (uint32_t)G * kFT;
-    o = (o + 15u) & ~15u;
-    L.qn = o; o += 4u * (uint32_t)G;
-    L.lse = o; o += 4u * kFT;
-    L.s0 = o; o += 4u * (uint32_t)G;
-    L.bars = o; o += 16u;
-    L.misc = o; o += 16u;
-    L.total = o;
-    return L;
-}
-
-__device__ __forceinline__ bool ftile_is_bulk(int64_t i0, int64_t N, int x_al16)
-{
-    return x_al16 && i0 + kFT <= N;
-}
-
-__global__ void __launch_bounds__(kFxThreads, 1) k_em_exact_mstep(ExArgs args)
-{
-    extern __shared__ __align__(128) unsigned char fx_raw[];
-    const EmPassArgs &a = args.a;
-    const TcLists &L = args.L;
-    if (skip_block(a.status, a.iter)) return;
-    const int D = a.D, G = a.G, S = 1 + 2 * D;
-    const FxSmem Ls = fx_layout(D, G);
-    const float2 *ops = reinterpret_cast<const float2 *>(fx_raw + Ls.ops);
-    const float *opc = reinterpret_cast<const float *>(fx_raw + Ls.opc);
-    uint8_t *qs = fx_raw + Ls.qs;
-    int *qn = reinterpret_cast<int *>(fx_raw + Ls.qn);
-    float *lse_t = reinterpret_cast<float *>(fx_raw + Ls.lse);
-    float *s0sm = reinterpret_cast<float *>(fx_raw + Ls.s0);   // sum of l per Gaussian (the owner's lane 0)
-    uint64_t *bars = reinterpret_cast<uint64_t *>(fx_raw + Ls.bars);
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(fx_raw + Ls.misc);
-    __shared__ double s_ll[kFxWarps];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int64_t ntiles = (a.N + kFT - 1) / kFT;
-    const int64_t t0 = ntiles * blockIdx.x / gridDim.x, t1 = ntiles * (blockIdx.x + 1) / gridDim.x;
-    const float keep = -args.screen;
-    const bool has0 = lane < D, has1 = lane + 32 < D;
-    const unsigned FULL = 0xffffffffu;
-
-    uint32_t iss0 = 0u, iss1 = 0u;   // issued bulk tiles per buffer (thread 0)
-    auto issue = [&](int64_t tile, int b) {   // thread 0 only
-        const int64_t i0 = tile * kFT;
-        const uint32_t xb = 4u * kFT * (uint32_t)D;
-        if (b) ++iss1; else ++iss0;
-        fence_proxy_async();
-        mbar_expect_tx(bars + b, xb + 32u * kFT + 2u * kFT);
-        bulk_g2s(fx_raw + Ls.X[b], a.X + i0 * D, xb, bars + b);
-        bulk_g2s(fx_raw + Ls.cand[b], L.cand + i0 * 32, 32u * kFT, bars + b);
-        bulk_g2s(fx_raw + Ls.cnt[b], L.cnt + i0 * 2, 2u * kFT, bars + b);
-    };
-    if (tid == 0) {
-        mbar_init(bars, 1);
-        mbar_init(bars + 1, 1);
-        *abort_flag = 0;
-        fence_mbar_init();
-    }
-    {
-        float2 *opw = reinterpret_cast<float2 *>(fx_raw + Ls.ops);
-        float *ocw = reinterpret_cast<float *>(fx_raw + Ls.opc);
-        for (int k = tid; k < G * D; k += kFxThreads) opw[k] = __ldg(a.op.sm + k);
-        for (int g = tid; g < G; g += kFxThreads) { ocw[g] = __ldg(a.op.c + g); qn[g] = 0; s0sm[g] = 0.f; }
-    }
-    __syncthreads();
-    if (tid == 0)
-        for (int k = 0; k < 2 && t0 + k < t1; ++k)
-            if (ftile_is_bulk((t0 + k) * kFT, a.N, args.x_al16)) issue(t0 + k, k);
-
-    // The statistics of the owned Gaussians g = warp + kFxWarps k live in tensor
-    // memory: lane 32 (warp % 4) + l of the warp's quarter holds, for dims
-    // d = l and l + 32, the sums (l t_d, l t_d^2, l t_{d+32}, l t_{d+32}^2) of
-    // its k-th Gaussian in columns 4 kFOwn (warp / 4) + 4 k ... + 3 (256
-    // columns in all).  Their sums of l are in shared memory.
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(fx_raw + Ls.misc + 4);
-    if (warp == 0) {
-        tmem_alloc(tslot, 256);
-        tmem_relinquish();
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tm = *tslot + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(4 * kFOwn * (warp >> 2));
-#pragma unroll
-    for (int k = 0; k < kFOwn; ++k) tmem_st4(tm + 4u * k, 0.f, 0.f, 0.f, 0.f);
-    tmem_wait_st();
-    double *P = a.partial + (size_t)blockIdx.x * G * S;
-    bool first_flush = true;
-    // the register sums -> the CTA's FP64 partial (written the first time, added to after)
-    // The tensor-memory sums are added to float-float (hi, lo) totals kept in
-    // the CTA's partial slots (8 bytes each) every kFlush tiles; at the end each
-    // slot becomes the FP64 value hi + lo.  So an FP32 sum holds at most
-    // kFT pairs in registers plus kFlush tile sums in tensor memory.
-    float2 *P2 = reinterpret_cast<float2 *>(P);
-    auto ffadd = [&](float2 *p, float v) {   // (hi, lo) += v, error-free two-sum of hi and v
-        if (first_flush) { *p = make_float2(v, 0.f); return; }
-        const float2 o = *p;
-        const float sum = o.x + v, bb = sum - o.x;
-        const float err = (o.x - (sum - bb)) + (v - bb);
-        *p = make_float2(sum, o.y + err);
-    };
-#define FX_FLUSH()                                                                                       \
-    do {                                                                                                 \
-        _Pragma("unroll 1") for (int k = 0; k < kFOwn; ++k) {                                            \
-            const int g = warp + kFxWarps * k;                                                           \
-            float va, vb, vc, vd;                                                                        \
-            tmem_ld4(tm + 4u * k, va, vb, vc, vd);                                                       \
-            tmem_wait_ld();                                                                              \
-            if (g < G) {                                                                                 \
-                float2 *pg = P2 + (size_t)g * S;                                                         \
-                if (lane == 0) { ffadd(pg, s0sm[g]); s0sm[g] = 0.f; }                                    \
-                if (has0) { ffadd(pg + 1 + lane, va); ffadd(pg + 1 + D + lane, vb); }                    \
-                if (has1) { ffadd(pg + 33 + lane, vc); ffadd(pg + 33 + D + lane, vd); }                  \
-            }                                                                                            \
-            tmem_st4(tm + 4u * k, 0.f, 0.f, 0.f, 0.f);                                                   \
-        }                                                                                                \
-        tmem_wait_st();                                                                                  \
-        first_flush = false;                                                                             \
-    } while (0)
-
-    double ll = 0.0;
-    uint32_t use0 = 0u, use1 = 0u;
-    for (int64_t t = t0; t < t1; ++t) {
-        const int b = (int)((t - t0) & 1);
-        const int64_t i0 = t * kFT;
-        const int nv = (int)min((int64_t)kFT, a.N - i0);
-        const float *xs = reinterpret_cast<const float *>(fx_raw + Ls.X[b]);
-        const uint8_t *cs = fx_raw + Ls.cand[b];
-        const uint8_t *ns = fx_raw + Ls.cnt[b];
-        if (ftile_is_bulk(i0, a.N, args.x_al16)) {
-            if (stage_wait(bars + b, (b ? use1 : use0) & 1u, a.wait_cycles, abort_flag)) {
-                if (b) ++use1; else ++use0;
-            }
-        } else {
-            float *xw = reinterpret_cast<float *>(fx_raw + Ls.X[b]);
-            uint8_t *cw = fx_raw + Ls.cand[b], *nw = fx_raw + Ls.cnt[b];
-            for (int k = tid; k < nv * D; k += kFxThreads) xw[k] = __ldg(a.X + i0 * D + k);
-            for (int k = tid; k < nv * 32; k += kFxThreads) cw[k] = L.cand[i0 * 32 + k];
-            for (int k = tid; k < nv * 2; k += kFxThreads) nw[k] = L.cnt[i0 * 2 + k];
-        }
-        __syncthreads();
-        if (*abort_flag) break;   // uniform: nothing sets the flag between the barrier and here
-        // ---- A. log p of each sample; the sample queued under its candidates
-        for (int si = warp; si < nv; si += kFxWarps) {
-            const float *xr = xs + si * D;
-            const float x0 = has0 ? xr[lane] : 0.f, x1 = has1 ? xr[lane + 32] : 0.f;
-            const int n0 = ns[2 * si], n1 = ns[2 * si + 1];
-            const int c0 = n0 > kCap ? min(128, G) : n0;
-            const int nc = c0 + (n1 > kCap ? max(0, min(128, G - 128)) : n1);
-            const uint8_t *cl = cs + si * 32;
-            auto cand_g = [&](int j) -> int {   // candidate j of the sample
-                if (j < c0) return n0 > kCap ? j : (int)cl[j];
-                return 128 + (n1 > kCap ? j - c0 : (int)cl[16 + (j - c0)]);
-            };
-            float M = -INFINITY, Ssum = 0.f;
-#pragma unroll 1
-            for (int j0 = 0; j0 < nc; j0 += 4) {
-                float p[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    p[u] = 0.f;
-                    if (j0 + u < nc) {
-                        const float2 *q = ops + cand_g(j0 + u) * D;
-                        float ta = 0.f, tb = 0.f;
-                        if (has0) { const float2 v = q[lane]; ta = fmaf(x0, v.x, -v.y); }
-                        if (has1) { const float2 v = q[lane + 32]; tb = fmaf(x1, v.x, -v.y); }
-                        p[u] = fmaf(ta, ta, tb * tb);
-                    }
-                }
-                // lane k ends with the sum of candidate j0 + k/8
-                const bool b4 = (lane & 16) != 0, b3 = (lane & 8) != 0;
-                float q2[2];
-#pragma unroll
-                for (int k = 0; k < 2; ++k)
-                    q2[k] = (b4 ? p[2 + k] : p[k]) + __shfl_xor_sync(FULL, b4 ? p[k] : p[2 + k], 16);
-                float v = (b3 ? q2[1] : q2[0]) + __shfl_xor_sync(FULL, b3 ? q2[0] : q2[1], 8);
-                v += __shfl_xor_sync(FULL, v, 4);
-                v += __shfl_xor_sync(FULL, v, 2);
-                v += __shfl_xor_sync(FULL, v, 1);
-                const int jm = j0 + (lane >> 3);
-                const float l = jm < nc ? fmaf(-0.5f, v, opc[cand_g(jm)]) : -INFINITY;
-                // online log-sum-exp (Eqs. 16-18): the lanes k, k^8, k^16, k^24 hold the four candidates once
-                float gm = fmaxf(l, __shfl_xor_sync(FULL, l, 8));
-                gm = fmaxf(gm, __shfl_xor_sync(FULL, gm, 16));
-                const float nM = fmaxf(M, gm);
-                float e = l > -INFINITY ? __expf(l - nM) : 0.f;
-                e += __shfl_xor_sync(FULL, e, 8);
-                e += __shfl_xor_sync(FULL, e, 16);
-                Ssum = (M == -INFINITY ? 0.f : Ssum * __expf(M - nM)) + e;
-                M = nM;
-            }
-            const float lse = M + logf(Ssum);
-            if (lane == 0) {
-                lse_t[si] = lse;
-                ll += (double)lse;
-            }
-            for (int j = lane; j < nc; j += 32) {
-                const int g = cand_g(j);
-                qs[g * kFT + atomicAdd(&qn[g], 1)] = (uint8_t)si;   // at most one entry per sample and Gaussian
-            }
-        }
-        __syncthreads();
-        // ---- B. the owned Gaussians' queued samples
-#pragma unroll 1
-        for (int k = 0; k < kFOwn; ++k) {
-            const int g = warp + kFxWarps * k;
-            const int n = g < G ? qn[g] : 0;
-            if (n > 0) {   // warp-uniform
-                const float2 qa = has0 ? ops[g * D + lane] : make_float2(0.f, 0.f);
-                const float2 qb = has1 ? ops[g * D + 32 + lane] : make_float2(0.f, 0.f);
-                const float cgv = opc[g];
-                const uint8_t *qg = qs + g * kFT;
-                float s1a, s2a, s1b, s2b;
-                tmem_ld4(tm + 4u * k, s1a, s2a, s1b, s2b);
-                tmem_wait_ld();
-                float sl = 0.f;
-                for (int j = 0; j < n; ++j) {
-                    const int si = qg[j];
-                    const float *xr = xs + si * D;
-                    const float ta = has0 ? fmaf(xr[lane], qa.x, -qa.y) : 0.f;
-                    const float tb = has1 ? fmaf(xr[lane + 32], qb.x, -qb.y) : 0.f;
-                    const float rl = fmaf(-0.5f, warp_sum_f(fmaf(ta, ta, tb * tb)), cgv) - lse_t[si];
-                    if (rl >= keep) {   // warp-uniform
-                        const float gam = __expf(rl);
-                        const float ua = gam * ta, ub = gam * tb;
-                        sl += gam;
-                        s1a += ua;
-                        s2a = fmaf(ua, ta, s2a);
-                        s1b += ub;
-                        s2b = fmaf(ub, tb, s2b);
-                    }
-                }
-                tmem_st4(tm + 4u * k, s1a, s2a, s1b, s2b);
-                if (lane == 0) {
-                    qn[g] = 0;
-                    s0sm[g] += sl;
-                }
-            }
-        }
-        tmem_wait_st();
-        __syncthreads();   // every warp is done with buffer b and the queues
-        if (tid == 0 && t + 2 < t1 && ftile_is_bulk((t + 2) * kFT, a.N, args.x_al16)) issue(t + 2, b);
-        if (((t - t0 + 1) % kFlush) == 0) FX_FLUSH();
-    }
-    // drain: no bulk copy may still be writing into shared memory at exit
-    if (tid == 0)
-        for (int bb = 0; bb < 2; ++bb) {
-            const uint32_t issued = bb ? iss1 : iss0;
-            const uint32_t used = bb ? use1 : use0;
-            const long long d0 = clock64();
-            for (uint32_t u = used; u < issued; ++u)
-                while (!mbar_try_wait(bars + bb, u & 1u) && clock64() - d0 < a.wait_cycles) {
-                }
-        }
-    FX_FLUSH();   // the rest (and zeros for a CTA without tiles)
-#undef FX_FLUSH
-    // float-float totals -> FP64 partial (each thread its own slots)
-    for (int k = 0; k < kFOwn; ++k) {
-        const int g = warp + kFxWarps * k;
-        if (g < G) {
-            const size_t o = (size_t)g * S;
-            auto fin = [&](size_t j) { const float2 v = P2[o + j]; P[o + j] = (double)v.x + (double)v.y; };
-            if (lane == 0) fin(0);
-            if (has0) { fin(1 + lane); fin(1 + D + lane); }
-            if (has1) { fin(33 + lane); fin(33 + D + lane); }
-        }
-    }
-    if (lane == 0) s_ll[warp] = ll;
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 0) {
-        tc_fence_after();
-        tmem_dealloc(*tslot, 256);
-    }
-    if (tid == 0) {
-        double tot = 0.0;
-        for (int w = 0; w < kFxWarps; ++w) tot += s_ll[w];
-        a.ll_partial[blockIdx.x] = tot;
-        if (*abort_flag) {
-            if (atomicCAS(&a.status->code, 0, (int)GMM_ERR_TIMEOUT) == 0) a.status->fail_iter = a.iter;
-            atomicExch(&a.status->halt, 1);
-        }
-    }
-}
-
 }  // namespace
 
 namespace {
@@ -1479,8 +1144,6 @@ int ex_wp(int D, int G)
 }
 }  // namespace
 
-int em_tc_shift_mode() { return kTcFused ? 1 : 0; }
-
 bool em_tc_supported(int32_t D, int32_t G)
 {
     if (D < 1 || D > 64 || G < 1 || G > 256) return false;
@@ -1489,9 +1152,8 @@ bool em_tc_supported(int32_t D, int32_t G)
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     // dynamic layouts plus the kernels' static shared memory
-    return tc_layout(D, NG).total + 1024u + 2048u <= (uint32_t)optin &&
-           (kTcFused ? fx_layout(D, G).total + 2048u <= (uint32_t)optin
-                     : ex_wp(D, G) >= 32 && ms_layout(D, G).total + 2048u <= (uint32_t)optin);
+    return tc_layout(D, NG).total + 1024u + 2048u <= (uint32_t)optin && ex_wp(D, G) >= 32 &&
+           ms_layout(D, G).total + 2048u <= (uint32_t)optin;
 }
 
 int em_tc_grid(int sms) { return sms; }
@@ -1536,17 +1198,6 @@ cudaError_t launch_em_pass_tc(const EmPassArgs &a, const TcLists &L, int32_t gri
     if (e != cudaSuccess) return e;
     k_em_screen_tc<<<grid, kThreads, sm1, s>>>(t);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (kTcFused) {
-        (void)ms_grid;
-        ExArgs x{a, L, scr, al, 0};
-        const size_t sm2 = fx_layout(a.D, a.G).total;
-        if ((e = cudaFuncSetAttribute(k_em_exact_mstep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2)) !=
-            cudaSuccess)
-            return e;
-        k_em_exact_mstep<<<grid, kFxThreads, sm2, s>>>(x);
-        count_launches(2);
-        return cudaGetLastError();
-    }
     ExArgs x{a, L, scr, al, ex_wp(a.D, a.G)};
     const size_t sm2 = ex_layout(a.D, a.G, x.wp).total;
     if ((e = cudaFuncSetAttribute(k_em_exact, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2)) != cudaSuccess)

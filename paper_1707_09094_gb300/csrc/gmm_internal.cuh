@@ -63,7 +63,7 @@ struct EmFinalizeArgs {
     const double *par_in;    // [G*D means | G*D dcovs | G hefts]
     double *par_out;
     double var_floor;
-    int32_t shift_mode;      // 0: statistics of x - mu_f (FP32 means op.mu); 1: of t = x s - mu s (op.sm)
+    int32_t shift_mode;      // reserved (0): the statistics are shifted by the FP32 means op.mu
     Operands op;
     const float *center;
     DevStatus *status;
@@ -223,6 +223,5 @@ int em_tc_grid(int sms);
 size_t em_tc_list_bytes(int64_t N, int grid);
 TcLists em_tc_lists(void *base, int64_t N, int grid);
 cudaError_t launch_em_pass_tc(const EmPassArgs &a, const TcLists &L, int32_t grid, int32_t ms_chunks, cudaStream_t s);
-int em_tc_shift_mode();   // EmFinalizeArgs::shift_mode of the statistics the tensor-core pass writes
 
 }  // namespace gmm

@@ -1068,18 +1068,10 @@ __global__ void k_em_finalize(EmFinalizeArgs a)
     for (int d = threadIdx.x; d < D; d += blockDim.x) {
         double mu = mi[d], v = vi[d];
         if (live) {
+            const double shift = (double)a.op.mu[(size_t)g * D + d];   // the passes' FP32 shift
             const double m1 = red[1 + d] / Lg;
-            if (a.shift_mode == 1) {
-                // standardized statistics: S1 = sum l t, S2 = sum l t^2 with
-                // t = x s - mu s in the FP32 operands (s, mu s) of the pass
-                const float2 q = a.op.sm[(size_t)g * D + d];
-                const double sg = (double)q.x;
-                mu = ((double)q.y + m1) / sg;
-                v = (red[1 + D + d] / Lg - m1 * m1) / (sg * sg);
-            } else {
-                mu = (double)a.op.mu[(size_t)g * D + d] + m1;   // the passes' FP32 shift
-                v = red[1 + D + d] / Lg - m1 * m1;
-            }
+            mu = shift + m1;
+            v = red[1 + D + d] / Lg - m1 * m1;
             v = v > a.var_floor ? v : a.var_floor;
         }
         if (!isfinite(mu) || !isfinite(v)) s_bad = 1;
