@@ -14,10 +14,10 @@ import numpy as np
 
 from . import _lib
 from ._lib import (GMM_BF16, GMM_EUCL, GMM_FP32, GMM_KEEP_EXISTING, GMM_MAHA, GMM_PROB,  # noqa: F401
-                   GMM_RANDOM_SPREAD, GMM_RANDOM_SUBSET, GMM_SPLIT_BF16, GMM_STATIC_SPREAD, GMM_STATIC_SUBSET,
-                   GMM_TF32, GmmError)
+                   GMM_RANDOM_SPREAD, GMM_RANDOM_SUBSET, GMM_STATIC_SPREAD, GMM_STATIC_SUBSET,
+                   GmmError)
 
-PREC = {"fp32": GMM_FP32, "bf16": GMM_BF16, "tf32": GMM_TF32, "split_bf16": GMM_SPLIT_BF16}
+PREC = {"fp32": GMM_FP32, "bf16": GMM_BF16}
 
 
 def _torch():

@@ -39,7 +39,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     headers = [os.path.join(SRC, f) for f in os.listdir(SRC) if f.endswith((".cuh", ".h"))]
     headers.append(os.path.join(ROOT, "include", "gmm_gb300.h"))
     flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include"),
-                    "-diag-suppress", "177"]
+                    "-diag-suppress", "177"] + os.environ.get("GMM_NVCC_FLAGS", "").split()
     jobs = []
     for src in SOURCES:
         s = os.path.join(SRC, src)

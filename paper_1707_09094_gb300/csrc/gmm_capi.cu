@@ -321,7 +321,6 @@ gmm_status run_em(gmm_model *m, const float *Xd, int64_t N, int32_t em_iter, dou
 {
     const int32_t D = m->D, G = m->G, S = 1 + 2 * D;
     const bool tc = prec == GMM_BF16;
-    if (prec == GMM_TF32 || prec == GMM_SPLIT_BF16) return fail(GMM_ERR_UNSUPPORTED, "prec %d is reserved", prec);
     if (tc && !gmm::em_tc_supported(D, G))
         return fail(GMM_ERR_UNSUPPORTED, "tensor-core E-step needs D <= 64 and n_gaus <= 256 (D=%d, G=%d)", D, G);
     const bool two_phase = !tc && !gmm::em_simt_supported(D, G);
@@ -464,7 +463,7 @@ gmm_status gmm_learn(gmm_model *m, const float *X, int64_t N, int32_t D, int32_t
     if (!(var_floor >= 0.0) || !std::isfinite(var_floor)) return fail(GMM_ERR_ARG, "var_floor must be finite and >= 0");
     if (o.dist != GMM_EUCL && o.dist != GMM_MAHA) return fail(GMM_ERR_ARG, "dist must be EUCL or MAHA");
     if (o.seed_mode < GMM_KEEP_EXISTING || o.seed_mode > GMM_RANDOM_SPREAD) return fail(GMM_ERR_ARG, "bad seed_mode");
-    if (o.prec < GMM_FP32 || o.prec > GMM_SPLIT_BF16) return fail(GMM_ERR_ARG, "bad prec");
+    if (o.prec < GMM_FP32 || o.prec > GMM_BF16) return fail(GMM_ERR_ARG, "bad prec");
     if (o.seed_mode == GMM_KEEP_EXISTING && !(m->has_params && m->D == D && m->G == n_gaus))
         return fail(GMM_ERR_STATE, "keep_existing needs parameters of shape (%d, %d)", n_gaus, D);
     cudaStream_t s = as_stream(o.stream);
@@ -517,7 +516,7 @@ gmm_status gmm_em_iterate(gmm_model *m, const float *X, int64_t N, int32_t n_ite
     gmm_status rc = validate_x(X, N, m->D);
     if (rc != GMM_OK) return rc;
     if (n_iter < 0 || !(var_floor >= 0.0) || !std::isfinite(var_floor)) return fail(GMM_ERR_ARG, "bad n_iter/var_floor");
-    if (prec < GMM_FP32 || prec > GMM_SPLIT_BF16) return fail(GMM_ERR_ARG, "bad prec");
+    if (prec < GMM_FP32 || prec > GMM_BF16) return fail(GMM_ERR_ARG, "bad prec");
     cudaStream_t s = as_stream(stream);
     const float *Xd = nullptr;
     const bool need_center = recompute_center || !(m->has_center && m->center_D == m->D);

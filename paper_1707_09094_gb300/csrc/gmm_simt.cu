@@ -20,8 +20,15 @@ namespace gmm {
 
 namespace {
 
-constexpr int kWarps = 8;
+#ifndef GMM_EM_WARPS
+#define GMM_EM_WARPS 16
+#endif
+constexpr int kWarps = GMM_EM_WARPS;   // warps of a CTA of the FP32 EM passes
 constexpr int kEmThreads = kWarps * 32;
+#ifndef GMM_EM_GSTEP
+#define GMM_EM_GSTEP 4
+#endif
+constexpr int kEmGs = GMM_EM_GSTEP;   // Gaussians per warp step of the FP32 E-step
 constexpr int kTile = 32;      // samples per tile of the FP32 EM pass
 constexpr int kTP = kTile + 1; // padded row stride of the tile buffers
 constexpr int kKmThreads = 128;
@@ -768,27 +775,48 @@ __global__ void __launch_bounds__(kEmThreads, 1) k_em_pass_simt(EmPassArgs a)
             float xr[DMAX];
 #pragma unroll
             for (int d = 0; d < DMAX; ++d) xr[d] = d < D ? xT[d * kTP + lane] : 0.f;
-            // four Gaussians per step: four independent FMA chains per thread
-            for (int g0 = w; g0 < G; g0 += 4 * kWarps) {
-                float acc[4] = {0.f, 0.f, 0.f, 0.f};
+            // kEmGs Gaussians per step, two dimensions per 128-bit operand load
+            // (even D): 2 kEmGs independent FMA chains per thread
+            for (int g0 = w; g0 < G; g0 += kEmGs * kWarps) {
+                float acc[kEmGs], acc2[kEmGs];
 #pragma unroll
-                for (int d = 0; d < DMAX; ++d) {
-                    if (d < D) {
+                for (int u = 0; u < kEmGs; ++u) { acc[u] = 0.f; acc2[u] = 0.f; }
+                if ((D & 1) == 0) {
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const int g = g0 + u * kWarps;
-                            if (g < G) {
-                                const float2 q = __ldg(a.op.sm + (size_t)g * D + d);
-                                const float t = fmaf(xr[d], q.x, -q.y);
-                                acc[u] = fmaf(t, t, acc[u]);
+                    for (int d = 0; d < DMAX; d += 2) {
+                        if (d < D) {
+#pragma unroll
+                            for (int u = 0; u < kEmGs; ++u) {
+                                const int g = g0 + u * kWarps;
+                                if (g < G) {
+                                    const float4 q = __ldg(reinterpret_cast<const float4 *>(a.op.sm + (size_t)g * D + d));
+                                    const float t0 = fmaf(xr[d], q.x, -q.y), t1 = fmaf(xr[d + 1], q.z, -q.w);
+                                    acc[u] = fmaf(t0, t0, acc[u]);
+                                    acc2[u] = fmaf(t1, t1, acc2[u]);
+                                }
+                            }
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int d = 0; d < DMAX; ++d) {
+                        if (d < D) {
+#pragma unroll
+                            for (int u = 0; u < kEmGs; ++u) {
+                                const int g = g0 + u * kWarps;
+                                if (g < G) {
+                                    const float2 q = __ldg(a.op.sm + (size_t)g * D + d);
+                                    const float t = fmaf(xr[d], q.x, -q.y);
+                                    acc[u] = fmaf(t, t, acc[u]);
+                                }
                             }
                         }
                     }
                 }
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < kEmGs; ++u) {
                     const int g = g0 + u * kWarps;
-                    if (g < G) L[g * kTP + lane] = fmaf(-0.5f, acc[u], __ldg(a.op.c + g));
+                    if (g < G) L[g * kTP + lane] = fmaf(-0.5f, acc[u] + acc2[u], __ldg(a.op.c + g));
                 }
             }
         }

@@ -1,21 +1,24 @@
 """Precision report: the error of every result of one EM iteration against the
-FP64 oracle, per E-step form, on a prefix of the c2 workload (N = 50,000,
-D = 60, N_G = 256) from a k-means start.
+FP64 oracle, per E-step form, on prefixes of the c2 workload (N = 50,000,
+D = 60, N_G = 256) and the c3 workload (N = 20,000, D = 128, N_G = 1024) from
+a k-means start.
 
-Results compared: log p(x_i) of the updated model (lse_i), the mean
-log-likelihood of the iteration, and the updated means, variances and
-weights (the sufficient statistics S0, S1, S2 enter only through them).  The
+Results compared: log p(x_i) under the E-step's parameters (lse_i, the FP32
+E-step formula), the mean log-likelihood of the iteration, and the updated
+means, variances and weights (the sufficient statistics S0, S1, S2 enter
+only through them).  The
 relative errors are printed (pytest -s) and held to the parity tolerances:
-1e-4 on parameters (floors 1e-4 * global std / variance / 1 / N_G), 1e-6 on
-the mean log-likelihood, and 3 (1e-5 + 1e-6 |log p|) on each log p(x_i): the
-FP32 evaluation sums log-density terms of a few hundred nats (u * 500 is
-3e-5)."""
+1e-4 on parameters (floors 1e-4 * global std / variance / 1 / N_G, or the
+oracle's FP32 budget where larger), 1e-6 on the mean log-likelihood, and
+3 (1e-5 + 1e-6 |log p|) on each log p(x_i): the FP32 evaluation sums
+log-density terms of a few hundred nats (u * 500 is 3e-5)."""
 import numpy as np
 import pytest
 import torch
 
 import oracle
 from paper_1707_09094_gb300 import GMM, GMM_MAHA, synth
+from test_gpu_parity import assert_params
 
 pytestmark = pytest.mark.gpu
 
@@ -31,26 +34,31 @@ def rel_err(got, ref, floor):
     return float(np.max(np.abs(got - ref) / (np.abs(ref) + floor)))
 
 
-def test_precision_report_c2_prefix():
-    X, _, _ = synth.make("c2", N=50000)
-    G = 256
+@pytest.mark.parametrize("kind,N,G,forms", [("c2", 50000, 256, ("fp32", "bf16")), ("c3", 20000, 1024, ("fp32",))])
+def test_precision_report(kind, N, G, forms):
+    """Per form and result, the relative error of one GPU EM iteration against
+    the oracle's.  c3 (D=128, N_G=1024, sigma down to 0.1) runs the FP32
+    two-phase form only: the tensor-core form needs D <= 64 and N_G <= 256."""
+    X, _, _ = synth.make(kind, N=N)
     _, gv = oracle.global_stats(X)
     gv = np.maximum(gv, 1e-10)
     seeds = synth.seeds_subset(X, G, 7)
     start = oracle.kmeans(X, seeds, 1.0 / gv, gv, 3, 1e-10)[:3]
-    M, V, H, ll = oracle.em_iterate(X, *start, 1, 1e-10)
-    lp_ref = oracle.log_p(X, M, V, H)
+    M, V, H, ll1, budget = oracle.em_fp32_budget(X, *start, 1e-10)
+    ll = [ll1]
+    lp_ref = oracle.log_p(X, *start)   # log p(x_i) of the E-step's parameters (lse_i)
     gstd = np.sqrt(X.astype(np.float64).var(axis=0))
     Xd = torch.from_numpy(X).cuda()
     rows = []
-    for prec in ("fp32", "bf16"):
+    for prec in forms:
         g = GMM().set_params(*start)
         g.em_iterate(Xd, 1, prec=prec, recompute_center=True)
         m, v, h = g.get_params()
-        lp = g.log_p(Xd).cpu().numpy()
+        lp = GMM().set_params(*start).log_p(Xd).cpu().numpy()
+        big = H * N >= 10   # the table: Gaussians with >= 10 samples' worth (the assertion: all, by the budget)
         r = {"form": prec,
-             "means": rel_err(m, M, gstd[None, :]),
-             "dcovs": rel_err(v, V, gstd[None, :] ** 2),
+             "means": rel_err(m[big], M[big], gstd[None, :]),
+             "dcovs": rel_err(v[big], V[big], gstd[None, :] ** 2),
              "hefts": rel_err(h, H, 1.0 / G),
              "LL": abs(g.ll_history()[0] - ll[0]) / abs(ll[0]),
              "log p(x_i)": rel_err(lp, lp_ref, 1.0),
@@ -58,9 +66,10 @@ def test_precision_report_c2_prefix():
         rows.append(r)
         k = int(np.argmax(np.abs(lp - lp_ref) / (1e-5 + 1e-6 * np.abs(lp_ref))))
         print("\n%s worst log p: got %.9g ref %.9g" % (prec, lp[k], lp_ref[k]))
-        assert r["means"] <= 1e-4 and r["dcovs"] <= 1e-4 and r["hefts"] <= 1e-4, r
+        assert_params((m, v, h), (M, V, H), X, budget=budget)
         assert r["LL"] <= 1e-6 and r["log p limit"] <= 3.0, r
     keys = ["means", "dcovs", "hefts", "LL", "log p(x_i)"]
-    print("\n| form | " + " | ".join(keys) + " |\n|---|" + "---:|" * len(keys))
+    print("\n%s prefix, N=%d, N_G=%d" % (kind, N, G))
+    print("| form | " + " | ".join(keys) + " |\n|---|" + "---:|" * len(keys))
     for r in rows:
         print("| %s | " % r["form"] + " | ".join("%.1e" % r[k] for k in keys) + " |")
