@@ -65,6 +65,7 @@ def _load():
                 "orc_assign": (ctypes.c_int, [P, i64, i32, i32, P, P, P, i32, P]),
                 "orc_learn": (ctypes.c_int, [P, i64, i32, i32, i32, i32, u64, i32, i32, f64, f64,
                                              i32, P, P, P, P, P]),
+                "orc_log_p_fp32_bound": (ctypes.c_int, [P, i64, i32, i32, P, P, P, i32, P]),
                 "orc_num_threads": (ctypes.c_int, []),
                 "orc_set_threads": (None, [i32]),
                 "orc_generate": (ctypes.c_int, [P, P, P, i32, i32, i64, u64, P, P]),
@@ -274,6 +275,17 @@ def em_fp32_budget(X, means, dcovs, hefts, var_floor: float, n_acc: int = 0, n_l
     _check(_load().orc_em_fp32_budget(_p(X), N, D, G, _p(m), _p(v), _p(h), var_floor, n_chunks, n_acc, n_lse, drop,
                                       ctypes.byref(ll), _p(bm), _p(bv), _p(bw)), "em_fp32_budget")
     return m, v, h, ll.value, (bm, bv, bw)
+
+
+def log_p_fp32_bound(X, means, dcovs, hefts, n_lse: int = 0):
+    """Per sample, the bound on |FP32 log p(x_i) - FP64 log p(x_i)| of
+    orc_log_p_fp32_bound (a parity tolerance)."""
+    X = _x(X)
+    m, v, h = _params(means, dcovs, hefts)
+    out = np.empty(X.shape[0], np.float64)
+    _check(_load().orc_log_p_fp32_bound(_p(X), X.shape[0], X.shape[1], m.shape[0], _p(m), _p(v), _p(h),
+                                        n_lse if n_lse > 0 else m.shape[0] + 8, _p(out)), "log_p_fp32_bound")
+    return out
 
 
 def em_step_twopass(X, means, dcovs, hefts, var_floor: float):

@@ -554,6 +554,10 @@ int orc_em_step_twopass(const float *X, int64_t N, int32_t D, int32_t G, double 
  * First-order bounds with u = 2^-24, from the exact FP64 quantities
  * t_d = (x_d - mu_d) / sigma_d and a_d = (|x_d| + |mu_d|) / sigma_d:
  *   logit   e_ig = u (|c_g| + |l_ig| + sum_d |t_d| a_d + (1 + D/2) sum_d t_d^2)
+ *                  + 4 u^2 sum_d (a_d + |t_d|)^2
+ *           (the last term is the square of the rounding of x s - mu s itself,
+ *           one or two roundings of size u (a_d + |t_d|); it matters only when
+ *           sigma is tiny against |x| + |mu|)
  *   log p   E_i = sum_h l_hi e_ih carried from the logits, and its own rounding
  *           r_i = sum_h l_hi u |l_ih - max_h l_ih| + (n_lse + 8) u + u |log p_i| + 2^-20 + G drop / N
  *           (n_lse: the longest chain of FP32 additions in the sum of Eq. 16)
@@ -614,14 +618,17 @@ int orc_em_fp32_budget(const float *X, int64_t N, int32_t D, int32_t G, double *
             double mx = -INFINITY;
             for (int32_t g = 0; g < G; ++g) {
                 const double *mu = m0 + (size_t)g * D, *sg = sd + (size_t)g * D;
-                double t2 = 0.0, ta = 0.0;
+                double t2 = 0.0, ta = 0.0, q2 = 0.0;
                 for (int32_t d = 0; d < D; ++d) {
                     double td = ((double)x[d] - mu[d]) / sg[d];
+                    double ad = (fabs((double)x[d]) + fabs(mu[d])) / sg[d];
                     t2 += td * td;
-                    ta += fabs(td) * (fabs((double)x[d]) + fabs(mu[d])) / sg[d];
+                    ta += fabs(td) * ad;
+                    q2 += (ad + fabs(td)) * (ad + fabs(td));
                 }
                 l[g] = cst[g] - 0.5 * t2;                       /* Eq. 15 */
-                e[g] = l[g] == -INFINITY ? 0.0 : u * (fabs(cst[g]) + fabs(l[g]) + ta + (1.0 + 0.5 * (double)D) * t2);
+                e[g] = l[g] == -INFINITY ? 0.0
+                                         : u * (fabs(cst[g]) + fabs(l[g]) + ta + (1.0 + 0.5 * (double)D) * t2) + 4.0 * u * u * q2;
                 if (l[g] > mx) mx = l[g];
             }
             if (mx == -INFINITY) continue;
@@ -687,6 +694,67 @@ int orc_em_fp32_budget(const float *X, int64_t N, int32_t D, int32_t G, double *
     }
     free(tot); free(acc); free(sd); free(cst); free(m0); free(v0); free(h0);
     return ORC_OK;
+}
+
+/*
+ * Per sample, a bound on how far an FP32 evaluation of log p(x_i) (Eq. 16
+ * with the log-densities of Eq. 15 as the CUDA forms compute them) may land
+ * from the FP64 value: E_i + r_i of orc_em_fp32_budget (first order, plus the
+ * square of the rounding of x s - mu s).  A parity tolerance, not part of the
+ * method.
+ */
+int orc_log_p_fp32_bound(const float *X, int64_t N, int32_t D, int32_t G, const double *means, const double *dcovs,
+                         const double *hefts, int32_t n_lse, double *out)
+{
+    if (N < 0 || D < 1 || G < 1 || n_lse < 1) return ORC_ERR_ARG;
+    const double u = 1.0 / 16777216.0;
+    size_t GD = (size_t)G * D;
+    double *sd = (double *)malloc(sizeof(double) * GD), *cst = (double *)malloc(sizeof(double) * (size_t)G);
+    if (!sd || !cst) { free(sd); free(cst); return ORC_ERR_OOM; }
+    for (int32_t g = 0; g < G; ++g) {
+        cst[g] = log(hefts[g]) - 0.5 * (double)D * ORC_LOG_2PI;
+        for (int32_t d = 0; d < D; ++d) {
+            sd[(size_t)g * D + d] = sqrt(dcovs[(size_t)g * D + d]);
+            cst[g] -= 0.5 * log(dcovs[(size_t)g * D + d]);
+        }
+    }
+    int rc = ORC_OK;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+    for (int64_t i = 0; i < N; ++i) {
+        const float *x = X + (size_t)i * D;
+        double *l = (double *)malloc(sizeof(double) * (size_t)G), *e = (double *)malloc(sizeof(double) * (size_t)G);
+        if (!l || !e) { free(l); free(e); rc = ORC_ERR_OOM; continue; }
+        double mx = -INFINITY;
+        for (int32_t g = 0; g < G; ++g) {
+            const double *mu = means + (size_t)g * D, *sg = sd + (size_t)g * D;
+            double t2 = 0.0, ta = 0.0, q2 = 0.0;
+            for (int32_t d = 0; d < D; ++d) {
+                double td = ((double)x[d] - mu[d]) / sg[d];
+                double ad = (fabs((double)x[d]) + fabs(mu[d])) / sg[d];
+                t2 += td * td;
+                ta += fabs(td) * ad;
+                q2 += (ad + fabs(td)) * (ad + fabs(td));
+            }
+            l[g] = cst[g] - 0.5 * t2;
+            e[g] = l[g] == -INFINITY ? 0.0
+                                     : u * (fabs(cst[g]) + fabs(l[g]) + ta + (1.0 + 0.5 * (double)D) * t2) + 4.0 * u * u * q2;
+            if (l[g] > mx) mx = l[g];
+        }
+        double se = 0.0;
+        for (int32_t g = 0; g < G; ++g) se += exp(l[g] - mx);
+        const double lse = mx + log(se);
+        double b = (double)(n_lse + 8) * u + u * fabs(lse) + 1.0 / 1048576.0;
+        for (int32_t g = 0; g < G; ++g)
+            if (l[g] > -INFINITY) b += exp(l[g] - lse) * (e[g] + u * fabs(l[g] - mx));
+        out[i] = b;
+        free(l);
+        free(e);
+    }
+    free(sd);
+    free(cst);
+    return rc;
 }
 
 /*

@@ -10,8 +10,10 @@ only through them).  The
 relative errors are printed (pytest -s) and held to the parity tolerances:
 1e-4 on parameters (floors 1e-4 * global std / variance / 1 / N_G, or the
 oracle's FP32 budget where larger), 1e-6 on the mean log-likelihood, and
-3 (1e-5 + 1e-6 |log p|) on each log p(x_i): the FP32 evaluation sums
-log-density terms of a few hundred nats (u * 500 is 3e-5)."""
+on each log p(x_i) 3 (1e-5 + 1e-6 |log p|) -- the FP32 evaluation sums
+log-density terms of a few hundred nats (u * 500 is 3e-5) -- or twice the
+oracle's per-sample FP32 bound where larger (samples of single-sample
+clusters at the 1e-10 variance floor: there x s and mu s reach 1e5 |x|)."""
 import numpy as np
 import pytest
 import torch
@@ -47,6 +49,7 @@ def test_precision_report(kind, N, G, forms):
     M, V, H, ll1, budget = oracle.em_fp32_budget(X, *start, 1e-10)
     ll = [ll1]
     lp_ref = oracle.log_p(X, *start)   # log p(x_i) of the E-step's parameters (lse_i)
+    lp_lim = np.maximum(3.0 * (1e-5 + 1e-6 * np.abs(lp_ref)), 2.0 * oracle.log_p_fp32_bound(X, *start))
     gstd = np.sqrt(X.astype(np.float64).var(axis=0))
     Xd = torch.from_numpy(X).cuda()
     rows = []
@@ -62,12 +65,12 @@ def test_precision_report(kind, N, G, forms):
              "hefts": rel_err(h, H, 1.0 / G),
              "LL": abs(g.ll_history()[0] - ll[0]) / abs(ll[0]),
              "log p(x_i)": rel_err(lp, lp_ref, 1.0),
-             "log p limit": float(np.max(np.abs(lp - lp_ref) / (1e-5 + 1e-6 * np.abs(lp_ref))))}
+             "log p limit": float(np.max(np.abs(lp - lp_ref) / lp_lim))}
         rows.append(r)
-        k = int(np.argmax(np.abs(lp - lp_ref) / (1e-5 + 1e-6 * np.abs(lp_ref))))
+        k = int(np.argmax(np.abs(lp - lp_ref) / lp_lim))
         print("\n%s worst log p: got %.9g ref %.9g" % (prec, lp[k], lp_ref[k]))
         assert_params((m, v, h), (M, V, H), X, budget=budget)
-        assert r["LL"] <= 1e-6 and r["log p limit"] <= 3.0, r
+        assert r["LL"] <= 1e-6 and r["log p limit"] <= 1.0, r
     keys = ["means", "dcovs", "hefts", "LL", "log p(x_i)"]
     print("\n%s prefix, N=%d, N_G=%d" % (kind, N, G))
     print("| form | " + " | ".join(keys) + " |\n|---|" + "---:|" * len(keys))

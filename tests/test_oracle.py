@@ -269,26 +269,37 @@ def _fp32_em_emulation(X, means, dcovs, hefts, var_floor):
     Sd = np.where(live, S0, 1.0)[:, None]
     mu = np.where(live[:, None], f.astype(np.float64) + S1 / Sd, means)
     var = np.where(live[:, None], np.maximum(S2 / Sd - (S1 / Sd) ** 2, var_floor), dcovs)
-    return mu, var, S0 / X.shape[0], float(lse.astype(np.float64).mean()), live
+    return mu, var, S0 / X.shape[0], lse.astype(np.float64), live
 
 
-@pytest.mark.parametrize("kind", ["c2", "overlap"])
+@pytest.mark.parametrize("kind", ["c2", "overlap", "floored"])
 def test_fp32_budget_covers_an_fp32_emulation(kind):
-    """The parity budget (orc_em_fp32_budget) bounds what an FP32 evaluation
-    of the iteration actually does: an independent numpy float32 emulation
-    lands inside it for every parameter of every Gaussian, including the
+    """The parity budget (orc_em_fp32_budget, orc_log_p_fp32_bound) bounds what
+    an FP32 evaluation of the iteration actually does: an independent numpy
+    float32 emulation lands inside it for log p of every sample and every
+    parameter of every Gaussian, including the
     weakly supported ones, while on the c2-like case (a start near the
     fit) the budget of the well supported Gaussians stays below the 1e-4
     parity tolerance, i.e. it widens nothing there."""
     if kind == "c2":
         X, _, mix = synth.make("c2", N=4000, G=64)
         start = (mix.means, mix.stds ** 2 * 1.2, mix.hefts)
-    else:
+    elif kind == "overlap":
         rng = np.random.default_rng(5)
         X = rng.normal(0, 1, (3000, 6)).astype(np.float32)
         start = (rng.normal(0, 1.5, (12, 6)), rng.uniform(0.2, 2, (12, 6)), rng.dirichlet(np.ones(12)))
+    else:
+        # a single-sample cluster at the 1e-10 variance floor, centred on its sample
+        X, _, mix = synth.make("c1", N=3000, D=10, G=8, seed=77)
+        means, dcovs = mix.means.copy(), mix.stds ** 2
+        means[0] = X[5].astype(np.float64)
+        dcovs[0] = 1e-10
+        start = (means, dcovs, mix.hefts)
     M, V, H, ll, (bm, bv, bw) = oracle.em_fp32_budget(X, *start, 1e-10)
-    m, v, h, ll32, live = _fp32_em_emulation(X, *start, 1e-10)
+    m, v, h, lse32, live = _fp32_em_emulation(X, *start, 1e-10)
+    ll32 = float(lse32.mean())
+    # per sample, log p within the oracle's FP32 bound
+    assert np.all(np.abs(lse32 - oracle.log_p(X, *start)) <= 2 * oracle.log_p_fp32_bound(X, *start))
     assert np.all(np.abs(m - M)[live] <= 2 * bm[live] + 1e-12)
     assert np.all(np.abs(v - V)[live] <= 2 * bv[live] + 1e-12)
     assert np.all(np.abs(h - H) <= 2 * bw + 1e-15)
