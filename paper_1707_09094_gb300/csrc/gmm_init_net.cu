@@ -98,7 +98,8 @@ __global__ void __launch_bounds__(256) k_gemm_bf16(const __nv_bfloat16 *__restri
 // the per-point layers: D[M][N] = sum_k A[m][k] B[n][k], A and B row-major
 // with K contiguous (K-major), rows a multiple of 8 elements apart.  A CTA
 // owns a 128 x BN tile; K advances in 64-wide blocks staged by cp.async into
-// 128-byte-swizzled shared memory (two stages), one thread issues the four
+// 128-byte-swizzled shared memory (kGemmStages stages, all but one block in
+// flight ahead of the MMAs), one thread issues the four
 // K=16 MMAs of a block and commits them to the stage's mbarrier.  Rows or K
 // beyond the operands are zero-filled.  Epilogues (tcgen05.ld, a warp per 32
 // rows): 0 FP32 atomics into C (split-K along grid z), 1 bias + ReLU to BF16,
@@ -122,6 +123,8 @@ __device__ __forceinline__ void cp_async16_zf(uint32_t dst, const void *src, int
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
 }
 
+constexpr int kGemmStages = 4;   // K blocks in flight: cp.async groups ahead of the MMAs
+
 template <int BN>
 __global__ void __launch_bounds__(128, 1) k_gemm_tc(TcGemm g)
 {
@@ -129,17 +132,17 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(TcGemm g)
     unsigned char *sb = gt_raw + ((1024u - (smem_u32(gt_raw) & 1023u)) & 1023u);
     constexpr uint32_t kStage = 16384u + (uint32_t)BN * 128u;
     constexpr uint32_t kCols = BN < 32 ? 32 : BN;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sb + 2 * kStage);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(sb + 2 * kStage + 16);
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(sb + 2 * kStage + 20);
+    constexpr int NST = kGemmStages;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sb + NST * kStage);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(sb + NST * kStage + 8 * NST);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(sb + NST * kStage + 8 * NST + 4);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.x * 128, n0 = blockIdx.y * BN;
     const int nkb_all = (g.K + 63) / 64;
     const int kb0 = blockIdx.z * g.kb_split, nkb = min(nkb_all, kb0 + g.kb_split) - kb0;
     if (nkb <= 0) return;   // uniform
     if (tid == 0) {
-        mbar_init(bars, 1);
-        mbar_init(bars + 1, 1);
+        for (int k = 0; k < NST; ++k) mbar_init(bars + k, 1);
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -167,17 +170,23 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(TcGemm g)
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
     const uint32_t idesc = idesc_bf16(128, BN);
-    load(kb0, 0);
+    // blocks 0 .. NST-2 in flight before the first MMA; then, per block i, the
+    // load of block i + NST - 1 goes to the stage the MMAs of block i - 1 read
+    // (after their commit), one cp.async group per block (empty past the end)
+    for (int j = 0; j < NST - 1; ++j) {
+        if (j < nkb) load(kb0 + j, j);
+        else asm volatile("cp.async.commit_group;" ::: "memory");
+    }
     for (int i = 0; i < nkb; ++i) {
-        const int st = i & 1;
-        if (i + 1 < nkb) {
-            // the other stage was read by the MMAs of block i-1
-            if (i >= 1) mbar_wait(bars + ((i + 1) & 1), (uint32_t)(((i - 1) >> 1) & 1), abort_flag, g.budget);
-            load(kb0 + i + 1, (i + 1) & 1);
-            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        const int st = i % NST;
+        const int j = i + NST - 1;
+        if (j < nkb) {
+            if (i >= 1) mbar_wait(bars + (j % NST), (uint32_t)(((i - 1) / NST) & 1), abort_flag, g.budget);
+            load(kb0 + j, j % NST);
         } else {
-            asm volatile("cp.async.wait_group 0;" ::: "memory");
+            asm volatile("cp.async.commit_group;" ::: "memory");
         }
+        asm volatile("cp.async.wait_group %0;" ::"n"(NST - 1) : "memory");   // block i has landed
         fence_proxy_async();
         __syncthreads();
         if (tid == 0) {
@@ -190,10 +199,12 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(TcGemm g)
         }
     }
     // every MMA has completed once the last block's commit has arrived
-    if (!mbar_wait(bars + ((nkb - 1) & 1), (uint32_t)(((nkb - 1) >> 1) & 1), abort_flag, g.budget)) {
+    const int ls = (nkb - 1) % NST;
+    const uint32_t lp = (uint32_t)(((nkb - 1) / NST) & 1);
+    if (!mbar_wait(bars + ls, lp, abort_flag, g.budget)) {
         // bounded drain (ignores the abort flag) before the memory is freed
         const long long d0 = clock64();
-        while (!mbar_try_wait(bars + ((nkb - 1) & 1), (uint32_t)(((nkb - 1) >> 1) & 1)) && clock64() - d0 < g.budget) {
+        while (!mbar_try_wait(bars + ls, lp) && clock64() - d0 < g.budget) {
         }
         if (tid == 0) atomicExch(g.err, 1);
     }
@@ -691,7 +702,7 @@ cudaError_t gemm_tc(const __nv_bfloat16 *A, const __nv_bfloat16 *B, int64_t M, i
     const int gz = (nkb + kb_split - 1) / kb_split;
     TcGemm g{A, B, (int)M, N, K, lda, ldb, kb_split, mode, C, ldc, bias, out, ldo, ref, ldr, 2000000000LL, err};
     const int BN = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
-    const size_t sm = 2 * (16384 + (size_t)BN * 128) + 64 + 1024;
+    const size_t sm = kGemmStages * (16384 + (size_t)BN * 128) + 64 + 1024;
     const dim3 grid((unsigned)((M + 127) / 128), (unsigned)((N + BN - 1) / BN), (unsigned)gz);
 #define GTC(BNV)                                                                                           \
     do {                                                                                                   \
