@@ -217,29 +217,55 @@ def whole_job_rate(units_per_rank: float, world: int, ms_per_step: float) -> flo
     return world * units_per_rank / (ms_per_step * 1e-3)
 
 
+def c2_config(N, D, G, head, world, x_bytes):
+    """The `config` object of the bench line (both arms)."""
+    return {"workload": "c2 EM iteration (fused E+M pass + FP64 reduce/update): N=%d D=%d N_G=%d, "
+                        "k-means-initialised, E-step %s" % (N, D, G, head),
+            "N": N, "D": D, "N_G": G, "form": head,
+            "l2": "inputs larger than L2 (X = %.0f MB)" % (x_bytes / 1e6),
+            "parallelism": "replicas" if world > 1 else "single"}
+
+
 def run_reference(args):
+    """The FP64 CPU oracle on the host cores, the same metric and config:
+    every step is one oracle EM iteration (MapReduce chunks over all cores)
+    on a prefix of the workload sized so the whole run takes about a minute;
+    value = units of that prefix / its median step time, ms_per_step the
+    measured step time."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     import oracle
     oracle.build()
     X = make_data()
-    vals = []
-    info = None
+    N, D = X.shape
+    G = G_FULL
+    cores = oracle.num_threads()
+    target = max(0.5, 60.0 / max(args.steps + args.warmup, 1))
+    _, _, sample = cpu_oracle_rate(X, target_s=4 * target)    # sizes the prefix: one step ~ target seconds
+    n = int(sample.split("first ")[1].split(" ")[0])
+    rng = np.random.default_rng(5)
+    idx = rng.choice(n, G, replace=False)
+    Xs = X[:n]
+    start = (Xs[idx].astype(np.float64), np.ones((G, D)), np.full(G, 1.0 / G))
+    times = []
     for k in range(args.warmup + args.steps):
-        rate, cores, sample = cpu_oracle_rate(X, target_s=max(2.0, 60.0 / max(args.steps + args.warmup, 1)))
+        t0 = time.perf_counter()
+        oracle.em_iterate(Xs, *start, 1, 1e-10, n_chunks=cores * 4)
+        dt = time.perf_counter() - t0
         if k >= args.warmup:
-            vals.append(rate)
-            info = (cores, sample)
-    v = statistics.median(vals)
-    units_per_iter = N_FULL * G_FULL * D_FULL
+            times.append(dt)
+    units = n * G * D
+    v = units / statistics.median(times)
+    head = args.forms[-1] if args.forms else "bf16"
+    smp = "each step: 1 FP64 EM iteration on the first %d of %d samples (D=%d, N_G=%d), %d OpenMP threads" % (
+        n, N, D, G, cores)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * units_per_iter / v,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": "c2 EM iteration: N=2000000 D=60 N_G=256 (FP64 CPU oracle, bounded prefix, "
-                                   "scaled per unit)", "N": N_FULL, "D": D_FULL, "N_G": G_FULL},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": info[0], "kind": "oracle", "sample": info[1]},
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+            "units_per_step": units, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "config": c2_config(N, D, G, head, 1, X.nbytes),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": smp,
+                             "cpu_model": cpu_model()},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -385,11 +411,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16"}[head],
         "data": "synthetic",
-        "config": {"workload": "c2 EM iteration (fused E+M pass + FP64 reduce/update): N=%d D=60 N_G=256, "
-                               "k-means-initialised, E-step %s" % (N, head),
-                   "N": N, "D": D, "N_G": G, "form": head,
-                   "l2": "inputs larger than L2 (X = %.0f MB)" % (X.nbytes / 1e6),
-                   "parallelism": "replicas" if world > 1 else "single"},
+        "config": c2_config(N, D, G, head, world, X.nbytes),
         "roofline": roof,
         "gpu_launches": int(r["launches"]),
         "clocks": r["clocks"],

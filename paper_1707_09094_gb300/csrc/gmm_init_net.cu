@@ -123,7 +123,7 @@ __device__ __forceinline__ void cp_async16_zf(uint32_t dst, const void *src, int
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
 }
 
-constexpr int kGemmStages = 4;   // K blocks in flight: cp.async groups ahead of the MMAs
+constexpr int kGemmStages = 2;   // K blocks staged at once (two stages keep two CTAs per SM)
 
 template <int BN>
 __global__ void __launch_bounds__(128, 1) k_gemm_tc(TcGemm g)
