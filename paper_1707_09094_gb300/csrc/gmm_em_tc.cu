@@ -780,7 +780,7 @@ __global__ void __launch_bounds__(kExThreads, 1) k_em_exact(ExArgs args)
                 for (int j = lane; j < cnt; j += 32) {
                     const float l = logit(gsel(j));
                     if (l > mx) { sm = sm * __expf(mx - l) + 1.f; mx = l; }
-                    else sm += __expf(l - mx);
+                    else if (l > -INFINITY) sm += __expf(l - mx);   // -inf terms add nothing (and -inf - -inf is NaN)
                 }
                 float M = mx;
 #pragma unroll

@@ -442,7 +442,7 @@ __global__ void __launch_bounds__(kLossPts) k_loss_chunk(const float *__restrict
             const float l = fmaf(-0.5f, q, cst[g]);
             gam[p * GS + g] = l;
             if (l > mx) { sm = sm * __expf(mx - l) + 1.f; mx = l; }
-            else sm += __expf(l - mx);
+            else if (l > -INFINITY) sm += __expf(l - mx);   // -inf terms add nothing (and -inf - -inf is NaN)
         }
         const float lse = mx + logf(sm);
         nl = -lse;

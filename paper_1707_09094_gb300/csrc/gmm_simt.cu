@@ -943,7 +943,7 @@ __global__ void __launch_bounds__(128) k_lse_pass(EmPassArgs a, float *__restric
             }
             const float l = fmaf(-0.5f, acc0 + acc1, __ldg(a.op.c + g));
             if (l > m) { s = s * __expf(m - l) + 1.f; m = l; }
-            else s += __expf(l - m);
+            else if (l > -INFINITY) s += __expf(l - m);   // -inf terms add nothing (and -inf - -inf is NaN)
         }
         const float ls = m + logf(s);
         lse[i] = ls;
@@ -968,7 +968,10 @@ __global__ void __launch_bounds__(kEmThreads, 1) k_em_slab_pass(EmPassArgs a, co
     float *S1 = S0 + GS;                          // [GS*D]
     float *S2 = S1 + (size_t)GS * D;              // [GS*D]
     float *lt = S2 + (size_t)GS * D;              // [kTile]
+    int *act = reinterpret_cast<int *>(lt + kTile);   // [GS] Gaussians that matter in the tile
+    __shared__ int s_nact;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const float keep = (float)(1e-9 / (double)(a.N_total > a.N ? a.N_total : a.N));
     for (int k = tid; k < gs; k += kEmThreads) S0[k] = 0.f;
     for (int k = tid; k < gs * D; k += kEmThreads) { S1[k] = 0.f; S2[k] = 0.f; }
     const int64_t ntiles = (a.N + kTile - 1) / kTile;
@@ -990,17 +993,36 @@ __global__ void __launch_bounds__(kEmThreads, 1) k_em_slab_pass(EmPassArgs a, co
             for (int d = 0; d < DMAX; ++d) xr[d] = d < D ? xT[d * kTP + lane] : 0.f;
             const float ls = lt[lane];
             for (int gb = w; gb < gs; gb += 4 * kWarps) {
-                float acc[4] = {0.f, 0.f, 0.f, 0.f};
+                float acc[4] = {0.f, 0.f, 0.f, 0.f}, acc2[4] = {0.f, 0.f, 0.f, 0.f};
+                if ((D & 1) == 0) {   // two dimensions per 128-bit operand load
 #pragma unroll
-                for (int d = 0; d < DMAX; ++d) {
-                    if (d < D) {
+                    for (int d = 0; d < DMAX; d += 2) {
+                        if (d < D) {
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const int gl = gb + u * kWarps;
-                            if (gl < gs) {
-                                const float2 q = __ldg(a.op.sm + (size_t)(g0 + gl) * D + d);
-                                const float t = fmaf(xr[d], q.x, -q.y);
-                                acc[u] = fmaf(t, t, acc[u]);
+                            for (int u = 0; u < 4; ++u) {
+                                const int gl = gb + u * kWarps;
+                                if (gl < gs) {
+                                    const float4 q =
+                                        __ldg(reinterpret_cast<const float4 *>(a.op.sm + (size_t)(g0 + gl) * D + d));
+                                    const float ta = fmaf(xr[d], q.x, -q.y), tb = fmaf(xr[d + 1], q.z, -q.w);
+                                    acc[u] = fmaf(ta, ta, acc[u]);
+                                    acc2[u] = fmaf(tb, tb, acc2[u]);
+                                }
+                            }
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int d = 0; d < DMAX; ++d) {
+                        if (d < D) {
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                const int gl = gb + u * kWarps;
+                                if (gl < gs) {
+                                    const float2 q = __ldg(a.op.sm + (size_t)(g0 + gl) * D + d);
+                                    const float t = fmaf(xr[d], q.x, -q.y);
+                                    acc[u] = fmaf(t, t, acc[u]);
+                                }
                             }
                         }
                     }
@@ -1008,20 +1030,32 @@ __global__ void __launch_bounds__(kEmThreads, 1) k_em_slab_pass(EmPassArgs a, co
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int gl = gb + u * kWarps;
-                    if (gl < gs) L[gl * kTP + lane] = __expf(fmaf(-0.5f, acc[u], __ldg(a.op.c + g0 + gl)) - ls);
+                    if (gl < gs)
+                        L[gl * kTP + lane] = __expf(fmaf(-0.5f, acc[u] + acc2[u], __ldg(a.op.c + g0 + gl)) - ls);
                 }
             }
         }
+        if (tid == 0) s_nact = 0;
         __syncthreads();
-        for (int p0 = tid; p0 < gs * D; p0 += 4 * kEmThreads) {
+        // the slab's Gaussians holding a responsibility >= 1e-9 / N somewhere in the
+        // tile (the one-pass form's rule): the others add less than 1e-9 in all
+        for (int gl = tid; gl < gs; gl += kEmThreads) {
+            float mx = 0.f;
+            for (int i = 0; i < kTile; ++i) mx = fmaxf(mx, L[gl * kTP + i]);
+            if (mx >= keep) act[atomicAdd(&s_nact, 1)] = gl;
+        }
+        __syncthreads();
+        const int na = s_nact;
+        for (int p0 = tid; p0 < na * D; p0 += 4 * kEmThreads) {
             int gq[4], dq[4];
             float mu[4], r1[4], r2[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const int p = min(p0 + u * kEmThreads, gs * D - 1);
-                gq[u] = p / D;
-                dq[u] = p - gq[u] * D;
-                mu[u] = __ldg(a.op.mu + (size_t)g0 * D + p);
+                const int p = min(p0 + u * kEmThreads, na * D - 1);
+                const int ga = p / D;
+                gq[u] = act[ga];
+                dq[u] = p - ga * D;
+                mu[u] = __ldg(a.op.mu + (size_t)(g0 + gq[u]) * D + dq[u]);
                 r1[u] = 0.f;
                 r2[u] = 0.f;
             }
@@ -1038,10 +1072,15 @@ __global__ void __launch_bounds__(kEmThreads, 1) k_em_slab_pass(EmPassArgs a, co
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int p = p0 + u * kEmThreads;
-                if (p < gs * D) { S1[p] += r1[u]; S2[p] += r2[u]; }
+                if (p < na * D) {
+                    const int q = gq[u] * D + dq[u];
+                    S1[q] += r1[u];
+                    S2[q] += r2[u];
+                }
             }
         }
-        for (int g = tid; g < gs; g += kEmThreads) {
+        for (int k = tid; k < na; k += kEmThreads) {
+            const int g = act[k];
             float r0 = 0.f;
             for (int i = 0; i < kTile; ++i) r0 += L[g * kTP + i];
             S0[g] += r0;
@@ -1141,7 +1180,7 @@ __global__ void __launch_bounds__(128) k_log_p(const float *__restrict__ X, int6
     for (int g = 0; g < G; ++g) {
         const float l = logit(g) + __ldg(op.c + g);
         if (l > m) { s = s * __expf(m - l) + 1.f; m = l; }
-        else s += __expf(l - m);
+        else if (l > -INFINITY) s += __expf(l - m);   // -inf terms add nothing (and -inf - -inf is NaN)
     }
     out[i] = (double)m + log((double)s);
 }
@@ -1265,7 +1304,7 @@ __global__ void __launch_bounds__(128) k_log_p_blocksum(const float *__restrict_
             for (int g = 0; g < G; ++g) {
                 const float l = logit(g) + __ldg(op.c + g);
                 if (l > m) { s = s * __expf(m - l) + 1.f; m = l; }
-                else s += __expf(l - m);
+                else if (l > -INFINITY) s += __expf(l - m);   // -inf terms add nothing (and -inf - -inf is NaN)
             }
             v = (double)m + log((double)s);
         }
@@ -1615,7 +1654,7 @@ int em_slab_width(int32_t D, int32_t G)
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const size_t fixed = sizeof(float) * ((size_t)D * kTP + kTile);
-    const size_t per_g = sizeof(float) * (kTP + 1 + 2 * (size_t)D);
+    const size_t per_g = sizeof(float) * (kTP + 1 + 2 * (size_t)D) + sizeof(int);
     long gs = (long)(((size_t)optin - 2048 - fixed) / per_g);
     gs = gs / 8 * 8;
     if (gs > G) gs = G;
@@ -1628,7 +1667,8 @@ cudaError_t launch_em_two_phase(const EmPassArgs &a, float *lse, int32_t n_chunk
     if (GS < 1) return cudaErrorInvalidConfiguration;
     const int n_slabs = (a.G + GS - 1) / GS;
     const int blocks1 = (int)((a.N + 127) / 128);
-    const size_t sm = sizeof(float) * ((size_t)a.D * kTP + (size_t)GS * kTP + GS + 2 * (size_t)GS * a.D + kTile);
+    const size_t sm = sizeof(float) * ((size_t)a.D * kTP + (size_t)GS * kTP + GS + 2 * (size_t)GS * a.D + kTile) +
+                      sizeof(int) * (size_t)GS;
     const int dm = dmax_for(a.D);
 #define TP_LAUNCH(DM)                                                                                       \
     do {                                                                                                    \

@@ -278,6 +278,37 @@ def test_log_p_and_assign_match_oracle(shape):
     np.testing.assert_allclose(g.norm_hist(Xd, GMM_EUCL), hist / N)
 
 
+@pytest.mark.parametrize("shape", [(4000, 6, 5), (3000, 128, 300)])
+def test_zero_heft_gaussian_first(shape):
+    """A Gaussian with heft exactly 0 (log w = -inf; EM produces one when no
+    sample of the data gives it any responsibility) placed first: log p,
+    avg_log_p, the allocation-free average, prob assignment and an EM
+    iteration (the one-pass form, and the two-phase form for the 128 x 300
+    shape) all equal the oracle's, which takes log 0 = -inf exactly."""
+    import ctypes
+    from paper_1707_09094_gb300 import _lib
+    N, D, G = shape
+    X, _, mix = synth.make("c1", N=N, D=D, G=G, seed=12)
+    h = mix.hefts.copy()
+    h[0] = 0.0
+    h /= h.sum()
+    m, v = mix.means, mix.stds ** 2
+    Xd = dev(X)
+    g = GMM().set_params(m, v, h)
+    ref = oracle.log_p(X, m, v, h)
+    np.testing.assert_allclose(g.log_p(Xd).cpu().numpy(), ref, rtol=1e-6, atol=1e-5)
+    assert g.avg_log_p(Xd) == pytest.approx(ref.mean(), rel=1e-6)
+    out = ctypes.c_double()
+    assert _lib.load().gmm_avg_log_p_noalloc(g._h, ctypes.c_void_p(Xd.data_ptr()), N, -1, ctypes.byref(out),
+                                            None) == 0
+    assert out.value == pytest.approx(ref.mean(), rel=1e-6)
+    assert (g.assign(Xd, GMM_PROB).cpu().numpy() != 0).all()
+    M, V, H, ll = oracle.em_iterate(X, m, v, h, 1, 1e-10)
+    g.em_iterate(Xd, 1, recompute_center=True)
+    np.testing.assert_allclose(g.ll_history(), ll, rtol=1e-6)
+    assert g.get_params()[2][0] == 0.0 and H[0] == 0.0
+
+
 # ------------------------------------------------------------ full size (c2)
 @pytest.fixture(scope="module")
 def c2():
