@@ -1,0 +1,458 @@
+// Register-blocked FP32 EM pass for shapes whose per-CTA statistics do not
+// fit in shared memory next to all N_G operands (e.g. N_G = 1024, D = 128).
+// The iteration is the paper's map step (Sec. 2.1) split over blocks of 64
+// Gaussians:
+//   k_blk_lse     grid (sample chunk) x (Gaussian block): FP32 log-densities
+//                 log w_g N(x_i | g) of the block (Eq. 15, the direct form
+//                 sum_d (x_d s_gd - mu_gd s_gd)^2 in two FMA chains of D/2
+//                 terms each), reduced per sample to a partial log-sum-exp
+//                 (max, sum of exp) over the block (Eqs. 16-18);
+//   k_blk_combine log p(x_i) = merge of the blocks' partials; the CTA's FP64
+//                 log-likelihood;
+//   k_blk_em      the same log-densities again, responsibilities
+//                 l_{g,i} = exp(log w_g N - log p(x_i)) (Eq. 3), those below
+//                 1e-9 / N set to 0 (every Gaussian loses less than 1e-9 of
+//                 mass), and the block's shifted statistics sum l,
+//                 sum l (x - mu_f), sum l (x - mu_f)^2 (Eqs. 9-11 about the
+//                 FP32 mean mu_f of the iteration start) into the rows of the
+//                 chunk's FP64 partial.
+// Both log-density kernels hold the block's operands (s, mu s) in shared
+// memory and stream the chunk's samples in tiles staged by cp.async two-deep;
+// each thread computes a register block of samples x 4 Gaussians, so a
+// 128-bit shared load feeds 8-16 FMAs.  FP32 sums: a statistic is summed over
+// at most 64 samples in registers, then over at most 64 tiles in shared
+// memory, then in FP64.
+#include <cmath>
+
+#include "gmm_internal.cuh"
+
+namespace gmm {
+
+namespace {
+
+constexpr int kBG = 64;        // Gaussians per block
+constexpr int kBThreads = 256; // threads per CTA: a 16 x 16 grid of register blocks
+constexpr int kBFlush = 64;    // tiles summed in shared memory between FP64 flushes
+
+__device__ __forceinline__ bool blk_skip(const DevStatus *st, int iter)
+{
+    __shared__ int s_skip;
+    if (threadIdx.x == 0) s_skip = (st->halt != 0 || iter > st->stop_after) ? 1 : 0;
+    __syncthreads();
+    return s_skip != 0;
+}
+
+// Padded widths: D8 = D rounded up to 8 (zero dimensions add nothing); the
+// sample-row stride XS and operand-row stride OS are odd multiples of 16
+// bytes, so rows read together by a load phase lie in distinct bank groups.
+__host__ __device__ inline int blk_d8(int D) { return (D + 7) & ~7; }
+__host__ __device__ inline int blk_odd16(int n) { return ((n / 4) & 1) ? n : n + 4; }   // n a multiple of 4
+__host__ __device__ inline int blk_xs(int D) { return blk_odd16(blk_d8(D)); }
+__host__ __device__ inline int blk_os(int D) { return blk_odd16(2 * blk_d8(D)); }
+constexpr int kGS = kBG + 4;   // responsibility-tile row stride
+
+struct BlkArgs {
+    EmPassArgs a;
+    int32_t n_gb;        // Gaussian blocks: ceil(G / 64)
+    int32_t n_chunks;    // sample chunks
+    int32_t x_v4;        // D % 4 == 0 and X 16-byte aligned: rows staged 16 bytes at a time
+    float2 *part;        // [n_gb][N] (max, sum of exp) per sample and block
+    float *lse;          // [N] log p(x_i)
+};
+
+__host__ __device__ inline size_t blk_smem(int D, int TS, bool em)
+{
+    size_t f = (size_t)kBG * blk_os(D) + kBG + 2 * (size_t)TS * blk_xs(D) + TS;
+    if (em) f += (size_t)TS * kGS + (size_t)kBG * 2 * blk_d8(D) + kBG;
+    return f * sizeof(float);
+}
+
+__device__ __forceinline__ void cp_async16(float *dst, const float *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(float *dst, const float *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// (m, s) partial log-sum-exp merge; -inf terms add nothing
+__device__ __forceinline__ float2 lse_merge(float2 p, float2 q)
+{
+    const float M = fmaxf(p.x, q.x);
+    if (M == -INFINITY) return make_float2(-INFINITY, 0.f);
+    return make_float2(M, p.y * __expf(p.x - M) + q.y * __expf(q.x - M));
+}
+
+// Operands of Gaussian block gb -> shared memory: row g = (s_0, mu_0 s_0,
+// s_1, mu_1 s_1, ...) over D8 dimensions (zeros past D; zero rows and c = -inf
+// past G).
+__device__ void blk_stage_operands(const EmPassArgs &a, int g0, float *op, float *cg)
+{
+    const int D = a.D, D8 = blk_d8(D), OS = blk_os(D);
+    for (int k = threadIdx.x; k < kBG * D8; k += kBThreads) {
+        const int g = k / D8, d = k - g * D8;
+        float2 q = make_float2(0.f, 0.f);
+        if (g0 + g < a.G && d < D) q = __ldg(a.op.sm + (size_t)(g0 + g) * D + d);
+        op[g * OS + 2 * d] = q.x;
+        op[g * OS + 2 * d + 1] = q.y;
+    }
+    for (int g = threadIdx.x; g < kBG; g += kBThreads) cg[g] = g0 + g < a.G ? __ldg(a.op.c + g0 + g) : -INFINITY;
+}
+
+// Sample tile t (TS rows) -> buffer xb: cp.async for the rows that exist,
+// zeros for the rest; the zero columns D..D8-1 are written once beforehand.
+template <int TS>
+__device__ void blk_stage_tile(const BlkArgs &b, int64_t t, float *xb)
+{
+    const EmPassArgs &a = b.a;
+    const int D = a.D, XS = blk_xs(D);
+    const int64_t i0 = t * TS;
+    const int nv = (int)min((int64_t)TS, a.N - i0);
+    if (b.x_v4) {
+        const int q4 = D / 4;
+        for (int k = threadIdx.x; k < TS * q4; k += kBThreads) {
+            const int r = k / q4, c = k - r * q4;
+            if (r < nv) cp_async16(xb + r * XS + 4 * c, a.X + (i0 + r) * D + 4 * c);
+            else *reinterpret_cast<float4 *>(xb + r * XS + 4 * c) = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    } else {
+        for (int k = threadIdx.x; k < TS * D; k += kBThreads) {
+            const int r = k / D, c = k - r * D;
+            if (r < nv) cp_async4(xb + r * XS + c, a.X + (i0 + r) * D + c);
+            else xb[r * XS + c] = 0.f;
+        }
+    }
+}
+
+// FP32 log-densities of this thread's register block: samples sg + 16 k
+// (k < RS), Gaussians gg + 16 j (j < 4); two FMA chains per pair (dimensions
+// 0, 2 mod 4 and 1, 3 mod 4), the direct form of the CUDA-core pass.
+template <int RS>
+__device__ __forceinline__ void blk_logits(const float *xb, const float *op, const float *cg, int XS, int OS, int D8,
+                                           int sg, int gg, float (&l)[RS][4])
+{
+    float a0[RS][4], a1[RS][4];
+#pragma unroll
+    for (int k = 0; k < RS; ++k)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) { a0[k][j] = 0.f; a1[k][j] = 0.f; }
+    for (int d4 = 0; d4 < D8 / 4; ++d4) {
+        float4 xv[RS];
+#pragma unroll
+        for (int k = 0; k < RS; ++k) xv[k] = *reinterpret_cast<const float4 *>(xb + (sg + 16 * k) * XS + 4 * d4);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float4 qa = *reinterpret_cast<const float4 *>(op + (gg + 16 * j) * OS + 8 * d4);
+            const float4 qb = *reinterpret_cast<const float4 *>(op + (gg + 16 * j) * OS + 8 * d4 + 4);
+#pragma unroll
+            for (int k = 0; k < RS; ++k) {
+                const float t0 = fmaf(xv[k].x, qa.x, -qa.y), t1 = fmaf(xv[k].y, qa.z, -qa.w);
+                const float t2 = fmaf(xv[k].z, qb.x, -qb.y), t3 = fmaf(xv[k].w, qb.z, -qb.w);
+                a0[k][j] = fmaf(t0, t0, a0[k][j]);
+                a1[k][j] = fmaf(t1, t1, a1[k][j]);
+                a0[k][j] = fmaf(t2, t2, a0[k][j]);
+                a1[k][j] = fmaf(t3, t3, a1[k][j]);
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float c = cg[gg + 16 * j];
+#pragma unroll
+        for (int k = 0; k < RS; ++k) l[k][j] = fmaf(-0.5f, a0[k][j] + a1[k][j], c);
+    }
+}
+
+// ------------------------------------------------------------------------
+// Phase 1: partial log-sum-exp of each sample over one block of Gaussians.
+// Thread (sg, gg): warp w, lane l -> sg = 8 (w & 1) + (l & 7),
+// gg = 4 (w >> 1) + (l >> 3).
+// ------------------------------------------------------------------------
+template <int RS>
+__global__ void __launch_bounds__(kBThreads, 1) k_blk_lse(BlkArgs b)
+{
+    constexpr int TS = 16 * RS;
+    extern __shared__ __align__(16) float bsm[];
+    const EmPassArgs &a = b.a;
+    if (blk_skip(a.status, a.iter)) return;
+    const int D = a.D, D8 = blk_d8(D), XS = blk_xs(D), OS = blk_os(D);
+    const int gb = blockIdx.x % b.n_gb, chunk = blockIdx.x / b.n_gb;   // the chunk's blocks run side by side
+    float *op = bsm, *cg = op + kBG * OS, *xt = cg + kBG;
+    float2 *red = reinterpret_cast<float2 *>(xt + 2 * TS * XS);   // [4][TS] partials of the four Gaussian quarters
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    const int sg = 8 * (w & 1) + (lane & 7), gg = 4 * (w >> 1) + (lane >> 3);
+    blk_stage_operands(a, gb * kBG, op, cg);
+    for (int k = tid; k < 2 * TS * (XS - D); k += kBThreads) {   // zero columns D..XS-1 of both buffers
+        const int r = k / (XS - D);
+        xt[r * XS + D + (k - r * (XS - D))] = 0.f;
+    }
+    const int64_t ntiles = (a.N + TS - 1) / TS;
+    const int64_t t0 = ntiles * chunk / b.n_chunks, t1 = ntiles * (chunk + 1) / b.n_chunks;
+    __syncthreads();
+    if (t0 < t1) blk_stage_tile<TS>(b, t0, xt);
+    cp_commit();
+    for (int64_t t = t0; t < t1; ++t) {
+        const int bi = (int)((t - t0) & 1);
+        if (t + 1 < t1) blk_stage_tile<TS>(b, t + 1, xt + (1 - bi) * TS * XS);
+        cp_commit();
+        cp_wait<1>();
+        __syncthreads();
+        float l[RS][4];
+        blk_logits<RS>(xt + bi * TS * XS, op, cg, XS, OS, D8, sg, gg, l);
+        // per sample: this thread's four Gaussians, then the warp's four
+        // Gaussian groups (lanes ^ 8, ^ 16), then the four warps' quarters
+#pragma unroll
+        for (int k = 0; k < RS; ++k) {
+            const float m = fmaxf(fmaxf(l[k][0], l[k][1]), fmaxf(l[k][2], l[k][3]));
+            float s = 0.f;
+            if (m != -INFINITY)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) s += l[k][j] > -INFINITY ? __expf(l[k][j] - m) : 0.f;
+            float2 p = make_float2(m, s);
+            p = lse_merge(p, make_float2(__shfl_xor_sync(0xffffffffu, p.x, 8), __shfl_xor_sync(0xffffffffu, p.y, 8)));
+            p = lse_merge(p, make_float2(__shfl_xor_sync(0xffffffffu, p.x, 16), __shfl_xor_sync(0xffffffffu, p.y, 16)));
+            if (lane < 8) red[(w >> 1) * TS + sg + 16 * k] = p;
+        }
+        __syncthreads();
+        const int64_t i0 = t * TS;
+        for (int s = tid; s < TS; s += kBThreads) {
+            if (i0 + s < a.N) {
+                float2 p = red[s];
+#pragma unroll
+                for (int q = 1; q < 4; ++q) p = lse_merge(p, red[q * TS + s]);
+                b.part[(size_t)gb * a.N + i0 + s] = p;
+            }
+        }
+        // the next iteration restages buffer bi only after its barrier, which
+        // every thread reaches after it is done with red and buffer bi
+    }
+    cp_wait<0>();
+}
+
+// log p(x_i) from the blocks' partials; FP64 log-likelihood per 128 samples.
+__global__ void __launch_bounds__(128) k_blk_combine(BlkArgs b)
+{
+    __shared__ double sh[128];
+    const EmPassArgs &a = b.a;
+    if (blk_skip(a.status, a.iter)) return;
+    const int64_t i = (int64_t)blockIdx.x * 128 + threadIdx.x;
+    double v = 0.0;
+    if (i < a.N) {
+        float2 p = b.part[i];
+        for (int q = 1; q < b.n_gb; ++q) p = lse_merge(p, b.part[(size_t)q * a.N + i]);
+        const float ls = p.x + logf(p.y);
+        b.lse[i] = ls;
+        v = (double)ls;
+    }
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = 64; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) a.ll_partial[blockIdx.x] = sh[0];
+}
+
+// ------------------------------------------------------------------------
+// Phase 2: responsibilities and statistics of one block of Gaussians over one
+// sample chunk.  E-step threads as in phase 1 (RS = 4: 64-sample tiles); the
+// responsibilities go to a [64 samples][64 Gaussians] tile.  M-step thread
+// t < 16 NDG (NDG = D8 / 8 dimension groups): Gaussians 4 (t / NDG) + j,
+// dimensions 8 (t % NDG) + e; the threads of a warp skip a sample together
+// when none of their Gaussians holds a responsibility there.
+// ------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBThreads, 1) k_blk_em(BlkArgs b)
+{
+    constexpr int RS = 4, TS = 16 * RS;
+    extern __shared__ __align__(16) float bsm[];
+    const EmPassArgs &a = b.a;
+    if (blk_skip(a.status, a.iter)) return;
+    const int D = a.D, G = a.G, D8 = blk_d8(D), XS = blk_xs(D), OS = blk_os(D), S = 1 + 2 * D;
+    const int gb = blockIdx.x % b.n_gb, chunk = blockIdx.x / b.n_gb, g0 = gb * kBG;
+    float *op = bsm, *cg = op + kBG * OS, *xt = cg + kBG, *lt = xt + 2 * TS * XS, *gam = lt + TS;
+    float *m1 = gam + TS * kGS, *m2 = m1 + kBG * D8, *m0 = m2 + kBG * D8;   // shared-memory FP32 sums
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    const int sg = 8 * (w & 1) + (lane & 7), gg = 4 * (w >> 1) + (lane >> 3);
+    const int NDG = D8 / 8;
+    const bool mact = tid < 16 * NDG;
+    const int mq = mact ? tid / NDG : 0, dg = mact ? tid - mq * NDG : 0;
+    const float keep = (float)(1e-9 / (double)(a.N_total > a.N ? a.N_total : a.N));
+    blk_stage_operands(a, g0, op, cg);
+    for (int k = tid; k < 2 * TS * (XS - D); k += kBThreads) {
+        const int r = k / (XS - D);
+        xt[r * XS + D + (k - r * (XS - D))] = 0.f;
+    }
+    for (int k = tid; k < kBG * 2 * D8 + kBG; k += kBThreads) m1[k] = 0.f;   // m1 | m2 | m0
+    // this thread's M-step shifts mu_f (0 past G or D)
+    float mu[4][8];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int g = g0 + 4 * mq + j, d = 8 * dg + e;
+            mu[j][e] = (mact && g < G && d < D) ? __ldg(a.op.mu + (size_t)g * D + d) : 0.f;
+        }
+    double *P = a.partial + (size_t)chunk * G * S;
+    int flushes = 0, since = 0;
+    // shared-memory sums -> FP64 partial rows of this block (the first flush writes)
+    auto flush = [&]() {
+        if (mact) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int gl = 4 * mq + j, g = g0 + gl;
+                if (g >= G) continue;
+                double *row = P + (size_t)g * S;
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const int d = 8 * dg + e;
+                    if (d >= D) continue;
+                    const double v1 = (double)m1[gl * D8 + d], v2 = (double)m2[gl * D8 + d];
+                    row[1 + d] = flushes ? row[1 + d] + v1 : v1;
+                    row[1 + D + d] = flushes ? row[1 + D + d] + v2 : v2;
+                    m1[gl * D8 + d] = 0.f;
+                    m2[gl * D8 + d] = 0.f;
+                }
+                if (dg == 0) {
+                    const double v0 = (double)m0[gl];
+                    row[0] = flushes ? row[0] + v0 : v0;
+                    m0[gl] = 0.f;
+                }
+            }
+        }
+        ++flushes;
+        since = 0;
+    };
+    const int64_t ntiles = (a.N + TS - 1) / TS;
+    const int64_t t0 = ntiles * chunk / b.n_chunks, t1 = ntiles * (chunk + 1) / b.n_chunks;
+    __syncthreads();
+    if (t0 < t1) {
+        blk_stage_tile<TS>(b, t0, xt);
+        for (int s = tid; s < TS; s += kBThreads) lt[s] = t0 * TS + s < a.N ? b.lse[t0 * TS + s] : 0.f;
+    }
+    cp_commit();
+    for (int64_t t = t0; t < t1; ++t) {
+        const int bi = (int)((t - t0) & 1);
+        float *xb = xt + bi * TS * XS;
+        cp_wait<0>();
+        __syncthreads();
+        // ---- E: log-densities -> responsibilities (0 below keep; 0 past N)
+        {
+            float l[RS][4];
+            blk_logits<RS>(xb, op, cg, XS, OS, D8, sg, gg, l);
+            const int64_t i0 = t * TS;
+#pragma unroll
+            for (int k = 0; k < RS; ++k) {
+                const int s = sg + 16 * k;
+                const float ls = lt[s];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    float gm = i0 + s < a.N ? __expf(l[k][j] - ls) : 0.f;
+                    gam[s * kGS + gg + 16 * j] = gm >= keep ? gm : 0.f;
+                }
+            }
+        }
+        __syncthreads();
+        // the next tile's samples (other buffer) and log p, while the M-step
+        // runs: the E-step is done with lt
+        if (t + 1 < t1) {
+            blk_stage_tile<TS>(b, t + 1, xt + (1 - bi) * TS * XS);
+            for (int s = tid; s < TS; s += kBThreads) lt[s] = (t + 1) * TS + s < a.N ? b.lse[(t + 1) * TS + s] : 0.f;
+        }
+        cp_commit();
+        // ---- M: this thread's 4 Gaussians x 8 dimensions over the tile's samples
+        float s1[4][8], s2[4][8], s0[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            s0[j] = 0.f;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) { s1[j][e] = 0.f; s2[j][e] = 0.f; }
+        }
+        for (int s = 0; s < TS; ++s) {
+            const float4 g4 = *reinterpret_cast<const float4 *>(gam + s * kGS + 4 * mq);
+            const bool any = mact && (g4.x > 0.f || g4.y > 0.f || g4.z > 0.f || g4.w > 0.f);
+            if (!__any_sync(0xffffffffu, any)) continue;
+            const float4 xa = *reinterpret_cast<const float4 *>(xb + s * XS + 8 * dg);
+            const float4 xc = *reinterpret_cast<const float4 *>(xb + s * XS + 8 * dg + 4);
+            const float xe[8] = {xa.x, xa.y, xa.z, xa.w, xc.x, xc.y, xc.z, xc.w};
+            const float gj[4] = {g4.x, g4.y, g4.z, g4.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                s0[j] += gj[j];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const float u = xe[e] - mu[j][e];
+                    const float v = gj[j] * u;
+                    s1[j][e] += v;
+                    s2[j][e] = fmaf(v, u, s2[j][e]);
+                }
+            }
+        }
+        if (mact) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int gl = 4 * mq + j;
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    m1[gl * D8 + 8 * dg + e] += s1[j][e];
+                    m2[gl * D8 + 8 * dg + e] += s2[j][e];
+                }
+                if (dg == 0) m0[gl] += s0[j];
+            }
+        }
+        if (++since == kBFlush) flush();
+        __syncthreads();   // buffer bi and gam are free
+    }
+    cp_wait<0>();
+    flush();   // also writes the rows of a chunk with no tiles (zeros)
+}
+
+}  // namespace
+
+bool em_blocked_supported(int32_t D, int32_t G)
+{
+    if (D < 1 || D > 128 || G < 1) return false;
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return blk_smem(D, 128, false) + 4 * 128 * sizeof(float2) + 1024 <= (size_t)optin &&
+           blk_smem(D, 64, true) + 1024 <= (size_t)optin;
+}
+
+int em_blocked_gblocks(int32_t G) { return (G + kBG - 1) / kBG; }
+
+// Sample chunks: the fewest that make (chunks x Gaussian blocks) a whole
+// number of waves of one CTA per SM (up to 4 waves), else one wave's worth.
+int em_blocked_chunks(int32_t G, int sms)
+{
+    const int nb = em_blocked_gblocks(G);
+    for (int m = 1; m <= 4; ++m)
+        if ((m * sms) % nb == 0) return m * sms / nb;
+    const int c = sms / nb;
+    return c > 0 ? c : 1;
+}
+
+cudaError_t launch_em_blocked(const EmPassArgs &a, float *lse, float2 *part, int32_t n_chunks, cudaStream_t s)
+{
+    BlkArgs b{a, em_blocked_gblocks(a.G), n_chunks,
+              (a.D % 4 == 0 && (reinterpret_cast<uintptr_t>(a.X) & 15u) == 0) ? 1 : 0, part, lse};
+    const size_t sm1 = blk_smem(a.D, 128, false) + 4 * 128 * sizeof(float2);
+    const size_t sm3 = blk_smem(a.D, 64, true);
+    cudaError_t e = cudaFuncSetAttribute(k_blk_lse<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_blk_em, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3)) != cudaSuccess)
+        return e;
+    const int grid = b.n_gb * n_chunks;
+    k_blk_lse<8><<<grid, kBThreads, sm1, s>>>(b);
+    k_blk_combine<<<(int)((a.N + 127) / 128), 128, 0, s>>>(b);
+    k_blk_em<<<grid, kBThreads, sm3, s>>>(b);
+    count_launches(3);
+    return cudaGetLastError();
+}
+
+}  // namespace gmm

@@ -133,6 +133,7 @@ struct gmm_model {
     cudaStream_t cstream = nullptr;                           // host-input copies that overlap the first pass
     std::vector<cudaEvent_t> cev;                             // [0] start, [1..] chunk copies
     float *lse = nullptr; size_t lse_cap = 0;
+    float2 *lsep = nullptr; size_t lsep_cap = 0;               // register-blocked form: [Gaussian blocks][N] partials
     double *llp = nullptr; size_t llp_cap = 0;
     double *lld = nullptr; size_t lld_cap = 0;
     double *counts = nullptr; size_t counts_cap = 0;
@@ -323,14 +324,17 @@ gmm_status run_em(gmm_model *m, const float *Xd, int64_t N, int32_t em_iter, dou
     const bool tc = prec == GMM_BF16;
     if (tc && !gmm::em_tc_supported(D, G))
         return fail(GMM_ERR_UNSUPPORTED, "tensor-core E-step needs D <= 64 and n_gaus <= 256 (D=%d, G=%d)", D, G);
+    // FP32: the one-pass form while all N_G operands and statistics fit in one
+    // CTA's shared memory, else the register-blocked two-phase form
     const bool two_phase = !tc && !gmm::em_simt_supported(D, G);
-    if (two_phase && gmm::em_slab_width(D, G) < 1)
+    if (two_phase && !gmm::em_blocked_supported(D, G))
         return fail(GMM_ERR_UNSUPPORTED, "FP32 E-step: shared memory too small for D=%d, G=%d", D, G);
     if (tc && !(m->has_center && m->center_D == D))
         return fail(GMM_ERR_STATE, "tensor-core E-step needs the global centre (run learn or recompute_center)");
     // one-pass forms: one partial per CTA; two-phase form: one per sample chunk
     // (and one log-likelihood partial per 128-sample block of the lse pass)
-    const int grid = tc ? gmm::em_tc_grid(m->sms) : (two_phase ? m->sms : gmm::em_simt_grid(D, G, m->sms));
+    const int grid = tc ? gmm::em_tc_grid(m->sms)
+                        : (two_phase ? gmm::em_blocked_chunks(G, m->sms) : gmm::em_simt_grid(D, G, m->sms));
     if (two_phase && cp) {   // the two-phase form makes two passes: all of X first
         CK(cudaStreamWaitEvent(s, cp->ready.back(), 0));
         cp = nullptr;
@@ -339,6 +343,7 @@ gmm_status run_em(gmm_model *m, const float *Xd, int64_t N, int32_t em_iter, dou
     const int n_llp = two_phase ? (int)((N + 127) / 128) : grid;
     CK(grow(m->partial, m->partial_cap, (size_t)nch * grid * G * S));
     if (two_phase) CK(grow(m->lse, m->lse_cap, (size_t)N));
+    if (two_phase) CK(grow(m->lsep, m->lsep_cap, (size_t)gmm::em_blocked_gblocks(G) * (size_t)N));
     if (tc) CK(grow(m->tclist, m->tclist_cap, gmm::em_tc_list_bytes(N, grid)));
     CK(grow(m->llp, m->llp_cap, (size_t)nch * n_llp));
     CK(grow(m->lld, m->lld_cap, (size_t)(em_iter > 0 ? em_iter : 1)));
@@ -358,7 +363,7 @@ gmm_status run_em(gmm_model *m, const float *Xd, int64_t N, int32_t em_iter, dou
                                m->llp + (size_t)c * n_llp, m->status, k, m->wait_cycles, m->skip_mma,
                                m->profiling ? m->sstats : nullptr, N};
             if (tc) CK(gmm::launch_em_pass_tc(pa, gmm::em_tc_lists(m->tclist, b1 - b0, grid), grid, grid, s));
-            else if (two_phase) CK(gmm::launch_em_two_phase(pa, m->lse, grid, s));
+            else if (two_phase) CK(gmm::launch_em_blocked(pa, m->lse, m->lsep, grid, s));
             else CK(gmm::launch_em_pass_simt(pa, grid, s));
         }
         if ((prc = prof_end(m, s, slot)) != GMM_OK) return prc;
@@ -443,7 +448,7 @@ void gmm_destroy(gmm_model *m)
     if (m->sstats) cudaFree(m->sstats);
     void *bufs[] = {m->par[0], m->par[1], m->op_sm, m->op_mu, m->op_c, m->op_B, m->gstat, m->fstat,
                     m->partial, m->slab, m->lse, m->llp, m->lld, m->counts, m->assign, m->xstage, m->dstage, m->idx,
-                    m->hist, m->status, m->tclist, m->kmop, m->spread};
+                    m->hist, m->status, m->tclist, m->kmop, m->spread, m->lsep};
     for (void *p : bufs)
         if (p) cudaFree(p);
     delete m;

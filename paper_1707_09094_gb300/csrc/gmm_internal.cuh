@@ -95,8 +95,12 @@ cudaError_t launch_em_prep(int32_t D, int32_t G, const double *par, Operands op,
                            int32_t build_tc, cudaStream_t s);
 cudaError_t launch_em_pass_simt(const EmPassArgs &a, int32_t grid, cudaStream_t s);
 cudaError_t launch_em_finalize(const EmFinalizeArgs &a, cudaStream_t s);
-int em_slab_width(int32_t D, int32_t G);
-cudaError_t launch_em_two_phase(const EmPassArgs &a, float *lse, int32_t n_chunks, cudaStream_t s);
+// ---- register-blocked FP32 form (gmm_blocked.cu): blocks of 64 Gaussians,
+// partial log-sum-exp per (block, sample) in part [gblocks][N]
+bool em_blocked_supported(int32_t D, int32_t G);
+int em_blocked_gblocks(int32_t G);
+int em_blocked_chunks(int32_t G, int sms);
+cudaError_t launch_em_blocked(const EmPassArgs &a, float *lse, float2 *part, int32_t n_chunks, cudaStream_t s);
 cudaError_t launch_log_p(const float *X, int64_t N, int32_t D, int32_t G, Operands op, int32_t g,
                          double *out, cudaStream_t s);
 cudaError_t launch_assign(const float *X, int64_t N, int32_t D, int32_t G, const double *par,

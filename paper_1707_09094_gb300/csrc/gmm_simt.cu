@@ -901,200 +901,6 @@ __global__ void __launch_bounds__(kEmThreads, 1) k_em_pass_simt(EmPassArgs a)
     }
 }
 
-// ------------------------------------------------------------------------
-// Two-phase FP32 form for shapes whose per-CTA statistics do not fit in
-// shared memory (e.g. N_G = 1024, D = 128).
-//   phase 1 (k_lse_pass)  log p(x_i) = log-sum-exp over all Gaussians of the
-//            FP32 log-densities (online max/sum per thread, Eqs. 16-18),
-//            written to lse[N]; per-CTA FP64 log-likelihood.
-//   phase 2 (k_em_slab_pass)  grid = (sample chunks) x (Gaussian slabs):
-//            each CTA recomputes the log-densities of its slab, takes
-//            l_{g,i} = exp(l_g - lse_i) (Eq. 3) and accumulates the slab's
-//            shifted statistics exactly as the one-pass FP32 form, into the
-//            rows of its chunk's FP64 partial.
-// ------------------------------------------------------------------------
-template <int DMAX>
-__global__ void __launch_bounds__(128) k_lse_pass(EmPassArgs a, float *__restrict__ lse)
-{
-    __shared__ double sh[128];
-    if (block_skip(a.status, a.iter)) return;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    double v = 0.0;
-    if (i < a.N) {
-        float xr[DMAX];
-#pragma unroll
-        for (int d = 0; d < DMAX; ++d) xr[d] = d < a.D ? a.X[i * a.D + d] : 0.f;
-        float m = -INFINITY, s = 0.f;
-        for (int g = 0; g < a.G; ++g) {
-            const float2 *p = a.op.sm + (size_t)g * a.D;
-            float acc0 = 0.f, acc1 = 0.f;
-#pragma unroll
-            for (int d = 0; d < DMAX; d += 2) {
-                if (d < a.D) {
-                    const float2 q = __ldg(p + d);
-                    const float t = fmaf(xr[d], q.x, -q.y);
-                    acc0 = fmaf(t, t, acc0);
-                }
-                if (d + 1 < a.D) {
-                    const float2 q = __ldg(p + d + 1);
-                    const float t = fmaf(xr[d + 1], q.x, -q.y);
-                    acc1 = fmaf(t, t, acc1);
-                }
-            }
-            const float l = fmaf(-0.5f, acc0 + acc1, __ldg(a.op.c + g));
-            if (l > m) { s = s * __expf(m - l) + 1.f; m = l; }
-            else if (l > -INFINITY) s += __expf(l - m);   // -inf terms add nothing (and -inf - -inf is NaN)
-        }
-        const float ls = m + logf(s);
-        lse[i] = ls;
-        v = (double)ls;
-    }
-    v = block_sum_d(v, sh);
-    if (threadIdx.x == 0) a.ll_partial[blockIdx.x] = v;
-}
-
-template <int DMAX>
-__global__ void __launch_bounds__(kEmThreads, 1) k_em_slab_pass(EmPassArgs a, const float *__restrict__ lse, int32_t GS,
-                                                              int32_t n_chunks)
-{
-    extern __shared__ __align__(16) float em_smem[];
-    if (block_skip(a.status, a.iter)) return;
-    const int D = a.D, G = a.G;
-    const int chunk = blockIdx.x % n_chunks, slab = blockIdx.x / n_chunks;
-    const int g0 = slab * GS, gs = min(GS, G - g0);
-    float *xT = em_smem;                          // [D][kTP]
-    float *L = xT + (size_t)D * kTP;              // [GS][kTP]
-    float *S0 = L + (size_t)GS * kTP;             // [GS]
-    float *S1 = S0 + GS;                          // [GS*D]
-    float *S2 = S1 + (size_t)GS * D;              // [GS*D]
-    float *lt = S2 + (size_t)GS * D;              // [kTile]
-    int *act = reinterpret_cast<int *>(lt + kTile);   // [GS] Gaussians that matter in the tile
-    __shared__ int s_nact;
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const float keep = (float)(1e-9 / (double)(a.N_total > a.N ? a.N_total : a.N));
-    for (int k = tid; k < gs; k += kEmThreads) S0[k] = 0.f;
-    for (int k = tid; k < gs * D; k += kEmThreads) { S1[k] = 0.f; S2[k] = 0.f; }
-    const int64_t ntiles = (a.N + kTile - 1) / kTile;
-    const int64_t t0 = ntiles * chunk / n_chunks, t1 = ntiles * (chunk + 1) / n_chunks;
-    for (int64_t tile = t0; tile < t1; ++tile) {
-        const int64_t i0 = tile * kTile;
-        const int n = (int)min((int64_t)kTile, a.N - i0);
-        __syncthreads();
-        const float *Xt = a.X + i0 * D;
-        for (int k = tid; k < kTile * D; k += kEmThreads) {
-            const int i = k / D, d = k - i * D;
-            xT[d * kTP + i] = i < n ? Xt[k] : 0.f;
-        }
-        for (int i = tid; i < kTile; i += kEmThreads) lt[i] = i < n ? lse[i0 + i] : INFINITY;
-        __syncthreads();
-        {
-            float xr[DMAX];
-#pragma unroll
-            for (int d = 0; d < DMAX; ++d) xr[d] = d < D ? xT[d * kTP + lane] : 0.f;
-            const float ls = lt[lane];
-            for (int gb = w; gb < gs; gb += 4 * kWarps) {
-                float acc[4] = {0.f, 0.f, 0.f, 0.f}, acc2[4] = {0.f, 0.f, 0.f, 0.f};
-                if ((D & 1) == 0) {   // two dimensions per 128-bit operand load
-#pragma unroll
-                    for (int d = 0; d < DMAX; d += 2) {
-                        if (d < D) {
-#pragma unroll
-                            for (int u = 0; u < 4; ++u) {
-                                const int gl = gb + u * kWarps;
-                                if (gl < gs) {
-                                    const float4 q =
-                                        __ldg(reinterpret_cast<const float4 *>(a.op.sm + (size_t)(g0 + gl) * D + d));
-                                    const float ta = fmaf(xr[d], q.x, -q.y), tb = fmaf(xr[d + 1], q.z, -q.w);
-                                    acc[u] = fmaf(ta, ta, acc[u]);
-                                    acc2[u] = fmaf(tb, tb, acc2[u]);
-                                }
-                            }
-                        }
-                    }
-                } else {
-#pragma unroll
-                    for (int d = 0; d < DMAX; ++d) {
-                        if (d < D) {
-#pragma unroll
-                            for (int u = 0; u < 4; ++u) {
-                                const int gl = gb + u * kWarps;
-                                if (gl < gs) {
-                                    const float2 q = __ldg(a.op.sm + (size_t)(g0 + gl) * D + d);
-                                    const float t = fmaf(xr[d], q.x, -q.y);
-                                    acc[u] = fmaf(t, t, acc[u]);
-                                }
-                            }
-                        }
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int gl = gb + u * kWarps;
-                    if (gl < gs)
-                        L[gl * kTP + lane] = __expf(fmaf(-0.5f, acc[u] + acc2[u], __ldg(a.op.c + g0 + gl)) - ls);
-                }
-            }
-        }
-        if (tid == 0) s_nact = 0;
-        __syncthreads();
-        // the slab's Gaussians holding a responsibility >= 1e-9 / N somewhere in the
-        // tile (the one-pass form's rule): the others add less than 1e-9 in all
-        for (int gl = tid; gl < gs; gl += kEmThreads) {
-            float mx = 0.f;
-            for (int i = 0; i < kTile; ++i) mx = fmaxf(mx, L[gl * kTP + i]);
-            if (mx >= keep) act[atomicAdd(&s_nact, 1)] = gl;
-        }
-        __syncthreads();
-        const int na = s_nact;
-        for (int p0 = tid; p0 < na * D; p0 += 4 * kEmThreads) {
-            int gq[4], dq[4];
-            float mu[4], r1[4], r2[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int p = min(p0 + u * kEmThreads, na * D - 1);
-                const int ga = p / D;
-                gq[u] = act[ga];
-                dq[u] = p - ga * D;
-                mu[u] = __ldg(a.op.mu + (size_t)(g0 + gq[u]) * D + dq[u]);
-                r1[u] = 0.f;
-                r2[u] = 0.f;
-            }
-#pragma unroll 4
-            for (int i = 0; i < kTile; ++i) {
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const float gm = L[gq[u] * kTP + i];
-                    const float uu = xT[dq[u] * kTP + i] - mu[u];
-                    r1[u] = fmaf(gm, uu, r1[u]);
-                    r2[u] = fmaf(gm * uu, uu, r2[u]);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int p = p0 + u * kEmThreads;
-                if (p < na * D) {
-                    const int q = gq[u] * D + dq[u];
-                    S1[q] += r1[u];
-                    S2[q] += r2[u];
-                }
-            }
-        }
-        for (int k = tid; k < na; k += kEmThreads) {
-            const int g = act[k];
-            float r0 = 0.f;
-            for (int i = 0; i < kTile; ++i) r0 += L[g * kTP + i];
-            S0[g] += r0;
-        }
-    }
-    __syncthreads();
-    const int S = 1 + 2 * D;
-    double *P = a.partial + ((size_t)chunk * G + g0) * S;
-    for (int k = tid; k < gs * S; k += kEmThreads) {
-        const int g = k / S, j = k - g * S;
-        P[k] = j == 0 ? (double)S0[g] : (j <= D ? (double)S1[g * D + j - 1] : (double)S2[g * D + j - 1 - D]);
-    }
-}
-
 // Log-likelihood reduce (CTA order) and the stopping rule: ll_hist[iter] =
 // log p(X | lambda_iter) / N; with em_tol > 0, iteration iter >= 1 whose gain
 // is below em_tol is the last one.
@@ -1643,45 +1449,6 @@ cudaError_t launch_em_pass_simt(const EmPassArgs &a, int32_t grid, cudaStream_t 
     else EM_LAUNCH(128);
 #undef EM_LAUNCH
     count_launches(1);
-    return cudaGetLastError();
-}
-
-// Two-phase form: the slab width GS (Gaussians per CTA) is the largest
-// multiple of 8 whose statistics and tile buffers fit in shared memory.
-int em_slab_width(int32_t D, int32_t G)
-{
-    int dev = 0, optin = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const size_t fixed = sizeof(float) * ((size_t)D * kTP + kTile);
-    const size_t per_g = sizeof(float) * (kTP + 1 + 2 * (size_t)D) + sizeof(int);
-    long gs = (long)(((size_t)optin - 2048 - fixed) / per_g);
-    gs = gs / 8 * 8;
-    if (gs > G) gs = G;
-    return gs < 8 ? (G < 8 ? G : 0) : (int)gs;
-}
-
-cudaError_t launch_em_two_phase(const EmPassArgs &a, float *lse, int32_t n_chunks, cudaStream_t s)
-{
-    const int GS = em_slab_width(a.D, a.G);
-    if (GS < 1) return cudaErrorInvalidConfiguration;
-    const int n_slabs = (a.G + GS - 1) / GS;
-    const int blocks1 = (int)((a.N + 127) / 128);
-    const size_t sm = sizeof(float) * ((size_t)a.D * kTP + (size_t)GS * kTP + GS + 2 * (size_t)GS * a.D + kTile) +
-                      sizeof(int) * (size_t)GS;
-    const int dm = dmax_for(a.D);
-#define TP_LAUNCH(DM)                                                                                       \
-    do {                                                                                                    \
-        k_lse_pass<DM><<<blocks1, 128, 0, s>>>(a, lse);                                                     \
-        cudaFuncSetAttribute(k_em_slab_pass<DM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);     \
-        k_em_slab_pass<DM><<<n_chunks * n_slabs, kEmThreads, sm, s>>>(a, lse, GS, n_chunks);                \
-    } while (0)
-    if (dm == 16) TP_LAUNCH(16);
-    else if (dm == 32) TP_LAUNCH(32);
-    else if (dm == 64) TP_LAUNCH(64);
-    else TP_LAUNCH(128);
-#undef TP_LAUNCH
-    count_launches(2);
     return cudaGetLastError();
 }
 

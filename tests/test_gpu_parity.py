@@ -340,7 +340,9 @@ def test_c2_full_size_log_p_sampled(c2):
 @pytest.mark.parametrize("shape", [(6000, 128, 300), (8000, 100, 600), (30000, 17, 2500)])
 def test_two_phase_em_matches_oracle(shape):
     """Shapes whose per-CTA statistics exceed shared memory run the two-phase
-    FP32 form (log-sum-exp pass, then per-Gaussian-slab passes).  Started from
+    FP32 form (partial log-sum-exps per block of 64 Gaussians and their merge,
+    then responsibilities and statistics per block; D = 17 takes the
+    unaligned staging path, N_G = 2500 a partial last block).  Started from
     k-means (>= 10 samples per Gaussian, as the paper recommends): from unit
     variances in 100+ dimensions the log-densities reach thousands of nats and
     FP32 resolves responsibilities only to ~1e-3."""
