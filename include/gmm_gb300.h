@@ -362,6 +362,14 @@ gmm_status gmm_profile_read(const gmm_model *m, double *pass_ms, int64_t *pass_l
  *                          both forms decide the nearest mean exactly);
  *                          1: on the CUDA cores. */
 #define GMM_DEBUG_KM_FORM 3
+/*   GMM_DEBUG_FP32_FORM    0 (default): the FP32 EM pass runs the one-pass
+ *                          form for N_G <= 128 where all N_G operands and
+ *                          statistics fit in one CTA's shared memory, else
+ *                          the register-blocked two-phase form; 1: the
+ *                          one-pass form wherever it fits; 2: the
+ *                          register-blocked form for every shape (the same
+ *                          results to FP32 rounding). */
+#define GMM_DEBUG_FP32_FORM 4
 gmm_status gmm_debug_set(gmm_model *m, int32_t key, int64_t value);
 
 /* Screening counters of the tensor-core pass, summed since the last

@@ -233,7 +233,7 @@ class GMM:
         return ms.value, n.value, k.value
 
     def debug_set(self, key, value):
-        """Test hooks (GMM_DEBUG_WAIT_CYCLES, GMM_DEBUG_SKIP_MMA, GMM_DEBUG_KM_FORM)."""
+        """Test hooks (GMM_DEBUG_WAIT_CYCLES, GMM_DEBUG_SKIP_MMA, GMM_DEBUG_KM_FORM, GMM_DEBUG_FP32_FORM)."""
         _lib.check(_lib.load().gmm_debug_set(self._h, key, int(value)), "gmm_debug_set")
         return self
 

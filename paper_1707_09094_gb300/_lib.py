@@ -17,7 +17,7 @@ GMM_ERR_TIMEOUT, GMM_ERR_OOM, GMM_ERR_STATE, GMM_ERR_UNSUPPORTED = -4, -5, -6, -
 GMM_EUCL, GMM_MAHA, GMM_PROB = 0, 1, 2
 GMM_KEEP_EXISTING, GMM_RANDOM_SUBSET, GMM_STATIC_SUBSET, GMM_STATIC_SPREAD, GMM_RANDOM_SPREAD = 0, 1, 2, 3, 4
 GMM_FP32, GMM_BF16 = 0, 1
-GMM_DEBUG_WAIT_CYCLES, GMM_DEBUG_SKIP_MMA, GMM_DEBUG_KM_FORM = 1, 2, 3
+GMM_DEBUG_WAIT_CYCLES, GMM_DEBUG_SKIP_MMA, GMM_DEBUG_KM_FORM, GMM_DEBUG_FP32_FORM = 1, 2, 3, 4
 GMM_STAT_SCREENED, GMM_STAT_KEPT, GMM_STAT_DENSE = 3, 4, 5
 GMM_STAT_KM_SCREENED, GMM_STAT_KM_DEFERRED, GMM_STAT_KM_FP64 = 14, 15, 16
 

@@ -50,6 +50,7 @@ __host__ __device__ inline int blk_odd16(int n) { return ((n / 4) & 1) ? n : n +
 __host__ __device__ inline int blk_xs(int D) { return blk_odd16(blk_d8(D)); }
 __host__ __device__ inline int blk_os(int D) { return blk_odd16(2 * blk_d8(D)); }
 constexpr int kGS = kBG + 4;   // responsibility-tile row stride
+constexpr int kMacc = 17;      // float4 slots of shared-memory sums per M-step thread: 8 S1, 8 S2, 1 S0
 
 struct BlkArgs {
     EmPassArgs a;
@@ -63,7 +64,7 @@ struct BlkArgs {
 __host__ __device__ inline size_t blk_smem(int D, int TS, bool em)
 {
     size_t f = (size_t)kBG * blk_os(D) + kBG + 2 * (size_t)TS * blk_xs(D) + TS;
-    if (em) f += (size_t)TS * kGS + (size_t)kBG * 2 * blk_d8(D) + kBG;
+    if (em) f += (size_t)TS * kGS + 4 * (size_t)kMacc * kBThreads;
     return f * sizeof(float);
 }
 
@@ -89,9 +90,10 @@ __device__ __forceinline__ float2 lse_merge(float2 p, float2 q)
     return make_float2(M, p.y * __expf(p.x - M) + q.y * __expf(q.x - M));
 }
 
-// Operands of Gaussian block gb -> shared memory: row g = (s_0, mu_0 s_0,
-// s_1, mu_1 s_1, ...) over D8 dimensions (zeros past D; zero rows and c = -inf
-// past G).
+// Operands of Gaussian block gb -> shared memory: row g holds, per pair of
+// dimensions (2p, 2p+1), (s_2p, s_2p+1, -mu_2p s_2p, -mu_2p+1 s_2p+1) over D8
+// dimensions (zeros past D; zero rows and c = -inf past G), the packed-FP32
+// operands of two dimensions.
 __device__ void blk_stage_operands(const EmPassArgs &a, int g0, float *op, float *cg)
 {
     const int D = a.D, D8 = blk_d8(D), OS = blk_os(D);
@@ -99,8 +101,8 @@ __device__ void blk_stage_operands(const EmPassArgs &a, int g0, float *op, float
         const int g = k / D8, d = k - g * D8;
         float2 q = make_float2(0.f, 0.f);
         if (g0 + g < a.G && d < D) q = __ldg(a.op.sm + (size_t)(g0 + g) * D + d);
-        op[g * OS + 2 * d] = q.x;
-        op[g * OS + 2 * d + 1] = q.y;
+        op[g * OS + 4 * (d >> 1) + (d & 1)] = q.x;
+        op[g * OS + 4 * (d >> 1) + 2 + (d & 1)] = -q.y;
     }
     for (int g = threadIdx.x; g < kBG; g += kBThreads) cg[g] = g0 + g < a.G ? __ldg(a.op.c + g0 + g) : -INFINITY;
 }
@@ -132,16 +134,19 @@ __device__ void blk_stage_tile(const BlkArgs &b, int64_t t, float *xb)
 
 // FP32 log-densities of this thread's register block: samples sg + 16 k
 // (k < RS), Gaussians gg + 16 j (j < 4); two FMA chains per pair (dimensions
-// 0, 2 mod 4 and 1, 3 mod 4), the direct form of the CUDA-core pass.
+// 0, 2 mod 4 and 1, 3 mod 4), the direct form of the CUDA-core pass, two
+// dimensions per packed FP32 instruction (each half an IEEE fma: the same
+// values as scalar FMAs).
 template <int RS>
 __device__ __forceinline__ void blk_logits(const float *xb, const float *op, const float *cg, int XS, int OS, int D8,
                                            int sg, int gg, float (&l)[RS][4])
 {
-    float a0[RS][4], a1[RS][4];
+    float2 acc[RS][4];
 #pragma unroll
     for (int k = 0; k < RS; ++k)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) { a0[k][j] = 0.f; a1[k][j] = 0.f; }
+        for (int j = 0; j < 4; ++j) acc[k][j] = make_float2(0.f, 0.f);
+#pragma unroll 2
     for (int d4 = 0; d4 < D8 / 4; ++d4) {
         float4 xv[RS];
 #pragma unroll
@@ -150,14 +155,14 @@ __device__ __forceinline__ void blk_logits(const float *xb, const float *op, con
         for (int j = 0; j < 4; ++j) {
             const float4 qa = *reinterpret_cast<const float4 *>(op + (gg + 16 * j) * OS + 8 * d4);
             const float4 qb = *reinterpret_cast<const float4 *>(op + (gg + 16 * j) * OS + 8 * d4 + 4);
+            const float2 sa = make_float2(qa.x, qa.y), ma = make_float2(qa.z, qa.w);
+            const float2 sb = make_float2(qb.x, qb.y), mb = make_float2(qb.z, qb.w);
 #pragma unroll
             for (int k = 0; k < RS; ++k) {
-                const float t0 = fmaf(xv[k].x, qa.x, -qa.y), t1 = fmaf(xv[k].y, qa.z, -qa.w);
-                const float t2 = fmaf(xv[k].z, qb.x, -qb.y), t3 = fmaf(xv[k].w, qb.z, -qb.w);
-                a0[k][j] = fmaf(t0, t0, a0[k][j]);
-                a1[k][j] = fmaf(t1, t1, a1[k][j]);
-                a0[k][j] = fmaf(t2, t2, a0[k][j]);
-                a1[k][j] = fmaf(t3, t3, a1[k][j]);
+                const float2 t01 = __ffma2_rn(make_float2(xv[k].x, xv[k].y), sa, ma);
+                const float2 t23 = __ffma2_rn(make_float2(xv[k].z, xv[k].w), sb, mb);
+                acc[k][j] = __ffma2_rn(t01, t01, acc[k][j]);
+                acc[k][j] = __ffma2_rn(t23, t23, acc[k][j]);
             }
         }
     }
@@ -165,7 +170,7 @@ __device__ __forceinline__ void blk_logits(const float *xb, const float *op, con
     for (int j = 0; j < 4; ++j) {
         const float c = cg[gg + 16 * j];
 #pragma unroll
-        for (int k = 0; k < RS; ++k) l[k][j] = fmaf(-0.5f, a0[k][j] + a1[k][j], c);
+        for (int k = 0; k < RS; ++k) l[k][j] = fmaf(-0.5f, acc[k][j].x + acc[k][j].y, c);
     }
 }
 
@@ -276,7 +281,10 @@ __global__ void __launch_bounds__(kBThreads, 1) k_blk_em(BlkArgs b)
     const int D = a.D, G = a.G, D8 = blk_d8(D), XS = blk_xs(D), OS = blk_os(D), S = 1 + 2 * D;
     const int gb = blockIdx.x % b.n_gb, chunk = blockIdx.x / b.n_gb, g0 = gb * kBG;
     float *op = bsm, *cg = op + kBG * OS, *xt = cg + kBG, *lt = xt + 2 * TS * XS, *gam = lt + TS;
-    float *m1 = gam + TS * kGS, *m2 = m1 + kBG * D8, *m0 = m2 + kBG * D8;   // shared-memory FP32 sums
+    // shared-memory FP32 sums, slot q of thread t at macc[q * kBThreads + t]:
+    // q = 2 j + h: S1 of Gaussian j, dimensions 4 h..4 h+3 of the group;
+    // 8 + 2 j + h: S2; 16: S0 of the four Gaussians
+    float4 *macc = reinterpret_cast<float4 *>(gam + TS * kGS);
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     const int sg = 8 * (w & 1) + (lane & 7), gg = 4 * (w >> 1) + (lane >> 3);
     const int NDG = D8 / 8;
@@ -288,42 +296,47 @@ __global__ void __launch_bounds__(kBThreads, 1) k_blk_em(BlkArgs b)
         const int r = k / (XS - D);
         xt[r * XS + D + (k - r * (XS - D))] = 0.f;
     }
-    for (int k = tid; k < kBG * 2 * D8 + kBG; k += kBThreads) m1[k] = 0.f;   // m1 | m2 | m0
-    // this thread's M-step shifts mu_f (0 past G or D)
-    float mu[4][8];
+    for (int q = 0; q < kMacc; ++q) macc[q * kBThreads + tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+    // this thread's M-step shifts, negated: -mu_f (0 past G or D), pairs of dimensions
+    float2 nmu[4][4];
 #pragma unroll
     for (int j = 0; j < 4; ++j)
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const int g = g0 + 4 * mq + j, d = 8 * dg + e;
-            mu[j][e] = (mact && g < G && d < D) ? __ldg(a.op.mu + (size_t)g * D + d) : 0.f;
+        for (int e = 0; e < 4; ++e) {
+            const int g = g0 + 4 * mq + j, d = 8 * dg + 2 * e;
+            nmu[j][e] = make_float2((mact && g < G && d < D) ? -__ldg(a.op.mu + (size_t)g * D + d) : 0.f,
+                                    (mact && g < G && d + 1 < D) ? -__ldg(a.op.mu + (size_t)g * D + d + 1) : 0.f);
         }
     double *P = a.partial + (size_t)chunk * G * S;
     int flushes = 0, since = 0;
     // shared-memory sums -> FP64 partial rows of this block (the first flush writes)
     auto flush = [&]() {
         if (mact) {
+            const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 f0 = macc[16 * kBThreads + tid];
+            const float s0v[4] = {f0.x, f0.y, f0.z, f0.w};
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const int gl = 4 * mq + j, g = g0 + gl;
+                const int g = g0 + 4 * mq + j;
                 if (g >= G) continue;
                 double *row = P + (size_t)g * S;
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const int d = 8 * dg + e;
-                    if (d >= D) continue;
-                    const double v1 = (double)m1[gl * D8 + d], v2 = (double)m2[gl * D8 + d];
-                    row[1 + d] = flushes ? row[1 + d] + v1 : v1;
-                    row[1 + D + d] = flushes ? row[1 + D + d] + v2 : v2;
-                    m1[gl * D8 + d] = 0.f;
-                    m2[gl * D8 + d] = 0.f;
+                for (int h = 0; h < 2; ++h) {
+                    const float4 f1 = macc[(2 * j + h) * kBThreads + tid], f2 = macc[(8 + 2 * j + h) * kBThreads + tid];
+                    const float v1[4] = {f1.x, f1.y, f1.z, f1.w}, v2[4] = {f2.x, f2.y, f2.z, f2.w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int d = 8 * dg + 4 * h + e;
+                        if (d >= D) continue;
+                        row[1 + d] = flushes ? row[1 + d] + (double)v1[e] : (double)v1[e];
+                        row[1 + D + d] = flushes ? row[1 + D + d] + (double)v2[e] : (double)v2[e];
+                    }
+                    macc[(2 * j + h) * kBThreads + tid] = z;
+                    macc[(8 + 2 * j + h) * kBThreads + tid] = z;
                 }
-                if (dg == 0) {
-                    const double v0 = (double)m0[gl];
-                    row[0] = flushes ? row[0] + v0 : v0;
-                    m0[gl] = 0.f;
-                }
+                if (dg == 0) row[0] = flushes ? row[0] + (double)s0v[j] : (double)s0v[j];
             }
+            macc[16 * kBThreads + tid] = z;
         }
         ++flushes;
         since = 0;
@@ -365,45 +378,79 @@ __global__ void __launch_bounds__(kBThreads, 1) k_blk_em(BlkArgs b)
             for (int s = tid; s < TS; s += kBThreads) lt[s] = (t + 1) * TS + s < a.N ? b.lse[(t + 1) * TS + s] : 0.f;
         }
         cp_commit();
-        // ---- M: this thread's 4 Gaussians x 8 dimensions over the tile's samples
-        float s1[4][8], s2[4][8], s0[4];
+        // ---- M: this thread's 4 Gaussians x 8 dimensions over the tile's
+        // samples, two dimensions per packed FP32 instruction
+        float2 s1[4][4], s2[4][4];
+        float s0[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             s0[j] = 0.f;
 #pragma unroll
-            for (int e = 0; e < 8; ++e) { s1[j][e] = 0.f; s2[j][e] = 0.f; }
+            for (int e = 0; e < 4; ++e) { s1[j][e] = make_float2(0.f, 0.f); s2[j][e] = make_float2(0.f, 0.f); }
         }
-        for (int s = 0; s < TS; ++s) {
+        // samples where one of the warp's Gaussians holds a responsibility
+        // (the warp's active M-step threads cover Gaussian quads mqa..mqb), a
+        // 64-bit mask, then two samples at a time
+        uint64_t amask;
+        {
+            const int mqa = (int)__reduce_min_sync(0xffffffffu, mact ? (unsigned)mq : 0xFFFFu);
+            const int mqb = (int)__reduce_max_sync(0xffffffffu, mact ? (unsigned)mq : 0u);
+            bool on[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                bool v = false;
+                for (int q = mqa; q <= mqb; ++q) {
+                    const float4 g4 = *reinterpret_cast<const float4 *>(gam + (lane + 32 * h) * kGS + 4 * q);
+                    v = v || g4.x > 0.f || g4.y > 0.f || g4.z > 0.f || g4.w > 0.f;
+                }
+                on[h] = v;   // sample lane + 32 h, whatever this lane's own M-step role
+            }
+            amask = (uint64_t)__ballot_sync(0xffffffffu, on[0]) | ((uint64_t)__ballot_sync(0xffffffffu, on[1]) << 32);
+        }
+        auto msample = [&](int s) {
             const float4 g4 = *reinterpret_cast<const float4 *>(gam + s * kGS + 4 * mq);
-            const bool any = mact && (g4.x > 0.f || g4.y > 0.f || g4.z > 0.f || g4.w > 0.f);
-            if (!__any_sync(0xffffffffu, any)) continue;
             const float4 xa = *reinterpret_cast<const float4 *>(xb + s * XS + 8 * dg);
             const float4 xc = *reinterpret_cast<const float4 *>(xb + s * XS + 8 * dg + 4);
-            const float xe[8] = {xa.x, xa.y, xa.z, xa.w, xc.x, xc.y, xc.z, xc.w};
+            const float2 xe[4] = {make_float2(xa.x, xa.y), make_float2(xa.z, xa.w), make_float2(xc.x, xc.y),
+                                  make_float2(xc.z, xc.w)};
             const float gj[4] = {g4.x, g4.y, g4.z, g4.w};
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 s0[j] += gj[j];
+                const float2 gg2 = make_float2(gj[j], gj[j]);
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const float u = xe[e] - mu[j][e];
-                    const float v = gj[j] * u;
-                    s1[j][e] += v;
-                    s2[j][e] = fmaf(v, u, s2[j][e]);
+                for (int e = 0; e < 4; ++e) {
+                    const float2 u = __fadd2_rn(xe[e], nmu[j][e]);
+                    const float2 v = __fmul2_rn(gg2, u);
+                    s1[j][e] = __fadd2_rn(s1[j][e], v);
+                    s2[j][e] = __ffma2_rn(v, u, s2[j][e]);
                 }
+            }
+        };
+        while (amask) {
+            const int sa = __ffsll((long long)amask) - 1;
+            amask &= amask - 1;
+            msample(sa);
+            if (amask) {
+                const int sb = __ffsll((long long)amask) - 1;
+                amask &= amask - 1;
+                msample(sb);
             }
         }
         if (mact) {
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int gl = 4 * mq + j;
+            for (int j = 0; j < 4; ++j)
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    m1[gl * D8 + 8 * dg + e] += s1[j][e];
-                    m2[gl * D8 + 8 * dg + e] += s2[j][e];
+                for (int h = 0; h < 2; ++h) {
+                    float4 f1 = macc[(2 * j + h) * kBThreads + tid], f2 = macc[(8 + 2 * j + h) * kBThreads + tid];
+                    f1.x += s1[j][2 * h].x; f1.y += s1[j][2 * h].y; f1.z += s1[j][2 * h + 1].x; f1.w += s1[j][2 * h + 1].y;
+                    f2.x += s2[j][2 * h].x; f2.y += s2[j][2 * h].y; f2.z += s2[j][2 * h + 1].x; f2.w += s2[j][2 * h + 1].y;
+                    macc[(2 * j + h) * kBThreads + tid] = f1;
+                    macc[(8 + 2 * j + h) * kBThreads + tid] = f2;
                 }
-                if (dg == 0) m0[gl] += s0[j];
-            }
+            float4 f0 = macc[16 * kBThreads + tid];
+            f0.x += s0[0]; f0.y += s0[1]; f0.z += s0[2]; f0.w += s0[3];
+            macc[16 * kBThreads + tid] = f0;
         }
         if (++since == kBFlush) flush();
         __syncthreads();   // buffer bi and gam are free

@@ -316,14 +316,17 @@ def c2():
     return X, dev(X), mix
 
 
-def test_c2_full_size_em_iteration_fp32(c2):
+@pytest.mark.parametrize("form", [0, 1])
+def test_c2_full_size_em_iteration_fp32(c2, form):
     """One FP32 EM iteration at the benchmark's full size (N=2e6, D=60,
     G=256), compared with the oracle run over the same data (MapReduce
-    chunks across the host cores)."""
+    chunks across the host cores): the default FP32 form at this shape (the
+    register-blocked one) and the one-pass form (GMM_DEBUG_FP32_FORM = 1)."""
+    from paper_1707_09094_gb300._lib import GMM_DEBUG_FP32_FORM
     X, Xd, mix = c2
     start = (mix.means, mix.stds ** 2 * 1.2, mix.hefts)
     start = tuple(np.array(a, dtype=np.float64) for a in start)
-    g = GMM().set_params(*start)
+    g = GMM().set_params(*start).debug_set(GMM_DEBUG_FP32_FORM, form)
     em_step_check(g, X, Xd, recompute_center=True)
 
 
@@ -337,6 +340,24 @@ def test_c2_full_size_log_p_sampled(c2):
 
 
 # ------------------------------------------------------------ large N_G * D
+@pytest.mark.parametrize("shape", [(100000, 10, 8), (20000, 60, 256), (3001, 64, 17), (160, 16, 16), (30, 3, 2),
+                                   (5000, 33, 65)])
+def test_register_blocked_form_on_small_shapes(shape):
+    """The register-blocked two-phase form forced onto shapes the one-pass
+    form would take (GMM_DEBUG_FP32_FORM = 2): N_G below one 64-Gaussian block,
+    partial blocks, D not a multiple of 4 or 8, a single short tile.  Each
+    iteration equals the oracle's."""
+    from paper_1707_09094_gb300._lib import GMM_DEBUG_FP32_FORM
+    N, D, G = shape
+    X, _, _ = synth.make("c1", N=N, D=D, G=G, seed=11 + N)
+    start = _start(X, G, 4)
+    Xd = dev(X)
+    g = GMM().set_params(*start).debug_set(GMM_DEBUG_FP32_FORM, 2)
+    g.em_iterate(Xd, 0, recompute_center=True)
+    for _ in range(2):
+        em_step_check(g, X, Xd)
+
+
 @pytest.mark.parametrize("shape", [(6000, 128, 300), (8000, 100, 600), (30000, 17, 2500)])
 def test_two_phase_em_matches_oracle(shape):
     """Shapes whose per-CTA statistics exceed shared memory run the two-phase
