@@ -37,7 +37,7 @@ constexpr int kBFlush = 64;    // tiles summed in shared memory between FP64 flu
 __device__ __forceinline__ bool blk_skip(const DevStatus *st, int iter)
 {
     __shared__ int s_skip;
-    if (threadIdx.x == 0) s_skip = (st->halt != 0 || iter > st->stop_after) ? 1 : 0;
+    if (threadIdx.x == 0) s_skip = (st && (st->halt != 0 || iter > st->stop_after)) ? 1 : 0;   // no status: inference
     __syncthreads();
     return s_skip != 0;
 }
@@ -59,6 +59,7 @@ struct BlkArgs {
     int32_t x_v4;        // D % 4 == 0 and X 16-byte aligned: rows staged 16 bytes at a time
     float2 *part;        // [n_gb][N] (max, sum of exp) per sample and block
     float *lse;          // [N] log p(x_i)
+    double *out;         // inference: log p(x_i) in FP64 here instead of lse and the log-likelihood
 };
 
 __host__ __device__ inline size_t blk_smem(int D, int TS, bool em)
@@ -251,10 +252,15 @@ __global__ void __launch_bounds__(128) k_blk_combine(BlkArgs b)
     if (i < a.N) {
         float2 p = b.part[i];
         for (int q = 1; q < b.n_gb; ++q) p = lse_merge(p, b.part[(size_t)q * a.N + i]);
+        if (b.out) {   // the inference kernel's form: max + log(sum) in FP64
+            b.out[i] = (double)p.x + log((double)p.y);
+            return;
+        }
         const float ls = p.x + logf(p.y);
         b.lse[i] = ls;
         v = (double)ls;
     }
+    if (b.out) return;   // the block's threads past N
     sh[threadIdx.x] = v;
     __syncthreads();
     for (int s = 64; s > 0; s >>= 1) {
@@ -487,7 +493,7 @@ int em_blocked_chunks(int32_t G, int sms)
 cudaError_t launch_em_blocked(const EmPassArgs &a, float *lse, float2 *part, int32_t n_chunks, cudaStream_t s)
 {
     BlkArgs b{a, em_blocked_gblocks(a.G), n_chunks,
-              (a.D % 4 == 0 && (reinterpret_cast<uintptr_t>(a.X) & 15u) == 0) ? 1 : 0, part, lse};
+              (a.D % 4 == 0 && (reinterpret_cast<uintptr_t>(a.X) & 15u) == 0) ? 1 : 0, part, lse, nullptr};
     const size_t sm1 = blk_smem(a.D, 128, false) + 4 * 128 * sizeof(float2);
     const size_t sm3 = blk_smem(a.D, 64, true);
     cudaError_t e = cudaFuncSetAttribute(k_blk_lse<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
@@ -499,6 +505,30 @@ cudaError_t launch_em_blocked(const EmPassArgs &a, float *lse, float2 *part, int
     k_blk_combine<<<(int)((a.N + 127) / 128), 128, 0, s>>>(b);
     k_blk_em<<<grid, kBThreads, sm3, s>>>(b);
     count_launches(3);
+    return cudaGetLastError();
+}
+
+// Inference: log p(x_i) of the mixture (Sec. 4.1 log_p) by the phase-1
+// kernels: partial log-sum-exps per block of 64 Gaussians, merged in FP64.
+cudaError_t launch_log_p_blocked(const float *X, int64_t N, int32_t D, int32_t G, Operands op, double *out,
+                                 float2 *part, int sms, cudaStream_t s)
+{
+    EmPassArgs a{};
+    a.X = X;
+    a.N = N;
+    a.D = D;
+    a.G = G;
+    a.op = op;
+    a.N_total = N;
+    const int n_chunks = em_blocked_chunks(G, sms);
+    BlkArgs b{a, em_blocked_gblocks(G), n_chunks, (D % 4 == 0 && (reinterpret_cast<uintptr_t>(X) & 15u) == 0) ? 1 : 0,
+              part, nullptr, out};
+    const size_t sm1 = blk_smem(D, 128, false) + 4 * 128 * sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute(k_blk_lse<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+    if (e != cudaSuccess) return e;
+    k_blk_lse<8><<<b.n_gb * n_chunks, kBThreads, sm1, s>>>(b);
+    k_blk_combine<<<(int)((N + 127) / 128), 128, 0, s>>>(b);
+    count_launches(2);
     return cudaGetLastError();
 }
 

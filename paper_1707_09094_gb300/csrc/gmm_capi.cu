@@ -593,6 +593,21 @@ gmm_status gmm_kmeans(gmm_model *m, const float *X, int64_t N, int32_t km_iter, 
     return GMM_OK;
 }
 
+namespace {
+// log p(x_i) into od (device): for the mixture with N_G > 128 by the
+// register-blocked partial log-sum-exps (the FP32 EM form's first phase),
+// else one sample per thread
+cudaError_t run_log_p(gmm_model *m, const float *Xd, int64_t N, int32_t g, double *od, cudaStream_t s)
+{
+    if (g < 0 && m->G > 128 && gmm::em_blocked_supported(m->D, m->G)) {
+        cudaError_t e = grow(m->lsep, m->lsep_cap, (size_t)gmm::em_blocked_gblocks(m->G) * (size_t)N);
+        if (e != cudaSuccess) return e;
+        return gmm::launch_log_p_blocked(Xd, N, m->D, m->G, m->op, od, m->lsep, m->sms, s);
+    }
+    return gmm::launch_log_p(Xd, N, m->D, m->G, m->op, g, od, s);
+}
+}  // namespace
+
 gmm_status gmm_log_p(const gmm_model *mc, const float *X, int64_t N, int32_t g, double *out, void *stream)
 {
     gmm_model *m = const_cast<gmm_model *>(mc);
@@ -611,7 +626,7 @@ gmm_status gmm_log_p(const gmm_model *mc, const float *X, int64_t N, int32_t g, 
         CK(grow(m->dstage, m->dstage_cap, (size_t)N));
         od = m->dstage;
     }
-    CK(gmm::launch_log_p(Xd, N, m->D, m->G, m->op, g, od, s));
+    CK(run_log_p(m, Xd, N, g, od, s));
     if (!dev_out) CK(cudaMemcpyAsync(out, od, sizeof(double) * (size_t)N, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     return GMM_OK;
@@ -630,6 +645,7 @@ gmm_status gmm_avg_log_p(const gmm_model *mc, const float *X, int64_t N, int32_t
     const float *Xd = nullptr;
     if ((rc = stage_x(m, X, N, m->D, s, &Xd)) != GMM_OK) return rc;
     CK(grow(m->dstage, m->dstage_cap, (size_t)N + 1));
+    // one sample per thread, as the allocation-free average, which returns this value
     CK(gmm::launch_log_p(Xd, N, m->D, m->G, m->op, g, m->dstage, s));
     CK(gmm::launch_sum_fp64(m->dstage, N, m->dstage + N, s));
     double sum = 0.0;

@@ -101,6 +101,9 @@ bool em_blocked_supported(int32_t D, int32_t G);
 int em_blocked_gblocks(int32_t G);
 int em_blocked_chunks(int32_t G, int sms);
 cudaError_t launch_em_blocked(const EmPassArgs &a, float *lse, float2 *part, int32_t n_chunks, cudaStream_t s);
+// log p(x_i) of the mixture into out [N] (FP64); part as above
+cudaError_t launch_log_p_blocked(const float *X, int64_t N, int32_t D, int32_t G, Operands op, double *out,
+                                 float2 *part, int sms, cudaStream_t s);
 cudaError_t launch_log_p(const float *X, int64_t N, int32_t D, int32_t G, Operands op, int32_t g,
                          double *out, cudaStream_t s);
 cudaError_t launch_assign(const float *X, int64_t N, int32_t D, int32_t G, const double *par,
