@@ -25,6 +25,7 @@
 #include <cmath>
 
 #include "gmm_internal.cuh"
+#include "gmm_km_exact.cuh"
 
 namespace gmm {
 
@@ -465,6 +466,414 @@ __global__ void __launch_bounds__(kBThreads, 1) k_blk_em(BlkArgs b)
     flush();   // also writes the rows of a chunk with no tiles (zeros)
 }
 
+
+// ------------------------------------------------------------------------
+// k-means map step (Sec. 3 with Sec. 2.1's chunking) for shapes beyond the
+// tiled CUDA-core form (D > 64 or N_G > 256), register-blocked like the EM
+// form, over blocks of 64 means:
+//   k_bkm_norms    max |cs_g|^2 over all means (the near-tie bound's norm);
+//   k_bkm_dist     grid (sample chunk) x (block of means): FP32 distances
+//                  sum_d (xs_d - cs_gd)^2 in scaled coordinates xs = x sqrt(w),
+//                  cs = mu sqrt(w) (two FMA chains, as the thread-per-sample
+//                  form), each sample's best, runner-up and argmin over the
+//                  block -> part [block][N];
+//   k_bkm_combine  per sample the blocks' results merged, then the exact
+//                  decision: the FP32 winner where the runner-up minus its
+//                  rounding bound exceeds the winner plus its bound, else
+//                  every mean re-decided in FP64 (lowest index on ties) ->
+//                  assign[N];
+//   k_bkm_stats    grid as k_bkm_dist: count, sum (x - mu_f), sum (x - mu_f)^2
+//                  of the block's means over the chunk's samples (mu_f the
+//                  old mean rounded to FP32), into the chunk's FP64 partial.
+// ------------------------------------------------------------------------
+struct BkmArgs {
+    const float *X;
+    int64_t N;
+    int32_t D, G;
+    const double *means;    // means at the start of the iteration
+    const double *w;        // [D] FP64 distance weights
+    const float *sw;        // [D] FP32 sqrt(w)
+    float2 *part;           // [n_gb][N] (best, runner-up) of each block
+    uint8_t *arg;           // [n_gb][N] the block's argmin (index within the block)
+    float *nmax;            // [1] max |cs_g|^2
+    float *snorm;           // [N] |xs_i|^2 (written by the first block's CTAs)
+    int32_t *defer;         // [N] samples left to the FP64 re-decision; defer_n their count
+    int32_t *defer_n;
+    int32_t *assign;        // [N]
+    double *partial;        // [n_chunks][G][1 + 2D]
+    int32_t n_gb, n_chunks, x_v4;
+    const DevStatus *status;
+};
+
+__global__ void __launch_bounds__(256) k_bkm_norms(BkmArgs b)
+{
+    __shared__ float s_m[256];
+    if (blk_skip(b.status, 0)) return;
+    float mx = 0.f;
+    for (int g = threadIdx.x; g < b.G; g += 256) {
+        float n = 0.f;
+        for (int d = 0; d < b.D; ++d) {
+            const float c = (float)(b.means[(size_t)g * b.D + d] * (double)b.sw[d]);
+            n = fmaf(c, c, n);
+        }
+        mx = fmaxf(mx, n);
+    }
+    s_m[threadIdx.x] = mx;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) s_m[threadIdx.x] = fmaxf(s_m[threadIdx.x], s_m[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        *b.nmax = s_m[0];
+        *b.defer_n = 0;
+    }
+}
+
+// (best, runner-up, argmin) merge; the lower index wins an exact tie
+struct Best2 {
+    float b1, b2;
+    int a1;
+};
+__device__ __forceinline__ Best2 best2_merge(Best2 p, Best2 q)
+{
+    if (q.b1 < p.b1 || (q.b1 == p.b1 && q.a1 < p.a1)) return Best2{q.b1, fminf(p.b1, q.b2), q.a1};
+    return Best2{p.b1, fminf(p.b2, q.b1), p.a1};
+}
+
+__host__ __device__ inline size_t bkm_dist_smem(int D)
+{
+    return sizeof(float) * ((size_t)kBG * blk_xs(D) + blk_d8(D) + 2 * 128 * (size_t)blk_xs(D)) +
+           sizeof(float4) * 4 * 128;
+}
+
+template <int RS>
+__global__ void __launch_bounds__(kBThreads, 1) k_bkm_dist(BkmArgs b)
+{
+    constexpr int TS = 16 * RS;
+    extern __shared__ __align__(16) float bsm[];
+    if (blk_skip(b.status, 0)) return;
+    const int D = b.D, D8 = blk_d8(D), XS = blk_xs(D), CS = XS;   // mean rows as sample rows
+    const int gb = blockIdx.x % b.n_gb, chunk = blockIdx.x / b.n_gb, g0 = gb * kBG;
+    float *ncs = bsm;                    // [64][CS] -cs (0 past D)
+    float *swd = ncs + kBG * CS;         // [D8]
+    float *xt = swd + D8;                // [2][TS][XS] scaled samples
+    float4 *red = reinterpret_cast<float4 *>(xt + 2 * TS * XS);   // [4][TS]
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    const int sg = 8 * (w & 1) + (lane & 7), gg = 4 * (w >> 1) + (lane >> 3);
+    for (int k = tid; k < kBG * D8; k += kBThreads) {
+        const int g = k / D8, d = k - g * D8;
+        ncs[g * CS + d] = (g0 + g < b.G && d < D) ? -(float)(b.means[(size_t)(g0 + g) * D + d] * (double)b.sw[d]) : 0.f;
+    }
+    for (int d = tid; d < D8; d += kBThreads) swd[d] = d < D ? b.sw[d] : 0.f;
+    for (int k = tid; k < 2 * TS * (XS - D); k += kBThreads) {
+        const int r = k / (XS - D);
+        xt[r * XS + D + (k - r * (XS - D))] = 0.f;
+    }
+    const int64_t ntiles = (b.N + TS - 1) / TS;
+    const int64_t t0 = ntiles * chunk / b.n_chunks, t1 = ntiles * (chunk + 1) / b.n_chunks;
+    auto stage = [&](int64_t t, float *xb) {
+        const int64_t i0 = t * TS;
+        const int nv = (int)min((int64_t)TS, b.N - i0);
+        if (b.x_v4) {
+            const int q4 = D / 4;
+            for (int k = tid; k < TS * q4; k += kBThreads) {
+                const int r = k / q4, c = k - r * q4;
+                if (r < nv) cp_async16(xb + r * XS + 4 * c, b.X + (i0 + r) * D + 4 * c);
+                else *reinterpret_cast<float4 *>(xb + r * XS + 4 * c) = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        } else {
+            for (int k = tid; k < TS * D; k += kBThreads) {
+                const int r = k / D, c = k - r * D;
+                if (r < nv) cp_async4(xb + r * XS + c, b.X + (i0 + r) * D + c);
+                else xb[r * XS + c] = 0.f;
+            }
+        }
+    };
+    __syncthreads();
+    if (t0 < t1) stage(t0, xt);
+    cp_commit();
+    for (int64_t t = t0; t < t1; ++t) {
+        const int bi = (int)((t - t0) & 1);
+        float *xb = xt + bi * TS * XS;
+        if (t + 1 < t1) stage(t + 1, xt + (1 - bi) * TS * XS);
+        cp_commit();
+        cp_wait<1>();
+        __syncthreads();
+        for (int k = tid; k < TS * D; k += kBThreads) {   // xs = x sqrt(w), in place
+            const int r = k / D, d = k - r * D;
+            xb[r * XS + d] *= swd[d];
+        }
+        __syncthreads();
+        if (gb == 0) {   // |xs|^2 per sample for the near-tie bound (any order: the bound has a 4x margin)
+            const int64_t i0 = t * TS;
+            for (int r = w; r < TS; r += kBThreads / 32) {
+                float v = 0.f;
+                for (int d = lane; d < D8; d += 32) v = fmaf(xb[r * XS + d], xb[r * XS + d], v);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0 && i0 + r < b.N) b.snorm[i0 + r] = v;
+            }
+        }
+        float2 acc[RS][4];
+#pragma unroll
+        for (int k = 0; k < RS; ++k)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[k][j] = make_float2(0.f, 0.f);
+#pragma unroll 2
+        for (int d4 = 0; d4 < D8 / 4; ++d4) {
+            float4 xv[RS];
+#pragma unroll
+            for (int k = 0; k < RS; ++k) xv[k] = *reinterpret_cast<const float4 *>(xb + (sg + 16 * k) * XS + 4 * d4);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float4 c = *reinterpret_cast<const float4 *>(ncs + (gg + 16 * j) * CS + 4 * d4);
+                const float2 ca = make_float2(c.x, c.y), cb = make_float2(c.z, c.w);
+#pragma unroll
+                for (int k = 0; k < RS; ++k) {
+                    const float2 t01 = __fadd2_rn(make_float2(xv[k].x, xv[k].y), ca);
+                    const float2 t23 = __fadd2_rn(make_float2(xv[k].z, xv[k].w), cb);
+                    acc[k][j] = __ffma2_rn(t01, t01, acc[k][j]);
+                    acc[k][j] = __ffma2_rn(t23, t23, acc[k][j]);
+                }
+            }
+        }
+        // per sample: best two over this thread's means (ascending), the
+        // warp's four mean groups (lanes ^ 8, ^ 16), the four warp pairs
+#pragma unroll
+        for (int k = 0; k < RS; ++k) {
+            Best2 p{INFINITY, INFINITY, 0};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int g = gg + 16 * j;
+                if (g0 + g < b.G) p = best2_merge(p, Best2{acc[k][j].x + acc[k][j].y, INFINITY, g});
+            }
+#pragma unroll
+            for (int o = 8; o <= 16; o <<= 1) {
+                Best2 q{__shfl_xor_sync(0xffffffffu, p.b1, o), __shfl_xor_sync(0xffffffffu, p.b2, o),
+                        __shfl_xor_sync(0xffffffffu, p.a1, o)};
+                p = best2_merge(p, q);
+            }
+            if (lane < 8) red[(w >> 1) * TS + sg + 16 * k] = make_float4(p.b1, p.b2, __int_as_float(p.a1), 0.f);
+        }
+        __syncthreads();
+        const int64_t i0 = t * TS;
+        for (int s = tid; s < TS; s += kBThreads) {
+            if (i0 + s < b.N) {
+                const float4 r0 = red[s];
+                Best2 p{r0.x, r0.y, __float_as_int(r0.z)};
+#pragma unroll
+                for (int q = 1; q < 4; ++q) {
+                    const float4 rq = red[q * TS + s];
+                    p = best2_merge(p, Best2{rq.x, rq.y, __float_as_int(rq.z)});
+                }
+                b.part[(size_t)gb * b.N + i0 + s] = make_float2(p.b1, p.b2);
+                b.arg[(size_t)gb * b.N + i0 + s] = (uint8_t)p.a1;
+            }
+        }
+    }
+    cp_wait<0>();
+}
+
+__global__ void __launch_bounds__(128) k_bkm_combine(BkmArgs b)
+{
+    if (blk_skip(b.status, 0)) return;
+    const int64_t i = (int64_t)blockIdx.x * 128 + threadIdx.x;
+    if (i >= b.N) return;
+    Best2 p{INFINITY, INFINITY, 0};
+    for (int q = 0; q < b.n_gb; ++q) {   // blocks in ascending order: lower index wins ties
+        const float2 v = b.part[(size_t)q * b.N + i];
+        p = best2_merge(p, Best2{v.x, v.y, q * kBG + b.arg[(size_t)q * b.N + i]});
+    }
+    const float norms = b.snorm[i] + *b.nmax;
+    b.assign[i] = p.a1;
+    // near tie: the FP64 re-decision runs in k_bkm_recheck, a warp per sample
+    // (inline, one thread's FP64 pass over every mean held a whole wave of
+    // blocks: 358 ms per c3 iteration for 0.06 % of the samples)
+    if (b.G > 1 && !(p.b2 - km_err(p.b2, norms, b.D) > p.b1 + km_err(p.b1, norms, b.D)))
+        b.defer[atomicAdd(b.defer_n, 1)] = (int32_t)i;
+}
+
+// FP64 re-decision of the deferred samples: the definition
+// sum_d w_d (x_d - mu_gd)^2 in order d = 0..D-1 without fused operations
+// (the thread-per-sample form's km_recheck_fp64), lanes over the means, the
+// lowest index among equal values.
+__global__ void __launch_bounds__(256) k_bkm_recheck(BkmArgs b)
+{
+    if (blk_skip(b.status, 0)) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int n = *b.defer_n;
+    for (int64_t e = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); e < n; e += nw) {
+        const int64_t i = b.defer[e];
+        const float *x = b.X + i * b.D;
+        double best = INFINITY;
+        int a = 0x7fffffff;
+        for (int g = lane; g < b.G; g += 32) {
+            const double *mu = b.means + (size_t)g * b.D;
+            double acc = 0.0;
+            for (int d = 0; d < b.D; ++d) {
+                const double t = __dsub_rn((double)x[d], mu[d]);
+                acc = __dadd_rn(acc, __dmul_rn(b.w[d], __dmul_rn(t, t)));
+            }
+            if (acc < best) { best = acc; a = g; }   // ascending g: the lane's lowest index on ties
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oa = __shfl_xor_sync(0xffffffffu, a, o);
+            if (ob < best || (ob == best && oa < a)) { best = ob; a = oa; }
+        }
+        if (lane == 0) b.assign[i] = a;
+    }
+}
+
+__host__ __device__ inline size_t bkm_stats_smem(int D)
+{
+    return sizeof(float) * 2 * 64 * (size_t)blk_xs(D) + sizeof(int) * 2 * 64 + sizeof(float4) * 18 * kBThreads +
+           sizeof(int) * (2 * 64 + 4);
+}
+
+__global__ void __launch_bounds__(kBThreads, 1) k_bkm_stats(BkmArgs b)
+{
+    constexpr int TS = 64, UPT = 8;   // samples per tile; units per thread at most (64 means x D8/4 <= 2048)
+    extern __shared__ __align__(16) float bsm[];
+    if (blk_skip(b.status, 0)) return;
+    const int D = b.D, G = b.G, D8 = blk_d8(D), XS = blk_xs(D), S = 1 + 2 * D, NQ = D8 / 4;
+    const int gb = blockIdx.x % b.n_gb, chunk = blockIdx.x / b.n_gb, g0 = gb * kBG;
+    float *xt = bsm;                                                // [2][64][XS]
+    int *asg = reinterpret_cast<int *>(xt + 2 * TS * XS);           // [2][64]
+    float4 *macc = reinterpret_cast<float4 *>(asg + 2 * TS);        // [18][256] per-thread sums
+    int *lst = reinterpret_cast<int *>(macc + 18 * kBThreads);       // [2][64] in-block samples of the tile, per warp
+    int *wcnt = lst + 2 * TS;                                         // [2] their counts
+    const int tid = threadIdx.x;
+    const int nu = kBG * NQ;   // units (mean of the block, 4 dimensions)
+    // this thread's units u = tid + 256 r: shifts mu_f (FP32 old means)
+    float4 mu[UPT];
+#pragma unroll
+    for (int r = 0; r < UPT; ++r) {
+        const int u = tid + kBThreads * r, gl = u / NQ, d = 4 * (u - gl * NQ), g = g0 + gl;
+        const bool on = u < nu && g < G;
+        mu[r] = make_float4(on && d < D ? (float)b.means[(size_t)g * D + d] : 0.f,
+                            on && d + 1 < D ? (float)b.means[(size_t)g * D + d + 1] : 0.f,
+                            on && d + 2 < D ? (float)b.means[(size_t)g * D + d + 2] : 0.f,
+                            on && d + 3 < D ? (float)b.means[(size_t)g * D + d + 3] : 0.f);
+    }
+    for (int q = 0; q < 18; ++q) macc[q * kBThreads + tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int k = tid; k < 2 * TS * (XS - D); k += kBThreads) {
+        const int r = k / (XS - D);
+        xt[r * XS + D + (k - r * (XS - D))] = 0.f;
+    }
+    double *P = b.partial + (size_t)chunk * G * S;
+    int flushes = 0, since = 0;
+    auto flush = [&]() {
+#pragma unroll
+        for (int r = 0; r < UPT; ++r) {
+            const int u = tid + kBThreads * r, gl = u / NQ, q = u - gl * NQ, d = 4 * q, g = g0 + gl;
+            if (u >= nu || g >= G) continue;
+            const float4 s1 = macc[(2 * r) * kBThreads + tid], s2 = macc[(2 * r + 1) * kBThreads + tid];
+            const float v1[4] = {s1.x, s1.y, s1.z, s1.w}, v2[4] = {s2.x, s2.y, s2.z, s2.w};
+            double *row = P + (size_t)g * S;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                if (d + e >= D) continue;
+                row[1 + d + e] = flushes ? row[1 + d + e] + (double)v1[e] : (double)v1[e];
+                row[1 + D + d + e] = flushes ? row[1 + D + d + e] + (double)v2[e] : (double)v2[e];
+            }
+            macc[(2 * r) * kBThreads + tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+            macc[(2 * r + 1) * kBThreads + tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        // counts: unit r of a thread with q == 0 keeps its mean's count in
+        // component r & 3 of slot 16 + (r >> 2)
+#pragma unroll
+        for (int r = 0; r < UPT; ++r) {
+            const int u = tid + kBThreads * r, gl = u / NQ, q = u - gl * NQ, g = g0 + gl;
+            if (u >= nu || g >= G || q != 0) continue;
+            float4 &c4 = macc[(16 + (r >> 2)) * kBThreads + tid];
+            const float c = (r & 3) == 0 ? c4.x : ((r & 3) == 1 ? c4.y : ((r & 3) == 2 ? c4.z : c4.w));
+            double *row = P + (size_t)g * S;
+            row[0] = flushes ? row[0] + (double)c : (double)c;
+        }
+        macc[16 * kBThreads + tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+        macc[17 * kBThreads + tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+        ++flushes;
+        since = 0;
+    };
+    const int64_t ntiles = (b.N + TS - 1) / TS;
+    const int64_t t0 = ntiles * chunk / b.n_chunks, t1 = ntiles * (chunk + 1) / b.n_chunks;
+    auto stage = [&](int64_t t, int bi) {
+        float *xb = xt + bi * TS * XS;
+        const int64_t i0 = t * TS;
+        const int nv = (int)min((int64_t)TS, b.N - i0);
+        if (b.x_v4) {
+            const int q4 = D / 4;
+            for (int k = tid; k < TS * q4; k += kBThreads) {
+                const int r = k / q4, c = k - r * q4;
+                if (r < nv) cp_async16(xb + r * XS + 4 * c, b.X + (i0 + r) * D + 4 * c);
+                else *reinterpret_cast<float4 *>(xb + r * XS + 4 * c) = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        } else {
+            for (int k = tid; k < TS * D; k += kBThreads) {
+                const int r = k / D, c = k - r * D;
+                if (r < nv) cp_async4(xb + r * XS + c, b.X + (i0 + r) * D + c);
+                else xb[r * XS + c] = 0.f;
+            }
+        }
+        for (int s = tid; s < TS; s += kBThreads) asg[bi * TS + s] = s < nv ? b.assign[i0 + s] : -1;
+    };
+    __syncthreads();
+    if (t0 < t1) stage(t0, 0);
+    cp_commit();
+    for (int64_t t = t0; t < t1; ++t) {
+        const int bi = (int)((t - t0) & 1);
+        const float *xb = xt + bi * TS * XS;
+        const int *ab = asg + bi * TS;
+        if (t + 1 < t1) stage(t + 1, 1 - bi);
+        cp_commit();
+        cp_wait<1>();
+        __syncthreads();
+        // the tile's samples assigned to this block's means, in sample order
+        if (tid < TS) {   // warps 0 and 1: samples 0..31, 32..63
+            const int gl = ab[tid] - g0;
+            const bool in = ab[tid] >= 0 && gl >= 0 && gl < kBG;
+            const unsigned bal = __ballot_sync(0xffffffffu, in);
+            if ((tid & 31) == 0) wcnt[tid >> 5] = __popc(bal);
+            if (in) lst[(tid >> 5) * TS + __popc(bal & ((1u << (tid & 31)) - 1u))] = tid;
+        }
+        __syncthreads();
+        const int n0 = wcnt[0], n1 = wcnt[1];
+#pragma unroll
+        for (int r = 0; r < UPT; ++r) {
+            const int u = tid + kBThreads * r;
+            if (u >= nu) continue;
+            const int gl = u / NQ, d = 4 * (u - gl * NQ), g = g0 + gl;
+            float4 s1 = make_float4(0.f, 0.f, 0.f, 0.f), s2 = s1;
+            float cnt = 0.f;
+            for (int e = 0; e < n0 + n1; ++e) {
+                const int s = e < n0 ? lst[e] : lst[TS + e - n0];
+                if (ab[s] != g) continue;
+                const float4 xv = *reinterpret_cast<const float4 *>(xb + s * XS + d);
+                const float u0 = xv.x - mu[r].x, u1 = xv.y - mu[r].y, u2 = xv.z - mu[r].z, u3 = xv.w - mu[r].w;
+                s1.x += u0; s1.y += u1; s1.z += u2; s1.w += u3;
+                s2.x = fmaf(u0, u0, s2.x); s2.y = fmaf(u1, u1, s2.y); s2.z = fmaf(u2, u2, s2.z); s2.w = fmaf(u3, u3, s2.w);
+                cnt += 1.f;
+            }
+            float4 &a1 = macc[(2 * r) * kBThreads + tid], &a2 = macc[(2 * r + 1) * kBThreads + tid];
+            a1.x += s1.x; a1.y += s1.y; a1.z += s1.z; a1.w += s1.w;
+            a2.x += s2.x; a2.y += s2.y; a2.z += s2.z; a2.w += s2.w;
+            float4 &c4 = macc[(16 + (r >> 2)) * kBThreads + tid];
+            if ((r & 3) == 0) c4.x += cnt;
+            else if ((r & 3) == 1) c4.y += cnt;
+            else if ((r & 3) == 2) c4.z += cnt;
+            else c4.w += cnt;
+        }
+        if (++since == kBFlush) flush();
+        __syncthreads();   // buffer bi is free
+    }
+    cp_wait<0>();
+    flush();   // also writes the rows of a chunk with no tiles (zeros)
+}
+
 }  // namespace
 
 bool em_blocked_supported(int32_t D, int32_t G)
@@ -505,6 +914,38 @@ cudaError_t launch_em_blocked(const EmPassArgs &a, float *lse, float2 *part, int
     k_blk_combine<<<(int)((a.N + 127) / 128), 128, 0, s>>>(b);
     k_blk_em<<<grid, kBThreads, sm3, s>>>(b);
     count_launches(3);
+    return cudaGetLastError();
+}
+
+bool km_blocked_supported(int32_t D, int32_t G)
+{
+    if (D < 1 || D > 128 || G < 1) return false;
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return bkm_dist_smem(D) + 1024 <= (size_t)optin && bkm_stats_smem(D) + 1024 <= (size_t)optin;
+}
+
+cudaError_t launch_km_blocked(const float *X, int64_t N, int32_t D, int32_t G, const double *means,
+                              const double *w, const float *sw, float2 *part, uint8_t *arg, float *nmax,
+                              float *snorm, int32_t *defer, int32_t *assign, double *partial, int32_t n_chunks,
+                              const DevStatus *status, cudaStream_t s)
+{
+    BkmArgs b{X, N, D, G, means, w, sw, part, arg, nmax, snorm, defer, defer + N, assign, partial, em_blocked_gblocks(G),
+              n_chunks,
+              (D % 4 == 0 && (reinterpret_cast<uintptr_t>(X) & 15u) == 0) ? 1 : 0, status};
+    const size_t smd = bkm_dist_smem(D), sms = bkm_stats_smem(D);
+    cudaError_t e = cudaFuncSetAttribute(k_bkm_dist<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smd);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_bkm_stats, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sms)) != cudaSuccess)
+        return e;
+    const int grid = b.n_gb * n_chunks;
+    k_bkm_norms<<<1, 256, 0, s>>>(b);
+    k_bkm_dist<8><<<grid, kBThreads, smd, s>>>(b);
+    k_bkm_combine<<<(int)((N + 127) / 128), 128, 0, s>>>(b);
+    k_bkm_recheck<<<grid, 256, 0, s>>>(b);
+    k_bkm_stats<<<grid, kBThreads, sms, s>>>(b);
+    count_launches(5);
     return cudaGetLastError();
 }
 

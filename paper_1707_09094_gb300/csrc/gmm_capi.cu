@@ -126,7 +126,7 @@ struct gmm_model {
     int32_t center_D = 0;
     // workspace
     double *partial = nullptr; size_t partial_cap = 0;
-    float *slab = nullptr; size_t slab_cap = 0;
+    uint8_t *kmarg = nullptr; size_t kmarg_cap = 0;           // register-blocked k-means: argmin per block | max norm
     unsigned char *tclist = nullptr; size_t tclist_cap = 0;   // tensor-core pass: per-sample records
     unsigned char *kmop = nullptr; size_t kmop_cap = 0;       // tensor-core k-means operands
     double *spread = nullptr; size_t spread_cap = 0;          // spread seeding: distances + block partials
@@ -269,14 +269,20 @@ gmm_status run_kmeans(gmm_model *m, const float *Xd, int64_t N, int32_t km_iter,
 {
     const int32_t D = m->D, G = m->G, S = 1 + 2 * D;
     const bool tc = m->km_form == 0 && m->has_center && m->center_D == D && gmm::km_tc_supported(D, G);
+    const bool blk = !tc && !gmm::km_tile_supported(D, G);   // register-blocked CUDA-core form
+    if (blk && !gmm::km_blocked_supported(D, G))
+        return fail(GMM_ERR_UNSUPPORTED, "k-means: shared memory too small for D=%d, G=%d", D, G);
     const int grid = tc ? m->sms : gmm::km_grid(D, G, m->sms);
     CK(grow(m->partial, m->partial_cap, (size_t)grid * G * S));
+    const size_t nb = (size_t)gmm::em_blocked_gblocks(G) * (size_t)N;
     if (tc) {
         CK(grow(m->tclist, m->tclist_cap, gmm::em_tc_list_bytes(N, grid)));
         CK(grow(m->kmop, m->kmop_cap, gmm::km_tc_ops_bytes(D, G)));
         m->ops_valid = false;   // the pass writes the FP32 means into the E-step operands
-    } else {
-        CK(grow(m->slab, m->slab_cap, gmm::km_slab_floats(D, G, grid)));
+    } else if (blk) {
+        CK(grow(m->lsep, m->lsep_cap, nb));                          // (best, runner-up) per block
+        // argmin per block | max |cs|^2 | |xs|^2 [N] | deferred samples [N] and their count
+        CK(grow(m->kmarg, m->kmarg_cap, ((nb + 15) & ~(size_t)15) + 16 + 8 * (size_t)N + 16));
     }
     CK(grow(m->assign, m->assign_cap, (size_t)N));
     CK(grow(m->counts, m->counts_cap, (size_t)G));
@@ -290,9 +296,15 @@ gmm_status run_kmeans(gmm_model *m, const float *Xd, int64_t N, int32_t km_iter,
                                       gmm::km_tc_ops(m->kmop, D, G), m->op, m->partial, grid, m->assign,
                                       gmm::em_tc_lists(m->tclist, N, grid), m->status, m->wait_cycles,
                                       m->profiling ? m->sstats + kStatKm : nullptr, s));
+        else if (blk)
+            CK(gmm::launch_km_blocked(Xd, N, D, G, m->par[m->cur], m->wdist(), m->sw(), m->lsep, m->kmarg,
+                                      reinterpret_cast<float *>(m->kmarg + ((nb + 15) & ~(size_t)15)),
+                                      reinterpret_cast<float *>(m->kmarg + ((nb + 15) & ~(size_t)15) + 16),
+                                      reinterpret_cast<int32_t *>(m->kmarg + ((nb + 15) & ~(size_t)15) + 16 + 4 * (size_t)N),
+                                      m->assign, m->partial, grid, m->status, s));
         else
-            CK(gmm::launch_km_pass(Xd, N, D, G, m->par[m->cur], m->wdist(), m->sw(), m->slab, m->partial, grid,
-                                   m->assign, m->status, s));
+            CK(gmm::launch_km_pass(Xd, N, D, G, m->par[m->cur], m->wdist(), m->sw(), m->partial, grid, m->assign,
+                                   m->status, s));
         if ((prc = prof_end(m, s, slot)) != GMM_OK) return prc;
         CK(gmm::launch_km_finalize(m->partial, np, N, D, G, m->par[m->cur], var_floor, it == km_iter - 1,
                                    m->counts, Xd, m->assign, m->gvar(), m->status, s));
@@ -451,7 +463,7 @@ void gmm_destroy(gmm_model *m)
     if (m->cstream) cudaStreamDestroy(m->cstream);
     if (m->sstats) cudaFree(m->sstats);
     void *bufs[] = {m->par[0], m->par[1], m->op_sm, m->op_mu, m->op_c, m->op_B, m->gstat, m->fstat,
-                    m->partial, m->slab, m->lse, m->llp, m->lld, m->counts, m->assign, m->xstage, m->dstage, m->idx,
+                    m->partial, m->kmarg, m->lse, m->llp, m->lld, m->counts, m->assign, m->xstage, m->dstage, m->idx,
                     m->hist, m->status, m->tclist, m->kmop, m->spread, m->lsep};
     for (void *p : bufs)
         if (p) cudaFree(p);

@@ -83,10 +83,11 @@ cudaError_t launch_global_stats(const float *X, int64_t N, int32_t D, double var
                                 double *wdist, float *sw, float *center, cudaStream_t s);
 cudaError_t launch_gather_seeds(const float *X, int32_t D, int32_t G, const int64_t *idx,
                                 double *par, cudaStream_t s);
+// tiled CUDA-core k-means map step (km_tile_supported shapes: D <= 64, N_G <= 256)
+bool km_tile_supported(int32_t D, int32_t G);
 cudaError_t launch_km_pass(const float *X, int64_t N, int32_t D, int32_t G, const double *par,
-                           const double *wdist, const float *sw, float *slab, double *partial, int32_t grid,
-                           int32_t *assign, DevStatus *status, cudaStream_t s);
-size_t km_slab_floats(int32_t D, int32_t G, int grid);
+                           const double *wdist, const float *sw, double *partial, int32_t grid, int32_t *assign,
+                           DevStatus *status, cudaStream_t s);
 cudaError_t launch_km_finalize(const double *partial, int32_t n_partial, int64_t N, int32_t D,
                                int32_t G, double *par, double var_floor, int32_t final_iter,
                                double *counts, const float *X, const int32_t *assign,
@@ -101,6 +102,15 @@ bool em_blocked_supported(int32_t D, int32_t G);
 int em_blocked_gblocks(int32_t G);
 int em_blocked_chunks(int32_t G, int sms);
 cudaError_t launch_em_blocked(const EmPassArgs &a, float *lse, float2 *part, int32_t n_chunks, cudaStream_t s);
+// k-means map step for shapes beyond the tiled form: assign [N] (exact
+// nearest mean) and the statistics into partial [n_chunks][G][1 + 2D];
+// part [gblocks][N], arg [gblocks][N], nmax [1], snorm [N] and defer [N + 1]
+// are work space
+bool km_blocked_supported(int32_t D, int32_t G);
+cudaError_t launch_km_blocked(const float *X, int64_t N, int32_t D, int32_t G, const double *means,
+                              const double *w, const float *sw, float2 *part, uint8_t *arg, float *nmax,
+                              float *snorm, int32_t *defer, int32_t *assign, double *partial, int32_t n_chunks,
+                              const DevStatus *status, cudaStream_t s);
 // log p(x_i) of the mixture into out [N] (FP64); part as above
 cudaError_t launch_log_p_blocked(const float *X, int64_t N, int32_t D, int32_t G, Operands op, double *out,
                                  float2 *part, int sms, cudaStream_t s);

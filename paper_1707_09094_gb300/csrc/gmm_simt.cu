@@ -15,6 +15,7 @@
 #include <cmath>
 
 #include "gmm_internal.cuh"
+#include "gmm_km_exact.cuh"
 
 namespace gmm {
 
@@ -198,39 +199,6 @@ __global__ void k_gather_seeds(const float *__restrict__ X, int32_t D, int32_t G
     if (threadIdx.x == 0) par[2 * (size_t)G * D + g] = 1.0 / (double)G;
 }
 
-// ------------------------------------------------------------------------
-// Nearest mean (Eq. 19) with an exact FP64 recheck of near ties.
-// FP32 distances use scaled coordinates xs = x*sqrt(w), cs = mu*sqrt(w).
-// Rounding bound of one FP32 distance d (x, mu rounded to FP32, t = xs - cs
-// rounded, FMA accumulation): |err| <= 2^-22 sqrt(2 d (|xs|^2 + |cs|^2))
-// + (D + 4) 2^-24 d.  If the runner-up minus its bound still exceeds the
-// winner plus its bound, the FP32 winner is the exact winner; otherwise all
-// Gaussians are re-evaluated in FP64 exactly as sum_d w_d (x_d - mu_d)^2 in
-// order d = 0..D-1 without fused operations, lowest index on exact ties.
-// ------------------------------------------------------------------------
-__device__ __forceinline__ float km_err(float d, float norms, int D)
-{
-    return 4.0f * (2.384185791015625e-07f * sqrtf(2.0f * d * norms) + (float)(D + 4) * 5.9604644775390625e-08f * d)
-           + 1e-30f;
-}
-
-__device__ int km_recheck_fp64(const float *__restrict__ x, int D, int G, const double *__restrict__ means,
-                               const double *__restrict__ w)
-{
-    double best = INFINITY;
-    int a = 0;
-    for (int g = 0; g < G; ++g) {
-        const double *mu = means + (size_t)g * D;
-        double acc = 0.0;
-        for (int d = 0; d < D; ++d) {
-            double t = __dsub_rn((double)x[d], mu[d]);
-            acc = __dadd_rn(acc, __dmul_rn(w[d], __dmul_rn(t, t)));
-        }
-        if (acc < best) { best = acc; a = g; }
-    }
-    return a;
-}
-
 struct KmArgs {
     const float *X;
     int64_t N;
@@ -238,128 +206,10 @@ struct KmArgs {
     const double *means;   // lambda (means at the start of the iteration)
     const double *w;       // [D] FP64 distance weights
     const float *sw;       // [D] FP32 sqrt(w)
-    float *slab;           // [grid][G][4 + 2*DP] FP32 per-CTA statistics (L2)
     double *partial;       // [grid][G][1+2D] FP64 per-CTA statistics (output)
     int32_t *assign;
     const DevStatus *status;
 };
-
-// k-means map step (Sec. 3 with Sec. 2.1's chunking): each CTA takes a
-// contiguous chunk of samples; per sample the nearest mean (exact), then the
-// hard statistics count, sum(x - mu_old), sum((x - mu_old)^2) of its mean,
-// shifted by the FP32 old mean so that FP32 sums stay small.  The sums go to
-// the CTA's FP32 slab in L2 as 16-byte vector atomics, one per two dimensions
-// (row layout [count, pad x3 | (S1_d, S2_d) for d < DP]); at the end the CTA
-// converts its slab to its FP64 partial.  Shared memory holds only the means.
-template <int DMAX>
-__global__ void __launch_bounds__(kKmThreads) k_km_pass(KmArgs a)
-{
-    extern __shared__ __align__(16) unsigned char km_smem[];
-    if (block_skip(a.status, 0)) return;
-    const int D = a.D, DP = a.DP, G = a.G, GS = a.GS, SP = 4 + 2 * DP;
-    float *cent = reinterpret_cast<float *>(km_smem);         // [GS][DP] scaled means
-    float *cnorm = cent + (size_t)GS * DP;                       // [GS]
-    __shared__ float s_nmax;
-    __shared__ float s_sw[GMM_MAX_DIMS];
-    float *slab = a.slab + (size_t)blockIdx.x * G * SP;
-
-    for (int d = threadIdx.x; d < D; d += blockDim.x) s_sw[d] = a.sw[d];
-    for (int k = threadIdx.x; k < G * SP; k += blockDim.x) slab[k] = 0.f;
-    __threadfence();
-    __syncthreads();
-
-    const int64_t per = (a.N + gridDim.x - 1) / gridDim.x;
-    const int64_t i0 = (int64_t)blockIdx.x * per;
-    const int64_t i1 = min(a.N, i0 + per);
-    const bool one_slab = GS >= G;
-
-    auto load_slab = [&](int g0, int gs) {
-        for (int k = threadIdx.x; k < gs * DP; k += blockDim.x) {
-            int gg = k / DP, d = k - gg * DP;
-            cent[k] = d < D ? (float)(a.means[(size_t)(g0 + gg) * D + d] * (double)s_sw[d]) : 0.f;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) s_nmax = 0.f;
-        __syncthreads();
-        for (int gg = threadIdx.x; gg < gs; gg += blockDim.x) {
-            float n = 0.f;
-            for (int d = 0; d < D; ++d) n = fmaf(cent[gg * DP + d], cent[gg * DP + d], n);
-            cnorm[gg] = n;
-            atomicMax(reinterpret_cast<int *>(&s_nmax), __float_as_int(n));  // n >= 0
-        }
-        __syncthreads();
-    };
-    float nmax_all = 0.f;
-    if (one_slab) { load_slab(0, G); nmax_all = s_nmax; }
-    else {
-        // max norm over every mean, for the near-tie bound
-        for (int g0 = 0; g0 < G; g0 += GS) { load_slab(g0, min(GS, G - g0)); nmax_all = fmaxf(nmax_all, s_nmax); }
-    }
-
-    for (int64_t base = i0; base < i1; base += blockDim.x) {
-        const int64_t i = base + threadIdx.x;
-        const bool valid = i < i1;
-        float xr[DMAX];
-        float xs[DMAX];
-        float snorm = 0.f;
-#pragma unroll
-        for (int d = 0; d < DMAX; ++d) {
-            float v = (valid && d < D) ? a.X[i * D + d] : 0.f;
-            xr[d] = v;
-            xs[d] = d < D ? v * s_sw[d] : 0.f;
-            snorm = fmaf(xs[d], xs[d], snorm);
-        }
-        float b1 = INFINITY, b2 = INFINITY;
-        int a1 = 0;
-        for (int g0 = 0; g0 < G; g0 += GS) {
-            const int gs = min(GS, G - g0);
-            if (!one_slab) { __syncthreads(); load_slab(g0, gs); }
-            for (int gg = 0; gg < gs; ++gg) {
-                const float4 *c4 = reinterpret_cast<const float4 *>(cent + gg * DP);
-                float acc0 = 0.f, acc1 = 0.f;
-#pragma unroll
-                for (int q = 0; q < DMAX / 4; ++q) {
-                    if (q * 4 < DP) {
-                        float4 c = c4[q];
-                        float t0 = xs[4 * q] - c.x, t1 = xs[4 * q + 1] - c.y;
-                        float t2 = xs[4 * q + 2] - c.z, t3 = xs[4 * q + 3] - c.w;
-                        acc0 = fmaf(t0, t0, acc0); acc1 = fmaf(t1, t1, acc1);
-                        acc0 = fmaf(t2, t2, acc0); acc1 = fmaf(t3, t3, acc1);
-                    }
-                }
-                const float acc = acc0 + acc1;
-                if (acc < b1) { b2 = b1; b1 = acc; a1 = g0 + gg; }
-                else if (acc < b2) { b2 = acc; }
-            }
-        }
-        if (!valid) continue;
-        const float norms = snorm + nmax_all;
-        int best = a1;
-        if (G > 1 && !(b2 - km_err(b2, norms, D) > b1 + km_err(b1, norms, D)))
-            best = km_recheck_fp64(a.X + i * D, D, G, a.means, a.w);
-        a.assign[i] = best;
-        const double *mu = a.means + (size_t)best * D;
-        float *sg = slab + (size_t)best * SP;
-        atomicAdd(sg, 1.f);
-#pragma unroll
-        for (int d = 0; d < DMAX; d += 2) {
-            if (d < D) {
-                const float u0 = xr[d] - (float)mu[d];
-                const float u1 = d + 1 < D ? xr[d + 1] - (float)mu[d + 1] : 0.f;
-                atomicAdd(reinterpret_cast<float4 *>(sg + 4 + 2 * d), make_float4(u0, u0 * u0, u1, u1 * u1));
-            }
-        }
-    }
-    __threadfence();
-    __syncthreads();
-    const int S = 1 + 2 * D;
-    double *P = a.partial + (size_t)blockIdx.x * G * S;
-    for (int k = threadIdx.x; k < G * S; k += blockDim.x) {
-        const int g = k / S, j = k - g * S;
-        const int src = j == 0 ? 0 : (j <= D ? 4 + 2 * (j - 1) : 4 + 2 * (j - 1 - D) + 1);
-        P[k] = (double)__ldcg(slab + (size_t)g * SP + src);
-    }
-}
 
 // Tiled form of the k-means map step for D <= 64, N_G <= 256 (one CTA per
 // SM, its contiguous chunk of samples).  With scaled coordinates
@@ -1346,10 +1196,12 @@ static bool km_tile_fits(int32_t D, int32_t G)
     return km_tile_smem(D, G) + 2048u <= (size_t)optin;
 }
 
+bool km_tile_supported(int32_t D, int32_t G) { return km_tile_fits(D, G); }
+
 int km_grid(int32_t D, int32_t G, int sms)
 {
     if (km_tile_fits(D, G)) return sms;   // tiled form: one CTA per SM
-    return sms * 3;                       // the means slab (<= 64 KB) lets three CTAs share an SM
+    return em_blocked_chunks(G, sms);     // register-blocked form: one partial per sample chunk
 }
 
 cudaError_t launch_global_stats(const float *X, int64_t N, int32_t D, double var_floor, int32_t dist,
@@ -1377,55 +1229,26 @@ cudaError_t launch_gather_seeds(const float *X, int32_t D, int32_t G, const int6
     return cudaGetLastError();
 }
 
-static size_t km_slab_smem(int32_t D, int32_t G, int *GS_out, int *DP_out)
-{
-    const int DP = (D + 3) & ~3;
-    int GS = (int)((64 * 1024) / (sizeof(float) * (DP + 1)));
-    if (GS > G) GS = G;
-    if (GS < 1) GS = 1;
-    *GS_out = GS;
-    *DP_out = DP;
-    return sizeof(float) * ((size_t)GS * DP + GS);
-}
-
 cudaError_t launch_km_pass(const float *X, int64_t N, int32_t D, int32_t G, const double *par,
-                           const double *wdist, const float *sw, float *slab, double *partial, int32_t grid,
-                           int32_t *assign, DevStatus *status, cudaStream_t s)
+                           const double *wdist, const float *sw, double *partial, int32_t grid, int32_t *assign,
+                           DevStatus *status, cudaStream_t s)
 {
-    int GS, DP;
-    const size_t sm = km_slab_smem(D, G, &GS, &DP);
-    KmArgs a{X, N, D, DP, G, GS, par, wdist, sw, slab, partial, assign, status};
-    if (km_tile_fits(D, G)) {
-        const size_t smt = km_tile_smem(D, G);
+    if (!km_tile_fits(D, G)) return cudaErrorInvalidConfiguration;   // the register-blocked form's shapes
+    KmArgs a{X, N, D, (D + 3) & ~3, G, G, par, wdist, sw, partial, assign, status};
+    const size_t smt = km_tile_smem(D, G);
 #define KMT_LAUNCH(NJ)                                                                              \
     do {                                                                                            \
         cudaFuncSetAttribute(k_km_tile<NJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smt); \
         k_km_tile<NJ><<<grid, kKmTileThreads, smt, s>>>(a);                                         \
     } while (0)
-        if (G <= 32) KMT_LAUNCH(1);
-        else if (G <= 64) KMT_LAUNCH(2);
-        else if (G <= 128) KMT_LAUNCH(4);
-        else KMT_LAUNCH(8);
+    if (G <= 32) KMT_LAUNCH(1);
+    else if (G <= 64) KMT_LAUNCH(2);
+    else if (G <= 128) KMT_LAUNCH(4);
+    else KMT_LAUNCH(8);
 #undef KMT_LAUNCH
-        count_launches(1);
-        return cudaGetLastError();
-    }
-    const int dm = dmax_for(D);
-#define KM_LAUNCH(DM)                                                                              \
-    do {                                                                                           \
-        cudaFuncSetAttribute(k_km_pass<DM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
-        k_km_pass<DM><<<grid, kKmThreads, sm, s>>>(a);                                             \
-    } while (0)
-    if (dm == 16) KM_LAUNCH(16);
-    else if (dm == 32) KM_LAUNCH(32);
-    else if (dm == 64) KM_LAUNCH(64);
-    else KM_LAUNCH(128);
-#undef KM_LAUNCH
     count_launches(1);
     return cudaGetLastError();
 }
-
-size_t km_slab_floats(int32_t D, int32_t G, int grid) { return (size_t)grid * G * (4 + 2 * ((D + 3) & ~3)); }
 
 cudaError_t launch_km_finalize(const double *partial, int32_t n_partial, int64_t N, int32_t D, int32_t G,
                                double *par, double var_floor, int32_t final_iter, double *counts,

@@ -383,17 +383,25 @@ def test_two_phase_em_matches_oracle(shape):
         em_step_check(g, X, Xd)
 
 
-def test_kmeans_multi_slab_exact():
-    """More means than one shared-memory slab holds: the pass walks slabs."""
-    X, _, _ = synth.make("c1", N=5000, D=128, G=300, seed=9)
-    seeds = synth.seeds_subset(X, 300, 4)
-    w, gv = km_weights(X, GMM_MAHA, 1e-10)
+@pytest.mark.parametrize("dist", [GMM_MAHA, GMM_EUCL])
+@pytest.mark.parametrize("shape", [(5000, 128, 300), (3001, 100, 40), (4000, 17, 400), (777, 65, 64), (90, 70, 3)])
+def test_kmeans_register_blocked_exact(shape, dist):
+    """Shapes beyond the tiled form (D > 64 or N_G > 256) take the
+    register-blocked k-means (blocks of 64 means, partial best two per block,
+    merged, near ties re-decided in FP64): the assignment equals the FP64
+    argmin away from near ties, and the updated parameters the oracle's."""
+    N, D, G = shape
+    X, _, _ = synth.make("c1", N=N, D=D, G=G, seed=9 + N)
+    seeds = synth.seeds_subset(X, G, 4)
+    w, gv = km_weights(X, dist, 1e-10)
     M, V, H, A = oracle.kmeans(X, seeds, w, gv, 1, 1e-10)
     _, b1, b2 = oracle.km_assign(X, seeds, w)
-    g = GMM().set_params(seeds, np.ones_like(seeds), np.full(300, 1.0 / 300))
-    a = g.kmeans(dev(X), 1).cpu().numpy()
+    g = GMM().set_params(seeds, np.ones_like(seeds), np.full(G, 1.0 / G))
+    a = g.kmeans(dev(X), 1, dist_mode=dist).cpu().numpy()
     ok = ~near_tie_mask(b1, b2)
     np.testing.assert_array_equal(a[ok], A[ok])
+    if ok.all():
+        assert_params(g.get_params(), (M, V, H), X, rtol=1e-6)
 
 
 def test_c3_full_size_fp32_properties_and_sampled_log_p():
