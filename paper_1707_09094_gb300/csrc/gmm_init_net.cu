@@ -24,6 +24,8 @@
 #include <cstring>
 #include <vector>
 
+#include <cuda.h>
+
 #include "gmm_internal.cuh"
 #include "tc_ptx.cuh"
 
@@ -256,6 +258,191 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(TcGemm g)
     tc_fence_before();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, kCols);
+}
+
+
+// ------------------------------------------------------------------------
+// Persistent tcgen05 GEMM for the per-point layers' forward and input-
+// gradient products (M = points, N = BN <= 256, K <= 256): out[M][N] =
+// epilogue(sum_k A[m][k] B[n][k]).  One CTA per SM walks 128-row tiles
+// (tile = blockIdx.x + j gridDim.x) with three warp roles:
+//   warp 0  loads B (all of K, once) and each tile's 64-wide K blocks of A
+//           by tiled TMA (128-byte swizzle, the MMA's K-major layout) into a
+//           ring of four stages, each stage freed by the MMAs' commit;
+//   warp 1  allocates two TMEM accumulators (2 BN columns) and issues the
+//           MMAs of tile j into accumulator j & 1;
+//   warps 2-9  the epilogue of tile j from accumulator j & 1 (warp w reads
+//           TMEM lanes 32 (w % 4).. and column half (w - 2) / 4), bias +
+//           ReLU or the ReLU-backward mask, to BF16, then free the
+//           accumulator for tile j + 2,
+// so loads, MMAs and the epilogue of consecutive tiles overlap.  K past the
+// operands is zero-filled by the TMA.  Every wait is bounded: on expiry the
+// CTA raises *err, drains its copies and MMAs, frees its TMEM and returns.
+// ------------------------------------------------------------------------
+struct TmaGemm {
+    int M, N, K;
+    int mode;                    // 1: bias + ReLU -> BF16; 2: masked by a stored activation -> BF16
+    const float *bias;
+    __nv_bfloat16 *out; int ldo;
+    const __nv_bfloat16 *ref; int ldr;
+    long long budget;
+    int *err;
+};
+
+constexpr int kTmaStages = 4;
+constexpr int kTmaThreads = 320;   // producer warp, MMA warp, eight epilogue warps
+
+template <int BN, int NKB>
+__global__ void __launch_bounds__(kTmaThreads, 1) k_gemm_tma(const __grid_constant__ CUtensorMap tmA,
+                                                     const __grid_constant__ CUtensorMap tmB, TmaGemm g)
+{
+    extern __shared__ __align__(1024) unsigned char gm_raw[];
+    unsigned char *sb = gm_raw + ((1024u - (smem_u32(gm_raw) & 1023u)) & 1023u);
+    constexpr uint32_t kA = 16384u;                 // 128 rows x 128 B
+    constexpr uint32_t kB = (uint32_t)BN * 128u;    // BN rows x 128 B per K block
+    constexpr int NS = kTmaStages;
+    unsigned char *sB = sb;
+    unsigned char *sA = sb + NKB * kB;
+    uint64_t *full = reinterpret_cast<uint64_t *>(sA + NS * kA);
+    uint64_t *empty = full + NS;
+    uint64_t *tfull = empty + NS;     // [2]
+    uint64_t *tempty = tfull + 2;     // [2]
+    uint64_t *bfull = tempty + 2;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bfull + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tslot + 1);
+    float *sbias = reinterpret_cast<float *>(tslot + 4);   // [BN]
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ntiles = (g.M + 127) / 128;
+    if (tid == 0) {
+        for (int k = 0; k < NS; ++k) { mbar_init(full + k, 1); mbar_init(empty + k, 1); }
+        for (int k = 0; k < 2; ++k) { mbar_init(tfull + k, 1); mbar_init(tempty + k, 8); }
+        mbar_init(bfull, 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(tslot, 2 * BN);
+        tmem_relinquish();
+    }
+    if (g.mode == 1)
+        for (int k = tid; k < BN; k += kTmaThreads) sbias[k] = k < g.N ? g.bias[k] : 0.f;
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    int issued = 0;   // A loads issued (producer)
+    if (warp == 0) {
+        if (lane == 0) {
+            mbar_expect_tx(bfull, NKB * kB);
+            for (int kb = 0; kb < NKB; ++kb) tma_load_2d(sB + kb * kB, &tmB, kb * 64, 0, bfull);
+            for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x)
+                for (int kb = 0; kb < NKB; ++kb) {
+                    const int s = issued % NS;
+                    if (issued >= NS && !mbar_wait(empty + s, (uint32_t)(((issued / NS) - 1) & 1), abort_flag, g.budget))
+                        break;
+                    mbar_expect_tx(full + s, kA);
+                    tma_load_2d(sA + s * kA, &tmA, kb * 64, t * 128, full + s);
+                    ++issued;
+                }
+        }
+    } else if (warp == 1) {
+        if (lane == 0 && mbar_wait(bfull, 0u, abort_flag, g.budget)) {
+            const uint32_t idesc = idesc_bf16(128, BN);
+            int used = 0, tc = 0;
+            for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x, ++tc) {
+                const int acc = tc & 1;
+                if (tc >= 2 && !mbar_wait(tempty + acc, (uint32_t)(((tc >> 1) - 1) & 1), abort_flag, g.budget)) break;
+                tc_fence_after();
+                bool ok = true;
+                for (int kb = 0; kb < NKB; ++kb) {
+                    const int s = used % NS;
+                    if (!mbar_wait(full + s, (uint32_t)((used / NS) & 1), abort_flag, g.budget)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t a = smem_u32(sA + s * kA), b = smem_u32(sB + kb * kB);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        tc_mma(tmem + (uint32_t)(acc * BN), desc_k_sw128(a + kk * 32u), desc_k_sw128(b + kk * 32u), idesc,
+                               (kb > 0 || kk > 0) ? 1u : 0u);
+                    tc_commit(empty + s);   // the stage is free once these MMAs are done
+                    ++used;
+                }
+                if (!ok) break;
+                tc_commit(tfull + acc);     // the accumulator is ready
+            }
+            // drain: every MMA issued must be complete before TMEM is freed
+            if (used > 0) {
+                const int s = (used - 1) % NS;
+                const uint32_t ph = (uint32_t)(((used - 1) / NS) & 1);
+                const long long d0 = clock64();
+                while (!mbar_try_wait(empty + s, ph) && clock64() - d0 < g.budget) {
+                }
+            }
+        }
+    } else {
+        // ---- epilogue warps 2..9: TMEM lane quadrant q = warp % 4, column half
+        const int q = warp & 3, ch = (warp - 2) >> 2;
+        int tc = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++tc) {
+            const int acc = tc & 1;
+            if (!mbar_wait(tfull + acc, (uint32_t)((tc >> 1) & 1), abort_flag, g.budget)) break;
+            tc_fence_after();
+            const int row = t * 128 + 32 * q + lane;
+            const uint32_t tl = tmem + (uint32_t)(acc * BN) + ((uint32_t)(32 * q) << 16);
+            const bool vec_ref = g.mode == 2 && (g.ldr & 7) == 0 && (reinterpret_cast<uintptr_t>(g.ref) & 15u) == 0;
+#pragma unroll 1
+            for (int c0 = ch * (BN / 2); c0 < (ch + 1) * (BN / 2); c0 += 16) {
+                uint32_t r[16];
+                tmem_ld16(tl + (uint32_t)c0, r);
+                tmem_wait_ld();
+                if (row >= g.M || c0 >= g.N) continue;
+                __nv_bfloat16 v[16];
+                if (g.mode == 1) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) v[j] = __float2bfloat16_rn(fmaxf(__uint_as_float(r[j]) + sbias[c0 + j], 0.f));
+                } else {
+                    const __nv_bfloat16 *h = g.ref + (size_t)row * g.ldr + c0;
+                    __nv_bfloat16 hv[16];
+                    if (vec_ref && c0 + 16 <= g.N) {
+                        *reinterpret_cast<uint4 *>(hv) = reinterpret_cast<const uint4 *>(h)[0];
+                        *reinterpret_cast<uint4 *>(hv + 8) = reinterpret_cast<const uint4 *>(h)[1];
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) hv[j] = (c0 + j < g.N) ? h[j] : __float2bfloat16_rn(0.f);
+                    }
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        v[j] = __float2bfloat16_rn(__bfloat162float(hv[j]) > 0.f ? __uint_as_float(r[j]) : 0.f);
+                }
+                __nv_bfloat16 *o = g.out + (size_t)row * g.ldo + c0;
+                if (c0 + 16 <= g.N && (g.ldo & 7) == 0 && (reinterpret_cast<uintptr_t>(o) & 15u) == 0) {
+                    reinterpret_cast<uint4 *>(o)[0] = *reinterpret_cast<const uint4 *>(v);
+                    reinterpret_cast<uint4 *>(o)[1] = *reinterpret_cast<const uint4 *>(v + 8);
+                } else {
+                    for (int j = 0; j < 16 && c0 + j < g.N; ++j) o[j] = v[j];
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tempty + acc);
+        }
+    }
+    // drain the producer's copies (bounded, whatever the abort flag) before the
+    // shared memory is released: the last load of every stage has landed
+    if (warp == 0 && lane == 0) {
+        const long long d0 = clock64();
+        for (int s = 0; s < NS && s < issued; ++s) {
+            const int last = issued - 1 - ((issued - 1 - s) % NS);   // the last load into stage s
+            const uint32_t ph = (uint32_t)((last / NS) & 1);
+            while (!mbar_try_wait(full + s, ph) && clock64() - d0 < g.budget) {
+            }
+        }
+        while (!mbar_try_wait(bfull, 0u) && clock64() - d0 < g.budget) {
+        }
+        if (*abort_flag) atomicExch(g.err, 1);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) tmem_dealloc(tmem, 2 * BN);
 }
 
 // out[c][r] = in[r][c] for a BF16 [R][C] matrix (32 x 32 tiles)
@@ -720,6 +907,88 @@ cudaError_t gemm_tc(const __nv_bfloat16 *A, const __nv_bfloat16 *B, int64_t M, i
     return cudaGetLastError();
 }
 
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library)
+EncodeTiledFn encode_tiled()
+{
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+// BF16 [rows][cols] (row stride ld elements) as boxes of 64 columns x box_rows
+// rows in the 128-byte swizzle; reads past the matrix return zeros
+bool make_map(CUtensorMap *m, const __nv_bfloat16 *base, int64_t rows, int cols, int ld, int box_rows)
+{
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 2u};
+    const cuuint32_t box[2] = {64u, (cuuint32_t)box_rows};
+    const cuuint32_t es[2] = {1u, 1u};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(base), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int sm_count()
+{
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n < 1) n = 1;
+    }
+    return n;
+}
+
+// The persistent TMA GEMM for out = epilogue(A B^T) (modes 1, 2 of k_gemm_tc)
+// with N = 256 and K <= 256; cudaErrorNotSupported (nothing launched) for
+// any other shape, alignment, or without the tensor-map entry point.
+cudaError_t gemm_tma(const __nv_bfloat16 *A, const __nv_bfloat16 *B, int64_t M, int N, int K, int lda, int ldb,
+                     int mode, const float *bias, __nv_bfloat16 *out, int ldo, const __nv_bfloat16 *ref, int ldr,
+                     int *err, cudaStream_t s)
+{
+    constexpr int BN = 256;
+    if (N != BN || K < 1 || K > 256 || K % 8 != 0 || lda % 8 != 0 || ldb % 8 != 0 || M < 1 || M > INT32_MAX ||
+        ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15u) != 0 || (mode != 1 && mode != 2))
+        return cudaErrorNotSupported;
+    CUtensorMap ta, tb;
+    if (!make_map(&ta, A, M, K, lda, 128) || !make_map(&tb, B, N, K, ldb, BN)) return cudaErrorNotSupported;
+    const int nkb = (K + 63) / 64;
+    TmaGemm gg{(int)M, N, K, mode, bias, out, ldo, ref, ldr, 2000000000LL, err};
+    const size_t sm = (size_t)nkb * BN * 128 + (size_t)kTmaStages * 16384 + 256 + 4 * BN + 1024;
+    const int ntiles = (int)((M + 127) / 128);
+    const int grid = std::min(ntiles, sm_count());
+#define GTMA(NKB)                                                                                              \
+    do {                                                                                                       \
+        cudaError_t e_ = cudaFuncSetAttribute(k_gemm_tma<BN, NKB>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                              (int)sm);                                                        \
+        if (e_ != cudaSuccess) return e_;                                                                      \
+        k_gemm_tma<BN, NKB><<<grid, kTmaThreads, sm, s>>>(ta, tb, gg);                                         \
+    } while (0)
+    if (nkb == 1) GTMA(1);
+    else if (nkb == 2) GTMA(2);
+    else if (nkb == 3) GTMA(3);
+    else GTMA(4);
+#undef GTMA
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t transpose_bf16(const __nv_bfloat16 *in, __nv_bfloat16 *out, int64_t R, int C, cudaStream_t s)
 {
     k_transpose_bf16<<<dim3((unsigned)((C + 31) / 32), (unsigned)((R + 31) / 32)), dim3(32, 8), 0, s>>>(in, out, R, C);
@@ -744,8 +1013,13 @@ cudaError_t net_forward(InitNet &n, const float *pts, int B, int P, Ws &w, cudaS
         const __nv_bfloat16 *W = n.wbf + n.w_off[l];
         if (tc_usable(in, W, kin, kin, kin)) {
             // tensor cores, bias + ReLU + BF16 in the epilogue
-            CKE(gemm_tc(in, W, BP, n.Hp, kin, kin, kin, 1, nullptr, 0, n.wgt + n.b_off[l], w.h[l], n.Hp, nullptr, 0, 1,
-                        n.err, s));
+            const cudaError_t e = gemm_tma(in, W, BP, n.Hp, kin, kin, kin, 1, n.wgt + n.b_off[l], w.h[l], n.Hp, nullptr, 0,
+                                           n.err, s);
+            if (e == cudaErrorNotSupported)
+                CKE(gemm_tc(in, W, BP, n.Hp, kin, kin, kin, 1, nullptr, 0, n.wgt + n.b_off[l], w.h[l], n.Hp, nullptr, 0,
+                            1, n.err, s));
+            else
+                CKE(e);
         } else {
             CKE(gemm(in, W, w.z, (int)BP, n.Hp, kin, kin, kin, n.Hp, 0, 0, 1, 0, s));
             k_bias_act<<<blocks_for(BP * n.Hp, 256), 256, 0, s>>>(w.z, n.wgt + n.b_off[l], w.h[l], nullptr, BP, n.Hp, 1);
@@ -814,8 +1088,13 @@ cudaError_t net_backward(InitNet &n, int B, int P, Ws &w, cudaStream_t s)
         // dZ_{l-1} = (cur W_l) masked by ReLU'(h_{l-1})
         if (tc_usable(cur, w.wT, n.Hp, n.Hp, n.Hp)) {
             CKE(transpose_bf16(W, w.wT, n.Hp, kin, s));
-            CKE(gemm_tc(cur, w.wT, BP, kin, n.Hp, n.Hp, n.Hp, 2, nullptr, 0, nullptr, nxt, kin, w.h[l - 1], kin, 1, n.err,
-                        s));
+            const cudaError_t e = gemm_tma(cur, w.wT, BP, kin, n.Hp, n.Hp, n.Hp, 2, nullptr, nxt, kin, w.h[l - 1], kin,
+                                           n.err, s);
+            if (e == cudaErrorNotSupported)
+                CKE(gemm_tc(cur, w.wT, BP, kin, n.Hp, n.Hp, n.Hp, 2, nullptr, 0, nullptr, nxt, kin, w.h[l - 1], kin, 1,
+                            n.err, s));
+            else
+                CKE(e);
             std::swap(cur, nxt);
         } else {
             CKE(gemm(cur, W, w.dh, (int)BP, kin, n.Hp, n.Hp, kin, kin, 0, 1, 1, 0, s));
