@@ -390,11 +390,9 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_gemm_tma(const __grid_consta
             const uint32_t tl = tmem + (uint32_t)(acc * BN) + ((uint32_t)(32 * q) << 16);
             const bool vec_ref = g.mode == 2 && (g.ldr & 7) == 0 && (reinterpret_cast<uintptr_t>(g.ref) & 15u) == 0;
 #pragma unroll 1
-            for (int c0 = ch * (BN / 2); c0 < (ch + 1) * (BN / 2); c0 += 16) {
-                uint32_t r[16];
-                tmem_ld16(tl + (uint32_t)c0, r);
-                tmem_wait_ld();
-                if (row >= g.M || c0 >= g.N) continue;
+            // 16 columns of this row -> BF16
+            auto emit = [&](int c0, const uint32_t (&r)[16]) {
+                if (row >= g.M || c0 >= g.N) return;
                 __nv_bfloat16 v[16];
                 if (g.mode == 1) {
 #pragma unroll
@@ -420,6 +418,16 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_gemm_tma(const __grid_consta
                 } else {
                     for (int j = 0; j < 16 && c0 + j < g.N; ++j) o[j] = v[j];
                 }
+            };
+            // 32 columns per TMEM round trip: two loads in flight, one wait
+#pragma unroll 1
+            for (int c0 = ch * (BN / 2); c0 < (ch + 1) * (BN / 2); c0 += 32) {
+                uint32_t ra[16], rb[16];
+                tmem_ld16(tl + (uint32_t)c0, ra);
+                tmem_ld16(tl + (uint32_t)(c0 + 16), rb);
+                tmem_wait_ld();
+                emit(c0, ra);
+                emit(c0 + 16, rb);
             }
             tc_fence_before();
             __syncwarp();
