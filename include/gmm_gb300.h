@@ -370,6 +370,12 @@ gmm_status gmm_profile_read(const gmm_model *m, double *pass_ms, int64_t *pass_l
  *                          register-blocked form for every shape (the same
  *                          results to FP32 rounding). */
 #define GMM_DEBUG_FP32_FORM 4
+/*   GMM_DEBUG_TC_FORM      0 (default): the BF16 EM pass runs the one-tile
+ *                          tensor-core form for D <= 64 and N_G <= 256, else
+ *                          the blocked split-BF16 form; 1: the blocked form
+ *                          for every shape it supports (the same results to
+ *                          FP32 rounding). */
+#define GMM_DEBUG_TC_FORM 5
 gmm_status gmm_debug_set(gmm_model *m, int32_t key, int64_t value);
 
 /* Screening counters of the tensor-core pass, summed since the last
@@ -393,6 +399,12 @@ gmm_status gmm_debug_set(gmm_model *m, int32_t key, int64_t value);
 #define GMM_STAT_KM_SCREENED 14
 #define GMM_STAT_KM_DEFERRED 15
 #define GMM_STAT_KM_FP64 16
+/* Blocked tensor-core EM pass: GMM_STAT_RECOMPUTED samples holding more
+ * responsibilities of at least 1e-9 / N than their record takes (8); the
+ * M-step recomputes them over every block of Gaussians.  (GMM_STAT_SCREENED,
+ * _KEPT and _DENSE count samples, candidates and samples screened with more
+ * than 64 candidates.) */
+#define GMM_STAT_RECOMPUTED 17
 gmm_status gmm_debug_get(const gmm_model *m, int32_t key, int64_t *value);
 
 /* Thread-local text of the last error ("" if none). */

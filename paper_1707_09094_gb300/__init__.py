@@ -233,7 +233,8 @@ class GMM:
         return ms.value, n.value, k.value
 
     def debug_set(self, key, value):
-        """Test hooks (GMM_DEBUG_WAIT_CYCLES, GMM_DEBUG_SKIP_MMA, GMM_DEBUG_KM_FORM, GMM_DEBUG_FP32_FORM)."""
+        """Test hooks (GMM_DEBUG_WAIT_CYCLES, GMM_DEBUG_SKIP_MMA, GMM_DEBUG_KM_FORM, GMM_DEBUG_FP32_FORM,
+        GMM_DEBUG_TC_FORM)."""
         _lib.check(_lib.load().gmm_debug_set(self._h, key, int(value)), "gmm_debug_set")
         return self
 
@@ -245,6 +246,13 @@ class GMM:
             _lib.check(_lib.load().gmm_debug_get(self._h, k, ctypes.byref(v)), "gmm_debug_get")
             out.append(v.value)
         return tuple(out)
+
+    def recomputed(self):
+        """Samples of the blocked tensor-core EM pass whose kept responsibilities
+        exceeded their record (recomputed in its M-step) since profile()."""
+        v = ctypes.c_int64()
+        _lib.check(_lib.load().gmm_debug_get(self._h, _lib.GMM_STAT_RECOMPUTED, ctypes.byref(v)), "gmm_debug_get")
+        return v.value
 
     def km_screen_stats(self):
         """(samples screened, deferred to the exact FP32 decision, re-decided in FP64) of the

@@ -17,7 +17,7 @@ SRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "libgmm_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["gmm_capi.cu", "gmm_simt.cu", "gmm_blocked.cu", "gmm_em_tc.cu", "gmm_km_tc.cu", "gmm_batched.cu",
+SOURCES = ["gmm_capi.cu", "gmm_simt.cu", "gmm_blocked.cu", "gmm_em_tc.cu", "gmm_em_wide.cu", "gmm_km_tc.cu", "gmm_batched.cu",
            "gmm_init_net.cu"]
 
 

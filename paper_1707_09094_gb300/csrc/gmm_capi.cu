@@ -24,7 +24,7 @@ namespace {
 
 // Device counters of gmm_profile: words 0-10 the EM screening kernel's,
 // words 11-13 the tensor-core k-means pass's (screened, deferred, FP64).
-constexpr int kStatWords = 14;
+constexpr int kStatWords = 15;
 constexpr int kStatKm = 11;
 
 thread_local std::string g_err;
@@ -128,6 +128,7 @@ struct gmm_model {
     double *partial = nullptr; size_t partial_cap = 0;
     uint8_t *kmarg = nullptr; size_t kmarg_cap = 0;           // register-blocked k-means: argmin per block | max norm
     unsigned char *tclist = nullptr; size_t tclist_cap = 0;   // tensor-core pass: per-sample records
+    unsigned char *wide = nullptr; size_t wide_cap = 0;       // tensor-core pass beyond D 64 / N_G 256
     unsigned char *kmop = nullptr; size_t kmop_cap = 0;       // tensor-core k-means operands
     double *spread = nullptr; size_t spread_cap = 0;          // spread seeding: distances + block partials
     cudaStream_t cstream = nullptr;                           // host-input copies that overlap the first pass
@@ -156,6 +157,7 @@ struct gmm_model {
     int skip_mma = 0;
     int km_form = 0;                        // 0: tensor cores where supported, 1: CUDA cores
     int fp32_form = 0;                      // 0: by shape, 1: one-pass where it fits, 2: register-blocked
+    int tc_form = 0;                        // 0: by shape, 1: the D <= 128 / N_G <= 4096 pass for every shape
     unsigned long long *sstats = nullptr;   // screening counters (device, [kStatWords])
 
     double *means() const { return par[cur]; }
@@ -335,8 +337,11 @@ gmm_status run_em(gmm_model *m, const float *Xd, int64_t N, int32_t em_iter, dou
 {
     const int32_t D = m->D, G = m->G, S = 1 + 2 * D;
     const bool tc = prec == GMM_BF16;
-    if (tc && !gmm::em_tc_supported(D, G))
-        return fail(GMM_ERR_UNSUPPORTED, "tensor-core E-step needs D <= 64 and n_gaus <= 256 (D=%d, G=%d)", D, G);
+    // tensor cores: the one-tile pass for D <= 64 and N_G <= 256, else the
+    // split-BF16 screen over blocks of Gaussians (D <= 128, N_G <= 4096)
+    const bool wide = tc && (m->tc_form == 1 || !gmm::em_tc_supported(D, G));
+    if (wide && !gmm::em_wide_supported(D, G))
+        return fail(GMM_ERR_UNSUPPORTED, "tensor-core E-step needs D <= 128 and n_gaus <= 4096 (D=%d, G=%d)", D, G);
     // FP32: the one-pass form for N_G <= 128 while all N_G operands and
     // statistics fit in one CTA's shared memory, else the register-blocked
     // two-phase form (faster from N_G = 256: 11.0 against 12.7 ms per
@@ -349,18 +354,20 @@ gmm_status run_em(gmm_model *m, const float *Xd, int64_t N, int32_t em_iter, dou
         return fail(GMM_ERR_STATE, "tensor-core E-step needs the global centre (run learn or recompute_center)");
     // one-pass forms: one partial per CTA; two-phase form: one per sample chunk
     // (and one log-likelihood partial per 128-sample block of the lse pass)
-    const int grid = tc ? gmm::em_tc_grid(m->sms)
-                        : (two_phase ? gmm::em_blocked_chunks(G, m->sms) : gmm::em_simt_grid(D, G, m->sms));
-    if (two_phase && cp) {   // the two-phase form makes two passes: all of X first
+    const int grid = wide ? gmm::em_wide_chunks(N, G, m->sms)
+                          : (tc ? gmm::em_tc_grid(m->sms)
+                                : (two_phase ? gmm::em_blocked_chunks(G, m->sms) : gmm::em_simt_grid(D, G, m->sms)));
+    if ((two_phase || wide) && cp) {   // these forms take all of X at once
         CK(cudaStreamWaitEvent(s, cp->ready.back(), 0));
         cp = nullptr;
     }
     const int nch = cp ? (int)cp->ready.size() : 1;
-    const int n_llp = two_phase ? (int)((N + 127) / 128) : grid;
+    const int n_llp = two_phase ? (int)((N + 127) / 128) : (wide ? gmm::em_wide_ll_grid(N, m->sms) : grid);
     CK(grow(m->partial, m->partial_cap, (size_t)nch * grid * G * S));
     if (two_phase) CK(grow(m->lse, m->lse_cap, (size_t)N));
     if (two_phase) CK(grow(m->lsep, m->lsep_cap, (size_t)gmm::em_blocked_gblocks(G) * (size_t)N));
-    if (tc) CK(grow(m->tclist, m->tclist_cap, gmm::em_tc_list_bytes(N, grid)));
+    if (tc && !wide) CK(grow(m->tclist, m->tclist_cap, gmm::em_tc_list_bytes(N, grid)));
+    if (wide) CK(grow(m->wide, m->wide_cap, gmm::em_wide_ws_bytes(N, D, G)));
     CK(grow(m->llp, m->llp_cap, (size_t)nch * n_llp));
     CK(grow(m->lld, m->lld_cap, (size_t)(em_iter > 0 ? em_iter : 1)));
     CK(gmm::launch_status_reset(m->status, s));
@@ -378,7 +385,10 @@ gmm_status run_em(gmm_model *m, const float *Xd, int64_t N, int32_t em_iter, dou
             gmm::EmPassArgs pa{Xd + b0 * D, b1 - b0, D, G, m->op, m->center(), m->partial + (size_t)c * grid * G * S,
                                m->llp + (size_t)c * n_llp, m->status, k, m->wait_cycles, m->skip_mma,
                                m->profiling ? m->sstats : nullptr, N};
-            if (tc) CK(gmm::launch_em_pass_tc(pa, gmm::em_tc_lists(m->tclist, b1 - b0, grid), grid, grid, s));
+            if (wide)
+                CK(gmm::launch_em_wide(pa, m->par[(base + k) & 1], gmm::em_wide_ws(m->wide, N, D, G), grid, n_llp,
+                                       m->sms, s));
+            else if (tc) CK(gmm::launch_em_pass_tc(pa, gmm::em_tc_lists(m->tclist, b1 - b0, grid), grid, grid, s));
             else if (two_phase) CK(gmm::launch_em_blocked(pa, m->lse, m->lsep, grid, s));
             else CK(gmm::launch_em_pass_simt(pa, grid, s));
         }
@@ -464,7 +474,7 @@ void gmm_destroy(gmm_model *m)
     if (m->sstats) cudaFree(m->sstats);
     void *bufs[] = {m->par[0], m->par[1], m->op_sm, m->op_mu, m->op_c, m->op_B, m->gstat, m->fstat,
                     m->partial, m->kmarg, m->lse, m->llp, m->lld, m->counts, m->assign, m->xstage, m->dstage, m->idx,
-                    m->hist, m->status, m->tclist, m->kmop, m->spread, m->lsep};
+                    m->hist, m->status, m->tclist, m->kmop, m->spread, m->lsep, m->wide};
     for (void *p : bufs)
         if (p) cudaFree(p);
     delete m;
@@ -895,6 +905,9 @@ gmm_status gmm_debug_set(gmm_model *m, int32_t key, int64_t value)
     } else if (key == GMM_DEBUG_FP32_FORM) {
         if (value < 0 || value > 2) return fail(GMM_ERR_ARG, "FP32 form must be 0, 1 or 2");
         m->fp32_form = (int)value;
+    } else if (key == GMM_DEBUG_TC_FORM) {
+        if (value < 0 || value > 1) return fail(GMM_ERR_ARG, "tensor-core form must be 0 or 1");
+        m->tc_form = (int)value;
     } else {
         return fail(GMM_ERR_ARG, "unknown debug key %d", key);
     }

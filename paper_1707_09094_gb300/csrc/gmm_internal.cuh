@@ -241,4 +241,26 @@ size_t em_tc_list_bytes(int64_t N, int grid);
 TcLists em_tc_lists(void *base, int64_t N, int grid);
 cudaError_t launch_em_pass_tc(const EmPassArgs &a, const TcLists &L, int32_t grid, int32_t ms_chunks, cudaStream_t s);
 
+// ---- tensor-core EM pass for D <= 128, N_G <= 4096 (gmm_em_wide.cu)
+struct WideWs {              // work space, grown once per model
+    unsigned char *img;      // split BF16 operand pieces of the screen
+    float2 *bnd;             // screening constants per Gaussian
+    uint8_t *cnt;            // [N] candidates per sample (255: every Gaussian)
+    uint16_t *cand;          // [N][16] candidate Gaussians
+    float *lse;              // [N] log p(x_i)
+    uint8_t *rc;             // [N] kept responsibilities in the record (255: recompute)
+    uint16_t *rg;            // [N][8] their Gaussians
+    float *rgam;             // [N][8] and values
+};
+bool em_wide_supported(int32_t D, int32_t G);
+int em_wide_chunks(int64_t N, int32_t G, int sms);
+int em_wide_ll_grid(int64_t N, int sms);
+size_t em_wide_ws_bytes(int64_t N, int32_t D, int32_t G);
+WideWs em_wide_ws(void *base, int64_t N, int32_t D, int32_t G);
+// One EM iteration's pass from par (the iteration's parameters; op holds
+// their FP32 operands): statistics into a.partial [n_chunks][G][1 + 2D],
+// log-likelihood partials into a.ll_partial [ll_grid].
+cudaError_t launch_em_wide(const EmPassArgs &a, const double *par, const WideWs &ws, int32_t n_chunks, int32_t ll_grid,
+                           int sms, cudaStream_t s);
+
 }  // namespace gmm

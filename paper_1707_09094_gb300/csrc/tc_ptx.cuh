@@ -142,6 +142,13 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
 
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 
+// Hint: bring [src, src + bytes) into L2 (src 16-byte aligned, bytes a
+// multiple of 16).
+__device__ __forceinline__ void prefetch_l2(const void *src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 // Tiled (tensor) TMA load of a 2-D box at coordinates (c0 inner, c1 outer)
 // described by the tensor map at tmap (a __grid_constant__ kernel
 // parameter), completing on an mbarrier.  c0 times the element size must be

@@ -1,0 +1,162 @@
+"""GPU parity of the blocked tensor-core EM pass (split-BF16 screen over blocks
+of 128 Gaussians, exact FP32 recompute of the candidates, M-step from the
+kept responsibilities) against the FP64 oracle.
+
+The pass runs by itself wherever D > 64 or N_G > 256 (up to D = 128,
+N_G = 4096), and on smaller shapes through the GMM_DEBUG_TC_FORM hook.  Its
+screen drops only Gaussians whose responsibility is provably below 1e-9 / N,
+so it is held to the FP32 tolerances of test_gpu_parity.py: 1e-4 relative on
+parameters (or the oracle's FP32 budget where larger) and 1e-6 on the
+log-likelihood."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1707_09094_gb300 import GMM, GMM_MAHA, synth
+from paper_1707_09094_gb300._lib import GMM_DEBUG_TC_FORM
+from test_gpu_parity import assert_params, dev, em_step_check, km_weights
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1707_09094_gb300 import build
+    build.build()
+
+
+def _start(X, G, seed):
+    seeds = synth.seeds_subset(X, G, seed)
+    if G == 1 or X.shape[0] < 50:
+        return seeds, np.ones_like(seeds), np.full(G, 1.0 / G)
+    w, gv = km_weights(X, GMM_MAHA, 1e-10)
+    return oracle.kmeans(X, seeds, w, gv, 5, 1e-10)[:3]
+
+
+# (N, D, G): forced onto the blocked form below D 64 / N_G 256; by shape above.
+# Ragged tiles and blocks, D not a multiple of 4 or 8, one and two K pieces.
+SHAPES = [(100000, 10, 8), (7, 3, 2), (33, 1, 3), (2049, 60, 40), (3001, 64, 17), (129, 16, 16),
+          (300, 5, 200), (5000, 100, 40), (4000, 20, 300), (3000, 128, 130), (1000, 127, 9), (6000, 65, 257)]
+
+
+def wide_step(g, X, Xd):
+    """One tensor-core iteration of g against the oracle's iteration from g's
+    parameters: each parameter within 1e-4 or its FP32 budget; the mean
+    log-likelihood within 1e-6 or twice the mean of the oracle's per-sample
+    FP32 bound on log p (Gaussians collapsed onto the variance floor make
+    x s and mu s large, and FP32 then resolves their samples' log p only to
+    that bound)."""
+    start = g.get_params()
+    M, V, H, ll, budget = oracle.em_fp32_budget(X, *start, 1e-10)
+    lim = max(1e-6 * abs(ll), 2.0 * float(np.mean(oracle.log_p_fp32_bound(X, *start))))
+    g.em_iterate(Xd, 1, prec="bf16")
+    assert_params(g.get_params(), (M, V, H), X, budget=budget)
+    assert abs(g.ll_history()[-1] - ll) <= lim, (g.ll_history()[-1], ll, lim)
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_wide_em_matches_oracle(shape):
+    """Three iterations from a k-means start, each against the oracle's."""
+    N, D, G = shape
+    X, _, _ = synth.make("c1", N=N, D=D, G=G, seed=5 + N + D)
+    Xd = dev(X)
+    g = GMM().set_params(*_start(X, G, 2))
+    g.debug_set(GMM_DEBUG_TC_FORM, 1)
+    g.em_iterate(Xd, 0, recompute_center=True)
+    for _ in range(3):
+        wide_step(g, X, Xd)
+
+
+@pytest.mark.parametrize("case", ["spread48", "all40", "all100"])
+def test_wide_dense_and_recompute_paths(case):
+    """Heavily overlapping Gaussians.  spread48: 48 of 128 Gaussians, 12 in each
+    quarter of the block's columns, are candidates of every sample (the
+    screen's lists hold 16 per quarter; the exact kernel takes two per lane),
+    the other 80 lie far away; all40 / all100: every Gaussian of a 40- or
+    100-Gaussian model is a candidate, past a quarter's list, so the exact
+    kernel takes every Gaussian; 40 kept responsibilities fit the sample's
+    record, 100 do not (the M-step recomputes the sample over each block)."""
+    rng = np.random.default_rng(3)
+    N, D = 4000, 8
+    X = rng.normal(0, 1, (N, D)).astype(np.float32)
+    if case == "spread48":
+        G = 128
+        means = 30.0 + rng.normal(0, 1, (G, D))
+        near = np.concatenate([np.arange(12) + 32 * k for k in range(4)])
+        means[near] = rng.normal(0, 0.05, (near.size, D))
+    else:
+        G = 40 if case == "all40" else 100
+        means = rng.normal(0, 0.05, (G, D))
+    start = (means, np.ones((G, D)), np.full(G, 1.0 / G))
+    M, V, H, ll = oracle.em_iterate(X, *start, 2, 1e-10)
+    g = GMM().set_params(*start)
+    g.debug_set(GMM_DEBUG_TC_FORM, 1)
+    g.profile(True)
+    g.em_iterate(dev(X), 2, prec="bf16", recompute_center=True)
+    n, kept, nd = g.screen_stats()
+    dense, recomputed = {"spread48": (False, False), "all40": (True, False), "all100": (True, True)}[case]
+    assert n == 2 * N and nd == (2 * N if dense else 0) and g.recomputed() == (2 * N if recomputed else 0)
+    if case == "spread48":
+        assert kept == 2 * N * 48
+    assert_params(g.get_params(), (M, V, H), X)
+    np.testing.assert_allclose(g.ll_history(), ll, rtol=1e-6)
+
+
+def test_wide_matches_one_tile_form():
+    """On a shape both tensor-core forms take, three iterations of each from the
+    same start agree to FP32 summation noise."""
+    X, _, _ = synth.make("c2", N=200_000)
+    Xd = dev(X)
+    start = GMM().learn(Xd, 256, km_iter=5, em_iter=0, seed=1002).get_params()
+    lls = []
+    for form in (0, 1):
+        g = GMM().set_params(*start)
+        g.debug_set(GMM_DEBUG_TC_FORM, form)
+        g.em_iterate(Xd, 3, prec="bf16", recompute_center=True)
+        lls.append(np.array(g.ll_history()))
+    np.testing.assert_allclose(lls[1], lls[0], rtol=1e-6)
+
+
+def test_c3_prefix_tensor_core_iterations_match_oracle():
+    """The precision workload's shape and value distributions (D=128,
+    N_G=1024, means ~ N(0, 3^2), sigma log-uniform on [0.1, 10]) on 200,000
+    samples: from a k-means start, two tensor-core EM iterations, each against
+    the oracle's iteration from the same parameters: every Gaussian within
+    1e-4 or its FP32 budget, the log-likelihood within 1e-6."""
+    X, _, _ = synth.make("c3", N=200_000)
+    Xd = dev(X)
+    g = GMM().learn(Xd, 1024, km_iter=3, em_iter=0, seed=1003, var_floor=1e-10)
+    g.em_iterate(Xd, 0, recompute_center=True)
+    g.profile(True)
+    for _ in range(2):
+        em_step_check(g, X, Xd, prec="bf16")
+    n, kept, dense = g.screen_stats()
+    print("\nc3 prefix: %.3f candidates per sample, %d dense" % (kept / n, dense))
+    assert n == 2 * X.shape[0]
+
+
+def test_c3_full_size_tensor_core_form():
+    """N=1e7, D=128, N_G=1024 on the tensor cores: from the k-means start of
+    the bench, three iterations; the log-likelihood does not decrease and
+    matches the FP32 register-blocked form's to FP32 summation noise, and
+    sampled per-sample log-densities match the oracle's."""
+    X, _, _ = synth.make("c3")
+    Xd = dev(X)
+    start = GMM().learn(Xd, 1024, km_iter=2, em_iter=0, seed=1003, var_floor=1e-10).get_params()
+    lls = {}
+    for prec in ("bf16", "fp32"):
+        g = GMM().set_params(*start)
+        g.em_iterate(Xd, 3, prec=prec, var_floor=1e-10, recompute_center=True)
+        lls[prec] = np.array(g.ll_history())
+        if prec == "bf16":
+            m, v, h = g.get_params()
+            assert h.sum() == pytest.approx(1.0, abs=1e-6)
+            idx = np.random.default_rng(2).choice(X.shape[0], 300, replace=False)
+            lp = g.log_p(Xd).cpu().numpy()[idx]
+            np.testing.assert_allclose(lp, oracle.log_p(X[idx], m, v, h), rtol=1e-5, atol=1e-4)
+    ll = lls["bf16"]
+    assert (np.diff(ll) >= -1e-6 * np.abs(ll[1:])).all()
+    np.testing.assert_allclose(ll, lls["fp32"], rtol=1e-6)
+    del Xd
+    torch.cuda.empty_cache()
