@@ -440,7 +440,7 @@ def run_ours(args):
     if not args.no_table1:
         line["table1_em_tol"] = run_table1_leg()
     if not args.no_c3:
-        line["c3_fp32"] = run_c3_leg(peaks, peak_src)
+        line["c3"] = run_c3_leg(peaks, peak_src)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, cores, sample = cpu_oracle_rate(X)
         line["cpu_baseline"] = cpu_baseline_line(X, rate, cores, sample)
@@ -589,40 +589,60 @@ def plain_copy_gbs(X, Xd, reps=5):
     return X.nbytes / (best * 1e-3) / 1e9
 
 
-def run_c3_leg(peaks, peak_src, steps=3):
+def run_c3_leg(peaks, peak_src, steps=3, n=None):
     """The precision workload at full size (N=1e7, D=128, N_G=1024; means
     N(0, 3^2), sigma log-uniform on [0.1, 10]): k-means (2 iterations, not
-    timed), then EM iterations of the FP32 form -- the register-blocked
-    two-phase form (partial log-sum-exps per block of 64 Gaussians, their
-    merge, then responsibilities and statistics per block), because the
-    statistics of 1024 Gaussians in 128 dimensions exceed shared memory and
-    the tensor-core form needs D <= 64, N_G <= 256.  Algorithmic work as the
-    headline: 8 flop per (i, g, d); the second phase recomputes the E-step."""
+    timed), then EM iterations of each form from the same start, each after
+    one untimed iteration:
+      bf16  the blocked tensor-core pass (split-BF16 screen over blocks of 128
+            Gaussians on tcgen05, exact FP32 log-densities of the candidates,
+            M-step from the kept responsibilities);
+      fp32  the register-blocked two-phase CUDA-core form.
+    Algorithmic work as the headline: 8 flop per (i, g, d); the bf16 roofline
+    is against the BF16 tensor peak, the fp32 one against the FP32 FMA peak.
+    n: the first n samples only (profiling captures)."""
     import torch
 
     from paper_1707_09094_gb300 import GMM, synth
-    X, _, _ = synth.make("c3")
+    X, _, _ = synth.make("c3", N=n) if n else synth.make("c3")
     Xd = torch.from_numpy(X).cuda()
     N, D = X.shape
     G = 1024
-    g = GMM().learn(Xd, G, km_iter=2, em_iter=0, seed=1003, var_floor=1e-10)
-    g.em_iterate(Xd, 1)   # warm-up
-    stream = torch.cuda.current_stream()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    ev0.record(stream)
-    g.em_iterate(Xd, steps)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1) / steps
+    start = GMM().learn(Xd, G, km_iter=2, em_iter=0, seed=1003, var_floor=1e-10).get_params()
     units = N * G * D
     alu = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-    achieved = 8.0 * units / (ms * 1e-3) / 1e12
-    out = {"N": N, "D": D, "N_G": G, "form": "fp32 (register-blocked, two phases)", "ms_per_iteration": ms,
-           "units_per_s": units / (ms * 1e-3), "mean_ll": g.ll_history()[-1],
-           "roofline": {"bound": "alu", "achieved": achieved, "peak": alu, "unit": "TFLOP/s", "frac": achieved / alu,
-                        "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (%s clock)"
-                                       % (peaks.get("sm_max_mhz", 2070.0), peak_src)}}
+    out = {"N": N, "D": D, "N_G": G, "forms": {}}
+    stream = torch.cuda.current_stream()
+    for prec in ("bf16", "fp32"):
+        g = GMM().set_params(*start)
+        g.em_iterate(Xd, 1, prec=prec, var_floor=1e-10, recompute_center=True)   # warm-up
+        g.profile(True)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        g.em_iterate(Xd, steps, prec=prec, var_floor=1e-10)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / steps
+        achieved = 8.0 * units / (ms * 1e-3) / 1e12
+        f = {"ms_per_iteration": ms, "units_per_s": units / (ms * 1e-3), "mean_ll": g.ll_history()[-1]}
+        if prec == "bf16":
+            sc, kept, dense = g.screen_stats()
+            f["form"] = "tensor cores (split-BF16 screen, exact FP32 candidates)"
+            f["candidates_per_sample"] = kept / max(sc, 1)
+            f["dense_samples"] = dense
+            f["recomputed_samples"] = g.recomputed()
+            peak = peaks["bf16_tflops"]
+            f["roofline"] = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                             "frac": achieved / peak, "peak_source": "bf16_tflops (%s)" % peak_src}
+        else:
+            f["form"] = "fp32 (register-blocked, two phases)"
+            f["roofline"] = {"bound": "alu", "achieved": achieved, "peak": alu, "unit": "TFLOP/s",
+                             "frac": achieved / alu,
+                             "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (%s clock)"
+                                            % (peaks.get("sm_max_mhz", 2070.0), peak_src)}
+        out["forms"][prec] = f
+    out["delta_ll_bf16_vs_fp32"] = out["forms"]["bf16"]["mean_ll"] - out["forms"]["fp32"]["mean_ll"]
     del Xd
     torch.cuda.empty_cache()
     return out

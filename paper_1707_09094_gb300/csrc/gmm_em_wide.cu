@@ -22,14 +22,16 @@
 //     lb_g = P1 + P2 + ctc_g - (K1 |P1| + k2_g) and lists the Gaussians
 //     whose upper bound lies within T = ln(N * 1e9) nats of it, dropping
 //     entries as that bound rises; after the last block the list holds the
-//     Gaussians that can reach a responsibility of 1e-9 / N: at most 64
-//     (16 per quarter of the blocks' columns), else every Gaussian.
+//     Gaussians that can reach a responsibility of 1e-9 / N: at most 64,
+//     else every Gaussian.
 //  2. k_wide_exact -- a warp per sample, lanes over dimensions: the exact
 //     FP32 log-density c_g - 1/2 sum_d (x_d s_gd - mu_gd s_gd)^2 of each
 //     candidate, log-sum-exp (Eqs. 16-18), log p(x_i) into the CTA's FP64
 //     log-likelihood, and the responsibilities (Eq. 3) of at least exp(-T)
-//     into the sample's record (at most 64; a sample with more is marked and
-//     its pairs are recomputed in step 3).
+//     into the sample's record (at most 64; a sample with more -- only one
+//     the screen left with every Gaussian, whose log-densities take one lane
+//     per Gaussian -- is marked and its pairs are recomputed in step 3 with
+//     the same arithmetic).
 //  3. k_wide_mstep -- grid (sample chunk) x (block of 64 Gaussians): per
 //     256-sample tile the records that fall in the block, compacted in sample
 //     order; the warp that owns a Gaussian (g mod 8) adds l, l (x - mu_f),
@@ -67,8 +69,7 @@ constexpr int kWEpi = 512;              // epilogue threads: 16 warps, four per 
 constexpr int kWThreads = kWEpi + 64;   // + the MMA warp + the operand-loading warp
 constexpr int kWStages = 3;             // B operand ring
 constexpr uint32_t kWPiece = 16384;     // one operand piece: 128 rows x 64 K in BF16
-constexpr int kWQuart = 16;             // candidates per (sample, quarter of each block) in the screen's lists
-constexpr int kWCap = 4 * kWQuart;      // candidates per sample before the dense fallback
+constexpr int kWCap = 64;               // candidates per sample before the dense fallback
 constexpr int kWKeep = 64;              // responsibilities per sample record
 constexpr float kWK1 = 4.8828125e-4f;   // 2^-11
 constexpr int kWxThreads = 512;         // exact kernel: 16 warps
@@ -186,8 +187,8 @@ __host__ __device__ inline WSmem w_layout(int nkb)
     uint32_t o = 0;
     L.A = o; o += 4u * (uint32_t)nkb * kWPiece;   // t_h | t_l | x_h | x_l, nkb pieces each
     L.R = o; o += (uint32_t)kWStages * kWPiece;   // B ring
-    L.lst = o; o += 4u * kWEpi * kWQuart;         // (Gaussian, upper bound) per (sample, quarter of a block)
-    L.lcnt = o; o += 4u * kWEpi;
+    L.lst = o; o += 4u * kWTM * kWCap;            // (Gaussian, upper bound) per sample
+    L.lcnt = o; o += 4u * kWTM;                   // entries per sample (past kWCap: some lost)
     L.xlo = o; o += 8u * kWEpi;                   // block maxima of the lower bounds, two buffers
     L.sbnd = o; o += 2u * 8u * kWGB;              // screening constants of a block, two buffers
     L.ctr = o; o += 4u * 128u;
@@ -274,6 +275,7 @@ __global__ void __launch_bounds__(kWThreads, 1) k_wide_screen(WideArgs w)
     }
     for (int d = tid; d < 128; d += kWThreads) ctr[d] = d < D ? __ldg(a.center + d) : 0.f;
     for (int k = tid; k < kWGB; k += kWThreads) sbnd[k] = __ldg(w.bnd + k);   // block 0: the first job's
+    for (int k = tid; k < kWTM; k += kWThreads) lcnt[k] = 0;
     if (warp == 16) {
         tmem_alloc(tmem_slot, 512);
         tmem_relinquish();
@@ -374,14 +376,14 @@ __global__ void __launch_bounds__(kWThreads, 1) k_wide_screen(WideArgs w)
         const int s = 32 * qd + lane;             // this thread's sample in the tile (TMEM lane)
         const int ts = tid & 127;                 // thread of quarter c of this sample: ts + 128 c
         const uint32_t tl = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(32 * qq);
-        uint32_t *my = lst + tid * kWQuart;       // (g | bf16 upper bound rounded up << 16)
+        uint32_t *sl = lst + s * kWCap;           // the sample's list: g | (bf16 upper bound rounded up) << 16
         unsigned long long st_n = 0, st_c = 0, st_d = 0;
-        // keep the entries whose upper bound reaches thr, in order
+        // the sample's owner thread keeps the entries whose bound reaches thr
         auto prune = [&](int n, float thr) -> int {
             int k = 0;
             for (int e = 0; e < n; ++e) {
-                const uint32_t v = my[e];
-                if (__uint_as_float(v & 0xFFFF0000u) >= thr) my[k++] = v;
+                const uint32_t v = sl[e];
+                if (__uint_as_float(v & 0xFFFF0000u) >= thr) sl[k++] = v;
             }
             return k;
         };
@@ -390,8 +392,7 @@ __global__ void __launch_bounds__(kWThreads, 1) k_wide_screen(WideArgs w)
             const int64_t i0 = (t0 + t) * kWTM;
             const int nvalid = (int)min((int64_t)kWTM, a.N - i0);
             float mrun = -INFINITY;   // best lower bound so far of this sample (the same on its four threads)
-            int n = 0;
-            bool over = false;
+            bool lost = false;        // owner: entries were lost to a full list
             for (int j = 0; j < nb; ++j, ++q) {
                 const uint32_t buf = q & 1u;
                 // the next job's constants (block (j + 1) mod nb) into the other buffer
@@ -431,57 +432,56 @@ __global__ void __launch_bounds__(kWThreads, 1) k_wide_screen(WideArgs w)
                 const float *xb = xlo + buf * kWEpi;
                 mrun = fmaxf(mrun, fmaxf(fmaxf(xb[ts], xb[ts + 128]), fmaxf(xb[ts + 256], xb[ts + 384])));
                 const float thr = mrun - w.screen;
+                if (qq == 0 && lcnt[s] > kWCap - 32) {   // room for this block's entries
+                    const int n0 = lcnt[s];
+                    lost = lost || n0 > kWCap;
+                    lcnt[s] = prune(min(n0, kWCap), thr);
+                }
+                wepi_sync();
                 const int g0 = j * kWGB + 32 * qq;
 #pragma unroll
                 for (int e = 0; e < 32; ++e) {
                     if (ub[e] >= thr && g0 + e < G) {
-                        if (n == kWQuart) n = prune(n, thr);
-                        if (n < kWQuart) {
+                        const int k = atomicAdd(lcnt + s, 1);
+                        if (k < kWCap) {
                             // bf16 of the bound rounded up: truncation moves a negative value up
                             const uint32_t u = __float_as_uint(ub[e]);
                             const uint32_t h = (u >> 16) + (((u >> 31) == 0u && (u & 0xFFFFu) != 0u) ? 1u : 0u);
-                            my[n++] = (uint32_t)(g0 + e) | (h << 16);
-                        } else {
-                            over = true;
+                            sl[k] = (uint32_t)(g0 + e) | (h << 16);
                         }
                     }
                 }
             }
-            // ---- the four quarters' lists, pruned at the final bound -> one record per sample
-            n = prune(n, mrun - w.screen);
-            lcnt[tid] = over ? kWQuart + 1 : n;
+            // ---- the owner prunes the list at the final bound, sorts it by Gaussian
+            // and writes the sample's record
             wepi_sync();
-            if (qq == 0 && s < nvalid) {
-                int nq[4], pq[4] = {0, 0, 0, 0}, tot = 0;
-                bool ov = false;
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    nq[c] = lcnt[ts + 128 * c];
-                    ov = ov || nq[c] > kWQuart;
-                    tot += nq[c];
-                }
-                const int64_t i = i0 + s;
-                if (ov || tot == 0) {
-                    w.cnt[i] = 255;   // every Gaussian (none listed only when every bound is NaN)
-                    ++st_d;
-                } else {
-                    uint16_t *dst = w.cand + i * kWCap;
-                    for (int k = 0; k < tot; ++k) {   // 4-way merge by Gaussian index
-                        int best = -1, bv = 0x10000;
-#pragma unroll
-                        for (int c = 0; c < 4; ++c)
-                            if (pq[c] < nq[c]) {
-                                const int v = (int)(lst[(ts + 128 * c) * kWQuart + pq[c]] & 0xFFFFu);
-                                if (v < bv) { bv = v; best = c; }
+            if (qq == 0) {
+                const int n0 = lcnt[s];
+                lost = lost || n0 > kWCap;
+                int n = prune(min(n0, kWCap), mrun - w.screen);
+                if (s < nvalid) {
+                    const int64_t i = i0 + s;
+                    if (lost || n == 0) {
+                        w.cnt[i] = 255;   // every Gaussian (none listed only when every bound is NaN)
+                        ++st_d;
+                    } else {
+                        for (int e = 1; e < n; ++e) {   // insertion sort by Gaussian index
+                            const uint32_t v = sl[e];
+                            int k = e - 1;
+                            while (k >= 0 && (sl[k] & 0xFFFFu) > (v & 0xFFFFu)) {
+                                sl[k + 1] = sl[k];
+                                --k;
                             }
-                        dst[k] = (uint16_t)bv;
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) pq[c] += (c == best);
+                            sl[k + 1] = v;
+                        }
+                        uint16_t *dst = w.cand + i * kWCap;
+                        for (int e = 0; e < n; ++e) dst[e] = (uint16_t)(sl[e] & 0xFFFFu);
+                        w.cnt[i] = (uint8_t)n;
                     }
-                    w.cnt[i] = (uint8_t)tot;
+                    ++st_n;
+                    st_c += (unsigned long long)n;
                 }
-                ++st_n;
-                st_c += (unsigned long long)tot;
+                lcnt[s] = 0;
             }
             wepi_sync();   // the lists are rewritten by the next tile
         }
@@ -569,6 +569,32 @@ __device__ __forceinline__ float wide_logit(const Operands &op, int D, int g, co
     return fmaf(-0.5f, r, __ldg(op.c + g));
 }
 
+// Exact FP32 log-density of Gaussian g for a sample staged in shared memory
+// (xs[0..D)), one thread over all D (two FMA chains, dimensions 0, 2, .. and
+// 1, 3, ..): the form for a lane that takes whole Gaussians.
+__device__ __forceinline__ float dense_logit(const Operands &op, int D, int g, const float *xs, bool v4)
+{
+    const float2 *q = op.sm + (size_t)g * D;
+    float r0 = 0.f, r1 = 0.f;
+    if (v4) {   // D even, rows 16-byte aligned: two dimensions per load
+        const float4 *q4 = reinterpret_cast<const float4 *>(q);
+#pragma unroll 4
+        for (int d2 = 0; d2 < D / 2; ++d2) {
+            const float4 u = __ldg(q4 + d2);
+            const float ta = fmaf(xs[2 * d2], u.x, -u.y), tb = fmaf(xs[2 * d2 + 1], u.z, -u.w);
+            r0 = fmaf(ta, ta, r0);
+            r1 = fmaf(tb, tb, r1);
+        }
+    } else {
+        for (int d = 0; d < D; ++d) {
+            const float2 u = __ldg(q + d);
+            const float ta = fmaf(xs[d], u.x, -u.y);
+            r0 = fmaf(ta, ta, r0);
+        }
+    }
+    return fmaf(-0.5f, r0 + r1, __ldg(op.c + g));
+}
+
 // One warp per sample over a contiguous sample range per CTA; the CTA's FP64
 // log-likelihood is summed per warp in sample order, then over the warps.
 __global__ void __launch_bounds__(kWxThreads) k_wide_exact(WxArgs w)
@@ -576,6 +602,7 @@ __global__ void __launch_bounds__(kWxThreads) k_wide_exact(WxArgs w)
     const EmPassArgs &a = w.a;
     if (wide_skip(a.status, a.iter)) return;
     __shared__ double s_ll[kWxThreads / 32];
+    __shared__ float s_x[kWxThreads / 32][128];   // a dense sample's x, per warp
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     constexpr int nw = kWxThreads / 32;
     const int D = a.D, G = a.G;
@@ -643,10 +670,15 @@ __global__ void __launch_bounds__(kWxThreads) k_wide_exact(WxArgs w)
                 }
             }
         } else {
-            // every Gaussian: online (max, sum of exp), then the kept pairs
+            // every Gaussian, lanes over Gaussians: online (max, sum of exp) per
+            // lane, merged over the warp; then the kept pairs in Gaussian order
+            float *xs = s_x[warp];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) xs[4 * lane + e] = x[e];
+            __syncwarp();
             float M = -INFINITY, S = 0.f;
-            for (int g = 0; g < G; ++g) {
-                const float l = wide_logit(a.op, D, g, x, lane, sv4);
+            for (int g = lane; g < G; g += 32) {
+                const float l = dense_logit(a.op, D, g, xs, sv4);
                 if (l > M) {
                     S = S * __expf(M - l) + 1.f;
                     M = l;
@@ -654,17 +686,26 @@ __global__ void __launch_bounds__(kWxThreads) k_wide_exact(WxArgs w)
                     S += __expf(l - M);
                 }
             }
-            lse = M + logf(S);
-            for (int g = 0; g < G; ++g) {
-                const float rl = wide_logit(a.op, D, g, x, lane, sv4) - lse;
-                if (rl >= keep) {   // uniform across the warp
-                    if (m < kWKeep && lane == 0) {
-                        w.rg[i * kWKeep + m] = (uint16_t)g;
-                        w.rgam[i * kWKeep + m] = __expf(rl);
-                    }
-                    ++m;
+            float Mw = M;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) Mw = fmaxf(Mw, __shfl_xor_sync(0xffffffffu, Mw, o));
+            float Sw = (M == -INFINITY) ? 0.f : S * __expf(M - Mw);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) Sw += __shfl_xor_sync(0xffffffffu, Sw, o);
+            lse = Mw + logf(Sw);
+            for (int g0 = 0; g0 < G; g0 += 32) {
+                const int g = g0 + lane;
+                const float rl = g < G ? dense_logit(a.op, D, g, xs, sv4) - lse : -INFINITY;
+                const bool kp = rl >= keep;
+                const unsigned bal = __ballot_sync(0xffffffffu, kp);
+                const int rank = m + __popc(bal & ((1u << lane) - 1u));
+                if (kp && rank < kWKeep) {
+                    w.rg[i * kWKeep + rank] = (uint16_t)g;
+                    w.rgam[i * kWKeep + rank] = __expf(rl);
                 }
+                m += __popc(bal);
             }
+            __syncwarp();
         }
         if (lane == 0) {
             w.rc[i] = (uint8_t)(m > kWKeep ? 255 : m);
@@ -694,7 +735,7 @@ struct WmArgs {
     const float *lse;
     int32_t n_gb, n_chunks;
     float screen;
-    int32_t x_v4, s_v4;
+    int32_t s_v4;
 };
 
 struct WmSmem {
@@ -729,10 +770,11 @@ __global__ void __launch_bounds__(kWmThreads) k_wide_mstep(WmArgs w)
     uint2 *ent = reinterpret_cast<uint2 *>(wm_raw + Ls.ent);
     int *ovf = reinterpret_cast<int *>(wm_raw + Ls.ovf);
     int *scan = reinterpret_cast<int *>(wm_raw + Ls.scan);
+    __shared__ float s_ox[128], s_og[kWmBG];   // a recomputed sample's x and responsibilities
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int D = a.D, G = a.G, S = 1 + 2 * D;
     const int gb = blockIdx.x % w.n_gb, chunk = blockIdx.x / w.n_gb, g0 = gb * kWmBG;
-    const bool xv4 = w.x_v4 != 0, sv4 = w.s_v4 != 0;
+    const bool sv4 = w.s_v4 != 0;
     const float keep = -w.screen;
     double *P = a.partial + (size_t)chunk * G * S;
     for (int k = tid; k < kWmBG * 256; k += kWmThreads) S12[k] = 0.f;
@@ -887,18 +929,25 @@ __global__ void __launch_bounds__(kWmThreads) k_wide_mstep(WmArgs w)
             }
             __syncthreads();   // the window is rewritten
         }
-        // ---- samples with more than kWKeep kept pairs: every Gaussian of the
-        // block recomputed exactly (the exact kernel's arithmetic), each warp
-        // over its own Gaussians
+        // ---- samples with more than kWKeep kept pairs (only samples the screen
+        // left dense): every Gaussian of the block recomputed with the exact
+        // kernel's dense arithmetic, then added by the owner warps
         for (int e = 0; e < to; ++e) {
             const int64_t io = i0 + ovf[e];
-            float x[4];
-            wide_x(a.X, io, D, lane, xv4, x);
-            const float ls = __ldg(w.lse + io);
-            for (int gl = warp; gl < kWmBG && g0 + gl < G; gl += kWmThreads / 32) {
-                const float rl = wide_logit(a.op, D, g0 + gl, x, lane, sv4) - ls;
-                if (rl >= keep) add_pair(io, gl, __expf(rl));   // uniform across the warp
+            for (int d = tid; d < D; d += kWmThreads) s_ox[d] = __ldg(a.X + io * D + d);
+            __syncthreads();
+            if (tid < kWmBG) {
+                float gm = 0.f;
+                if (g0 + tid < G) {
+                    const float rl = dense_logit(a.op, D, g0 + tid, s_ox, sv4) - __ldg(w.lse + io);
+                    gm = rl >= keep ? __expf(rl) : 0.f;
+                }
+                s_og[tid] = gm;
             }
+            __syncthreads();
+            for (int gl = warp; gl < kWmBG; gl += kWmThreads / 32)
+                if (s_og[gl] > 0.f) add_pair(io, gl, s_og[gl]);   // uniform across the warp
+            __syncthreads();   // s_ox, s_og are rewritten
         }
         __syncthreads();   // ent, ovf and scan are rewritten by the next tile
     }
@@ -982,7 +1031,7 @@ cudaError_t launch_em_wide(const EmPassArgs &a, const double *par, const WideWs 
     k_wide_exact<<<ll_grid, kWxThreads, 0, s>>>(x);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int n_gb = (a.G + kWmBG - 1) / kWmBG;
-    WmArgs m{a, ws.rc, ws.rg, ws.rgam, ws.lse, n_gb, n_chunks, scr, xv4, sv4};
+    WmArgs m{a, ws.rc, ws.rg, ws.rgam, ws.lse, n_gb, n_chunks, scr, sv4};
     const size_t sm3 = wm_layout().total;
     if ((e = cudaFuncSetAttribute(k_wide_mstep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3)) != cudaSuccess)
         return e;

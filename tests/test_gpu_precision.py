@@ -36,11 +36,12 @@ def rel_err(got, ref, floor):
     return float(np.max(np.abs(got - ref) / (np.abs(ref) + floor)))
 
 
-@pytest.mark.parametrize("kind,N,G,forms", [("c2", 50000, 256, ("fp32", "bf16")), ("c3", 20000, 1024, ("fp32",))])
+@pytest.mark.parametrize("kind,N,G,forms", [("c2", 50000, 256, ("fp32", "bf16")), ("c3", 20000, 1024, ("fp32", "bf16"))])
 def test_precision_report(kind, N, G, forms):
     """Per form and result, the relative error of one GPU EM iteration against
-    the oracle's.  c3 (D=128, N_G=1024, sigma down to 0.1) runs the FP32
-    two-phase form only: the tensor-core form needs D <= 64 and N_G <= 256."""
+    the oracle's.  On c3 (D=128, N_G=1024, sigma down to 0.1) the FP32
+    form is the register-blocked two-phase one and the tensor-core form the
+    blocked split-BF16 screen with exact FP32 candidates."""
     X, _, _ = synth.make(kind, N=N)
     _, gv = oracle.global_stats(X)
     gv = np.maximum(gv, 1e-10)

@@ -73,10 +73,12 @@ def test_wide_dense_and_recompute_paths(case):
     """Heavily overlapping Gaussians.  spread48: 48 of 128 Gaussians, 12 in each
     quarter of the block's columns, are candidates of every sample (the
     screen's lists hold 16 per quarter; the exact kernel takes two per lane),
-    the other 80 lie far away; all40 / all100: every Gaussian of a 40- or
-    100-Gaussian model is a candidate, past a quarter's list, so the exact
-    kernel takes every Gaussian; 40 kept responsibilities fit the sample's
-    record, 100 do not (the M-step recomputes the sample over each block)."""
+    the other 80 lie far away; all40: the 40 Gaussians of a model, all in the
+    first quarter of the block's columns, are candidates of every sample
+    (the screen keeps one list per sample, up to 64); all100: 100 candidates,
+    more than a list holds, so the exact kernel takes every Gaussian, and
+    100 kept responsibilities do not fit the sample's record (the M-step
+    recomputes the sample over each block)."""
     rng = np.random.default_rng(3)
     N, D = 4000, 8
     X = rng.normal(0, 1, (N, D)).astype(np.float32)
@@ -95,10 +97,10 @@ def test_wide_dense_and_recompute_paths(case):
     g.profile(True)
     g.em_iterate(dev(X), 2, prec="bf16", recompute_center=True)
     n, kept, nd = g.screen_stats()
-    dense, recomputed = {"spread48": (False, False), "all40": (True, False), "all100": (True, True)}[case]
+    dense, recomputed = {"spread48": (False, False), "all40": (False, False), "all100": (True, True)}[case]
     assert n == 2 * N and nd == (2 * N if dense else 0) and g.recomputed() == (2 * N if recomputed else 0)
-    if case == "spread48":
-        assert kept == 2 * N * 48
+    if not dense:
+        assert kept == 2 * N * (48 if case == "spread48" else 40)
     assert_params(g.get_params(), (M, V, H), X)
     np.testing.assert_allclose(g.ll_history(), ll, rtol=1e-6)
 
