@@ -630,8 +630,7 @@ def run_c3_leg(peaks, peak_src, steps=3, n=None):
             sc, kept, dense = g.screen_stats()
             f["form"] = "tensor cores (split-BF16 screen, exact FP32 candidates)"
             f["candidates_per_sample"] = kept / max(sc, 1)
-            f["dense_samples"] = dense
-            f["recomputed_samples"] = g.recomputed()
+            f["samples_to_fp32_form"] = dense
             peak = peaks["bf16_tflops"]
             f["roofline"] = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                              "frac": achieved / peak, "peak_source": "bf16_tflops (%s)" % peak_src}
@@ -682,10 +681,16 @@ def main():
     ap.add_argument("--no-c3", action="store_true", help="skip the full-size precision workload (N=1e7, D=128)")
     ap.add_argument("--n", type=int, default=None,
                     help="time on the first n samples only (profiling captures); the default is the full workload")
+    ap.add_argument("--c3-only", action="store_true",
+                    help="run only the precision-workload leg (with --n: its first n samples) and print its JSON")
     args = ap.parse_args()
     args.forms = [f for f in args.forms.split(",") if f]
     if args.impl == "reference":
         return run_reference(args)
+    if args.c3_only:
+        peaks, peak_src = _peaks()
+        print(json.dumps(run_c3_leg(peaks, peak_src, steps=args.steps, n=args.n)), flush=True)
+        return 0
     return run_ours(args)
 
 

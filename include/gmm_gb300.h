@@ -399,12 +399,6 @@ gmm_status gmm_debug_set(gmm_model *m, int32_t key, int64_t value);
 #define GMM_STAT_KM_SCREENED 14
 #define GMM_STAT_KM_DEFERRED 15
 #define GMM_STAT_KM_FP64 16
-/* Blocked tensor-core EM pass: GMM_STAT_RECOMPUTED samples holding more
- * responsibilities of at least 1e-9 / N than their record takes (8); the
- * M-step recomputes them over every block of Gaussians.  (GMM_STAT_SCREENED,
- * _KEPT and _DENSE count samples, candidates and samples screened with more
- * than 64 candidates.) */
-#define GMM_STAT_RECOMPUTED 17
 gmm_status gmm_debug_get(const gmm_model *m, int32_t key, int64_t *value);
 
 /* Thread-local text of the last error ("" if none). */

@@ -247,13 +247,6 @@ class GMM:
             out.append(v.value)
         return tuple(out)
 
-    def recomputed(self):
-        """Samples of the blocked tensor-core EM pass whose kept responsibilities
-        exceeded their record (recomputed in its M-step) since profile()."""
-        v = ctypes.c_int64()
-        _lib.check(_lib.load().gmm_debug_get(self._h, _lib.GMM_STAT_RECOMPUTED, ctypes.byref(v)), "gmm_debug_get")
-        return v.value
-
     def km_screen_stats(self):
         """(samples screened, deferred to the exact FP32 decision, re-decided in FP64) of the
         tensor-core k-means since profile()."""

@@ -20,7 +20,6 @@ GMM_FP32, GMM_BF16 = 0, 1
 GMM_DEBUG_WAIT_CYCLES, GMM_DEBUG_SKIP_MMA, GMM_DEBUG_KM_FORM, GMM_DEBUG_FP32_FORM, GMM_DEBUG_TC_FORM = 1, 2, 3, 4, 5
 GMM_STAT_SCREENED, GMM_STAT_KEPT, GMM_STAT_DENSE = 3, 4, 5
 GMM_STAT_KM_SCREENED, GMM_STAT_KM_DEFERRED, GMM_STAT_KM_FP64 = 14, 15, 16
-GMM_STAT_RECOMPUTED = 17
 
 STATUS_NAMES = {0: "GMM_OK", -1: "GMM_ERR_ARG", -2: "GMM_ERR_NONFINITE", -3: "GMM_ERR_CUDA",
                 -4: "GMM_ERR_TIMEOUT", -5: "GMM_ERR_OOM", -6: "GMM_ERR_STATE", -7: "GMM_ERR_UNSUPPORTED"}

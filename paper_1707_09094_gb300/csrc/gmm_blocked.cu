@@ -61,7 +61,11 @@ struct BlkArgs {
     float2 *part;        // [n_gb][N] (max, sum of exp) per sample and block
     float *lse;          // [N] log p(x_i)
     double *out;         // inference: log p(x_i) in FP64 here instead of lse and the log-likelihood
+    const int64_t *n_dev;   // non-null: the samples actually present (device), at most N (part's stride)
 };
+
+// Samples present: a.N, or fewer when the count is known only on the device.
+__device__ __forceinline__ int64_t blk_n(const BlkArgs &b) { return b.n_dev ? *b.n_dev : b.a.N; }
 
 __host__ __device__ inline size_t blk_smem(int D, int TS, bool em)
 {
@@ -112,12 +116,12 @@ __device__ void blk_stage_operands(const EmPassArgs &a, int g0, float *op, float
 // Sample tile t (TS rows) -> buffer xb: cp.async for the rows that exist,
 // zeros for the rest; the zero columns D..D8-1 are written once beforehand.
 template <int TS>
-__device__ void blk_stage_tile(const BlkArgs &b, int64_t t, float *xb)
+__device__ void blk_stage_tile(const BlkArgs &b, int64_t N, int64_t t, float *xb)
 {
     const EmPassArgs &a = b.a;
     const int D = a.D, XS = blk_xs(D);
     const int64_t i0 = t * TS;
-    const int nv = (int)min((int64_t)TS, a.N - i0);
+    const int nv = (int)min((int64_t)TS, N - i0);
     if (b.x_v4) {
         const int q4 = D / 4;
         for (int k = threadIdx.x; k < TS * q4; k += kBThreads) {
@@ -188,6 +192,7 @@ __global__ void __launch_bounds__(kBThreads, 1) k_blk_lse(BlkArgs b)
     extern __shared__ __align__(16) float bsm[];
     const EmPassArgs &a = b.a;
     if (blk_skip(a.status, a.iter)) return;
+    if (blk_n(b) == 0) return;   // nothing to write (uniform)
     const int D = a.D, D8 = blk_d8(D), XS = blk_xs(D), OS = blk_os(D);
     const int gb = blockIdx.x % b.n_gb, chunk = blockIdx.x / b.n_gb;   // the chunk's blocks run side by side
     float *op = bsm, *cg = op + kBG * OS, *xt = cg + kBG;
@@ -199,14 +204,15 @@ __global__ void __launch_bounds__(kBThreads, 1) k_blk_lse(BlkArgs b)
         const int r = k / (XS - D);
         xt[r * XS + D + (k - r * (XS - D))] = 0.f;
     }
-    const int64_t ntiles = (a.N + TS - 1) / TS;
+    const int64_t N = blk_n(b);
+    const int64_t ntiles = (N + TS - 1) / TS;
     const int64_t t0 = ntiles * chunk / b.n_chunks, t1 = ntiles * (chunk + 1) / b.n_chunks;
     __syncthreads();
-    if (t0 < t1) blk_stage_tile<TS>(b, t0, xt);
+    if (t0 < t1) blk_stage_tile<TS>(b, N, t0, xt);
     cp_commit();
     for (int64_t t = t0; t < t1; ++t) {
         const int bi = (int)((t - t0) & 1);
-        if (t + 1 < t1) blk_stage_tile<TS>(b, t + 1, xt + (1 - bi) * TS * XS);
+        if (t + 1 < t1) blk_stage_tile<TS>(b, N, t + 1, xt + (1 - bi) * TS * XS);
         cp_commit();
         cp_wait<1>();
         __syncthreads();
@@ -229,7 +235,7 @@ __global__ void __launch_bounds__(kBThreads, 1) k_blk_lse(BlkArgs b)
         __syncthreads();
         const int64_t i0 = t * TS;
         for (int s = tid; s < TS; s += kBThreads) {
-            if (i0 + s < a.N) {
+            if (i0 + s < N) {
                 float2 p = red[s];
 #pragma unroll
                 for (int q = 1; q < 4; ++q) p = lse_merge(p, red[q * TS + s]);
@@ -250,7 +256,7 @@ __global__ void __launch_bounds__(128) k_blk_combine(BlkArgs b)
     if (blk_skip(a.status, a.iter)) return;
     const int64_t i = (int64_t)blockIdx.x * 128 + threadIdx.x;
     double v = 0.0;
-    if (i < a.N) {
+    if (i < blk_n(b)) {
         float2 p = b.part[i];
         for (int q = 1; q < b.n_gb; ++q) p = lse_merge(p, b.part[(size_t)q * a.N + i]);
         if (b.out) {   // the inference kernel's form: max + log(sum) in FP64
@@ -348,12 +354,13 @@ __global__ void __launch_bounds__(kBThreads, 1) k_blk_em(BlkArgs b)
         ++flushes;
         since = 0;
     };
-    const int64_t ntiles = (a.N + TS - 1) / TS;
+    const int64_t N = blk_n(b);
+    const int64_t ntiles = (N + TS - 1) / TS;
     const int64_t t0 = ntiles * chunk / b.n_chunks, t1 = ntiles * (chunk + 1) / b.n_chunks;
     __syncthreads();
     if (t0 < t1) {
-        blk_stage_tile<TS>(b, t0, xt);
-        for (int s = tid; s < TS; s += kBThreads) lt[s] = t0 * TS + s < a.N ? b.lse[t0 * TS + s] : 0.f;
+        blk_stage_tile<TS>(b, N, t0, xt);
+        for (int s = tid; s < TS; s += kBThreads) lt[s] = t0 * TS + s < N ? b.lse[t0 * TS + s] : 0.f;
     }
     cp_commit();
     for (int64_t t = t0; t < t1; ++t) {
@@ -372,7 +379,7 @@ __global__ void __launch_bounds__(kBThreads, 1) k_blk_em(BlkArgs b)
                 const float ls = lt[s];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    float gm = i0 + s < a.N ? __expf(l[k][j] - ls) : 0.f;
+                    float gm = i0 + s < N ? __expf(l[k][j] - ls) : 0.f;
                     gam[s * kGS + gg + 16 * j] = gm >= keep ? gm : 0.f;
                 }
             }
@@ -381,8 +388,8 @@ __global__ void __launch_bounds__(kBThreads, 1) k_blk_em(BlkArgs b)
         // the next tile's samples (other buffer) and log p, while the M-step
         // runs: the E-step is done with lt
         if (t + 1 < t1) {
-            blk_stage_tile<TS>(b, t + 1, xt + (1 - bi) * TS * XS);
-            for (int s = tid; s < TS; s += kBThreads) lt[s] = (t + 1) * TS + s < a.N ? b.lse[(t + 1) * TS + s] : 0.f;
+            blk_stage_tile<TS>(b, N, t + 1, xt + (1 - bi) * TS * XS);
+            for (int s = tid; s < TS; s += kBThreads) lt[s] = (t + 1) * TS + s < N ? b.lse[(t + 1) * TS + s] : 0.f;
         }
         cp_commit();
         // ---- M: this thread's 4 Gaussians x 8 dimensions over the tile's
@@ -899,10 +906,11 @@ int em_blocked_chunks(int32_t G, int sms)
     return c > 0 ? c : 1;
 }
 
-cudaError_t launch_em_blocked(const EmPassArgs &a, float *lse, float2 *part, int32_t n_chunks, cudaStream_t s)
+cudaError_t launch_em_blocked(const EmPassArgs &a, float *lse, float2 *part, int32_t n_chunks, cudaStream_t s,
+                              const int64_t *n_dev)
 {
     BlkArgs b{a, em_blocked_gblocks(a.G), n_chunks,
-              (a.D % 4 == 0 && (reinterpret_cast<uintptr_t>(a.X) & 15u) == 0) ? 1 : 0, part, lse, nullptr};
+              (a.D % 4 == 0 && (reinterpret_cast<uintptr_t>(a.X) & 15u) == 0) ? 1 : 0, part, lse, nullptr, n_dev};
     const size_t sm1 = blk_smem(a.D, 128, false) + 4 * 128 * sizeof(float2);
     const size_t sm3 = blk_smem(a.D, 64, true);
     cudaError_t e = cudaFuncSetAttribute(k_blk_lse<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);

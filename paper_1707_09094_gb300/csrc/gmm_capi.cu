@@ -24,7 +24,7 @@ namespace {
 
 // Device counters of gmm_profile: words 0-10 the EM screening kernel's,
 // words 11-13 the tensor-core k-means pass's (screened, deferred, FP64).
-constexpr int kStatWords = 15;
+constexpr int kStatWords = 14;
 constexpr int kStatKm = 11;
 
 thread_local std::string g_err;
@@ -354,7 +354,7 @@ gmm_status run_em(gmm_model *m, const float *Xd, int64_t N, int32_t em_iter, dou
         return fail(GMM_ERR_STATE, "tensor-core E-step needs the global centre (run learn or recompute_center)");
     // one-pass forms: one partial per CTA; two-phase form: one per sample chunk
     // (and one log-likelihood partial per 128-sample block of the lse pass)
-    const int grid = wide ? gmm::em_wide_chunks(N, G, m->sms)
+    const int grid = wide ? gmm::em_wide_partials(N, G, m->sms)
                           : (tc ? gmm::em_tc_grid(m->sms)
                                 : (two_phase ? gmm::em_blocked_chunks(G, m->sms) : gmm::em_simt_grid(D, G, m->sms)));
     if ((two_phase || wide) && cp) {   // these forms take all of X at once
@@ -362,7 +362,7 @@ gmm_status run_em(gmm_model *m, const float *Xd, int64_t N, int32_t em_iter, dou
         cp = nullptr;
     }
     const int nch = cp ? (int)cp->ready.size() : 1;
-    const int n_llp = two_phase ? (int)((N + 127) / 128) : (wide ? gmm::em_wide_ll_grid(N, m->sms) : grid);
+    const int n_llp = two_phase ? (int)((N + 127) / 128) : (wide ? gmm::em_wide_ll_partials(N, m->sms) : grid);
     CK(grow(m->partial, m->partial_cap, (size_t)nch * grid * G * S));
     if (two_phase) CK(grow(m->lse, m->lse_cap, (size_t)N));
     if (two_phase) CK(grow(m->lsep, m->lsep_cap, (size_t)gmm::em_blocked_gblocks(G) * (size_t)N));
@@ -386,8 +386,7 @@ gmm_status run_em(gmm_model *m, const float *Xd, int64_t N, int32_t em_iter, dou
                                m->llp + (size_t)c * n_llp, m->status, k, m->wait_cycles, m->skip_mma,
                                m->profiling ? m->sstats : nullptr, N};
             if (wide)
-                CK(gmm::launch_em_wide(pa, m->par[(base + k) & 1], gmm::em_wide_ws(m->wide, N, D, G), grid, n_llp,
-                                       m->sms, s));
+                CK(gmm::launch_em_wide(pa, m->par[(base + k) & 1], gmm::em_wide_ws(m->wide, N, D, G), m->sms, s));
             else if (tc) CK(gmm::launch_em_pass_tc(pa, gmm::em_tc_lists(m->tclist, b1 - b0, grid), grid, grid, s));
             else if (two_phase) CK(gmm::launch_em_blocked(pa, m->lse, m->lsep, grid, s));
             else CK(gmm::launch_em_pass_simt(pa, grid, s));

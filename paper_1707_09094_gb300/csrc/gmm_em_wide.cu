@@ -22,16 +22,16 @@
 //     lb_g = P1 + P2 + ctc_g - (K1 |P1| + k2_g) and lists the Gaussians
 //     whose upper bound lies within T = ln(N * 1e9) nats of it, dropping
 //     entries as that bound rises; after the last block the list holds the
-//     Gaussians that can reach a responsibility of 1e-9 / N: at most 64,
-//     else every Gaussian.
+//     Gaussians that can reach a responsibility of 1e-9 / N: at most 64.
+//     A sample with more (a start far from converged, where many broad
+//     Gaussians overlap) goes with the other such samples, gathered in sample
+//     order, to the register-blocked FP32 form (every Gaussian), whose
+//     statistics and log-likelihood partials follow this pass's own.
 //  2. k_wide_exact -- a warp per sample, lanes over dimensions: the exact
 //     FP32 log-density c_g - 1/2 sum_d (x_d s_gd - mu_gd s_gd)^2 of each
 //     candidate, log-sum-exp (Eqs. 16-18), log p(x_i) into the CTA's FP64
 //     log-likelihood, and the responsibilities (Eq. 3) of at least exp(-T)
-//     into the sample's record (at most 64; a sample with more -- only one
-//     the screen left with every Gaussian, whose log-densities take one lane
-//     per Gaussian -- is marked and its pairs are recomputed in step 3 with
-//     the same arithmetic).
+//     into the sample's record (at most 64, one per candidate).
 //  3. k_wide_mstep -- grid (sample chunk) x (block of 64 Gaussians): per
 //     256-sample tile the records that fall in the block, compacted in sample
 //     order; the warp that owns a Gaussian (g mod 8) adds l, l (x - mu_f),
@@ -518,8 +518,7 @@ struct WxArgs {
     EmPassArgs a;
     const uint8_t *cnt;
     const uint16_t *cand;
-    float *lse;        // [N] log p(x_i)
-    uint8_t *rc;       // [N] kept responsibilities in the record (255: more than kWKeep)
+    uint8_t *rc;       // [N] kept responsibilities in the record
     uint16_t *rg;      // [N][kWKeep] their Gaussians
     float *rgam;       // [N][kWKeep] and values
     float screen;
@@ -569,32 +568,6 @@ __device__ __forceinline__ float wide_logit(const Operands &op, int D, int g, co
     return fmaf(-0.5f, r, __ldg(op.c + g));
 }
 
-// Exact FP32 log-density of Gaussian g for a sample staged in shared memory
-// (xs[0..D)), one thread over all D (two FMA chains, dimensions 0, 2, .. and
-// 1, 3, ..): the form for a lane that takes whole Gaussians.
-__device__ __forceinline__ float dense_logit(const Operands &op, int D, int g, const float *xs, bool v4)
-{
-    const float2 *q = op.sm + (size_t)g * D;
-    float r0 = 0.f, r1 = 0.f;
-    if (v4) {   // D even, rows 16-byte aligned: two dimensions per load
-        const float4 *q4 = reinterpret_cast<const float4 *>(q);
-#pragma unroll 4
-        for (int d2 = 0; d2 < D / 2; ++d2) {
-            const float4 u = __ldg(q4 + d2);
-            const float ta = fmaf(xs[2 * d2], u.x, -u.y), tb = fmaf(xs[2 * d2 + 1], u.z, -u.w);
-            r0 = fmaf(ta, ta, r0);
-            r1 = fmaf(tb, tb, r1);
-        }
-    } else {
-        for (int d = 0; d < D; ++d) {
-            const float2 u = __ldg(q + d);
-            const float ta = fmaf(xs[d], u.x, -u.y);
-            r0 = fmaf(ta, ta, r0);
-        }
-    }
-    return fmaf(-0.5f, r0 + r1, __ldg(op.c + g));
-}
-
 // One warp per sample over a contiguous sample range per CTA; the CTA's FP64
 // log-likelihood is summed per warp in sample order, then over the warps.
 __global__ void __launch_bounds__(kWxThreads) k_wide_exact(WxArgs w)
@@ -602,7 +575,6 @@ __global__ void __launch_bounds__(kWxThreads) k_wide_exact(WxArgs w)
     const EmPassArgs &a = w.a;
     if (wide_skip(a.status, a.iter)) return;
     __shared__ double s_ll[kWxThreads / 32];
-    __shared__ float s_x[kWxThreads / 32][128];   // a dense sample's x, per warp
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     constexpr int nw = kWxThreads / 32;
     const int D = a.D, G = a.G;
@@ -610,12 +582,11 @@ __global__ void __launch_bounds__(kWxThreads) k_wide_exact(WxArgs w)
     const float keep = -w.screen;
     const int64_t i0 = a.N * blockIdx.x / gridDim.x, i1 = a.N * (blockIdx.x + 1) / gridDim.x;
     double ll = 0.0;
-    unsigned long long novf = 0;   // samples whose kept pairs exceed the record
     for (int64_t i = i0 + warp; i < i1; i += nw) {
         float x[4];
         wide_x(a.X, i, D, lane, xv4, x);
-        const int n = w.cnt[i];   // <= kWCap, or 255: every Gaussian
-        float lse;
+        const int n = w.cnt[i];   // <= kWCap, or 255: left to the FP32 form
+        float lse = 0.f;
         int m = 0;
         if (n <= kWCap) {
             // candidate k on lane k % 32, slot k / 32
@@ -669,52 +640,12 @@ __global__ void __launch_bounds__(kWxThreads) k_wide_exact(WxArgs w)
                     base += __popc(bal[u]);
                 }
             }
-        } else {
-            // every Gaussian, lanes over Gaussians: online (max, sum of exp) per
-            // lane, merged over the warp; then the kept pairs in Gaussian order
-            float *xs = s_x[warp];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) xs[4 * lane + e] = x[e];
-            __syncwarp();
-            float M = -INFINITY, S = 0.f;
-            for (int g = lane; g < G; g += 32) {
-                const float l = dense_logit(a.op, D, g, xs, sv4);
-                if (l > M) {
-                    S = S * __expf(M - l) + 1.f;
-                    M = l;
-                } else if (l > -INFINITY) {
-                    S += __expf(l - M);
-                }
-            }
-            float Mw = M;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) Mw = fmaxf(Mw, __shfl_xor_sync(0xffffffffu, Mw, o));
-            float Sw = (M == -INFINITY) ? 0.f : S * __expf(M - Mw);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) Sw += __shfl_xor_sync(0xffffffffu, Sw, o);
-            lse = Mw + logf(Sw);
-            for (int g0 = 0; g0 < G; g0 += 32) {
-                const int g = g0 + lane;
-                const float rl = g < G ? dense_logit(a.op, D, g, xs, sv4) - lse : -INFINITY;
-                const bool kp = rl >= keep;
-                const unsigned bal = __ballot_sync(0xffffffffu, kp);
-                const int rank = m + __popc(bal & ((1u << lane) - 1u));
-                if (kp && rank < kWKeep) {
-                    w.rg[i * kWKeep + rank] = (uint16_t)g;
-                    w.rgam[i * kWKeep + rank] = __expf(rl);
-                }
-                m += __popc(bal);
-            }
-            __syncwarp();
         }
         if (lane == 0) {
-            w.rc[i] = (uint8_t)(m > kWKeep ? 255 : m);
-            w.lse[i] = lse;
+            w.rc[i] = (uint8_t)min(m, kWKeep);   // m <= n <= kWKeep; 0 for a sample left to the FP32 form
             ll += (double)lse;
-            novf += m > kWKeep;
         }
     }
-    if (lane == 0 && a.screen_stats && novf) atomicAdd(a.screen_stats + 14, novf);
     if (lane == 0) s_ll[warp] = ll;
     __syncthreads();
     if (tid == 0) {
@@ -732,14 +663,11 @@ struct WmArgs {
     const uint8_t *rc;
     const uint16_t *rg;
     const float *rgam;
-    const float *lse;
     int32_t n_gb, n_chunks;
-    float screen;
-    int32_t s_v4;
 };
 
 struct WmSmem {
-    uint32_t S12, S0, cntg, fl, ent, ovf, scan, total;
+    uint32_t S12, S0, cntg, fl, ent, scan, total;
 };
 
 __host__ __device__ inline WmSmem wm_layout()
@@ -751,8 +679,7 @@ __host__ __device__ inline WmSmem wm_layout()
     L.cntg = o; o += 4u * kWmBG;                // FP32 additions since the last flush
     L.fl = o; o += 4u * kWmBG;                  // rows already flushed once
     L.ent = o; o += 8u * kWmEnt;                // (sample | g_local << 16, responsibility)
-    L.ovf = o; o += 4u * kWmTile;               // samples recomputed over the block
-    L.scan = o; o += 4u * 2u * 32u;
+    L.scan = o; o += 4u * 32u;
     L.total = o;
     return L;
 }
@@ -768,14 +695,10 @@ __global__ void __launch_bounds__(kWmThreads) k_wide_mstep(WmArgs w)
     int *cntg = reinterpret_cast<int *>(wm_raw + Ls.cntg);
     int *fl = reinterpret_cast<int *>(wm_raw + Ls.fl);
     uint2 *ent = reinterpret_cast<uint2 *>(wm_raw + Ls.ent);
-    int *ovf = reinterpret_cast<int *>(wm_raw + Ls.ovf);
     int *scan = reinterpret_cast<int *>(wm_raw + Ls.scan);
-    __shared__ float s_ox[128], s_og[kWmBG];   // a recomputed sample's x and responsibilities
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int D = a.D, G = a.G, S = 1 + 2 * D;
     const int gb = blockIdx.x % w.n_gb, chunk = blockIdx.x / w.n_gb, g0 = gb * kWmBG;
-    const bool sv4 = w.s_v4 != 0;
-    const float keep = -w.screen;
     double *P = a.partial + (size_t)chunk * G * S;
     for (int k = tid; k < kWmBG * 256; k += kWmThreads) S12[k] = 0.f;
     for (int k = tid; k < kWmBG; k += kWmThreads) {
@@ -834,54 +757,40 @@ __global__ void __launch_bounds__(kWmThreads) k_wide_mstep(WmArgs w)
         __syncwarp();
         if (cntg[gl] >= kWmFlush) flush(gl);
     };
-    auto add_pair = [&](int64_t i, int gl, float gam) {
-        float v[4];
-        load_pair(i, gl, v);
-        acc_pair(gl, gam, v);
-    };
     const int64_t ntiles = (a.N + kWmTile - 1) / kWmTile;
     const int64_t tb0 = ntiles * chunk / w.n_chunks, tb1 = ntiles * (chunk + 1) / w.n_chunks;
     __syncthreads();
     for (int64_t t = tb0; t < tb1; ++t) {
         const int64_t i0 = t * kWmTile, i = i0 + tid;
-        int nm = 0, isov = 0;
-        int rcv = 0;
+        int nm = 0, rcv = 0;
         const uint16_t *rgi = w.rg + i * kWKeep;
         if (i < a.N) {
-            rcv = w.rc[i];
-            if (rcv == 255) {
-                isov = 1;
-                rcv = 0;
-            } else {
-                rcv = min(rcv, kWKeep);
-                for (int k8 = 0; k8 < rcv; k8 += 8) {   // eight slots per 16-byte load
-                    const uint4 u = __ldg(reinterpret_cast<const uint4 *>(rgi + k8));
-                    const uint32_t uw[4] = {u.x, u.y, u.z, u.w};
+            rcv = min((int)w.rc[i], kWKeep);
+            for (int k8 = 0; k8 < rcv; k8 += 8) {   // eight slots per 16-byte load
+                const uint4 u = __ldg(reinterpret_cast<const uint4 *>(rgi + k8));
+                const uint32_t uw[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) {
-                        const int g = (int)((uw[k >> 1] >> (16 * (k & 1))) & 0xFFFFu);
-                        nm += (k8 + k < rcv && g < G && (g >> 6) == gb);
-                    }
+                for (int k = 0; k < 8; ++k) {
+                    const int g = (int)((uw[k >> 1] >> (16 * (k & 1))) & 0xFFFFu);
+                    nm += (k8 + k < rcv && g < G && (g >> 6) == gb);
                 }
             }
         }
-        // exclusive prefix sums of (pairs, overflow samples) over the tile, in sample order
-        int pn = nm, po = isov;
+        // exclusive prefix sum of the pairs over the tile, in sample order
+        int pn = nm;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const int a1 = __shfl_up_sync(0xffffffffu, pn, o), a2 = __shfl_up_sync(0xffffffffu, po, o);
-            if (lane >= o) { pn += a1; po += a2; }
+            const int a1 = __shfl_up_sync(0xffffffffu, pn, o);
+            if (lane >= o) pn += a1;
         }
-        if (lane == 31) { scan[warp] = pn; scan[32 + warp] = po; }
+        if (lane == 31) scan[warp] = pn;
         __syncthreads();
-        int bp = 0, bo = 0, tp = 0, to = 0;
+        int bp = 0, tp = 0;
         for (int k = 0; k < kWmThreads / 32; ++k) {
-            if (k < warp) { bp += scan[k]; bo += scan[32 + k]; }
+            if (k < warp) bp += scan[k];
             tp += scan[k];
-            to += scan[32 + k];
         }
         const int pos0 = bp + pn - nm;
-        if (isov) ovf[bo + po - 1] = tid;
         // ---- the pairs in windows of kWmEnt list entries; owner warps take the
         // pairs of Gaussians g_local = warp (mod 8), in list order
         for (int r0 = 0; r0 < tp; r0 += kWmEnt) {
@@ -927,46 +836,107 @@ __global__ void __launch_bounds__(kWmThreads) k_wide_mstep(WmArgs w)
                         }
                 }
             }
-            __syncthreads();   // the window is rewritten
+            __syncthreads();   // the window (and scan) are rewritten
         }
-        // ---- samples with more than kWKeep kept pairs (only samples the screen
-        // left dense): every Gaussian of the block recomputed with the exact
-        // kernel's dense arithmetic, then added by the owner warps
-        for (int e = 0; e < to; ++e) {
-            const int64_t io = i0 + ovf[e];
-            for (int d = tid; d < D; d += kWmThreads) s_ox[d] = __ldg(a.X + io * D + d);
-            __syncthreads();
-            if (tid < kWmBG) {
-                float gm = 0.f;
-                if (g0 + tid < G) {
-                    const float rl = dense_logit(a.op, D, g0 + tid, s_ox, sv4) - __ldg(w.lse + io);
-                    gm = rl >= keep ? __expf(rl) : 0.f;
-                }
-                s_og[tid] = gm;
-            }
-            __syncthreads();
-            for (int gl = warp; gl < kWmBG; gl += kWmThreads / 32)
-                if (s_og[gl] > 0.f) add_pair(io, gl, s_og[gl]);   // uniform across the warp
-            __syncthreads();   // s_ox, s_og are rewritten
-        }
-        __syncthreads();   // ent, ovf and scan are rewritten by the next tile
+        if (tp == 0) __syncthreads();   // scan is rewritten by the next tile
     }
     // final flush of this warp's rows (rows never touched are written as zeros)
     for (int gl = warp; gl < kWmBG; gl += kWmThreads / 32) flush(gl);
+}
+
+// ------------------------------------------------------------------------
+// Samples with more candidates than a list holds go to the register-blocked
+// FP32 form (every Gaussian, the same log-densities to FP32 rounding): their
+// indices are compacted in sample order and their rows gathered into Xd.
+// Per 1024 samples: the count, then the offsets, then the rows.
+// ------------------------------------------------------------------------
+constexpr int kWdBlock = 1024;
+
+__global__ void __launch_bounds__(kWdBlock) k_wide_dcount(const uint8_t *__restrict__ cnt, int64_t N,
+                                                          int32_t *__restrict__ bcnt)
+{
+    const int64_t i = (int64_t)blockIdx.x * kWdBlock + threadIdx.x;
+    const int f = __syncthreads_count(i < N && cnt[i] == 255);
+    if (threadIdx.x == 0) bcnt[blockIdx.x] = f;
+}
+
+// Exclusive prefix sum of the nblk counts in place (one CTA), the total to *n_dense.
+__global__ void __launch_bounds__(1024) k_wide_dscan(int32_t *__restrict__ bcnt, int32_t nblk, int64_t *__restrict__ n_dense)
+{
+    __shared__ int32_t s_w[32];
+    __shared__ int64_t s_base;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_base = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < nblk; b0 += 1024) {
+        const int b = b0 + tid;
+        const int v = b < nblk ? bcnt[b] : 0;
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_w[warp] = x;
+        __syncthreads();
+        int wb = 0, tot = 0;
+        for (int k = 0; k < 32; ++k) {
+            if (k < warp) wb += s_w[k];
+            tot += s_w[k];
+        }
+        const int64_t base = s_base;
+        if (b < nblk) bcnt[b] = (int32_t)(base + wb + x - v);
+        __syncthreads();
+        if (tid == 0) s_base = base + tot;
+        __syncthreads();
+    }
+    if (tid == 0) *n_dense = s_base;
+}
+
+__global__ void __launch_bounds__(kWdBlock) k_wide_dgather(const uint8_t *__restrict__ cnt, const float *__restrict__ X,
+                                                           int64_t N, int32_t D, const int32_t *__restrict__ boff,
+                                                           float *__restrict__ Xd)
+{
+    __shared__ int32_t s_w[32];
+    __shared__ int64_t s_idx[kWdBlock];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t i = (int64_t)blockIdx.x * kWdBlock + tid;
+    const int f = (i < N && cnt[i] == 255) ? 1 : 0;
+    int x = f;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[warp] = x;
+    __syncthreads();
+    int wb = 0, tot = 0;
+    for (int k = 0; k < 32; ++k) {
+        if (k < warp) wb += s_w[k];
+        tot += s_w[k];
+    }
+    if (f) s_idx[wb + x - 1] = i;
+    __syncthreads();
+    const int64_t o0 = boff[blockIdx.x];
+    for (int k = warp; k < tot; k += kWdBlock / 32) {   // a warp per row
+        const int64_t src = s_idx[k];
+        for (int d = lane; d < D; d += 32) Xd[(o0 + k) * D + d] = __ldg(X + src * D + d);
+    }
 }
 
 }  // namespace
 
 bool em_wide_supported(int32_t D, int32_t G)
 {
-    if (D < 1 || D > 128 || G < 1 || G > kWMaxG) return false;
+    if (D < 1 || D > 128 || G < 1 || G > kWMaxG || !em_blocked_supported(D, G)) return false;
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     return w_layout((D + 63) / 64).total + 1024u + 1024u <= (uint32_t)optin;
 }
 
-int em_wide_chunks(int64_t N, int32_t G, int sms)
+namespace {
+int wide_mchunks(int64_t N, int32_t G, int sms)
 {
     const int n_gb = (G + kWmBG - 1) / kWmBG;
     int64_t c = (8LL * sms + n_gb - 1) / n_gb;                 // about four waves of two CTAs per SM
@@ -975,47 +945,57 @@ int em_wide_chunks(int64_t N, int32_t G, int sms)
     return (int)(c < 1 ? 1 : c);
 }
 
-int em_wide_ll_grid(int64_t N, int sms)
+int wide_xgrid(int64_t N, int sms)
 {
     const int64_t g = 2LL * sms, w = (N + 15) / 16;            // at least 16 samples per CTA
     return (int)(g < w ? g : (w < 1 ? 1 : w));
 }
 
-namespace {
 size_t wal256(size_t n) { return (n + 255u) & ~(size_t)255u; }
-}
+}  // namespace
+
+int em_wide_partials(int64_t N, int32_t G, int sms) { return wide_mchunks(N, G, sms) + em_blocked_chunks(G, sms); }
+
+int em_wide_ll_partials(int64_t N, int sms) { return wide_xgrid(N, sms) + (int)((N + 127) / 128); }
 
 size_t em_wide_ws_bytes(int64_t N, int32_t D, int32_t G)
 {
     const size_t n = (size_t)N, nkb = (size_t)((D + 63) / 64), ngp = (size_t)((G + kWGB - 1) / kWGB) * kWGB;
+    const size_t nblk = (n + kWdBlock - 1) / kWdBlock;
     return wal256(ngp / kWGB * 4 * nkb * kWPiece) + wal256(8u * ngp) + wal256(n) + wal256(2u * kWCap * n) +
-           wal256(4u * n) + wal256(n) + wal256(2u * kWKeep * n) + wal256(4u * kWKeep * n) + 256u;
+           wal256(n) + wal256(2u * kWKeep * n) + wal256(4u * kWKeep * n) + wal256(4u * nblk) + wal256(8u) +
+           wal256(4u * n * (size_t)D) + wal256(4u * n) + wal256(8u * n * (size_t)em_blocked_gblocks(G)) + 256u;
 }
 
 WideWs em_wide_ws(void *base, int64_t N, int32_t D, int32_t G)
 {
     const size_t n = (size_t)N, nkb = (size_t)((D + 63) / 64), ngp = (size_t)((G + kWGB - 1) / kWGB) * kWGB;
+    const size_t nblk = (n + kWdBlock - 1) / kWdBlock;
     unsigned char *p = static_cast<unsigned char *>(base);
     WideWs w;
     w.img = p;                                    p += wal256(ngp / kWGB * 4 * nkb * kWPiece);
     w.bnd = reinterpret_cast<float2 *>(p);        p += wal256(8u * ngp);
     w.cnt = p;                                    p += wal256(n);
     w.cand = reinterpret_cast<uint16_t *>(p);     p += wal256(2u * kWCap * n);
-    w.lse = reinterpret_cast<float *>(p);         p += wal256(4u * n);
     w.rc = p;                                     p += wal256(n);
     w.rg = reinterpret_cast<uint16_t *>(p);       p += wal256(2u * kWKeep * n);
-    w.rgam = reinterpret_cast<float *>(p);
+    w.rgam = reinterpret_cast<float *>(p);        p += wal256(4u * kWKeep * n);
+    w.bcnt = reinterpret_cast<int32_t *>(p);      p += wal256(4u * nblk);
+    w.n_dense = reinterpret_cast<int64_t *>(p);   p += wal256(8u);
+    w.Xd = reinterpret_cast<float *>(p);          p += wal256(4u * n * (size_t)D);
+    w.lse_d = reinterpret_cast<float *>(p);       p += wal256(4u * n);
+    w.part_d = reinterpret_cast<float2 *>(p);
     return w;
 }
 
-cudaError_t launch_em_wide(const EmPassArgs &a, const double *par, const WideWs &ws, int32_t n_chunks, int32_t ll_grid,
-                           int sms, cudaStream_t s)
+cudaError_t launch_em_wide(const EmPassArgs &a, const double *par, const WideWs &ws, int sms, cudaStream_t s)
 {
     const int nkb = (a.D + 63) / 64, nb = (a.G + kWGB - 1) / kWGB;
     const float scr = (float)std::log((double)(a.N_total > a.N ? a.N_total : a.N) * 1e9);
     const bool x16 = (reinterpret_cast<uintptr_t>(a.X) & 15u) == 0;
     const int xv4 = (x16 && a.D % 4 == 0) ? 1 : 0;
     const int sv4 = ((reinterpret_cast<uintptr_t>(a.op.sm) & 15u) == 0 && a.D % 2 == 0) ? 1 : 0;
+    const int mch = wide_mchunks(a.N, a.G, sms), xg = wide_xgrid(a.N, sms);
     k_wide_prep<<<nb * kWGB, 128, 0, s>>>(a.D, a.G, nkb, par, a.center, ws.img, ws.bnd);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -1026,18 +1006,30 @@ cudaError_t launch_em_wide(const EmPassArgs &a, const double *par, const WideWs 
     const int64_t ntiles = (a.N + kWTM - 1) / kWTM;
     const int g1 = (int)(ntiles < sms ? ntiles : sms);
     k_wide_screen<<<g1, kWThreads, sm1, s>>>(w);
+    // the samples left to the FP32 form, in sample order
+    const int nblk = (int)((a.N + kWdBlock - 1) / kWdBlock);
+    k_wide_dcount<<<nblk, kWdBlock, 0, s>>>(ws.cnt, a.N, ws.bcnt);
+    k_wide_dscan<<<1, 1024, 0, s>>>(ws.bcnt, nblk, ws.n_dense);
+    k_wide_dgather<<<nblk, kWdBlock, 0, s>>>(ws.cnt, a.X, a.N, a.D, ws.bcnt, ws.Xd);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    WxArgs x{a, ws.cnt, ws.cand, ws.lse, ws.rc, ws.rg, ws.rgam, scr, xv4, sv4};
-    k_wide_exact<<<ll_grid, kWxThreads, 0, s>>>(x);
+    WxArgs x{a, ws.cnt, ws.cand, ws.rc, ws.rg, ws.rgam, scr, xv4, sv4};
+    k_wide_exact<<<xg, kWxThreads, 0, s>>>(x);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int n_gb = (a.G + kWmBG - 1) / kWmBG;
-    WmArgs m{a, ws.rc, ws.rg, ws.rgam, ws.lse, n_gb, n_chunks, scr, sv4};
+    WmArgs m{a, ws.rc, ws.rg, ws.rgam, n_gb, mch};
     const size_t sm3 = wm_layout().total;
     if ((e = cudaFuncSetAttribute(k_wide_mstep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3)) != cudaSuccess)
         return e;
-    k_wide_mstep<<<n_chunks * n_gb, kWmThreads, sm3, s>>>(m);
-    count_launches(4);
-    return cudaGetLastError();
+    k_wide_mstep<<<mch * n_gb, kWmThreads, sm3, s>>>(m);
+    count_launches(7);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // the FP32 form over the gathered samples: statistics after the pass's
+    // own partials, log-likelihood partials after the exact kernel's
+    EmPassArgs d = a;
+    d.X = ws.Xd;
+    d.partial = a.partial + (size_t)mch * a.G * (1 + 2 * a.D);
+    d.ll_partial = a.ll_partial + xg;
+    return launch_em_blocked(d, ws.lse_d, ws.part_d, em_blocked_chunks(a.G, sms), s, ws.n_dense);
 }
 
 }  // namespace gmm

@@ -101,7 +101,10 @@ cudaError_t launch_em_finalize(const EmFinalizeArgs &a, cudaStream_t s);
 bool em_blocked_supported(int32_t D, int32_t G);
 int em_blocked_gblocks(int32_t G);
 int em_blocked_chunks(int32_t G, int sms);
-cudaError_t launch_em_blocked(const EmPassArgs &a, float *lse, float2 *part, int32_t n_chunks, cudaStream_t s);
+// n_dev (optional, device): the samples actually present, at most a.N (a.N is
+// the stride of part and lse and sizes the launch)
+cudaError_t launch_em_blocked(const EmPassArgs &a, float *lse, float2 *part, int32_t n_chunks, cudaStream_t s,
+                              const int64_t *n_dev = nullptr);
 // k-means map step for shapes beyond the tiled form: assign [N] (exact
 // nearest mean) and the statistics into partial [n_chunks][G][1 + 2D];
 // part [gblocks][N], arg [gblocks][N], nmax [1], snorm [N] and defer [N + 1]
@@ -245,22 +248,26 @@ cudaError_t launch_em_pass_tc(const EmPassArgs &a, const TcLists &L, int32_t gri
 struct WideWs {              // work space, grown once per model
     unsigned char *img;      // split BF16 operand pieces of the screen
     float2 *bnd;             // screening constants per Gaussian
-    uint8_t *cnt;            // [N] candidates per sample (255: every Gaussian)
-    uint16_t *cand;          // [N][16] candidate Gaussians
-    float *lse;              // [N] log p(x_i)
-    uint8_t *rc;             // [N] kept responsibilities in the record (255: recompute)
-    uint16_t *rg;            // [N][8] their Gaussians
-    float *rgam;             // [N][8] and values
+    uint8_t *cnt;            // [N] candidates per sample (255: more than a list holds)
+    uint16_t *cand;          // [N][64] candidate Gaussians
+    uint8_t *rc;             // [N] kept responsibilities in the record
+    uint16_t *rg;            // [N][64] their Gaussians
+    float *rgam;             // [N][64] and values
+    int32_t *bcnt;           // per 1024 samples: samples left to the FP32 form, then their offsets
+    int64_t *n_dense;        // [1] samples left to the FP32 form
+    float *Xd;               // [N][D] their rows, gathered in sample order
+    float *lse_d;            // [N] their log p(x_i)
+    float2 *part_d;          // [ceil(G / 64)][N] their partial log-sum-exps
 };
 bool em_wide_supported(int32_t D, int32_t G);
-int em_wide_chunks(int64_t N, int32_t G, int sms);
-int em_wide_ll_grid(int64_t N, int sms);
+// statistics partials [em_wide_partials][G][1 + 2D] and log-likelihood
+// partials [em_wide_ll_partials] of one pass
+int em_wide_partials(int64_t N, int32_t G, int sms);
+int em_wide_ll_partials(int64_t N, int sms);
 size_t em_wide_ws_bytes(int64_t N, int32_t D, int32_t G);
 WideWs em_wide_ws(void *base, int64_t N, int32_t D, int32_t G);
 // One EM iteration's pass from par (the iteration's parameters; op holds
-// their FP32 operands): statistics into a.partial [n_chunks][G][1 + 2D],
-// log-likelihood partials into a.ll_partial [ll_grid].
-cudaError_t launch_em_wide(const EmPassArgs &a, const double *par, const WideWs &ws, int32_t n_chunks, int32_t ll_grid,
-                           int sms, cudaStream_t s);
+// their FP32 operands) into a.partial and a.ll_partial.
+cudaError_t launch_em_wide(const EmPassArgs &a, const double *par, const WideWs &ws, int sms, cudaStream_t s);
 
 }  // namespace gmm

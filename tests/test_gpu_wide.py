@@ -69,16 +69,15 @@ def test_wide_em_matches_oracle(shape):
 
 
 @pytest.mark.parametrize("case", ["spread48", "all40", "all100"])
-def test_wide_dense_and_recompute_paths(case):
+def test_wide_candidate_lists_and_fp32_handoff(case):
     """Heavily overlapping Gaussians.  spread48: 48 of 128 Gaussians, 12 in each
     quarter of the block's columns, are candidates of every sample (the
-    screen's lists hold 16 per quarter; the exact kernel takes two per lane),
-    the other 80 lie far away; all40: the 40 Gaussians of a model, all in the
-    first quarter of the block's columns, are candidates of every sample
-    (the screen keeps one list per sample, up to 64); all100: 100 candidates,
-    more than a list holds, so the exact kernel takes every Gaussian, and
-    100 kept responsibilities do not fit the sample's record (the M-step
-    recomputes the sample over each block)."""
+    exact kernel takes two per lane), the other 80 lie far away; all40: the
+    40 Gaussians of a model, all in the first quarter of the block's columns,
+    are candidates of every sample (one list per sample, up to 64); all100:
+    100 candidates, more than a list holds, so every sample goes to the
+    register-blocked FP32 form, whose statistics and log-likelihood join the
+    pass's."""
     rng = np.random.default_rng(3)
     N, D = 4000, 8
     X = rng.normal(0, 1, (N, D)).astype(np.float32)
@@ -97,12 +96,32 @@ def test_wide_dense_and_recompute_paths(case):
     g.profile(True)
     g.em_iterate(dev(X), 2, prec="bf16", recompute_center=True)
     n, kept, nd = g.screen_stats()
-    dense, recomputed = {"spread48": (False, False), "all40": (False, False), "all100": (True, True)}[case]
-    assert n == 2 * N and nd == (2 * N if dense else 0) and g.recomputed() == (2 * N if recomputed else 0)
-    if not dense:
+    assert n == 2 * N and nd == (2 * N if case == "all100" else 0)
+    if case != "all100":
         assert kept == 2 * N * (48 if case == "spread48" else 40)
     assert_params(g.get_params(), (M, V, H), X)
     np.testing.assert_allclose(g.ll_history(), ll, rtol=1e-6)
+
+
+def test_wide_some_samples_to_fp32_form():
+    """A mixture where part of the samples have more than 64 candidates: those
+    go to the FP32 form, the rest stay on the tensor-core path, and the
+    iteration matches the oracle's."""
+    rng = np.random.default_rng(5)
+    N, D, G = 6000, 8, 160
+    X = rng.normal(0, 1, (N, D)).astype(np.float32)
+    X[: N // 3] += 40.0   # a third of the samples near the 100 overlapping means, the rest near 60 others
+    means = np.concatenate([40.0 + rng.normal(0, 0.05, (100, D)), rng.normal(0, 0.5, (60, D))])
+    start = (means, np.ones((G, D)), np.full(G, 1.0 / G))
+    M, V, H, ll = oracle.em_iterate(X, *start, 2, 1e-10)
+    g2 = GMM().set_params(*start)
+    g2.debug_set(GMM_DEBUG_TC_FORM, 1)
+    g2.profile(True)
+    g2.em_iterate(dev(X), 2, prec="bf16", recompute_center=True)
+    n, kept, nd = g2.screen_stats()
+    assert 0 < nd < n
+    assert_params(g2.get_params(), (M, V, H), X)
+    np.testing.assert_allclose(g2.ll_history(), ll, rtol=1e-6)
 
 
 def test_wide_matches_one_tile_form():
