@@ -33,8 +33,8 @@
 //     log-likelihood, and the responsibilities (Eq. 3) of at least exp(-T)
 //     into the sample's record (at most 64, one per candidate).
 //  3. k_wide_mstep -- grid (sample chunk) x (block of 64 Gaussians): per
-//     256-sample tile the records that fall in the block, compacted in sample
-//     order; the warp that owns a Gaussian (g mod 8) adds l, l (x - mu_f),
+//     512-sample tile the records that fall in the block, compacted in sample
+//     order; the warp that owns a Gaussian (g mod 16) adds l, l (x - mu_f),
 //     l (x - mu_f)^2 (Eqs. 9-11 about the FP32 mean mu_f) to the block's FP32
 //     sums in shared memory, which move to the chunk's FP64 partial after at
 //     most 128 additions.
@@ -73,8 +73,8 @@ constexpr int kWCap = 64;               // candidates per sample before the dens
 constexpr int kWKeep = 64;              // responsibilities per sample record
 constexpr float kWK1 = 4.8828125e-4f;   // 2^-11
 constexpr int kWxThreads = 512;         // exact kernel: 16 warps
-constexpr int kWmThreads = 256;         // M-step kernel: 8 warps
-constexpr int kWmTile = 256;            // samples per M-step tile
+constexpr int kWmThreads = 512;         // M-step kernel: 16 warps
+constexpr int kWmTile = 512;            // samples per M-step tile (one per thread)
 constexpr int kWmBG = 64;               // Gaussians per M-step block
 constexpr int kWmFlush = 128;           // FP32 additions per sum between FP64 flushes
 constexpr int kWmEnt = 2048;            // list entries per window of an M-step tile
@@ -667,7 +667,7 @@ struct WmArgs {
 };
 
 struct WmSmem {
-    uint32_t S12, S0, cntg, fl, ent, scan, total;
+    uint32_t S12, ent, scan, total;
 };
 
 __host__ __device__ inline WmSmem wm_layout()
@@ -675,55 +675,51 @@ __host__ __device__ inline WmSmem wm_layout()
     WmSmem L;
     uint32_t o = 0;
     L.S12 = o; o += 4u * kWmBG * 256u;          // [64][S1: 128 | S2: 128]
-    L.S0 = o; o += 4u * kWmBG;
-    L.cntg = o; o += 4u * kWmBG;                // FP32 additions since the last flush
-    L.fl = o; o += 4u * kWmBG;                  // rows already flushed once
     L.ent = o; o += 8u * kWmEnt;                // (sample | g_local << 16, responsibility)
     L.scan = o; o += 4u * 32u;
     L.total = o;
     return L;
 }
 
-__global__ void __launch_bounds__(kWmThreads) k_wide_mstep(WmArgs w)
+__global__ void __launch_bounds__(kWmThreads, 2) k_wide_mstep(WmArgs w)
 {
     extern __shared__ __align__(16) unsigned char wm_raw[];
     const EmPassArgs &a = w.a;
     if (wide_skip(a.status, a.iter)) return;
     const WmSmem Ls = wm_layout();
     float *S12 = reinterpret_cast<float *>(wm_raw + Ls.S12);
-    float *S0 = reinterpret_cast<float *>(wm_raw + Ls.S0);
-    int *cntg = reinterpret_cast<int *>(wm_raw + Ls.cntg);
-    int *fl = reinterpret_cast<int *>(wm_raw + Ls.fl);
     uint2 *ent = reinterpret_cast<uint2 *>(wm_raw + Ls.ent);
     int *scan = reinterpret_cast<int *>(wm_raw + Ls.scan);
+    constexpr int nw = kWmThreads / 32;          // warp w owns the Gaussians g_local = w + nw j
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int D = a.D, G = a.G, S = 1 + 2 * D;
     const int gb = blockIdx.x % w.n_gb, chunk = blockIdx.x / w.n_gb, g0 = gb * kWmBG;
     double *P = a.partial + (size_t)chunk * G * S;
     for (int k = tid; k < kWmBG * 256; k += kWmThreads) S12[k] = 0.f;
-    for (int k = tid; k < kWmBG; k += kWmThreads) {
-        S0[k] = 0.f;
-        cntg[k] = 0;
-        fl[k] = 0;
-    }
-    // FP32 sums of row gl (owned by this warp) -> the chunk's FP64 partial
+    // lane j < kWmBG / nw keeps, for the warp's Gaussian g_local = warp + nw j:
+    // the sum of l, the FP32 additions since the last flush, whether flushed once
+    float s0r = 0.f;
+    int cnr = 0, flr = 0;
+    // FP32 sums of this warp's Gaussian gl -> the chunk's FP64 partial
     auto flush = [&](int gl) {
-        const int g = g0 + gl;
-        if (g >= G) return;
-        double *row = P + (size_t)g * S;
-        const bool add = fl[gl] != 0;
-        float *s1 = S12 + gl * 256, *s2 = s1 + 128;
-        for (int d = lane; d < D; d += 32) {
-            row[1 + d] = add ? row[1 + d] + (double)s1[d] : (double)s1[d];
-            row[1 + D + d] = add ? row[1 + D + d] + (double)s2[d] : (double)s2[d];
-            s1[d] = 0.f;
-            s2[d] = 0.f;
+        const int g = g0 + gl, j = gl / nw;
+        const float s0 = __shfl_sync(0xffffffffu, s0r, j);
+        const bool add = __shfl_sync(0xffffffffu, flr, j) != 0;
+        if (g < G) {
+            double *row = P + (size_t)g * S;
+            float *s1 = S12 + gl * 256, *s2 = s1 + 128;
+            for (int d = lane; d < D; d += 32) {
+                row[1 + d] = add ? row[1 + d] + (double)s1[d] : (double)s1[d];
+                row[1 + D + d] = add ? row[1 + D + d] + (double)s2[d] : (double)s2[d];
+                s1[d] = 0.f;
+                s2[d] = 0.f;
+            }
+            if (lane == 0) row[0] = add ? row[0] + (double)s0 : (double)s0;
         }
-        if (lane == 0) {
-            row[0] = add ? row[0] + (double)S0[gl] : (double)S0[gl];
-            S0[gl] = 0.f;
-            cntg[gl] = 0;
-            fl[gl] = 1;
+        if (lane == j) {
+            s0r = 0.f;
+            cnr = 0;
+            flr = 1;
         }
         __syncwarp();
     };
@@ -749,13 +745,12 @@ __global__ void __launch_bounds__(kWmThreads) k_wide_mstep(WmArgs w)
                 s2[d] = fmaf(gv, v[u], s2[d]);
             }
         }
-        __syncwarp();
-        if (lane == 0) {
-            S0[gl] += gam;
-            ++cntg[gl];
+        const int j = gl / nw;
+        if (lane == j) {
+            s0r += gam;
+            ++cnr;
         }
-        __syncwarp();
-        if (cntg[gl] >= kWmFlush) flush(gl);
+        if (__shfl_sync(0xffffffffu, cnr, j) >= kWmFlush) flush(gl);
     };
     const int64_t ntiles = (a.N + kWmTile - 1) / kWmTile;
     const int64_t tb0 = ntiles * chunk / w.n_chunks, tb1 = ntiles * (chunk + 1) / w.n_chunks;
@@ -786,13 +781,14 @@ __global__ void __launch_bounds__(kWmThreads) k_wide_mstep(WmArgs w)
         if (lane == 31) scan[warp] = pn;
         __syncthreads();
         int bp = 0, tp = 0;
-        for (int k = 0; k < kWmThreads / 32; ++k) {
+#pragma unroll
+        for (int k = 0; k < nw; ++k) {
             if (k < warp) bp += scan[k];
             tp += scan[k];
         }
         const int pos0 = bp + pn - nm;
         // ---- the pairs in windows of kWmEnt list entries; owner warps take the
-        // pairs of Gaussians g_local = warp (mod 8), in list order
+        // pairs of Gaussians g_local = warp (mod 16), in list order
         for (int r0 = 0; r0 < tp; r0 += kWmEnt) {
             if (nm > 0 && pos0 < r0 + kWmEnt && pos0 + nm > r0) {
                 int p = pos0;
@@ -809,7 +805,7 @@ __global__ void __launch_bounds__(kWmThreads) k_wide_mstep(WmArgs w)
             __syncthreads();
             const int ne = min(kWmEnt, tp - r0);
             for (int e0 = 0; e0 < ne; e0 += 32) {
-                const bool own = e0 + lane < ne && (int)((ent[e0 + lane].x >> 16) & 7u) == warp;
+                const bool own = e0 + lane < ne && (int)((ent[e0 + lane].x >> 16) % nw) == warp;
                 unsigned mask = __ballot_sync(0xffffffffu, own);
                 while (mask) {   // up to four of this warp's pairs at a time
                     int idx[4];
@@ -841,7 +837,7 @@ __global__ void __launch_bounds__(kWmThreads) k_wide_mstep(WmArgs w)
         if (tp == 0) __syncthreads();   // scan is rewritten by the next tile
     }
     // final flush of this warp's rows (rows never touched are written as zeros)
-    for (int gl = warp; gl < kWmBG; gl += kWmThreads / 32) flush(gl);
+    for (int gl = warp; gl < kWmBG; gl += nw) flush(gl);
 }
 
 // ------------------------------------------------------------------------
