@@ -298,24 +298,32 @@ __global__ void __launch_bounds__(kWThreads, 1) k_wide_screen(WideArgs w)
             const uint32_t aS = smem_u32(sA), rS = smem_u32(sR);
             uint32_t q = 0, pc = 0;
             bool ok = true;
+            unsigned long long w_a = 0, w_b = 0;   // cycles waiting for A / a TMEM buffer, for B pieces (profiling)
+            long long c0 = clock64();
             for (int t = 0; t < T && ok; ++t) {
+                c0 = clock64();
                 if (!mbar_wait(b_afull, (uint32_t)(t & 1), abort_flag, budget)) break;
+                w_a += (unsigned long long)(clock64() - c0);
                 tc_fence_after();
                 if (a.skip_mma) break;   // test hook: the epilogue's wait must run out
                 for (int j = 0; j < nb && ok; ++j, ++q) {
                     const uint32_t buf = q & 1u;
+                    c0 = clock64();
                     if (q >= 2 && !mbar_wait(b_tfree + buf, ((q >> 1) - 1u) & 1u, abort_flag, budget)) {
                         ok = false;
                         break;
                     }
+                    w_a += (unsigned long long)(clock64() - c0);
                     tc_fence_after();
                     const uint32_t d1 = tmem + buf * 256u, d2 = d1 + 128u;
                     for (int p = 0; p < npc; ++p, ++pc) {
                         const uint32_t slot = pc % kWStages;
+                        c0 = clock64();
                         if (!mbar_wait(b_bfull + slot, (pc / kWStages) & 1u, abort_flag, budget)) {
                             ok = false;
                             break;
                         }
+                        w_b += (unsigned long long)(clock64() - c0);
                         tc_fence_after();
                         const int part = p / nkb, k = p - part * nkb;
                         const uint32_t bs = rS + slot * kWPiece;
@@ -333,6 +341,10 @@ __global__ void __launch_bounds__(kWThreads, 1) k_wide_screen(WideArgs w)
                     }
                     if (ok) tc_commit(b_tfull + buf);
                 }
+            }
+            if (a.screen_stats) {
+                atomicAdd(a.screen_stats + 9, w_a);
+                atomicAdd(a.screen_stats + 10, w_b);
             }
             // drain: every MMA issued above completes before TMEM is freed
             // (this wait ignores the abort flag; it is still bounded)
@@ -378,6 +390,13 @@ __global__ void __launch_bounds__(kWThreads, 1) k_wide_screen(WideArgs w)
         const uint32_t tl = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(32 * qq);
         uint32_t *sl = lst + s * kWCap;           // the sample's list: g | (bf16 upper bound rounded up) << 16
         unsigned long long st_n = 0, st_c = 0, st_d = 0;
+        unsigned long long tp[6] = {0, 0, 0, 0, 0, 0};   // phase cycles of thread 0 (profiling)
+        long long tmark = clock64();
+        auto phase = [&](int k) {
+            const long long now = clock64();
+            tp[k] += (unsigned long long)(now - tmark);
+            tmark = now;
+        };
         // the sample's owner thread keeps the entries whose bound reaches thr
         auto prune = [&](int n, float thr) -> int {
             int k = 0;
@@ -395,16 +414,21 @@ __global__ void __launch_bounds__(kWThreads, 1) k_wide_screen(WideArgs w)
             bool lost = false;        // owner: entries were lost to a full list
             for (int j = 0; j < nb; ++j, ++q) {
                 const uint32_t buf = q & 1u;
-                // the next job's constants (block (j + 1) mod nb) into the other buffer
-                if (tid < kWGB) sbnd[(buf ^ 1u) * kWGB + tid] = __ldg(w.bnd + (j + 1 < nb ? j + 1 : 0) * kWGB + tid);
+                // the next job's constants (block (j + 1) mod nb), stored into the
+                // other buffer once the load has landed (after this job's bounds)
+                float2 nbnd = make_float2(0.f, 0.f);
+                if (tid < kWGB) nbnd = __ldg(w.bnd + (j + 1 < nb ? j + 1 : 0) * kWGB + tid);
+                phase(4);
                 mbar_wait(b_tfull + buf, (q >> 1) & 1u, abort_flag, budget);
                 tc_fence_after();
+                phase(0);
                 if (j == nb - 1 && t + 1 < T) {
                     // every MMA of this tile is complete: A takes the next tile
                     build_a(t0 + t + 1);
                     fence_proxy_async();
                     wepi_sync();
                     if (tid == 0) mbar_arrive(b_afull);
+                    phase(1);
                 }
                 const uint32_t tb = tl + buf * 256u;
                 const float2 *cb = sbnd + buf * kWGB + 32 * qq;
@@ -426,6 +450,8 @@ __global__ void __launch_bounds__(kWThreads, 1) k_wide_screen(WideArgs w)
                     }
                 }
                 tc_fence_before();
+                phase(2);
+                if (tid < kWGB) sbnd[(buf ^ 1u) * kWGB + tid] = nbnd;
                 xlo[buf * kWEpi + tid] = lmax;
                 wepi_sync();
                 if (tid == 0) mbar_arrive(b_tfree + buf);
@@ -438,6 +464,7 @@ __global__ void __launch_bounds__(kWThreads, 1) k_wide_screen(WideArgs w)
                     lcnt[s] = prune(min(n0, kWCap), thr);
                 }
                 wepi_sync();
+                phase(3);
                 const int g0 = j * kWGB + 32 * qq;
 #pragma unroll
                 for (int e = 0; e < 32; ++e) {
@@ -454,6 +481,7 @@ __global__ void __launch_bounds__(kWThreads, 1) k_wide_screen(WideArgs w)
             }
             // ---- the owner prunes the list at the final bound, sorts it by Gaussian
             // and writes the sample's record
+            phase(4);
             wepi_sync();
             if (qq == 0) {
                 const int n0 = lcnt[s];
@@ -474,8 +502,13 @@ __global__ void __launch_bounds__(kWThreads, 1) k_wide_screen(WideArgs w)
                             }
                             sl[k + 1] = v;
                         }
-                        uint16_t *dst = w.cand + i * kWCap;
-                        for (int e = 0; e < n; ++e) dst[e] = (uint16_t)(sl[e] & 0xFFFFu);
+                        uint2 *dst = reinterpret_cast<uint2 *>(w.cand + i * kWCap);   // four per 8-byte store
+                        for (int e = 0; e < n; e += 4) {
+                            uint32_t v[4];
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) v[k] = e + k < n ? (sl[e + k] & 0xFFFFu) : 0u;
+                            dst[e >> 2] = make_uint2(v[0] | (v[1] << 16), v[2] | (v[3] << 16));
+                        }
                         w.cnt[i] = (uint8_t)n;
                     }
                     ++st_n;
@@ -484,6 +517,7 @@ __global__ void __launch_bounds__(kWThreads, 1) k_wide_screen(WideArgs w)
                 lcnt[s] = 0;
             }
             wepi_sync();   // the lists are rewritten by the next tile
+            phase(5);
         }
         tc_fence_before();
         if (a.screen_stats) {
@@ -498,6 +532,8 @@ __global__ void __launch_bounds__(kWThreads, 1) k_wide_screen(WideArgs w)
                 atomicAdd(a.screen_stats + 1, st_c);
                 atomicAdd(a.screen_stats + 2, st_d);
             }
+            if (tid == 0)
+                for (int k = 0; k < 6; ++k) atomicAdd(a.screen_stats + 3 + k, tp[k]);
         }
     }
     __syncthreads();
