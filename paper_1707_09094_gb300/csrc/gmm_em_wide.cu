@@ -32,9 +32,9 @@
 //     candidate, log-sum-exp (Eqs. 16-18), log p(x_i) into the CTA's FP64
 //     log-likelihood, and the responsibilities (Eq. 3) of at least exp(-T)
 //     into the sample's record (at most 64, one per candidate).
-//  3. k_wide_mstep -- grid (sample chunk) x (block of 64 Gaussians): per
-//     512-sample tile the records that fall in the block, compacted in sample
-//     order; the warp that owns a Gaussian (g mod 16) adds l, l (x - mu_f),
+//  3. k_wide_mstep -- grid (sample chunk) x (block of 192 Gaussians): per
+//     1024-sample tile the records that fall in the block, compacted in
+//     sample order; the warp that owns a Gaussian (g mod 32) adds l, l (x - mu_f),
 //     l (x - mu_f)^2 (Eqs. 9-11 about the FP32 mean mu_f) to the block's FP32
 //     sums in shared memory, which move to the chunk's FP64 partial after at
 //     most 128 additions.
@@ -73,9 +73,9 @@ constexpr int kWCap = 64;               // candidates per sample before the dens
 constexpr int kWKeep = 64;              // responsibilities per sample record
 constexpr float kWK1 = 4.8828125e-4f;   // 2^-11
 constexpr int kWxThreads = 512;         // exact kernel: 16 warps
-constexpr int kWmThreads = 512;         // M-step kernel: 16 warps
-constexpr int kWmTile = 512;            // samples per M-step tile (one per thread)
-constexpr int kWmBG = 64;               // Gaussians per M-step block
+constexpr int kWmThreads = 1024;        // M-step kernel: 32 warps
+constexpr int kWmTile = 1024;           // samples per M-step tile (one per thread)
+constexpr int kWmBG = 192;              // Gaussians per M-step block (FP32 sums: 192 KB of shared memory)
 constexpr int kWmFlush = 128;           // FP32 additions per sum between FP64 flushes
 constexpr int kWmEnt = 2048;            // list entries per window of an M-step tile
 constexpr int kWMaxG = 4096;
@@ -710,14 +710,14 @@ __host__ __device__ inline WmSmem wm_layout()
 {
     WmSmem L;
     uint32_t o = 0;
-    L.S12 = o; o += 4u * kWmBG * 256u;          // [64][S1: 128 | S2: 128]
+    L.S12 = o; o += 4u * kWmBG * 256u;          // [kWmBG][S1: 128 | S2: 128]
     L.ent = o; o += 8u * kWmEnt;                // (sample | g_local << 16, responsibility)
     L.scan = o; o += 4u * 32u;
     L.total = o;
     return L;
 }
 
-__global__ void __launch_bounds__(kWmThreads, 2) k_wide_mstep(WmArgs w)
+__global__ void __launch_bounds__(kWmThreads, 1) k_wide_mstep(WmArgs w)
 {
     extern __shared__ __align__(16) unsigned char wm_raw[];
     const EmPassArgs &a = w.a;
@@ -803,7 +803,7 @@ __global__ void __launch_bounds__(kWmThreads, 2) k_wide_mstep(WmArgs w)
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
                     const int g = (int)((uw[k >> 1] >> (16 * (k & 1))) & 0xFFFFu);
-                    nm += (k8 + k < rcv && g < G && (g >> 6) == gb);
+                    nm += (k8 + k < rcv && g < G && g / kWmBG == gb);
                 }
             }
         }
@@ -824,13 +824,13 @@ __global__ void __launch_bounds__(kWmThreads, 2) k_wide_mstep(WmArgs w)
         }
         const int pos0 = bp + pn - nm;
         // ---- the pairs in windows of kWmEnt list entries; owner warps take the
-        // pairs of Gaussians g_local = warp (mod 16), in list order
+        // pairs of Gaussians g_local = warp (mod 32), in list order
         for (int r0 = 0; r0 < tp; r0 += kWmEnt) {
             if (nm > 0 && pos0 < r0 + kWmEnt && pos0 + nm > r0) {
                 int p = pos0;
                 for (int k = 0; k < rcv; ++k) {
                     const int g = __ldg(rgi + k);
-                    if (g < G && (g >> 6) == gb) {
+                    if (g < G && g / kWmBG == gb) {
                         if (p >= r0 && p < r0 + kWmEnt)
                             ent[p - r0] = make_uint2((uint32_t)tid | ((uint32_t)(g - g0) << 16),
                                                      __float_as_uint(__ldg(w.rgam + i * kWKeep + k)));
@@ -971,7 +971,7 @@ namespace {
 int wide_mchunks(int64_t N, int32_t G, int sms)
 {
     const int n_gb = (G + kWmBG - 1) / kWmBG;
-    int64_t c = (8LL * sms + n_gb - 1) / n_gb;                 // about four waves of two CTAs per SM
+    int64_t c = (4LL * sms + n_gb - 1) / n_gb;                 // about four waves of one CTA per SM
     const int64_t tiles = (N + kWmTile - 1) / kWmTile;
     c = c < tiles ? c : tiles;
     return (int)(c < 1 ? 1 : c);

@@ -148,8 +148,11 @@ def test_tc_bounded_wait_times_out_and_context_survives():
 
 
 def test_tc_rejects_unsupported_shapes():
-    X, _, _ = synth.make("c1", N=1000, D=70, G=4, seed=1)
-    g = GMM().set_params(X[:4].astype(np.float64), np.ones((4, 70)), np.full(4, 0.25))
+    """The tensor-core forms take D <= 128 and N_G <= 4096 (D <= 64 and
+    N_G <= 256 in one tile, the rest in blocks of Gaussians)."""
+    G = 4097
+    X, _, _ = synth.make("c1", N=8200, D=3, G=4, seed=1)
+    g = GMM().set_params(X[:G].astype(np.float64), np.ones((G, 3)), np.full(G, 1.0 / G))
     with pytest.raises(GmmError) as e:
         g.em_iterate(dev(X), 1, prec="bf16", recompute_center=True)
     assert e.value.status == -7
