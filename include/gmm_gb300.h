@@ -79,20 +79,24 @@ typedef enum {
  *          iteration's means, reduced in FP64) over the Gaussians holding a
  *          responsibility >= 1e-9 / N somewhere in a 32-sample tile.
  *   BF16   tcgen05 tensor cores: the expanded log-density (x'^2 and x' blocks,
- *          data centred by the global mean) in BF16 with FP32 accumulation
- *          screens every Gaussian with a rigorous rounding bound; the
- *          Gaussians that can hold a responsibility >= 1e-9 / N are
- *          recomputed exactly in FP32, and those whose exact responsibility
- *          reaches 1e-9 / N enter log-sum-exp and the M-step.  (For every
- *          Gaussian the responsibility left out sums to less than 1e-9.)
- *          Needs D <= 64 and n_gaus <= 256.
+ *          data centred by the global mean) with FP32 accumulation screens
+ *          every Gaussian with a rigorous rounding bound; the Gaussians that
+ *          can hold a responsibility >= 1e-9 / N are recomputed exactly in
+ *          FP32, and those whose exact responsibility reaches 1e-9 / N enter
+ *          log-sum-exp and the M-step.  (For every Gaussian the
+ *          responsibility left out sums to less than 1e-9.)  D <= 64 and
+ *          n_gaus <= 256: BF16 operands, all Gaussians in one tile.  Up to
+ *          D = 128 and n_gaus = 4096: operands split into BF16 hi + lo parts
+ *          (three products), blocks of 128 Gaussians; a sample with more
+ *          than 64 candidates is evaluated by the register-blocked FP32
+ *          kernels instead.
  * Sufficient statistics are reduced in FP64 in every mode.  There is no TF32
- * or split-BF16 E-step: used directly, the expanded contraction loses ~2^-11
- * (TF32) or ~2^-16 (split BF16) of terms that reach 10^3-10^4 nats when a
- * Gaussian's mean lies many of its standard deviations from the global
- * centre, far more than the FP32 form's responsibilities allow; as a screen
- * the BF16 bound already leaves only ~12% more candidates than an exact
- * screen would on the benchmark data. */
+ * E-step, and no E-step that uses a reduced-precision contraction directly:
+ * that loses ~2^-9 (BF16), ~2^-11 (TF32) or ~2^-16 (split BF16) of terms that
+ * reach 10^3-10^4 nats when a Gaussian's mean lies many of its standard
+ * deviations from the global centre, far more than the FP32 form's
+ * responsibilities allow; as a screen the bound only widens the candidate
+ * set. */
 typedef enum { GMM_FP32 = 0, GMM_BF16 = 1 } gmm_prec;
 
 typedef struct {
@@ -107,9 +111,9 @@ typedef struct {
 
 /* Per-call limits of the kernels: D <= GMM_MAX_DIMS everywhere.  The FP32
  * EM form runs one fused pass when its per-CTA statistics (4 n_gaus (2D+1)
- * bytes plus tile buffers) fit in shared memory, and otherwise two phases (a
- * log-sum-exp pass, then one pass per slab of Gaussians).  The tensor-core
- * EM pass needs D <= 64 and n_gaus <= 256 (else GMM_ERR_UNSUPPORTED). */
+ * bytes plus tile buffers) fit in shared memory and n_gaus <= 128, and
+ * otherwise the register-blocked two-phase form.  The tensor-core EM pass
+ * needs n_gaus <= 4096 (else GMM_ERR_UNSUPPORTED). */
 #define GMM_MAX_DIMS 128
 
 /* Create an empty model (no parameters) on the current CUDA device. */
