@@ -13,8 +13,8 @@ import pytest
 import torch
 
 import oracle
-from paper_1707_09094_gb300 import GMM, GMM_MAHA, synth
-from paper_1707_09094_gb300._lib import GMM_DEBUG_TC_FORM
+from paper_1707_09094_gb300 import GMM, GMM_MAHA, GmmError, synth
+from paper_1707_09094_gb300._lib import GMM_DEBUG_SKIP_MMA, GMM_DEBUG_TC_FORM, GMM_DEBUG_WAIT_CYCLES
 from test_gpu_parity import assert_params, dev, em_step_check, km_weights
 
 pytestmark = pytest.mark.gpu
@@ -181,3 +181,47 @@ def test_c3_full_size_tensor_core_form():
     np.testing.assert_allclose(ll, lls["fp32"], rtol=1e-6)
     del Xd
     torch.cuda.empty_cache()
+
+
+def test_wide_unaligned_and_host_input_match_aligned():
+    """An X that starts 4 bytes into its buffer (scalar sample loads, no L2
+    prefetch of whole tiles) and a host X (copied in chunks behind the first
+    pass in the one-tile form; taken whole here) give the aligned device
+    result, to FP32 summation order."""
+    X, _, _ = synth.make("c1", N=50_000, D=100, G=300, seed=22)
+    flat = torch.zeros(X.size + 1, dtype=torch.float32, device="cuda")
+    flat[1:] = torch.from_numpy(X.ravel()).cuda()
+    Xu = flat[1:].view(X.shape)
+    assert Xu.data_ptr() % 16 == 4
+    Xa = dev(X)
+    start = GMM().learn(Xa, 300, km_iter=5, em_iter=0, seed=3).get_params()
+    runs = []
+    for Xin in (Xa, Xu, X):
+        g = GMM().set_params(*start)
+        g.em_iterate(Xin, 3, prec="bf16", recompute_center=True)
+        runs.append(g)
+    for b in runs[1:]:
+        np.testing.assert_allclose(b.ll_history(), runs[0].ll_history(), rtol=1e-7)
+        assert_params(b.get_params(), runs[0].get_params(), X, rtol=1e-6)
+
+
+def test_wide_bounded_wait_times_out_and_context_survives():
+    """Failure detection without a fault, blocked form: the MMA thread issues
+    nothing, the epilogue's and the operand loader's bounded waits run out,
+    the screen drains its copies, frees its tensor memory and records
+    GMM_ERR_TIMEOUT; the later kernels of the pass stand down, the model is
+    kept and the context stays usable."""
+    X, _, _ = synth.make("c1", N=4096, D=80, G=8, seed=2)
+    Xd = dev(X)
+    g = GMM().learn(Xd, 8, km_iter=2, em_iter=1, seed=1)
+    before = g.get_params()
+    g.debug_set(GMM_DEBUG_WAIT_CYCLES, 2_000_000).debug_set(GMM_DEBUG_SKIP_MMA, 1)
+    with pytest.raises(GmmError) as e:
+        g.em_iterate(Xd, 1, prec="bf16")
+    assert e.value.status == -4
+    for p, q in zip(before, g.get_params()):
+        np.testing.assert_array_equal(p, q)
+    g.debug_set(GMM_DEBUG_SKIP_MMA, 0).debug_set(GMM_DEBUG_WAIT_CYCLES, 0)
+    g.em_iterate(Xd, 1, prec="bf16")
+    torch.cuda.synchronize()
+    assert np.isfinite(g.ll_history()).all()
