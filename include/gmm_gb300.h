@@ -218,7 +218,7 @@ gmm_status gmm_avg_log_p(const gmm_model *m, const float *X, int64_t N, int32_t 
  *   out  host double, written on return (the call synchronises `stream`).
  * The first call on each device looks up the device address of the array
  * (cudaGetSymbolAddress, with that device current) and keeps it for the
- * life of the process; make that first call before any stream capture.  A
+ * life of the process.  A
  * cudaDeviceReset (or any other teardown of the device's primary context)
  * invalidates the kept address: this entry point must not be called after
  * one.  All calls share the array and every call
