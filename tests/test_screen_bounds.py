@@ -137,3 +137,89 @@ def test_kmeans_bound_random_and_adversarial():
         cs = below_midpoint(D, rng)[None, :]
         err, bound = km_case(x, cs, 0)
         assert err <= bound, (err, bound)
+
+
+# ---------------------------------------------------------------- blocked (split-BF16) EM screen
+# The blocked tensor-core pass splits every FP32 operand v into BF16 parts
+# v_h = bf16(v), v_l = bf16(v - v_h) and accumulates t_h a_h + t_l a_h + t_h a_l
+# (t = x'^2) and x_h b_h + x_l b_h + x_h b_l in FP32; it assumes the result is
+# within K1s |P1~| + k2s of the exact kernel's FP32 value
+# c - 1/2 sum_d (x_d s_d - (mu s)_d)^2, with K1s = 2^-11 and
+# k2s = 2^-12 q + 2^-18 r + 2^-20 |ctc| + 1e-3 (r = sum_d m_d^2 iv_d).
+K1S = 2.0 ** -11
+
+
+def _split(v):
+    h = bf16(v)
+    return h, bf16(np.asarray(v, np.float32) - h)
+
+
+def _seq_sum32(p):
+    """Sequential FP32 accumulation along the last axis (the MMA chain's
+    order is not known; any order obeys the same bound)."""
+    return np.add.accumulate(np.asarray(p, np.float32), axis=-1, dtype=np.float32)[..., -1]
+
+
+def split_em_case(x, m, mu, var, w):
+    """x: [P][D] FP32 samples, m: [D] FP32 centre, mu/var: [P][D] FP64 Gaussian
+    parameters (one per pair), w: [P] weights.  Returns (|screen - exact|, bound)."""
+    x = np.asarray(x, np.float32)
+    D = x.shape[1]
+    xc = (x - m[None, :]).astype(np.float32)                    # x' in FP32
+    t = (xc * xc).astype(np.float32)
+    iv = 1.0 / var
+    a = (-0.5 * iv).astype(np.float32)
+    b = ((mu - m[None, :].astype(np.float64)) * iv).astype(np.float32)
+    th, tl = _split(t)
+    xh, xl = _split(xc)
+    ah, al = _split(a)
+    bh, bl = _split(b)
+    p1 = _seq_sum32(np.concatenate([th * ah, tl * ah, th * al], axis=1).astype(np.float32))
+    p2 = _seq_sum32(np.concatenate([xh * bh, xl * bh, xh * bl], axis=1).astype(np.float32))
+    mc = mu - m[None, :].astype(np.float64)
+    q = np.sum(mc * mc * iv, axis=1)
+    r = np.sum(m[None, :].astype(np.float64) ** 2 * iv, axis=1)
+    c = np.log(w) - 0.5 * D * np.log(2 * np.pi) - 0.5 * np.sum(np.log(var), axis=1)
+    ctc = (c - 0.5 * q).astype(np.float32)
+    screen = (p1 + p2).astype(np.float32) + ctc
+    # the exact kernel: s = 1/sigma, mu s in FP32, t = fma(x, s, -mu s), sum of t^2, c - r/2
+    s = (1.0 / np.sqrt(var)).astype(np.float32)
+    ms = (mu * (1.0 / np.sqrt(var))).astype(np.float32)
+    td = (x.astype(np.float64) * s - ms).astype(np.float32)       # one rounding, as an FMA
+    rr = _seq_sum32((td * td).astype(np.float32))
+    exact = (c.astype(np.float32) - np.float32(0.5) * rr).astype(np.float32)
+    k2 = 2.0 ** -12 * q + 2.0 ** -18 * r + 2.0 ** -20 * np.abs(ctc.astype(np.float64)) + 1e-3
+    err = np.abs(screen.astype(np.float64) - exact.astype(np.float64))
+    return err, K1S * np.abs(p1.astype(np.float64)) + k2
+
+
+def test_split_em_bound_c3_like():
+    """Pairs shaped like the precision workload (means ~ N(0, 3^2), sigma
+    log-uniform on [0.1, 10], D = 128): samples of the pair's own Gaussian
+    and of other Gaussians, centre near the data mean."""
+    rng = np.random.default_rng(7)
+    P, D = 2000, 128
+    mu = rng.normal(0, 3, (P, D))
+    sd = np.exp(rng.uniform(np.log(0.1), np.log(10), (P, D)))
+    own = rng.random(P) < 0.5
+    other_mu = rng.normal(0, 3, (P, D))
+    other_sd = np.exp(rng.uniform(np.log(0.1), np.log(10), (P, D)))
+    x = np.where(own[:, None], mu + sd * rng.normal(size=(P, D)), other_mu + other_sd * rng.normal(size=(P, D)))
+    m = rng.normal(0, 0.3, D).astype(np.float32)
+    err, bound = split_em_case(x.astype(np.float32), m, mu, sd ** 2, rng.uniform(1e-4, 1e-2, P))
+    assert (err <= bound).all(), float(np.max(err / bound))
+    assert np.max(err / bound) < 0.5   # the constants hold with room to spare
+
+
+def test_split_em_bound_wide_ranges():
+    """Variances from 1e-4 to 1e2, centres far from the data, D from 1 to 128."""
+    rng = np.random.default_rng(8)
+    for _ in range(40):
+        D = int(rng.integers(1, 129))
+        P = 200
+        mu = rng.normal(0, rng.uniform(0.1, 30), (P, D))
+        var = np.exp(rng.uniform(np.log(1e-4), np.log(1e2), (P, D)))
+        x = (mu + np.sqrt(var) * rng.normal(size=(P, D)) * rng.uniform(0.1, 20)).astype(np.float32)
+        m = rng.normal(0, rng.uniform(0.1, 30), D).astype(np.float32)
+        err, bound = split_em_case(x, m, mu, var, rng.uniform(1e-6, 1, P))
+        assert (err <= bound).all(), float(np.max(err / bound))
