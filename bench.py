@@ -597,7 +597,8 @@ def run_c3_leg(peaks, peak_src, steps=3, n=None):
       bf16  the blocked tensor-core pass (split-BF16 screen over blocks of 128
             Gaussians on tcgen05, exact FP32 log-densities of the candidates,
             M-step from the kept responsibilities);
-      fp32  the register-blocked two-phase CUDA-core form.
+      fp32  the register-blocked two-phase CUDA-core form (log-densities
+            computed once: the first phase records each block's candidates).
     Algorithmic work as the headline: 8 flop per (i, g, d); the bf16 roofline
     is against the BF16 tensor peak, the fp32 one against the FP32 FMA peak.
     n: the first n samples only (profiling captures)."""
@@ -635,7 +636,7 @@ def run_c3_leg(peaks, peak_src, steps=3, n=None):
             f["roofline"] = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                              "frac": achieved / peak, "peak_source": "bf16_tflops (%s)" % peak_src}
         else:
-            f["form"] = "fp32 (register-blocked, two phases)"
+            f["form"] = "fp32 (register-blocked, two phases, log-densities recorded once)"
             f["roofline"] = {"bound": "alu", "achieved": achieved, "peak": alu, "unit": "TFLOP/s",
                              "frac": achieved / alu,
                              "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (%s clock)"

@@ -371,8 +371,10 @@ gmm_status gmm_profile_read(const gmm_model *m, double *pass_ms, int64_t *pass_l
  *                          statistics fit in one CTA's shared memory, else
  *                          the register-blocked two-phase form; 1: the
  *                          one-pass form wherever it fits; 2: the
- *                          register-blocked form for every shape (the same
- *                          results to FP32 rounding). */
+ *                          register-blocked form for every shape; 3: the
+ *                          same with the log-densities recomputed in the
+ *                          second phase instead of recorded in the first
+ *                          (the same results to FP32 rounding). */
 #define GMM_DEBUG_FP32_FORM 4
 /*   GMM_DEBUG_TC_FORM      0 (default): the BF16 EM pass runs the one-tile
  *                          tensor-core form for D <= 64 and N_G <= 256, else

@@ -62,7 +62,18 @@ struct BlkArgs {
     float *lse;          // [N] log p(x_i)
     double *out;         // inference: log p(x_i) in FP64 here instead of lse and the log-likelihood
     const int64_t *n_dev;   // non-null: the samples actually present (device), at most N (part's stride)
+    // candidate records (non-null rec_n): per (block, sample) the Gaussians
+    // whose log-density lies within `screen` of the block's best
+    uint8_t *rec_n;         // [n_gb][N] count (> kBRec: some not recorded)
+    uint16_t *rec_g;        // [n_gb][N][kBRec]
+    float *rec_l;           // [n_gb][N][kBRec] their log-densities
+    float screen;           // ln(N * 1e9)
+    // per-sample records of the kept responsibilities (k_blk_combine_rec)
+    uint8_t *rc;            // [N] count (255: the sample goes through k_blk_em)
+    uint16_t *rg;           // [N][kRecSlots]
+    float *rgam;            // [N][kRecSlots]
 };
+constexpr int kBRec = 8;    // recorded candidates per (block, sample)
 
 // Samples present: a.N, or fewer when the count is known only on the device.
 __device__ __forceinline__ int64_t blk_n(const BlkArgs &b) { return b.n_dev ? *b.n_dev : b.a.N; }
@@ -197,8 +208,12 @@ __global__ void __launch_bounds__(kBThreads, 1) k_blk_lse(BlkArgs b)
     const int gb = blockIdx.x % b.n_gb, chunk = blockIdx.x / b.n_gb;   // the chunk's blocks run side by side
     float *op = bsm, *cg = op + kBG * OS, *xt = cg + kBG;
     float2 *red = reinterpret_cast<float2 *>(xt + 2 * TS * XS);   // [4][TS] partials of the four Gaussian quarters
+    float *mb = reinterpret_cast<float *>(red + 4 * TS);           // [TS] block maximum per sample (records)
+    int *cntb = reinterpret_cast<int *>(mb + TS);                  // [TS] candidates recorded per sample
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     const int sg = 8 * (w & 1) + (lane & 7), gg = 4 * (w >> 1) + (lane >> 3);
+    const bool rec = b.rec_n != nullptr;
+    for (int s = tid; s < TS; s += kBThreads) cntb[s] = 0;
     blk_stage_operands(a, gb * kBG, op, cg);
     for (int k = tid; k < 2 * TS * (XS - D); k += kBThreads) {   // zero columns D..XS-1 of both buffers
         const int r = k / (XS - D);
@@ -235,11 +250,40 @@ __global__ void __launch_bounds__(kBThreads, 1) k_blk_lse(BlkArgs b)
         __syncthreads();
         const int64_t i0 = t * TS;
         for (int s = tid; s < TS; s += kBThreads) {
+            float2 p = make_float2(-INFINITY, 0.f);
             if (i0 + s < N) {
-                float2 p = red[s];
+                p = red[s];
 #pragma unroll
                 for (int q = 1; q < 4; ++q) p = lse_merge(p, red[q * TS + s]);
                 b.part[(size_t)gb * a.N + i0 + s] = p;
+            }
+            if (rec) mb[s] = p.x;
+        }
+        if (rec) {   // uniform
+            // candidates: log-density within `screen` of the block's best (a
+            // superset of those within it of the best over all blocks)
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < RS; ++k) {
+                const int s = sg + 16 * k;
+                if (i0 + s < N) {
+                    const float thr = mb[s] - b.screen;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (l[k][j] >= thr) {   // -inf logits (past N_G) never pass
+                            const int slot = atomicAdd(cntb + s, 1);
+                            if (slot < kBRec) {
+                                const size_t o = ((size_t)gb * a.N + i0 + s) * kBRec + slot;
+                                b.rec_g[o] = (uint16_t)(gb * kBG + gg + 16 * j);
+                                b.rec_l[o] = l[k][j];
+                            }
+                        }
+                }
+            }
+            __syncthreads();
+            for (int s = tid; s < TS; s += kBThreads) {
+                if (i0 + s < N) b.rec_n[(size_t)gb * a.N + i0 + s] = (uint8_t)min(cntb[s], 255);
+                cntb[s] = 0;
             }
         }
         // the next iteration restages buffer bi only after its barrier, which
@@ -266,6 +310,48 @@ __global__ void __launch_bounds__(128) k_blk_combine(BlkArgs b)
         const float ls = p.x + logf(p.y);
         b.lse[i] = ls;
         v = (double)ls;
+        if (b.rc) {
+            // the recorded candidates whose responsibility reaches exp(-screen),
+            // block after block, each block's in Gaussian order
+            int m = 0;
+            bool over = false;
+            for (int q = 0; q < b.n_gb; ++q) {
+                const size_t base = (size_t)q * a.N + i;
+                const int n = b.rec_n[base];
+                if (n > kBRec) {
+                    over = true;
+                    continue;
+                }
+                int eg[kBRec];
+                float el[kBRec];
+#pragma unroll
+                for (int e = 0; e < kBRec; ++e) {
+                    eg[e] = e < n ? (int)b.rec_g[base * kBRec + e] : 0xFFFF;
+                    el[e] = e < n ? b.rec_l[base * kBRec + e] : -INFINITY;
+                }
+                int last = -1;
+                for (int r = 0; r < n; ++r) {
+                    int bg = 0x10000;
+                    float bl = -INFINITY;
+#pragma unroll
+                    for (int e = 0; e < kBRec; ++e)
+                        if (eg[e] > last && eg[e] < bg) {
+                            bg = eg[e];
+                            bl = el[e];
+                        }
+                    last = bg;
+                    const float rl = bl - ls;
+                    if (rl >= -b.screen) {
+                        if (m < kRecSlots) {
+                            b.rg[i * kRecSlots + m] = (uint16_t)bg;
+                            b.rgam[i * kRecSlots + m] = __expf(rl);
+                        }
+                        ++m;
+                    }
+                }
+            }
+            b.rc[i] = (uint8_t)((over || m > kRecSlots) ? 255 : m);
+        }
     }
     if (b.out) return;   // the block's threads past N
     sh[threadIdx.x] = v;
@@ -889,7 +975,7 @@ bool em_blocked_supported(int32_t D, int32_t G)
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    return blk_smem(D, 128, false) + 4 * 128 * sizeof(float2) + 1024 <= (size_t)optin &&
+    return blk_smem(D, 128, false) + 4 * 128 * sizeof(float2) + 2 * 128 * 4 + 1024 <= (size_t)optin &&
            blk_smem(D, 64, true) + 1024 <= (size_t)optin;
 }
 
@@ -911,7 +997,7 @@ cudaError_t launch_em_blocked(const EmPassArgs &a, float *lse, float2 *part, int
 {
     BlkArgs b{a, em_blocked_gblocks(a.G), n_chunks,
               (a.D % 4 == 0 && (reinterpret_cast<uintptr_t>(a.X) & 15u) == 0) ? 1 : 0, part, lse, nullptr, n_dev};
-    const size_t sm1 = blk_smem(a.D, 128, false) + 4 * 128 * sizeof(float2);
+    const size_t sm1 = blk_smem(a.D, 128, false) + 4 * 128 * sizeof(float2) + 2 * 128 * 4;
     const size_t sm3 = blk_smem(a.D, 64, true);
     cudaError_t e = cudaFuncSetAttribute(k_blk_lse<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
     if (e != cudaSuccess) return e;
@@ -922,6 +1008,69 @@ cudaError_t launch_em_blocked(const EmPassArgs &a, float *lse, float2 *part, int
     k_blk_combine<<<(int)((a.N + 127) / 128), 128, 0, s>>>(b);
     k_blk_em<<<grid, kBThreads, sm3, s>>>(b);
     count_launches(3);
+    return cudaGetLastError();
+}
+
+size_t em_rec_ws_bytes(int64_t N, int32_t D, int32_t G)
+{
+    const size_t n = (size_t)N, nb = (size_t)em_blocked_gblocks(G), nblk = (n + 1023) / 1024;
+    auto al = [](size_t x) { return (x + 255u) & ~(size_t)255u; };
+    return al(nb * n) + al(2u * nb * n * kBRec) + al(4u * nb * n * kBRec) + al(n) + al(2u * n * kRecSlots) +
+           al(4u * n * kRecSlots) + al(4u * nblk) + al(8u) + al(4u * n * (size_t)D) + al(4u * n) + al(8u * nb * n) + 256u;
+}
+
+RecWs em_rec_ws(void *base, int64_t N, int32_t D, int32_t G)
+{
+    const size_t n = (size_t)N, nb = (size_t)em_blocked_gblocks(G), nblk = (n + 1023) / 1024;
+    auto al = [](size_t x) { return (x + 255u) & ~(size_t)255u; };
+    unsigned char *p = static_cast<unsigned char *>(base);
+    RecWs w;
+    w.rec_n = p;                                   p += al(nb * n);
+    w.rec_g = reinterpret_cast<uint16_t *>(p);     p += al(2u * nb * n * kBRec);
+    w.rec_l = reinterpret_cast<float *>(p);        p += al(4u * nb * n * kBRec);
+    w.rc = p;                                      p += al(n);
+    w.rg = reinterpret_cast<uint16_t *>(p);        p += al(2u * n * kRecSlots);
+    w.rgam = reinterpret_cast<float *>(p);         p += al(4u * n * kRecSlots);
+    w.bcnt = reinterpret_cast<int32_t *>(p);       p += al(4u * nblk);
+    w.n_mark = reinterpret_cast<int64_t *>(p);     p += al(8u);
+    w.Xd = reinterpret_cast<float *>(p);           p += al(4u * n * (size_t)D);
+    w.lse_d = reinterpret_cast<float *>(p);        p += al(4u * n);
+    w.part_d = reinterpret_cast<float2 *>(p);
+    return w;
+}
+
+int em_rec_partials(int64_t N, int32_t G, int sms) { return record_mstep_chunks(N, G, sms) + em_blocked_chunks(G, sms); }
+
+cudaError_t launch_em_blocked_rec(const EmPassArgs &a, float *lse, float2 *part, const RecWs &ws, int sms, cudaStream_t s)
+{
+    const int nch = em_blocked_chunks(a.G, sms), n_gb = em_blocked_gblocks(a.G);
+    const float scr = (float)std::log((double)(a.N_total > a.N ? a.N_total : a.N) * 1e9);
+    BlkArgs b{a, n_gb, nch, (a.D % 4 == 0 && (reinterpret_cast<uintptr_t>(a.X) & 15u) == 0) ? 1 : 0, part, lse, nullptr,
+              nullptr, ws.rec_n, ws.rec_g, ws.rec_l, scr, ws.rc, ws.rg, ws.rgam};
+    const size_t sm1 = blk_smem(a.D, 128, false) + 4 * 128 * sizeof(float2) + 2 * 128 * 4;
+    const size_t sm3 = blk_smem(a.D, 64, true);
+    cudaError_t e = cudaFuncSetAttribute(k_blk_lse<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_blk_em, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3)) != cudaSuccess)
+        return e;
+    // log-sum-exp partials and the candidates per block; log p, the
+    // log-likelihood and the kept responsibilities per sample
+    k_blk_lse<8><<<n_gb * nch, kBThreads, sm1, s>>>(b);
+    k_blk_combine<<<(int)((a.N + 127) / 128), 128, 0, s>>>(b);
+    count_launches(2);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // samples whose records overflowed, gathered with their log p
+    if ((e = launch_gather_marked(ws.rc, a.X, lse, a.N, a.D, ws.bcnt, ws.n_mark, ws.Xd, ws.lse_d, s)) != cudaSuccess)
+        return e;
+    // statistics from the records, then those samples' from their recomputed
+    // responsibilities (partials after the records')
+    if ((e = launch_record_mstep(a, ws.rc, ws.rg, ws.rgam, sms, s)) != cudaSuccess) return e;
+    EmPassArgs d = a;
+    d.X = ws.Xd;
+    d.partial = a.partial + (size_t)record_mstep_chunks(a.N, a.G, sms) * a.G * (1 + 2 * a.D);
+    BlkArgs bd{d, n_gb, nch, a.D % 4 == 0 ? 1 : 0, ws.part_d, ws.lse_d, nullptr, ws.n_mark};
+    k_blk_em<<<n_gb * nch, kBThreads, sm3, s>>>(bd);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -972,7 +1121,7 @@ cudaError_t launch_log_p_blocked(const float *X, int64_t N, int32_t D, int32_t G
     const int n_chunks = em_blocked_chunks(G, sms);
     BlkArgs b{a, em_blocked_gblocks(G), n_chunks, (D % 4 == 0 && (reinterpret_cast<uintptr_t>(X) & 15u) == 0) ? 1 : 0,
               part, nullptr, out};
-    const size_t sm1 = blk_smem(D, 128, false) + 4 * 128 * sizeof(float2);
+    const size_t sm1 = blk_smem(D, 128, false) + 4 * 128 * sizeof(float2) + 2 * 128 * 4;
     cudaError_t e = cudaFuncSetAttribute(k_blk_lse<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
     if (e != cudaSuccess) return e;
     k_blk_lse<8><<<b.n_gb * n_chunks, kBThreads, sm1, s>>>(b);

@@ -129,6 +129,7 @@ struct gmm_model {
     uint8_t *kmarg = nullptr; size_t kmarg_cap = 0;           // register-blocked k-means: argmin per block | max norm
     unsigned char *tclist = nullptr; size_t tclist_cap = 0;   // tensor-core pass: per-sample records
     unsigned char *wide = nullptr; size_t wide_cap = 0;       // tensor-core pass beyond D 64 / N_G 256
+    unsigned char *recws = nullptr; size_t recws_cap = 0;     // FP32 two-phase form: candidate and kept records
     unsigned char *kmop = nullptr; size_t kmop_cap = 0;       // tensor-core k-means operands
     double *spread = nullptr; size_t spread_cap = 0;          // spread seeding: distances + block partials
     cudaStream_t cstream = nullptr;                           // host-input copies that overlap the first pass
@@ -156,7 +157,7 @@ struct gmm_model {
     long long wait_cycles = 2000000000LL;
     int skip_mma = 0;
     int km_form = 0;                        // 0: tensor cores where supported, 1: CUDA cores
-    int fp32_form = 0;                      // 0: by shape, 1: one-pass where it fits, 2: register-blocked
+    int fp32_form = 0;                      // 0: by shape, 1: one-pass where it fits, 2: register-blocked, 3: same, recomputed second phase
     int tc_form = 0;                        // 0: by shape, 1: the D <= 128 / N_G <= 4096 pass for every shape
     unsigned long long *sstats = nullptr;   // screening counters (device, [kStatWords])
 
@@ -347,16 +348,18 @@ gmm_status run_em(gmm_model *m, const float *Xd, int64_t N, int32_t em_iter, dou
     // two-phase form (faster from N_G = 256: 11.0 against 12.7 ms per
     // iteration at N = 2e6, D = 60)
     const bool one_pass_fits = gmm::em_simt_supported(D, G);
-    const bool two_phase = !tc && (m->fp32_form == 2 || !one_pass_fits || (m->fp32_form == 0 && G > 128));
+    const bool two_phase = !tc && (m->fp32_form >= 2 || !one_pass_fits || (m->fp32_form == 0 && G > 128));
     if (two_phase && !gmm::em_blocked_supported(D, G))
         return fail(GMM_ERR_UNSUPPORTED, "FP32 E-step: shared memory too small for D=%d, G=%d", D, G);
     if (tc && !(m->has_center && m->center_D == D))
         return fail(GMM_ERR_STATE, "tensor-core E-step needs the global centre (run learn or recompute_center)");
     // one-pass forms: one partial per CTA; two-phase form: one per sample chunk
     // (and one log-likelihood partial per 128-sample block of the lse pass)
+    const bool rec = two_phase && m->fp32_form != 3;   // records of the kept responsibilities (else recompute)
     const int grid = wide ? gmm::em_wide_partials(N, G, m->sms)
                           : (tc ? gmm::em_tc_grid(m->sms)
-                                : (two_phase ? gmm::em_blocked_chunks(G, m->sms) : gmm::em_simt_grid(D, G, m->sms)));
+                                : (two_phase ? (rec ? gmm::em_rec_partials(N, G, m->sms) : gmm::em_blocked_chunks(G, m->sms))
+                                             : gmm::em_simt_grid(D, G, m->sms)));
     if ((two_phase || wide) && cp) {   // these forms take all of X at once
         CK(cudaStreamWaitEvent(s, cp->ready.back(), 0));
         cp = nullptr;
@@ -368,6 +371,7 @@ gmm_status run_em(gmm_model *m, const float *Xd, int64_t N, int32_t em_iter, dou
     if (two_phase) CK(grow(m->lsep, m->lsep_cap, (size_t)gmm::em_blocked_gblocks(G) * (size_t)N));
     if (tc && !wide) CK(grow(m->tclist, m->tclist_cap, gmm::em_tc_list_bytes(N, grid)));
     if (wide) CK(grow(m->wide, m->wide_cap, gmm::em_wide_ws_bytes(N, D, G)));
+    if (rec) CK(grow(m->recws, m->recws_cap, gmm::em_rec_ws_bytes(N, D, G)));
     CK(grow(m->llp, m->llp_cap, (size_t)nch * n_llp));
     CK(grow(m->lld, m->lld_cap, (size_t)(em_iter > 0 ? em_iter : 1)));
     CK(gmm::launch_status_reset(m->status, s));
@@ -388,6 +392,7 @@ gmm_status run_em(gmm_model *m, const float *Xd, int64_t N, int32_t em_iter, dou
             if (wide)
                 CK(gmm::launch_em_wide(pa, m->par[(base + k) & 1], gmm::em_wide_ws(m->wide, N, D, G), m->sms, s));
             else if (tc) CK(gmm::launch_em_pass_tc(pa, gmm::em_tc_lists(m->tclist, b1 - b0, grid), grid, grid, s));
+            else if (rec) CK(gmm::launch_em_blocked_rec(pa, m->lse, m->lsep, gmm::em_rec_ws(m->recws, N, D, G), m->sms, s));
             else if (two_phase) CK(gmm::launch_em_blocked(pa, m->lse, m->lsep, grid, s));
             else CK(gmm::launch_em_pass_simt(pa, grid, s));
         }
@@ -473,7 +478,7 @@ void gmm_destroy(gmm_model *m)
     if (m->sstats) cudaFree(m->sstats);
     void *bufs[] = {m->par[0], m->par[1], m->op_sm, m->op_mu, m->op_c, m->op_B, m->gstat, m->fstat,
                     m->partial, m->kmarg, m->lse, m->llp, m->lld, m->counts, m->assign, m->xstage, m->dstage, m->idx,
-                    m->hist, m->status, m->tclist, m->kmop, m->spread, m->lsep, m->wide};
+                    m->hist, m->status, m->tclist, m->kmop, m->spread, m->lsep, m->wide, m->recws};
     for (void *p : bufs)
         if (p) cudaFree(p);
     delete m;
@@ -902,7 +907,7 @@ gmm_status gmm_debug_set(gmm_model *m, int32_t key, int64_t value)
         if (value < 0 || value > 1) return fail(GMM_ERR_ARG, "k-means form must be 0 or 1");
         m->km_form = (int)value;
     } else if (key == GMM_DEBUG_FP32_FORM) {
-        if (value < 0 || value > 2) return fail(GMM_ERR_ARG, "FP32 form must be 0, 1 or 2");
+        if (value < 0 || value > 3) return fail(GMM_ERR_ARG, "FP32 form must be 0, 1, 2 or 3");
         m->fp32_form = (int)value;
     } else if (key == GMM_DEBUG_TC_FORM) {
         if (value < 0 || value > 1) return fail(GMM_ERR_ARG, "tensor-core form must be 0 or 1");

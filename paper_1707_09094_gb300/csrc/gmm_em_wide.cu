@@ -70,7 +70,7 @@ constexpr int kWThreads = kWEpi + 64;   // + the MMA warp + the operand-loading 
 constexpr int kWStages = 3;             // B operand ring
 constexpr uint32_t kWPiece = 16384;     // one operand piece: 128 rows x 64 K in BF16
 constexpr int kWCap = 64;               // candidates per sample before the dense fallback
-constexpr int kWKeep = 64;              // responsibilities per sample record
+constexpr int kWKeep = kRecSlots;       // responsibilities per sample record
 constexpr float kWK1 = 4.8828125e-4f;   // 2^-11
 constexpr int kWxThreads = 512;         // exact kernel: 16 warps
 constexpr int kWmThreads = 1024;        // M-step kernel: 32 warps
@@ -796,7 +796,8 @@ __global__ void __launch_bounds__(kWmThreads, 1) k_wide_mstep(WmArgs w)
         int nm = 0, rcv = 0;
         const uint16_t *rgi = w.rg + i * kWKeep;
         if (i < a.N) {
-            rcv = min((int)w.rc[i], kWKeep);
+            const int r = w.rc[i];
+            rcv = r == 255 ? 0 : min(r, kWKeep);   // 255: the sample's statistics come from elsewhere
             for (int k8 = 0; k8 < rcv; k8 += 8) {   // eight slots per 16-byte load
                 const uint4 u = __ldg(reinterpret_cast<const uint4 *>(rgi + k8));
                 const uint32_t uw[4] = {u.x, u.y, u.z, u.w};
@@ -927,7 +928,8 @@ __global__ void __launch_bounds__(1024) k_wide_dscan(int32_t *__restrict__ bcnt,
 
 __global__ void __launch_bounds__(kWdBlock) k_wide_dgather(const uint8_t *__restrict__ cnt, const float *__restrict__ X,
                                                            int64_t N, int32_t D, const int32_t *__restrict__ boff,
-                                                           float *__restrict__ Xd)
+                                                           float *__restrict__ Xd, const float *__restrict__ v,
+                                                           float *__restrict__ vd)
 {
     __shared__ int32_t s_w[32];
     __shared__ int64_t s_idx[kWdBlock];
@@ -947,7 +949,10 @@ __global__ void __launch_bounds__(kWdBlock) k_wide_dgather(const uint8_t *__rest
         if (k < warp) wb += s_w[k];
         tot += s_w[k];
     }
-    if (f) s_idx[wb + x - 1] = i;
+    if (f) {
+        s_idx[wb + x - 1] = i;
+        if (v) vd[boff[blockIdx.x] + wb + x - 1] = v[i];   // a per-sample value travels with the row
+    }
     __syncthreads();
     const int64_t o0 = boff[blockIdx.x];
     for (int k = warp; k < tot; k += kWdBlock / 32) {   // a warp per row
@@ -1020,6 +1025,32 @@ WideWs em_wide_ws(void *base, int64_t N, int32_t D, int32_t G)
     return w;
 }
 
+int record_mstep_chunks(int64_t N, int32_t G, int sms) { return wide_mchunks(N, G, sms); }
+
+cudaError_t launch_record_mstep(const EmPassArgs &a, const uint8_t *rc, const uint16_t *rg, const float *rgam, int sms,
+                                cudaStream_t s)
+{
+    const int mch = wide_mchunks(a.N, a.G, sms), n_gb = (a.G + kWmBG - 1) / kWmBG;
+    WmArgs m{a, rc, rg, rgam, n_gb, mch};
+    const size_t sm3 = wm_layout().total;
+    cudaError_t e = cudaFuncSetAttribute(k_wide_mstep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3);
+    if (e != cudaSuccess) return e;
+    k_wide_mstep<<<mch * n_gb, kWmThreads, sm3, s>>>(m);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_marked(const uint8_t *flag, const float *X, const float *v, int64_t N, int32_t D, int32_t *bcnt,
+                                 int64_t *n_marked, float *Xd, float *vd, cudaStream_t s)
+{
+    const int nblk = (int)((N + kWdBlock - 1) / kWdBlock);
+    k_wide_dcount<<<nblk, kWdBlock, 0, s>>>(flag, N, bcnt);
+    k_wide_dscan<<<1, 1024, 0, s>>>(bcnt, nblk, n_marked);
+    k_wide_dgather<<<nblk, kWdBlock, 0, s>>>(flag, X, N, D, bcnt, Xd, v, vd);
+    count_launches(3);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_em_wide(const EmPassArgs &a, const double *par, const WideWs &ws, int sms, cudaStream_t s)
 {
     const int nkb = (a.D + 63) / 64, nb = (a.G + kWGB - 1) / kWGB;
@@ -1042,7 +1073,7 @@ cudaError_t launch_em_wide(const EmPassArgs &a, const double *par, const WideWs 
     const int nblk = (int)((a.N + kWdBlock - 1) / kWdBlock);
     k_wide_dcount<<<nblk, kWdBlock, 0, s>>>(ws.cnt, a.N, ws.bcnt);
     k_wide_dscan<<<1, 1024, 0, s>>>(ws.bcnt, nblk, ws.n_dense);
-    k_wide_dgather<<<nblk, kWdBlock, 0, s>>>(ws.cnt, a.X, a.N, a.D, ws.bcnt, ws.Xd);
+    k_wide_dgather<<<nblk, kWdBlock, 0, s>>>(ws.cnt, a.X, a.N, a.D, ws.bcnt, ws.Xd, nullptr, nullptr);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     WxArgs x{a, ws.cnt, ws.cand, ws.rc, ws.rg, ws.rgam, scr, xv4, sv4};
     k_wide_exact<<<xg, kWxThreads, 0, s>>>(x);

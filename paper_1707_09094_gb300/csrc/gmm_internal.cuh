@@ -10,6 +10,7 @@
 namespace gmm {
 
 constexpr double kLog2Pi = 1.83787706640934548356065947281123527;
+constexpr int kRecSlots = 64;   // kept responsibilities per sample record (record M-step)
 
 // Device-side status block, one per model.  Kernels never trap: they record
 // what went wrong here and return, and the host reads it after the stream
@@ -105,6 +106,29 @@ int em_blocked_chunks(int32_t G, int sms);
 // the stride of part and lse and sizes the launch)
 cudaError_t launch_em_blocked(const EmPassArgs &a, float *lse, float2 *part, int32_t n_chunks, cudaStream_t s,
                               const int64_t *n_dev = nullptr);
+// The same form with the log-densities computed once: the first phase also
+// records each block's candidates, the merge turns them into per-sample
+// records of the kept responsibilities, the M-step reads those; samples whose
+// records overflow go through the recomputing second phase.  Statistics
+// partials [em_rec_partials][G][1 + 2D]; log-likelihood partials per 128
+// samples as launch_em_blocked.
+struct RecWs {
+    uint8_t *rec_n;          // [n_gb][N]
+    uint16_t *rec_g;         // [n_gb][N][8]
+    float *rec_l;            // [n_gb][N][8]
+    uint8_t *rc;             // [N]
+    uint16_t *rg;            // [N][kRecSlots]
+    float *rgam;             // [N][kRecSlots]
+    int32_t *bcnt;           // ceil(N / 1024)
+    int64_t *n_mark;         // [1]
+    float *Xd;               // [N][D]
+    float *lse_d;            // [N]
+    float2 *part_d;          // [n_gb][N]
+};
+size_t em_rec_ws_bytes(int64_t N, int32_t D, int32_t G);
+RecWs em_rec_ws(void *base, int64_t N, int32_t D, int32_t G);
+int em_rec_partials(int64_t N, int32_t G, int sms);
+cudaError_t launch_em_blocked_rec(const EmPassArgs &a, float *lse, float2 *part, const RecWs &ws, int sms, cudaStream_t s);
 // k-means map step for shapes beyond the tiled form: assign [N] (exact
 // nearest mean) and the statistics into partial [n_chunks][G][1 + 2D];
 // part [gblocks][N], arg [gblocks][N], nmax [1], snorm [N] and defer [N + 1]
@@ -269,5 +293,16 @@ WideWs em_wide_ws(void *base, int64_t N, int32_t D, int32_t G);
 // One EM iteration's pass from par (the iteration's parameters; op holds
 // their FP32 operands) into a.partial and a.ll_partial.
 cudaError_t launch_em_wide(const EmPassArgs &a, const double *par, const WideWs &ws, int sms, cudaStream_t s);
+// M-step from per-sample records (rc [N] counts, rg/rgam [N][kRecSlots]
+// Gaussians and responsibilities) into a.partial [record_mstep_chunks][G][1 + 2D]
+
+int record_mstep_chunks(int64_t N, int32_t G, int sms);
+cudaError_t launch_record_mstep(const EmPassArgs &a, const uint8_t *rc, const uint16_t *rg, const float *rgam, int sms,
+                                cudaStream_t s);
+// the samples whose flag is 255, in sample order: their rows into Xd, v[i]
+// into vd (when v is given), their count into *n_marked; bcnt holds
+// ceil(N / 1024) ints of work space
+cudaError_t launch_gather_marked(const uint8_t *flag, const float *X, const float *v, int64_t N, int32_t D, int32_t *bcnt,
+                                 int64_t *n_marked, float *Xd, float *vd, cudaStream_t s);
 
 }  // namespace gmm

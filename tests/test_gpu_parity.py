@@ -340,19 +340,45 @@ def test_c2_full_size_log_p_sampled(c2):
 
 
 # ------------------------------------------------------------ large N_G * D
+@pytest.mark.parametrize("form", [2, 3])
 @pytest.mark.parametrize("shape", [(100000, 10, 8), (20000, 60, 256), (3001, 64, 17), (160, 16, 16), (30, 3, 2),
                                    (5000, 33, 65)])
-def test_register_blocked_form_on_small_shapes(shape):
+def test_register_blocked_form_on_small_shapes(shape, form):
     """The register-blocked two-phase form forced onto shapes the one-pass
-    form would take (GMM_DEBUG_FP32_FORM = 2): N_G below one 64-Gaussian block,
-    partial blocks, D not a multiple of 4 or 8, a single short tile.  Each
-    iteration equals the oracle's."""
+    form would take: N_G below one 64-Gaussian block, partial blocks, D not a
+    multiple of 4 or 8, a single short tile; with the log-densities recorded
+    in the first phase (GMM_DEBUG_FP32_FORM = 2) and recomputed in the second
+    (3).  Each iteration equals the oracle's."""
     from paper_1707_09094_gb300._lib import GMM_DEBUG_FP32_FORM
     N, D, G = shape
     X, _, _ = synth.make("c1", N=N, D=D, G=G, seed=11 + N)
     start = _start(X, G, 4)
     Xd = dev(X)
-    g = GMM().set_params(*start).debug_set(GMM_DEBUG_FP32_FORM, 2)
+    g = GMM().set_params(*start).debug_set(GMM_DEBUG_FP32_FORM, form)
+    g.em_iterate(Xd, 0, recompute_center=True)
+    for _ in range(2):
+        em_step_check(g, X, Xd)
+
+
+@pytest.mark.parametrize("part", [1.0, 0.3])
+def test_register_blocked_records_overflow(part):
+    """Overlapping Gaussians: a sample near 100 overlapping means has more
+    candidates in a 64-Gaussian block than its record holds (8), so it is
+    gathered and its responsibilities are recomputed in the second phase;
+    all samples (part 1.0) or 30 % of them (0.3, the rest near 60 others).
+    Each iteration equals the oracle's."""
+    from paper_1707_09094_gb300._lib import GMM_DEBUG_FP32_FORM
+    rng = np.random.default_rng(9)
+    N, D = 6000, 8
+    X = rng.normal(0, 1, (N, D)).astype(np.float32)
+    n_near = int(part * N)
+    X[:n_near] += 40.0
+    means = 40.0 + rng.normal(0, 0.05, (100, D))
+    if part < 1.0:
+        means = np.concatenate([means, rng.normal(0, 0.5, (60, D))])
+    G = means.shape[0]
+    g = GMM().set_params(means, np.ones((G, D)), np.full(G, 1.0 / G)).debug_set(GMM_DEBUG_FP32_FORM, 2)
+    Xd = dev(X)
     g.em_iterate(Xd, 0, recompute_center=True)
     for _ in range(2):
         em_step_check(g, X, Xd)
