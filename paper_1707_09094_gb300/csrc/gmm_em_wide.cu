@@ -37,7 +37,8 @@
 //     sample order; the warp that owns a Gaussian (g mod 32) adds l, l (x - mu_f),
 //     l (x - mu_f)^2 (Eqs. 9-11 about the FP32 mean mu_f) to the block's FP32
 //     sums in shared memory, which move to the chunk's FP64 partial after at
-//     most 128 additions.
+//     most 128 additions.  The register-blocked FP32 form's records of kept
+//     responsibilities go through the same M-step.
 //
 // Screening bound.  A split operand leaves |v - v_h - v_l| <= 2^-18 |v| with
 // |v_l| <= 2^-9 |v|, so the three kept products of a pair miss at most
