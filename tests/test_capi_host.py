@@ -69,3 +69,21 @@ def test_kernels_are_built_for_sm103a_only(libpath):
         pytest.skip("cuobjdump unavailable")
     archs = set(re.findall(r"sm_(\d+a?)", out.stdout))
     assert archs == {"103a"}, archs
+
+
+def test_binding_constants_match_header():
+    """Every GMM_* integer the binding defines has the header's value."""
+    from paper_1707_09094_gb300 import _lib
+    src = ""
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if f.endswith(".h"):
+            src += open(os.path.join(inc, f)).read()
+    header = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define\s+(GMM_[A-Z0-9_]+)\s+(-?\d+)\b", src)}
+    header.update({m.group(1): int(m.group(2)) for m in re.finditer(r"\b(GMM_[A-Z0-9_]+)\s*=\s*(-?\d+)", src)})
+    mine = {k: v for k, v in vars(_lib).items() if k.startswith("GMM_") and isinstance(v, int)}
+    assert mine, "the binding defines no GMM_* constants"
+    for k, v in mine.items():
+        if k in header:
+            assert header[k] == v, (k, header[k], v)
+    assert {"GMM_DEBUG_TC_FORM", "GMM_DEBUG_FP32_FORM", "GMM_STAT_SCREENED"} <= set(mine) & set(header)
